@@ -1,0 +1,282 @@
+"""CPU oracle for the CDFCI column update (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library and never calls it.
+
+The numerical core is ``cdfci_oracle.c`` (plain serial C, FP64 with binary128
+scalars), loaded with ctypes:
+
+  * ``column_literal``  - <D'|H|D> by literal ladder-operator application of
+    Eq. (general-ham); the definition of a column.
+  * ``column_sc``       - the Slater-Condon rules of Eq. (entry).
+  * ``dense_H`` / ``sparse_H`` - H on a whole FCI space.
+  * ``ground_energy``   - smallest eigenvalue of H (LAPACK ``eigh`` on the dense
+    matrix, or ARPACK ``eigsh`` on the sparse one: library eigensolvers used
+    as one step).
+  * ``CDFCI``           - Algorithm 1 (m = 1) and Algorithm 2 (m > 1), serial.
+  * ``line_search``     - the appendix's Cardano + Newton step.
+  * ``rdm``             - spin-summed 1- and 2-RDMs by literal operator
+    application (Sec. "Optimal Orbital Selections").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cdfci_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+c_dp = ctypes.POINTER(ctypes.c_double)
+c_u64p = ctypes.POINTER(ctypes.c_uint64)
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C core into oracle/liboracle.so."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                        _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        L.orc_column_literal.restype = ctypes.c_int64
+        L.orc_column_literal.argtypes = [ctypes.c_int, c_dp, c_dp, ctypes.c_uint64, ctypes.c_uint64, c_u64p, c_dp, ctypes.c_int64]
+        L.orc_column_sc.restype = ctypes.c_int64
+        L.orc_column_sc.argtypes = L.orc_column_literal.argtypes
+        L.orc_diag.restype = ctypes.c_double
+        L.orc_diag.argtypes = [ctypes.c_int, c_dp, c_dp, ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_fci_dim.restype = ctypes.c_int64
+        L.orc_fci_dim.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_fci_dets.restype = ctypes.c_int
+        L.orc_fci_dets.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_u64p]
+        L.orc_fci_index.restype = ctypes.c_int64
+        L.orc_fci_index.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_dense_H.restype = ctypes.c_int
+        L.orc_dense_H.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_dp, c_dp]
+        L.orc_sparse_H.restype = ctypes.c_int64
+        L.orc_sparse_H.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_dp, c_i64p, c_i64p, c_dp, ctypes.c_int64]
+        L.orc_line_search.restype = ctypes.c_double
+        L.orc_line_search.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_sym_eig.restype = ctypes.c_int
+        L.orc_sym_eig.argtypes = [ctypes.c_int, c_dp, c_dp, c_dp]
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_dp, ctypes.c_uint64, ctypes.c_uint64,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_double]
+        L.orc_destroy.restype = None
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        L.orc_energy.restype = ctypes.c_double
+        L.orc_energy.argtypes = [ctypes.c_void_p]
+        L.orc_info.restype = None
+        L.orc_info.argtypes = [ctypes.c_void_p, c_dp]
+        L.orc_export.restype = ctypes.c_int64
+        L.orc_export.argtypes = [ctypes.c_void_p, c_u64p, c_dp, c_dp, ctypes.c_int64]
+        L.orc_last_step.restype = ctypes.c_int64
+        L.orc_last_step.argtypes = [ctypes.c_void_p, c_u64p, c_dp, ctypes.c_int64]
+        L.orc_candidates.restype = ctypes.c_int64
+        L.orc_candidates.argtypes = [ctypes.c_void_p, c_u64p, ctypes.c_int64]
+        L.orc_rdm.restype = ctypes.c_int
+        L.orc_rdm.argtypes = [ctypes.c_int, ctypes.c_int64, c_u64p, c_dp, c_dp, c_dp]
+        _lib = L
+    return _lib
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(c_dp)
+
+
+def _u(a: np.ndarray):
+    return a.ctypes.data_as(c_u64p)
+
+
+def _ints(h, g):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    return h, g
+
+
+def _column(fn, N, h, g, key) -> Tuple[np.ndarray, np.ndarray]:
+    h, g = _ints(h, g)
+    cap = 1 << 12
+    while True:
+        keys = np.zeros((cap, 2), dtype=np.uint64)
+        vals = np.zeros(cap)
+        n = fn(N, _d(h), _d(g), int(key[0]), int(key[1]), _u(keys), _d(vals), cap)
+        if n >= 0:
+            return keys[:n].copy(), vals[:n].copy()
+        if n == -1:
+            raise MemoryError("oracle column failed")
+        cap = -n
+
+
+def column_literal(N, h, g, key):
+    """All (D', <D'|H|D>) with a nonzero value, by literal operator application."""
+    return _column(lib().orc_column_literal, N, h, g, key)
+
+
+def column_sc(N, h, g, key):
+    """All (D', H_{D'D}) with a nonzero value, by the Slater-Condon rules of Eq. (entry)."""
+    return _column(lib().orc_column_sc, N, h, g, key)
+
+
+def diag(N, h, g, key) -> float:
+    h, g = _ints(h, g)
+    return lib().orc_diag(N, _d(h), _d(g), int(key[0]), int(key[1]))
+
+
+def fci_dim(N, na, nb) -> int:
+    return int(lib().orc_fci_dim(N, na, nb))
+
+
+def fci_dets(N, na, nb) -> np.ndarray:
+    dim = fci_dim(N, na, nb)
+    keys = np.zeros((dim, 2), dtype=np.uint64)
+    lib().orc_fci_dets(N, na, nb, _u(keys))
+    return keys
+
+
+def fci_index(N, na, nb, key) -> int:
+    return int(lib().orc_fci_index(N, na, nb, int(key[0]), int(key[1])))
+
+
+def dense_H(N, na, nb, h, g) -> np.ndarray:
+    h, g = _ints(h, g)
+    dim = fci_dim(N, na, nb)
+    H = np.zeros((dim, dim))
+    if lib().orc_dense_H(N, na, nb, _d(h), _d(g), _d(H)):
+        raise MemoryError("oracle dense_H failed")
+    return H
+
+
+def sparse_H(N, na, nb, h, g):
+    import scipy.sparse as sp
+    h, g = _ints(h, g)
+    dim = fci_dim(N, na, nb)
+    cap = max(1024, dim * 64)
+    while True:
+        rows = np.zeros(cap, dtype=np.int64)
+        cols = np.zeros(cap, dtype=np.int64)
+        vals = np.zeros(cap)
+        n = lib().orc_sparse_H(N, na, nb, _d(h), _d(g), rows.ctypes.data_as(c_i64p),
+                               cols.ctypes.data_as(c_i64p), _d(vals), cap)
+        if n >= 0:
+            return sp.csr_matrix((vals[:n], (rows[:n], cols[:n])), shape=(dim, dim))
+        if n == -1:
+            raise MemoryError("oracle sparse_H failed")
+        cap = -n
+
+
+def ground_energy(N, na, nb, h, g, dense_limit: int = 2500) -> float:
+    """Smallest eigenvalue of H over the FCI space (dense LAPACK or sparse ARPACK)."""
+    dim = fci_dim(N, na, nb)
+    if dim <= dense_limit:
+        return float(np.linalg.eigvalsh(dense_H(N, na, nb, h, g))[0])
+    from scipy.sparse.linalg import eigsh
+    Hs = sparse_H(N, na, nb, h, g)
+    w = eigsh(Hs, k=1, which="SA", tol=1e-14, ncv=min(dim - 1, 64), maxiter=100000,
+              v0=np.ones(dim) / np.sqrt(dim))[0]
+    return float(w[0])
+
+
+def line_search(v1: float, v2: float, v3: float) -> float:
+    """argmin_eta eta^4 + v3 eta^3 + v2 eta^2 + v1 eta (appendix: Cardano + Newton)."""
+    return float(lib().orc_line_search(v1, v2, v3))
+
+
+def sym_eig(A: np.ndarray):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    lib().orc_sym_eig(n, _d(A), _d(w), _d(V))
+    return w, V
+
+
+def rdm(N: int, keys: np.ndarray, c: np.ndarray):
+    """Spin-summed gamma[p,q] = sum_s <a+_ps a_qs> / c.c and
+    Gamma[p,q,r,s] = sum_{st} <a+_ps a+_rt a_st a_qs> / c.c (chemists' index order,
+    so that E = sum h gamma + 1/2 sum (pq|rs) Gamma)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    g1 = np.zeros((N, N))
+    g2 = np.zeros((N, N, N, N))
+    if lib().orc_rdm(N, len(c), _u(keys), _d(c), _d(g1), _d(g2)):
+        raise MemoryError("oracle rdm failed")
+    return g1, g2
+
+
+class CDFCI:
+    """Serial Algorithm 1 (m = 1) / Algorithm 2 (m > 1)."""
+
+    def __init__(self, N, na, nb, h, g, ref=(0, 0), tau=0.0, m=1, theta=0.9):
+        self.h, self.g = _ints(h, g)
+        self.N, self.na, self.nb, self.m = N, na, nb, m
+        self._p = lib().orc_create(N, na, nb, _d(self.h), _d(self.g), int(ref[0]), int(ref[1]),
+                                   float(tau), int(m), float(theta))
+        if not self._p:
+            raise ValueError("oracle create failed")
+
+    def step(self, n: int = 1):
+        r = lib().orc_step(self._p, int(n))
+        if r:
+            raise RuntimeError(f"oracle step failed ({r})")
+
+    def energy(self) -> float:
+        return float(lib().orc_energy(self._p))
+
+    def info(self) -> dict:
+        out = np.zeros(10)
+        lib().orc_info(self._p, _d(out))
+        k = ["mu", "alpha", "dx", "iterations", "entries", "nnz_c", "elements", "applied", "dropped",
+             "degenerate_steps"]
+        return {a: (float(v) if a in ("mu", "alpha", "dx") else int(v)) for a, v in zip(k, out)}
+
+    def export(self):
+        n = self.info()["entries"]
+        keys = np.zeros((n, 2), dtype=np.uint64)
+        c = np.zeros(n)
+        b = np.zeros(n)
+        lib().orc_export(self._p, _u(keys), _d(c), _d(b), n)
+        return keys, c, b
+
+    def last_step(self):
+        cap = max(self.m, 1)
+        keys = np.zeros((cap, 2), dtype=np.uint64)
+        eta = np.zeros(cap)
+        m = lib().orc_last_step(self._p, _u(keys), _d(eta), cap)
+        return keys[:m].copy(), eta[:m].copy()
+
+    def candidates(self):
+        cap = 1 << 16
+        while True:
+            keys = np.zeros((cap, 2), dtype=np.uint64)
+            n = lib().orc_candidates(self._p, _u(keys), cap)
+            if n >= 0:
+                return keys[:n].copy()
+            cap = -n
+
+    def close(self):
+        if self._p:
+            lib().orc_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
