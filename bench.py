@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the CDFCI column update on GB300: H elements/s into the hash table of b.
+
+Workload (one GPU): synthetic ab initio Hamiltonian, N = 24 spatial orbitals,
+6 alpha + 6 beta electrons, seed 2, 48 Cholesky vectors, aufbau start,
+compression tau = 1e-5, one coordinate per iteration (CDFCI, Algorithm 1),
+a 2^27-slot (4 GiB) device hash table.  Column length 16,471.
+
+A step is `iters_per_step` iterations of the whole hot path (choice, step size,
+column enumeration, Slater-Condon elements, compression, hash scatter,
+recalculation of b_i), i.e. one cdfci_step call.  The table (4 GiB) is larger
+than L2, so no flush is needed between steps.
+
+Extra keys: roofline of the fused column kernel, the CPU oracle as the
+baseline, end-to-end throughput through the C-ABI from host buffers, time to
+reach a stored exact energy within 1e-6 Ha on the 8-site chain, and SM clocks
+sampled during the timed region.
+
+Multi-GPU (torchrun): every rank runs an independent replica of the same solve
+(one CDFCI trajectory does not shard without an exchange step); value = all
+ranks' elements / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES_PER_ELEMENT = 40      # 16 B key compare + 8 B c read + 8 B b read + 8 B b write
+WORKLOAD = dict(name="abinitio_N24_6a6b_seed2", N=24, n_alpha=6, n_beta=6, seed=2, tau=1e-5, log2_capacity=27, m=1)
+KERNEL_SOURCES = ["paper_2605_04483_gb300/csrc/cdfci_kernels.cu", "paper_2605_04483_gb300/csrc/cdfci_internal.cuh"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_cd_iter_abinitio_N24.txt")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    try:
+        vals = {}
+        for line in open(PROFILE_SUMMARY):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_hash") != kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def load_reference_energy(name: str) -> float:
+    for line in open(os.path.join(ROOT, "tests", "golden", "reference_energies.txt")):
+        if line.startswith(name + " "):
+            return float(line.split()[-1])
+    raise KeyError(name)
+
+
+def cpu_baseline(seconds: float) -> dict:
+    """The CPU oracle's serial CDFCI on the same workload, one host core, bounded sample."""
+    import oracle
+    from paper_2605_04483_gb300 import inputs
+    w = inputs.config2()
+    o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, (0, 0), WORKLOAD["tau"], 1)
+    o.step(20)
+    e0 = o.info()["elements"]
+    it = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(20)
+        it += 20
+    dt = time.perf_counter() - t0
+    el = o.info()["elements"] - e0
+    o.close()
+    return {"value": el / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"{it} CDFCI iterations of the same workload after 20 warm-up iterations "
+                      f"({dt:.1f} s, serial C oracle, 1 thread)"}
+
+
+def run_reference_arm(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2605_04483_gb300 import inputs
+    w = inputs.config2()
+    iters = args.ref_iters_per_step
+    o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, (0, 0), WORKLOAD["tau"], 1)
+    for _ in range(args.warmup):
+        o.step(iters)
+    e0 = o.info()["elements"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(iters)
+    dt = time.perf_counter() - t0
+    el = o.info()["elements"] - e0
+    value = el / dt
+    line = {"impl": "reference", "metric": "H elements/s into hash b (CDFCI, Algorithm 1)", "value": value,
+            "unit": "elements/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=1",
+                       "iters_per_step": iters, "note": "CPU oracle (serial C), bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps x {iters} iterations after {args.warmup} warm-up steps"},
+            "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--iters-per-step", type=int, default=4000)
+    ap.add_argument("--ref-iters-per-step", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true", help="only the device-timed value (for profiling)")
+    ap.add_argument("--log2-capacity", type=int, default=WORKLOAD["log2_capacity"],
+                    help="hash table size (smaller only for profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        run_reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2605_04483_gb300 import api, inputs
+
+    w = inputs.config2()
+    h_host = torch.tensor(w.h).pin_memory()
+    g_host = torch.tensor(w.g).pin_memory()
+    h_dev = h_host.cuda()
+    g_dev = g_host.cuda()
+    stream = torch.cuda.Stream()
+    params = dict(log2_capacity=args.log2_capacity, z_threshold=WORKLOAD["tau"],
+                  cuda_stream=stream.cuda_stream)
+    ips = args.iters_per_step
+
+    # ---- device-resident throughput -------------------------------------------------
+    s = api.Solver(h_dev, g_dev, w.N, w.n_alpha, w.n_beta, **params)
+    for _ in range(args.warmup):
+        s.step(ips)
+    st0 = s.stats()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+    for _ in range(args.steps):
+        st = s.step(ips)
+    with torch.cuda.stream(stream):
+        ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    elements = st["elements"] - st0["elements"]
+    launches = st["iterations"] - st0["iterations"]
+    if world > 1:
+        t = torch.tensor([ms, float(elements)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_max, total_el = float(tmax[0]), float(tsum[1])
+    else:
+        ms_max, total_el = ms, float(elements)
+    value = total_el / (ms_max * 1e-3)
+    final_energy = st["energy"]
+    s.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    avg_launch_s = ms * 1e-3 / max(launches, 1)
+    el_per_launch = elements / max(launches, 1)
+    achieved = el_per_launch * ALGO_BYTES_PER_ELEMENT / avg_launch_s / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_cd_iter (fused column update, one launch per iteration)",
+                "algorithmic_bytes_per_launch": el_per_launch * ALGO_BYTES_PER_ELEMENT,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
+
+    line = {"metric": "H elements/s into hash b (CDFCI, Algorithm 1)", "value": value, "unit": "elements/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=1, 2^{args.log2_capacity}-slot table",
+                       "iters_per_step": ips, "column_length": 16471,
+                       "l2": "inputs larger than L2 (4 GiB hash table), no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk,
+            "energy_after_timed_steps": final_energy,
+            "us_per_iteration": ms / max(launches, 1) * 1e3}
+
+    if not args.no_extras:
+        # ---- end to end through the C-ABI from pinned host buffers ----------------------
+        # each step: create from host h, g (H2D copy, table set-up, initial column), ips
+        # iterations, the stats (energy) read back to the host; elements counted as above
+        nrep = 3
+        e_el = 0
+        t0 = time.perf_counter()
+        for _ in range(nrep):
+            s2 = api.Solver(h_host, g_host, w.N, w.n_alpha, w.n_beta, **params)
+            st2 = s2.step(ips)
+            e_el += st2["elements"]
+            s2.close()
+        e_dt = time.perf_counter() - t0
+        line["e2e"] = {"value": e_el / e_dt, "unit": "elements/s",
+                       "h2d_bytes_per_step": int(h_host.numel() * 8 + g_host.numel() * 8),
+                       "d2h_bytes_per_step": int(__import__("ctypes").sizeof(api.cdfci_stats)),
+                       "note": f"{nrep} steps of create(host h, g) + {ips} iterations + stats read; wall clock"}
+        # ---- time to E within 1e-6 Ha on the 8-site chain (stored exact energy) ------------
+        wc = inputs.config1()
+        E_ref = load_reference_energy("config1_hubbard_chain8_obc_U4")
+        s3 = api.Solver(wc.h, wc.g, wc.N, wc.n_alpha, wc.n_beta, log2_capacity=16,
+                        ref_alpha=int(wc.ref[0]), ref_beta=int(wc.ref[1]))
+        t0 = time.perf_counter()
+        it = 0
+        reached = None
+        while it < 400000:
+            st3 = s3.step(1000)
+            it += 1000
+            if abs(st3["energy"] - E_ref) <= 1e-6:
+                reached = time.perf_counter() - t0
+                break
+        s3.close()
+        line["time_to_E"] = {"workload": "hubbard_chain8_obc_U4 (FCI dim 4,900), m=1", "threshold_ha": 1e-6,
+                             "seconds": reached, "iterations": it, "check_every": 1000, "E_ref": E_ref}
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * cdfci.h - C-ABI of libcdfci, the GB300 (sm_103a) column-update engine for
+ * coordinate-descent FCI (CDFCI, Algorithm 1; mCDFCI, Algorithm 2 of the
+ * paper "CDFCI: High-Performance Parallel Software for Quantum Many-Body
+ * Eigenvalue Problems").
+ *
+ * Model.  The Hamiltonian is Eq. (general-ham) over N spatial orbitals with
+ * real integrals:
+ *   h : N*N doubles, row-major, h[p*N+q] = h_pq (Eq. 1int), symmetric;
+ *   g : N^4 doubles, row-major, g[((p*N+q)*N+r)*N+s] = (pq|rs) in chemists'
+ *       order, 8-fold symmetric; the physicists' v_pqrs of Eq. (2int) is (pr|qs).
+ * A determinant is a key of two 64-bit words {A, B}: bit p of A means spatial
+ * orbital p holds an alpha electron, bit p of B a beta electron.  Signs use
+ * the Jordan-Wigner order in which every alpha spin-orbital precedes every
+ * beta one.  N <= 63 (bit 63 is reserved by the table).
+ *
+ * Conventions for every call:
+ *   - Return value 0 = success, a negative CDFCI_ERR_* code otherwise; the
+ *     message of the last failure on the calling thread is cdfci_last_error().
+ *   - Pointer arguments may be host or device memory (the library asks the
+ *     CUDA driver which); the library copies what it needs and never keeps a
+ *     caller pointer.  The caller owns every buffer it passes.
+ *   - The library owns all memory behind a handle and frees it in
+ *     cdfci_destroy.  No call aborts the process, traps or waits without
+ *     bound on the GPU: every device-side loop is bounded and reports
+ *     CDFCI_ERR_TABLE_FULL / CDFCI_ERR_TIMEOUT / CDFCI_ERR_NONFINITE instead.
+ *   - Energies are Hartree (the unit of h and g), FP64.
+ */
+#ifndef CDFCI_H
+#define CDFCI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDFCI_OK                 0
+#define CDFCI_ERR_ARG           -1   /* invalid argument (sizes, symmetry, start determinant) */
+#define CDFCI_ERR_NONFINITE     -2   /* NaN/Inf in the integrals or in a step */
+#define CDFCI_ERR_TABLE_FULL    -3   /* stored determinants exceed max_load * capacity, or probe limit hit */
+#define CDFCI_ERR_TIMEOUT       -4   /* a bounded device wait gave up */
+#define CDFCI_ERR_CUDA          -5   /* a CUDA runtime call failed */
+#define CDFCI_ERR_UNIMPLEMENTED -6   /* entry point not available in this build */
+#define CDFCI_ERR_NOMEM         -7   /* host or device allocation failed */
+#define CDFCI_ERR_CAPACITY      -8   /* caller's output buffer too small (required size returned) */
+#define CDFCI_ERR_NOT_NEGATIVE  -9   /* reduced problem has no negative eigenvalue (needs E0 < 0) */
+
+typedef struct cdfci_ctx *cdfci_handle;
+
+/*
+ * Solver options (Sec. "Example Usage", JSON block solver/cdfci; Sec.
+ * "Solvers for Ground and Excited States" for the stopping rule).
+ */
+typedef struct {
+    int32_t  num_coordinates;  /* m: 1 = CDFCI (Alg. 1), >1 = mCDFCI (Alg. 2, m <= 1024) */
+    int32_t  log2_capacity;    /* hash table holds 2^log2_capacity slots of 32 bytes */
+    double   z_threshold;      /* tau of the compression rule (Sec. CDFCI); 0 = none */
+    double   max_load;         /* stored determinants <= max_load * capacity (default 0.79) */
+    double   dx_damping;       /* theta of the damped accumulator d <- theta d + (1-theta)|eta| */
+    double   dx_threshold;     /* stop once d < this (0 = run the requested iterations) */
+    uint64_t ref_alpha;        /* start determinant {A, B}; both 0 = aufbau on h_pp */
+    uint64_t ref_beta;
+    int32_t  block_threads;    /* threads per CTA of the column kernel (0 = default 256) */
+    int32_t  grid_blocks;      /* CTAs of the column kernel (0 = sized from the column length) */
+    int32_t  graph_chunk;      /* iterations per captured CUDA graph (0 = default 64) */
+    int32_t  deterministic;    /* 1 = fixed-order reductions everywhere (default 1) */
+    void    *cuda_stream;      /* cudaStream_t the work is queued on; NULL = a library stream */
+} cdfci_params;
+
+/* Progress report (the console row of Sec. "Expected Console Output"). */
+typedef struct {
+    int64_t iterations;        /* completed coordinate (block) updates */
+    double  energy;            /* alpha / mu: Rayleigh-quotient estimate (Alg. 1/2, last line) */
+    double  mu;                /* c^T c (leading double of the double-double value) */
+    double  alpha;             /* c^T H c accumulated by Eq. (update-var) (leading double) */
+    double  dx;                /* damped step accumulator */
+    int64_t nnz_c;             /* |x|_0: stored coefficients that are nonzero */
+    int64_t n_slots;           /* |z|_0: determinants stored in the table */
+    int64_t last_column;       /* |H_i|_0: nonzero elements of the last processed column(s) */
+    int64_t elements;          /* cumulative nonzero H elements evaluated by column updates */
+    int64_t applied;           /* ... of which passed the compression rule and updated b */
+    int64_t dropped;           /* ... of which were dropped by the compression rule */
+    int64_t inserted;          /* cumulative new table entries */
+    double  load;              /* n_slots / capacity */
+    int32_t status;            /* sticky device status (0 or a CDFCI_ERR_* code) */
+    int32_t converged;         /* 1 once dx < dx_threshold */
+} cdfci_stats;
+
+/* Fills *p with the defaults (m = 1, 2^22 slots, tau = 0, max_load = 0.79,
+   theta = 0.9, no early stop, aufbau start, deterministic). */
+void cdfci_default_params(cdfci_params *p);
+
+/*
+ * Build a solver: copies h and g to the device, allocates the hash table,
+ * and performs the initialisation of Algorithms 1 and 2: c = e_ref,
+ * b = H c (one column, compression applied), mu = 1, alpha = H_ref,ref, the
+ * candidate set = that column.  The start determinant is params->ref_{alpha,
+ * beta} or, when both are 0, the aufbau determinant of h_pp (smallest
+ * diagonal first, ties to the lower index) standing in for the Hartree-Fock
+ * reference of Sec. "Example Usage".
+ * Errors: CDFCI_ERR_ARG (N, n_alpha, n_beta out of range, a start key with
+ * the wrong electron counts, asymmetric h or g), CDFCI_ERR_NONFINITE,
+ * CDFCI_ERR_NOMEM, CDFCI_ERR_CUDA.  *out is NULL on failure.
+ */
+int cdfci_create(const double *h, const double *g, int N, int n_alpha, int n_beta,
+                 const cdfci_params *params, cdfci_handle *out);
+
+/*
+ * Run n_iter iterations of Algorithm 1 (m = 1: Gauss-Southwell choice over the
+ * last column, Eq. choose-i; exact line search, appendix; Eq. update-var with
+ * compression; recalculation of b_i, Eq. recalculate-b) or Algorithm 2
+ * (m > 1: top-m choice, Eq. choose-I; (m+1)-dimensional reduced eigenproblem;
+ * c <- gamma c + E_I eta, b <- gamma b + H_{:,I} eta; recalculation of b_I).
+ * Work is queued on the handle's stream; the call returns after the stats
+ * are copied back (stats may be NULL).  Stops early once dx < dx_threshold.
+ */
+int cdfci_step(cdfci_handle h, int64_t n_iter, cdfci_stats *stats);
+
+/*
+ * Energy of the current vector: mode 0 = alpha / mu (double-double ratio,
+ * Alg. 1 last line); mode 1 = exact Rayleigh quotient sum_i c_i (Hc)_i / c.c
+ * recomputed from the stored c with fresh columns (independent of b).
+ */
+int cdfci_energy(cdfci_handle h, int mode, double *E);
+
+/*
+ * get_column of Sec. "The Hamiltonian Class": all (D', H_{D',D}) with a
+ * nonzero FP64 value (Eq. entry), diagonal included, as an unordered list.
+ * key = {A, B} (host or device, 2 words).  keys_out (2 words per entry) and
+ * vals_out hold up to cap entries; *n_out receives the column length (host
+ * pointer).  Returns CDFCI_ERR_CAPACITY when cap is too small (nothing written).
+ */
+int cdfci_get_column(cdfci_handle h, const uint64_t *key, uint64_t *keys_out, double *vals_out,
+                     int64_t cap, int64_t *n_out);
+
+/*
+ * All stored determinants with their true (unscaled) c and b values, in
+ * table order.  keys (2 words per entry), c, b hold up to cap entries (c or b
+ * may be NULL); *n_out = number stored.  CDFCI_ERR_CAPACITY if cap is too small.
+ */
+int cdfci_export(cdfci_handle h, uint64_t *keys, double *c, double *b, int64_t cap, int64_t *n_out);
+
+/*
+ * The coordinates chosen by the most recent iteration and their step sizes
+ * (eta, in true units), up to cap entries; *m_out receives the count.
+ */
+int cdfci_last_step(cdfci_handle h, uint64_t *keys, double *eta, int64_t cap, int64_t *m_out);
+
+/* Current stats without running an iteration. */
+int cdfci_get_stats(cdfci_handle h, cdfci_stats *stats);
+
+/* Frees everything the handle owns (safe on NULL). */
+void cdfci_destroy(cdfci_handle h);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *cdfci_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDFCI_H */

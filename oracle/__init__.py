@@ -90,6 +90,8 @@ def lib():
         L.orc_last_step.argtypes = [ctypes.c_void_p, c_u64p, c_dp, ctypes.c_int64]
         L.orc_candidates.restype = ctypes.c_int64
         L.orc_candidates.argtypes = [ctypes.c_void_p, c_u64p, ctypes.c_int64]
+        L.orc_step_choice.restype = ctypes.c_int
+        L.orc_step_choice.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, c_dp, c_dp]
         L.orc_rdm.restype = ctypes.c_int
         L.orc_rdm.argtypes = [ctypes.c_int, ctypes.c_int64, c_u64p, c_dp, c_dp, c_dp]
         _lib = L
@@ -235,6 +237,15 @@ class CDFCI:
         r = lib().orc_step(self._p, int(n))
         if r:
             raise RuntimeError(f"oracle step failed ({r})")
+
+    def step_choice(self, key):
+        """One Algorithm-1 step on the given coordinate; returns (|g| of it, max |g|) before the step."""
+        gc = ctypes.c_double()
+        gm = ctypes.c_double()
+        r = lib().orc_step_choice(self._p, int(key[0]), int(key[1]), ctypes.byref(gc), ctypes.byref(gm))
+        if r:
+            raise RuntimeError(f"oracle step_choice failed ({r})")
+        return gc.value, gm.value
 
     def energy(self) -> float:
         return float(lib().orc_energy(self._p))

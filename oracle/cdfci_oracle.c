@@ -1012,3 +1012,30 @@ int orc_rdm(int N, int64_t n, const uint64_t *keys, const double *c, double *g1,
     dmap_free(&pos);
     return 0;
 }
+
+/*
+ * Algorithm 1 step whose coordinate is given (for comparing runs whose
+ * argmax differs only at exact ties of |4 b + 4 mu c|).  On return g_choice
+ * is |4 b_i + 4 mu c_i| of the given coordinate and g_max the largest over the
+ * candidates, both before the step; returns -5 if the key is not a candidate.
+ */
+int orc_step_choice(orc_state *st, uint64_t A, uint64_t B, double *g_choice, double *g_max) {
+    if (st->m != 1) return -1;
+    det_t want = {A, B};
+    int64_t pick = -1;
+    double gm = 0.0;
+    for (int64_t t = 0; t < st->ncand; t++) {
+        int64_t k = st->cand[t];
+        double gk = grad_abs(st, k);
+        if (gk > gm) gm = gk;
+        if (st->key[k].a == want.a && st->key[k].b == want.b) pick = k;
+    }
+    *g_max = gm;
+    if (pick < 0) return -5;
+    *g_choice = grad_abs(st, pick);
+    /* move the chosen candidate to the front and run the usual step on a
+       one-element candidate list */
+    st->cand[0] = pick;
+    st->ncand = 1;
+    return step_cd(st);
+}

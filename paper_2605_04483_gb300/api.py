@@ -1,0 +1,217 @@
+"""Thin Python binding of libcdfci (include/cdfci.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays may be
+numpy arrays (host memory) or torch tensors on the GPU (device memory); the
+library detects which.  Nothing here computes any part of the method, and
+there is no fallback: if libcdfci.so is missing or cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcdfci.so")
+
+CDFCI_OK = 0
+ERRORS = {-1: "ARG", -2: "NONFINITE", -3: "TABLE_FULL", -4: "TIMEOUT", -5: "CUDA", -6: "UNIMPLEMENTED",
+          -7: "NOMEM", -8: "CAPACITY", -9: "NOT_NEGATIVE"}
+
+
+class cdfci_params(ctypes.Structure):
+    _fields_ = [("num_coordinates", ctypes.c_int32), ("log2_capacity", ctypes.c_int32),
+                ("z_threshold", ctypes.c_double), ("max_load", ctypes.c_double),
+                ("dx_damping", ctypes.c_double), ("dx_threshold", ctypes.c_double),
+                ("ref_alpha", ctypes.c_uint64), ("ref_beta", ctypes.c_uint64),
+                ("block_threads", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+                ("graph_chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class cdfci_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("energy", ctypes.c_double), ("mu", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("dx", ctypes.c_double), ("nnz_c", ctypes.c_int64),
+                ("n_slots", ctypes.c_int64), ("last_column", ctypes.c_int64), ("elements", ctypes.c_int64),
+                ("applied", ctypes.c_int64), ("dropped", ctypes.c_int64), ("inserted", ctypes.c_int64),
+                ("load", ctypes.c_double), ("status", ctypes.c_int32), ("converged", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class CdfciError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libcdfci error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libcdfci (raises if the CUDA library was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, u64p, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p
+        L.cdfci_default_params.argtypes = [ctypes.POINTER(cdfci_params)]
+        L.cdfci_default_params.restype = None
+        L.cdfci_create.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cdfci_params),
+                                   ctypes.POINTER(vp)]
+        L.cdfci_step.argtypes = [vp, i64, ctypes.POINTER(cdfci_stats)]
+        L.cdfci_get_stats.argtypes = [vp, ctypes.POINTER(cdfci_stats)]
+        L.cdfci_energy.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        L.cdfci_get_column.argtypes = [vp, u64p, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.cdfci_export.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.cdfci_last_step.argtypes = [vp, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.cdfci_destroy.argtypes = [vp]
+        L.cdfci_destroy.restype = None
+        L.cdfci_last_error.argtypes = []
+        L.cdfci_last_error.restype = ctypes.c_char_p
+        for name in ("cdfci_create", "cdfci_step", "cdfci_get_stats", "cdfci_energy", "cdfci_get_column",
+                     "cdfci_export", "cdfci_last_step"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != CDFCI_OK:
+        raise CdfciError(rc, lib().cdfci_last_error().decode())
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def cdfci_default_params(**overrides) -> cdfci_params:
+    p = cdfci_params()
+    lib().cdfci_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def cdfci_create(h, g, N: int, n_alpha: int, n_beta: int, params: Optional[cdfci_params] = None) -> int:
+    handle = ctypes.c_void_p()
+    p = params if params is not None else cdfci_default_params()
+    _check(lib().cdfci_create(_ptr(h), _ptr(g), N, n_alpha, n_beta, ctypes.byref(p), ctypes.byref(handle)))
+    return handle.value
+
+
+def cdfci_step(handle: int, n_iter: int) -> dict:
+    s = cdfci_stats()
+    _check(lib().cdfci_step(handle, int(n_iter), ctypes.byref(s)))
+    return s.as_dict()
+
+
+def cdfci_get_stats(handle: int) -> dict:
+    s = cdfci_stats()
+    _check(lib().cdfci_get_stats(handle, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def cdfci_energy(handle: int, mode: int = 0) -> float:
+    e = ctypes.c_double()
+    _check(lib().cdfci_energy(handle, int(mode), ctypes.byref(e)))
+    return e.value
+
+
+def cdfci_get_column(handle: int, key, cap: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray]:
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64).reshape(2))
+    n = ctypes.c_int64()
+    if cap is None:
+        rc = lib().cdfci_get_column(handle, _ptr(k), None, None, 0, ctypes.byref(n))
+        if rc not in (CDFCI_OK, -8):
+            _check(rc)
+        cap = n.value
+    keys = np.zeros((max(cap, 1), 2), dtype=np.uint64)
+    vals = np.zeros(max(cap, 1))
+    _check(lib().cdfci_get_column(handle, _ptr(k), _ptr(keys), _ptr(vals), cap, ctypes.byref(n)))
+    return keys[:n.value], vals[:n.value]
+
+
+def cdfci_export(handle: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    n = ctypes.c_int64()
+    rc = lib().cdfci_export(handle, None, None, None, 0, ctypes.byref(n))
+    if rc not in (CDFCI_OK, -8):
+        _check(rc)
+    cap = n.value
+    keys = np.zeros((max(cap, 1), 2), dtype=np.uint64)
+    c = np.zeros(max(cap, 1))
+    b = np.zeros(max(cap, 1))
+    _check(lib().cdfci_export(handle, _ptr(keys), _ptr(c), _ptr(b), cap, ctypes.byref(n)))
+    return keys[:n.value], c[:n.value], b[:n.value]
+
+
+def cdfci_last_step(handle: int, cap: int = 1024) -> Tuple[np.ndarray, np.ndarray]:
+    keys = np.zeros((cap, 2), dtype=np.uint64)
+    eta = np.zeros(cap)
+    m = ctypes.c_int64()
+    _check(lib().cdfci_last_step(handle, _ptr(keys), _ptr(eta), cap, ctypes.byref(m)))
+    return keys[:m.value], eta[:m.value]
+
+
+def cdfci_destroy(handle: int) -> None:
+    if handle:
+        lib().cdfci_destroy(handle)
+
+
+def cdfci_last_error() -> str:
+    return lib().cdfci_last_error().decode()
+
+
+class Solver:
+    """Owning wrapper around a handle (convenience for tests and the benchmark)."""
+
+    def __init__(self, h, g, N, n_alpha, n_beta, **params):
+        self.p = cdfci_default_params(**params)
+        self.handle = cdfci_create(np.ascontiguousarray(h, dtype=np.float64) if isinstance(h, np.ndarray) else h,
+                                   np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g,
+                                   N, n_alpha, n_beta, self.p)
+
+    def step(self, n: int) -> dict:
+        return cdfci_step(self.handle, n)
+
+    def stats(self) -> dict:
+        return cdfci_get_stats(self.handle)
+
+    def energy(self, mode: int = 0) -> float:
+        return cdfci_energy(self.handle, mode)
+
+    def column(self, key):
+        return cdfci_get_column(self.handle, key)
+
+    def export(self):
+        return cdfci_export(self.handle)
+
+    def last_step(self):
+        return cdfci_last_step(self.handle)
+
+    def close(self):
+        if self.handle:
+            cdfci_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,437 @@
+// Host side of the libcdfci C-ABI (include/cdfci.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cdfci.h"
+#include "cdfci_internal.cuh"
+#include "cdfci_kernels.h"
+
+using namespace cdfci;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(CDFCI_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaMemcpyKind kind_to_device(const void *src) {
+    return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+long long binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+std::vector<unsigned short> pair_table(int n) {
+    std::vector<unsigned short> t;
+    for (int j = 1; j < n; ++j)
+        for (int i = 0; i < j; ++i) t.push_back((unsigned short)(i | (j << 8)));
+    return t;
+}
+
+}  // namespace
+
+struct cdfci_ctx {
+    cdfci_params prm;
+    int N, na, nb;
+    Problem P;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device buffers
+    double *d_h = nullptr, *d_g = nullptr, *d_J = nullptr, *d_K = nullptr;
+    unsigned short *d_pairs = nullptr;
+    Slot *d_table = nullptr;
+    IterState *d_st = nullptr;
+    CdPartial *d_part = nullptr;
+    int *d_flags = nullptr;                      // [0] status, [1] has_doubles
+    unsigned long long *d_counter = nullptr;     // scratch counter for compaction kernels
+    unsigned long long *d_colkeys = nullptr;     // get_column staging (2 * nh)
+    double *d_colvals = nullptr;
+    IterState *h_st = nullptr;                   // pinned copy of the state
+    int grid = 1;
+    int chunk = 64;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+void free_ctx(cdfci_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    cudaFree(c->d_h); cudaFree(c->d_g); cudaFree(c->d_J); cudaFree(c->d_K);
+    cudaFree(c->d_pairs); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part);
+    cudaFree(c->d_flags); cudaFree(c->d_counter); cudaFree(c->d_colkeys); cudaFree(c->d_colvals);
+    if (c->h_st) cudaFreeHost(c->h_st);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
+    CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const IterState &t = *c->h_st;
+    if (s) {
+        s->iterations = t.iterations;
+        s->energy = t.energy;
+        s->mu = t.mu.hi;
+        s->alpha = t.alpha.hi;
+        s->dx = t.dx;
+        s->nnz_c = t.nnz_c;
+        s->n_slots = t.n_slots;
+        s->last_column = t.last_column;
+        s->elements = t.elements;
+        s->applied = t.applied;
+        s->dropped = t.dropped;
+        s->inserted = t.inserted;
+        s->load = (double)t.n_slots / (double)c->P.capacity;
+        s->status = t.status;
+        s->converged = t.done;
+    }
+    if (t.status != 0) {
+        const char *what = t.status == CDFCI_ERR_TABLE_FULL ? "hash table full (raise log2_capacity or z_threshold)"
+                           : t.status == CDFCI_ERR_NONFINITE ? "non-finite value in an update"
+                           : t.status == CDFCI_ERR_TIMEOUT   ? "bounded device wait expired"
+                                                             : "device error";
+        return fail(t.status, "%s", what);
+    }
+    return CDFCI_OK;
+}
+
+int build_graph(cdfci_ctx *c) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < c->chunk; ++i) {
+        cudaError_t e = launch_cd_iter(c->P, c->d_st, c->d_part, c->grid, c->stream);
+        if (e != cudaSuccess) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(c->stream, &junk);
+            if (junk) cudaGraphDestroy(junk);
+            return fail(CDFCI_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+        }
+    }
+    CK(cudaStreamEndCapture(c->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return CDFCI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+#define CDFCI_API __attribute__((visibility("default")))
+
+CDFCI_API void cdfci_default_params(cdfci_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->num_coordinates = 1;
+    p->log2_capacity = 22;
+    p->z_threshold = 0.0;
+    p->max_load = 0.79;
+    p->dx_damping = 0.9;
+    p->dx_threshold = 0.0;
+    p->deterministic = 1;
+}
+
+CDFCI_API const char *cdfci_last_error(void) { return g_last_error.c_str(); }
+
+CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha, int n_beta, const cdfci_params *params,
+                 cdfci_handle *out) {
+    if (!out) return fail(CDFCI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!h || !g) return fail(CDFCI_ERR_ARG, "h or g is NULL");
+    if (N < 1 || N > kMaxN) return fail(CDFCI_ERR_ARG, "N = %d outside [1, %d]", N, kMaxN);
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N || n_alpha + n_beta == 0)
+        return fail(CDFCI_ERR_ARG, "electron counts (%d, %d) invalid for N = %d", n_alpha, n_beta, N);
+    cdfci_params prm;
+    if (params) prm = *params; else cdfci_default_params(&prm);
+    if (prm.num_coordinates != 1)
+        return fail(CDFCI_ERR_UNIMPLEMENTED, "num_coordinates = %d: only m = 1 is available", prm.num_coordinates);
+    if (prm.log2_capacity < 4 || prm.log2_capacity > 34)
+        return fail(CDFCI_ERR_ARG, "log2_capacity = %d outside [4, 34]", prm.log2_capacity);
+    if (!(prm.max_load > 0.0 && prm.max_load <= 0.95)) return fail(CDFCI_ERR_ARG, "max_load must be in (0, 0.95]");
+    if (!(prm.z_threshold >= 0.0) || !std::isfinite(prm.z_threshold)) return fail(CDFCI_ERR_ARG, "z_threshold invalid");
+    if (!(prm.dx_damping >= 0.0 && prm.dx_damping < 1.0)) return fail(CDFCI_ERR_ARG, "dx_damping must be in [0, 1)");
+    unsigned long long refA = prm.ref_alpha, refB = prm.ref_beta;
+    const unsigned long long full = N == 64 ? ~0ull : ((1ull << N) - 1ull);
+    if (refA != 0ull || refB != 0ull) {
+        if ((refA & ~full) || (refB & ~full) || __builtin_popcountll(refA) != n_alpha ||
+            __builtin_popcountll(refB) != n_beta)
+            return fail(CDFCI_ERR_ARG, "start determinant does not match N, n_alpha, n_beta");
+    }
+
+    cdfci_ctx *c = new (std::nothrow) cdfci_ctx();
+    if (!c) return fail(CDFCI_ERR_NOMEM, "host allocation failed");
+    c->prm = prm;
+    c->N = N; c->na = n_alpha; c->nb = n_beta;
+    int rc = CDFCI_OK;
+    auto bail = [&](int code) { free_ctx(c); return code; };
+
+    if (prm.cuda_stream) {
+        c->stream = (cudaStream_t)prm.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(CDFCI_ERR_CUDA, "stream creation failed"));
+        c->own_stream = true;
+    }
+    cudaStream_t s = c->stream;
+    const size_t n2 = (size_t)N * N, n4 = n2 * n2;
+
+    Problem &P = c->P;
+    std::memset(&P, 0, sizeof(P));
+    P.N = N; P.na = n_alpha; P.nb = n_beta; P.va = N - n_alpha; P.vb = N - n_beta;
+    P.ca2 = (int)binom(P.na, 2); P.cb2 = (int)binom(P.nb, 2);
+    P.cva2 = (int)binom(P.va, 2); P.cvb2 = (int)binom(P.vb, 2);
+    P.seg[0] = 1;
+    P.seg[1] = P.seg[0] + (long long)P.na * P.va;
+    P.seg[2] = P.seg[1] + (long long)P.nb * P.vb;
+    P.seg[3] = P.seg[2] + (long long)P.ca2 * P.cva2;
+    P.seg[4] = P.seg[3] + (long long)P.cb2 * P.cvb2;
+    P.seg[5] = P.seg[4] + (long long)P.na * P.va * P.nb * P.vb;
+    P.nh = P.seg[5];
+    P.capacity = 1ll << prm.log2_capacity;
+    P.mask = (unsigned long long)P.capacity - 1ull;
+    P.max_entries = (long long)std::floor(prm.max_load * (double)P.capacity);
+    P.max_probe = (int)std::min<long long>(P.capacity, 1 << 16);
+    P.tau = prm.z_threshold;
+    P.theta = prm.dx_damping;
+    P.dx_threshold = prm.dx_threshold;
+
+    // integrals and derived tables
+    if (cudaMalloc(&c->d_h, n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_g, n4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_J, n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_K, n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_flags, 4 * sizeof(int)) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_NOMEM, "device allocation of the integrals failed"));
+    if (cudaMemcpyAsync(c->d_h, h, n2 * sizeof(double), kind_to_device(h), s) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_g, g, n4 * sizeof(double), kind_to_device(g), s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_CUDA, "copy of the integrals failed"));
+    if (launch_setup(c->d_h, c->d_g, N, c->d_J, c->d_K, c->d_flags, c->d_flags + 1, s) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_CUDA, "set-up kernels failed to launch"));
+    int flags[4];
+    if (cudaMemcpyAsync(flags, c->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_CUDA, "set-up failed"));
+    if (flags[0] == CDFCI_ERR_NONFINITE) return bail(fail(CDFCI_ERR_NONFINITE, "h or g holds NaN/Inf"));
+    if (flags[0] != 0) return bail(fail(CDFCI_ERR_ARG, "h is not symmetric or g is not 8-fold symmetric"));
+    P.doubles_vanish = flags[1] ? 0 : 1;
+
+    // pair tables: occupied alpha, occupied beta, virtual alpha, virtual beta
+    std::vector<unsigned short> poa = pair_table(P.na), pob = pair_table(P.nb), pva = pair_table(P.va),
+                                pvb = pair_table(P.vb);
+    size_t npairs = poa.size() + pob.size() + pva.size() + pvb.size() + 1;
+    std::vector<unsigned short> all;
+    all.reserve(npairs);
+    all.insert(all.end(), poa.begin(), poa.end());
+    all.insert(all.end(), pob.begin(), pob.end());
+    all.insert(all.end(), pva.begin(), pva.end());
+    all.insert(all.end(), pvb.begin(), pvb.end());
+    all.push_back(0);
+    if (cudaMalloc(&c->d_pairs, all.size() * sizeof(unsigned short)) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_NOMEM, "device allocation failed"));
+    if (cudaMemcpyAsync(c->d_pairs, all.data(), all.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return bail(fail(CDFCI_ERR_CUDA, "copy of pair tables failed"));
+    P.pair_oa = c->d_pairs;
+    P.pair_ob = P.pair_oa + poa.size();
+    P.pair_va = P.pair_ob + pob.size();
+    P.pair_vb = P.pair_va + pva.size();
+    P.h = c->d_h; P.g = c->d_g; P.J = c->d_J; P.K = c->d_K;
+
+    // table, state, partials, scratch
+    if (cudaMalloc(&c->d_table, (size_t)P.capacity * sizeof(Slot)) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_NOMEM, "hash table of 2^%d slots (%.2f GiB) does not fit", prm.log2_capacity,
+                         (double)P.capacity * sizeof(Slot) / (1 << 30)));
+    P.table = c->d_table;
+    c->grid = prm.grid_blocks > 0 ? prm.grid_blocks
+                                  : (int)std::max<long long>(1, std::min<long long>((P.nh - 1 + 255) / 256, 1216));
+    c->chunk = prm.graph_chunk > 0 ? prm.graph_chunk : 64;
+    if (cudaMemsetAsync(c->d_table, 0, (size_t)P.capacity * sizeof(Slot), s) != cudaSuccess ||
+        cudaMalloc(&c->d_st, sizeof(IterState)) != cudaSuccess ||
+        cudaMalloc(&c->d_part, (size_t)c->grid * sizeof(CdPartial)) != cudaSuccess ||
+        cudaMalloc(&c->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_colkeys, (size_t)P.nh * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_colvals, (size_t)P.nh * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_st, sizeof(IterState)) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_NOMEM, "device allocation failed"));
+    if (cudaMemsetAsync(c->d_st, 0, sizeof(IterState), s) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_CUDA, "memset failed"));
+
+    // start determinant: given, or aufbau on h_pp (smallest first, ties to the lower index)
+    if (refA == 0ull && refB == 0ull) {
+        std::vector<double> hd(n2);
+        if (cudaMemcpyAsync(hd.data(), c->d_h, n2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return bail(fail(CDFCI_ERR_CUDA, "copy of h failed"));
+        std::vector<int> order(N);
+        for (int p = 0; p < N; ++p) order[p] = p;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return hd[(size_t)x * N + x] < hd[(size_t)y * N + y]; });
+        for (int k = 0; k < n_alpha; ++k) refA |= 1ull << order[k];
+        for (int k = 0; k < n_beta; ++k) refB |= 1ull << order[k];
+    }
+    if (launch_init_state(P, c->d_st, refA, refB, s) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_CUDA, "init launch failed"));
+    // initialisation launch: c = e_ref, b = H e_ref (compression applied)
+    if (launch_cd_iter(P, c->d_st, c->d_part, c->grid, s) != cudaSuccess)
+        return bail(fail(CDFCI_ERR_CUDA, "initial column launch failed"));
+    rc = fill_stats(c, nullptr);
+    if (rc != CDFCI_OK) return bail(rc);
+    rc = build_graph(c);
+    if (rc != CDFCI_OK) return bail(rc);
+    *out = c;
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_step(cdfci_handle c, int64_t n_iter, cdfci_stats *stats) {
+    if (!c) return fail(CDFCI_ERR_ARG, "handle is NULL");
+    if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
+    int64_t full = n_iter / c->chunk, rest = n_iter % c->chunk;
+    for (int64_t i = 0; i < full; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
+    for (int64_t i = 0; i < rest; ++i) CK(launch_cd_iter(c->P, c->d_st, c->d_part, c->grid, c->stream));
+    return fill_stats(c, stats);
+}
+
+CDFCI_API int cdfci_get_stats(cdfci_handle c, cdfci_stats *stats) {
+    if (!c) return fail(CDFCI_ERR_ARG, "handle is NULL");
+    return fill_stats(c, stats);
+}
+
+CDFCI_API int cdfci_energy(cdfci_handle c, int mode, double *E) {
+    if (!c || !E) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (mode == 0) {
+        int rc = fill_stats(c, nullptr);
+        if (rc) return rc;
+        *E = dd_div_to_d(c->h_st->alpha, c->h_st->mu);
+        return CDFCI_OK;
+    }
+    if (mode != 1) return fail(CDFCI_ERR_ARG, "mode must be 0 or 1");
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    long long n = c->h_st->n_slots;
+    long long *list = nullptr;
+    double *partial = nullptr, *dE = nullptr;
+    const int nblocks = 152 * 4;
+    if (cudaMalloc(&list, (size_t)std::max<long long>(n, 1) * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&partial, (size_t)nblocks * 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dE, sizeof(double)) != cudaSuccess) {
+        cudaFree(list); cudaFree(partial); cudaFree(dE);
+        return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = launch_rq(c->P, c->d_st, list, n, c->d_counter, partial, nblocks, dE, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(list); cudaFree(partial); cudaFree(dE);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "energy: %s", cudaGetErrorString(e));
+    return fill_stats(c, nullptr);
+}
+
+CDFCI_API int cdfci_get_column(cdfci_handle c, const uint64_t *key, uint64_t *keys_out, double *vals_out, int64_t cap,
+                     int64_t *n_out) {
+    if (!c || !key || !n_out) return fail(CDFCI_ERR_ARG, "NULL argument");
+    uint64_t k[2];
+    if (is_device_ptr(key)) {
+        CK(cudaMemcpy(k, key, sizeof(k), cudaMemcpyDeviceToHost));
+    } else {
+        k[0] = key[0]; k[1] = key[1];
+    }
+    const unsigned long long full = (1ull << c->N) - 1ull;
+    if ((k[0] & ~full) || (k[1] & ~full) || __builtin_popcountll(k[0]) != c->na || __builtin_popcountll(k[1]) != c->nb)
+        return fail(CDFCI_ERR_ARG, "key does not match N, n_alpha, n_beta");
+    CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_column(c->P, k[0], k[1], c->d_colkeys, c->d_colvals, c->P.nh, c->d_counter, c->stream));
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, c->d_counter, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *n_out = (int64_t)n;
+    if ((int64_t)n > cap) return fail(CDFCI_ERR_CAPACITY, "column has %lld entries, cap is %lld", (long long)n, (long long)cap);
+    if (n > 0) {
+        if (keys_out)
+            CK(cudaMemcpyAsync(keys_out, c->d_colkeys, n * 2 * sizeof(uint64_t), cudaMemcpyDefault, c->stream));
+        if (vals_out) CK(cudaMemcpyAsync(vals_out, c->d_colvals, n * sizeof(double), cudaMemcpyDefault, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_export(cdfci_handle c, uint64_t *keys, double *cv, double *bv, int64_t cap, int64_t *n_out) {
+    if (!c || !n_out) return fail(CDFCI_ERR_ARG, "NULL argument");
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    long long n = c->h_st->n_slots;
+    *n_out = n;
+    if (n > cap) return fail(CDFCI_ERR_CAPACITY, "%lld entries stored, cap is %lld", n, (long long)cap);
+    if (n == 0) return CDFCI_OK;
+    unsigned long long *dk = nullptr;
+    double *dc = nullptr, *db = nullptr;
+    if (cudaMalloc(&dk, (size_t)n * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&dc, (size_t)n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&db, (size_t)n * sizeof(double)) != cudaSuccess) {
+        cudaFree(dk); cudaFree(dc); cudaFree(db);
+        return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = launch_export(c->P, c->d_st, dk, dc, db, n, c->d_counter, c->stream);
+    if (e == cudaSuccess && keys) e = cudaMemcpyAsync(keys, dk, (size_t)n * 2 * sizeof(uint64_t), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && cv) e = cudaMemcpyAsync(cv, dc, (size_t)n * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && bv) e = cudaMemcpyAsync(bv, db, (size_t)n * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(dk); cudaFree(dc); cudaFree(db);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "export: %s", cudaGetErrorString(e));
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_last_step(cdfci_handle c, uint64_t *keys, double *eta, int64_t cap, int64_t *m_out) {
+    if (!c || !m_out) return fail(CDFCI_ERR_ARG, "NULL argument");
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    *m_out = 1;
+    if (cap < 1) return fail(CDFCI_ERR_CAPACITY, "cap < 1");
+    uint64_t k[2] = {c->h_st->last_a, c->h_st->last_b};
+    double e = c->h_st->last_eta;
+    if (keys) CK(cudaMemcpy(keys, k, sizeof(k), cudaMemcpyDefault));
+    if (eta) CK(cudaMemcpy(eta, &e, sizeof(e), cudaMemcpyDefault));
+    return CDFCI_OK;
+}
+
+CDFCI_API void cdfci_destroy(cdfci_handle c) { free_ctx(c); }
+
+}  // extern "C"

@@ -1,0 +1,22 @@
+// Host-side launch wrappers of the kernels in cdfci_kernels.cu (library-internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "cdfci_internal.cuh"
+
+namespace cdfci {
+
+cudaError_t launch_cd_iter(const Problem &P, IterState *st, CdPartial *part, int grid, cudaStream_t s);
+int cd_threads();
+cudaError_t launch_column(const Problem &P, unsigned long long A, unsigned long long B, unsigned long long *keys,
+                          double *vals, long long cap, unsigned long long *counter, cudaStream_t s);
+cudaError_t launch_export(const Problem &P, const IterState *st, unsigned long long *keys, double *c, double *b,
+                          long long cap, unsigned long long *counter, cudaStream_t s);
+cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long long cap, unsigned long long *counter,
+                      double *partial, int nblocks, double *out, cudaStream_t s);
+cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int *status, int *has_doubles,
+                         cudaStream_t s);
+cudaError_t launch_init_state(const Problem &P, IterState *st, unsigned long long A, unsigned long long B,
+                              cudaStream_t s);
+
+}  // namespace cdfci

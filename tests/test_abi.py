@@ -1,0 +1,86 @@
+"""The C-ABI library loads and exports every entry point include/cdfci.h declares,
+and the Python binding's structures have the C layout (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cdfci.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_04483_gb300 import api
+    return api
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cdfci_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(built):
+    names = declared_functions()
+    assert "cdfci_create" in names and "cdfci_step" in names
+    L = built.lib()
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/cdfci.h but not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", built.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (cdfci_\w+)", out))
+    assert set(names) == exported, (set(names) ^ exported)
+
+
+def test_struct_layouts_match_header(built, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "cdfci.h"
+#define F(T, f) printf("%s.%s %zu\\n", #T, #f, offsetof(T, f));
+int main(void) {
+  printf("cdfci_params %zu\\n", sizeof(cdfci_params));
+  printf("cdfci_stats %zu\\n", sizeof(cdfci_stats));
+  F(cdfci_params, z_threshold) F(cdfci_params, ref_alpha) F(cdfci_params, block_threads)
+  F(cdfci_params, deterministic) F(cdfci_params, cuda_stream)
+  F(cdfci_stats, energy) F(cdfci_stats, nnz_c) F(cdfci_stats, load) F(cdfci_stats, status) F(cdfci_stats, converged)
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    vals = dict(l.split() for l in lines if l.strip())
+    P, S = built.cdfci_params, built.cdfci_stats
+    assert int(vals["cdfci_params"]) == ctypes.sizeof(P)
+    assert int(vals["cdfci_stats"]) == ctypes.sizeof(S)
+    for k, v in vals.items():
+        if "." in k:
+            t, f = k.split(".")
+            cls = P if t == "cdfci_params" else S
+            assert getattr(cls, f).offset == int(v), k
+
+
+def test_defaults_and_errors_without_gpu(built):
+    p = built.cdfci_default_params()
+    assert p.num_coordinates == 1 and abs(p.max_load - 0.79) < 1e-15 and p.z_threshold == 0.0
+    assert p.deterministic == 1
+    # argument errors are reported before any device work
+    import numpy as np
+    h = np.zeros((4, 4))
+    g = np.zeros((4, 4, 4, 4))
+    with pytest.raises(built.CdfciError) as e:
+        built.cdfci_create(h, g, 70, 1, 1)
+    assert e.value.code == -1
+    with pytest.raises(built.CdfciError) as e:
+        built.cdfci_create(h, g, 4, 5, 1)
+    assert e.value.code == -1
+    bad_ref = built.cdfci_default_params(ref_alpha=0b111, ref_beta=0b1)
+    with pytest.raises(built.CdfciError) as e:
+        built.cdfci_create(h, g, 4, 2, 1, bad_ref)
+    assert e.value.code == -1

@@ -1,0 +1,198 @@
+"""GPU CDFCI (Algorithm 1) against the oracle: trajectories, vectors, energies,
+compression counters, convergence to exact diagonalisation, error paths."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_04483_gb300 import inputs
+from gpu_util import require_gpu, vec_by_key
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def solver(w, **kw):
+    from paper_2605_04483_gb300 import api
+    kw.setdefault("log2_capacity", 16)
+    return api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]), **kw)
+
+
+def run_trajectory(w, n_iter, tau=0.0, vec_every=0, log2_capacity=16):
+    """Step the GPU one iteration at a time; the oracle takes the GPU's choice,
+    which must be an argmax of |4 b + 4 mu c| over the oracle's candidates
+    (within 1e-12 relative: exact ties, e.g. between alpha/beta mirror
+    determinants, may be broken either way by rounding), and then applies the
+    update with its own arithmetic.  eta and the energy must agree each step."""
+    g = solver(w, z_threshold=tau, log2_capacity=log2_capacity)
+    o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, w.ref, tau, 1)
+    ties = 0
+    try:
+        for it in range(n_iter):
+            st = g.step(1)
+            (kg,), (eg,) = g.last_step()
+            gc, gm = o.step_choice(kg)
+            assert gc >= gm * (1 - 1e-12), (it, gc, gm)
+            ties += gc < gm
+            (ko,), (eo,) = o.last_step()
+            assert (int(ko[0]), int(ko[1])) == (int(kg[0]), int(kg[1]))
+            assert abs(eg - eo) <= 1e-10 * max(1.0, abs(eo)), (it, eg, eo)
+            assert abs(st["energy"] - o.energy()) <= 1e-11 * max(1.0, abs(o.energy())), (it, st["energy"], o.energy())
+            if vec_every and (it + 1) % vec_every == 0:
+                compare_vectors(g, o, tau)
+        return n_iter, g, o
+    except Exception:
+        g.close()
+        raise
+
+
+def compare_vectors(g, o, tau):
+    kg, cg, bg = g.export()
+    ko, co, bo = o.export()
+    mc_g, mb_g = vec_by_key(kg, cg), vec_by_key(kg, bg)
+    mc_o, mb_o = vec_by_key(ko, co), vec_by_key(ko, bo)
+    assert set(mc_g) == set(mc_o), "stored determinant sets differ"
+    scale = max(1.0, max(abs(v) for v in mb_o.values()))
+    for k in mc_o:
+        assert abs(mc_g[k] - mc_o[k]) <= 1e-11 * max(1.0, abs(mc_o[k])), ("c", k, mc_g[k], mc_o[k])
+        assert abs(mb_g[k] - mb_o[k]) <= 1e-11 * scale, ("b", k, mb_g[k], mb_o[k])
+    ig, io = g.stats(), o.info()
+    assert ig["n_slots"] == io["entries"]
+    assert ig["nnz_c"] == io["nnz_c"]
+    assert ig["elements"] == io["elements"] and ig["applied"] == io["applied"] and ig["dropped"] == io["dropped"]
+
+
+def test_trajectory_config1():
+    w = inputs.config1()
+    agreed, g, o = run_trajectory(w, 400, vec_every=100)
+    g.close()
+    assert agreed >= 50
+
+
+def test_trajectory_ab_initio_with_vectors():
+    w = inputs.ab_initio(8, 3, 3, seed=7)
+    agreed, g, o = run_trajectory(w, 300, vec_every=50)
+    g.close()
+    assert agreed == 300
+
+
+def test_trajectory_compression_counters():
+    """tau > 0: the same drops, inserts and stored sets as the oracle."""
+    w = inputs.ab_initio(10, 4, 4, seed=8)
+    agreed, g, o = run_trajectory(w, 200, tau=3e-4, vec_every=40)
+    assert g.stats()["dropped"] > 0
+    g.close()
+    assert agreed == 200
+
+
+def test_trajectory_config2_full_size():
+    """Config 2 (N = 24, 6 + 6, tau = 1e-5) in the launch configuration the benchmark times."""
+    w = inputs.config2()
+    agreed, g, o = run_trajectory(w, 60, tau=1e-5, vec_every=30, log2_capacity=21)
+    g.close()
+    assert agreed == 60
+
+
+def test_batched_steps_equal_single_steps():
+    """cdfci_step(n) through the captured graph == n calls of cdfci_step(1) (deterministic)."""
+    w = inputs.ab_initio(10, 4, 4, seed=9)
+    a = solver(w)
+    b = solver(w)
+    sa = a.step(200)
+    for _ in range(200):
+        sb = b.step(1)
+    assert sa["energy"] == sb["energy"] and sa["iterations"] == sb["iterations"] == 200
+    ka, ca, ba = a.export()
+    kb, cb, bb = b.export()
+    assert vec_by_key(ka, ca) == vec_by_key(kb, cb)
+    assert vec_by_key(ka, ba) == vec_by_key(kb, bb)
+    a.close()
+    b.close()
+
+
+def test_converges_config1_to_exact_diagonalisation():
+    w = inputs.config1()
+    E0 = oracle.ground_energy(8, 4, 4, w.h, w.g, dense_limit=5000)
+    g = solver(w)
+    st = g.step(300000)
+    assert abs(st["energy"] - E0) < 1e-10, st["energy"] - E0
+    assert abs(g.energy(1) - E0) < 1e-10
+    assert abs(st["mu"] + E0) < 1e-8
+    g.close()
+
+
+def test_converges_ab_initio_to_exact_diagonalisation():
+    w = inputs.ab_initio(10, 3, 3, seed=11)
+    E0 = oracle.ground_energy(10, 3, 3, w.h, w.g)
+    g = solver(w)
+    st = g.step(150000)
+    assert abs(st["energy"] - E0) < 1e-8, st["energy"] - E0
+    assert abs(g.energy(1) - st["energy"]) < 1e-10
+    g.close()
+
+
+def test_exact_energy_mode_matches_running_quotient():
+    w = inputs.ab_initio(8, 3, 3, seed=7)
+    g = solver(w)
+    g.step(2000)
+    assert abs(g.energy(1) - g.energy(0)) < 1e-11
+    g.close()
+
+
+def test_host_and_device_inputs_agree():
+    import torch
+    from paper_2605_04483_gb300 import api
+    w = inputs.ab_initio(8, 3, 3, seed=7)
+    a = api.Solver(w.h, w.g, 8, 3, 3, log2_capacity=14)
+    b = api.Solver(torch.tensor(w.h, device="cuda"), torch.tensor(w.g, device="cuda"), 8, 3, 3, log2_capacity=14)
+    assert a.step(500)["energy"] == b.step(500)["energy"]
+    a.close()
+    b.close()
+
+
+def test_dx_stopping_rule():
+    w = inputs.ab_initio(6, 2, 2, seed=3)
+    g = solver(w, dx_threshold=1e-9)
+    st = g.step(1000000)
+    assert st["converged"] == 1 and st["iterations"] < 1000000 and st["dx"] < 1e-9
+    g.close()
+
+
+def test_edge_single_determinant_space():
+    """N = 1, 1 + 1: a one-determinant space; c converges to sqrt(-H_00)."""
+    h = np.array([[-1.5]])
+    gg = np.array([[[[0.7]]]])
+    from paper_2605_04483_gb300 import api
+    s = api.Solver(h, gg, 1, 1, 1, log2_capacity=4)
+    st = s.step(5)
+    H00 = 2 * -1.5 + 0.7
+    assert abs(st["energy"] - H00) < 1e-14 and abs(st["mu"] + H00) < 1e-12
+    s.close()
+
+
+def test_error_table_full_is_reported():
+    from paper_2605_04483_gb300 import api
+    w = inputs.config1()
+    s = solver(w, log2_capacity=5)     # 32 slots, at most 25 entries
+    with pytest.raises(api.CdfciError) as e:
+        s.step(100)
+    assert e.value.code == -3
+    s.close()
+
+
+def test_error_bad_integrals():
+    from paper_2605_04483_gb300 import api
+    w = inputs.ab_initio(6, 2, 2, seed=1)
+    h = w.h.copy()
+    h[1, 2] = np.nan
+    with pytest.raises(api.CdfciError) as e:
+        api.Solver(h, w.g, 6, 2, 2)
+    assert e.value.code == -2
+    g = w.g.copy()
+    g[0, 1, 2, 3] += 1e-3
+    with pytest.raises(api.CdfciError) as e:
+        api.Solver(w.h, g, 6, 2, 2)
+    assert e.value.code == -1
