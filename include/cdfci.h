@@ -150,6 +150,33 @@ int cdfci_last_step(cdfci_handle h, uint64_t *keys, double *eta, int64_t cap, in
 /* Current stats without running an iteration. */
 int cdfci_get_stats(cdfci_handle h, cdfci_stats *stats);
 
+/*
+ * get_column without any device allocation, for callers that cannot call
+ * cudaMalloc (code running inside a memory pool or allocator it does not own,
+ * or a framework that forbids allocation on its hot path).  The paper has no
+ * counterpart: it is the cdfci_get_column operation without a handle.
+ *
+ * h (N*N) and g (N^4, exactly 8-fold symmetric for bit-for-bit agreement with
+ * cdfci_get_column, which canonicalises its copy) must be device memory, as
+ * must keys_out (2 words per entry) and vals_out when cap > 0; key ({A, B})
+ * may be host or device memory; *n_out (host) receives the column length.
+ * Work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream) and the call returns after it finished.
+ * Scratch: a fixed array of about 80 KB inside the library image (counter,
+ * J/K tables, pair tables), held by every GPU that loads the library until
+ * the process exits.  Limit: N <= 63 orbitals; larger N is rejected with
+ * CDFCI_ERR_ARG.  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture.  All calls on a
+ * device share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Errors: CDFCI_ERR_ARG (sizes, host memory where device memory is needed,
+ * a key with the wrong electron counts), CDFCI_ERR_CAPACITY (*n_out holds the
+ * required size; the buffers then hold an unspecified part of the column),
+ * CDFCI_ERR_CUDA.
+ */
+int cdfci_column_noalloc(const double *h, const double *g, int N, int n_alpha, int n_beta, const uint64_t *key,
+                         uint64_t *keys_out, double *vals_out, int64_t cap, int64_t *n_out, void *cuda_stream);
+
 /* Frees everything the handle owns (safe on NULL). */
 void cdfci_destroy(cdfci_handle h);
 

@@ -70,6 +70,9 @@ def lib():
         L.cdfci_get_column.argtypes = [vp, u64p, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_export.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_last_step.argtypes = [vp, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.cdfci_column_noalloc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p, dp, i64,
+                                           ctypes.POINTER(ctypes.c_int64), vp]
+        L.cdfci_column_noalloc.restype = ctypes.c_int
         L.cdfci_destroy.argtypes = [vp]
         L.cdfci_destroy.restype = None
         L.cdfci_last_error.argtypes = []
@@ -167,6 +170,16 @@ def cdfci_last_step(handle: int, cap: int = 1024) -> Tuple[np.ndarray, np.ndarra
     m = ctypes.c_int64()
     _check(lib().cdfci_last_step(handle, _ptr(keys), _ptr(eta), cap, ctypes.byref(m)))
     return keys[:m.value], eta[:m.value]
+
+
+def cdfci_column_noalloc(h, g, N: int, n_alpha: int, n_beta: int, key, keys_out, vals_out, cap: int,
+                         stream: int = 0) -> int:
+    """get_column for callers that cannot allocate device memory: h, g, keys_out and
+    vals_out are device tensors the caller owns; returns the column length."""
+    n = ctypes.c_int64()
+    _check(lib().cdfci_column_noalloc(_ptr(h), _ptr(g), N, n_alpha, n_beta, _ptr(key), _ptr(keys_out),
+                                      _ptr(vals_out), int(cap), ctypes.byref(n), stream))
+    return n.value
 
 
 def cdfci_destroy(handle: int) -> None:

@@ -65,6 +65,8 @@ std::vector<unsigned short> pair_table(int n) {
 
 }  // namespace
 
+void cdfci::set_last_error_message(const char *msg) { g_last_error = msg; }
+
 struct cdfci_ctx {
     cdfci_params prm;
     int N, na, nb;

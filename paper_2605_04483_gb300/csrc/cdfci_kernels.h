@@ -19,4 +19,7 @@ cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int 
 cudaError_t launch_init_state(const Problem &P, IterState *st, unsigned long long A, unsigned long long B,
                               cudaStream_t s);
 
+// sets the message returned by cdfci_last_error() on the calling thread
+void set_last_error_message(const char *msg);
+
 }  // namespace cdfci
