@@ -17,6 +17,9 @@ def colmap(keys, vals):
     return {(int(k[0]), int(k[1])): float(v) for k, v in zip(keys, vals)}
 
 
+_scale_cache = {}
+
+
 def element_tol(w, v):
     """|gpu - oracle| bound for one column element.  A single is a sum of
     1 + 2n terms (n electrons) each bounded by S = max|h| + max|g|; two
@@ -24,7 +27,10 @@ def element_tol(w, v):
     summation bound).  Doubles are one subtraction of the same two doubles on
     both sides.  Plus 1e-12 relative."""
     n = w.n_alpha + w.n_beta
-    S = np.abs(w.h).max() + (2 * n + 1) * np.abs(w.g).max()
+    key = id(w)
+    if key not in _scale_cache or _scale_cache[key][0] is not w:
+        _scale_cache[key] = (w, np.abs(w.h).max() + (2 * n + 1) * np.abs(w.g).max())
+    S = _scale_cache[key][1]
     return 1e-12 * abs(v) + 2 * (2 * n + 1) * EPS * S
 
 
