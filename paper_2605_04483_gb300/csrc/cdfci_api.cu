@@ -78,15 +78,15 @@ struct cdfci_ctx {
     unsigned short *d_pairs = nullptr;
     Slot *d_table = nullptr;
     IterState *d_st = nullptr;
-    CdPartial *d_part = nullptr;
+    CdRecord *d_rec = nullptr;                   // state between launches of the cluster loop
+    CdPartial *d_part = nullptr;                 // one partial per CTA of the cluster
     int *d_flags = nullptr;                      // [0] status, [1] has_doubles
     unsigned long long *d_counter = nullptr;     // scratch counter for compaction kernels
     unsigned long long *d_colkeys = nullptr;     // get_column staging (2 * nh)
     double *d_colvals = nullptr;
     IterState *h_st = nullptr;                   // pinned copy of the state
-    int grid = 1;
-    int chunk = 64;
-    cudaGraphExec_t graph = nullptr;
+    int grid = 1;                                // CTAs of the cluster
+    long long chunk = 1 << 16;                   // iterations per launch
 };
 
 namespace {
@@ -94,16 +94,25 @@ namespace {
 void free_ctx(cdfci_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
     cudaFree(c->d_h); cudaFree(c->d_g); cudaFree(c->d_J); cudaFree(c->d_K);
-    cudaFree(c->d_pairs); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part);
+    cudaFree(c->d_pairs); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part); cudaFree(c->d_rec);
     cudaFree(c->d_flags); cudaFree(c->d_counter); cudaFree(c->d_colkeys); cudaFree(c->d_colvals);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
+int run_iterations(cdfci_ctx *c, long long n) {
+    while (n > 0) {
+        long long k = std::min(n, c->chunk);
+        CK(launch_cd_loop(c->P, c->d_st, c->d_rec, c->d_part, c->grid, k, c->stream));
+        n -= k;
+    }
+    return CDFCI_OK;
+}
+
 int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
+    CK(launch_cd_finalize(c->P, c->d_st, c->d_rec, c->d_part, c->grid, c->stream));
     CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     const IterState &t = *c->h_st;
@@ -131,25 +140,6 @@ int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
                                                              : "device error";
         return fail(t.status, "%s", what);
     }
-    return CDFCI_OK;
-}
-
-int build_graph(cdfci_ctx *c) {
-    cudaGraph_t g;
-    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < c->chunk; ++i) {
-        cudaError_t e = launch_cd_iter(c->P, c->d_st, c->d_part, c->grid, c->stream);
-        if (e != cudaSuccess) {
-            cudaGraph_t junk;
-            cudaStreamEndCapture(c->stream, &junk);
-            if (junk) cudaGraphDestroy(junk);
-            return fail(CDFCI_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
-        }
-    }
-    CK(cudaStreamEndCapture(c->stream, &g));
-    cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     return CDFCI_OK;
 }
 
@@ -282,18 +272,25 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         return bail(fail(CDFCI_ERR_NOMEM, "hash table of 2^%d slots (%.2f GiB) does not fit", prm.log2_capacity,
                          (double)P.capacity * sizeof(Slot) / (1 << 30)));
     P.table = c->d_table;
-    c->grid = prm.grid_blocks > 0 ? prm.grid_blocks
-                                  : (int)std::max<long long>(1, std::min<long long>((P.nh - 1 + 255) / 256, 1216));
-    c->chunk = prm.graph_chunk > 0 ? prm.graph_chunk : 64;
+    {
+        const long long per_cta = (long long)cd_threads() * cd_elements_per_thread();
+        const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
+        const long long want = prm.grid_blocks > 0 ? prm.grid_blocks : (nh_eff - 1 + per_cta - 1) / per_cta;
+        c->grid = cd_pick_cluster((int)std::max<long long>(1, std::min<long long>(want, 16)));
+    }
+    if (prm.graph_chunk > 0) c->chunk = prm.graph_chunk;
     if (cudaMemsetAsync(c->d_table, 0, (size_t)P.capacity * sizeof(Slot), s) != cudaSuccess ||
         cudaMalloc(&c->d_st, sizeof(IterState)) != cudaSuccess ||
         cudaMalloc(&c->d_part, (size_t)c->grid * sizeof(CdPartial)) != cudaSuccess ||
+        cudaMalloc(&c->d_rec, sizeof(CdRecord)) != cudaSuccess ||
         cudaMalloc(&c->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_colkeys, (size_t)P.nh * 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_colvals, (size_t)P.nh * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->h_st, sizeof(IterState)) != cudaSuccess)
         return bail(fail(CDFCI_ERR_NOMEM, "device allocation failed"));
-    if (cudaMemsetAsync(c->d_st, 0, sizeof(IterState), s) != cudaSuccess)
+    if (cudaMemsetAsync(c->d_st, 0, sizeof(IterState), s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_rec, 0, sizeof(CdRecord), s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_part, 0, (size_t)c->grid * sizeof(CdPartial), s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "memset failed"));
 
     // start determinant: given, or aufbau on h_pp (smallest first, ties to the lower index)
@@ -309,14 +306,12 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         for (int k = 0; k < n_alpha; ++k) refA |= 1ull << order[k];
         for (int k = 0; k < n_beta; ++k) refB |= 1ull << order[k];
     }
-    if (launch_init_state(P, c->d_st, refA, refB, s) != cudaSuccess)
+    if (launch_init_state(P, c->d_st, c->d_rec, refA, refB, s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "init launch failed"));
-    // initialisation launch: c = e_ref, b = H e_ref (compression applied)
-    if (launch_cd_iter(P, c->d_st, c->d_part, c->grid, s) != cudaSuccess)
-        return bail(fail(CDFCI_ERR_CUDA, "initial column launch failed"));
-    rc = fill_stats(c, nullptr);
+    // initialisation iteration: c = e_ref, b = H e_ref (compression applied)
+    rc = run_iterations(c, 1);
     if (rc != CDFCI_OK) return bail(rc);
-    rc = build_graph(c);
+    rc = fill_stats(c, nullptr);
     if (rc != CDFCI_OK) return bail(rc);
     *out = c;
     return CDFCI_OK;
@@ -325,9 +320,8 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
 CDFCI_API int cdfci_step(cdfci_handle c, int64_t n_iter, cdfci_stats *stats) {
     if (!c) return fail(CDFCI_ERR_ARG, "handle is NULL");
     if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
-    int64_t full = n_iter / c->chunk, rest = n_iter % c->chunk;
-    for (int64_t i = 0; i < full; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
-    for (int64_t i = 0; i < rest; ++i) CK(launch_cd_iter(c->P, c->d_st, c->d_part, c->grid, c->stream));
+    int rc = run_iterations(c, n_iter);
+    if (rc) return rc;
     return fill_stats(c, stats);
 }
 
@@ -341,7 +335,7 @@ CDFCI_API int cdfci_energy(cdfci_handle c, int mode, double *E) {
     if (mode == 0) {
         int rc = fill_stats(c, nullptr);
         if (rc) return rc;
-        *E = dd_div_to_d(c->h_st->alpha, c->h_st->mu);
+        *E = c->h_st->energy;
         return CDFCI_OK;
     }
     if (mode != 1) return fail(CDFCI_ERR_ARG, "mode must be 0 or 1");

@@ -62,6 +62,12 @@ __host__ __device__ __forceinline__ dd dd_add(dd a, dd b) {
     s.lo += t.lo;
     return dd_fast_two_sum(s.hi, s.lo);
 }
+// Dekker's shorter addition (relative error about 2^-104 instead of 2^-106):
+// TwoSum of the leading parts, the trailing parts folded in once.
+__host__ __device__ __forceinline__ dd dd_add_fast(dd a, dd b) {
+    dd s = dd_two_sum(a.hi, b.hi);
+    return dd_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
 __host__ __device__ __forceinline__ dd dd_mul_d(dd a, double b) {
     dd p = dd_two_prod(a.hi, b);
     p.lo = fma(a.lo, b, p.lo);
@@ -81,36 +87,43 @@ __host__ __device__ __forceinline__ double dd_div_to_d(dd a, dd b) {
 __host__ __device__ __forceinline__ dd dd_from(double x) { return {x, 0.0}; }
 
 // ---------------------------------------------------------------------------
-// Per-handle device state of the iteration (one copy in device memory).
+// Per-handle device state between launches of the m = 1 cluster loop.
 // ---------------------------------------------------------------------------
-struct IterState {
-    // coordinate chosen for the next update (written by the tail of a launch)
-    unsigned long long sel_a, sel_b;
-    long long sel_slot;
-    int forced_eta_one;        // 1 = initialisation: c = e_ref (eta = 1 from c = 0)
-    int done;                  // 1 = converged (dx < threshold); launches return at once
-    int status;                // first error code (sticky)
-    unsigned int arrive;       // arrival ticket of the fused column kernel
-    // scalars (double-double), global scale, damped accumulator
-    dd mu, alpha;
-    dd scale;                  // s: c_true = s * c_stored
-    double dx;
-    double energy;
-    long long iterations;
-    // record of the last update
-    double last_eta;
-    unsigned long long last_a, last_b;
-    // counters
-    long long nnz_c, n_slots, last_column, elements, applied, dropped, inserted;
+struct CdRecord {                  // written at the end of a launch, read at the start of the next
+    unsigned long long a, b;       // coordinate i processed by launch l
+    long long slot;
+    double c_new;                  // c_i after the update
+    double Hii;                    // H_ii
+    double eta;                    // step of launch l
+    dd mu, alpha;                  // c.c and c.Hc after the update (double-double)
+    double mu_g;                   // the mu used in the gradients of the last column
+    double dx, energy;
+    long long iterations, nnz_c, n_slots, elements, applied, dropped, inserted, last_column;
+    int forced;                    // 1: the next launch processes (a, b, slot) with eta = 1 (start vector)
+    int done;                      // 1: dx < threshold; later launches only forward the state
 };
 
-// per-CTA partial results of the fused m = 1 column kernel
-struct __align__(16) CdPartial {
-    double gather;                 // sum_j H_ji c_j over this CTA's elements
-    unsigned long long gbits;      // |gradient| bits of this CTA's best candidate
+struct __align__(16) CdPartial {   // per CTA: its share of the last processed column
+    double gather;                 // sum_j H_ji c_j over this CTA's elements (for the recalculation of b_i)
+    unsigned long long gbits;      // |4 b_j + 4 mu c_j| bits of this CTA's best candidate
     unsigned long long ka, kb;     // its key
     long long slot;                // its slot
+    double bj, cj;                 // its b and c after the update
     int elements, applied, dropped, inserted;
+    int err;                       // nonzero: this CTA hit an error (the status word holds the code)
+};
+
+// Control word and host-visible snapshot (one per handle).
+struct IterState {
+    int status;                    // first error code (sticky)
+    int last_parity;               // parity of the most recent launch (its record is the current one)
+    dd scale;                      // s: c_true = s * c_stored (1 for m = 1)
+    // snapshot written by the finalisation kernel after each batch of launches
+    long long iterations, nnz_c, n_slots, last_column, elements, applied, dropped, inserted;
+    dd mu, alpha;
+    double dx, energy, last_eta;
+    unsigned long long last_a, last_b;
+    int done;
 };
 
 // Everything a kernel needs about the problem and the table.
@@ -141,8 +154,9 @@ __device__ __forceinline__ unsigned long long between_mask(int x, int y) {   // 
     int lo = x < y ? x : y, hi = x < y ? y : x;
     return low_mask(hi) & ~low_mask(lo + 1);
 }
-__device__ __forceinline__ double parity_sign(unsigned long long x) {
-    return (__popcll(x) & 1) ? -1.0 : 1.0;
+// x times (-1)^popcount(m), as a flip of the sign bit (exact, no FP64 operation)
+__device__ __forceinline__ double apply_parity(double x, unsigned long long m) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(__popcll(m) & 1) << 63));
 }
 // SplitMix64 output finalizer (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
@@ -177,6 +191,11 @@ __device__ __forceinline__ void cas128(unsigned long long *p, unsigned long long
 __device__ __forceinline__ void set_status(IterState *st, int code) {
     atomicCAS(&st->status, 0, code);
 }
+
+// Programmatic dependent launch (sm_90+): wait for the preceding grid's
+// completion and memory, and let the next grid start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Look up key {a, b}; insert it if absent and `insert` is set.  Returns the
 // slot index, or -1 (absent, not inserted), or -2 (probe limit / timeout;
@@ -230,103 +249,148 @@ __device__ __forceinline__ double gi(const double *g, int N, int p, int q, int r
     return __ldg(g + (((size_t)p * N + q) * N + r) * N + s);
 }
 
+// A decoded column element: which excitation of the column determinant.
+struct ElemIdx {
+    int kind;                          // 0 single alpha, 1 single beta, 2 double aa, 3 double bb, 4 double ab
+    int i, a, j, b;                    // orbitals (j, b unused for singles)
+    unsigned long long sgn;            // bits whose parity gives the sign (two masks folded by xor)
+};
+
+// Integer part of column element e in [1, nh): the excitation and the key D'.
+// Signs: the bits of the same-spin string strictly between the two orbitals
+// of each elementary excitation, applied in the order i->a then j->b.
+__device__ __forceinline__ void decode_element(const Problem &P, const ColLists &L, unsigned long long A,
+                                               unsigned long long B, long long e, unsigned long long &oa,
+                                               unsigned long long &ob, ElemIdx &x) {
+    if (e < P.seg[2]) {                       // singles
+        const bool alpha = e < P.seg[1];
+        const unsigned idx = (unsigned)(e - (alpha ? P.seg[0] : P.seg[1]));
+        const unsigned v = (unsigned)(alpha ? P.va : P.vb);
+        const int o = (int)(idx / v), w = (int)(idx - (unsigned)o * v);
+        const int i = alpha ? L.occA[o] : L.occB[o];
+        const int a = alpha ? L.virA[w] : L.virB[w];
+        const unsigned long long X = alpha ? A : B;
+        const unsigned long long flip = (1ull << i) | (1ull << a);
+        x.kind = alpha ? 0 : 1;
+        x.i = i; x.a = a; x.j = 0; x.b = 0;
+        x.sgn = X & between_mask(i, a);
+        oa = alpha ? (A ^ flip) : A;
+        ob = alpha ? B : (B ^ flip);
+        return;
+    }
+    if (e < P.seg[4]) {                       // same-spin doubles
+        const bool alpha = e < P.seg[3];
+        const unsigned idx = (unsigned)(e - (alpha ? P.seg[2] : P.seg[3]));
+        const unsigned cv = (unsigned)(alpha ? P.cva2 : P.cvb2);
+        const int op = (int)(idx / cv), vp = (int)(idx - (unsigned)op * cv);
+        const unsigned short po = __ldg((alpha ? P.pair_oa : P.pair_ob) + op);
+        const unsigned short pv = __ldg((alpha ? P.pair_va : P.pair_vb) + vp);
+        const unsigned char *os = alpha ? L.occA : L.occB;
+        const unsigned char *vs = alpha ? L.virA : L.virB;
+        const int i = os[po & 0xff], j = os[po >> 8], a = vs[pv & 0xff], b = vs[pv >> 8];
+        const unsigned long long X = alpha ? A : B;
+        const unsigned long long m1 = X & between_mask(i, a);
+        const unsigned long long X1 = X ^ (1ull << i) ^ (1ull << a);
+        const unsigned long long m2 = X1 & between_mask(j, b);
+        const unsigned long long X2 = X1 ^ (1ull << j) ^ (1ull << b);
+        x.kind = alpha ? 2 : 3;
+        x.i = i; x.a = a; x.j = j; x.b = b;
+        x.sgn = m1 ^ m2;                      // popcount parity of m1 ^ m2 = parity(m1) xor parity(m2)
+        oa = alpha ? X2 : A;
+        ob = alpha ? B : X2;
+        return;
+    }
+    const unsigned idx = (unsigned)(e - P.seg[4]);   // opposite-spin doubles
+    const unsigned nsb = (unsigned)(P.nb * P.vb);
+    const unsigned sa = idx / nsb;
+    const unsigned sb = idx - sa * nsb;
+    const int oa_i = (int)(sa / (unsigned)P.va), va_i = (int)(sa - (unsigned)oa_i * (unsigned)P.va);
+    const int ob_i = (int)(sb / (unsigned)P.vb), vb_i = (int)(sb - (unsigned)ob_i * (unsigned)P.vb);
+    const int i = L.occA[oa_i], a = L.virA[va_i], j = L.occB[ob_i], b = L.virB[vb_i];
+    x.kind = 4;
+    x.i = i; x.a = a; x.j = j; x.b = b;
+    x.sgn = (A & between_mask(i, a)) ^ (B & between_mask(j, b));
+    oa = A ^ (1ull << i) ^ (1ull << a);
+    ob = B ^ (1ull << j) ^ (1ull << b);
+}
+
+// Value part (Eq. entry): singles h_ia + sum_{k in occ same spin} [(ia|kk) - (ik|ka)]
+// + sum_{k in occ other spin} (ia|kk); same-spin doubles (ia|jb) - (ib|ja);
+// opposite-spin doubles (ia|jb); all times the sign.
+__device__ __forceinline__ double element_value(const Problem &P, const ColLists &L, const ElemIdx &x) {
+    const int N = P.N;
+    const double *g = P.g;
+    double v;
+    if (x.kind <= 1) {
+        const bool alpha = x.kind == 0;
+        const int i = x.i, a = x.a;
+        const unsigned char *os = alpha ? L.occA : L.occB;
+        const unsigned char *oo = alpha ? L.occB : L.occA;
+        const int ns = alpha ? P.na : P.nb, no = alpha ? P.nb : P.na;
+        // sum in a fixed order: four interleaved partial sums (k mod 4), combined pairwise
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k0 = 0; k0 < ns; k0 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + u;
+                if (k < ns) {
+                    const int kk = os[k];
+                    s4[u] += gi(g, N, i, a, kk, kk) - gi(g, N, i, kk, kk, a);
+                }
+            }
+        }
+        for (int k0 = 0; k0 < no; k0 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + u;
+                if (k < no) s4[u] += gi(g, N, i, a, oo[k], oo[k]);
+            }
+        }
+        v = __ldg(P.h + i * N + a) + ((s4[0] + s4[1]) + (s4[2] + s4[3]));
+    } else if (x.kind <= 3) {
+        v = gi(g, N, x.i, x.a, x.j, x.b) - gi(g, N, x.i, x.b, x.j, x.a);
+    } else {
+        v = gi(g, N, x.i, x.a, x.j, x.b);
+    }
+    return apply_parity(v, x.sgn);
+}
+
 // One element of the column of {A, B}: flat index e in [1, nh).  Returns the
 // value H_{D',D} (0.0 when the Slater-Condon element vanishes) and the key D'.
-// Singles (i -> a, same spin): h_ia + sum_{k in occ same spin} [(ia|kk) - (ik|ka)]
-// + sum_{k in occ other spin} (ia|kk), times the sign of the bits strictly
-// between i and a.  Same-spin doubles (i<j -> a<b, applied as i->a then
-// j->b): sign1 * sign2 * [(ia|jb) - (ib|ja)].  Opposite-spin doubles
-// (i->a alpha, j->b beta): signA * signB * (ia|jb).
 __device__ __forceinline__ double column_element(const Problem &P, const ColLists &L, unsigned long long A,
                                                  unsigned long long B, long long e, unsigned long long &oa,
                                                  unsigned long long &ob) {
-    const int N = P.N;
-    const double *g = P.g;
-    if (e < P.seg[2]) {                       // singles
-        bool alpha = e < P.seg[1];
-        long long idx = e - (alpha ? P.seg[0] : P.seg[1]);
-        int v = alpha ? P.va : P.vb;
-        int o = (int)(idx / v), w = (int)(idx - (long long)o * v);
-        int i = alpha ? L.occA[o] : L.occB[o];
-        int a = alpha ? L.virA[w] : L.virB[w];
-        unsigned long long X = alpha ? A : B;
-        double x = __ldg(P.h + i * N + a);
-        const unsigned char *os = alpha ? L.occA : L.occB;
-        const unsigned char *oo = alpha ? L.occB : L.occA;
-        int ns = alpha ? P.na : P.nb, no = alpha ? P.nb : P.na;
-        for (int k = 0; k < ns; ++k) {
-            int kk = os[k];
-            x += gi(g, N, i, a, kk, kk) - gi(g, N, i, kk, kk, a);
-        }
-        for (int k = 0; k < no; ++k) {
-            int kk = oo[k];
-            x += gi(g, N, i, a, kk, kk);
-        }
-        x *= parity_sign(X & between_mask(i, a));
-        unsigned long long flip = (1ull << i) | (1ull << a);
-        oa = alpha ? (A ^ flip) : A;
-        ob = alpha ? B : (B ^ flip);
-        return x;
-    }
-    if (e < P.seg[4]) {                       // same-spin doubles
-        bool alpha = e < P.seg[3];
-        long long idx = e - (alpha ? P.seg[2] : P.seg[3]);
-        int cv = alpha ? P.cva2 : P.cvb2;
-        int op = (int)(idx / cv), vp = (int)(idx - (long long)op * cv);
-        unsigned short po = __ldg((alpha ? P.pair_oa : P.pair_ob) + op);
-        unsigned short pv = __ldg((alpha ? P.pair_va : P.pair_vb) + vp);
-        const unsigned char *os = alpha ? L.occA : L.occB;
-        const unsigned char *vs = alpha ? L.virA : L.virB;
-        int i = os[po & 0xff], j = os[po >> 8], a = vs[pv & 0xff], b = vs[pv >> 8];
-        unsigned long long X = alpha ? A : B;
-        double s1 = parity_sign(X & between_mask(i, a));
-        unsigned long long X1 = X ^ (1ull << i) ^ (1ull << a);
-        double s2 = parity_sign(X1 & between_mask(j, b));
-        unsigned long long X2 = X1 ^ (1ull << j) ^ (1ull << b);
-        double x = s1 * s2 * (gi(g, N, i, a, j, b) - gi(g, N, i, b, j, a));
-        oa = alpha ? X2 : A;
-        ob = alpha ? B : X2;
-        return x;
-    }
-    // opposite-spin doubles
-    long long idx = e - P.seg[4];
-    long long nsb = (long long)P.nb * P.vb;
-    int sa = (int)(idx / nsb);
-    int sb = (int)(idx - (long long)sa * nsb);
-    int oa_i = sa / P.va, va_i = sa - oa_i * P.va;
-    int ob_i = sb / P.vb, vb_i = sb - ob_i * P.vb;
-    int i = L.occA[oa_i], a = L.virA[va_i], j = L.occB[ob_i], b = L.virB[vb_i];
-    double s = parity_sign(A & between_mask(i, a)) * parity_sign(B & between_mask(j, b));
-    double x = s * gi(g, N, i, a, j, b);
-    oa = A ^ (1ull << i) ^ (1ull << a);
-    ob = B ^ (1ull << j) ^ (1ull << b);
-    return x;
+    ElemIdx x;
+    decode_element(P, L, A, B, e, oa, ob, x);
+    return element_value(P, L, x);
 }
 
 // Diagonal element: sum_p h_pp + sum_{p<q same spin} (J_pq - K_pq) + sum_{p alpha, q beta} J_pq,
-// evaluated by one warp in a fixed order (lane-strided, then a butterfly sum).
+// evaluated by one warp in a fixed order (lane-strided over all ordered pairs
+// of occupied spin-orbitals, then a shuffle-down tree; every lane returns the
+// same value).  An ordered same-spin pair contributes (J - K) / 2, an ordered
+// opposite-spin pair J / 2, so each unordered pair is counted once.
 __device__ __forceinline__ double diag_warp(const Problem &P, const ColLists &L) {
     const int lane = threadIdx.x & 31;
-    const int N = P.N;
+    const int N = P.N, n = P.na + P.nb;
     double x = 0.0;
-    for (int t = lane; t < P.na; t += 32) x += __ldg(P.h + L.occA[t] * (N + 1));
-    for (int t = lane; t < P.nb; t += 32) x += __ldg(P.h + L.occB[t] * (N + 1));
-    for (int t = lane; t < P.ca2; t += 32) {
-        unsigned short pp = __ldg(P.pair_oa + t);
-        int p = L.occA[pp & 0xff], q = L.occA[pp >> 8];
-        x += __ldg(P.J + p * N + q) - __ldg(P.K + p * N + q);
+    for (int t = lane; t < n; t += 32) {
+        const int p = t < P.na ? L.occA[t] : L.occB[t - P.na];
+        x += __ldg(P.h + p * (N + 1));
     }
-    for (int t = lane; t < P.cb2; t += 32) {
-        unsigned short pp = __ldg(P.pair_ob + t);
-        int p = L.occB[pp & 0xff], q = L.occB[pp >> 8];
-        x += __ldg(P.J + p * N + q) - __ldg(P.K + p * N + q);
+    double y = 0.0;
+    for (int t = lane; t < n * n; t += 32) {
+        const int u = t / n, w = t - u * n;
+        if (u == w) continue;
+        const bool ua = u < P.na, wa = w < P.na;
+        const int p = ua ? L.occA[u] : L.occB[u - P.na];
+        const int q = wa ? L.occA[w] : L.occB[w - P.na];
+        const double jv = __ldg(P.J + p * N + q);
+        y += (ua == wa) ? (jv - __ldg(P.K + p * N + q)) : jv;
     }
-    for (int t = lane; t < P.na * P.nb; t += 32) {
-        int p = L.occA[t / P.nb], q = L.occB[t % P.nb];
-        x += __ldg(P.J + p * N + q);
-    }
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    return x;
+    x = fma(0.5, y, x);
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    return __shfl_sync(0xffffffffu, x, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -339,41 +403,64 @@ __device__ __forceinline__ double diag_warp(const Problem &P, const ColLists &L)
 // one with the smaller quartic value is kept: that is the root farther from
 // the middle one, the choice the appendix prescribes.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double newton_cubic(double x, double v1, double v2, double v3) {
-    for (int it = 0; it < 8; ++it) {
-        double f = fma(fma(fma(4.0, x, 3.0 * v3), x, 2.0 * v2), x, v1);
-        double fp = fma(fma(12.0, x, 6.0 * v3), x, 2.0 * v2);
-        float fpf = (float)fp;
-        if (fpf == 0.0f || !isfinite(fpf)) break;
-        double step = f * (double)__frcp_rn(fpf);
-        x -= step;
-        if (fabs(step) <= 1e-15 * fabs(x)) break;
+// Reciprocal of d to about 1e-14 relative: single-precision estimate plus one
+// Newton-Raphson correction in FP64.
+__device__ __forceinline__ double recip(double d) {
+    const double r = (double)__frcp_rn((float)d);
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
+// One Halley step (cubic convergence) on 4x^3 + 3 v3 x^2 + 2 v2 x + v1 = 0.
+__device__ __forceinline__ double halley_cubic(double x, double v1, double v2, double v3) {
+    const double f = fma(fma(fma(4.0, x, 3.0 * v3), x, 2.0 * v2), x, v1);
+    const double f1 = fma(fma(12.0, x, 6.0 * v3), x, 2.0 * v2);
+    const double f2 = fma(24.0, x, 6.0 * v3);
+    const double den = fma(2.0 * f1, f1, -f * f2);
+    if (!(den != 0.0) || !isfinite(den)) return x;
+    return x - 2.0 * f * f1 * recip(den);
+}
+
+// Two single-precision Newton steps on the cubic in eta itself (so a root
+// near 0 keeps its relative accuracy).
+__device__ __forceinline__ float newton_f32(float x, float v1, float v2, float v3) {
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const float f = fmaf(fmaf(fmaf(4.0f, x, 3.0f * v3), x, 2.0f * v2), x, v1);
+        const float f1 = fmaf(fmaf(12.0f, x, 6.0f * v3), x, 2.0f * v2);
+        if (f1 != 0.0f) x -= f * __frcp_rn(f1);
     }
     return x;
 }
 
+// Step size (appendix "Determining Step Size"): the global minimiser of
+// eta^4 + v3 eta^3 + v2 eta^2 + v1 eta.  Cardano's method on the cubic
+// derivative, with the depressed cubic in single precision; each root is
+// polished by two single-precision Newton steps in eta and one FP64 Halley
+// step.  With three real roots the outer two are kept and the one with the
+// smaller quartic value wins, which is the root farther from the middle one.
 __device__ __forceinline__ double line_search(double v1, double v2, double v3) {
-    const float b = 3.0f * (float)v3, c = 2.0f * (float)v2, d = (float)v1;
+    const float f1 = (float)v1, f2 = (float)v2, f3 = (float)v3;
+    const float b = 3.0f * f3, c = 2.0f * f2, d = f1;
     const float sh = b * (1.0f / 12.0f);
     const float p = (12.0f * c - b * b) * (1.0f / 48.0f);
     const float q = (2.0f * b * b * b - 36.0f * b * c + 432.0f * d) * (1.0f / 1728.0f);
     const float hq = 0.5f * q, tp = p * (1.0f / 3.0f);
     const float del = hq * hq + tp * tp * tp;
     if (!(del < 0.0f) || !(p < 0.0f)) {
-        float sd = sqrtf(fmaxf(del, 0.0f));
-        float x = cbrtf(-hq + sd) + cbrtf(-hq - sd);
-        return newton_cubic((double)(x - sh), v1, v2, v3);
+        const float sd = sqrtf(fmaxf(del, 0.0f));
+        const float x = cbrtf(-hq + sd) + cbrtf(-hq - sd) - sh;
+        return halley_cubic((double)newton_f32(x, f1, f2, f3), v1, v2, v3);
     }
-    float m = 2.0f * sqrtf(-tp);
+    const float m = 2.0f * sqrtf(-tp);
     float arg = (3.0f * q / (2.0f * p)) * sqrtf(-3.0f / p);
     arg = fminf(1.0f, fmaxf(-1.0f, arg));
-    float th = acosf(arg) * (1.0f / 3.0f);
-    float xhi = m * cosf(th) - sh;                               // largest root
-    float xlo = m * cosf(th - 4.18879020478639098f) - sh;        // smallest root (th - 4 pi / 3)
-    double r1 = newton_cubic((double)xlo, v1, v2, v3);
-    double r3 = newton_cubic((double)xhi, v1, v2, v3);
-    double h1 = (((r1 + v3) * r1 + v2) * r1 + v1) * r1;
-    double h3 = (((r3 + v3) * r3 + v2) * r3 + v1) * r3;
+    const float th = acosf(arg) * (1.0f / 3.0f);
+    const float xhi = newton_f32(m * cosf(th) - sh, f1, f2, f3);                    // largest root
+    const float xlo = newton_f32(m * cosf(th - 4.18879020478639098f) - sh, f1, f2, f3);  // smallest root
+    const double r1 = halley_cubic((double)xlo, v1, v2, v3);
+    const double r3 = halley_cubic((double)xhi, v1, v2, v3);
+    const double h1 = (((r1 + v3) * r1 + v2) * r1 + v1) * r1;
+    const double h3 = (((r3 + v3) * r3 + v2) * r3 + v1) * r3;
     return (h3 < h1) ? r3 : r1;
 }
 

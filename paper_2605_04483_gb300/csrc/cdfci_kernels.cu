@@ -1,22 +1,27 @@
 // CUDA kernels of libcdfci (sm_103a).
 //
-// The m = 1 iteration (Algorithm 1) is one launch of k_cd_iter:
-//   prologue  (every CTA, identical results): orbital lists of the chosen
-//             determinant i, H_ii, the step size eta (appendix), the new
-//             c_i, mu and alpha (Eq. update-var, double-double);
-//   scatter   (grid-stride over the flat excitation index of column i): the
-//             Slater-Condon element H_ji, the compression test
-//             (c_j != 0 or |eta H_ji| >= tau), hash probe / 16-byte CAS
-//             insert, atomicAdd of eta H_ji on b_j, the gather sum_j H_ji c_j
-//             for the recalculation of b_i (Eq. recalculate-b), and the
-//             running argmax of |4 b_j + 4 mu c_j| over the updated entries,
-//             which are the candidates I_H(i) of the next choice (Eq. choose-i);
-//   tail      (the last CTA to arrive): fixed-order reduction of the per-CTA
-//             partials, the write of c_i and the recalculated b_i, the next
-//             coordinate, the scalars and the counters.
-// Within a column every j appears once, so atomicAdd returns the final b_j
-// of this iteration and the fused argmax sees exactly the values the
-// selection of Algorithm 1 would read.
+// The m = 1 iteration (Algorithm 1) runs inside k_cd_loop: one thread-block
+// cluster (up to 16 CTAs, one per SM) that performs many iterations per
+// launch.  Per iteration:
+//   1. warp 0 of every CTA reads the partials of the previous iteration from
+//      every CTA's shared memory (distributed shared memory) and reduces them
+//      in a fixed order: the recalculated b of the previous coordinate
+//      (Eq. recalculate-b) and the argmax of |b_j + mu c_j| over the previous
+//      column and that coordinate (Eq. choose-i; the factor 4 does not change
+//      the argmax) -> i, identical in every CTA;
+//   2. every warp builds the orbital lists of i, decodes its share of the
+//      column (Slater-Condon, Eq. entry) and issues the 32-byte slot loads;
+//   3. meanwhile one lane computes H_ii and the step size eta (appendix);
+//      single lanes of two other warps update mu and alpha (double-double);
+//   4. every thread applies b_j += eta H_ji with the compression rule
+//      (c_j != 0 or |eta H_ji| >= tau), inserting absent keys with a 16-byte
+//      CAS, and accumulates the gather sum_j H_ji c_j and its best candidate;
+//   5. the CTA writes its partial to its own shared memory; cluster barrier.
+// In an m = 1 column every j occurs once, so each b_j has a single writer:
+// plain loads and stores, no atomics.  The previous coordinate's slot is
+// written by the thread whose excitation equals it, with the recalculated b.
+#include <cooperative_groups.h>
+
 #include "cdfci_internal.cuh"
 #include "cdfci_kernels.h"
 
@@ -58,6 +63,8 @@ __device__ __forceinline__ CdPartial load_partial(const CdPartial *p) {
     x.ka = __ldcg(&p->ka);
     x.kb = __ldcg(&p->kb);
     x.slot = __ldcg(&p->slot);
+    x.bj = __ldcg(&p->bj);
+    x.cj = __ldcg(&p->cj);
     x.elements = __ldcg(&p->elements);
     x.applied = __ldcg(&p->applied);
     x.dropped = __ldcg(&p->dropped);
@@ -65,204 +72,477 @@ __device__ __forceinline__ CdPartial load_partial(const CdPartial *p) {
     return x;
 }
 
-constexpr int kCdThreads = 256;
+constexpr int kCdThreads = 384;                 // threads per CTA of the cluster
 constexpr int kCdWarps = kCdThreads / 32;
+constexpr int kCdMaxE = 3;                      // elements whose slot loads a thread keeps in flight
+constexpr int kCdMaxCluster = 16;
 
-__global__ void __launch_bounds__(kCdThreads) k_cd_iter(Problem P, IterState *st, CdPartial *part) {
-    __shared__ ColLists L;
-    __shared__ unsigned long long s_a, s_b;
-    __shared__ long long s_slot;
-    __shared__ int s_skip, s_last, s_forced;
-    __shared__ double s_eta, s_ci_old, s_ci_new, s_Hii;
-    __shared__ dd s_mu, s_alpha;
+// One pending column element of a thread.
+struct Elem {
+    unsigned long long ka, kb;         // key D'
+    ElemIdx ix;
+    double H;
+    ulonglong2 k0;                     // first probed slot: key ...
+    double2 cb0;                       // ... and (c, b)
+    long long pos;                     // probe position
+    int state;                         // 0 none, 1 found, 2 absent (pos = first empty slot), 3 previous coordinate,
+                                       // 4 first probe issued, not yet resolved
+};
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// Decode element e and issue the load of its first probe slot (32 bytes).
+__device__ __forceinline__ void issue_elem(const Problem &P, const ColLists &L, unsigned long long iA,
+                                           unsigned long long iB, long long e, long long nh, bool have_prev,
+                                           unsigned long long pA, unsigned long long pB, Elem &x) {
+    x.state = 0;
+    if (e >= nh) return;
+    decode_element(P, L, iA, iB, e, x.ka, x.kb, x.ix);
+    if (have_prev && x.ka == pA && x.kb == pB) { x.state = 3; return; }
+    x.pos = (long long)(key_hash(x.ka, x.kb) & P.mask);
+    const Slot *s = P.table + x.pos;
+    x.k0 = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
+    x.cb0 = __ldcg(reinterpret_cast<const double2 *>(&s->c));
+    x.state = 4;
+}
+
+// Finish the lookup of an issued element: compare the first slot, probe on if
+// needed.  Sets state 1 (found: c, bv), 2 (absent at pos) or 0 (value zero or
+// error, *err set).
+__device__ __forceinline__ void resolve_elem(const Problem &P, IterState *st, Elem &x, int *err) {
+    if (x.state != 4) return;
+    if (x.H == 0.0) { x.state = 0; return; }
+    const bool both_nonzero = (P.na > 0) && (P.nb > 0);
+    unsigned long long p = (unsigned long long)x.pos;
+    ulonglong2 k = x.k0;
+    double2 cb = x.cb0;
+    for (int probe = 0; probe < P.max_probe; ++probe) {
+        int spins = 0;
+        while (both_nonzero && ((k.x == 0ull) != (k.y == 0ull))) {
+            if (++spins > (1 << 20)) { set_status(st, kErrTimeout); *err = 1; x.state = 0; return; }
+            k = __ldcg(reinterpret_cast<const ulonglong2 *>(P.table + p));
+            cb = __ldcg(reinterpret_cast<const double2 *>(&P.table[p].c));
+        }
+        if (k.x == x.ka && k.y == x.kb) { x.pos = (long long)p; x.cb0 = cb; x.state = 1; return; }
+        if (k.x == 0ull && k.y == 0ull) { x.pos = (long long)p; x.state = 2; return; }
+        p = (p + 1) & P.mask;
+        k = __ldcg(reinterpret_cast<const ulonglong2 *>(P.table + p));
+        cb = __ldcg(reinterpret_cast<const double2 *>(&P.table[p].c));
+    }
+    set_status(st, kErrTableFull);
+    *err = 1;
+    x.state = 0;
+}
+
+// Claim an empty slot for a key that no other thread inserts concurrently (in
+// an m = 1 column every determinant occurs once), starting at `pos`.
+__device__ __forceinline__ long long claim_slot(const Problem &P, IterState *st, unsigned long long a,
+                                                unsigned long long b, long long pos, int *err) {
+    unsigned long long p = (unsigned long long)pos;
+    for (int probe = 0; probe < P.max_probe; ++probe) {
+        unsigned long long oa, ob;
+        cas128(&P.table[p].a, 0ull, 0ull, a, b, oa, ob);
+        if (oa == 0ull && ob == 0ull) return (long long)p;
+        p = (p + 1) & P.mask;
+    }
+    set_status(st, kErrTableFull);
+    *err = 1;
+    return -1;
+}
+
+// The coordinate chosen for an iteration and what every warp needs about it.
+struct Sel {
+    unsigned long long iA, iB;
+    long long islot;
+    double bi, ci;
+    unsigned long long pA, pB;         // previous coordinate (its b is pending)
+    long long pslot;
+    double pb, pc;
+    double eta, mu_g;                  // step size; mu used in the gradients of this column
+    int have_prev, forced, stop, bad;
+};
+
+// Cluster-wide state kept in shared memory (identical in every CTA).
+struct LoopState {
+    unsigned long long pA, pB;
+    long long pslot;
+    double pc, pHii, pmu_g, peta;      // previous coordinate: c after its update, H_ii, the mu of its column, eta
+    dd mu, alpha;
+    double dx;
+    long long iterations, nnz_c, n_slots, elements, applied, dropped, inserted, last_column;
+    int forced, done;
+};
+
+// Warp-level combine: argmax of (gbits desc, key asc) with payload (slot, b, c),
+// sums of the counters and a lane-ordered sum of the nonzero gather values;
+// every lane returns the result.  The maximum of gbits comes from a
+// butterfly on gbits alone; only exact ties look at the keys.
+__device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb, double &gather, int cnt[4], int &err) {
+    unsigned long long gmax = best.g;
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, gmax, off);
+        gmax = y > gmax ? y : gmax;
+    }
+    const unsigned int cand = __ballot_sync(0xffffffffu, best.g == gmax && best.slot >= 0);
+    int win = cand ? __ffs(cand) - 1 : 0;
+    if (__popc(cand) > 1) {
+        unsigned long long wa = __shfl_sync(0xffffffffu, best.a, win), wb = __shfl_sync(0xffffffffu, best.b, win);
+        unsigned int rest = cand & (cand - 1);
+        while (rest) {
+            const int l = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const unsigned long long la = __shfl_sync(0xffffffffu, best.a, l), lb = __shfl_sync(0xffffffffu, best.b, l);
+            if (key_less(la, lb, wa, wb)) { win = l; wa = la; wb = lb; }
+        }
+    }
+    if (cand) {
+        best.g = gmax;
+        best.a = __shfl_sync(0xffffffffu, best.a, win);
+        best.b = __shfl_sync(0xffffffffu, best.b, win);
+        best.slot = __shfl_sync(0xffffffffu, best.slot, win);
+        bb = __shfl_sync(0xffffffffu, bb, win);
+        cb = __shfl_sync(0xffffffffu, cb, win);
+    } else {
+        best = Best{0ull, ~0ull, ~0ull, -1};
+        bb = 0.0;
+        cb = 0.0;
+    }
+    for (int k = 0; k < 4; ++k) cnt[k] = __reduce_add_sync(0xffffffffu, (unsigned)cnt[k]);
+    err = (int)__reduce_or_sync(0xffffffffu, (unsigned)err);
+    // gather: a fixed shuffle-down tree (skipped when every lane holds 0)
+    if (__any_sync(0xffffffffu, gather != 0.0)) {
+        for (int off = 16; off > 0; off >>= 1) gather += __shfl_down_sync(0xffffffffu, gather, off);
+        gather = __shfl_sync(0xffffffffu, gather, 0);
+    }
+}
+
+// Algorithm 1 by one thread-block cluster that keeps running: each iteration
+// every CTA scatters a share of the column, writes a partial (best candidate,
+// gather, counters) into its own shared memory, and after the cluster barrier
+// warp 0 of every CTA reads all partials through distributed shared memory and
+// reduces them in a fixed order, so every CTA makes the same choice.  The
+// serial steps (H_ii, eta, the double-double scalars) run on single lanes;
+// their results reach the other warps through shared memory.  Every exit
+// decision uses data all CTAs read identically, so all CTAs reach every
+// cluster barrier.
+__global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState *st, CdRecord *rec,
+                                                           CdPartial *gpart, long long n_iter) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int G = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    __shared__ CdPartial spart[2];
+    __shared__ ColLists Lw[kCdWarps];
     __shared__ Best r_best[kCdWarps];
-    __shared__ double r_gather[kCdWarps];
+    __shared__ double r_bc[kCdWarps][3];
     __shared__ int r_cnt[4][kCdWarps];
+    __shared__ Sel sel;
+    __shared__ int s_done;
+    LoopState ls;                                // meaningful in the control warp (warp 0) only
+    __shared__ double s_hii;
+    __shared__ dd s_mu_n, s_al_n;
+    __shared__ int s_err;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        volatile IterState *vs = st;
-        s_skip = vs->done | vs->status;
-        s_a = st->sel_a;
-        s_b = st->sel_b;
-        s_slot = st->sel_slot;
-        s_forced = st->forced_eta_one;
-    }
-    __syncthreads();
-    if (s_skip) return;
-    const unsigned long long A = s_a, B = s_b;
-    build_lists(L, P.N, A, B);
-    __syncthreads();
-
-    // ---- prologue: H_ii, step size, scalars (identical in every CTA) ----
+    if (rec->done) return;                       // uniform: nothing has synchronised yet
     if (warp == 0) {
-        double Hii = diag_warp(P, L);
+        const CdRecord &R = *rec;
+        ls.pA = R.a; ls.pB = R.b; ls.pslot = R.slot;
+        ls.pc = R.c_new; ls.pHii = R.Hii; ls.pmu_g = R.mu_g; ls.peta = R.eta;
+        ls.mu = R.mu; ls.alpha = R.alpha; ls.dx = R.dx;
+        ls.iterations = R.iterations; ls.nnz_c = R.nnz_c; ls.n_slots = R.n_slots; ls.elements = R.elements;
+        ls.applied = R.applied; ls.dropped = R.dropped; ls.inserted = R.inserted; ls.last_column = R.last_column;
+        ls.forced = R.forced; ls.done = 0;
         if (lane == 0) {
-            Slot *si = P.table + s_slot;
-            double c = __ldcg(&si->c), b = __ldcg(&si->bv);
-            dd mu = st->mu, alpha = st->alpha;
-            double eta;
-            if (s_forced) {
-                eta = 1.0;
-            } else {
-                double v1 = 4.0 * b + 4.0 * mu.hi * c;
-                double v2 = 2.0 * Hii + 4.0 * c * c + 2.0 * mu.hi;
-                double v3 = 4.0 * c;
-                eta = line_search(v1, v2, v3);
-            }
-            // mu += 2 eta c + eta^2 ; alpha += 2 eta b + eta^2 H_ii
-            dd e2 = dd_two_prod(eta, eta);
-            dd mu_n = dd_add(dd_add(mu, dd_two_prod(2.0 * eta, c)), e2);
-            dd al_n = dd_add(dd_add(alpha, dd_two_prod(2.0 * eta, b)), dd_mul_d(e2, Hii));
-            s_eta = eta;
-            s_ci_old = c;
-            s_ci_new = c + eta;
-            s_Hii = Hii;
-            s_mu = mu_n;
-            s_alpha = al_n;
+            spart[1] = gpart[rank];
+            s_err = 0;
+            s_done = 0;
         }
     }
-    __syncthreads();
-    const double eta = s_eta, mu = s_mu.hi, tau = P.tau;
+    cluster.sync();
+
+    // Element e - 1 = lane + 32 * (rank + G * (w + W' * j)), w = warp - 1, W' = warps - 1,
+    // j = 0, 1, ...: 32 consecutive elements per warp, consecutive warps' worth
+    // on different CTAs.  The single excitations (the first elements, each an
+    // O(n) sum) thus fill whole warps spread over CTAs: their FP64 sums run
+    // with all lanes active.  Warp 0 is the control warp and owns no elements.
     const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
+    constexpr int Wp = kCdWarps - 1;
+    const long long stride = (long long)G * Wp * 32;
+    const long long e0 = warp == 0 ? nh : 1 + lane + 32ll * (rank + (long long)G * (warp - 1));
+    int lastp = 1;
+    for (long long it = 0; it < n_iter; ++it) {
+        const int pin = lastp, pout = lastp ^ 1;
+        // ---- choice of i (Eq. choose-i), by the control warp ----
+        if (warp == 0) {
+            if (ls.forced) {
+                if (lane == 0) {
+                    sel.iA = ls.pA; sel.iB = ls.pB; sel.islot = ls.pslot; sel.bi = 0.0; sel.ci = 0.0;
+                    sel.have_prev = 0; sel.forced = 1; sel.stop = 0;
+                }
+            } else {
+                CdPartial x;
+                const bool have = lane < G;   // all lanes take part in the combine
+                if (have) x = *cluster.map_shared_rank(&spart[pin], lane);
+                Best bb = have ? Best{x.gbits, x.ka, x.kb, x.slot} : Best{0ull, ~0ull, ~0ull, -1};
+                double bj = have ? x.bj : 0.0, cj = have ? x.cj : 0.0, gsum = have ? x.gather : 0.0;
+                int cnt[4] = {have ? x.elements : 0, have ? x.applied : 0, have ? x.dropped : 0, have ? x.inserted : 0};
+                int err = have ? x.err : 0;
+                warp_combine(bb, bj, cj, gsum, cnt, err);
+                // recalculated b of the previous coordinate (Eq. recalculate-b) and its gradient
+                const double pb = fma(ls.pHii, ls.pc, gsum);
+                const unsigned long long gp = abs_bits(fma(ls.pmu_g, ls.pc, pb));
+                const long long nslots = ls.n_slots + cnt[3];
+                if (lane == 0) {
+                    sel.pA = ls.pA; sel.pB = ls.pB; sel.pslot = ls.pslot; sel.pb = pb; sel.pc = ls.pc;
+                    sel.have_prev = 1; sel.forced = 0;
+                    if (better(gp, ls.pA, ls.pB, bb.g, bb.a, bb.b)) {
+                        sel.iA = ls.pA; sel.iB = ls.pB; sel.islot = ls.pslot; sel.bi = pb; sel.ci = ls.pc;
+                        sel.stop = (err != 0) || (nslots > P.max_entries);
+                    } else {
+                        sel.iA = bb.a; sel.iB = bb.b; sel.islot = bb.slot; sel.bi = bj; sel.ci = cj;
+                        sel.stop = (err != 0) || (nslots > P.max_entries) || (bb.slot < 0);
+                    }
+                    if (nslots > P.max_entries) set_status(st, kErrTableFull);
+                }
+                const long long pdiag = ls.pHii != 0.0 ? 1 : 0;
+                ls.elements += cnt[0] + pdiag;
+                ls.applied += cnt[1] + pdiag;
+                ls.dropped += cnt[2];
+                ls.inserted += cnt[3];
+                ls.n_slots = nslots;
+                ls.last_column = cnt[0] + pdiag;
+            }
+        }
+        __syncthreads();
+        if (sel.stop) break;                          // identical in every CTA of the cluster
+        const unsigned long long iA = sel.iA, iB = sel.iB;
+        const bool have_prev = sel.have_prev != 0;
+        const unsigned long long pA = sel.pA, pB = sel.pB;
 
-    // ---- scatter / gather / argmax over this CTA's elements ----
-    Best best{0ull, ~0ull, ~0ull, -1};
-    double gather = 0.0;
-    int n_el = 0, n_app = 0, n_drop = 0, n_ins = 0;
-    for (long long e = 1 + (long long)blockIdx.x * kCdThreads + tid; e < nh; e += (long long)gridDim.x * kCdThreads) {
-        unsigned long long oa, ob;
-        double H = column_element(P, L, A, B, e, oa, ob);
-        if (H == 0.0) continue;
-        ++n_el;
-        double v = eta * H;
-        bool big = fabs(v) >= tau;
-        bool ins = false;
-        long long s = table_find(P, st, oa, ob, big, &ins);
-        if (s == -2) break;
-        if (s < 0) { ++n_drop; continue; }
-        Slot *sj = P.table + s;
-        double cj = __ldcg(&sj->c);
-        if (cj != 0.0 || big) {
-            double old = atomicAdd(&sj->bv, v);
-            double bn = old + v;
-            ++n_app;
-            n_ins += ins ? 1 : 0;
-            unsigned long long gb = (unsigned long long)__double_as_longlong(fabs(4.0 * (bn + mu * cj)));
-            if (better(gb, oa, ob, best.g, best.a, best.b)) best = Best{gb, oa, ob, s};
-            gather = fma(H, cj, gather);
+        // ---- lists (every warp) ----
+        ColLists &L = Lw[warp];
+        for (int t = lane; t < P.N; t += 32) {
+            int ra = __popcll(iA & low_mask(t)), rb = __popcll(iB & low_mask(t));
+            if ((iA >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+            if ((iB >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+        }
+        __syncwarp();
+        Elem el[kCdMaxE];
+        if (warp == 0) {
+            // ---- control warp: H_ii and the step size (appendix) ----
+            const double Hii = diag_warp(P, L);
+            if (lane == 0) {
+                const double bi = sel.bi, ci = sel.ci;
+                double eta;
+                if (sel.forced) {
+                    eta = 1.0;
+                } else {
+                    const double mu0 = ls.pmu_g;          // c.c within 2 ulp (the double-double value runs behind)
+                    eta = line_search(4.0 * bi + 4.0 * mu0 * ci, 2.0 * Hii + 4.0 * ci * ci + 2.0 * mu0, 4.0 * ci);
+                }
+                sel.eta = eta;
+                sel.mu_g = ls.mu.hi + fma(2.0 * eta, ci, eta * eta);
+                sel.bad = !isfinite(eta);
+                s_hii = Hii;
+            }
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k) el[k].state = 0;
         } else {
-            ++n_drop;
+            // ---- element warps: decode, issue first probes, values ----
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k) issue_elem(P, L, iA, iB, e0 + k * stride, nh, have_prev, pA, pB, el[k]);
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k)
+                if (el[k].state != 0) el[k].H = element_value(P, L, el[k].ix);
         }
-    }
-    warp_best(best);
-    gather = warp_sum(gather);
-    n_el = warp_isum(n_el);
-    n_app = warp_isum(n_app);
-    n_drop = warp_isum(n_drop);
-    n_ins = warp_isum(n_ins);
-    if (lane == 0) {
-        r_best[warp] = best;
-        r_gather[warp] = gather;
-        r_cnt[0][warp] = n_el;
-        r_cnt[1][warp] = n_app;
-        r_cnt[2][warp] = n_drop;
-        r_cnt[3][warp] = n_ins;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        Best b = r_best[0];
-        double gs = r_gather[0];
-        int c0 = r_cnt[0][0], c1 = r_cnt[1][0], c2 = r_cnt[2][0], c3 = r_cnt[3][0];
-        for (int w = 1; w < kCdWarps; ++w) {
-            if (better(r_best[w].g, r_best[w].a, r_best[w].b, b.g, b.a, b.b)) b = r_best[w];
-            gs += r_gather[w];
-            c0 += r_cnt[0][w]; c1 += r_cnt[1][w]; c2 += r_cnt[2][w]; c3 += r_cnt[3][w];
+        __syncthreads();
+        if (warp == 0 && lane < 2) {
+            // lane 0: mu += 2 eta c_i + eta^2; lane 1: alpha += 2 eta b_i + eta^2 H_ii (double-double)
+            const double eta = sel.eta;
+            const dd x0 = lane == 0 ? ls.mu : ls.alpha;
+            const double y1 = lane == 0 ? sel.ci : sel.bi;
+            const double y2 = lane == 0 ? 1.0 : s_hii;
+            const dd t = dd_add_fast(dd_two_prod(2.0 * eta, y1), dd_mul_d(dd_two_prod(eta, eta), y2));
+            const dd r = dd_add_fast(x0, t);
+            if (lane == 0) s_mu_n = r; else s_al_n = r;
         }
-        CdPartial pp;
-        pp.gather = gs; pp.gbits = b.g; pp.ka = b.a; pp.kb = b.b; pp.slot = b.slot;
-        pp.elements = c0; pp.applied = c1; pp.dropped = c2; pp.inserted = c3;
-        part[blockIdx.x] = pp;
-        __threadfence();
-        unsigned int t = atomicAdd(&st->arrive, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+        const double eta = sel.eta;
+        const double mu = sel.mu_g;
+        const unsigned long long tau_bits = abs_bits(P.tau);
+        const long long pslot = sel.pslot;
+        const double pb = sel.pb, pc = sel.pc;
+        const bool bad = sel.bad != 0;
 
-    // ---- tail: the last CTA to arrive finishes the iteration ----
-    Best tb{0ull, ~0ull, ~0ull, -1};
-    double tg = 0.0;
-    long long tc[4] = {0, 0, 0, 0};
-    for (int q = tid; q < (int)gridDim.x; q += kCdThreads) {   // fixed order per thread
-        CdPartial pp = load_partial(part + q);
-        if (better(pp.gbits, pp.ka, pp.kb, tb.g, tb.a, tb.b)) tb = Best{pp.gbits, pp.ka, pp.kb, pp.slot};
-        tg += pp.gather;
-        tc[0] += pp.elements; tc[1] += pp.applied; tc[2] += pp.dropped; tc[3] += pp.inserted;
+        // ---- apply: b_j += eta H_ji with compression, gather, candidates ----
+        Best best{0ull, ~0ull, ~0ull, -1};
+        double bbest = 0.0, cbest = 0.0, gather = 0.0;
+        int cnt[4] = {0, 0, 0, 0};                     // elements, applied, dropped, inserted
+        int err = 0;
+        for (long long eb = e0; !bad && eb < nh;) {
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k) resolve_elem(P, st, el[k], &err);
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k) {
+                Elem &x = el[k];
+                if (x.state == 0) continue;
+                const double H = x.H;
+                const double v = eta * H;
+                const bool big = abs_bits(v) >= tau_bits;
+                double cj, bn;
+                long long sj;
+                if (x.state == 3) {                       // the previous coordinate: c and b known
+                    cj = pc;
+                    sj = pslot;
+                    if (H == 0.0) { P.table[sj].bv = pb; continue; }
+                    ++cnt[0];
+                    if (!(cj != 0.0 || big)) { P.table[sj].bv = pb; ++cnt[2]; continue; }
+                    bn = pb + v;
+                } else if (x.state == 1) {
+                    cj = x.cb0.x;
+                    sj = x.pos;
+                    ++cnt[0];
+                    if (!(cj != 0.0 || big)) { ++cnt[2]; continue; }
+                    bn = x.cb0.y + v;
+                } else {                                  // absent
+                    ++cnt[0];
+                    if (!big) { ++cnt[2]; continue; }
+                    sj = claim_slot(P, st, x.ka, x.kb, x.pos, &err);
+                    if (sj < 0) continue;
+                    cj = 0.0;
+                    bn = v;
+                    ++cnt[3];
+                }
+                ++cnt[1];
+                P.table[sj].bv = bn;
+                unsigned long long gb;
+                if (cj != 0.0) {
+                    gather = fma(H, cj, gather);
+                    gb = abs_bits(fma(mu, cj, bn));
+                } else {
+                    gb = abs_bits(bn);
+                }
+                if (better(gb, x.ka, x.kb, best.g, best.a, best.b)) {
+                    best = Best{gb, x.ka, x.kb, sj};
+                    bbest = bn;
+                    cbest = cj;
+                }
+            }
+            eb += kCdMaxE * stride;
+            if (eb >= nh) break;
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k) issue_elem(P, L, iA, iB, eb + k * stride, nh, have_prev, pA, pB, el[k]);
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k)
+                if (el[k].state != 0) el[k].H = element_value(P, L, el[k].ix);
+        }
+
+        // ---- CTA partial into this CTA's shared memory ----
+        warp_combine(best, bbest, cbest, gather, cnt, err);
+        if (lane == 0) {
+            r_best[warp] = best;
+            r_bc[warp][0] = bbest;
+            r_bc[warp][1] = cbest;
+            r_bc[warp][2] = gather;
+            for (int k = 0; k < 4; ++k) r_cnt[k][warp] = cnt[k];
+            if (err) atomicOr(&s_err, 1);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const bool have = lane < kCdWarps;
+            Best b = have ? r_best[lane] : Best{0ull, ~0ull, ~0ull, -1};
+            double bj = have ? r_bc[lane][0] : 0.0, cj = have ? r_bc[lane][1] : 0.0;
+            double gs = have ? r_bc[lane][2] : 0.0;
+            int c4[4] = {have ? r_cnt[0][lane] : 0, have ? r_cnt[1][lane] : 0, have ? r_cnt[2][lane] : 0,
+                         have ? r_cnt[3][lane] : 0};
+            int e2 = 0;
+            warp_combine(b, bj, cj, gs, c4, e2);
+            if (lane == 0) {
+                CdPartial pp;
+                pp.gbits = b.g; pp.ka = b.a; pp.kb = b.b; pp.slot = b.slot;
+                pp.bj = bj; pp.cj = cj; pp.gather = gs;
+                pp.elements = c4[0]; pp.applied = c4[1]; pp.dropped = c4[2]; pp.inserted = c4[3];
+                pp.err = s_err | (bad ? 1 : 0);
+                spart[pout] = pp;
+                // the coordinate's own slot: c_i += eta, b_i as used (rank 0 writes)
+                const double ci = sel.ci, ci_new = ci + sel.eta;
+                if (rank == 0 && !bad) {
+                    P.table[sel.islot].c = ci_new;
+                    P.table[sel.islot].bv = sel.bi;
+                }
+                if (bad && rank == 0) set_status(st, kErrNonfinite);
+            }
+            // every lane of the control warp keeps the same copy of the state
+            const double ci = sel.ci, ci_new = ci + sel.eta;
+            ls.pA = sel.iA; ls.pB = sel.iB; ls.pslot = sel.islot;
+            ls.pc = ci_new; ls.pHii = s_hii; ls.pmu_g = sel.mu_g; ls.peta = sel.eta;
+            ls.mu = s_mu_n; ls.alpha = s_al_n;
+            if (!sel.forced) {
+                ls.iterations += 1;
+                ls.dx = P.theta * ls.dx + (1.0 - P.theta) * fabs(sel.eta);
+                if (P.dx_threshold > 0.0 && ls.dx < P.dx_threshold) ls.done = 1;
+            }
+            ls.nnz_c += ((ci == 0.0 && ci_new != 0.0) ? 1 : 0) - ((ci != 0.0 && ci_new == 0.0) ? 1 : 0);
+            ls.forced = 0;
+            if (lane == 0) s_done = ls.done;
+        }
+        if (G == 1) __syncthreads(); else cluster.sync();   // partials and table writes visible cluster-wide
+        lastp = pout;
+        if (s_done || bad) break;                         // identical in every CTA
     }
-    warp_best(tb);
-    tg = warp_sum(tg);
-    for (int k = 0; k < 4; ++k)
-        for (int off = 16; off > 0; off >>= 1) tc[k] += __shfl_down_sync(0xffffffffu, tc[k], off);
-    __shared__ long long r_tc[4][kCdWarps];
-    if (lane == 0) {
-        r_best[warp] = tb;
-        r_gather[warp] = tg;
-        for (int k = 0; k < 4; ++k) r_tc[k][warp] = tc[k];
+
+    // ---- state for the next launch / the finalisation ----
+    if (tid == 0) gpart[rank] = spart[lastp];
+    if (tid == 0 && rank == 0) {      // lane 0 of the control warp holds the state
+        CdRecord o;
+        o.a = ls.pA; o.b = ls.pB; o.slot = ls.pslot;
+        o.c_new = ls.pc; o.Hii = ls.pHii; o.eta = ls.peta;
+        o.mu = ls.mu; o.alpha = ls.alpha; o.dx = ls.dx; o.mu_g = ls.pmu_g;
+        o.energy = dd_div_to_d(ls.alpha, ls.mu);
+        o.iterations = ls.iterations; o.nnz_c = ls.nnz_c; o.n_slots = ls.n_slots; o.elements = ls.elements;
+        o.applied = ls.applied; o.dropped = ls.dropped; o.inserted = ls.inserted; o.last_column = ls.last_column;
+        o.forced = ls.forced; o.done = ls.done;
+        *rec = o;
     }
-    __syncthreads();
-    if (tid != 0) return;
-    Best b = r_best[0];
-    double gsum = r_gather[0];
-    long long cnt[4] = {r_tc[0][0], r_tc[1][0], r_tc[2][0], r_tc[3][0]};
-    for (int w = 1; w < kCdWarps; ++w) {
-        if (better(r_best[w].g, r_best[w].a, r_best[w].b, b.g, b.a, b.b)) b = r_best[w];
-        gsum += r_gather[w];
-        for (int k = 0; k < 4; ++k) cnt[k] += r_tc[k][w];
+}
+
+// After a batch of iterations: write the pending recalculated b_i of the last
+// processed coordinate and a host-visible snapshot of the counters.
+__global__ void k_cd_finalize(Problem P, IterState *st, const CdRecord *rec, const CdPartial *gpart, int G) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const CdRecord R = *rec;
+    CdPartial x;
+    const bool have = lane < G && !R.forced;
+    if (have) x = gpart[lane];
+    double gsum = have ? x.gather : 0.0;
+    long long cnt[4] = {have ? x.elements : 0, have ? x.applied : 0, have ? x.dropped : 0, have ? x.inserted : 0};
+    for (int off = 16; off > 0; off >>= 1) {
+        gsum += __shfl_down_sync(0xffffffffu, gsum, off);
+        for (int k = 0; k < 4; ++k) cnt[k] += __shfl_down_sync(0xffffffffu, cnt[k], off);
     }
-    // recalculated b_i = H_ii c_i + sum_{j != i} H_ji c_j with the updated c
-    const double ci = s_ci_new;
-    const double bi = fma(s_Hii, ci, gsum);
-    Slot *si = P.table + s_slot;
-    si->c = ci;
-    si->bv = bi;
-    unsigned long long gi_bits = (unsigned long long)__double_as_longlong(fabs(4.0 * (bi + mu * ci)));
-    if (better(gi_bits, A, B, b.g, b.a, b.b)) b = Best{gi_bits, A, B, s_slot};
-    if (!isfinite(__longlong_as_double((long long)b.g)) || !isfinite(eta) || !isfinite(s_mu.hi) ||
-        !isfinite(s_alpha.hi))
-        set_status(st, kErrNonfinite);
-    if (b.slot < 0 || b.slot >= P.capacity) {   // cannot happen: i itself is always a candidate
-        set_status(st, kErrArg);
-        b = Best{gi_bits, A, B, s_slot};
-    }
-    st->sel_a = b.a;
-    st->sel_b = b.b;
-    st->sel_slot = b.slot;
-    st->mu = s_mu;
-    st->alpha = s_alpha;
-    st->energy = dd_div_to_d(s_alpha, s_mu);
-    st->last_eta = eta;
-    st->last_a = A;
-    st->last_b = B;
-    if (s_forced) {
-        st->forced_eta_one = 0;
-    } else {
-        st->iterations += 1;
-        st->dx = P.theta * st->dx + (1.0 - P.theta) * fabs(eta);
-        if (P.dx_threshold > 0.0 && st->dx < P.dx_threshold) st->done = 1;
-    }
-    if (s_ci_old == 0.0 && ci != 0.0) st->nnz_c += 1;
-    if (s_ci_old != 0.0 && ci == 0.0) st->nnz_c -= 1;
-    const int diag_nz = (s_Hii != 0.0) ? 1 : 0;
-    st->elements += cnt[0] + diag_nz;
-    st->applied += cnt[1] + diag_nz;
-    st->dropped += cnt[2];
-    st->inserted += cnt[3];
-    st->n_slots += cnt[3];
-    st->last_column = cnt[0] + diag_nz;
+    if (lane != 0) return;
+    const long long pdiag = (!R.forced && R.Hii != 0.0) ? 1 : 0;
+    if (!R.forced && st->status == 0) P.table[R.slot].bv = fma(R.Hii, R.c_new, gsum);
+    st->iterations = R.iterations;
+    st->nnz_c = R.nnz_c;
+    st->n_slots = R.n_slots + cnt[3];
+    st->elements = R.elements + cnt[0] + pdiag;
+    st->applied = R.applied + cnt[1] + pdiag;
+    st->dropped = R.dropped + cnt[2];
+    st->inserted = R.inserted + cnt[3];
+    st->last_column = R.forced ? 0 : cnt[0] + pdiag;
+    st->mu = R.mu;
+    st->alpha = R.alpha;
+    st->dx = R.dx;
+    st->energy = R.energy;
+    st->last_eta = R.eta;
+    st->last_a = R.a;
+    st->last_b = R.b;
+    st->done = R.done;
     if (st->n_slots > P.max_entries) set_status(st, kErrTableFull);
-    st->arrive = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -446,45 +726,83 @@ __global__ void k_jk(const double *g, int N, double *J, double *K, int *has_doub
     }
 }
 
-// Insert the start determinant and set the state for the initialisation launch
-// (c = e_ref reached from c = 0 with eta = 1: mu = 1, alpha = H_ref,ref).
-__global__ void k_init_state(Problem P, IterState *st, unsigned long long A, unsigned long long B) {
+// Insert the start determinant and write the record that makes the next
+// iteration the initialisation: c = e_ref reached from c = 0 with eta = 1,
+// so mu = 1 and alpha = H_ref,ref.
+__global__ void k_init_state(Problem P, IterState *st, CdRecord *rec, unsigned long long A, unsigned long long B) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     bool ins = false;
     long long s = table_find(P, st, A, B, true, &ins);
-    st->sel_a = A;
-    st->sel_b = B;
-    st->sel_slot = s < 0 ? 0 : s;
-    if (s < 0) set_status(st, kErrTableFull);
-    st->forced_eta_one = 1;
-    st->done = 0;
-    st->arrive = 0u;
-    st->mu = dd_from(0.0);
-    st->alpha = dd_from(0.0);
+    if (s < 0) { set_status(st, kErrTableFull); s = 0; }
+    CdRecord r;
+    r.a = A; r.b = B; r.slot = s;
+    r.c_new = 0.0; r.Hii = 0.0; r.eta = 0.0;
+    r.mu = dd_from(0.0); r.alpha = dd_from(0.0);
+    r.dx = 0.0; r.energy = 0.0;
+    r.iterations = 0; r.nnz_c = 0; r.n_slots = 1; r.elements = 0; r.applied = 0; r.dropped = 0;
+    r.inserted = 1; r.last_column = 0;
+    r.forced = 1;
+    r.done = 0;
+    r.mu_g = 0.0;
+    rec[0] = r;
+    st->last_parity = 0;
     st->scale = dd_from(1.0);
-    st->dx = 0.0;
-    st->energy = 0.0;
-    st->iterations = 0;
-    st->last_eta = 0.0;
-    st->last_a = A;
-    st->last_b = B;
-    st->nnz_c = 0;
-    st->n_slots = 1;
-    st->last_column = 0;
-    st->elements = 0;
-    st->applied = 0;
-    st->dropped = 0;
-    st->inserted = 1;
 }
 
 // ---------------------------------------------------------------------------
 // Launch wrappers (host)
 // ---------------------------------------------------------------------------
-cudaError_t launch_cd_iter(const Problem &P, IterState *st, CdPartial *part, int grid, cudaStream_t s) {
-    k_cd_iter<<<grid, kCdThreads, 0, s>>>(P, st, part);
+cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
+                           long long n_iter, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = dim3(kCdThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_cd_loop, P, st, rec, part, n_iter);
+}
+
+// Largest cluster size <= want (power of two) that can be resident.
+int cd_pick_cluster(int want) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        attr_set = true;
+    }
+    int c = 1;
+    while (c < want && c * 2 <= kCdMaxCluster) c *= 2;
+    for (; c > 1; c /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kCdThreads);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_cd_loop, &cfg) == cudaSuccess && n >= 1) return c;
+        cudaGetLastError();
+    }
+    return 1;
+}
+
+cudaError_t launch_cd_finalize(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
+                               cudaStream_t s) {
+    k_cd_finalize<<<1, 32, 0, s>>>(P, st, rec, part, cluster);
     return cudaGetLastError();
 }
-int cd_threads() { return kCdThreads; }
+int cd_threads() { return kCdThreads - 32; }
+int cd_elements_per_thread() { return kCdMaxE; }
 
 cudaError_t launch_column(const Problem &P, unsigned long long A, unsigned long long B, unsigned long long *keys,
                           double *vals, long long cap, unsigned long long *counter, cudaStream_t s) {
@@ -527,9 +845,9 @@ cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_state(const Problem &P, IterState *st, unsigned long long A, unsigned long long B,
-                              cudaStream_t s) {
-    k_init_state<<<1, 32, 0, s>>>(P, st, A, B);
+cudaError_t launch_init_state(const Problem &P, IterState *st, CdRecord *rec, unsigned long long A,
+                              unsigned long long B, cudaStream_t s) {
+    k_init_state<<<1, 32, 0, s>>>(P, st, rec, A, B);
     return cudaGetLastError();
 }
 

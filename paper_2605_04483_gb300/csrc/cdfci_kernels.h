@@ -6,8 +6,13 @@
 
 namespace cdfci {
 
-cudaError_t launch_cd_iter(const Problem &P, IterState *st, CdPartial *part, int grid, cudaStream_t s);
+cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
+                           long long n_iter, cudaStream_t s);
+int cd_pick_cluster(int want);
+cudaError_t launch_cd_finalize(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
+                               cudaStream_t s);
 int cd_threads();
+int cd_elements_per_thread();
 cudaError_t launch_column(const Problem &P, unsigned long long A, unsigned long long B, unsigned long long *keys,
                           double *vals, long long cap, unsigned long long *counter, cudaStream_t s);
 cudaError_t launch_export(const Problem &P, const IterState *st, unsigned long long *keys, double *c, double *b,
@@ -16,8 +21,8 @@ cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long lon
                       double *partial, int nblocks, double *out, cudaStream_t s);
 cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int *status, int *has_doubles,
                          cudaStream_t s);
-cudaError_t launch_init_state(const Problem &P, IterState *st, unsigned long long A, unsigned long long B,
-                              cudaStream_t s);
+cudaError_t launch_init_state(const Problem &P, IterState *st, CdRecord *rec, unsigned long long A,
+                              unsigned long long B, cudaStream_t s);
 
 // sets the message returned by cdfci_last_error() on the calling thread
 void set_last_error_message(const char *msg);
