@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 ALGO_BYTES_PER_ELEMENT = 40      # 16 B key compare + 8 B c read + 8 B b read + 8 B b write
 WORKLOAD = dict(name="abinitio_N24_6a6b_seed2", N=24, n_alpha=6, n_beta=6, seed=2, tau=1e-5, log2_capacity=27, m=1)
 KERNEL_SOURCES = ["paper_2605_04483_gb300/csrc/cdfci_kernels.cu", "paper_2605_04483_gb300/csrc/cdfci_internal.cuh"]
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_cd_iter_abinitio_N24.txt")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_cd_loop_abinitio_N24.txt")
 
 
 def kernel_hash() -> str:
@@ -274,12 +274,14 @@ def main():
         return
 
     peak, peak_kind = measured_peaks()
-    avg_launch_s = ms * 1e-3 / max(launches, 1)
-    el_per_launch = elements / max(launches, 1)
+    # one k_cd_loop launch per step runs all its iterations (plus one small finalisation launch)
+    loop_launches = args.steps
+    avg_launch_s = ms * 1e-3 / loop_launches
+    el_per_launch = elements / loop_launches
     achieved = el_per_launch * ALGO_BYTES_PER_ELEMENT / avg_launch_s / 1e9
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_cd_iter (fused column update, one launch per iteration)",
+                "traffic": traffic, "kernel": f"k_cd_loop (persistent 16-CTA cluster, {ips} iterations per launch)",
                 "algorithmic_bytes_per_launch": el_per_launch * ALGO_BYTES_PER_ELEMENT,
                 "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
 
@@ -291,9 +293,9 @@ def main():
                        "iters_per_step": ips, "column_length": 16471,
                        "l2": "inputs larger than L2 (4 GiB hash table), no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": roofline, "gpu_launches": int(2 * args.steps), "clocks": clk,
             "energy_after_timed_steps": final_energy,
-            "us_per_iteration": ms / max(launches, 1) * 1e3}
+            "us_per_iteration": ms / max(launches, 1) * 1e3, "iterations_timed": int(launches)}
 
     if not args.no_extras:
         # ---- end to end through the C-ABI from pinned host buffers ----------------------

@@ -215,6 +215,9 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
     P.seg[3] = P.seg[2] + (long long)P.ca2 * P.cva2;
     P.seg[4] = P.seg[3] + (long long)P.cb2 * P.cvb2;
     P.seg[5] = P.seg[4] + (long long)P.na * P.va * P.nb * P.vb;
+    P.mg_va = fdiv_magic((unsigned)P.va); P.mg_vb = fdiv_magic((unsigned)P.vb);
+    P.mg_nsb = fdiv_magic((unsigned)(P.nb * P.vb));
+    P.mg_cva2 = fdiv_magic((unsigned)P.cva2); P.mg_cvb2 = fdiv_magic((unsigned)P.cvb2);
     P.nh = P.seg[5];
     P.capacity = 1ll << prm.log2_capacity;
     P.mask = (unsigned long long)P.capacity - 1ull;
@@ -276,7 +279,7 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         const long long per_cta = (long long)cd_threads() * cd_elements_per_thread();
         const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
         const long long want = prm.grid_blocks > 0 ? prm.grid_blocks : (nh_eff - 1 + per_cta - 1) / per_cta;
-        c->grid = cd_pick_cluster((int)std::max<long long>(1, std::min<long long>(want, 16)));
+        c->grid = cd_pick_cluster((int)std::max<long long>(1, std::min<long long>(want, 16)), cd_dynamic_smem(P));
     }
     if (prm.graph_chunk > 0) c->chunk = prm.graph_chunk;
     if (cudaMemsetAsync(c->d_table, 0, (size_t)P.capacity * sizeof(Slot), s) != cudaSuccess ||

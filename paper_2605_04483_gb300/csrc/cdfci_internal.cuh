@@ -142,6 +142,7 @@ struct Problem {
     int max_probe;
     double tau;
     double theta, dx_threshold;
+    unsigned long long mg_va, mg_vb, mg_nsb, mg_cva2, mg_cvb2;   // fdiv multipliers
 };
 
 // ---------------------------------------------------------------------------
@@ -164,9 +165,28 @@ __host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long 
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
     return z ^ (z >> 31);
 }
-__host__ __device__ __forceinline__ unsigned long long key_hash(unsigned long long a, unsigned long long b) {
-    return mix64(a ^ mix64(b ^ 0x9e3779b97f4a7c15ull));
+// Slot hash of a determinant: the xor of independent hashes of its alpha and
+// beta strings (two-character tabulation-style combination), so that the
+// hash of an excitation can be assembled from per-column tables.
+__host__ __device__ __forceinline__ unsigned long long hash_alpha(unsigned long long a) {
+    return mix64(a ^ 0x9e3779b97f4a7c15ull);
 }
+__host__ __device__ __forceinline__ unsigned long long hash_beta(unsigned long long b) {
+    return mix64(b ^ 0xd1b54a32d192ed03ull);
+}
+__host__ __device__ __forceinline__ unsigned long long key_hash(unsigned long long a, unsigned long long b) {
+    return hash_alpha(a) ^ hash_beta(b);
+}
+
+// floor(n / d) for n < 2^24, d < 2^16 with M = floor(2^40 / d) + 1 (the
+// rounding error n (M - 2^40/d) / 2^40 < 1/d cannot reach the next integer).
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned n, unsigned long long M) {
+    return (unsigned)(((unsigned long long)n * M) >> 40);
+}
+__host__ __forceinline__ unsigned long long fdiv_magic(unsigned d) { return d ? (1ull << 40) / d + 1 : 0; }
+
+// +0.0 or -0.0, tested on the bit pattern (keeps the test off the FP64 pipe)
+__device__ __forceinline__ bool is_zero(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull; }
 // key order for tie-breaks: unsigned 128-bit (B << 64) | A
 __device__ __forceinline__ bool key_less(unsigned long long a1, unsigned long long b1,
                                          unsigned long long a2, unsigned long long b2) {
@@ -254,6 +274,7 @@ struct ElemIdx {
     int kind;                          // 0 single alpha, 1 single beta, 2 double aa, 3 double bb, 4 double ab
     int i, a, j, b;                    // orbitals (j, b unused for singles)
     unsigned long long sgn;            // bits whose parity gives the sign (two masks folded by xor)
+    int gidx;                          // for kind 4: index of (ia|jb) in g, or -1
 };
 
 // Integer part of column element e in [1, nh): the excitation and the key D'.
@@ -266,7 +287,7 @@ __device__ __forceinline__ void decode_element(const Problem &P, const ColLists 
         const bool alpha = e < P.seg[1];
         const unsigned idx = (unsigned)(e - (alpha ? P.seg[0] : P.seg[1]));
         const unsigned v = (unsigned)(alpha ? P.va : P.vb);
-        const int o = (int)(idx / v), w = (int)(idx - (unsigned)o * v);
+        const int o = (int)fdiv(idx, alpha ? P.mg_va : P.mg_vb), w = (int)(idx - (unsigned)o * v);
         const int i = alpha ? L.occA[o] : L.occB[o];
         const int a = alpha ? L.virA[w] : L.virB[w];
         const unsigned long long X = alpha ? A : B;
@@ -274,6 +295,7 @@ __device__ __forceinline__ void decode_element(const Problem &P, const ColLists 
         x.kind = alpha ? 0 : 1;
         x.i = i; x.a = a; x.j = 0; x.b = 0;
         x.sgn = X & between_mask(i, a);
+        x.gidx = -1;
         oa = alpha ? (A ^ flip) : A;
         ob = alpha ? B : (B ^ flip);
         return;
@@ -282,7 +304,7 @@ __device__ __forceinline__ void decode_element(const Problem &P, const ColLists 
         const bool alpha = e < P.seg[3];
         const unsigned idx = (unsigned)(e - (alpha ? P.seg[2] : P.seg[3]));
         const unsigned cv = (unsigned)(alpha ? P.cva2 : P.cvb2);
-        const int op = (int)(idx / cv), vp = (int)(idx - (unsigned)op * cv);
+        const int op = (int)fdiv(idx, alpha ? P.mg_cva2 : P.mg_cvb2), vp = (int)(idx - (unsigned)op * cv);
         const unsigned short po = __ldg((alpha ? P.pair_oa : P.pair_ob) + op);
         const unsigned short pv = __ldg((alpha ? P.pair_va : P.pair_vb) + vp);
         const unsigned char *os = alpha ? L.occA : L.occB;
@@ -295,21 +317,23 @@ __device__ __forceinline__ void decode_element(const Problem &P, const ColLists 
         const unsigned long long X2 = X1 ^ (1ull << j) ^ (1ull << b);
         x.kind = alpha ? 2 : 3;
         x.i = i; x.a = a; x.j = j; x.b = b;
-        x.sgn = m1 ^ m2;                      // popcount parity of m1 ^ m2 = parity(m1) xor parity(m2)
+        x.sgn = m1 ^ m2;
+        x.gidx = -1;                      // popcount parity of m1 ^ m2 = parity(m1) xor parity(m2)
         oa = alpha ? X2 : A;
         ob = alpha ? B : X2;
         return;
     }
     const unsigned idx = (unsigned)(e - P.seg[4]);   // opposite-spin doubles
     const unsigned nsb = (unsigned)(P.nb * P.vb);
-    const unsigned sa = idx / nsb;
+    const unsigned sa = fdiv(idx, P.mg_nsb);
     const unsigned sb = idx - sa * nsb;
-    const int oa_i = (int)(sa / (unsigned)P.va), va_i = (int)(sa - (unsigned)oa_i * (unsigned)P.va);
-    const int ob_i = (int)(sb / (unsigned)P.vb), vb_i = (int)(sb - (unsigned)ob_i * (unsigned)P.vb);
+    const int oa_i = (int)fdiv(sa, P.mg_va), va_i = (int)(sa - (unsigned)oa_i * (unsigned)P.va);
+    const int ob_i = (int)fdiv(sb, P.mg_vb), vb_i = (int)(sb - (unsigned)ob_i * (unsigned)P.vb);
     const int i = L.occA[oa_i], a = L.virA[va_i], j = L.occB[ob_i], b = L.virB[vb_i];
     x.kind = 4;
     x.i = i; x.a = a; x.j = j; x.b = b;
     x.sgn = (A & between_mask(i, a)) ^ (B & between_mask(j, b));
+    x.gidx = -1;
     oa = A ^ (1ull << i) ^ (1ull << a);
     ob = B ^ (1ull << j) ^ (1ull << b);
 }
@@ -350,7 +374,7 @@ __device__ __forceinline__ double element_value(const Problem &P, const ColLists
     } else if (x.kind <= 3) {
         v = gi(g, N, x.i, x.a, x.j, x.b) - gi(g, N, x.i, x.b, x.j, x.a);
     } else {
-        v = gi(g, N, x.i, x.a, x.j, x.b);
+        v = x.gidx >= 0 ? __ldg(g + x.gidx) : gi(g, N, x.i, x.a, x.j, x.b);
     }
     return apply_parity(v, x.sgn);
 }

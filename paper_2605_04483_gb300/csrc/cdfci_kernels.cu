@@ -93,15 +93,74 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// Decode element e and issue the load of its first probe slot (32 bytes).
-__device__ __forceinline__ void issue_elem(const Problem &P, const ColLists &L, unsigned long long iA,
-                                           unsigned long long iB, long long e, long long nh, bool have_prev,
-                                           unsigned long long pA, unsigned long long pB, Elem &x) {
+// One single excitation of the column determinant (per-iteration table): the
+// changed string, its hash, the offset of its orbital pair in g, the sign and
+// the orbitals (info = sign | i << 8 | a << 16).
+struct SingleEnt {
+    unsigned long long key, h;
+    int goff;                          // alpha table: (i N + a) N^2;  beta table: j N + b
+    int info;
+};
+
+__device__ __forceinline__ int j_b_off(int N, int j, int b) { return j * N + b; }
+
+__device__ __forceinline__ void build_singles(const Problem &P, const ColLists &L, unsigned long long iA,
+                                              unsigned long long iB, SingleEnt *tabA, SingleEnt *tabB, int t0, int nt) {
+    const int na_va = P.na * P.va, nb_vb = P.nb * P.vb, N = P.N;
+    for (int s = t0; s < na_va + nb_vb; s += nt) {
+        const bool alpha = s < na_va;
+        const int sl = alpha ? s : s - na_va;
+        const int o = (int)fdiv((unsigned)sl, alpha ? P.mg_va : P.mg_vb);
+        const int w = sl - o * (alpha ? P.va : P.vb);
+        const int i = alpha ? L.occA[o] : L.occB[o];
+        const int a = alpha ? L.virA[w] : L.virB[w];
+        const unsigned long long X = alpha ? iA : iB;
+        SingleEnt e;
+        e.key = X ^ (1ull << i) ^ (1ull << a);
+        e.h = alpha ? hash_alpha(e.key) : hash_beta(e.key);
+        e.goff = alpha ? (i * N + a) * N * N : j_b_off(N, i, a);
+        e.info = (__popcll(X & between_mask(i, a)) & 1) | (i << 8) | (a << 16);
+        (alpha ? tabA : tabB)[sl] = e;
+    }
+}
+
+// Decode element e (singles and opposite-spin doubles from the tables) and
+// issue the load of its first probe slot (32 bytes).
+__device__ __forceinline__ void issue_elem(const Problem &P, const ColLists &L, const SingleEnt *tabA,
+                                           const SingleEnt *tabB, unsigned long long iA, unsigned long long iB,
+                                           unsigned long long hA, unsigned long long hB, long long e, long long nh,
+                                           bool have_prev, unsigned long long pA, unsigned long long pB, Elem &x) {
     x.state = 0;
     if (e >= nh) return;
-    decode_element(P, L, iA, iB, e, x.ka, x.kb, x.ix);
+    unsigned long long h;
+    if (e >= P.seg[4]) {                                   // opposite-spin double from two singles
+        const unsigned idx = (unsigned)(e - P.seg[4]);
+        const unsigned sa = fdiv(idx, P.mg_nsb);
+        const unsigned sb = idx - sa * (unsigned)(P.nb * P.vb);
+        const SingleEnt ea = tabA[sa], eb = tabB[sb];
+        x.ka = ea.key;
+        x.kb = eb.key;
+        h = ea.h ^ eb.h;
+        x.ix.kind = 4;
+        x.ix.sgn = (unsigned long long)((ea.info ^ eb.info) & 1);
+        x.ix.gidx = ea.goff + eb.goff;
+    } else if (e < P.seg[2]) {                             // single
+        const bool alpha = e < P.seg[1];
+        const SingleEnt es = alpha ? tabA[e - P.seg[0]] : tabB[e - P.seg[1]];
+        x.ka = alpha ? es.key : iA;
+        x.kb = alpha ? iB : es.key;
+        h = alpha ? (es.h ^ hB) : (hA ^ es.h);
+        x.ix.kind = alpha ? 0 : 1;
+        x.ix.sgn = (unsigned long long)(es.info & 1);
+        x.ix.i = (es.info >> 8) & 0xff;
+        x.ix.a = (es.info >> 16) & 0xff;
+        x.ix.gidx = -1;
+    } else {                                               // same-spin double
+        decode_element(P, L, iA, iB, e, x.ka, x.kb, x.ix);
+        h = (x.ix.kind == 2) ? (hash_alpha(x.ka) ^ hB) : (hA ^ hash_beta(x.kb));
+    }
     if (have_prev && x.ka == pA && x.kb == pB) { x.state = 3; return; }
-    x.pos = (long long)(key_hash(x.ka, x.kb) & P.mask);
+    x.pos = (long long)(h & P.mask);
     const Slot *s = P.table + x.pos;
     x.k0 = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
     x.cb0 = __ldcg(reinterpret_cast<const double2 *>(&s->c));
@@ -113,7 +172,7 @@ __device__ __forceinline__ void issue_elem(const Problem &P, const ColLists &L, 
 // error, *err set).
 __device__ __forceinline__ void resolve_elem(const Problem &P, IterState *st, Elem &x, int *err) {
     if (x.state != 4) return;
-    if (x.H == 0.0) { x.state = 0; return; }
+    if (is_zero(x.H)) { x.state = 0; return; }
     const bool both_nonzero = (P.na > 0) && (P.nb > 0);
     unsigned long long p = (unsigned long long)x.pos;
     ulonglong2 k = x.k0;
@@ -244,6 +303,8 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
     __shared__ double s_hii;
     __shared__ dd s_mu_n, s_al_n;
     __shared__ int s_err;
+    extern __shared__ SingleEnt s_tab[];         // singles of the column: alpha then beta
+    SingleEnt *tabA = s_tab, *tabB = s_tab + P.na * P.va;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (rec->done) return;                       // uniform: nothing has synchronised yet
@@ -331,6 +392,7 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
         }
         __syncwarp();
         Elem el[kCdMaxE];
+        unsigned long long hAc = 0ull, hBc = 0ull;
         if (warp == 0) {
             // ---- control warp: H_ii and the step size (appendix) ----
             const double Hii = diag_warp(P, L);
@@ -351,9 +413,14 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
 #pragma unroll
             for (int k = 0; k < kCdMaxE; ++k) el[k].state = 0;
         } else {
-            // ---- element warps: decode, issue first probes, values ----
+            // ---- element warps: the column's single-excitation tables, then decode, first probes, values ----
+            build_singles(P, L, iA, iB, tabA, tabB, tid - 32, kCdThreads - 32);
+            asm volatile("bar.sync 1, %0;" ::"r"(kCdThreads - 32) : "memory");
+            hAc = hash_alpha(iA);
+            hBc = hash_beta(iB);
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k) issue_elem(P, L, iA, iB, e0 + k * stride, nh, have_prev, pA, pB, el[k]);
+            for (int k = 0; k < kCdMaxE; ++k)
+                issue_elem(P, L, tabA, tabB, iA, iB, hAc, hBc, e0 + k * stride, nh, have_prev, pA, pB, el[k]);
 #pragma unroll
             for (int k = 0; k < kCdMaxE; ++k)
                 if (el[k].state != 0) el[k].H = element_value(P, L, el[k].ix);
@@ -396,15 +463,15 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
                 if (x.state == 3) {                       // the previous coordinate: c and b known
                     cj = pc;
                     sj = pslot;
-                    if (H == 0.0) { P.table[sj].bv = pb; continue; }
+                    if (is_zero(H)) { P.table[sj].bv = pb; continue; }
                     ++cnt[0];
-                    if (!(cj != 0.0 || big)) { P.table[sj].bv = pb; ++cnt[2]; continue; }
+                    if (!(!is_zero(cj) || big)) { P.table[sj].bv = pb; ++cnt[2]; continue; }
                     bn = pb + v;
                 } else if (x.state == 1) {
                     cj = x.cb0.x;
                     sj = x.pos;
                     ++cnt[0];
-                    if (!(cj != 0.0 || big)) { ++cnt[2]; continue; }
+                    if (!(!is_zero(cj) || big)) { ++cnt[2]; continue; }
                     bn = x.cb0.y + v;
                 } else {                                  // absent
                     ++cnt[0];
@@ -418,7 +485,7 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
                 ++cnt[1];
                 P.table[sj].bv = bn;
                 unsigned long long gb;
-                if (cj != 0.0) {
+                if (!is_zero(cj)) {
                     gather = fma(H, cj, gather);
                     gb = abs_bits(fma(mu, cj, bn));
                 } else {
@@ -433,7 +500,8 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
             eb += kCdMaxE * stride;
             if (eb >= nh) break;
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k) issue_elem(P, L, iA, iB, eb + k * stride, nh, have_prev, pA, pB, el[k]);
+            for (int k = 0; k < kCdMaxE; ++k)
+                issue_elem(P, L, tabA, tabB, iA, iB, hAc, hBc, eb + k * stride, nh, have_prev, pA, pB, el[k]);
 #pragma unroll
             for (int k = 0; k < kCdMaxE; ++k)
                 if (el[k].state != 0) el[k].H = element_value(P, L, el[k].ix);
@@ -757,7 +825,7 @@ cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPar
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster);
     cfg.blockDim = dim3(kCdThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = cd_dynamic_smem(P);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -769,11 +837,16 @@ cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPar
     return cudaLaunchKernelEx(&cfg, k_cd_loop, P, st, rec, part, n_iter);
 }
 
-// Largest cluster size <= want (power of two) that can be resident.
-int cd_pick_cluster(int want) {
+size_t cd_dynamic_smem(const Problem &P) {
+    return (size_t)(P.na * P.va + P.nb * P.vb + 1) * sizeof(SingleEnt);
+}
+
+// Smallest power-of-two cluster size >= want (at most 16) that can be resident.
+int cd_pick_cluster(int want, size_t smem) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         attr_set = true;
     }
     int c = 1;
@@ -782,6 +855,7 @@ int cd_pick_cluster(int want) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
         cfg.blockDim = dim3(kCdThreads);
+        cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = c;

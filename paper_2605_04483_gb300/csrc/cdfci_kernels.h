@@ -8,7 +8,8 @@ namespace cdfci {
 
 cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
                            long long n_iter, cudaStream_t s);
-int cd_pick_cluster(int want);
+size_t cd_dynamic_smem(const Problem &P);
+int cd_pick_cluster(int want, size_t smem);
 cudaError_t launch_cd_finalize(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
                                cudaStream_t s);
 int cd_threads();

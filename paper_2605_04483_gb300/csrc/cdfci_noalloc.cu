@@ -152,6 +152,9 @@ extern "C" __attribute__((visibility("default"))) int cdfci_column_noalloc(
     P.seg[3] = P.seg[2] + (long long)P.ca2 * P.cva2;
     P.seg[4] = P.seg[3] + (long long)P.cb2 * P.cvb2;
     P.seg[5] = P.seg[4] + (long long)P.na * P.va * P.nb * P.vb;
+    P.mg_va = fdiv_magic((unsigned)P.va); P.mg_vb = fdiv_magic((unsigned)P.vb);
+    P.mg_nsb = fdiv_magic((unsigned)(P.nb * P.vb));
+    P.mg_cva2 = fdiv_magic((unsigned)P.cva2); P.mg_cvb2 = fdiv_magic((unsigned)P.cvb2);
     P.nh = P.seg[5];
     P.h = h; P.g = g; P.J = J; P.K = K;
     P.pair_oa = pairs;
