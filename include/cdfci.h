@@ -85,6 +85,7 @@ typedef struct {
     double  load;              /* n_slots / capacity */
     int32_t status;            /* sticky device status (0 or a CDFCI_ERR_* code) */
     int32_t converged;         /* 1 once dx < dx_threshold */
+    int64_t reduced_iterations;/* m > 1: cumulative iterations of the reduced eigensolver (0 for m = 1) */
 } cdfci_stats;
 
 /* Fills *p with the defaults (m = 1, 2^22 slots, tau = 0, max_load = 0.79,

@@ -87,6 +87,13 @@ struct cdfci_ctx {
     IterState *h_st = nullptr;                   // pinned copy of the state
     int grid = 1;                                // CTAs of the cluster
     long long chunk = 1 << 16;                   // iterations per launch
+    // multicoordinate (m > 1) iteration
+    bool block = false;
+    McBuffers mb;
+    void *mb_alloc[20] = {};
+    int mb_nalloc = 0;
+    int mchunk = 8;                              // iterations per captured graph
+    cudaGraphExec_t mgraph = nullptr;
 };
 
 namespace {
@@ -94,6 +101,8 @@ namespace {
 void free_ctx(cdfci_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
+    for (int i = 0; i < c->mb_nalloc; ++i) cudaFree(c->mb_alloc[i]);
     cudaFree(c->d_h); cudaFree(c->d_g); cudaFree(c->d_J); cudaFree(c->d_K);
     cudaFree(c->d_pairs); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part); cudaFree(c->d_rec);
     cudaFree(c->d_flags); cudaFree(c->d_counter); cudaFree(c->d_colkeys); cudaFree(c->d_colvals);
@@ -112,7 +121,7 @@ int run_iterations(cdfci_ctx *c, long long n) {
 }
 
 int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
-    CK(launch_cd_finalize(c->P, c->d_st, c->d_rec, c->d_part, c->grid, c->stream));
+    if (!c->block) CK(launch_cd_finalize(c->P, c->d_st, c->d_rec, c->d_part, c->grid, c->stream));
     CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     const IterState &t = *c->h_st;
@@ -132,6 +141,7 @@ int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
         s->load = (double)t.n_slots / (double)c->P.capacity;
         s->status = t.status;
         s->converged = t.done;
+        s->reduced_iterations = t.eig_iters;
     }
     if (t.status != 0) {
         const char *what = t.status == CDFCI_ERR_TABLE_FULL ? "hash table full (raise log2_capacity or z_threshold)"
@@ -140,6 +150,58 @@ int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
                                                              : "device error";
         return fail(t.status, "%s", what);
     }
+    return CDFCI_OK;
+}
+
+template <typename T>
+int mb_alloc(cdfci_ctx *c, T **p, size_t count) {
+    if (cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return -1;
+    c->mb_alloc[c->mb_nalloc++] = (void *)*p;
+    return cudaMemsetAsync(*p, 0, std::max<size_t>(count, 1) * sizeof(T), c->stream) == cudaSuccess ? 0 : -1;
+}
+
+int setup_block(cdfci_ctx *c, int m) {
+    McBuffers &b = c->mb;
+    const Problem &P = c->P;
+    const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
+    b.m = m;
+    b.tpc = nh_eff >= 4096 ? 256 : (nh_eff >= 512 ? 128 : 32);
+    b.chunk = b.tpc * 16;
+    b.nchunk = (int)std::max<long long>(1, (nh_eff - 1 + b.chunk - 1) / b.chunk);
+    const long long cap_cand = (long long)m * nh_eff + m + 64;
+    b.cand_grid = 152 * 4;
+    const long long items = (long long)m * b.nchunk, gpb = 256 / b.tpc;
+    b.scatter_grid = (int)std::max<long long>(1, std::min<long long>((items + gpb - 1) / gpb, 152 * 16));
+    b.st = c->d_st;
+    const size_t n1 = (size_t)m + 1;
+    b.ldr = (int)(32 * ((n1 + 31) / 32));
+    if (mb_alloc(c, &b.ms, 1) || mb_alloc(c, &b.cand, (size_t)cap_cand) || mb_alloc(c, &b.gkey, (size_t)cap_cand) ||
+        mb_alloc(c, &b.hist, 4096 + 1) || mb_alloc(c, &b.sel, (size_t)m) || mb_alloc(c, &b.inbin, 4096) ||
+        mb_alloc(c, &b.cI, (size_t)m) || mb_alloc(c, &b.bI, (size_t)m) || mb_alloc(c, &b.Hdiag, (size_t)m) ||
+        mb_alloc(c, &b.HIIc, (size_t)m) || mb_alloc(c, &b.Rh, n1 * (size_t)b.ldr) ||
+        mb_alloc(c, &b.Rl, n1 * (size_t)b.ldr) ||
+        mb_alloc(c, &b.w, (size_t)m) || mb_alloc(c, &b.thr, (size_t)m) || mb_alloc(c, &b.eta, (size_t)m) ||
+        mb_alloc(c, &b.gathp, (size_t)m * b.nchunk))
+        return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
+    CK(mc_configure());
+    return CDFCI_OK;
+}
+
+int build_block_graph(cdfci_ctx *c) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < c->mchunk && e == cudaSuccess; ++i) e = launch_mc_iteration(c->P, c->mb, c->stream);
+    cudaGraph_t got = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &got);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (got) cudaGraphDestroy(got);
+        return fail(CDFCI_ERR_CUDA, "capture of the multicoordinate iteration failed");
+    }
+    g = got;
+    e = cudaGraphInstantiate(&c->mgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     return CDFCI_OK;
 }
 
@@ -172,8 +234,8 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         return fail(CDFCI_ERR_ARG, "electron counts (%d, %d) invalid for N = %d", n_alpha, n_beta, N);
     cdfci_params prm;
     if (params) prm = *params; else cdfci_default_params(&prm);
-    if (prm.num_coordinates != 1)
-        return fail(CDFCI_ERR_UNIMPLEMENTED, "num_coordinates = %d: only m = 1 is available", prm.num_coordinates);
+    if (prm.num_coordinates < 1 || prm.num_coordinates > mc_max_m())
+        return fail(CDFCI_ERR_ARG, "num_coordinates = %d outside [1, %d]", prm.num_coordinates, mc_max_m());
     if (prm.log2_capacity < 4 || prm.log2_capacity > 34)
         return fail(CDFCI_ERR_ARG, "log2_capacity = %d outside [4, 34]", prm.log2_capacity);
     if (!(prm.max_load > 0.0 && prm.max_load <= 0.95)) return fail(CDFCI_ERR_ARG, "max_load must be in (0, 0.95]");
@@ -309,6 +371,22 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         for (int k = 0; k < n_alpha; ++k) refA |= 1ull << order[k];
         for (int k = 0; k < n_beta; ++k) refB |= 1ull << order[k];
     }
+    if (prm.num_coordinates > 1) {
+        c->block = true;
+        rc = setup_block(c, prm.num_coordinates);
+        if (rc != CDFCI_OK) return bail(rc);
+        if (prm.graph_chunk > 0) c->mchunk = prm.graph_chunk;
+        // start vector c = e_ref, b = H e_ref (compression applied): first column with eta = 1
+        if (launch_mc_init(P, c->mb, refA, refB, s) != cudaSuccess ||
+            launch_mc_scatter_finalize(P, c->mb, s) != cudaSuccess)
+            return bail(fail(CDFCI_ERR_CUDA, "initial column launch failed"));
+        rc = fill_stats(c, nullptr);
+        if (rc != CDFCI_OK) return bail(rc);
+        rc = build_block_graph(c);
+        if (rc != CDFCI_OK) return bail(rc);
+        *out = c;
+        return CDFCI_OK;
+    }
     if (launch_init_state(P, c->d_st, c->d_rec, refA, refB, s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "init launch failed"));
     // initialisation iteration: c = e_ref, b = H e_ref (compression applied)
@@ -323,6 +401,11 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
 CDFCI_API int cdfci_step(cdfci_handle c, int64_t n_iter, cdfci_stats *stats) {
     if (!c) return fail(CDFCI_ERR_ARG, "handle is NULL");
     if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
+    if (c->block) {
+        for (int64_t i = 0; i < n_iter / c->mchunk; ++i) CK(cudaGraphLaunch(c->mgraph, c->stream));
+        for (int64_t i = 0; i < n_iter % c->mchunk; ++i) CK(launch_mc_iteration(c->P, c->mb, c->stream));
+        return fill_stats(c, stats);
+    }
     int rc = run_iterations(c, n_iter);
     if (rc) return rc;
     return fill_stats(c, stats);
@@ -422,6 +505,24 @@ CDFCI_API int cdfci_last_step(cdfci_handle c, uint64_t *keys, double *eta, int64
     if (!c || !m_out) return fail(CDFCI_ERR_ARG, "NULL argument");
     int rc = fill_stats(c, nullptr);
     if (rc) return rc;
+    if (c->block) {
+        McState ms;
+        CK(cudaMemcpy(&ms, c->mb.ms, sizeof(ms), cudaMemcpyDeviceToHost));
+        const int m = ms.m_sel;
+        *m_out = m;
+        if (cap < m) return fail(CDFCI_ERR_CAPACITY, "%d coordinates, cap is %lld", m, (long long)cap);
+        std::vector<McSel> sel(m > 0 ? m : 1);
+        std::vector<double> et(m > 0 ? m : 1);
+        if (m > 0) {
+            CK(cudaMemcpy(sel.data(), c->mb.sel, m * sizeof(McSel), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(et.data(), c->mb.eta, m * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        std::vector<uint64_t> kk(2 * (m > 0 ? m : 1));
+        for (int i = 0; i < m; ++i) { kk[2 * i] = sel[i].A; kk[2 * i + 1] = sel[i].B; }
+        if (keys && m > 0) CK(cudaMemcpy(keys, kk.data(), 2 * m * sizeof(uint64_t), cudaMemcpyDefault));
+        if (eta && m > 0) CK(cudaMemcpy(eta, et.data(), m * sizeof(double), cudaMemcpyDefault));
+        return CDFCI_OK;
+    }
     *m_out = 1;
     if (cap < 1) return fail(CDFCI_ERR_CAPACITY, "cap < 1");
     uint64_t k[2] = {c->h_st->last_a, c->h_st->last_b};

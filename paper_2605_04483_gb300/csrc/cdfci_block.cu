@@ -1,0 +1,1115 @@
+// mCDFCI (Algorithm 2): m coordinates per iteration.
+//
+// One iteration is a fixed sequence of kernels (captured once in a CUDA graph):
+//   k_mc_gkeys     |g_j| ~ |b_j + mu c_j| of every candidate (the union of the
+//                  last columns, deduplicated by a mark bit), clearing the marks;
+//   k_mc_hist/scan radix selection of the m largest |g| on the 64-bit pattern,
+//                  16 bits per pass;
+//   k_mc_collect   the candidates above the threshold digit prefix, and the ones
+//                  on it (sorted by (|g| desc, key asc) in k_mc_sortsel);
+//   k_mc_prepare   c_I, b_I, H_II (Slater-Condon between the selected
+//                  determinants) and H_II c_I;
+//   k_mc_eigen     the reduced (m+1)-dimensional problem R = Q^T H Q with
+//                  Q = [c~ / nu, E_I]; its lowest eigenpair (LOBPCG with a
+//                  float-float residual, one thread per row) gives
+//                  z = [nu gamma; c_I gamma + eta]; the scalars mu, alpha
+//                  (double-double) and the global scale;
+//   k_mc_scatter   b_j += H_ji eta_i for the m columns (compression, atomics,
+//                  16-byte CAS inserts), the gather sum_j H_ji c_j per column,
+//                  new candidates;
+//   k_mc_finalize  the recalculated b_I, counters, snapshot.
+// Stored values are c_j / s and b_j / s for a global scale s, so that
+// c <- gamma c costs O(1): s <- gamma s.
+#include <cuda_runtime.h>
+
+#include "cdfci_internal.cuh"
+#include "cdfci_kernels.h"
+
+namespace cdfci {
+
+namespace {
+
+constexpr int kInBin = 4096;          // candidates sorted in one CTA on the threshold digit
+
+__device__ __forceinline__ bool mc_better(unsigned long long g1, unsigned long long a1, unsigned long long b1,
+                                          unsigned long long g2, unsigned long long a2, unsigned long long b2) {
+    return g1 > g2 || (g1 == g2 && key_less(a1, b1, a2, b2));
+}
+
+// <D1|H|D2> for two determinants differing by at most a double excitation
+// (Eq. entry; same sign convention as the column enumeration: D1 is reached
+// from D2 by i->a then j->b with i < j occupied, a < b empty).  Diagonal: 0
+// (computed separately).
+__device__ double hij_pair(const Problem &P, unsigned long long A1, unsigned long long B1, unsigned long long A2,
+                           unsigned long long B2) {
+    const unsigned long long dA = A1 ^ A2, dB = B1 ^ B2;
+    const int la = __popcll(dA), lb = __popcll(dB);
+    if (la + lb == 0 || la + lb > 4) return 0.0;
+    const int N = P.N;
+    const double *g = P.g;
+    if (la + lb == 2) {                                  // single
+        const bool alpha = la == 2;
+        const unsigned long long X2 = alpha ? A2 : B2, X1 = alpha ? A1 : B1, Y2 = alpha ? B2 : A2;
+        const int i = __ffsll((long long)(X2 & (alpha ? dA : dB))) - 1;
+        const int a = __ffsll((long long)(X1 & (alpha ? dA : dB))) - 1;
+        double v = __ldg(P.h + i * N + a);
+        for (unsigned long long m = X2; m; m &= m - 1) {
+            const int k = __ffsll((long long)m) - 1;
+            v += gi(g, N, i, a, k, k) - gi(g, N, i, k, k, a);
+        }
+        for (unsigned long long m = Y2; m; m &= m - 1) {
+            const int k = __ffsll((long long)m) - 1;
+            v += gi(g, N, i, a, k, k);
+        }
+        return apply_parity(v, X2 & between_mask(i, a));
+    }
+    if (la == 4 || lb == 4) {                            // same-spin double
+        const bool alpha = la == 4;
+        const unsigned long long X2 = alpha ? A2 : B2, X1 = alpha ? A1 : B1, d = alpha ? dA : dB;
+        unsigned long long occ = X2 & d, vir = X1 & d;
+        const int i = __ffsll((long long)occ) - 1;
+        occ &= occ - 1;
+        const int j = __ffsll((long long)occ) - 1;
+        const int a = __ffsll((long long)vir) - 1;
+        vir &= vir - 1;
+        const int b = __ffsll((long long)vir) - 1;
+        const unsigned long long m1 = X2 & between_mask(i, a);
+        const unsigned long long Xm = X2 ^ (1ull << i) ^ (1ull << a);
+        const unsigned long long m2 = Xm & between_mask(j, b);
+        return apply_parity(gi(g, N, i, a, j, b) - gi(g, N, i, b, j, a), m1 ^ m2);
+    }
+    // opposite-spin double
+    const int i = __ffsll((long long)(A2 & dA)) - 1, a = __ffsll((long long)(A1 & dA)) - 1;
+    const int j = __ffsll((long long)(B2 & dB)) - 1, b = __ffsll((long long)(B1 & dB)) - 1;
+    return apply_parity(gi(g, N, i, a, j, b), (A2 & between_mask(i, a)) ^ (B2 & between_mask(j, b)));
+}
+
+// ---------------------------------------------------------------------------
+// Float-float numbers on the FP32 pipe (this part runs FP64 at a small
+// fraction of its FP32 rate).  A value is hi + lo with |lo| <= ulp(hi) / 2,
+// about 48 significant bits.  TwoSum (Knuth) and the FMA form of TwoProduct
+// are error-free transformations; the _rn intrinsics keep the compiler from
+// contracting or reassociating them.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// |hi| >= |lo| (or hi = 0)
+__device__ __forceinline__ ff ff_norm(float hi, float lo) {
+    const float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    return ff_norm(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const ff r = ff_add(a, ff_neg(ff_mul_f(b, q1)));
+    return ff_norm(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ ff ff_from_double(double v) {
+    const float hi = __double2float_rn(v);
+    return {hi, __double2float_rn(v - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ float ff_to_float(ff a) { return __fadd_rn(a.hi, a.lo); }
+// (sh, sl) += (ah + al) * x, an unnormalised float-float accumulator
+__device__ __forceinline__ void ff_mac(float &sh, float &sl, float ah, float al, ff x) {
+    const float p = __fmul_rn(ah, x.hi);
+    float e = __fmaf_rn(ah, x.hi, -p);
+    e = __fmaf_rn(ah, x.lo, e);
+    e = __fmaf_rn(al, x.hi, e);
+    const ff s = ff_two_sum(sh, p);
+    sh = s.hi;
+    sl = __fadd_rn(sl, __fadd_rn(s.lo, e));
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions with one barrier each.  Every warp reduces in a fixed tree,
+// lane 0 stores the warp's value, and after the barrier every thread adds the
+// warps' values in warp order, so all threads hold bit-identical results.  Two
+// scratch halves alternate: a half is rewritten only after the barrier of the
+// following reduction, which every reader of it has passed.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void bsum_f(float (&v)[K], float *scr, int &half) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int off = 16; off > 0; off >>= 1) v[k] = __fadd_rn(v[k], __shfl_down_sync(0xffffffffu, v[k], off));
+    float *s = scr + half * 32 * 8;                      // fixed stride: K <= 8
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[warp * K + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float t = s[k];
+        for (int w = 1; w < nw; ++w) t = __fadd_rn(t, s[w * K + k]);
+        v[k] = t;
+    }
+    half ^= 1;
+}
+
+template <int K>
+__device__ __forceinline__ void bsum_ff(ff (&v)[K], ff *scr, int &half) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int off = 16; off > 0; off >>= 1) {
+            const ff o = {__shfl_down_sync(0xffffffffu, v[k].hi, off), __shfl_down_sync(0xffffffffu, v[k].lo, off)};
+            v[k] = ff_add(v[k], o);
+        }
+    ff *s = scr + half * 32 * 2;                         // fixed stride: K <= 2
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[warp * K + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        ff t = s[k];
+        for (int w = 1; w < nw; ++w) t = ff_add(t, s[w * K + k]);
+        v[k] = t;
+    }
+    half ^= 1;
+}
+
+// FP64 warp sum, result in every lane (fixed tree, broadcast from lane 0)
+__device__ __forceinline__ double wsum_d(double v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// Lowest eigenpair of the symmetric 3 x 3 matrix [a00 a01 a02; . a11 a12; . . a22]
+// in FP32: the trigonometric form of the three real roots of the characteristic
+// cubic, and the eigenvector as the longest cross product of two rows of
+// (A - lambda I).  v is returned with unit length.
+__device__ __forceinline__ void sym3_lowest(float a00, float a01, float a02, float a11, float a12, float a22,
+                                            float &lam, float &v0, float &v1, float &v2) {
+    const float sc = fmaxf(fmaxf(fmaxf(fabsf(a00), fabsf(a01)), fmaxf(fabsf(a02), fabsf(a11))),
+                           fmaxf(fabsf(a12), fabsf(a22)));
+    if (!(sc > 0.0f)) {
+        lam = 0.0f; v0 = 1.0f; v1 = 0.0f; v2 = 0.0f;
+        return;
+    }
+    const float is = 1.0f / sc;
+    a00 *= is; a01 *= is; a02 *= is; a11 *= is; a12 *= is; a22 *= is;
+    const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+    const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * (a01 * a01 + a02 * a02 + a12 * a12);
+    float l = q;
+    if (p2 > 0.0f) {
+        const float p = sqrtf(p2 * (1.0f / 6.0f));
+        const float ip = 1.0f / p;
+        const float c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+        float r = 0.5f * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
+        r = fminf(1.0f, fmaxf(-1.0f, r));
+        l = q + 2.0f * p * cosf(acosf(r) * (1.0f / 3.0f) + 2.0943951023931953f);
+    }
+    const float m00 = a00 - l, m11 = a11 - l, m22 = a22 - l;
+    float x0 = a01 * a12 - a02 * m11, x1 = a02 * a01 - m00 * a12, x2 = m00 * m11 - a01 * a01;   // r0 x r1
+    float y0 = a01 * m22 - a02 * a12, y1 = a02 * a02 - m00 * m22, y2 = m00 * a12 - a01 * a02;   // r0 x r2
+    float z0 = m11 * m22 - a12 * a12, z1 = a12 * a02 - a01 * m22, z2 = a01 * a12 - m11 * a02;   // r1 x r2
+    const float nx = x0 * x0 + x1 * x1 + x2 * x2, ny = y0 * y0 + y1 * y1 + y2 * y2, nz = z0 * z0 + z1 * z1 + z2 * z2;
+    float n2 = nz;
+    v0 = z0; v1 = z1; v2 = z2;
+    if (ny > n2) { v0 = y0; v1 = y1; v2 = y2; n2 = ny; }
+    if (nx > n2) { v0 = x0; v1 = x1; v2 = x2; n2 = nx; }
+    if (!(n2 > 0.0f)) {              // a multiple of the identity
+        v0 = 1.0f; v1 = 0.0f; v2 = 0.0f;
+    } else {
+        const float in = rsqrtf(n2);
+        v0 *= in; v1 *= in; v2 *= in;
+    }
+    lam = l * sc;
+}
+
+// Lowest eigenpair of [a00 a01; a01 a11] (FP32), v of unit length.
+__device__ __forceinline__ void sym2_lowest(float a00, float a01, float a11, float &lam, float &v0, float &v1) {
+    const float h = 0.5f * (a00 - a11);
+    const float rad = sqrtf(h * h + a01 * a01);
+    lam = 0.5f * (a00 + a11) - rad;
+    // (a00 - lam, a01) and (a01, a11 - lam) are rows of A - lam I; take the longer normal
+    const float u0 = a01, u1 = lam - a00;             // normal of row 0
+    const float w0 = a11 - lam, w1 = -a01;            // normal of row 1
+    const float nu = u0 * u0 + u1 * u1, nw = w0 * w0 + w1 * w1;
+    if (nu >= nw && nu > 0.0f) { const float in = rsqrtf(nu); v0 = u0 * in; v1 = u1 * in; }
+    else if (nw > 0.0f) { const float in = rsqrtf(nw); v0 = w0 * in; v1 = w1 * in; }
+    else { v0 = 1.0f; v1 = 0.0f; }
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Candidates and selection (Alg. 2, choice of I): the m largest choice keys
+// |b_j + mu c_j| (the bit pattern of a non-negative double orders like the
+// value), ties to the smaller key.  Radix selection from the top, 12 bits per
+// level (12 x 5 + 4 = 64 bits): a block counts its keys in a shared-memory
+// histogram and adds it to the global one; the last block to finish (a device
+// counter, after a fence) finds the digit holding the key of rank sel_need,
+// narrows the prefix and clears the histogram.  Most selections resolve after
+// one or two levels; later levels return at once.
+// ---------------------------------------------------------------------------
+constexpr int kSelBins = 4096;
+constexpr int kSelLevels = 6;
+
+__device__ __forceinline__ int sel_bits(int level) { return level < 5 ? 12 : 4; }
+__device__ __forceinline__ int sel_cover(int levels) { return levels < 6 ? 12 * levels : 64; }   // bits fixed
+// the top `levels` digits of k
+__device__ __forceinline__ unsigned long long sel_top(unsigned long long k, int levels) {
+    const int c = sel_cover(levels);
+    return c == 0 ? 0ull : (c == 64 ? k : (k >> (64 - c)));
+}
+__device__ __forceinline__ unsigned int sel_digit(unsigned long long k, int level) {
+    const int lo = 64 - sel_cover(level + 1);
+    return (unsigned int)((k >> lo) & ((1ull << sel_bits(level)) - 1ull));
+}
+
+// Count the keys of this block's share into sh (block-local), then add the
+// nonzero bins to hist; true in the block that finishes last.
+__device__ bool sel_count(const unsigned long long *gkey, int n, int level, unsigned long long prefix,
+                          unsigned int *sh, unsigned int *hist, unsigned int *counter) {
+    __shared__ int s_any;
+    __shared__ bool s_last;
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    int any = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const unsigned long long k = gkey[t];
+        if (level > 0 && sel_top(k, level) != prefix) continue;
+        atomicAdd(&sh[sel_digit(k, level)], 1u);
+        any = 1;
+    }
+    if (any) s_any = 1;
+    __syncthreads();
+    if (s_any)
+        for (int d = threadIdx.x; d < kSelBins; d += blockDim.x)
+            if (sh[d]) atomicAdd(&hist[d], sh[d]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
+// In the last block: the digit of the key of rank need (1 = largest) among the
+// counted ones; record it, clear the histogram and the counter.
+__device__ void sel_scan(McState *ms, unsigned int *hist, unsigned int *counter, int level, int need) {
+    __shared__ unsigned int s_warp[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int per = kSelBins / blockDim.x;             // consecutive bins per thread, from the top
+    const int top = kSelBins - 1 - tid * per;
+    unsigned int loc = 0;
+    for (int q = 0; q < per; ++q) loc += __ldcg(&hist[top - q]);
+    // exclusive prefix of loc over threads (thread 0 owns the largest digits)
+    unsigned int inc = loc;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += v;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    unsigned int base = 0;
+    for (int w = 0; w < warp; ++w) base += s_warp[w];
+    const unsigned int before = base + inc - loc;
+    if (before < (unsigned int)need && (unsigned int)need <= before + loc) {
+        unsigned int acc = before;
+        for (int q = 0; q < per; ++q) {
+            const unsigned int c = __ldcg(&hist[top - q]);
+            if (acc + c >= (unsigned int)need) {
+                ms->sel_prefix = (ms->sel_prefix << sel_bits(level)) | (unsigned long long)(top - q);
+                ms->sel_need = need - (int)acc;
+                ms->sel_level = level + 1;
+                ms->sel_nbin = (int)c;
+                ms->sel_resolved = (c <= (unsigned int)kInBin || level == kSelLevels - 1) ? 1 : 0;
+                break;
+            }
+            acc += c;
+        }
+    }
+    (void)nw;
+    __syncthreads();
+    for (int q = 0; q < per; ++q) hist[top - q] = 0u;
+    if (tid == 0) *counter = 0u;
+}
+
+// choice keys of the candidates, clearing their marks; level-0 histogram
+__global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, const long long *cand,
+                                                  unsigned long long *gkey, unsigned int *hist, int m) {
+    __shared__ unsigned int sh[kSelBins];
+    if (ms->done) return;
+    const int n = ms->n_cand;
+    const double mu = ms->mu.hi;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        Slot *s = P.table + cand[t];
+        const double c = s->c, b = s->bv;
+        gkey[t] = (unsigned long long)__double_as_longlong(fma(mu, c, b)) & 0x7fffffffffffffffull;
+        s->b = s->b & kKeyMaskB;                       // clear the candidate mark
+    }
+    if (n <= m) {                                      // every candidate is chosen
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ms->sel_prefix = 0ull;
+            ms->sel_need = 0;
+            ms->sel_level = 0;
+            ms->sel_nbin = 0;
+            ms->sel_resolved = 1;
+        }
+        return;
+    }
+    __syncthreads();                                   // this block's keys are written
+    if (sel_count(gkey, n, 0, 0ull, sh, hist, hist + kSelBins)) {
+        if (threadIdx.x == 0) ms->sel_prefix = 0ull;
+        __syncthreads();
+        sel_scan(ms, hist, hist + kSelBins, 0, m);
+    }
+}
+
+// level >= 1: the keys on the current prefix
+__global__ void __launch_bounds__(256) k_mc_hist(McState *ms, const unsigned long long *gkey, unsigned int *hist,
+                                                 int level) {
+    __shared__ unsigned int sh[kSelBins];
+    if (ms->done || ms->sel_resolved) return;
+    if (sel_count(gkey, ms->n_cand, level, ms->sel_prefix, sh, hist, hist + kSelBins))
+        sel_scan(ms, hist, hist + kSelBins, level, ms->sel_need);
+}
+
+__global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, const unsigned long long *gkey,
+                             McSel *sel, McSel *inbin) {
+    if (ms->done) return;
+    const int n = ms->n_cand;
+    const bool all = ms->sel_level == 0;                 // n_cand <= m: every candidate is selected
+    const int L = ms->sel_level;
+    const unsigned long long prefix = ms->sel_prefix;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const unsigned long long k = gkey[t];
+        const unsigned long long top = sel_top(k, L);
+        McSel x;
+        x.slot = cand[t];
+        x.gkey = k;
+        if (all || top > prefix) {
+            const int pos = atomicAdd(&ms->n_above, 1);
+            const Slot s = P.table[x.slot];
+            x.A = s.a;
+            x.B = s.b & kKeyMaskB;
+            sel[pos] = x;
+        } else if (top == prefix) {
+            const int pos = atomicAdd(&ms->n_inbin, 1);
+            if (pos < kInBin) {
+                const Slot s = P.table[x.slot];
+                x.A = s.a;
+                x.B = s.b & kKeyMaskB;
+                inbin[pos] = x;
+            }
+        }
+    }
+}
+
+// bitonic sort of up to 4096 entries in shared memory by (gkey desc, key asc)
+__device__ void bitonic_sort(McSel *a, int n_pow2) {
+    for (int k = 2; k <= n_pow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n_pow2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const McSel x = a[i], y = a[l];
+                    const bool y_first = mc_better(y.gkey, y.A, y.B, x.gkey, x.A, x.B);
+                    if (up ? y_first : !y_first) { a[i] = y; a[l] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, const McSel *inbin, int m,
+                                                      IterState *st) {
+    extern __shared__ McSel sh[];
+    const int tid = threadIdx.x;
+    if (ms->done) return;
+    const int n_above = ms->n_above;
+    int n_in = ms->n_inbin;
+    if (ms->sel_level > 0 && n_in > kInBin) {
+        if (tid == 0) set_status(st, kErrArg);            // more than 4096 exactly equal |g| values
+        n_in = kInBin;
+    }
+    const int need = ms->sel_level == 0 ? 0 : ms->sel_need;
+    // sort the threshold-digit candidates, keep the first `need`
+    int p2 = 1;
+    while (p2 < n_in) p2 <<= 1;
+    for (int i = tid; i < p2; i += blockDim.x) {
+        if (i < n_in) sh[i] = inbin[i];
+        else { McSel z; z.slot = -1; z.gkey = 0ull; z.A = ~0ull; z.B = ~0ull; sh[i] = z; }
+    }
+    __syncthreads();
+    if (n_in > 1) bitonic_sort(sh, p2);
+    __syncthreads();
+    const int take = need < n_in ? need : n_in;
+    for (int i = tid; i < take; i += blockDim.x) sel[n_above + i] = sh[i];
+    __syncthreads();
+    // canonical order of the selected set
+    const int msel = n_above + take;
+    int q2 = 1;
+    while (q2 < msel) q2 <<= 1;
+    for (int i = tid; i < q2; i += blockDim.x) {
+        if (i < msel) sh[i] = sel[i];
+        else { McSel z; z.slot = -1; z.gkey = 0ull; z.A = ~0ull; z.B = ~0ull; sh[i] = z; }
+    }
+    __syncthreads();
+    if (msel > 1) bitonic_sort(sh, q2);
+    __syncthreads();
+    for (int i = tid; i < msel; i += blockDim.x) sel[i] = sh[i];
+    if (tid == 0) {
+        ms->m_sel = msel;
+        ms->n_above = 0;
+        ms->n_inbin = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// c_I, b_I, H_II, H_II c_I: one warp per selected row.  H_II goes to rows and
+// columns 1..m of R as float-float pairs (Rh, Rl; leading dimension ldr).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, const McSel *sel, double *cI,
+                                                    double *bI, double *Hdiag, double *HIIc, float *Rh, float *Rl,
+                                                    int ldr) {
+    __shared__ ColLists Lw[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (ms->done) return;
+    const int m = ms->m_sel;
+    const double s = ms->scale.hi;
+    for (int r = blockIdx.x * 8 + warp; r < m; r += gridDim.x * 8) {
+        const McSel xr = sel[r];
+        ColLists &L = Lw[warp];
+        for (int t = lane; t < P.N; t += 32) {
+            int ra = __popcll(xr.A & low_mask(t)), rb = __popcll(xr.B & low_mask(t));
+            if ((xr.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+            if ((xr.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+        }
+        __syncwarp();
+        const double hd = diag_warp(P, L);
+        double acc = 0.0;
+        for (int c = lane; c < m; c += 32) {
+            const McSel xc = sel[c];
+            const double h = (c == r) ? hd : hij_pair(P, xr.A, xr.B, xc.A, xc.B);
+            const ff hf = ff_from_double(h);
+            Rh[(size_t)(r + 1) * ldr + (c + 1)] = hf.hi;
+            Rl[(size_t)(r + 1) * ldr + (c + 1)] = hf.lo;
+            const double cc = P.table[xc.slot].c * s;
+            acc = fma(h, cc, acc);
+        }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+            const Slot sl = P.table[xr.slot];
+            cI[r] = sl.c * s;
+            bI[r] = sl.bv * s;
+            Hdiag[r] = hd;
+            HIIc[r] = acc;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The reduced problem: the lowest eigenpair of the active block A of
+// R = Q^T H Q, Q = [c~ / nu, E_I] (rows/columns 1.. only when c lies in
+// span(E_I)), on one CTA with one thread per row.
+//
+// LOBPCG (Knyazev's locally optimal block preconditioned conjugate gradient)
+// for one vector, with the diagonal (Davidson) preconditioner, started from
+// the current point [nu; c_I].  x and A x are float-float; the search vectors
+// w, p and their images are FP32.  The Rayleigh-Ritz step on span{x, w, p}
+// uses the float-float residual r = A x - theta x for the x-couplings
+// (x^T A w = r^T w once w is orthogonal to x), so the iteration converges to
+// the accuracy of the float-float residual, about 1e-14 relative, with all
+// vector arithmetic on the FP32 pipe.
+// ---------------------------------------------------------------------------
+constexpr int kEigSmemN = 160;      // A in shared memory (hi and lo) up to this size
+constexpr int kEigMaxN = 1024;      // m + 1 <= 1024: one thread per row
+constexpr int kEigMaxIt = 200;
+
+// row i of A times the float-float vector xs (interleaved hi, lo)
+__device__ __forceinline__ ff ff_row(const float *Ah, const float *Al, int lda, int n, int i, const float *xs) {
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+    int j = 0;
+    for (; j + 1 < n; j += 2) {
+        ff_mac(h0, l0, Ah[(size_t)j * lda + i], Al[(size_t)j * lda + i], ff{xs[2 * j], xs[2 * j + 1]});
+        ff_mac(h1, l1, Ah[(size_t)(j + 1) * lda + i], Al[(size_t)(j + 1) * lda + i], ff{xs[2 * j + 2], xs[2 * j + 3]});
+    }
+    if (j < n) ff_mac(h0, l0, Ah[(size_t)j * lda + i], Al[(size_t)j * lda + i], ff{xs[2 * j], xs[2 * j + 1]});
+    return ff_add(ff_norm(h0, l0), ff_norm(h1, l1));
+}
+// row i of A (hi part) times the FP32 vector ws
+__device__ __forceinline__ float f_row(const float *Ah, int lda, int n, int i, const float *ws) {
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    int j = 0;
+    for (; j + 3 < n; j += 4) {
+        a0 = fmaf(Ah[(size_t)j * lda + i], ws[j], a0);
+        a1 = fmaf(Ah[(size_t)(j + 1) * lda + i], ws[j + 1], a1);
+        a2 = fmaf(Ah[(size_t)(j + 2) * lda + i], ws[j + 2], a2);
+        a3 = fmaf(Ah[(size_t)(j + 3) * lda + i], ws[j + 3], a3);
+    }
+    for (; j < n; ++j) a0 = fmaf(Ah[(size_t)j * lda + i], ws[j], a0);
+    return (a0 + a1) + (a2 + a3);
+}
+
+__global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, IterState *st, const McSel *sel,
+                                                       const double *cI, const double *bI, const double *HIIc,
+                                                       float *Rh, float *Rl, int ldr, int use_smem, double *w,
+                                                       double *thr, double *etaout) {
+    extern __shared__ float sm[];
+    __shared__ float s_rf[2 * 32 * 8];
+    __shared__ ff s_rff[2 * 32 * 2];
+    __shared__ double s_sc[4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (ms->done || st->status) return;
+    const int m = ms->m_sel;
+    int hf = 0, hff = 0;
+
+    // 1. scalars over I (warp 0, FP64): nonzeros, c.c, c.b, c.H_II c; the
+    //    degenerate case (c has no support outside I); nu = |c - E_I c_I|; R_00
+    if (warp == 0) {
+        int nz = 0;
+        double cc = 0.0, cb = 0.0, chc = 0.0;
+        for (int i = lane; i < m; i += 32) {
+            const double c = cI[i];
+            nz += (c != 0.0) ? 1 : 0;
+            cc = fma(c, c, cc);
+            cb = fma(c, bI[i], cb);
+            chc = fma(c, HIIc[i], chc);
+        }
+        nz = __reduce_add_sync(0xffffffffu, nz);
+        cc = wsum_d(cc);
+        cb = wsum_d(cb);
+        chc = wsum_d(chc);
+        if (lane == 0) {
+            const dd nu2 = dd_add(ms->mu, dd{-cc, 0.0});
+            const bool deg = (nz >= ms->nnz_c) || !(nu2.hi > 0.0);
+            s_sc[0] = deg ? 1.0 : 0.0;
+            s_sc[1] = deg ? 0.0 : sqrt(nu2.hi);
+            s_sc[2] = deg ? 0.0 : dd_div_to_d(dd_add(dd_add(ms->alpha, dd{-2.0 * cb, 0.0}), dd{chc, 0.0}), nu2);
+            s_sc[3] = cc;
+        }
+    }
+    __syncthreads();
+    const bool deg = s_sc[0] != 0.0;
+    const double nu = s_sc[1];
+    const int off = deg ? 1 : 0;
+    const int n = m + 1 - off;                          // active size
+    const int k0 = 1 - off;                             // active index of coordinate 0
+    if (!deg) {
+        for (int i = tid; i < m; i += blockDim.x) {
+            const ff r0 = ff_from_double((bI[i] - HIIc[i]) / nu);
+            Rh[i + 1] = r0.hi; Rl[i + 1] = r0.lo;
+            Rh[(size_t)(i + 1) * ldr] = r0.hi; Rl[(size_t)(i + 1) * ldr] = r0.lo;
+        }
+        if (tid == 0) {
+            const ff r00 = ff_from_double(s_sc[2]);
+            Rh[0] = r00.hi; Rl[0] = r00.lo;
+        }
+    }
+    __syncthreads();
+    const float *Ah, *Al;
+    int lda;
+    float *vec;
+    if (use_smem) {
+        float *sh = sm, *sl = sm + (size_t)n * n;
+        for (int r = warp; r < n; r += (int)(blockDim.x >> 5))
+            for (int c = lane; c < n; c += 32) {
+                sh[r * n + c] = Rh[(size_t)(r + off) * ldr + (c + off)];
+                sl[r * n + c] = Rl[(size_t)(r + off) * ldr + (c + off)];
+            }
+        Ah = sh; Al = sl; lda = n;
+        vec = sm + 2 * (size_t)n * n;
+    } else {
+        Ah = Rh + (size_t)off * ldr + off;
+        Al = Rl + (size_t)off * ldr + off;
+        lda = ldr;
+        vec = sm;
+    }
+    float *xs = vec;                                    // float-float x (2 n floats)
+    float *ws = vec + 2 * n;                            // FP32 w (n floats)
+    double *zd = reinterpret_cast<double *>(vec + 4 * ((3 * n + 3) / 4));   // n doubles
+
+    // 2. start: x = [nu; c_I] / |.|
+    const bool act = tid < n;
+    const double zz0 = (deg ? 0.0 : nu * nu) + s_sc[3];
+    const double inv0 = zz0 > 0.0 ? 1.0 / sqrt(zz0) : 0.0;
+    ff x = {0.0f, 0.0f};
+    if (act) {
+        const double v0 = (tid < k0) ? nu : cI[tid - k0];
+        x = ff_from_double(zz0 > 0.0 ? v0 * inv0 : (tid == 0 ? 1.0 : 0.0));
+    }
+    __syncthreads();                                    // the copy of A is complete
+    const float d = act ? Ah[(size_t)tid * lda + tid] : 0.0f;
+    float pv = 0.0f, apv = 0.0f;                        // search direction p and A p
+    bool have_p = false;
+    ff theta = {0.0f, 0.0f}, xx = {1.0f, 0.0f};
+    float best = 3.0e38f;
+    int stall = 0, it = 0;
+    float drms;                                         // RMS of diag A, a scale for the tests below
+    {
+        float t[1] = {d * d};
+        bsum_f<1>(t, s_rf, hf);
+        drms = sqrtf(t[0] / (float)n);
+    }
+    for (;; ++it) {
+        // (a) A x in float-float
+        if (act) { xs[2 * tid] = x.hi; xs[2 * tid + 1] = x.lo; }
+        __syncthreads();
+        const ff ax = act ? ff_row(Ah, Al, lda, n, tid, xs) : ff{0.0f, 0.0f};
+        // (b) theta = x.Ax / x.x, r = A x - theta x
+        {
+            ff t[2] = {ff_mul(x, ax), ff_mul(x, x)};
+            bsum_ff<2>(t, s_rff, hff);
+            xx = t[1];
+            theta = ff_div(t[0], t[1]);
+        }
+        const float r = act ? ff_to_float(ff_add(ax, ff_neg(ff_mul(theta, x)))) : 0.0f;
+        const float th = ff_to_float(theta);
+        const float scale = fmaxf(fabsf(th), drms);
+        // (c) preconditioned residual w = r / |A_ii - theta|: the absolute value
+        //     keeps the preconditioner positive definite while theta is still
+        //     above some diagonal entries (an indefinite one stalls the iteration)
+        const float den = fmaxf(fabsf(d - th), 1e-4f * fmaxf(scale, 1e-30f));
+        float wv = act ? r / den : 0.0f;
+        const float xh = x.hi;
+        float red[3] = {r * r, xh * wv, xh * pv};
+        bsum_f<3>(red, s_rf, hf);
+        const float rr = red[0];
+        const float tol = 1e-14f * scale;
+        const float nres = sqrtf(rr);
+        // stop at the float-float floor, at the cap, or when progress has ended well below it
+        if (nres < best * 0.7f) { best = nres; stall = 0; } else ++stall;
+        if (!(nres > tol * sqrtf((float)n)) || it >= kEigMaxIt || (stall >= 4 && nres < 1e-11f * scale)) break;
+        // orthogonalise w and p against x (x.x ~ 1)
+        const float ixx = 1.0f / ff_to_float(xx);
+        wv -= red[1] * ixx * xh;
+        if (have_p) {
+            pv -= red[2] * ixx * xh;
+            apv -= red[2] * ixx * ff_to_float(ax);
+        }
+        // (d) A w
+        if (act) ws[tid] = wv;
+        __syncthreads();
+        const float awv = act ? f_row(Ah, lda, n, tid, ws) : 0.0f;
+        // (e) projections on span{x, w, p}
+        float pr[8] = {r * wv, r * pv, wv * awv, wv * apv, pv * apv, wv * wv, wv * pv, pv * pv};
+        bsum_f<8>(pr, s_rf, hf);
+        const float rw = pr[0], rp = pr[1], waw = pr[2], wap = pr[3], pap = pr[4], ww = pr[5], wp = pr[6], pp = pr[7];
+        // (f) Rayleigh-Ritz with the pencil shifted by theta, in the basis
+        //     x / |x|, w / |w|, and p orthogonalised against w
+        const float ix = sqrtf(ixx);
+        float yx = 1.0f, yw = 0.0f, yp = 0.0f;
+        if (ww > 0.0f) {
+            const float l11 = sqrtf(ww);
+            const float il11 = 1.0f / l11;
+            const float a0 = rw * il11 * ix;
+            const float hww = (waw - th * ww) * il11 * il11;
+            float l21 = 0.0f, l22sq = 0.0f;
+            bool use_p = have_p && pp > 0.0f;
+            if (use_p) {
+                l21 = wp * il11;
+                l22sq = pp - l21 * l21;
+                use_p = l22sq > 1e-6f * pp;
+            }
+            if (use_p) {
+                const float il22 = rsqrtf(l22sq);
+                // L^-1 [rw rp]^T and L^-1 H' L^-T for L = [l11 0; l21 l22]
+                const float a1 = (rp * ix - l21 * a0) * il22;
+                const float hwp = ((wap - th * wp) * il11 - l21 * hww) * il22;
+                const float hpp0 = (pap - th * pp);
+                // hpp = (hpp0 - 2 l21 (wap - th wp) / l11 + l21^2 hww) / l22^2
+                const float hpp = (hpp0 - 2.0f * l21 * (wap - th * wp) * il11 + l21 * l21 * hww) * il22 * il22;
+                float lam, v0, v1, v2;
+                sym3_lowest(0.0f, a0, a1, hww, hwp, hpp, lam, v0, v1, v2);
+                if (v0 < 0.0f) { v0 = -v0; v1 = -v1; v2 = -v2; }
+                yx = v0 * ix;
+                yp = v2 * il22;
+                yw = (v1 - l21 * yp) * il11;
+            } else {
+                float lam, v0, v1;
+                sym2_lowest(0.0f, a0, hww, lam, v0, v1);
+                if (v0 < 0.0f) { v0 = -v0; v1 = -v1; }
+                yx = v0 * ix;
+                yw = v1 * il11;
+                yp = 0.0f;
+            }
+        }
+        // (g) x <- yx x + yw w + yp p, p <- yw w + yp p (unit length), A p likewise
+        const float np = yw * wv + yp * pv;
+        const float nap = yw * awv + yp * apv;
+        const float pn2 = yw * yw * ww + 2.0f * yw * yp * wp + yp * yp * pp;
+        x = ff_add(ff_mul_f(x, yx), ff{np, 0.0f});
+        if (pn2 > 0.0f) {
+            const float ip = rsqrtf(pn2);
+            pv = np * ip;
+            apv = nap * ip;
+            have_p = true;
+        } else {
+            pv = 0.0f; apv = 0.0f; have_p = false;
+        }
+    }
+    // 3. z = sqrt(-lambda) x / |x| (FP64); the reduced problem needs lambda < 0
+    const double lamd = ff_to_double(theta);
+    if (!(lamd < 0.0)) {
+        if (tid == 0) set_status(st, kErrNotNegative);
+        return;
+    }
+    const double zs = sqrt(-lamd / ff_to_double(xx));
+    const double zi = act ? ff_to_double(x) * zs : 0.0;
+    if (act) zd[tid] = zi;
+    __syncthreads();
+    // sign (Eq. def-z wants gamma >= 0): z_0 >= 0; degenerate or z_0 = 0: z . [nu; c_I] >= 0
+    if (warp == 0) {
+        double dot = 0.0;
+        for (int i = lane; i < m; i += 32) dot = fma(zd[i + k0], cI[i], dot);
+        dot = wsum_d(dot);
+        if (lane == 0) {
+            const double z0 = deg ? 0.0 : zd[0];
+            const double sgn = (z0 < 0.0 || (z0 == 0.0 && dot < 0.0)) ? -1.0 : 1.0;
+            const double gamma = deg ? 1.0 : sgn * z0 / nu;
+            s_sc[0] = sgn;
+            s_sc[1] = gamma;
+        }
+    }
+    __syncthreads();
+    const double sgn = s_sc[0], gamma = s_sc[1];
+    const bool bad = !isfinite(gamma) || !(gamma > 1e-200);
+    const dd s_new = dd_mul_d(ms->scale, gamma);
+    const double rsc = 1.0 / s_new.hi;
+    // 4. eta (Eq. def-z), the new stored c_I, the scatter weights
+    double eta = 0.0;
+    int nz_from = 0, nz_to = 0;
+    if (tid < m) {
+        const double zn = sgn * zd[tid + k0];
+        const double ci = cI[tid];
+        eta = zn - gamma * ci;
+        etaout[tid] = eta;
+        w[tid] = eta * rsc;
+        thr[tid] = eta != 0.0 ? P.tau / fabs(eta) : 1.0e308;
+        if (!bad) P.table[sel[tid].slot].c = zn * rsc;
+        nz_from = (ci != 0.0 && zn == 0.0) ? 1 : 0;
+        nz_to = (ci == 0.0 && zn != 0.0) ? 1 : 0;
+    }
+    // eta in the active indexing (float-float) for eta^T H_II eta
+    __syncthreads();                                    // zd reads are done
+    if (act) {
+        const ff e = (tid >= k0) ? ff_from_double(sgn * zd[tid] - gamma * cI[tid - k0]) : ff{0.0f, 0.0f};
+        xs[2 * tid] = e.hi;
+        xs[2 * tid + 1] = e.lo;
+    }
+    __syncthreads();
+    {
+        const ff he = act ? ff_row(Ah, Al, lda, n, tid, xs) : ff{0.0f, 0.0f};
+        ff t[1] = {act ? ff_mul(ff{xs[2 * tid], xs[2 * tid + 1]}, he) : ff{0.0f, 0.0f}};
+        bsum_ff<1>(t, s_rff, hff);
+        if (tid == 0) s_sc[2] = ff_to_double(t[0]);
+    }
+    // eta . c_I, eta . b_I, eta . eta (warp 0, FP64) and the nonzero changes
+    if (tid < m) zd[tid] = eta;
+    {
+        int a = __reduce_add_sync(0xffffffffu, nz_from), b = __reduce_add_sync(0xffffffffu, nz_to);
+        __shared__ int s_nz[2][32];
+        if (lane == 0) { s_nz[0][warp] = a; s_nz[1][warp] = b; }
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            int fa = 0, fb = 0;
+            for (int q = 0; q < nw; ++q) { fa += s_nz[0][q]; fb += s_nz[1][q]; }
+            double ec = 0.0, eb = 0.0, ee = 0.0;
+            for (int i = lane; i < m; i += 32) {
+                const double e = zd[i];
+                ec = fma(e, cI[i], ec);
+                eb = fma(e, bI[i], eb);
+                ee = fma(e, e, ee);
+            }
+            ec = wsum_d(ec);
+            eb = wsum_d(eb);
+            ee = wsum_d(ee);
+            const double eHe = s_sc[2];
+            // mu and alpha (Alg. 2 update of c) in double-double: lane 0 mu, lane 1 alpha
+            const dd g2 = dd_two_prod(gamma, gamma);
+            dd out = {0.0, 0.0};
+            if (lane == 0) out = dd_add(dd_add(dd_mul(g2, ms->mu), dd_two_prod(2.0 * gamma, ec)), dd{ee, 0.0});
+            if (lane == 1) out = dd_add(dd_add(dd_mul(g2, ms->alpha), dd_two_prod(2.0 * gamma, eb)), dd{eHe, 0.0});
+            const dd al_n = {__shfl_sync(0xffffffffu, out.hi, 1), __shfl_sync(0xffffffffu, out.lo, 1)};
+            if (lane == 0) {
+                const dd mu_n = out;
+                if (bad || !isfinite(mu_n.hi) || !isfinite(al_n.hi)) {
+                    set_status(st, kErrNonfinite);
+                } else {
+                    ms->mu = mu_n;
+                    ms->alpha = al_n;
+                    ms->scale = s_new;
+                    st->scale = s_new;
+                }
+                ms->energy = dd_div_to_d(ms->alpha, ms->mu);
+                ms->iterations += 1;
+                ms->dx = P.theta * ms->dx + (1.0 - P.theta) * sqrt(ee);
+                if (P.dx_threshold > 0.0 && ms->dx < P.dx_threshold) ms->done_pending = 1;
+                ms->nnz_c += fb - fa;
+                ms->degenerate = deg ? 1 : 0;
+                ms->last_gamma = gamma;
+                ms->eig_iters = it;
+                ms->eig_iters_total += it;
+                ms->n_cand = 0;                         // the scatter builds the next candidate list
+            }
+        }
+    }
+}
+// ---------------------------------------------------------------------------
+// b += H_{:,I} eta for the m columns (stored units), gather, candidates.
+// A group of TPC threads handles one (column, chunk) work item.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
+                                                    const double *w, const double *thr, long long *cand,
+                                                    double *gathp, int tpc, int nchunk, int chunk) {
+    __shared__ ColLists Lg[8];
+    __shared__ double sred[256];
+    __shared__ long long scnt[4];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (ms->done || st->status) return;
+    const int gpb = 256 / tpc;                          // groups per block
+    const int grp = tid / tpc, gt = tid - grp * tpc;
+    const int m = ms->m_sel;
+    const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
+    const long long items = (long long)m * nchunk;
+    if (tid < 4) scnt[tid] = 0;
+    __syncthreads();
+    long long c_el = 0, c_app = 0, c_drop = 0, c_ins = 0;
+    for (long long base = (long long)blockIdx.x * gpb; base < items; base += (long long)gridDim.x * gpb) {
+        const long long item = base + grp;
+        const bool act = item < items;
+        const int col = act ? (int)(item / nchunk) : 0;
+        const int ck = act ? (int)(item - (long long)col * nchunk) : 0;
+        const McSel xs = sel[col];
+        ColLists &L = Lg[grp];
+        if (act)
+            for (int t = gt; t < P.N; t += tpc) {
+                int ra = __popcll(xs.A & low_mask(t)), rb = __popcll(xs.B & low_mask(t));
+                if ((xs.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+                if ((xs.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+            }
+        __syncthreads();
+        double gather = 0.0;
+        if (act) {
+            const double wi = w[col], ti = thr[col];
+            const long long e_beg = 1 + (long long)ck * chunk;
+            const long long e_end = e_beg + chunk < nh ? e_beg + chunk : nh;
+            for (long long e = e_beg + gt; e < e_end; e += tpc) {
+                unsigned long long oa, ob;
+                const double H = column_element(P, L, xs.A, xs.B, e, oa, ob);
+                if (is_zero(H)) continue;
+                ++c_el;
+                const bool big = fabs(H) >= ti;
+                bool ins = false;
+                const long long s = table_find(P, st, oa, ob, big, &ins);
+                if (s == -2) break;
+                if (s < 0) { ++c_drop; continue; }
+                Slot *sj = P.table + s;
+                const double cj = __ldcg(&sj->c);
+                if (!(!is_zero(cj) || big)) { ++c_drop; continue; }
+                atomicAdd(&sj->bv, wi * H);
+                ++c_app;
+                c_ins += ins ? 1 : 0;
+                gather = fma(H, cj, gather);
+                // candidate mark: the first thread to mark a slot appends it
+                bool first = false;
+                const unsigned long long kb = __ldcg(&sj->b);
+                if (!(kb & kMarkB)) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
+                const unsigned int fm = __ballot_sync(__activemask(), first);
+                if (first) {
+                    const int leader = __ffs(fm) - 1;
+                    int basepos = 0;
+                    if (lane == leader) basepos = atomicAdd(&ms->n_cand, __popc(fm));
+                    basepos = __shfl_sync(fm, basepos, leader);
+                    cand[basepos + __popc(fm & ((1u << lane) - 1u))] = s;
+                }
+            }
+        }
+        // fixed-order group sum of the gather
+        sred[tid] = gather;
+        __syncthreads();
+        if (act && gt == 0) {
+            double t = 0.0;
+            for (int q = 0; q < tpc; ++q) t += sred[grp * tpc + q];
+            gathp[(size_t)col * nchunk + ck] = t;
+        }
+        __syncthreads();
+    }
+    atomicAdd((unsigned long long *)&scnt[0], (unsigned long long)c_el);
+    atomicAdd((unsigned long long *)&scnt[1], (unsigned long long)c_app);
+    atomicAdd((unsigned long long *)&scnt[2], (unsigned long long)c_drop);
+    atomicAdd((unsigned long long *)&scnt[3], (unsigned long long)c_ins);
+    __syncthreads();
+    if (tid < 4) atomicAdd((unsigned long long *)&ms->cnt[tid], (unsigned long long)scnt[tid]);
+}
+
+// b_I recalculated (Eq. recalculate-b), the chosen coordinates join the
+// candidates, counters and the host snapshot.
+__global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel *sel, const double *Hdiag,
+                              const double *gathp, long long *cand, const double *etaout, int nchunk) {
+    if (ms->done || st->status) return;
+    const int m = ms->m_sel;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const long long slot = sel[i].slot;
+        double t = 0.0;
+        for (int k = 0; k < nchunk; ++k) t += gathp[(size_t)i * nchunk + k];
+        Slot *s = P.table + slot;
+        s->bv = fma(Hdiag[i], s->c, t);
+        const unsigned long long kb = s->b;
+        if (!(kb & kMarkB)) {
+            s->b = kb | kMarkB;
+            const int pos = atomicAdd(&ms->n_cand, 1);
+            cand[pos] = slot;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long nd = 0;
+        for (int i = 0; i < m; ++i) nd += Hdiag[i] != 0.0 ? 1 : 0;
+        ms->elements += ms->cnt[0] + nd;
+        ms->applied += ms->cnt[1] + nd;
+        ms->dropped += ms->cnt[2];
+        ms->inserted += ms->cnt[3];
+        ms->n_slots += ms->cnt[3];
+        ms->last_column = ms->cnt[0] + nd;
+        for (int k = 0; k < 4; ++k) ms->cnt[k] = 0;
+        if (ms->n_slots > P.max_entries) set_status(st, kErrTableFull);
+        st->iterations = ms->iterations;
+        st->nnz_c = ms->nnz_c;
+        st->n_slots = ms->n_slots;
+        st->elements = ms->elements;
+        st->applied = ms->applied;
+        st->dropped = ms->dropped;
+        st->inserted = ms->inserted;
+        st->last_column = ms->last_column;
+        st->eig_iters = ms->eig_iters_total;
+        st->mu = ms->mu;
+        st->alpha = ms->alpha;
+        st->dx = ms->dx;
+        st->energy = ms->energy;
+        st->last_eta = m > 0 ? etaout[0] : 0.0;
+        st->last_a = m > 0 ? sel[0].A : 0ull;
+        st->last_b = m > 0 ? sel[0].B : 0ull;
+        if (ms->done_pending) ms->done = 1;
+        st->done = ms->done;
+    }
+}
+
+// Start vector c = e_ref (as a forced first "step" with eta = 1 from c = 0).
+__global__ void k_mc_init(Problem P, McState *ms, IterState *st, McSel *sel, double *Hdiag, double *w, double *thr,
+                          double *etaout, unsigned long long A, unsigned long long B) {
+    __shared__ ColLists L;
+    __shared__ long long s_slot;
+    if (threadIdx.x == 0) {
+        bool ins = false;
+        long long s = table_find(P, st, A, B, true, &ins);
+        if (s < 0) { set_status(st, kErrTableFull); s = 0; }
+        s_slot = s;
+        P.table[s].c = 1.0;
+    }
+    for (int t = threadIdx.x; t < P.N; t += blockDim.x) {
+        int ra = __popcll(A & low_mask(t)), rb = __popcll(B & low_mask(t));
+        if ((A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+        if ((B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const double hd = diag_warp(P, L);
+        if (threadIdx.x == 0) {
+            McSel x;
+            x.slot = s_slot; x.gkey = 0ull; x.A = A; x.B = B;
+            sel[0] = x;
+            Hdiag[0] = hd;
+            w[0] = 1.0;
+            thr[0] = P.tau;
+            etaout[0] = 1.0;
+            ms->m_sel = 1;
+            ms->n_cand = 0;
+            ms->mu = dd_from(1.0);
+            ms->alpha = dd_from(hd);
+            ms->scale = dd_from(1.0);
+            st->scale = dd_from(1.0);
+            ms->energy = hd;
+            ms->dx = 0.0;
+            ms->iterations = 0;
+            ms->nnz_c = 1;
+            ms->n_slots = 1;
+            ms->inserted = 1;
+            ms->elements = 0; ms->applied = 0; ms->dropped = 0; ms->last_column = 0;
+            for (int k = 0; k < 4; ++k) ms->cnt[k] = 0;
+            ms->done = 0;
+            ms->done_pending = 0;
+            ms->n_above = 0;
+            ms->n_inbin = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+size_t mc_eigen_smem(int m) {
+    const size_t n = (size_t)m + 1;
+    const size_t vec = 4 * ((3 * n + 3) / 4) + 2 * n;           // x (float-float), w, eta (FP64)
+    return ((n <= (size_t)kEigSmemN ? 2 * n * n : 0) + vec) * sizeof(float);
+}
+int mc_eigen_threads(int m) { return 32 * ((m + 1 + 31) / 32); }
+int mc_max_m() { return kEigMaxN - 1; }
+
+cudaError_t mc_configure() {
+    cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mc_eigen_smem(kEigSmemN - 1));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mc_sortsel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kInBin * sizeof(McSel)));
+}
+
+cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
+                           cudaStream_t s) {
+    k_mc_init<<<1, 64, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.w, b.thr, b.eta, A, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s) {
+    k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp, b.tpc, b.nchunk,
+                                                b.chunk);
+    k_mc_finalize<<<1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.nchunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s) {
+    k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.hist, b.m);
+    for (int level = 1; level < kSelLevels; ++level) k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, level);
+    k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
+    k_mc_sortsel<<<1, 1024, kInBin * sizeof(McSel), s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
+    k_mc_prepare<<<(b.m + 7) / 8, 256, 0, s>>>(P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr);
+    k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Rh,
+                                                                    b.Rl, b.ldr, b.m + 1 <= kEigSmemN ? 1 : 0,
+                                                                    b.w, b.thr, b.eta);
+    return launch_mc_scatter_finalize(P, b, s);
+}
+
+}  // namespace cdfci

@@ -17,6 +17,10 @@
 namespace cdfci {
 
 constexpr int kMaxN = 63;
+// Bit 63 of the beta word of a stored key marks "already a candidate" during a
+// multicoordinate iteration (N <= 63 leaves it free); key comparisons ignore it.
+constexpr unsigned long long kMarkB = 1ull << 63;
+constexpr unsigned long long kKeyMaskB = ~kMarkB;
 constexpr int kMaxPairs = 63 * 62 / 2;     // C(63, 2)
 constexpr int kStatusOk = 0;
 
@@ -123,7 +127,27 @@ struct IterState {
     dd mu, alpha;
     double dx, energy, last_eta;
     unsigned long long last_a, last_b;
+    long long eig_iters;           // m > 1: cumulative reduced-eigensolver iterations
     int done;
+};
+
+// Multicoordinate (m > 1) iteration state, one per handle.
+struct McSel {                     // a chosen coordinate
+    long long slot;
+    unsigned long long gkey;       // |b + mu c| bits (the choice key)
+    unsigned long long A, B;       // its determinant
+};
+struct McState {
+    dd mu, alpha, scale;           // c.c, c.Hc (true units), global scale s (stored = true / s)
+    double dx, energy, last_gamma;
+    long long iterations, nnz_c, n_slots, elements, applied, dropped, inserted, last_column;
+    unsigned long long cnt[4];     // counters of the running scatter
+    unsigned long long sel_prefix; // radix selection: digits fixed so far
+    int n_cand, m_sel, degenerate, done, done_pending;
+    int sel_need, sel_level, sel_nbin, sel_resolved;
+    int n_above, n_inbin;
+    int eig_iters;                 // LOBPCG iterations of the last reduced problem
+    long long eig_iters_total;
 };
 
 // Everything a kernel needs about the problem and the table.
@@ -234,13 +258,14 @@ __device__ __forceinline__ long long table_find(const Problem &P, IterState *st,
             ka = __ldcg(&s->a);
             kb = __ldcg(&s->b);
         }
-        if (ka == a && kb == b) return (long long)pos;
+        if (ka == a && (kb & kKeyMaskB) == b) return (long long)pos;
         if (ka == 0ull && kb == 0ull) {
             if (!insert) return -1;
             unsigned long long oa, ob;
             cas128(&s->a, 0ull, 0ull, a, b, oa, ob);
             if (oa == 0ull && ob == 0ull) { *inserted = true; return (long long)pos; }
-            if (oa == a && ob == b) return (long long)pos;
+            // lost to an insert of the same key (which may already carry the candidate mark)
+            if (oa == a && (ob & kKeyMaskB) == b) return (long long)pos;
         }
         pos = (pos + 1) & P.mask;
     }

@@ -184,7 +184,7 @@ __device__ __forceinline__ void resolve_elem(const Problem &P, IterState *st, El
             k = __ldcg(reinterpret_cast<const ulonglong2 *>(P.table + p));
             cb = __ldcg(reinterpret_cast<const double2 *>(&P.table[p].c));
         }
-        if (k.x == x.ka && k.y == x.kb) { x.pos = (long long)p; x.cb0 = cb; x.state = 1; return; }
+        if (k.x == x.ka && (k.y & kKeyMaskB) == x.kb) { x.pos = (long long)p; x.cb0 = cb; x.state = 1; return; }
         if (k.x == 0ull && k.y == 0ull) { x.pos = (long long)p; x.state = 2; return; }
         p = (p + 1) & P.mask;
         k = __ldcg(reinterpret_cast<const ulonglong2 *>(P.table + p));
@@ -654,7 +654,7 @@ __global__ void k_export(Problem P, const IterState *st, unsigned long long *key
         unsigned long long pos = atomicAdd(counter, 1ull);
         if ((long long)pos < cap) {
             keys[2 * pos] = sl.a;
-            keys[2 * pos + 1] = sl.b;
+            keys[2 * pos + 1] = sl.b & kKeyMaskB;
             if (c) c[pos] = sl.c * s;
             if (b) b[pos] = sl.bv * s;
         }
@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(256) k_rq_partial(Problem P, IterState *st, co
     for (long long k = blockIdx.x; k < n; k += gridDim.x) {
         if (threadIdx.x == 0) {
             Slot sl = P.table[list[k]];
-            s_a = sl.a; s_b = sl.b; s_ci = sl.c;
+            s_a = sl.a; s_b = sl.b & kKeyMaskB; s_ci = sl.c;
         }
         __syncthreads();
         build_lists(L, P.N, s_a, s_b);

@@ -25,6 +25,27 @@ cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int 
 cudaError_t launch_init_state(const Problem &P, IterState *st, CdRecord *rec, unsigned long long A,
                               unsigned long long B, cudaStream_t s);
 
+// Device buffers of the multicoordinate iteration.
+struct McBuffers {
+    McState *ms;
+    IterState *st;
+    long long *cand;               // candidate slots (deduplicated)
+    unsigned long long *gkey;      // their choice keys
+    unsigned int *hist;            // 4096-bin radix histogram, then the last-block counter
+    McSel *sel, *inbin;
+    double *cI, *bI, *Hdiag, *HIIc, *w, *thr, *eta, *gathp;
+    float *Rh, *Rl;                // reduced matrix R as float-float pairs, leading dimension ldr
+    int ldr;
+    int m, cand_grid, scatter_grid, tpc, nchunk, chunk;
+};
+size_t mc_eigen_smem(int m);
+int mc_max_m();
+cudaError_t mc_configure();
+cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
+                           cudaStream_t s);
+cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
+cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s);
+
 // sets the message returned by cdfci_last_error() on the calling thread
 void set_last_error_message(const char *msg);
 

@@ -48,7 +48,7 @@ int main(void) {
   printf("cdfci_stats %zu\\n", sizeof(cdfci_stats));
   F(cdfci_params, z_threshold) F(cdfci_params, ref_alpha) F(cdfci_params, block_threads)
   F(cdfci_params, deterministic) F(cdfci_params, cuda_stream)
-  F(cdfci_stats, energy) F(cdfci_stats, nnz_c) F(cdfci_stats, load) F(cdfci_stats, status) F(cdfci_stats, converged)
+  F(cdfci_stats, energy) F(cdfci_stats, nnz_c) F(cdfci_stats, load) F(cdfci_stats, status) F(cdfci_stats, converged) F(cdfci_stats, reduced_iterations)
   return 0;
 }
 """)
