@@ -148,6 +148,30 @@ int cdfci_export(cdfci_handle h, uint64_t *keys, double *c, double *b, int64_t c
  */
 int cdfci_last_step(cdfci_handle h, uint64_t *keys, double *eta, int64_t cap, int64_t *m_out);
 
+/*
+ * Spin-summed reduced density matrices of the current vector, normalised by
+ * c.c (Sec. "Optimal Orbital Selections"):
+ *   rdm1[p*N+q]               = gamma_pq   = sum_s  <a+_ps a_qs>
+ *   rdm2[((p*N+q)*N+r)*N+s]   = Gamma_pqrs = sum_st <a+_ps a+_rt a_st a_qs>
+ * in chemists' order, so that E = sum h_pq gamma_pq + 1/2 sum (pq|rs) Gamma_pqrs.
+ * rdm1 (N*N doubles) and rdm2 (N^4 doubles, or NULL) are host or device memory.
+ * Cost: one pass over the stored determinants, each enumerating all its
+ * single and double excitations with a table lookup per excitation.
+ */
+int cdfci_rdm(cdfci_handle h, double *rdm1, double *rdm2);
+
+/*
+ * Derivatives of the energy E = sum h gamma + 1/2 sum (pq|rs) Gamma of the
+ * current vector (Hellmann-Feynman at convergence): dE_dh = gamma (N*N),
+ * dE_dg = 1/2 Gamma averaged over the 8-fold symmetry of (pq|rs) (N^4: the
+ * derivative along 8-fold symmetric perturbations), dE_dkappa = 2 (F - F^T)
+ * (N*N, antisymmetric) for orbitals rotated by U = exp(kappa),
+ * F_pq = sum_r h_pr gamma_qr + sum_rst (pr|st) Gamma_qrst, so that
+ * dE = 1/2 sum_pq dE_dkappa[p][q] dkappa_pq.  h and g are the handle's
+ * (symmetrised) integrals.  Any output may be NULL; host or device memory.
+ */
+int cdfci_gradient(cdfci_handle h, double *dE_dh, double *dE_dg, double *dE_dkappa);
+
 /* Current stats without running an iteration. */
 int cdfci_get_stats(cdfci_handle h, cdfci_stats *stats);
 

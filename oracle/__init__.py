@@ -18,6 +18,9 @@ scalars), loaded with ctypes:
   * ``line_search``     - the appendix's Cardano + Newton step.
   * ``rdm``             - spin-summed 1- and 2-RDMs by literal operator
     application (Sec. "Optimal Orbital Selections").
+  * ``rotate_integrals`` / ``orbital_gradient`` - h, g in rotated orbitals
+    U = exp(kappa) and the energy's derivative with respect to kappa, from
+    the RDMs (Sec. "Optimal Orbital Selections", the rotated-integral energy).
 """
 from __future__ import annotations
 
@@ -291,3 +294,24 @@ class CDFCI:
             self.close()
         except Exception:
             pass
+
+
+def rotate_integrals(h: np.ndarray, g: np.ndarray, kappa: np.ndarray):
+    """Integrals in the orbitals (phi) = (psi) U with U = exp(kappa), kappa
+    antisymmetric: h'_pq = sum_ab U_ap h_ab U_bq and
+    g'_pqrs = sum_abcd U_ap U_bq U_cr U_ds g_abcd (Sec. "Optimal Orbital
+    Selections"; the exponential is the library's matrix exponential)."""
+    from scipy.linalg import expm
+    U = expm(np.asarray(kappa, dtype=np.float64))
+    h2 = U.T @ h @ U
+    g2 = np.einsum("ap,bq,cr,ds,abcd->pqrs", U, U, U, U, g, optimize=True)
+    return h2, g2
+
+
+def orbital_gradient(h: np.ndarray, g: np.ndarray, g1: np.ndarray, g2: np.ndarray) -> np.ndarray:
+    """dE/dkappa at kappa = 0 for E = sum h' gamma + 1/2 sum g' Gamma with the
+    integrals rotated by U = exp(kappa): the antisymmetric 2 (F - F^T), with
+    F_pq = sum_r h_pr gamma_qr + sum_rst (pr|st) Gamma_qrst, so that
+    dE = 1/2 sum_pq G_pq dkappa_pq for an antisymmetric dkappa."""
+    F = h @ g1.T + np.einsum("prst,qrst->pq", g, g2)
+    return 2.0 * (F - F.T)

@@ -70,6 +70,8 @@ def lib():
         L.cdfci_energy.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.cdfci_get_column.argtypes = [vp, u64p, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_export.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.cdfci_rdm.argtypes = [vp, dp, dp]
+        L.cdfci_gradient.argtypes = [vp, dp, dp, dp]
         L.cdfci_last_step.argtypes = [vp, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_column_noalloc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p, dp, i64,
                                            ctypes.POINTER(ctypes.c_int64), vp]
@@ -165,6 +167,21 @@ def cdfci_export(handle: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     return keys[:n.value], c[:n.value], b[:n.value]
 
 
+def cdfci_rdm(handle: int, N: int, two_body: bool = True) -> Tuple[np.ndarray, Optional[np.ndarray]]:
+    """Spin-summed gamma (N, N) and Gamma (N, N, N, N) of the current vector."""
+    g1 = np.zeros((N, N))
+    g2 = np.zeros((N, N, N, N)) if two_body else None
+    _check(lib().cdfci_rdm(handle, _ptr(g1), _ptr(g2) if two_body else None))
+    return g1, g2
+
+
+def cdfci_gradient(handle: int, N: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """dE/dh (N, N), dE/dg (N, N, N, N) and dE/dkappa (N, N) of the current vector."""
+    dh, dg, dk = np.zeros((N, N)), np.zeros((N, N, N, N)), np.zeros((N, N))
+    _check(lib().cdfci_gradient(handle, _ptr(dh), _ptr(dg), _ptr(dk)))
+    return dh, dg, dk
+
+
 def cdfci_last_step(handle: int, cap: int = 1024) -> Tuple[np.ndarray, np.ndarray]:
     keys = np.zeros((cap, 2), dtype=np.uint64)
     eta = np.zeros(cap)
@@ -196,6 +213,7 @@ class Solver:
     """Owning wrapper around a handle (convenience for tests and the benchmark)."""
 
     def __init__(self, h, g, N, n_alpha, n_beta, **params):
+        self.N = N
         self.p = cdfci_default_params(**params)
         self.handle = cdfci_create(np.ascontiguousarray(h, dtype=np.float64) if isinstance(h, np.ndarray) else h,
                                    np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g,
@@ -218,6 +236,12 @@ class Solver:
 
     def last_step(self):
         return cdfci_last_step(self.handle)
+
+    def rdm(self, two_body: bool = True):
+        return cdfci_rdm(self.handle, self.N, two_body)
+
+    def gradient(self):
+        return cdfci_gradient(self.handle, self.N)
 
     def close(self):
         if self.handle:

@@ -501,6 +501,73 @@ CDFCI_API int cdfci_export(cdfci_handle c, uint64_t *keys, double *cv, double *b
     return CDFCI_OK;
 }
 
+namespace {
+// RDMs into device buffers owned by the caller of this helper (N*N and N^4)
+int rdm_device(cdfci_ctx *c, double *g1, double *g2) {
+    const size_t n2 = (size_t)c->P.N * c->P.N, n4 = n2 * n2;
+    double *raw1 = nullptr, *raw2 = nullptr, *nrm = nullptr;
+    if (cudaMalloc(&raw1, n2 * sizeof(double)) != cudaSuccess || cudaMalloc(&raw2, n4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&nrm, sizeof(double)) != cudaSuccess) {
+        cudaFree(raw1); cudaFree(raw2); cudaFree(nrm);
+        return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    }
+    cudaError_t e = launch_rdm(c->P, c->d_st, raw1, raw2, nrm, g1, g2, c->stream);
+    double norm = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&norm, nrm, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(raw1); cudaFree(raw2); cudaFree(nrm);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "rdm: %s", cudaGetErrorString(e));
+    if (!(norm > 0.0)) return fail(CDFCI_ERR_ARG, "rdm: the stored vector is zero");
+    return CDFCI_OK;
+}
+}  // namespace
+
+CDFCI_API int cdfci_rdm(cdfci_handle c, double *rdm1, double *rdm2) {
+    if (!c || !rdm1) return fail(CDFCI_ERR_ARG, "NULL argument");
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    const size_t n2 = (size_t)c->P.N * c->P.N, n4 = n2 * n2;
+    double *g1 = nullptr, *g2 = nullptr;
+    if (cudaMalloc(&g1, n2 * sizeof(double)) != cudaSuccess || cudaMalloc(&g2, n4 * sizeof(double)) != cudaSuccess) {
+        cudaFree(g1); cudaFree(g2);
+        return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    }
+    rc = rdm_device(c, g1, g2);
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaMemcpyAsync(rdm1, g1, n2 * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (!rc && e == cudaSuccess && rdm2) e = cudaMemcpyAsync(rdm2, g2, n4 * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(g1); cudaFree(g2);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "rdm copy: %s", cudaGetErrorString(e));
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_gradient(cdfci_handle c, double *dE_dh, double *dE_dg, double *dE_dkappa) {
+    if (!c) return fail(CDFCI_ERR_ARG, "NULL argument");
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    const int N = c->P.N;
+    const size_t n2 = (size_t)N * N, n4 = n2 * n2;
+    double *g1 = nullptr, *g2 = nullptr, *F = nullptr, *oh = nullptr, *og = nullptr, *ok = nullptr;
+    bool okm = cudaMalloc(&g1, n2 * sizeof(double)) == cudaSuccess && cudaMalloc(&g2, n4 * sizeof(double)) == cudaSuccess &&
+               cudaMalloc(&F, n2 * sizeof(double)) == cudaSuccess && cudaMalloc(&oh, n2 * sizeof(double)) == cudaSuccess &&
+               cudaMalloc(&og, n4 * sizeof(double)) == cudaSuccess && cudaMalloc(&ok, n2 * sizeof(double)) == cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!okm) rc = fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    if (!rc) rc = rdm_device(c, g1, g2);
+    if (!rc) e = launch_gradient(N, c->d_h, c->d_g, g1, g2, F, dE_dh ? oh : nullptr, dE_dg ? og : nullptr,
+                                 dE_dkappa ? ok : nullptr, c->stream);
+    if (!rc && e == cudaSuccess && dE_dh) e = cudaMemcpyAsync(dE_dh, oh, n2 * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (!rc && e == cudaSuccess && dE_dg) e = cudaMemcpyAsync(dE_dg, og, n4 * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (!rc && e == cudaSuccess && dE_dkappa) e = cudaMemcpyAsync(dE_dkappa, ok, n2 * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(g1); cudaFree(g2); cudaFree(F); cudaFree(oh); cudaFree(og); cudaFree(ok);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "gradient: %s", cudaGetErrorString(e));
+    return CDFCI_OK;
+}
+
 CDFCI_API int cdfci_last_step(cdfci_handle c, uint64_t *keys, double *eta, int64_t cap, int64_t *m_out) {
     if (!c || !m_out) return fail(CDFCI_ERR_ARG, "NULL argument");
     int rc = fill_stats(c, nullptr);

@@ -29,12 +29,7 @@ namespace cdfci {
 
 namespace {
 
-constexpr int kInBin = 4096;          // candidates sorted in one CTA on the threshold digit
-
-__device__ __forceinline__ bool mc_better(unsigned long long g1, unsigned long long a1, unsigned long long b1,
-                                          unsigned long long g2, unsigned long long a2, unsigned long long b2) {
-    return g1 > g2 || (g1 == g2 && key_less(a1, b1, a2, b2));
-}
+constexpr int kInBin = 1024;          // candidates sorted in one CTA on the threshold digit
 
 // <D1|H|D2> for two determinants differing by at most a double excitation
 // (Eq. entry; same sign convention as the column enumeration: D1 is reached
@@ -283,27 +278,24 @@ __device__ __forceinline__ unsigned int sel_digit(unsigned long long k, int leve
     return (unsigned int)((k >> lo) & ((1ull << sel_bits(level)) - 1ull));
 }
 
-// Count the keys of this block's share into sh (block-local), then add the
-// nonzero bins to hist; true in the block that finishes last.
-__device__ bool sel_count(const unsigned long long *gkey, int n, int level, unsigned long long prefix,
-                          unsigned int *sh, unsigned int *hist, unsigned int *counter) {
-    __shared__ int s_any;
-    __shared__ bool s_last;
-    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
-    if (threadIdx.x == 0) s_any = 0;
-    __syncthreads();
-    int any = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const unsigned long long k = gkey[t];
-        if (level > 0 && sel_top(k, level) != prefix) continue;
-        atomicAdd(&sh[sel_digit(k, level)], 1u);
-        any = 1;
+// Add one key's digit to the block histogram sh: lanes of a warp with the same
+// digit are combined first (a level's keys crowd into a few bins).  Called by
+// whole warps; ok = this lane has a key to count.
+__device__ __forceinline__ void sel_bin_add(unsigned int *sh, bool ok, unsigned int dg) {
+    const unsigned int act = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+        const unsigned int grp = __match_any_sync(act, dg);
+        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&sh[dg], (unsigned int)__popc(grp));
     }
-    if (any) s_any = 1;
+}
+
+// Add the block histogram to the global one (nonzero bins only); true in the
+// block that finishes last.
+__device__ bool sel_merge(unsigned int *sh, unsigned int *hist, unsigned int *counter) {
+    __shared__ bool s_last;
     __syncthreads();
-    if (s_any)
-        for (int d = threadIdx.x; d < kSelBins; d += blockDim.x)
-            if (sh[d]) atomicAdd(&hist[d], sh[d]);
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x)
+        if (sh[d]) atomicAdd(&hist[d], sh[d]);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
@@ -360,13 +352,25 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, const 
     if (ms->done) return;
     const int n = ms->n_cand;
     const double mu = ms->mu.hi;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        Slot *s = P.table + cand[t];
-        const double c = s->c, b = s->bv;
-        gkey[t] = (unsigned long long)__double_as_longlong(fma(mu, c, b)) & 0x7fffffffffffffffull;
-        s->b = s->b & kKeyMaskB;                       // clear the candidate mark
+    const bool count = n > m;
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
+    __syncthreads();
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int t = base + threadIdx.x;
+        const bool ok = t < n;
+        unsigned long long k = 0ull;
+        if (ok) {
+            Slot *s = P.table + cand[t];
+            const ulonglong2 key = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(&s->c));
+            k = (unsigned long long)__double_as_longlong(fma(mu, v.x, v.y)) & 0x7fffffffffffffffull;
+            gkey[t] = k;
+            if (key.y & kMarkB) s->b = key.y & kKeyMaskB;     // clear the candidate mark
+        }
+        if (count) sel_bin_add(sh, ok, sel_digit(k, 0));
     }
-    if (n <= m) {                                      // every candidate is chosen
+    if (!count) {                                      // every candidate is chosen
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ms->sel_prefix = 0ull;
             ms->sel_need = 0;
@@ -376,8 +380,7 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, const 
         }
         return;
     }
-    __syncthreads();                                   // this block's keys are written
-    if (sel_count(gkey, n, 0, 0ull, sh, hist, hist + kSelBins)) {
+    if (sel_merge(sh, hist, hist + kSelBins)) {
         if (threadIdx.x == 0) ms->sel_prefix = 0ull;
         __syncthreads();
         sel_scan(ms, hist, hist + kSelBins, 0, m);
@@ -389,8 +392,19 @@ __global__ void __launch_bounds__(256) k_mc_hist(McState *ms, const unsigned lon
                                                  int level) {
     __shared__ unsigned int sh[kSelBins];
     if (ms->done || ms->sel_resolved) return;
-    if (sel_count(gkey, ms->n_cand, level, ms->sel_prefix, sh, hist, hist + kSelBins))
-        sel_scan(ms, hist, hist + kSelBins, level, ms->sel_need);
+    const int n = ms->n_cand;
+    const unsigned long long prefix = ms->sel_prefix;
+    const int need = ms->sel_need;
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
+    __syncthreads();
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int t = base + threadIdx.x;
+        unsigned long long k = t < n ? gkey[t] : 0ull;
+        const bool ok = t < n && sel_top(k, level) == prefix;
+        sel_bin_add(sh, ok, sel_digit(k, level));
+    }
+    if (sel_merge(sh, hist, hist + kSelBins)) sel_scan(ms, hist, hist + kSelBins, level, need);
 }
 
 __global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, const unsigned long long *gkey,
@@ -424,17 +438,28 @@ __global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, cons
     }
 }
 
-// bitonic sort of up to 4096 entries in shared memory by (gkey desc, key asc)
-__device__ void bitonic_sort(McSel *a, int n_pow2) {
+// Bitonic sort, in shared memory, of (choice key, index) pairs into the choice
+// order: |g| descending, then the determinant key ascending (looked up in src
+// for exact ties only).  Padding entries (index -1) sort last.
+struct SelKey {
+    unsigned long long g;
+    int i, pad;
+};
+__device__ __forceinline__ bool sk_before(const SelKey &x, const SelKey &y, const McSel *src) {
+    if (y.i < 0) return x.i >= 0;
+    if (x.i < 0) return false;
+    if (x.g != y.g) return x.g > y.g;
+    return key_less(src[x.i].A, src[x.i].B, src[y.i].A, src[y.i].B);
+}
+__device__ void bitonic_sk(SelKey *a, int n_pow2, const McSel *src) {
     for (int k = 2; k <= n_pow2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < n_pow2; i += blockDim.x) {
                 const int l = i ^ j;
                 if (l > i) {
-                    const bool up = (i & k) == 0;
-                    const McSel x = a[i], y = a[l];
-                    const bool y_first = mc_better(y.gkey, y.A, y.B, x.gkey, x.A, x.B);
-                    if (up ? y_first : !y_first) { a[i] = y; a[l] = x; }
+                    const SelKey x = a[i], y = a[l];
+                    const bool y_first = sk_before(y, x, src);
+                    if (((i & k) == 0) ? y_first : !y_first) { a[i] = y; a[l] = x; }
                 }
             }
             __syncthreads();
@@ -442,43 +467,40 @@ __device__ void bitonic_sort(McSel *a, int n_pow2) {
     }
 }
 
+// The in-bin candidates sorted, the first sel_need of them join the chosen
+// set; then the chosen set in the choice order (a canonical order for the
+// reduced problem's rows).
 __global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, const McSel *inbin, int m,
                                                       IterState *st) {
-    extern __shared__ McSel sh[];
+    __shared__ SelKey sk[kInBin];
+    __shared__ McSel tmp[kInBin];
     const int tid = threadIdx.x;
     if (ms->done) return;
     const int n_above = ms->n_above;
     int n_in = ms->n_inbin;
     if (ms->sel_level > 0 && n_in > kInBin) {
-        if (tid == 0) set_status(st, kErrArg);            // more than 4096 exactly equal |g| values
+        if (tid == 0) set_status(st, kErrArg);            // more than kInBin candidates with one key pattern
         n_in = kInBin;
     }
     const int need = ms->sel_level == 0 ? 0 : ms->sel_need;
-    // sort the threshold-digit candidates, keep the first `need`
     int p2 = 1;
     while (p2 < n_in) p2 <<= 1;
-    for (int i = tid; i < p2; i += blockDim.x) {
-        if (i < n_in) sh[i] = inbin[i];
-        else { McSel z; z.slot = -1; z.gkey = 0ull; z.A = ~0ull; z.B = ~0ull; sh[i] = z; }
-    }
+    for (int i = tid; i < p2; i += blockDim.x) sk[i] = SelKey{i < n_in ? inbin[i].gkey : 0ull, i < n_in ? i : -1, 0};
     __syncthreads();
-    if (n_in > 1) bitonic_sort(sh, p2);
-    __syncthreads();
+    if (n_in > 1) bitonic_sk(sk, p2, inbin);
     const int take = need < n_in ? need : n_in;
-    for (int i = tid; i < take; i += blockDim.x) sel[n_above + i] = sh[i];
+    for (int i = tid; i < take; i += blockDim.x) sel[n_above + i] = inbin[sk[i].i];
     __syncthreads();
-    // canonical order of the selected set
     const int msel = n_above + take;
     int q2 = 1;
     while (q2 < msel) q2 <<= 1;
     for (int i = tid; i < q2; i += blockDim.x) {
-        if (i < msel) sh[i] = sel[i];
-        else { McSel z; z.slot = -1; z.gkey = 0ull; z.A = ~0ull; z.B = ~0ull; sh[i] = z; }
+        if (i < msel) tmp[i] = sel[i];
+        sk[i] = SelKey{i < msel ? sel[i].gkey : 0ull, i < msel ? i : -1, 0};
     }
     __syncthreads();
-    if (msel > 1) bitonic_sort(sh, q2);
-    __syncthreads();
-    for (int i = tid; i < msel; i += blockDim.x) sel[i] = sh[i];
+    if (msel > 1) bitonic_sk(sk, q2, tmp);
+    for (int i = tid; i < msel; i += blockDim.x) sel[i] = tmp[sk[i].i];
     if (tid == 0) {
         ms->m_sel = msel;
         ms->n_above = 0;
@@ -548,35 +570,63 @@ constexpr int kEigSmemN = 160;      // A in shared memory (hi and lo) up to this
 constexpr int kEigMaxN = 1024;      // m + 1 <= 1024: one thread per row
 constexpr int kEigMaxIt = 200;
 
-// row i of A times the float-float vector xs (interleaved hi, lo)
-__device__ __forceinline__ ff ff_row(const float *Ah, const float *Al, int lda, int n, int i, const float *xs) {
+// Row `row` of A times a vector: this thread's share, the columns j = k,
+// k + tpr, ... (k = its rank in the row's group of tpr threads); A(i, j) is
+// read at j * ld + i (A is symmetric), so a warp's groups read consecutive i.
+__device__ __forceinline__ ff ff_row_part(const float *Ah, const float *Al, int ld, int n, int row, int k, int tpr,
+                                          const float *xs) {
     float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
-    int j = 0;
-    for (; j + 1 < n; j += 2) {
-        ff_mac(h0, l0, Ah[(size_t)j * lda + i], Al[(size_t)j * lda + i], ff{xs[2 * j], xs[2 * j + 1]});
-        ff_mac(h1, l1, Ah[(size_t)(j + 1) * lda + i], Al[(size_t)(j + 1) * lda + i], ff{xs[2 * j + 2], xs[2 * j + 3]});
+    int j = k;
+    for (; j + tpr < n; j += 2 * tpr) {
+        ff_mac(h0, l0, Ah[j * ld + row], Al[j * ld + row], ff{xs[2 * j], xs[2 * j + 1]});
+        const int j2 = j + tpr;
+        ff_mac(h1, l1, Ah[j2 * ld + row], Al[j2 * ld + row], ff{xs[2 * j2], xs[2 * j2 + 1]});
     }
-    if (j < n) ff_mac(h0, l0, Ah[(size_t)j * lda + i], Al[(size_t)j * lda + i], ff{xs[2 * j], xs[2 * j + 1]});
+    if (j < n) ff_mac(h0, l0, Ah[j * ld + row], Al[j * ld + row], ff{xs[2 * j], xs[2 * j + 1]});
     return ff_add(ff_norm(h0, l0), ff_norm(h1, l1));
 }
-// row i of A (hi part) times the FP32 vector ws
-__device__ __forceinline__ float f_row(const float *Ah, int lda, int n, int i, const float *ws) {
+__device__ __forceinline__ float f_row_part(const float *Ah, int ld, int n, int row, int k, int tpr, const float *ws) {
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    int j = 0;
-    for (; j + 3 < n; j += 4) {
-        a0 = fmaf(Ah[(size_t)j * lda + i], ws[j], a0);
-        a1 = fmaf(Ah[(size_t)(j + 1) * lda + i], ws[j + 1], a1);
-        a2 = fmaf(Ah[(size_t)(j + 2) * lda + i], ws[j + 2], a2);
-        a3 = fmaf(Ah[(size_t)(j + 3) * lda + i], ws[j + 3], a3);
+    int j = k;
+    for (; j + 3 * tpr < n; j += 4 * tpr) {
+        a0 = fmaf(Ah[j * ld + row], ws[j], a0);
+        a1 = fmaf(Ah[(j + tpr) * ld + row], ws[j + tpr], a1);
+        a2 = fmaf(Ah[(j + 2 * tpr) * ld + row], ws[j + 2 * tpr], a2);
+        a3 = fmaf(Ah[(j + 3 * tpr) * ld + row], ws[j + 3 * tpr], a3);
     }
-    for (; j < n; ++j) a0 = fmaf(Ah[(size_t)j * lda + i], ws[j], a0);
+    for (; j < n; j += tpr) a0 = fmaf(Ah[j * ld + row], ws[j], a0);
     return (a0 + a1) + (a2 + a3);
 }
+// sums over the tpr lanes of a row's group (xor butterfly: sums of commutative
+// pairs, identical in every lane of the group)
+__device__ __forceinline__ ff ff_group_sum(ff v, int tpr) {
+    for (int o = 1; o < tpr; o <<= 1)
+        v = ff_add(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    return v;
+}
+__device__ __forceinline__ float f_group_sum(float v, int tpr) {
+    for (int o = 1; o < tpr; o <<= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// A x (float-float) and A w (FP32) for the row; every lane of the group holds it
+__device__ __forceinline__ ff ff_row(const float *Ah, const float *Al, int ld, int n, int row, int k, int tpr,
+                                     bool act, const float *xs) {
+    return ff_group_sum(act ? ff_row_part(Ah, Al, ld, n, row, k, tpr, xs) : ff{0.0f, 0.0f}, tpr);
+}
+__device__ __forceinline__ float f_row(const float *Ah, int ld, int n, int row, int k, int tpr, bool act,
+                                       const float *ws) {
+    return f_group_sum(act ? f_row_part(Ah, ld, n, row, k, tpr, ws) : 0.0f, tpr);
+}
+
+// Threads per row of the reduced problem and the shared-memory row stride for
+// a problem of size n1 = m + 1 (columns padded to ldr).
+__host__ __device__ __forceinline__ int eig_tpr(int n1) { return n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1); }
+__host__ __device__ __forceinline__ int eig_lds(int ldr, int tpr) { return ldr + 32 / tpr; }
 
 __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                        const double *cI, const double *bI, const double *HIIc,
-                                                       float *Rh, float *Rl, int ldr, int use_smem, double *w,
-                                                       double *thr, double *etaout) {
+                                                       float *Rh, float *Rl, int ldr, int tpr, int use_smem,
+                                                       double *w, double *thr, double *etaout) {
     extern __shared__ float sm[];
     __shared__ float s_rf[2 * 32 * 8];
     __shared__ ff s_rff[2 * 32 * 2];
@@ -630,38 +680,59 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     }
     __syncthreads();
     const float *Ah, *Al;
-    int lda;
+    int ld;
     float *vec;
     if (use_smem) {
-        float *sh = sm, *sl = sm + (size_t)n * n;
-        for (int r = warp; r < n; r += (int)(blockDim.x >> 5))
-            for (int c = lane; c < n; c += 32) {
-                sh[r * n + c] = Rh[(size_t)(r + off) * ldr + (c + off)];
-                sl[r * n + c] = Rl[(size_t)(r + off) * ldr + (c + off)];
+        // rows 0..m of R into shared memory with the row stride lds (no bank
+        // conflicts for the groups' reads); 16-byte loads, eight in flight per thread
+        const int lds = eig_lds(ldr, tpr);
+        float *sh = sm, *sl = sm + (size_t)(m + 1) * lds;
+        const float4 *gh = reinterpret_cast<const float4 *>(Rh), *gl = reinterpret_cast<const float4 *>(Rl);
+        const int q = ldr / 4, nv = (m + 1) * q;
+        for (int t0 = tid; t0 < nv; t0 += 4 * (int)blockDim.x) {
+            float4 a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * (int)blockDim.x;
+                if (t < nv) { a[u] = __ldcg(gh + t); b[u] = __ldcg(gl + t); }
             }
-        Ah = sh; Al = sl; lda = n;
-        vec = sm + 2 * (size_t)n * n;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * (int)blockDim.x;
+                if (t < nv) {
+                    const int r = t / q, c = 4 * (t - r * q);
+                    *reinterpret_cast<float4 *>(sh + r * lds + c) = a[u];
+                    *reinterpret_cast<float4 *>(sl + r * lds + c) = b[u];
+                }
+            }
+        }
+        Ah = sh + off * lds + off;
+        Al = sl + off * lds + off;
+        ld = lds;
+        vec = sm + 2 * (size_t)(m + 1) * lds;
     } else {
         Ah = Rh + (size_t)off * ldr + off;
         Al = Rl + (size_t)off * ldr + off;
-        lda = ldr;
+        ld = ldr;
         vec = sm;
     }
     float *xs = vec;                                    // float-float x (2 n floats)
     float *ws = vec + 2 * n;                            // FP32 w (n floats)
     double *zd = reinterpret_cast<double *>(vec + 4 * ((3 * n + 3) / 4));   // n doubles
 
-    // 2. start: x = [nu; c_I] / |.|
-    const bool act = tid < n;
+    // 2. start: x = [nu; c_I] / |.|; one row per group of tpr threads, the
+    //    group's first lane (lead) speaks for the row in sums
+    const int row = tid / tpr, kk = tid - row * tpr;
+    const bool act = row < n, lead = act && kk == 0;
     const double zz0 = (deg ? 0.0 : nu * nu) + s_sc[3];
     const double inv0 = zz0 > 0.0 ? 1.0 / sqrt(zz0) : 0.0;
     ff x = {0.0f, 0.0f};
     if (act) {
-        const double v0 = (tid < k0) ? nu : cI[tid - k0];
-        x = ff_from_double(zz0 > 0.0 ? v0 * inv0 : (tid == 0 ? 1.0 : 0.0));
+        const double v0 = (row < k0) ? nu : cI[row - k0];
+        x = ff_from_double(zz0 > 0.0 ? v0 * inv0 : (row == 0 ? 1.0 : 0.0));
     }
     __syncthreads();                                    // the copy of A is complete
-    const float d = act ? Ah[(size_t)tid * lda + tid] : 0.0f;
+    const float d = act ? Ah[row * ld + row] : 0.0f;
     float pv = 0.0f, apv = 0.0f;                        // search direction p and A p
     bool have_p = false;
     ff theta = {0.0f, 0.0f}, xx = {1.0f, 0.0f};
@@ -669,18 +740,18 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     int stall = 0, it = 0;
     float drms;                                         // RMS of diag A, a scale for the tests below
     {
-        float t[1] = {d * d};
+        float t[1] = {lead ? d * d : 0.0f};
         bsum_f<1>(t, s_rf, hf);
         drms = sqrtf(t[0] / (float)n);
     }
     for (;; ++it) {
         // (a) A x in float-float
-        if (act) { xs[2 * tid] = x.hi; xs[2 * tid + 1] = x.lo; }
+        if (lead) { xs[2 * row] = x.hi; xs[2 * row + 1] = x.lo; }
         __syncthreads();
-        const ff ax = act ? ff_row(Ah, Al, lda, n, tid, xs) : ff{0.0f, 0.0f};
+        const ff ax = ff_row(Ah, Al, ld, n, row, kk, tpr, act, xs);
         // (b) theta = x.Ax / x.x, r = A x - theta x
         {
-            ff t[2] = {ff_mul(x, ax), ff_mul(x, x)};
+            ff t[2] = {lead ? ff_mul(x, ax) : ff{0.0f, 0.0f}, lead ? ff_mul(x, x) : ff{0.0f, 0.0f}};
             bsum_ff<2>(t, s_rff, hff);
             xx = t[1];
             theta = ff_div(t[0], t[1]);
@@ -694,7 +765,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         const float den = fmaxf(fabsf(d - th), 1e-4f * fmaxf(scale, 1e-30f));
         float wv = act ? r / den : 0.0f;
         const float xh = x.hi;
-        float red[3] = {r * r, xh * wv, xh * pv};
+        float red[3] = {lead ? r * r : 0.0f, lead ? xh * wv : 0.0f, lead ? xh * pv : 0.0f};
         bsum_f<3>(red, s_rf, hf);
         const float rr = red[0];
         const float tol = 1e-14f * scale;
@@ -710,11 +781,14 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             apv -= red[2] * ixx * ff_to_float(ax);
         }
         // (d) A w
-        if (act) ws[tid] = wv;
+        if (lead) ws[row] = wv;
         __syncthreads();
-        const float awv = act ? f_row(Ah, lda, n, tid, ws) : 0.0f;
+        const float awv = f_row(Ah, ld, n, row, kk, tpr, act, ws);
         // (e) projections on span{x, w, p}
         float pr[8] = {r * wv, r * pv, wv * awv, wv * apv, pv * apv, wv * wv, wv * pv, pv * pv};
+        if (!lead)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) pr[q] = 0.0f;
         bsum_f<8>(pr, s_rf, hf);
         const float rw = pr[0], rp = pr[1], waw = pr[2], wap = pr[3], pap = pr[4], ww = pr[5], wp = pr[6], pp = pr[7];
         // (f) Rayleigh-Ritz with the pencil shifted by theta, in the basis
@@ -738,9 +812,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
                 // L^-1 [rw rp]^T and L^-1 H' L^-T for L = [l11 0; l21 l22]
                 const float a1 = (rp * ix - l21 * a0) * il22;
                 const float hwp = ((wap - th * wp) * il11 - l21 * hww) * il22;
-                const float hpp0 = (pap - th * pp);
-                // hpp = (hpp0 - 2 l21 (wap - th wp) / l11 + l21^2 hww) / l22^2
-                const float hpp = (hpp0 - 2.0f * l21 * (wap - th * wp) * il11 + l21 * l21 * hww) * il22 * il22;
+                const float hpp = ((pap - th * pp) - 2.0f * l21 * (wap - th * wp) * il11 + l21 * l21 * hww) * il22 * il22;
                 float lam, v0, v1, v2;
                 sym3_lowest(0.0f, a0, a1, hww, hwp, hpp, lam, v0, v1, v2);
                 if (v0 < 0.0f) { v0 = -v0; v1 = -v1; v2 = -v2; }
@@ -777,8 +849,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         return;
     }
     const double zs = sqrt(-lamd / ff_to_double(xx));
-    const double zi = act ? ff_to_double(x) * zs : 0.0;
-    if (act) zd[tid] = zi;
+    if (lead) zd[row] = ff_to_double(x) * zs;
     __syncthreads();
     // sign (Eq. def-z wants gamma >= 0): z_0 >= 0; degenerate or z_0 = 0: z . [nu; c_I] >= 0
     if (warp == 0) {
@@ -798,7 +869,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     const bool bad = !isfinite(gamma) || !(gamma > 1e-200);
     const dd s_new = dd_mul_d(ms->scale, gamma);
     const double rsc = 1.0 / s_new.hi;
-    // 4. eta (Eq. def-z), the new stored c_I, the scatter weights
+    // 4. eta (Eq. def-z), the new stored c_I, the scatter weights (thread i: coordinate i)
     double eta = 0.0;
     int nz_from = 0, nz_to = 0;
     if (tid < m) {
@@ -814,15 +885,15 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     }
     // eta in the active indexing (float-float) for eta^T H_II eta
     __syncthreads();                                    // zd reads are done
-    if (act) {
-        const ff e = (tid >= k0) ? ff_from_double(sgn * zd[tid] - gamma * cI[tid - k0]) : ff{0.0f, 0.0f};
-        xs[2 * tid] = e.hi;
-        xs[2 * tid + 1] = e.lo;
+    if (lead) {
+        const ff e = (row >= k0) ? ff_from_double(sgn * zd[row] - gamma * cI[row - k0]) : ff{0.0f, 0.0f};
+        xs[2 * row] = e.hi;
+        xs[2 * row + 1] = e.lo;
     }
     __syncthreads();
     {
-        const ff he = act ? ff_row(Ah, Al, lda, n, tid, xs) : ff{0.0f, 0.0f};
-        ff t[1] = {act ? ff_mul(ff{xs[2 * tid], xs[2 * tid + 1]}, he) : ff{0.0f, 0.0f}};
+        const ff he = ff_row(Ah, Al, ld, n, row, kk, tpr, act, xs);
+        ff t[1] = {lead ? ff_mul(ff{xs[2 * row], xs[2 * row + 1]}, he) : ff{0.0f, 0.0f}};
         bsum_ff<1>(t, s_rff, hff);
         if (tid == 0) s_sc[2] = ff_to_double(t[0]);
     }
@@ -878,16 +949,67 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         }
     }
 }
+
 // ---------------------------------------------------------------------------
 // b += H_{:,I} eta for the m columns (stored units), gather, candidates.
 // A group of TPC threads handles one (column, chunk) work item.
 // ---------------------------------------------------------------------------
+constexpr int kScatterBuf = 4096;   // new candidates of one block pass (groups x chunk elements)
+
+// Probe for {a, b}: the key and the value halves of the slot are read by two
+// independent 16-byte loads.  A new key is inserted with the candidate mark
+// already set (its inserter is the one that appends it).  Returns the slot,
+// or -1 (absent, not inserted) / -2 (error, status set).  c: the slot's
+// stored c; marked: the slot carried the mark when it was read.
+__device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, unsigned long long a,
+                                              unsigned long long b, bool insert, bool &inserted, double &c,
+                                              bool &marked) {
+    unsigned long long pos = key_hash(a, b) & P.mask;
+    const bool both_nonzero = (P.na > 0) && (P.nb > 0);
+    for (int probe = 0; probe < P.max_probe; ++probe) {
+        Slot *s = P.table + pos;
+        ulonglong2 k = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(&s->c));
+        int spins = 0;
+        while (both_nonzero && ((k.x == 0ull) != (k.y == 0ull))) {     // an insert in flight
+            if (++spins > (1 << 20)) { set_status(st, kErrTimeout); return -2; }
+            k = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
+        }
+        if (k.x == a && (k.y & kKeyMaskB) == b) {
+            c = v.x;
+            marked = (k.y & kMarkB) != 0ull;
+            return (long long)pos;
+        }
+        if (k.x == 0ull && k.y == 0ull) {
+            if (!insert) return -1;
+            unsigned long long oa, ob;
+            cas128(&s->a, 0ull, 0ull, a, b | kMarkB, oa, ob);
+            if (oa == 0ull && ob == 0ull) {
+                inserted = true;
+                c = 0.0;
+                marked = false;                          // marked by this thread
+                return (long long)pos;
+            }
+            if (oa == a && (ob & kKeyMaskB) == b) {      // lost to an insert of the same key
+                c = __ldcg(&s->c);
+                marked = true;
+                return (long long)pos;
+            }
+        }
+        pos = (pos + 1) & P.mask;
+    }
+    set_status(st, kErrTableFull);
+    return -2;
+}
+
 __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                     const double *w, const double *thr, long long *cand,
                                                     double *gathp, int tpc, int nchunk, int chunk) {
     __shared__ ColLists Lg[8];
     __shared__ double sred[256];
-    __shared__ long long scnt[4];
+    __shared__ long long s_cand[kScatterBuf];
+    __shared__ int s_ncand, s_base;
+    __shared__ unsigned long long scnt[4];
     const int tid = threadIdx.x, lane = tid & 31;
     if (ms->done || st->status) return;
     const int gpb = 256 / tpc;                          // groups per block
@@ -896,7 +1018,6 @@ __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, Iter
     const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
     const long long items = (long long)m * nchunk;
     if (tid < 4) scnt[tid] = 0;
-    __syncthreads();
     long long c_el = 0, c_app = 0, c_drop = 0, c_ins = 0;
     for (long long base = (long long)blockIdx.x * gpb; base < items; base += (long long)gridDim.x * gpb) {
         const long long item = base + grp;
@@ -911,6 +1032,7 @@ __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, Iter
                 if ((xs.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
                 if ((xs.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
             }
+        if (tid == 0) s_ncand = 0;
         __syncthreads();
         double gather = 0.0;
         if (act) {
@@ -923,28 +1045,27 @@ __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, Iter
                 if (is_zero(H)) continue;
                 ++c_el;
                 const bool big = fabs(H) >= ti;
-                bool ins = false;
-                const long long s = table_find(P, st, oa, ob, big, &ins);
+                bool ins = false, marked = false;
+                double cj = 0.0;
+                const long long s = mc_probe(P, st, oa, ob, big, ins, cj, marked);
                 if (s == -2) break;
                 if (s < 0) { ++c_drop; continue; }
-                Slot *sj = P.table + s;
-                const double cj = __ldcg(&sj->c);
                 if (!(!is_zero(cj) || big)) { ++c_drop; continue; }
+                Slot *sj = P.table + s;
                 atomicAdd(&sj->bv, wi * H);
                 ++c_app;
                 c_ins += ins ? 1 : 0;
                 gather = fma(H, cj, gather);
-                // candidate mark: the first thread to mark a slot appends it
-                bool first = false;
-                const unsigned long long kb = __ldcg(&sj->b);
-                if (!(kb & kMarkB)) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
+                // the thread that marks a slot appends it
+                bool first = ins;
+                if (!ins && !marked) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
                 const unsigned int fm = __ballot_sync(__activemask(), first);
                 if (first) {
                     const int leader = __ffs(fm) - 1;
-                    int basepos = 0;
-                    if (lane == leader) basepos = atomicAdd(&ms->n_cand, __popc(fm));
-                    basepos = __shfl_sync(fm, basepos, leader);
-                    cand[basepos + __popc(fm & ((1u << lane) - 1u))] = s;
+                    int pos = 0;
+                    if (lane == leader) pos = atomicAdd(&s_ncand, __popc(fm));
+                    pos = __shfl_sync(fm, pos, leader);
+                    s_cand[pos + __popc(fm & ((1u << lane) - 1u))] = s;
                 }
             }
         }
@@ -956,6 +1077,10 @@ __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, Iter
             for (int q = 0; q < tpc; ++q) t += sred[grp * tpc + q];
             gathp[(size_t)col * nchunk + ck] = t;
         }
+        // this pass's new candidates: one reservation per block
+        if (tid == 0) s_base = s_ncand > 0 ? atomicAdd(&ms->n_cand, s_ncand) : 0;
+        __syncthreads();
+        for (int i = tid; i < s_ncand; i += 256) cand[s_base + i] = s_cand[i];
         __syncthreads();
     }
     atomicAdd((unsigned long long *)&scnt[0], (unsigned long long)c_el);
@@ -1072,19 +1197,19 @@ __global__ void k_mc_init(Problem P, McState *ms, IterState *st, McSel *sel, dou
 // host wrappers
 // ---------------------------------------------------------------------------
 size_t mc_eigen_smem(int m) {
-    const size_t n = (size_t)m + 1;
-    const size_t vec = 4 * ((3 * n + 3) / 4) + 2 * n;           // x (float-float), w, eta (FP64)
-    return ((n <= (size_t)kEigSmemN ? 2 * n * n : 0) + vec) * sizeof(float);
+    const int n1 = m + 1, ldr = 32 * ((n1 + 31) / 32);
+    const size_t lds = (size_t)eig_lds(ldr, eig_tpr(n1));
+    const size_t vec = 4 * ((3 * (size_t)n1 + 3) / 4) + 2 * (size_t)n1;   // x (float-float), w, eta (FP64)
+    return ((n1 <= kEigSmemN ? 2 * (size_t)n1 * lds : 0) + vec) * sizeof(float);
 }
-int mc_eigen_threads(int m) { return 32 * ((m + 1 + 31) / 32); }
+int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
 int mc_max_m() { return kEigMaxN - 1; }
 
 cudaError_t mc_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)mc_eigen_smem(kEigSmemN - 1));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_mc_sortsel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(kInBin * sizeof(McSel)));
+    return cudaSuccess;
 }
 
 cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
@@ -1104,10 +1229,11 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
     k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.hist, b.m);
     for (int level = 1; level < kSelLevels; ++level) k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, level);
     k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
-    k_mc_sortsel<<<1, 1024, kInBin * sizeof(McSel), s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
+    k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
     k_mc_prepare<<<(b.m + 7) / 8, 256, 0, s>>>(P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr);
     k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Rh,
-                                                                    b.Rl, b.ldr, b.m + 1 <= kEigSmemN ? 1 : 0,
+                                                                    b.Rl, b.ldr, eig_tpr(b.m + 1),
+                                                                    b.m + 1 <= kEigSmemN ? 1 : 0,
                                                                     b.w, b.thr, b.eta);
     return launch_mc_scatter_finalize(P, b, s);
 }

@@ -46,6 +46,12 @@ cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long l
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s);
 
+// reduced density matrices and the energy's derivatives (cdfci_rdm.cu)
+cudaError_t launch_rdm(const Problem &P, IterState *st, double *g1_raw, double *g2_raw, double *norm, double *g1,
+                       double *g2, cudaStream_t s);
+cudaError_t launch_gradient(int N, const double *h, const double *g, const double *G1, const double *G2, double *F,
+                            double *dh, double *dg, double *dk, cudaStream_t s);
+
 // sets the message returned by cdfci_last_error() on the calling thread
 void set_last_error_message(const char *msg);
 

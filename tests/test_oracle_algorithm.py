@@ -246,3 +246,32 @@ def test_rdm_identities_and_hellmann_feynman():
     Ep = np.linalg.eigvalsh(oracle.dense_H(5, 2, 2, w.h + eps * D, w.g))[0]
     Em = np.linalg.eigvalsh(oracle.dense_H(5, 2, 2, w.h - eps * D, w.g))[0]
     assert abs((Ep - Em) / (2 * eps) - np.sum(D * g1)) < 1e-7
+
+
+def test_orbital_gradient_matches_finite_differences_of_exact_energy():
+    """dE/dkappa from the RDMs (the rotated-integral energy of Sec. "Optimal
+    Orbital Selections") against a central difference, step 1e-5, of the
+    exact ground energy of the rotated integrals; the rotation itself is
+    pinned by the invariance of the spectrum."""
+    w = inputs.ab_initio(5, 2, 2, seed=12)
+    H, idx = _dense(w)
+    evals, evecs = np.linalg.eigh(H)
+    dets = oracle.fci_dets(5, 2, 2)
+    g1, g2 = oracle.rdm(5, dets, evecs[:, 0])
+    G = oracle.orbital_gradient(w.h, w.g, g1, g2)
+    assert np.abs(G + G.T).max() < 1e-14
+    rng = np.random.default_rng(8)
+    K = rng.normal(size=(5, 5))
+    K = K - K.T
+    # a full rotation of the orbitals leaves the spectrum of H unchanged
+    hr, gr = oracle.rotate_integrals(w.h, w.g, 0.7 * K)
+    assert np.abs(np.linalg.eigvalsh(oracle.dense_H(5, 2, 2, hr, gr)) - evals).max() < 1e-10
+    eps = 1e-5
+    Ep = np.linalg.eigvalsh(oracle.dense_H(5, 2, 2, *oracle.rotate_integrals(w.h, w.g, eps * K)))[0]
+    Em = np.linalg.eigvalsh(oracle.dense_H(5, 2, 2, *oracle.rotate_integrals(w.h, w.g, -eps * K)))[0]
+    fd = (Ep - Em) / (2 * eps)
+    assert abs(fd - 0.5 * np.sum(G * K)) < 1e-7 * max(1.0, abs(fd))
+    # a wrong transpose in F (the classic slip) breaks the same check
+    F_bad = w.h @ g1 + np.einsum("prst,rqst->pq", w.g, g2)
+    assert abs(fd - np.sum((F_bad - F_bad.T) * K)) > 1e-6 or np.allclose(F_bad, F_bad.T)
+
