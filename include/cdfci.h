@@ -172,6 +172,23 @@ int cdfci_rdm(cdfci_handle h, double *rdm1, double *rdm2);
  */
 int cdfci_gradient(cdfci_handle h, double *dE_dh, double *dE_dg, double *dE_dkappa);
 
+/*
+ * Batches: many independent m = 1 solvers (problems of different sizes:
+ * molecules, lattices) stepped together.  One persistent launch (replayed from
+ * a captured CUDA graph) runs every problem, one thread-block cluster per
+ * problem, each cluster executing Algorithm 1 on its own problem with no
+ * communication between clusters.  The batch does not own the handles, which
+ * must outlive it, have num_coordinates = 1 and the same grid_blocks (CTAs per
+ * problem), and are queued on the first handle's stream while batched.  A
+ * handle stays usable on its own: cdfci_step continues from the batch's state.
+ * stats (n entries, or NULL) receives every problem's report; the return code
+ * is the first problem's error, if any.
+ */
+typedef struct cdfci_batch *cdfci_batch_handle;
+int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_handle *out);
+int cdfci_batch_step(cdfci_batch_handle b, int64_t n_iter, cdfci_stats *stats);
+void cdfci_batch_destroy(cdfci_batch_handle b);
+
 /* Current stats without running an iteration. */
 int cdfci_get_stats(cdfci_handle h, cdfci_stats *stats);
 

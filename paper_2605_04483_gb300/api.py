@@ -71,6 +71,10 @@ def lib():
         L.cdfci_get_column.argtypes = [vp, u64p, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_export.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_rdm.argtypes = [vp, dp, dp]
+        L.cdfci_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.cdfci_batch_step.argtypes = [vp, i64, ctypes.POINTER(cdfci_stats)]
+        L.cdfci_batch_destroy.argtypes = [vp]
+        L.cdfci_batch_destroy.restype = None
         L.cdfci_gradient.argtypes = [vp, dp, dp, dp]
         L.cdfci_last_step.argtypes = [vp, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_column_noalloc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p, dp, i64,
@@ -253,3 +257,31 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many m = 1 solvers stepped in one launch (cdfci_batch_*); does not own them."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[sv.handle for sv in self.solvers])
+        out = ctypes.c_void_p()
+        _check(lib().cdfci_batch_create(arr, len(self.solvers), ctypes.byref(out)))
+        self.handle = out.value
+
+    def step(self, n: int):
+        st = (cdfci_stats * len(self.solvers))()
+        _check(lib().cdfci_batch_step(self.handle, int(n), st))
+        return [x.as_dict() for x in st]
+
+    def close(self):
+        if self.handle:
+            lib().cdfci_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -120,10 +120,17 @@ int run_iterations(cdfci_ctx *c, long long n) {
     return CDFCI_OK;
 }
 
+int stats_from_snapshot(cdfci_ctx *c, cdfci_stats *s);
+
 int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
     if (!c->block) CK(launch_cd_finalize(c->P, c->d_st, c->d_rec, c->d_part, c->grid, c->stream));
     CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return stats_from_snapshot(c, s);
+}
+
+// the host snapshot c->h_st as cdfci_stats; the sticky device status as the return code
+int stats_from_snapshot(cdfci_ctx *c, cdfci_stats *s) {
     const IterState &t = *c->h_st;
     if (s) {
         s->iterations = t.iterations;
@@ -566,6 +573,111 @@ CDFCI_API int cdfci_gradient(cdfci_handle c, double *dE_dh, double *dE_dg, doubl
     if (rc) return rc;
     if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "gradient: %s", cudaGetErrorString(e));
     return CDFCI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent m = 1 solvers
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct cdfci_batch {
+    std::vector<cdfci_ctx *> hs;
+    CdInstance *d_inst = nullptr;
+    int cluster = 1;
+    size_t smem = 0;
+    cudaStream_t stream = nullptr;
+    long long chunk = 1 << 16;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_iters = 0;
+};
+
+namespace {
+int batch_graph(cdfci_batch *b, long long k) {
+    if (b->graph && b->graph_iters == k) return CDFCI_OK;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_cd_loop_batch(b->d_inst, (int)b->hs.size(), b->cluster, b->smem, k, b->stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(CDFCI_ERR_CUDA, "capture of the batched launch failed");
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    b->graph_iters = k;
+    return CDFCI_OK;
+}
+}  // namespace
+
+extern "C" {
+
+CDFCI_API int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_handle *out) {
+    if (!out) return fail(CDFCI_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (!hs || n < 1) return fail(CDFCI_ERR_ARG, "empty batch");
+    for (int k = 0; k < n; ++k) {
+        if (!hs[k]) return fail(CDFCI_ERR_ARG, "handle %d is NULL", k);
+        if (hs[k]->block) return fail(CDFCI_ERR_ARG, "handle %d has num_coordinates > 1 (batches take m = 1 solvers)", k);
+        if (hs[k]->grid != hs[0]->grid)
+            return fail(CDFCI_ERR_ARG, "handle %d uses %d CTAs per problem, handle 0 uses %d (create all with the same grid_blocks)",
+                        k, hs[k]->grid, hs[0]->grid);
+        for (int q = 0; q < k; ++q)
+            if (hs[q] == hs[k]) return fail(CDFCI_ERR_ARG, "handle %d appears twice", k);
+    }
+    cdfci_batch *b = new (std::nothrow) cdfci_batch;
+    if (!b) return fail(CDFCI_ERR_NOMEM, "host allocation failed");
+    b->hs.assign(hs, hs + n);
+    b->cluster = hs[0]->grid;
+    b->stream = hs[0]->stream;
+    b->chunk = hs[0]->chunk;
+    std::vector<CdInstance> inst(n);
+    for (int k = 0; k < n; ++k) {
+        inst[k] = CdInstance{hs[k]->P, hs[k]->d_st, hs[k]->d_rec, hs[k]->d_part};
+        b->smem = std::max(b->smem, cd_dynamic_smem(hs[k]->P));
+    }
+    // every handle's queued work is complete before the batch touches its state
+    for (int k = 0; k < n; ++k)
+        if (cudaStreamSynchronize(hs[k]->stream) != cudaSuccess) { delete b; return fail(CDFCI_ERR_CUDA, "stream sync failed"); }
+    if (cudaMalloc(&b->d_inst, n * sizeof(CdInstance)) != cudaSuccess) { delete b; return fail(CDFCI_ERR_NOMEM, "device allocation failed"); }
+    if (cudaMemcpy(b->d_inst, inst.data(), n * sizeof(CdInstance), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(b->d_inst); delete b;
+        return fail(CDFCI_ERR_CUDA, "copy of the instance table failed");
+    }
+    *out = b;
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_batch_step(cdfci_batch_handle b, int64_t n_iter, cdfci_stats *stats) {
+    if (!b) return fail(CDFCI_ERR_ARG, "NULL batch");
+    if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
+    const int n = (int)b->hs.size();
+    long long left = n_iter;
+    while (left > 0) {
+        const long long k = std::min(left, b->chunk);
+        int rc = batch_graph(b, k);
+        if (rc) return rc;
+        CK(cudaGraphLaunch(b->graph, b->stream));
+        left -= k;
+    }
+    CK(launch_cd_finalize_batch(b->d_inst, n, b->cluster, b->stream));
+    for (int k = 0; k < n; ++k)
+        CK(cudaMemcpyAsync(b->hs[k]->h_st, b->hs[k]->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    int first = CDFCI_OK;
+    for (int k = 0; k < n; ++k) {
+        const int rc = stats_from_snapshot(b->hs[k], stats ? stats + k : nullptr);
+        if (rc && !first) first = rc;
+    }
+    return first;
+}
+
+CDFCI_API void cdfci_batch_destroy(cdfci_batch_handle b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_inst);
+    delete b;
 }
 
 CDFCI_API int cdfci_last_step(cdfci_handle c, uint64_t *keys, double *eta, int64_t cap, int64_t *m_out) {

@@ -273,6 +273,14 @@ __device__ __forceinline__ long long table_find(const Problem &P, IterState *st,
     return -2;
 }
 
+// One problem of a batch of independent m = 1 solvers stepped in one launch.
+struct CdInstance {
+    Problem P;
+    IterState *st;
+    CdRecord *rec;
+    CdPartial *part;
+};
+
 // ---------------------------------------------------------------------------
 // Column decoding.  Per column the CTA holds the occupied / virtual orbital
 // lists of both spins in shared memory.

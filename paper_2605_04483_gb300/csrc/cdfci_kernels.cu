@@ -286,8 +286,8 @@ __device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb,
 // their results reach the other warps through shared memory.  Every exit
 // decision uses data all CTAs read identically, so all CTAs reach every
 // cluster barrier.
-__global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState *st, CdRecord *rec,
-                                                           CdPartial *gpart, long long n_iter) {
+__device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart,
+                                             long long n_iter) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int G = (int)cluster.num_blocks();
@@ -576,9 +576,30 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
     }
 }
 
+__global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState *st, CdRecord *rec,
+                                                           CdPartial *gpart, long long n_iter) {
+    cd_loop_body(P, st, rec, gpart, n_iter);
+}
+
+// Many independent problems in one launch: cluster k (blocks k*G .. k*G+G-1)
+// runs the loop above on instance k, whose description it first copies into
+// shared memory.  Clusters never wait on one another.
+__global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop_batch(const CdInstance *inst, int n_inst,
+                                                                 long long n_iter) {
+    __shared__ Problem sP;
+    namespace cg = cooperative_groups;
+    const int k = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+    if (k >= n_inst) return;                           // uniform in the cluster
+    for (int t = threadIdx.x; t < (int)(sizeof(Problem) / 8); t += blockDim.x)
+        reinterpret_cast<unsigned long long *>(&sP)[t] = reinterpret_cast<const unsigned long long *>(&inst[k].P)[t];
+    __syncthreads();
+    cd_loop_body(sP, inst[k].st, inst[k].rec, inst[k].part, n_iter);
+}
+
 // After a batch of iterations: write the pending recalculated b_i of the last
 // processed coordinate and a host-visible snapshot of the counters.
-__global__ void k_cd_finalize(Problem P, IterState *st, const CdRecord *rec, const CdPartial *gpart, int G) {
+__device__ __forceinline__ void cd_finalize_body(const Problem &P, IterState *st, const CdRecord *rec,
+                                                 const CdPartial *gpart, int G) {
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     const CdRecord R = *rec;
@@ -611,6 +632,17 @@ __global__ void k_cd_finalize(Problem P, IterState *st, const CdRecord *rec, con
     st->last_b = R.b;
     st->done = R.done;
     if (st->n_slots > P.max_entries) set_status(st, kErrTableFull);
+}
+
+__global__ void k_cd_finalize(Problem P, IterState *st, const CdRecord *rec, const CdPartial *gpart, int G) {
+    cd_finalize_body(P, st, rec, gpart, G);
+}
+
+// one warp per instance
+__global__ void k_cd_finalize_batch(const CdInstance *inst, int n_inst, int G) {
+    const int k = blockIdx.x;
+    if (k >= n_inst) return;
+    cd_finalize_body(inst[k].P, inst[k].st, inst[k].rec, inst[k].part, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -835,6 +867,34 @@ cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPar
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_cd_loop, P, st, rec, part, n_iter);
+}
+
+cudaError_t launch_cd_loop_batch(const CdInstance *inst, int n_inst, int cluster, size_t smem, long long n_iter,
+                                 cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_cd_loop_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_cd_loop_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_inst * cluster));
+    cfg.blockDim = dim3(kCdThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_cd_loop_batch, inst, n_inst, n_iter);
+}
+
+cudaError_t launch_cd_finalize_batch(const CdInstance *inst, int n_inst, int cluster, cudaStream_t s) {
+    k_cd_finalize_batch<<<n_inst, 32, 0, s>>>(inst, n_inst, cluster);
+    return cudaGetLastError();
 }
 
 size_t cd_dynamic_smem(const Problem &P) {

@@ -46,6 +46,11 @@ cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long l
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s);
 
+// batches of independent m = 1 problems: one launch, one cluster per instance
+cudaError_t launch_cd_loop_batch(const CdInstance *inst, int n_inst, int cluster, size_t smem, long long n_iter,
+                                 cudaStream_t s);
+cudaError_t launch_cd_finalize_batch(const CdInstance *inst, int n_inst, int cluster, cudaStream_t s);
+
 // reduced density matrices and the energy's derivatives (cdfci_rdm.cu)
 cudaError_t launch_rdm(const Problem &P, IterState *st, double *g1_raw, double *g2_raw, double *norm, double *g1,
                        double *g2, cudaStream_t s);
