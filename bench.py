@@ -13,8 +13,10 @@ than L2, so no flush is needed between steps.
 
 Extra keys: roofline of the fused column kernel, the CPU oracle as the
 baseline, end-to-end throughput through the C-ABI from host buffers, time to
-reach a stored exact energy within 1e-6 Ha on the 8-site chain, and SM clocks
-sampled during the timed region.
+reach a stored exact energy within 1e-6 Ha on the 8-site chain, SM clocks
+sampled during the timed region, and the batched paths: mCDFCI (m = 128) on
+the same workload, the 4x4 Hubbard lattice with m = 256, 96 uneven problems
+stepped in one launch, and the RDM/derivative pass on the N = 16 workload.
 
 Multi-GPU (torchrun): every rank runs an independent replica of the same solve
 (one CDFCI trajectory does not shard without an exchange step); value = all
@@ -180,6 +182,86 @@ def run_reference_arm(args) -> None:
     print(json.dumps(line))
 
 
+def timed_block_run(api, w, m, tau, log2_capacity, warm_iters, iters, **kw) -> dict:
+    """mCDFCI (Algorithm 2) throughput: elements/s over `iters` block iterations after `warm_iters`."""
+    s = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, num_coordinates=m, z_threshold=tau,
+                   log2_capacity=log2_capacity, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]), **kw)
+    try:
+        s.step(warm_iters)
+        st0 = s.stats()
+        t0 = time.perf_counter()
+        st = s.step(iters)
+        dt = time.perf_counter() - t0
+    finally:
+        s.close()
+    el = st["elements"] - st0["elements"]
+    return {"value": el / dt, "unit": "elements/s", "us_per_iteration": dt / iters * 1e6,
+            "elements_per_iteration": el / iters, "iterations": iters, "after_warmup_iterations": warm_iters,
+            "reduced_eig_iterations_per_iteration": (st["reduced_iterations"] - st0["reduced_iterations"]) / iters,
+            "energy": st["energy"], "load": st["load"]}
+
+
+def fci_dim(N: int, na: int, nb: int) -> int:
+    import math
+    return math.comb(N, na) * math.comb(N, nb)
+
+
+def batch_c4(api, inputs, iters: int) -> dict:
+    """The uneven batch (64 ab initio + 32 Hubbard problems) stepped in one launch, one CTA each."""
+    import math
+    ws = inputs.config4_instances()
+    solvers = []
+    total_bytes = 0
+    try:
+        for w in ws:
+            dim = fci_dim(w.N, w.n_alpha, w.n_beta)
+            need = dim / 0.6
+            lc = max(10, min(24, math.ceil(math.log2(need))))
+            tau = 0.0 if need <= 2 ** 24 else 1e-5
+            total_bytes += (1 << lc) * 32
+            solvers.append(api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, log2_capacity=lc, z_threshold=tau,
+                                      grid_blocks=1, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1])))
+        b = api.Batch(solvers)
+        try:
+            b.step(20)
+            st0 = [s.stats() for s in solvers]
+            t0 = time.perf_counter()
+            st = b.step(iters)
+            dt = time.perf_counter() - t0
+        finally:
+            b.close()
+        el = sum(x["elements"] - y["elements"] for x, y in zip(st, st0))
+        return {"value": el / dt, "unit": "elements/s", "problems": len(ws), "iterations_each": iters,
+                "ms_per_batch_step": dt * 1e3, "gpu_launches_timed": 2, "cluster_ctas_per_problem": 1,
+                "tables_gib": total_bytes / 2 ** 30,
+                "column_lengths": [min(x["last_column"] for x in st), max(x["last_column"] for x in st)]}
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def adjoint_c5(api, inputs, m: int, iters: int) -> dict:
+    """RDMs and dE/dh, dE/dg, dE/dkappa of a config-5 mCDFCI vector (after `iters` iterations)."""
+    w = inputs.config5()
+    s = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, num_coordinates=m, log2_capacity=25,
+                   ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]))
+    try:
+        t0 = time.perf_counter()
+        st = s.step(iters)
+        t_solve = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        dh, dg, dk = s.gradient()
+        t_grad = time.perf_counter() - t0
+        nnz = st["nnz_c"]
+    finally:
+        s.close()
+    return {"workload": "abinitio_N16_5a5b_seed5 (FCI dim 19,079,424, column 4,236), m=%d" % m,
+            "solve_iterations": iters, "solve_seconds": t_solve, "energy": st["energy"],
+            "nonzeros_c": nnz, "gradient_seconds": t_grad,
+            "rdm_lookups_per_s": nnz * 4236 / t_grad, "dE_dkappa_norm": float((dk ** 2).sum() ** 0.5),
+            "trace_dE_dh": float(dh.trace())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,6 +413,17 @@ def main():
         s3.close()
         line["time_to_E"] = {"workload": "hubbard_chain8_obc_U4 (FCI dim 4,900), m=1", "threshold_ha": 1e-6,
                              "seconds": reached, "iterations": it, "check_every": 1000, "E_ref": E_ref}
+        # ---- batched coordinate updates (mCDFCI, Algorithm 2) on the same workload ------------
+        line["mcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=128, 2^27-slot table",
+                              **timed_block_run(api, w, 128, WORKLOAD["tau"], 27, 200, 200))
+        # ---- 2D Hubbard 4x4 periodic, U=8, 8+8 (FCI dim 165,636,900), m=256, 2^28 slots ------------
+        line["hubbard_4x4"] = dict(workload="hubbard_4x4_pbc_U8 (dim 1.66e8, column <= 65), m=256, 2^28-slot table",
+                                   **timed_block_run(api, inputs.config3(8.0), 256, 0.0, 28, 100, 200))
+        # ---- uneven batch of 96 problems in one launch --------------------------------------
+        line["batch_96"] = dict(workload="64 ab initio (N 12..32, 3..8 electrons per spin) + 32 Hubbard problems, m=1",
+                                **batch_c4(api, inputs, 200))
+        # ---- adjoint: RDMs and energy derivatives ----------------------------------------------
+        line["adjoint"] = adjoint_c5(api, inputs, 128, 300)
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line))

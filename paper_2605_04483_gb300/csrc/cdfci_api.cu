@@ -183,7 +183,7 @@ int setup_block(cdfci_ctx *c, int m) {
     const size_t n1 = (size_t)m + 1;
     b.ldr = (int)(32 * ((n1 + 31) / 32));
     if (mb_alloc(c, &b.ms, 1) || mb_alloc(c, &b.cand, (size_t)cap_cand) || mb_alloc(c, &b.gkey, (size_t)cap_cand) ||
-        mb_alloc(c, &b.hist, 4096 + 1) || mb_alloc(c, &b.sel, (size_t)m) || mb_alloc(c, &b.inbin, 4096) ||
+        mb_alloc(c, &b.hist, 4096 + 1) || mb_alloc(c, &b.sel, (size_t)m) || mb_alloc(c, &b.inbin, 4096) || mb_alloc(c, &b.ties, (size_t)cap_cand) ||
         mb_alloc(c, &b.cI, (size_t)m) || mb_alloc(c, &b.bI, (size_t)m) || mb_alloc(c, &b.Hdiag, (size_t)m) ||
         mb_alloc(c, &b.HIIc, (size_t)m) || mb_alloc(c, &b.Rh, n1 * (size_t)b.ldr) ||
         mb_alloc(c, &b.Rl, n1 * (size_t)b.ldr) ||

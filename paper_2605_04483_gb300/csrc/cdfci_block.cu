@@ -438,6 +438,85 @@ __global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, cons
     }
 }
 
+// Exact ties beyond the in-bin capacity: when every 64 bits of the choice key
+// are fixed and more than kInBin candidates carry that key, the sel_need
+// smallest determinant keys among them are chosen (ties go to the smaller key)
+// by a radix selection on the 128-bit key (B, A), 8 bits per pass from the
+// top, in one CTA over a compacted copy of the tied candidates.  The chosen
+// ones replace the in-bin buffer.  Symmetric lattices produce such groups.
+__global__ void __launch_bounds__(1024) k_mc_ties(Problem P, McState *ms, const long long *cand,
+                                                   const unsigned long long *gkey, McSel *ties, McSel *inbin) {
+    __shared__ unsigned int hist[256];
+    __shared__ int s_n, s_out, s_digit;
+    __shared__ unsigned int s_below;
+    if (ms->done || ms->sel_level < kSelLevels || ms->n_inbin <= kInBin) return;
+    const int n = ms->n_cand, tid = threadIdx.x;
+    const unsigned long long g = ms->sel_prefix;
+    int need = ms->sel_need;
+    if (tid == 0) { s_n = 0; s_out = 0; }
+    __syncthreads();
+    for (int t = tid; t < n; t += blockDim.x) {
+        if (gkey[t] != g) continue;
+        const Slot sl = P.table[cand[t]];
+        ties[atomicAdd(&s_n, 1)] = McSel{cand[t], g, sl.a, sl.b & kKeyMaskB};
+    }
+    __syncthreads();
+    const int nt = s_n;
+    // digit q of the key: bits [120 - 8q, 128 - 8q) of (B << 64) | A
+    unsigned long long pB = 0ull, pA = 0ull;           // the fixed top digits (as bit patterns)
+    int fixed = 0;                                     // bits fixed so far
+    for (int q = 0; q < 16 && need > 0; ++q) {
+        for (int d = tid; d < 256; d += blockDim.x) hist[d] = 0u;
+        __syncthreads();
+        for (int t = tid; t < nt; t += blockDim.x) {
+            const McSel x = ties[t];
+            const bool on = fixed == 0 ||
+                            (fixed <= 64 ? (x.B >> (64 - fixed)) == (pB >> (64 - fixed))
+                                         : (x.B == pB && (x.A >> (128 - fixed)) == (pA >> (128 - fixed))));
+            if (!on) continue;
+            const unsigned int dg = q < 8 ? (unsigned int)((x.B >> (56 - 8 * q)) & 0xffu)
+                                          : (unsigned int)((x.A >> (56 - 8 * (q - 8))) & 0xffu);
+            atomicAdd(&hist[dg], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned int acc = 0;
+            int d = 0;
+            for (; d < 256; ++d) {
+                if (acc + hist[d] >= (unsigned int)need) break;
+                acc += hist[d];
+            }
+            s_digit = d;
+            s_below = acc;
+        }
+        __syncthreads();
+        const int dsel = s_digit;
+        // every key on the prefix with a smaller digit is chosen
+        for (int t = tid; t < nt; t += blockDim.x) {
+            const McSel x = ties[t];
+            const bool on = fixed == 0 ||
+                            (fixed <= 64 ? (x.B >> (64 - fixed)) == (pB >> (64 - fixed))
+                                         : (x.B == pB && (x.A >> (128 - fixed)) == (pA >> (128 - fixed))));
+            if (!on) continue;
+            const int dg = q < 8 ? (int)((x.B >> (56 - 8 * q)) & 0xffu) : (int)((x.A >> (56 - 8 * (q - 8))) & 0xffu);
+            if (dg < dsel) inbin[atomicAdd(&s_out, 1)] = x;
+        }
+        need -= (int)s_below;
+        if (q < 8) pB |= (unsigned long long)dsel << (56 - 8 * q);
+        else pA |= (unsigned long long)dsel << (56 - 8 * (q - 8));
+        fixed += 8;
+        __syncthreads();
+    }
+    // keys are unique, so after the last digit exactly `need` (0 or 1) entries match the full key
+    if (need > 0)
+        for (int t = tid; t < nt; t += blockDim.x) {
+            const McSel x = ties[t];
+            if (x.B == pB && x.A == pA) inbin[atomicAdd(&s_out, 1)] = x;
+        }
+    __syncthreads();
+    if (tid == 0) ms->n_inbin = s_out;                 // = sel_need
+}
+
 // Bitonic sort, in shared memory, of (choice key, index) pairs into the choice
 // order: |g| descending, then the determinant key ascending (looked up in src
 // for exact ties only).  Padding entries (index -1) sort last.
@@ -1229,6 +1308,7 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
     k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.hist, b.m);
     for (int level = 1; level < kSelLevels; ++level) k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, level);
     k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
+    k_mc_ties<<<1, 1024, 0, s>>>(P, b.ms, b.cand, b.gkey, b.ties, b.inbin);
     k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
     k_mc_prepare<<<(b.m + 7) / 8, 256, 0, s>>>(P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr);
     k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Rh,

@@ -32,7 +32,7 @@ struct McBuffers {
     long long *cand;               // candidate slots (deduplicated)
     unsigned long long *gkey;      // their choice keys
     unsigned int *hist;            // 4096-bin radix histogram, then the last-block counter
-    McSel *sel, *inbin;
+    McSel *sel, *inbin, *ties;     // chosen set, threshold-digit candidates, exact-tie scratch
     double *cI, *bI, *Hdiag, *HIIc, *w, *thr, *eta, *gathp;
     float *Rh, *Rl;                // reduced matrix R as float-float pairs, leading dimension ldr
     int ldr;
