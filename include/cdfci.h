@@ -12,7 +12,7 @@
  * A determinant is a key of two 64-bit words {A, B}: bit p of A means spatial
  * orbital p holds an alpha electron, bit p of B a beta electron.  Signs use
  * the Jordan-Wigner order in which every alpha spin-orbital precedes every
- * beta one.  N <= 63 (bit 63 is reserved by the table).
+ * beta one.  N <= 63 (bit 63 of the beta word marks candidates in the table).
  *
  * Conventions for every call:
  *   - Return value 0 = success, a negative CDFCI_ERR_* code otherwise; the
@@ -53,7 +53,7 @@ typedef struct cdfci_ctx *cdfci_handle;
  * "Solvers for Ground and Excited States" for the stopping rule).
  */
 typedef struct {
-    int32_t  num_coordinates;  /* m: 1 = CDFCI (Alg. 1), >1 = mCDFCI (Alg. 2, m <= 1024) */
+    int32_t  num_coordinates;  /* m: 1 = CDFCI (Alg. 1), 2..1023 = mCDFCI (Alg. 2) */
     int32_t  log2_capacity;    /* hash table holds 2^log2_capacity slots of 32 bytes */
     double   z_threshold;      /* tau of the compression rule (Sec. CDFCI); 0 = none */
     double   max_load;         /* stored determinants <= max_load * capacity (default 0.79) */
@@ -61,10 +61,15 @@ typedef struct {
     double   dx_threshold;     /* stop once d < this (0 = run the requested iterations) */
     uint64_t ref_alpha;        /* start determinant {A, B}; both 0 = aufbau on h_pp */
     uint64_t ref_beta;
-    int32_t  block_threads;    /* threads per CTA of the column kernel (0 = default 256) */
-    int32_t  grid_blocks;      /* CTAs of the column kernel (0 = sized from the column length) */
-    int32_t  graph_chunk;      /* iterations per captured CUDA graph (0 = default 64) */
-    int32_t  deterministic;    /* 1 = fixed-order reductions everywhere (default 1) */
+    int32_t  block_threads;    /* reserved (the kernels' block sizes are fixed); ignored */
+    int32_t  grid_blocks;      /* m = 1: CTAs of the thread-block cluster that runs the loop (0 = sized
+                                  from the column length; at most 16, a power of two that can be
+                                  resident); m > 1: ignored */
+    int32_t  graph_chunk;      /* m = 1: iterations per persistent launch (0 = 65536);
+                                  m > 1: iterations per captured CUDA graph (0 = 8) */
+    int32_t  deterministic;    /* reserved.  m = 1 is deterministic (fixed-order reductions, one update
+                                  per b_j per iteration); m > 1 adds several columns' contributions to
+                                  one b_j with FP64 atomics, whose order (last-bit rounding) can vary */
     void    *cuda_stream;      /* cudaStream_t the work is queued on; NULL = a library stream */
 } cdfci_params;
 
