@@ -45,6 +45,7 @@ extern "C" {
 #define CDFCI_ERR_NOMEM         -7   /* host or device allocation failed */
 #define CDFCI_ERR_CAPACITY      -8   /* caller's output buffer too small (required size returned) */
 #define CDFCI_ERR_NOT_NEGATIVE  -9   /* reduced problem has no negative eigenvalue (needs E0 < 0) */
+#define CDFCI_ERR_INTERNAL     -10   /* a device-side consistency check failed (the access was skipped) */
 
 typedef struct cdfci_ctx *cdfci_handle;
 

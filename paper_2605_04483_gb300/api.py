@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libcdfci.so")
 
 CDFCI_OK = 0
 ERRORS = {-1: "ARG", -2: "NONFINITE", -3: "TABLE_FULL", -4: "TIMEOUT", -5: "CUDA", -6: "UNIMPLEMENTED",
-          -7: "NOMEM", -8: "CAPACITY", -9: "NOT_NEGATIVE"}
+          -7: "NOMEM", -8: "CAPACITY", -9: "NOT_NEGATIVE", -10: "INTERNAL"}
 
 
 class cdfci_params(ctypes.Structure):

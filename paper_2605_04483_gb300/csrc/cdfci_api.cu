@@ -154,6 +154,7 @@ int stats_from_snapshot(cdfci_ctx *c, cdfci_stats *s) {
         const char *what = t.status == CDFCI_ERR_TABLE_FULL ? "hash table full (raise log2_capacity or z_threshold)"
                            : t.status == CDFCI_ERR_NONFINITE ? "non-finite value in an update"
                            : t.status == CDFCI_ERR_TIMEOUT   ? "bounded device wait expired"
+                           : t.status == CDFCI_ERR_INTERNAL  ? "device consistency check failed"
                                                              : "device error";
         return fail(t.status, "%s", what);
     }

@@ -346,7 +346,7 @@ __device__ void sel_scan(McState *ms, unsigned int *hist, unsigned int *counter,
 }
 
 // choice keys of the candidates, clearing their marks; level-0 histogram
-__global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, const long long *cand,
+__global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterState *st, const long long *cand,
                                                   unsigned long long *gkey, unsigned int *hist, int m) {
     __shared__ unsigned int sh[kSelBins];
     if (ms->done) return;
@@ -360,7 +360,10 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, const 
         const int t = base + threadIdx.x;
         const bool ok = t < n;
         unsigned long long k = 0ull;
-        if (ok) {
+        if (ok && (unsigned long long)cand[t] >= (unsigned long long)P.capacity) {
+            set_status(st, kErrInternal);                  // a candidate outside the table: skip it
+            gkey[t] = 0ull;
+        } else if (ok) {
             Slot *s = P.table + cand[t];
             const ulonglong2 key = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
             const double2 v = __ldcg(reinterpret_cast<const double2 *>(&s->c));
@@ -1144,7 +1147,9 @@ __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, Iter
                     int pos = 0;
                     if (lane == leader) pos = atomicAdd(&s_ncand, __popc(fm));
                     pos = __shfl_sync(fm, pos, leader);
-                    s_cand[pos + __popc(fm & ((1u << lane) - 1u))] = s;
+                    const int at = pos + __popc(fm & ((1u << lane) - 1u));
+                    if (at < kScatterBuf) s_cand[at] = s;
+                    else set_status(st, kErrInternal);
                 }
             }
         }
@@ -1157,9 +1162,10 @@ __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, Iter
             gathp[(size_t)col * nchunk + ck] = t;
         }
         // this pass's new candidates: one reservation per block
-        if (tid == 0) s_base = s_ncand > 0 ? atomicAdd(&ms->n_cand, s_ncand) : 0;
+        const int nb = min(s_ncand, kScatterBuf);
+        if (tid == 0) s_base = nb > 0 ? atomicAdd(&ms->n_cand, nb) : 0;
         __syncthreads();
-        for (int i = tid; i < s_ncand; i += 256) cand[s_base + i] = s_cand[i];
+        for (int i = tid; i < nb; i += 256) cand[s_base + i] = s_cand[i];
         __syncthreads();
     }
     atomicAdd((unsigned long long *)&scnt[0], (unsigned long long)c_el);
@@ -1305,7 +1311,7 @@ cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cud
 }
 
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s) {
-    k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.hist, b.m);
+    k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.st, b.cand, b.gkey, b.hist, b.m);
     for (int level = 1; level < kSelLevels; ++level) k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, level);
     k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
     k_mc_ties<<<1, 1024, 0, s>>>(P, b.ms, b.cand, b.gkey, b.ties, b.inbin);

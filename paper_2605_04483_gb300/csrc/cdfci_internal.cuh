@@ -26,7 +26,7 @@ constexpr int kStatusOk = 0;
 
 // error codes mirror include/cdfci.h
 constexpr int kErrArg = -1, kErrNonfinite = -2, kErrTableFull = -3, kErrTimeout = -4,
-              kErrNotNegative = -9;
+              kErrNotNegative = -9, kErrInternal = -10;
 
 struct __align__(32) Slot {
     unsigned long long a, b;
