@@ -262,6 +262,47 @@ def adjoint_c5(api, inputs, m: int, iters: int) -> dict:
             "trace_dE_dh": float(dh.trace())}
 
 
+def time_to_energy(api, w, E_ref: float, m: int, check_every: int, log2_capacity: int, cap_s: float = 30.0):
+    """Seconds from cdfci_create's return to the first check with |E - E_ref| <= 1e-6 Ha."""
+    s = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, num_coordinates=m, log2_capacity=log2_capacity,
+                   ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]))
+    try:
+        t0 = time.perf_counter()
+        it = 0
+        while time.perf_counter() - t0 < cap_s:
+            st = s.step(check_every)
+            it += check_every
+            if abs(st["energy"] - E_ref) <= 1e-6:
+                return {"seconds": time.perf_counter() - t0, "iterations": it, "check_every": check_every,
+                        "elements": st["elements"]}
+        return {"seconds": None, "iterations": it, "check_every": check_every, "note": f"not reached in {cap_s} s"}
+    finally:
+        s.close()
+
+
+def time_to_e_batched_vs_plain(api, inputs) -> list:
+    import math
+    out = []
+    cases = [("config1_hubbard_chain8_obc_U4", inputs.config1()),
+             ("abinitio_N12_3a3b_seed2", inputs.ab_initio(12, 3, 3, seed=2)),
+             ("abinitio_N10_4a4b_seed7", inputs.ab_initio(10, 4, 4, seed=7)),
+             ("hubbard_chain10_obc_U4_5a5b", inputs.hubbard((10,), 5, 5, U=4.0, periodic=False))]
+    for name, w in cases:
+        E_ref = load_reference_energy(name)
+        lc = max(12, math.ceil(math.log2(w.fci_dim / 0.6)))
+        ref = dict(ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]), log2_capacity=lc)
+        t0 = time.perf_counter()
+        tuned, rep = api.cdfci_autotune(w.h, w.g, w.N, w.n_alpha, w.n_beta, seconds=1.0, **ref)
+        t_tune = time.perf_counter() - t0
+        m = tuned["num_coordinates"]
+        plain = time_to_energy(api, w, E_ref, 1, 2000, lc)
+        batched = time_to_energy(api, w, E_ref, m, 16 if m > 1 else 2000, lc)
+        out.append({"workload": f"{name} (FCI dim {w.fci_dim:,})", "E_ref": E_ref, "threshold_ha": 1e-6,
+                    "plain_m1": plain, "batched": dict(batched, m=m, autotune_seconds=t_tune,
+                                                       autotune_seconds_to_target=dict(zip(rep["m"], rep["score"])))})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,6 +454,8 @@ def main():
         s3.close()
         line["time_to_E"] = {"workload": "hubbard_chain8_obc_U4 (FCI dim 4,900), m=1", "threshold_ha": 1e-6,
                              "seconds": reached, "iterations": it, "check_every": 1000, "E_ref": E_ref}
+        # ---- time to E within 1e-6 Ha: batched (autotuned m) vs plain (m = 1) -------------------
+        line["time_to_E_batched_vs_plain"] = time_to_e_batched_vs_plain(api, inputs)
         # ---- batched coordinate updates (mCDFCI, Algorithm 2) on the same workload ------------
         line["mcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=128, 2^27-slot table",
                               **timed_block_run(api, w, 128, WORKLOAD["tau"], 27, 200, 200))

@@ -195,6 +195,32 @@ int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_handle *out);
 int cdfci_batch_step(cdfci_batch_handle b, int64_t n_iter, cdfci_stats *stats);
 void cdfci_batch_destroy(cdfci_batch_handle b);
 
+/*
+ * Autotuner: picks the block size m (num_coordinates) that reaches a given
+ * energy soonest on this problem (a proxy for time-to-E).  Candidates m in
+ * {1, 4, 16, 64, 256} (at most the library's limit) start from the same
+ * point.  m = 1 runs for an equal share of `seconds`, and the energy it
+ * reaches is the target; each other m runs until it reaches the target or
+ * twice the share has passed.  The time spent in cdfci_step is what counts.
+ * m = 1 keeps params->grid_blocks (0 = sized from the column).
+ * On return params->num_coordinates holds the fastest; report (may be NULL)
+ * receives every candidate's m, iterations, seconds, energy drop and score
+ * (seconds to the target, -1 if not reached) and the index of the winner.
+ * Errors as for cdfci_create; a candidate whose table fills up is scored by
+ * what it reached before.
+ */
+typedef struct {
+    int32_t n;                 /* candidates tried */
+    int32_t chosen;            /* index of the winner */
+    int32_t m[8];
+    int64_t iterations[8];
+    double  seconds[8];
+    double  energy_drop[8];    /* Hartree */
+    double  score[8];          /* seconds to the target energy, -1 if not reached */
+} cdfci_tune_report;
+int cdfci_autotune(const double *h, const double *g, int N, int n_alpha, int n_beta, cdfci_params *params,
+                   double seconds, cdfci_tune_report *report);
+
 /* Current stats without running an iteration. */
 int cdfci_get_stats(cdfci_handle h, cdfci_stats *stats);
 

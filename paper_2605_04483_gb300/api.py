@@ -32,6 +32,12 @@ class cdfci_params(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p)]
 
 
+class cdfci_tune_report(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("chosen", ctypes.c_int32), ("m", ctypes.c_int32 * 8),
+                ("iterations", ctypes.c_int64 * 8), ("seconds", ctypes.c_double * 8),
+                ("energy_drop", ctypes.c_double * 8), ("score", ctypes.c_double * 8)]
+
+
 class cdfci_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("energy", ctypes.c_double), ("mu", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("dx", ctypes.c_double), ("nnz_c", ctypes.c_int64),
@@ -71,6 +77,8 @@ def lib():
         L.cdfci_get_column.argtypes = [vp, u64p, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_export.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_rdm.argtypes = [vp, dp, dp]
+        L.cdfci_autotune.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cdfci_params),
+                                     ctypes.c_double, ctypes.POINTER(cdfci_tune_report)]
         L.cdfci_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.cdfci_batch_step.argtypes = [vp, i64, ctypes.POINTER(cdfci_stats)]
         L.cdfci_batch_destroy.argtypes = [vp]
@@ -169,6 +177,21 @@ def cdfci_export(handle: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     b = np.zeros(max(cap, 1))
     _check(lib().cdfci_export(handle, _ptr(keys), _ptr(c), _ptr(b), cap, ctypes.byref(n)))
     return keys[:n.value], c[:n.value], b[:n.value]
+
+
+def cdfci_autotune(h, g, N: int, n_alpha: int, n_beta: int, seconds: float = 2.0, **params) -> Tuple[dict, dict]:
+    """Picks num_coordinates by the measured energy decrease per second; returns
+    (the tuned params as a dict, the report)."""
+    p = cdfci_default_params(**params)
+    rep = cdfci_tune_report()
+    h = np.ascontiguousarray(h, dtype=np.float64) if isinstance(h, np.ndarray) else h
+    g = np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g
+    _check(lib().cdfci_autotune(_ptr(h), _ptr(g), N, n_alpha, n_beta, ctypes.byref(p), float(seconds), ctypes.byref(rep)))
+    tuned = dict(params, num_coordinates=p.num_coordinates)
+    report = {"chosen_m": rep.m[rep.chosen], "m": list(rep.m[:rep.n]), "iterations": list(rep.iterations[:rep.n]),
+              "seconds": list(rep.seconds[:rep.n]), "energy_drop": list(rep.energy_drop[:rep.n]),
+              "score": list(rep.score[:rep.n])}
+    return tuned, report
 
 
 def cdfci_rdm(handle: int, N: int, two_body: bool = True) -> Tuple[np.ndarray, Optional[np.ndarray]]:

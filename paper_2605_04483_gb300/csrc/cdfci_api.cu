@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
 #include <new>
 #include <string>
 #include <vector>
@@ -679,6 +680,56 @@ CDFCI_API void cdfci_batch_destroy(cdfci_batch_handle b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->d_inst);
     delete b;
+}
+
+CDFCI_API int cdfci_autotune(const double *h, const double *g, int N, int n_alpha, int n_beta, cdfci_params *params,
+                             double seconds, cdfci_tune_report *report) {
+    if (!params) return fail(CDFCI_ERR_ARG, "NULL params");
+    if (!(seconds > 0.0)) return fail(CDFCI_ERR_ARG, "seconds must be > 0");
+    const int cands[] = {1, 4, 16, 64, 256};
+    std::vector<int> ms;
+    for (int m : cands)
+        if (m <= mc_max_m()) ms.push_back(m);
+    cdfci_tune_report rep;
+    memset(&rep, 0, sizeof(rep));
+    const double share = seconds / (double)ms.size();
+    double target = 0.0, best = 1e300;
+    for (size_t k = 0; k < ms.size(); ++k) {
+        cdfci_params p = *params;
+        p.num_coordinates = ms[k];
+        cdfci_handle hd = nullptr;
+        int rc = cdfci_create(h, g, N, n_alpha, n_beta, &p, &hd);
+        if (rc) return rc;
+        cdfci_stats st0, st;
+        rc = cdfci_get_stats(hd, &st0);
+        st = st0;
+        double spent = 0.0, reached = -1.0;
+        long long it = 0;
+        const int64_t chunk = ms[k] == 1 ? 256 : 4;
+        // m = 1 runs its share and sets the target energy; the others run until they reach it
+        const double limit = k == 0 ? share : 2.0 * share;
+        while (!rc && spent < limit && !st.converged) {
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = cdfci_step(hd, chunk, &st);
+            spent += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (!rc) it += chunk;
+            if (!rc && k > 0 && st.energy <= target) { reached = spent; break; }
+        }
+        if (rc == CDFCI_ERR_TABLE_FULL) rc = CDFCI_OK;  // scored by what it reached
+        cdfci_destroy(hd);
+        if (rc) return rc;
+        if (k == 0) { target = st.energy; reached = spent; }
+        rep.m[k] = ms[k];
+        rep.iterations[k] = it;
+        rep.seconds[k] = spent;
+        rep.energy_drop[k] = st0.energy - st.energy;
+        rep.score[k] = reached;                      // seconds to the target energy, -1 if not reached
+        if (reached >= 0.0 && reached < best) { best = reached; rep.chosen = (int)k; }
+    }
+    rep.n = (int)ms.size();
+    params->num_coordinates = rep.m[rep.chosen];
+    if (report) *report = rep;
+    return CDFCI_OK;
 }
 
 CDFCI_API int cdfci_last_step(cdfci_handle c, uint64_t *keys, double *eta, int64_t cap, int64_t *m_out) {

@@ -14,6 +14,8 @@ CASES = [
     ("config1_hubbard_chain8_obc_U4", inputs.config1()),
     ("abinitio_N10_3a3b_seed11", inputs.ab_initio(10, 3, 3, seed=11)),
     ("abinitio_N12_3a3b_seed2", inputs.ab_initio(12, 3, 3, seed=2)),
+    ("hubbard_chain10_obc_U4_5a5b", inputs.hubbard((10,), 5, 5, U=4.0, periodic=False)),
+    ("abinitio_N10_4a4b_seed7", inputs.ab_initio(10, 4, 4, seed=7)),
 ]
 
 if __name__ == "__main__":

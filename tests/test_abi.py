@@ -46,9 +46,12 @@ def test_struct_layouts_match_header(built, tmp_path):
 int main(void) {
   printf("cdfci_params %zu\\n", sizeof(cdfci_params));
   printf("cdfci_stats %zu\\n", sizeof(cdfci_stats));
+  printf("cdfci_tune_report %zu\\n", sizeof(cdfci_tune_report));
   F(cdfci_params, z_threshold) F(cdfci_params, ref_alpha) F(cdfci_params, block_threads)
   F(cdfci_params, deterministic) F(cdfci_params, cuda_stream)
   F(cdfci_stats, energy) F(cdfci_stats, nnz_c) F(cdfci_stats, load) F(cdfci_stats, status) F(cdfci_stats, converged) F(cdfci_stats, reduced_iterations)
+  F(cdfci_tune_report, chosen) F(cdfci_tune_report, m) F(cdfci_tune_report, iterations) F(cdfci_tune_report, seconds)
+  F(cdfci_tune_report, energy_drop) F(cdfci_tune_report, score)
   return 0;
 }
 """)
@@ -56,13 +59,14 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     vals = dict(l.split() for l in lines if l.strip())
-    P, S = built.cdfci_params, built.cdfci_stats
+    P, S, R = built.cdfci_params, built.cdfci_stats, built.cdfci_tune_report
     assert int(vals["cdfci_params"]) == ctypes.sizeof(P)
     assert int(vals["cdfci_stats"]) == ctypes.sizeof(S)
+    assert int(vals["cdfci_tune_report"]) == ctypes.sizeof(R)
     for k, v in vals.items():
         if "." in k:
             t, f = k.split(".")
-            cls = P if t == "cdfci_params" else S
+            cls = {"cdfci_params": P, "cdfci_stats": S, "cdfci_tune_report": R}[t]
             assert getattr(cls, f).offset == int(v), k
 
 

@@ -189,3 +189,13 @@ def test_block_symmetric_lattice_choices_are_valid_top_m():
         assert abs(st["energy"] - E0) < 1e-8, st["energy"] - E0
     finally:
         g.close()
+
+
+def test_autotune_report_and_choice():
+    from paper_2605_04483_gb300 import api
+    w = inputs.ab_initio(10, 3, 3, seed=11)
+    tuned, rep = api.cdfci_autotune(w.h, w.g, w.N, w.n_alpha, w.n_beta, seconds=1.0, log2_capacity=16)
+    assert rep["m"][:2] == [1, 4] and len(rep["m"]) == 5
+    reached = [(t, m) for t, m in zip(rep["score"], rep["m"]) if t >= 0]
+    assert reached and tuned["num_coordinates"] == min(reached)[1] == rep["chosen_m"]
+    assert all(x > 0 for x in rep["iterations"]) and all(d >= 0 for d in rep["energy_drop"])
