@@ -303,6 +303,19 @@ def time_to_e_batched_vs_plain(api, inputs) -> list:
     return out
 
 
+def aggregate_ranks(ms: float, elements: float, dist=None, device: str = "cpu"):
+    """Replicas: the slowest rank's time and all ranks' elements (weak scaling,
+    no data-path collective; this reduction only reports)."""
+    if dist is None:
+        return ms, elements
+    import torch
+    t = torch.tensor([ms, elements], dtype=torch.float64, device=device)
+    tmax, tsum = t.clone(), t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,15 +390,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     elements = st["elements"] - st0["elements"]
     launches = st["iterations"] - st0["iterations"]
-    if world > 1:
-        t = torch.tensor([ms, float(elements)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms_max, total_el = float(tmax[0]), float(tsum[1])
-    else:
-        ms_max, total_el = ms, float(elements)
+    ms_max, total_el = aggregate_ranks(ms, float(elements), dist if world > 1 else None, "cuda")
     value = total_el / (ms_max * 1e-3)
     final_energy = st["energy"]
     s.close()
