@@ -151,15 +151,17 @@ __device__ __forceinline__ void bsum_f(float (&v)[K], float *scr, int &half) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
         for (int off = 16; off > 0; off >>= 1) v[k] = __fadd_rn(v[k], __shfl_down_sync(0xffffffffu, v[k], off));
-    float *s = scr + half * 32 * 8;                      // fixed stride: K <= 8
+    float *s = scr + half * 32 * 16;                     // fixed stride: K <= 16
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < K; ++k) s[warp * K + k] = v[k];
     __syncthreads();
+    // every warp sums the warps' values with an xor butterfly: each step adds
+    // commutative pairs, so all lanes of all warps end with the same bits
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float t = s[k];
-        for (int w = 1; w < nw; ++w) t = __fadd_rn(t, s[w * K + k]);
+        float t = lane < nw ? s[lane * K + k] : 0.0f;
+        for (int off = 16; off > 0; off >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
         v[k] = t;
     }
     half ^= 1;
@@ -179,10 +181,13 @@ __device__ __forceinline__ void bsum_ff(ff (&v)[K], ff *scr, int &half) {
 #pragma unroll
         for (int k = 0; k < K; ++k) s[warp * K + k] = v[k];
     __syncthreads();
+    // xor butterfly over the warps' values (ff_add is commutative bit for bit:
+    // TwoSum's error term is exact), identical in every lane and warp
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        ff t = s[k];
-        for (int w = 1; w < nw; ++w) t = ff_add(t, s[w * K + k]);
+        ff t = lane < nw ? s[lane * K + k] : ff{0.0f, 0.0f};
+        for (int off = 16; off > 0; off >>= 1)
+            t = ff_add(t, ff{__shfl_xor_sync(0xffffffffu, t.hi, off), __shfl_xor_sync(0xffffffffu, t.lo, off)});
         v[k] = t;
     }
     half ^= 1;
@@ -710,7 +715,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
                                                        float *Rh, float *Rl, int ldr, int tpr, int use_smem,
                                                        double *w, double *thr, double *etaout) {
     extern __shared__ float sm[];
-    __shared__ float s_rf[2 * 32 * 8];
+    __shared__ float s_rf[2 * 32 * 16];
     __shared__ ff s_rff[2 * 32 * 2];
     __shared__ double s_sc[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
