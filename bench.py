@@ -66,6 +66,29 @@ def profiled_traffic():
         return None
 
 
+def random_sector_peak(torch, seconds: float = 0.5) -> float:
+    """GB/s of DRAM sectors moved by scattered 8-byte reads (each read costs one
+    32-byte sector) over a 4 GiB buffer: the ceiling of random hash-slot traffic,
+    measured with torch's gather kernel beside the copy peak."""
+    x = torch.empty(1 << 29, dtype=torch.float64, device="cuda")
+    x.fill_(1.0)
+    idx = torch.randint(0, 1 << 29, (1 << 24,), device="cuda")
+    for _ in range(3):
+        y = x[idx]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        y = x[idx]
+    e1.record()
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) * 1e-3 / reps
+    del x, idx, y
+    torch.cuda.empty_cache()
+    return (1 << 24) * 32 / dt / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -408,7 +431,9 @@ def main():
     el_per_launch = elements / loop_launches
     achieved = el_per_launch * ALGO_BYTES_PER_ELEMENT / avg_launch_s / 1e9
     traffic = profiled_traffic()
+    rs_peak = random_sector_peak(torch)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "random_sector_peak_gbs": rs_peak, "frac_of_random_sector_peak": achieved / rs_peak,
                 "traffic": traffic, "kernel": f"k_cd_loop (persistent 16-CTA cluster, {ips} iterations per launch)",
                 "algorithmic_bytes_per_launch": el_per_launch * ALGO_BYTES_PER_ELEMENT,
                 "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
