@@ -229,8 +229,9 @@ def fci_dim(N: int, na: int, nb: int) -> int:
     return math.comb(N, na) * math.comb(N, nb)
 
 
-def batch_c4(api, inputs, iters: int) -> dict:
-    """The uneven batch (64 ab initio + 32 Hubbard problems) stepped in one launch, one CTA each."""
+def batch_c4(api, inputs, iters: int, grid_blocks: int = 1) -> dict:
+    """The uneven batch (64 ab initio + 32 Hubbard problems) stepped in one launch, one
+    thread-block cluster of grid_blocks CTAs per problem."""
     import math
     ws = inputs.config4_instances()
     solvers = []
@@ -243,7 +244,7 @@ def batch_c4(api, inputs, iters: int) -> dict:
             tau = 0.0 if need <= 2 ** 24 else 1e-5
             total_bytes += (1 << lc) * 32
             solvers.append(api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, log2_capacity=lc, z_threshold=tau,
-                                      grid_blocks=1, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1])))
+                                      grid_blocks=grid_blocks, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1])))
         b = api.Batch(solvers)
         try:
             b.step(20)
@@ -255,7 +256,7 @@ def batch_c4(api, inputs, iters: int) -> dict:
             b.close()
         el = sum(x["elements"] - y["elements"] for x, y in zip(st, st0))
         return {"value": el / dt, "unit": "elements/s", "problems": len(ws), "iterations_each": iters,
-                "ms_per_batch_step": dt * 1e3, "gpu_launches_timed": 2, "cluster_ctas_per_problem": 1,
+                "ms_per_batch_step": dt * 1e3, "gpu_launches_timed": 2, "cluster_ctas_per_problem": grid_blocks,
                 "tables_gib": total_bytes / 2 ** 30,
                 "column_lengths": [min(x["last_column"] for x in st), max(x["last_column"] for x in st)]}
     finally:
@@ -493,8 +494,10 @@ def main():
         line["hubbard_4x4"] = dict(workload="hubbard_4x4_pbc_U8 (dim 1.66e8, column <= 65), m=256, 2^28-slot table",
                                    **timed_block_run(api, inputs.config3(8.0), 256, 0.0, 28, 100, 200))
         # ---- uneven batch of 96 problems in one launch --------------------------------------
+        sweep = {gb: batch_c4(api, inputs, 200, gb) for gb in (1, 2, 4, 8, 16)}
+        best = max(sweep, key=lambda gb: sweep[gb]["value"])
         line["batch_96"] = dict(workload="64 ab initio (N 12..32, 3..8 electrons per spin) + 32 Hubbard problems, m=1",
-                                **batch_c4(api, inputs, 200))
+                                **sweep[best], by_cluster_ctas={gb: v["value"] for gb, v in sweep.items()})
         # ---- adjoint: RDMs and energy derivatives ----------------------------------------------
         line["adjoint"] = adjoint_c5(api, inputs, 128, 300)
         if world == 1:

@@ -196,15 +196,18 @@ int cdfci_batch_step(cdfci_batch_handle b, int64_t n_iter, cdfci_stats *stats);
 void cdfci_batch_destroy(cdfci_batch_handle b);
 
 /*
- * Autotuner: picks the block size m (num_coordinates) that reaches a given
- * energy soonest on this problem (a proxy for time-to-E).  Candidates m in
- * {1, 4, 16, 64, 256} (at most the library's limit) start from the same
- * point.  m = 1 runs for an equal share of `seconds`, and the energy it
- * reaches is the target; each other m runs until it reaches the target or
- * twice the share has passed.  The time spent in cdfci_step is what counts.
- * m = 1 keeps params->grid_blocks (0 = sized from the column).
- * On return params->num_coordinates holds the fastest; report (may be NULL)
- * receives every candidate's m, iterations, seconds, energy drop and score
+ * Autotuner: picks the block size m (num_coordinates) and, for m = 1, the CTAs
+ * per column (grid_blocks, the width of the cluster that evaluates one
+ * determinant's column) that reach a given energy soonest on this problem (a
+ * proxy for time-to-E).  All candidates start from the same point.  First m =
+ * 1 with the configured grid_blocks (0 = sized from the column) runs for an
+ * equal share of `seconds`, and the energy it reaches is the target.  Then m
+ * = 1 with grid_blocks in {1, 2, 4, 8, 16} (the trajectory is the same, only
+ * the speed differs) and m in {4, 16, 64, 256} (at most the library's limit)
+ * each run until they reach the target or twice the share has passed.  The
+ * time spent in cdfci_step is what counts.  On return params->num_coordinates
+ * and params->grid_blocks hold the fastest; report (may be NULL) receives
+ * every candidate's m, grid_blocks, iterations, seconds, energy drop and score
  * (seconds to the target, -1 if not reached) and the index of the winner.
  * Errors as for cdfci_create; a candidate whose table fills up is scored by
  * what it reached before.
@@ -212,11 +215,12 @@ void cdfci_batch_destroy(cdfci_batch_handle b);
 typedef struct {
     int32_t n;                 /* candidates tried */
     int32_t chosen;            /* index of the winner */
-    int32_t m[8];
-    int64_t iterations[8];
-    double  seconds[8];
-    double  energy_drop[8];    /* Hartree */
-    double  score[8];          /* seconds to the target energy, -1 if not reached */
+    int32_t m[16];
+    int32_t grid_blocks[16];   /* CTAs per column for m = 1 (as resolved by the library); 0 for m > 1 */
+    int64_t iterations[16];
+    double  seconds[16];
+    double  energy_drop[16];   /* Hartree */
+    double  score[16];         /* seconds to the target energy, -1 if not reached */
 } cdfci_tune_report;
 int cdfci_autotune(const double *h, const double *g, int N, int n_alpha, int n_beta, cdfci_params *params,
                    double seconds, cdfci_tune_report *report);

@@ -33,9 +33,10 @@ class cdfci_params(ctypes.Structure):
 
 
 class cdfci_tune_report(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32), ("chosen", ctypes.c_int32), ("m", ctypes.c_int32 * 8),
-                ("iterations", ctypes.c_int64 * 8), ("seconds", ctypes.c_double * 8),
-                ("energy_drop", ctypes.c_double * 8), ("score", ctypes.c_double * 8)]
+    _fields_ = [("n", ctypes.c_int32), ("chosen", ctypes.c_int32), ("m", ctypes.c_int32 * 16),
+                ("grid_blocks", ctypes.c_int32 * 16), ("iterations", ctypes.c_int64 * 16),
+                ("seconds", ctypes.c_double * 16), ("energy_drop", ctypes.c_double * 16),
+                ("score", ctypes.c_double * 16)]
 
 
 class cdfci_stats(ctypes.Structure):
@@ -187,8 +188,10 @@ def cdfci_autotune(h, g, N: int, n_alpha: int, n_beta: int, seconds: float = 2.0
     h = np.ascontiguousarray(h, dtype=np.float64) if isinstance(h, np.ndarray) else h
     g = np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g
     _check(lib().cdfci_autotune(_ptr(h), _ptr(g), N, n_alpha, n_beta, ctypes.byref(p), float(seconds), ctypes.byref(rep)))
-    tuned = dict(params, num_coordinates=p.num_coordinates)
-    report = {"chosen_m": rep.m[rep.chosen], "m": list(rep.m[:rep.n]), "iterations": list(rep.iterations[:rep.n]),
+    tuned = dict(params, num_coordinates=p.num_coordinates, grid_blocks=p.grid_blocks)
+    report = {"chosen_m": rep.m[rep.chosen], "chosen_grid_blocks": rep.grid_blocks[rep.chosen],
+              "m": list(rep.m[:rep.n]), "grid_blocks": list(rep.grid_blocks[:rep.n]),
+              "iterations": list(rep.iterations[:rep.n]),
               "seconds": list(rep.seconds[:rep.n]), "energy_drop": list(rep.energy_drop[:rep.n]),
               "score": list(rep.score[:rep.n])}
     return tuned, report

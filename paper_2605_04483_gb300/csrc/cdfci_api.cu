@@ -686,27 +686,32 @@ CDFCI_API int cdfci_autotune(const double *h, const double *g, int N, int n_alph
                              double seconds, cdfci_tune_report *report) {
     if (!params) return fail(CDFCI_ERR_ARG, "NULL params");
     if (!(seconds > 0.0)) return fail(CDFCI_ERR_ARG, "seconds must be > 0");
-    const int cands[] = {1, 4, 16, 64, 256};
-    std::vector<int> ms;
-    for (int m : cands)
-        if (m <= mc_max_m()) ms.push_back(m);
+    struct Cand { int m, grid; };
+    std::vector<Cand> cs;
+    cs.push_back({1, params->grid_blocks});
+    for (int gb : {1, 2, 4, 8, 16})
+        if (gb != params->grid_blocks) cs.push_back({1, gb});
+    for (int m : {4, 16, 64, 256})
+        if (m <= mc_max_m()) cs.push_back({m, params->grid_blocks});
     cdfci_tune_report rep;
     memset(&rep, 0, sizeof(rep));
-    const double share = seconds / (double)ms.size();
+    const double share = seconds / (double)cs.size();
     double target = 0.0, best = 1e300;
-    for (size_t k = 0; k < ms.size(); ++k) {
+    for (size_t k = 0; k < cs.size() && k < 16; ++k) {
         cdfci_params p = *params;
-        p.num_coordinates = ms[k];
+        p.num_coordinates = cs[k].m;
+        p.grid_blocks = cs[k].grid;
         cdfci_handle hd = nullptr;
         int rc = cdfci_create(h, g, N, n_alpha, n_beta, &p, &hd);
         if (rc) return rc;
+        const int resolved_grid = cs[k].m == 1 ? hd->grid : 0;
         cdfci_stats st0, st;
         rc = cdfci_get_stats(hd, &st0);
         st = st0;
         double spent = 0.0, reached = -1.0;
         long long it = 0;
-        const int64_t chunk = ms[k] == 1 ? 256 : 4;
-        // m = 1 runs its share and sets the target energy; the others run until they reach it
+        const int64_t chunk = cs[k].m == 1 ? 256 : 4;
+        // the first candidate runs its share and sets the target energy; the others run until they reach it
         const double limit = k == 0 ? share : 2.0 * share;
         while (!rc && spent < limit && !st.converged) {
             const auto t0 = std::chrono::steady_clock::now();
@@ -719,15 +724,17 @@ CDFCI_API int cdfci_autotune(const double *h, const double *g, int N, int n_alph
         cdfci_destroy(hd);
         if (rc) return rc;
         if (k == 0) { target = st.energy; reached = spent; }
-        rep.m[k] = ms[k];
+        rep.m[k] = cs[k].m;
+        rep.grid_blocks[k] = resolved_grid;
         rep.iterations[k] = it;
         rep.seconds[k] = spent;
         rep.energy_drop[k] = st0.energy - st.energy;
         rep.score[k] = reached;                      // seconds to the target energy, -1 if not reached
         if (reached >= 0.0 && reached < best) { best = reached; rep.chosen = (int)k; }
+        rep.n = (int)k + 1;
     }
-    rep.n = (int)ms.size();
     params->num_coordinates = rep.m[rep.chosen];
+    if (rep.m[rep.chosen] == 1) params->grid_blocks = rep.grid_blocks[rep.chosen];
     if (report) *report = rep;
     return CDFCI_OK;
 }

@@ -195,7 +195,12 @@ def test_autotune_report_and_choice():
     from paper_2605_04483_gb300 import api
     w = inputs.ab_initio(10, 3, 3, seed=11)
     tuned, rep = api.cdfci_autotune(w.h, w.g, w.N, w.n_alpha, w.n_beta, seconds=1.0, log2_capacity=16)
-    assert rep["m"][:2] == [1, 4] and len(rep["m"]) == 5
-    reached = [(t, m) for t, m in zip(rep["score"], rep["m"]) if t >= 0]
-    assert reached and tuned["num_coordinates"] == min(reached)[1] == rep["chosen_m"]
+    assert rep["m"][0] == 1 and rep["m"][-4:] == [4, 16, 64, 256] and len(rep["m"]) >= 8
+    assert sorted(set(gb for m, gb in zip(rep["m"], rep["grid_blocks"]) if m == 1)) == [1, 2, 4, 8, 16] or \
+        len(set(gb for m, gb in zip(rep["m"], rep["grid_blocks"]) if m == 1)) >= 3
+    reached = [(t, k) for k, t in enumerate(rep["score"]) if t >= 0]
+    k = min(reached)[1]
+    assert tuned["num_coordinates"] == rep["m"][k] == rep["chosen_m"]
+    if rep["m"][k] == 1:
+        assert tuned["grid_blocks"] == rep["grid_blocks"][k]
     assert all(x > 0 for x in rep["iterations"]) and all(d >= 0 for d in rep["energy_drop"])
