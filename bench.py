@@ -352,12 +352,22 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the device-timed value (for profiling)")
     ap.add_argument("--log2-capacity", type=int, default=WORKLOAD["log2_capacity"],
                     help="hash table size (smaller only for profiling captures)")
+    ap.add_argument("--only", choices=["mcdfci"], default=None,
+                    help="run only the m = 128 block leg on the same workload (for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
     if args.impl == "reference":
         run_reference_arm(args)
+        return
+    if args.only == "mcdfci":
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2605_04483_gb300 import api, inputs
+        r = timed_block_run(api, inputs.config2(), 128, WORKLOAD["tau"], args.log2_capacity, args.warmup * 10,
+                            args.iters_per_step)
+        print(json.dumps({"mcdfci_m128": r}))
         return
 
     import numpy as np
