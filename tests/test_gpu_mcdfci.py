@@ -204,3 +204,28 @@ def test_autotune_report_and_choice():
     if rep["m"][k] == 1:
         assert tuned["grid_blocks"] == rep["grid_blocks"][k]
     assert all(x > 0 for x in rep["iterations"]) and all(d >= 0 for d in rep["energy_drop"])
+
+
+@pytest.mark.parametrize("m", [4, 16])
+def test_block_trajectory_with_compression_matches_oracle(m):
+    """tau > 0: the compression rule in the block scatter (updates of absent keys
+    below tau dropped, b_j of stored keys always updated) per iteration against
+    the oracle's Algorithm 2 with the same tau."""
+    w = inputs.ab_initio(8, 4, 3, seed=17)
+    tau = 2e-3
+    g = solver(w, m, z_threshold=tau)
+    o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, w.ref, tau, m)
+    try:
+        for it in range(25):
+            st = g.step(1)
+            o.step(1)
+            kg, eg = g.last_step()
+            ko, eo = o.last_step()
+            assert keyset(kg) == keyset(ko), f"iteration {it}: chosen blocks differ"
+            assert abs(st["energy"] - o.energy()) <= 1e-10 * max(1.0, abs(o.energy())), (it, st["energy"], o.energy())
+        info = o.info()
+        assert st["n_slots"] == info["entries"], (st["n_slots"], info["entries"])
+        assert st["dropped"] > 0
+    finally:
+        g.close()
+        o.close()
