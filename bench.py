@@ -229,6 +229,13 @@ def fci_dim(N: int, na: int, nb: int) -> int:
     return math.comb(N, na) * math.comb(N, nb)
 
 
+def loop_kernel_name(st: dict, ips: int) -> str:
+    """The m = 1 loop kernel the library launched, with its shape."""
+    if st.get("grid_wide"):
+        return f"k_cd_loop_grid (persistent cooperative grid of {st['grid_blocks']} CTAs, {ips} iterations per launch)"
+    return f"k_cd_loop (persistent {st['grid_blocks']}-CTA cluster, {ips} iterations per launch)"
+
+
 def batch_c4(api, inputs, iters: int, grid_blocks: int = 1) -> dict:
     """The uneven batch (64 ab initio + 32 Hubbard problems) stepped in one launch, one
     thread-block cluster of grid_blocks CTAs per problem."""
@@ -445,7 +452,7 @@ def main():
     rs_peak = random_sector_peak(torch)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "random_sector_peak_gbs": rs_peak, "frac_of_random_sector_peak": achieved / rs_peak,
-                "traffic": traffic, "kernel": f"k_cd_loop (persistent 16-CTA cluster, {ips} iterations per launch)",
+                "traffic": traffic, "kernel": loop_kernel_name(st, ips),
                 "algorithmic_bytes_per_launch": el_per_launch * ALGO_BYTES_PER_ELEMENT,
                 "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
 

@@ -63,9 +63,13 @@ typedef struct {
     uint64_t ref_alpha;        /* start determinant {A, B}; both 0 = aufbau on h_pp */
     uint64_t ref_beta;
     int32_t  block_threads;    /* reserved (the kernels' block sizes are fixed); ignored */
-    int32_t  grid_blocks;      /* m = 1: CTAs of the thread-block cluster that runs the loop (0 = sized
-                                  from the column length; at most 16, a power of two that can be
-                                  resident); m > 1: ignored */
+    int32_t  grid_blocks;      /* m = 1: CTAs that evaluate one column (0 = sized from the column
+                                  length, about one element per thread).  Up to 16 they form one
+                                  thread-block cluster (rounded to a size that can be resident);
+                                  above 16 the loop runs as one cooperative grid of that many CTAs
+                                  (at most the number that can be co-resident, clamped) whose CTAs
+                                  meet at a bounded software barrier once per iteration; m > 1:
+                                  ignored */
     int32_t  graph_chunk;      /* m = 1: iterations per persistent launch (0 = 65536);
                                   m > 1: iterations per captured CUDA graph (0 = 8) */
     int32_t  deterministic;    /* reserved.  m = 1 is deterministic (fixed-order reductions, one update
@@ -92,6 +96,8 @@ typedef struct {
     int32_t status;            /* sticky device status (0 or a CDFCI_ERR_* code) */
     int32_t converged;         /* 1 once dx < dx_threshold */
     int64_t reduced_iterations;/* m > 1: cumulative iterations of the reduced eigensolver (0 for m = 1) */
+    int32_t grid_blocks;       /* m = 1: CTAs that evaluate a column (as resolved); 0 for m > 1 */
+    int32_t grid_wide;         /* m = 1: 1 if they run as a cooperative grid (more than a cluster holds) */
 } cdfci_stats;
 
 /* Fills *p with the defaults (m = 1, 2^22 slots, tau = 0, max_load = 0.79,
@@ -185,7 +191,7 @@ int cdfci_gradient(cdfci_handle h, double *dE_dh, double *dE_dg, double *dE_dkap
  * problem, each cluster executing Algorithm 1 on its own problem with no
  * communication between clusters.  The batch does not own the handles, which
  * must outlive it, have num_coordinates = 1 and the same grid_blocks (CTAs per
- * problem), and are queued on the first handle's stream while batched.  A
+ * problem, at most 16: a grid-wide handle is rejected), and are queued on the first handle's stream while batched.  A
  * handle stays usable on its own: cdfci_step continues from the batch's state.
  * stats (n entries, or NULL) receives every problem's report; the return code
  * is the first problem's error, if any.
@@ -197,12 +203,12 @@ void cdfci_batch_destroy(cdfci_batch_handle b);
 
 /*
  * Autotuner: picks the block size m (num_coordinates) and, for m = 1, the CTAs
- * per column (grid_blocks, the width of the cluster that evaluates one
- * determinant's column) that reach a given energy soonest on this problem (a
+ * per column (grid_blocks, the CTAs that evaluate one determinant's
+ * column) that reach a given energy soonest on this problem (a
  * proxy for time-to-E).  All candidates start from the same point.  First m =
  * 1 with the configured grid_blocks (0 = sized from the column) runs for an
  * equal share of `seconds`, and the energy it reaches is the target.  Then m
- * = 1 with grid_blocks in {1, 2, 4, 8, 16} (the trajectory is the same, only
+ * = 1 with grid_blocks in {1, 2, 4, 8, 16, 32, 64, 128} (the trajectory is the same, only
  * the speed differs) and m in {4, 16, 64, 256} (at most the library's limit)
  * each run until they reach the target or twice the share has passed.  The
  * time spent in cdfci_step is what counts.  On return params->num_coordinates

@@ -45,7 +45,8 @@ class cdfci_stats(ctypes.Structure):
                 ("n_slots", ctypes.c_int64), ("last_column", ctypes.c_int64), ("elements", ctypes.c_int64),
                 ("applied", ctypes.c_int64), ("dropped", ctypes.c_int64), ("inserted", ctypes.c_int64),
                 ("load", ctypes.c_double), ("status", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("reduced_iterations", ctypes.c_int64)]
+                ("reduced_iterations", ctypes.c_int64), ("grid_blocks", ctypes.c_int32),
+                ("grid_wide", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

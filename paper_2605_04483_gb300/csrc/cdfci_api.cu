@@ -80,7 +80,9 @@ struct cdfci_ctx {
     Slot *d_table = nullptr;
     IterState *d_st = nullptr;
     CdRecord *d_rec = nullptr;                   // state between launches of the cluster loop
-    CdPartial *d_part = nullptr;                 // one partial per CTA of the cluster
+    CdPartial *d_part = nullptr;                 // one partial per CTA of the cluster (two sets in grid mode)
+    GridBar *d_bar = nullptr;                    // grid mode: the software grid barrier
+    bool gridmode = false;                       // m = 1 over more CTAs than a cluster holds
     int *d_flags = nullptr;                      // [0] status, [1] has_doubles
     unsigned long long *d_counter = nullptr;     // scratch counter for compaction kernels
     unsigned long long *d_colkeys = nullptr;     // get_column staging (2 * nh)
@@ -106,6 +108,7 @@ void free_ctx(cdfci_ctx *c) {
     for (int i = 0; i < c->mb_nalloc; ++i) cudaFree(c->mb_alloc[i]);
     cudaFree(c->d_h); cudaFree(c->d_g); cudaFree(c->d_J); cudaFree(c->d_K);
     cudaFree(c->d_pairs); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part); cudaFree(c->d_rec);
+    cudaFree(c->d_bar);
     cudaFree(c->d_flags); cudaFree(c->d_counter); cudaFree(c->d_colkeys); cudaFree(c->d_colvals);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -115,7 +118,11 @@ void free_ctx(cdfci_ctx *c) {
 int run_iterations(cdfci_ctx *c, long long n) {
     while (n > 0) {
         long long k = std::min(n, c->chunk);
-        CK(launch_cd_loop(c->P, c->d_st, c->d_rec, c->d_part, c->grid, k, c->stream));
+        if (c->gridmode)
+            CK(launch_cd_loop_grid(c->P, c->d_st, c->d_rec, c->d_part, c->d_part + c->grid, c->d_bar, c->grid, k,
+                                   c->stream));
+        else
+            CK(launch_cd_loop(c->P, c->d_st, c->d_rec, c->d_part, c->grid, k, c->stream));
         n -= k;
     }
     return CDFCI_OK;
@@ -150,6 +157,8 @@ int stats_from_snapshot(cdfci_ctx *c, cdfci_stats *s) {
         s->status = t.status;
         s->converged = t.done;
         s->reduced_iterations = t.eig_iters;
+        s->grid_blocks = c->block ? 0 : c->grid;
+        s->grid_wide = c->gridmode ? 1 : 0;
     }
     if (t.status != 0) {
         const char *what = t.status == CDFCI_ERR_TABLE_FULL ? "hash table full (raise log2_capacity or z_threshold)"
@@ -347,15 +356,26 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
                          (double)P.capacity * sizeof(Slot) / (1 << 30)));
     P.table = c->d_table;
     {
-        const long long per_cta = (long long)cd_threads() * cd_elements_per_thread();
+        // About one column element per element thread: the loop is bound by the latency of each
+        // element's dependent chain (generate, probe, update), not by bandwidth, so spreading a
+        // column over more SMs pays until the per-iteration grid barrier dominates.
+        const long long per_cta = (long long)cd_threads();
         const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
         const long long want = prm.grid_blocks > 0 ? prm.grid_blocks : (nh_eff - 1 + per_cta - 1) / per_cta;
-        c->grid = cd_pick_cluster((int)std::max<long long>(1, std::min<long long>(want, 16)), cd_dynamic_smem(P));
+        const int maxg = want > 16 ? cd_max_grid(cd_dynamic_smem(P)) : 0;
+        if (want > 16 && maxg > 16) {            // more CTAs than a cluster: the grid-wide loop
+            c->gridmode = true;
+            c->grid = (int)std::min<long long>(want, maxg);
+        } else {
+            c->grid = cd_pick_cluster((int)std::max<long long>(1, std::min<long long>(want, 16)), cd_dynamic_smem(P));
+        }
     }
+    const size_t nparts = (size_t)c->grid * (c->gridmode ? 2 : 1);
     if (prm.graph_chunk > 0) c->chunk = prm.graph_chunk;
     if (cudaMemsetAsync(c->d_table, 0, (size_t)P.capacity * sizeof(Slot), s) != cudaSuccess ||
         cudaMalloc(&c->d_st, sizeof(IterState)) != cudaSuccess ||
-        cudaMalloc(&c->d_part, (size_t)c->grid * sizeof(CdPartial)) != cudaSuccess ||
+        cudaMalloc(&c->d_part, nparts * sizeof(CdPartial)) != cudaSuccess ||
+        cudaMalloc(&c->d_bar, sizeof(GridBar)) != cudaSuccess ||
         cudaMalloc(&c->d_rec, sizeof(CdRecord)) != cudaSuccess ||
         cudaMalloc(&c->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_colkeys, (size_t)P.nh * 2 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -364,7 +384,8 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         return bail(fail(CDFCI_ERR_NOMEM, "device allocation failed"));
     if (cudaMemsetAsync(c->d_st, 0, sizeof(IterState), s) != cudaSuccess ||
         cudaMemsetAsync(c->d_rec, 0, sizeof(CdRecord), s) != cudaSuccess ||
-        cudaMemsetAsync(c->d_part, 0, (size_t)c->grid * sizeof(CdPartial), s) != cudaSuccess)
+        cudaMemsetAsync(c->d_part, 0, nparts * sizeof(CdPartial), s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "memset failed"));
 
     // start determinant: given, or aufbau on h_pp (smallest first, ties to the lower index)
@@ -622,6 +643,9 @@ CDFCI_API int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_hand
     for (int k = 0; k < n; ++k) {
         if (!hs[k]) return fail(CDFCI_ERR_ARG, "handle %d is NULL", k);
         if (hs[k]->block) return fail(CDFCI_ERR_ARG, "handle %d has num_coordinates > 1 (batches take m = 1 solvers)", k);
+        if (hs[k]->gridmode)
+            return fail(CDFCI_ERR_ARG, "handle %d runs on %d CTAs, more than a cluster (batches take grid_blocks <= 16)",
+                        k, hs[k]->grid);
         if (hs[k]->grid != hs[0]->grid)
             return fail(CDFCI_ERR_ARG, "handle %d uses %d CTAs per problem, handle 0 uses %d (create all with the same grid_blocks)",
                         k, hs[k]->grid, hs[0]->grid);
@@ -689,7 +713,7 @@ CDFCI_API int cdfci_autotune(const double *h, const double *g, int N, int n_alph
     struct Cand { int m, grid; };
     std::vector<Cand> cs;
     cs.push_back({1, params->grid_blocks});
-    for (int gb : {1, 2, 4, 8, 16})
+    for (int gb : {1, 2, 4, 8, 16, 32, 64, 128})
         if (gb != params->grid_blocks) cs.push_back({1, gb});
     for (int m : {4, 16, 64, 256})
         if (m <= mc_max_m()) cs.push_back({m, params->grid_blocks});

@@ -273,6 +273,14 @@ __device__ __forceinline__ long long table_find(const Problem &P, IterState *st,
     return -2;
 }
 
+// Software grid barrier of the grid-wide m = 1 loop (all CTAs co-resident:
+// cooperative launch).  count: arrivals of the current round; gen: rounds
+// completed.  Zero-initialised.
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+};
+
 // One problem of a batch of independent m = 1 solvers stepped in one launch.
 struct CdInstance {
     Problem P;

@@ -277,6 +277,69 @@ __device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb,
     }
 }
 
+// Grid-wide barrier for the co-resident CTAs of a cooperative launch: a
+// sense-reversing counter with fences on both sides (every CTA's table writes
+// and partial are visible after it).  The wait is bounded: on expiry the status
+// becomes CDFCI_ERR_TIMEOUT and false is returned (all CTAs then leave).
+__device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, IterState *st) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        volatile unsigned int *gen = &bar->gen;
+        const unsigned int g0 = *gen;
+        int ok = 1;
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > (1ll << 26)) { set_status(st, kErrTimeout); ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// A partial written by another SM in this round: read through L2 (an L1 line of
+// the same buffer from two rounds ago may be stale).
+__device__ __forceinline__ CdPartial ldcg_partial(const CdPartial *p) {
+    static_assert(sizeof(CdPartial) % 16 == 0, "CdPartial is read as 16-byte words");
+    CdPartial x;
+    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p);
+    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&x);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(CdPartial) / 16); ++i) dst[i] = __ldcg(src + i);
+    return x;
+}
+
+// Fold the partials r = lane, lane + 32, ... (fixed order) into this lane's
+// accumulators: the best candidate (larger |g|, then the smaller key), the
+// gather sum and the counters.
+__device__ __forceinline__ void fold_partial(const CdPartial &x, bool first, Best &bb, double &bj, double &cj,
+                                             double &gsum, int cnt[4], int &err) {
+    if (first) {
+        bb = Best{x.gbits, x.ka, x.kb, x.slot};
+        bj = x.bj; cj = x.cj; gsum = x.gather;
+        cnt[0] = x.elements; cnt[1] = x.applied; cnt[2] = x.dropped; cnt[3] = x.inserted;
+        err = x.err;
+        return;
+    }
+    if (x.slot >= 0 && (bb.slot < 0 || better(x.gbits, x.ka, x.kb, bb.g, bb.a, bb.b))) {
+        bb = Best{x.gbits, x.ka, x.kb, x.slot};
+        bj = x.bj; cj = x.cj;
+    }
+    gsum += x.gather;
+    cnt[0] += x.elements; cnt[1] += x.applied; cnt[2] += x.dropped; cnt[3] += x.inserted;
+    err |= x.err;
+}
+
 // Algorithm 1 by one thread-block cluster that keeps running: each iteration
 // every CTA scatters a share of the column, writes a partial (best candidate,
 // gather, counters) into its own shared memory, and after the cluster barrier
@@ -286,12 +349,19 @@ __device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb,
 // their results reach the other warps through shared memory.  Every exit
 // decision uses data all CTAs read identically, so all CTAs reach every
 // cluster barrier.
+//
+// kGrid: the same loop over every CTA of a cooperative launch (more CTAs than
+// a cluster holds).  The partials then go through global memory (gbuf[0],
+// gbuf[1] = gpart, alternating) and a software grid barrier replaces the
+// cluster barrier.
+template <bool kGrid>
 __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart,
-                                             long long n_iter) {
+                                             CdPartial *galt, GridBar *bar, long long n_iter) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    const int G = (int)cluster.num_blocks();
-    const int rank = (int)cluster.block_rank();
+    const int G = kGrid ? (int)gridDim.x : (int)cluster.num_blocks();
+    const int rank = kGrid ? (int)blockIdx.x : (int)cluster.block_rank();
+    CdPartial *gbuf[2] = {galt, gpart};
     __shared__ CdPartial spart[2];
     __shared__ ColLists Lw[kCdWarps];
     __shared__ Best r_best[kCdWarps];
@@ -317,12 +387,12 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         ls.applied = R.applied; ls.dropped = R.dropped; ls.inserted = R.inserted; ls.last_column = R.last_column;
         ls.forced = R.forced; ls.done = 0;
         if (lane == 0) {
-            spart[1] = gpart[rank];
+            if (!kGrid) spart[1] = gpart[rank];
             s_err = 0;
             s_done = 0;
         }
     }
-    cluster.sync();
+    if (kGrid) __syncthreads(); else cluster.sync();
 
     // Element e - 1 = lane + 32 * (rank + G * (w + W' * j)), w = warp - 1, W' = warps - 1,
     // j = 0, 1, ...: 32 consecutive elements per warp, consecutive warps' worth
@@ -344,13 +414,16 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                     sel.have_prev = 0; sel.forced = 1; sel.stop = 0;
                 }
             } else {
-                CdPartial x;
-                const bool have = lane < G;   // all lanes take part in the combine
-                if (have) x = *cluster.map_shared_rank(&spart[pin], lane);
-                Best bb = have ? Best{x.gbits, x.ka, x.kb, x.slot} : Best{0ull, ~0ull, ~0ull, -1};
-                double bj = have ? x.bj : 0.0, cj = have ? x.cj : 0.0, gsum = have ? x.gather : 0.0;
-                int cnt[4] = {have ? x.elements : 0, have ? x.applied : 0, have ? x.dropped : 0, have ? x.inserted : 0};
-                int err = have ? x.err : 0;
+                // every CTA's partial of the last column: lane l folds CTAs l, l + 32, ...
+                // (all lanes take part in the combine)
+                Best bb{0ull, ~0ull, ~0ull, -1};
+                double bj = 0.0, cj = 0.0, gsum = 0.0;
+                int cnt[4] = {0, 0, 0, 0};
+                int err = 0;
+                for (int r = lane; r < G; r += 32) {
+                    const CdPartial x = kGrid ? ldcg_partial(gbuf[pin] + r) : *cluster.map_shared_rank(&spart[pin], r);
+                    fold_partial(x, r == lane, bb, bj, cj, gsum, cnt, err);
+                }
                 warp_combine(bb, bj, cj, gsum, cnt, err);
                 // recalculated b of the previous coordinate (Eq. recalculate-b) and its gradient
                 const double pb = fma(ls.pHii, ls.pc, gsum);
@@ -533,7 +606,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 pp.bj = bj; pp.cj = cj; pp.gather = gs;
                 pp.elements = c4[0]; pp.applied = c4[1]; pp.dropped = c4[2]; pp.inserted = c4[3];
                 pp.err = s_err | (bad ? 1 : 0);
-                spart[pout] = pp;
+                if (kGrid) gbuf[pout][rank] = pp; else spart[pout] = pp;
                 // the coordinate's own slot: c_i += eta, b_i as used (rank 0 writes)
                 const double ci = sel.ci, ci_new = ci + sel.eta;
                 if (rank == 0 && !bad) {
@@ -556,13 +629,19 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
             ls.forced = 0;
             if (lane == 0) s_done = ls.done;
         }
-        if (G == 1) __syncthreads(); else cluster.sync();   // partials and table writes visible cluster-wide
+        bool synced = true;
+        if (kGrid) synced = grid_barrier(bar, (unsigned)G, st);     // partials and table writes visible grid-wide
+        else if (G == 1) __syncthreads();
+        else cluster.sync();                                         // ... cluster-wide
         lastp = pout;
-        if (s_done || bad) break;                         // identical in every CTA
+        if (s_done || bad || !synced) break;              // identical in every CTA
     }
 
     // ---- state for the next launch / the finalisation ----
-    if (tid == 0) gpart[rank] = spart[lastp];
+    if (tid == 0) {
+        if (!kGrid) gpart[rank] = spart[lastp];
+        else if (lastp == 0) gpart[rank] = gbuf[0][rank];
+    }
     if (tid == 0 && rank == 0) {      // lane 0 of the control warp holds the state
         CdRecord o;
         o.a = ls.pA; o.b = ls.pB; o.slot = ls.pslot;
@@ -578,7 +657,14 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
 
 __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState *st, CdRecord *rec,
                                                            CdPartial *gpart, long long n_iter) {
-    cd_loop_body(P, st, rec, gpart, n_iter);
+    cd_loop_body<false>(P, st, rec, gpart, nullptr, nullptr, n_iter);
+}
+
+// the loop over every CTA of a cooperative launch (see cd_loop_body)
+__global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop_grid(Problem P, IterState *st, CdRecord *rec,
+                                                                CdPartial *gpart, CdPartial *galt, GridBar *bar,
+                                                                long long n_iter) {
+    cd_loop_body<true>(P, st, rec, gpart, galt, bar, n_iter);
 }
 
 // Many independent problems in one launch: cluster k (blocks k*G .. k*G+G-1)
@@ -593,7 +679,7 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop_batch(const CdInstanc
     for (int t = threadIdx.x; t < (int)(sizeof(Problem) / 8); t += blockDim.x)
         reinterpret_cast<unsigned long long *>(&sP)[t] = reinterpret_cast<const unsigned long long *>(&inst[k].P)[t];
     __syncthreads();
-    cd_loop_body(sP, inst[k].st, inst[k].rec, inst[k].part, n_iter);
+    cd_loop_body<false>(sP, inst[k].st, inst[k].rec, inst[k].part, nullptr, nullptr, n_iter);
 }
 
 // After a batch of iterations: write the pending recalculated b_i of the last
@@ -603,11 +689,15 @@ __device__ __forceinline__ void cd_finalize_body(const Problem &P, IterState *st
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     const CdRecord R = *rec;
-    CdPartial x;
-    const bool have = lane < G && !R.forced;
-    if (have) x = gpart[lane];
-    double gsum = have ? x.gather : 0.0;
-    long long cnt[4] = {have ? x.elements : 0, have ? x.applied : 0, have ? x.dropped : 0, have ? x.inserted : 0};
+    // the same per-lane fold (CTAs lane, lane + 32, ...) and tree as the loop's choice
+    double gsum = 0.0;
+    long long cnt[4] = {0, 0, 0, 0};
+    if (!R.forced)
+        for (int r = lane; r < G; r += 32) {
+            const CdPartial x = gpart[r];
+            gsum = (r == lane) ? x.gather : gsum + x.gather;
+            cnt[0] += x.elements; cnt[1] += x.applied; cnt[2] += x.dropped; cnt[3] += x.inserted;
+        }
     for (int off = 16; off > 0; off >>= 1) {
         gsum += __shfl_down_sync(0xffffffffu, gsum, off);
         for (int k = 0; k < 4; ++k) cnt[k] += __shfl_down_sync(0xffffffffu, cnt[k], off);
@@ -895,6 +985,39 @@ cudaError_t launch_cd_loop_batch(const CdInstance *inst, int n_inst, int cluster
 cudaError_t launch_cd_finalize_batch(const CdInstance *inst, int n_inst, int cluster, cudaStream_t s) {
     k_cd_finalize_batch<<<n_inst, 32, 0, s>>>(inst, n_inst, cluster);
     return cudaGetLastError();
+}
+
+// The grid-wide loop: G co-resident CTAs (cooperative launch); gpart and galt
+// hold G partials each, bar a zeroed GridBar.
+cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart, CdPartial *galt,
+                                GridBar *bar, int G, long long n_iter, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kCdThreads);
+    cfg.dynamicSmemBytes = cd_dynamic_smem(P);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_cd_loop_grid, P, st, rec, gpart, galt, bar, n_iter);
+}
+
+// The largest CTA count of the grid-wide loop that can be co-resident (0 if none).
+int cd_max_grid(size_t smem) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_cd_loop_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        attr_set = true;
+    }
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cd_loop_grid, kCdThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms * per;
 }
 
 size_t cd_dynamic_smem(const Problem &P) {

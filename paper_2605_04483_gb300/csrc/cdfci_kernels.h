@@ -46,6 +46,11 @@ cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long l
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s);
 
+// the m = 1 loop over more CTAs than a cluster holds (cooperative launch)
+cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart, CdPartial *galt,
+                                GridBar *bar, int G, long long n_iter, cudaStream_t s);
+int cd_max_grid(size_t smem);
+
 // batches of independent m = 1 problems: one launch, one cluster per instance
 cudaError_t launch_cd_loop_batch(const CdInstance *inst, int n_inst, int cluster, size_t smem, long long n_iter,
                                  cudaStream_t s);

@@ -50,6 +50,7 @@ int main(void) {
   F(cdfci_params, z_threshold) F(cdfci_params, ref_alpha) F(cdfci_params, block_threads)
   F(cdfci_params, deterministic) F(cdfci_params, cuda_stream)
   F(cdfci_stats, energy) F(cdfci_stats, nnz_c) F(cdfci_stats, load) F(cdfci_stats, status) F(cdfci_stats, converged) F(cdfci_stats, reduced_iterations)
+  F(cdfci_stats, grid_blocks) F(cdfci_stats, grid_wide)
   F(cdfci_tune_report, chosen) F(cdfci_tune_report, m) F(cdfci_tune_report, grid_blocks) F(cdfci_tune_report, iterations) F(cdfci_tune_report, seconds)
   F(cdfci_tune_report, energy_drop) F(cdfci_tune_report, score)
   return 0;

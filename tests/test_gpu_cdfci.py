@@ -21,13 +21,13 @@ def solver(w, **kw):
     return api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]), **kw)
 
 
-def run_trajectory(w, n_iter, tau=0.0, vec_every=0, log2_capacity=16):
+def run_trajectory(w, n_iter, tau=0.0, vec_every=0, log2_capacity=16, **kw):
     """Step the GPU one iteration at a time; the oracle takes the GPU's choice,
     which must be an argmax of |4 b + 4 mu c| over the oracle's candidates
     (within 1e-12 relative: exact ties, e.g. between alpha/beta mirror
     determinants, may be broken either way by rounding), and then applies the
     update with its own arithmetic.  eta and the energy must agree each step."""
-    g = solver(w, z_threshold=tau, log2_capacity=log2_capacity)
+    g = solver(w, z_threshold=tau, log2_capacity=log2_capacity, **kw)
     o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, w.ref, tau, 1)
     ties = 0
     try:
@@ -92,8 +92,40 @@ def test_trajectory_config2_full_size():
     """Config 2 (N = 24, 6 + 6, tau = 1e-5) in the launch configuration the benchmark times."""
     w = inputs.config2()
     agreed, g, o = run_trajectory(w, 60, tau=1e-5, vec_every=30, log2_capacity=21)
+    st = g.stats()
     g.close()
     assert agreed == 60
+    # sized from the column (about one element per thread): more CTAs than a cluster holds
+    assert st["grid_wide"] == 1 and st["grid_blocks"] > 16
+
+
+@pytest.mark.parametrize("grid_blocks", [24, 48, 152])
+def test_trajectory_config2_grid_wide(grid_blocks):
+    """The m = 1 loop over more CTAs than a cluster (cooperative launch, partials
+    through global memory, software grid barrier) follows the oracle as well."""
+    w = inputs.config2()
+    agreed, g, o = run_trajectory(w, 40, tau=1e-5, vec_every=20, log2_capacity=21, grid_blocks=grid_blocks)
+    st = g.stats()
+    g.close()
+    assert agreed == 40
+    assert st["grid_wide"] == 1 and st["grid_blocks"] == grid_blocks
+
+
+def test_grid_wide_steps_are_deterministic():
+    """Grid-wide loop: cdfci_step(n) == n calls of cdfci_step(1), and reruns are bit-identical."""
+    w = inputs.ab_initio(12, 4, 4, seed=3)
+    a = solver(w, grid_blocks=40)
+    b = solver(w, grid_blocks=40)
+    sa = a.step(300)
+    for _ in range(300):
+        sb = b.step(1)
+    assert sa["energy"] == sb["energy"] and sa["iterations"] == sb["iterations"] == 300
+    ka, ca, ba = a.export()
+    kb, cb, bb = b.export()
+    assert vec_by_key(ka, ca) == vec_by_key(kb, cb)
+    assert vec_by_key(ka, ba) == vec_by_key(kb, bb)
+    a.close()
+    b.close()
 
 
 def test_batched_steps_equal_single_steps():
