@@ -464,7 +464,11 @@ int64_t orc_sparse_H(int N, int na, int nb, const double *h, const double *g,
  * The derivative 4 eta^3 + 3 v3 eta^2 + 2 v2 eta + v1 is depressed by
  * eta = x - b/(3a) to x^3 + p x + q; Delta = (q/2)^2 + (p/3)^3.  Delta >= 0:
  * the real root (for Delta = 0 the simple one); Delta < 0: of the three roots
- * x1 < x2 < x3 the one farther from x2 (x1 on an exact tie).  Then Newton on
+ * x1 < x2 < x3 the one farther from x2, which has the lower value (the quartic
+ * differs between x3 and x1 by -(x3 - x1)^3 ((x3 - x2) - (x2 - x1)) / 3); x1
+ * on a tie, where a tie is a difference of the two distances below 1e-9 of
+ * their sum (a symmetric quartic, e.g. a coordinate that is the only nonzero
+ * one, ties exactly, and rounding must not pick a side).  Then Newton on
  * the cubic until the relative change is below 1e-15 (absolute at 0), at most
  * 8 steps.
  */
@@ -491,7 +495,7 @@ double orc_line_search(double v1, double v2, double v3) {
             for (int j = i + 1; j < 3; j++)
                 if (xs[j] < xs[i]) { double t = xs[i]; xs[i] = xs[j]; xs[j] = t; }
         double d1 = xs[1] - xs[0], d3 = xs[2] - xs[1];
-        x = (d3 > d1) ? xs[2] : xs[0];
+        x = (d3 - d1 > 1e-9 * (d1 + d3)) ? xs[2] : xs[0];
     }
     double eta = x - b / (3.0 * a);
     for (int it = 0; it < 8; it++) {

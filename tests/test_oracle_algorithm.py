@@ -47,6 +47,22 @@ def test_line_search_three_roots_picks_the_far_root():
         assert abs(eta - far) < 1e-12
 
 
+def test_line_search_symmetric_tie_goes_to_the_smaller_root():
+    """A coordinate that is the only nonzero one (c_i = 1, mu = 1, b_i = H_ii):
+    the quartic is symmetric about eta = -1, its minima -1 -+ sqrt(-H_ii) have
+    equal values, and the tie goes to the smaller root x1 whatever the rounding
+    of the depressed cubic."""
+    for H in (-5.0, -2.5, -30.25, -53.1, -4.235806999129704):
+        v1, v2, v3 = 4.0 * H + 4.0, 2.0 * H + 6.0, 4.0
+        eta = oracle.line_search(v1, v2, v3)
+        assert abs(eta - (-1.0 - np.sqrt(-H))) <= 1e-12 * (1.0 + np.sqrt(-H)), (H, eta)
+    for roots in [(-2.0, 0.0, 2.0), (-3.5, -1.0, 1.5), (-0.75, 0.5, 1.75)]:
+        c = 4.0 * np.poly(roots)
+        v3, v2, v1 = c[1] / 3.0, c[2] / 2.0, c[3]
+        eta = oracle.line_search(v1, v2, v3)
+        assert abs(eta - roots[0]) < 1e-12, (roots, eta)
+
+
 def test_line_search_small_gradient():
     """Near convergence v1 -> 0 and eta ~ -v1 / (2 v2) to first order."""
     for v1 in (1e-8, -1e-10, 3e-13):
