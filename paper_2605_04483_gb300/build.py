@@ -15,6 +15,11 @@ HEADERS = ["cdfci_internal.cuh", "cdfci_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+# The m = 1 loop is inlined into three kernels (cluster, cooperative grid,
+# batch) whose trajectories must agree bit for bit: no implicit contraction of
+# a product into an addition there, so every fused multiply-add is an explicit
+# fma() and the rounding does not depend on the kernel it was inlined into.
+SOURCE_FLAGS = {"cdfci_kernels.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -42,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *SOURCE_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

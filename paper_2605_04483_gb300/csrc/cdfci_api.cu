@@ -75,7 +75,7 @@ struct cdfci_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     // device buffers
-    double *d_h = nullptr, *d_g = nullptr, *d_J = nullptr, *d_K = nullptr;
+    double *d_h = nullptr, *d_g = nullptr, *d_J = nullptr, *d_K = nullptr, *d_W3 = nullptr, *d_V3 = nullptr;
     unsigned short *d_pairs = nullptr;
     Slot *d_table = nullptr;
     IterState *d_st = nullptr;
@@ -106,7 +106,7 @@ void free_ctx(cdfci_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
     for (int i = 0; i < c->mb_nalloc; ++i) cudaFree(c->mb_alloc[i]);
-    cudaFree(c->d_h); cudaFree(c->d_g); cudaFree(c->d_J); cudaFree(c->d_K);
+    cudaFree(c->d_h); cudaFree(c->d_g); cudaFree(c->d_J); cudaFree(c->d_K); cudaFree(c->d_W3); cudaFree(c->d_V3);
     cudaFree(c->d_pairs); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part); cudaFree(c->d_rec);
     cudaFree(c->d_bar);
     cudaFree(c->d_flags); cudaFree(c->d_counter); cudaFree(c->d_colkeys); cudaFree(c->d_colvals);
@@ -312,13 +312,16 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         cudaMalloc(&c->d_g, n4 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_J, n2 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_K, n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_W3, (size_t)N * n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_V3, (size_t)N * n2 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_flags, 4 * sizeof(int)) != cudaSuccess)
         return bail(fail(CDFCI_ERR_NOMEM, "device allocation of the integrals failed"));
     if (cudaMemcpyAsync(c->d_h, h, n2 * sizeof(double), kind_to_device(h), s) != cudaSuccess ||
         cudaMemcpyAsync(c->d_g, g, n4 * sizeof(double), kind_to_device(g), s) != cudaSuccess ||
         cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "copy of the integrals failed"));
-    if (launch_setup(c->d_h, c->d_g, N, c->d_J, c->d_K, c->d_flags, c->d_flags + 1, s) != cudaSuccess)
+    if (launch_setup(c->d_h, c->d_g, N, c->d_J, c->d_K, c->d_W3, c->d_V3, c->d_flags, c->d_flags + 1, s) !=
+        cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "set-up kernels failed to launch"));
     int flags[4];
     if (cudaMemcpyAsync(flags, c->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -348,7 +351,7 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
     P.pair_ob = P.pair_oa + poa.size();
     P.pair_va = P.pair_ob + pob.size();
     P.pair_vb = P.pair_va + pva.size();
-    P.h = c->d_h; P.g = c->d_g; P.J = c->d_J; P.K = c->d_K;
+    P.h = c->d_h; P.g = c->d_g; P.J = c->d_J; P.K = c->d_K; P.W3 = c->d_W3; P.V3 = c->d_V3;
 
     // table, state, partials, scratch
     if (cudaMalloc(&c->d_table, (size_t)P.capacity * sizeof(Slot)) != cudaSuccess)

@@ -158,6 +158,7 @@ struct Problem {
     long long nh;                  // enumeration length (= seg[5])
     int doubles_vanish;            // all (pq|rs) with p != q and r != s are zero (e.g. Hubbard)
     const double *h, *g, *J, *K;
+    const double *W3, *V3;         // single-excitation terms, (i N + a) N + k: (ia|kk) - (ik|ka) and (ia|kk)
     const unsigned short *pair_oa, *pair_ob, *pair_va, *pair_vb;   // (i | j << 8), i < j
     Slot *table;
     unsigned long long mask;       // capacity - 1
@@ -276,9 +277,10 @@ __device__ __forceinline__ long long table_find(const Problem &P, IterState *st,
 // Software grid barrier of the grid-wide m = 1 loop (all CTAs co-resident:
 // cooperative launch).  count: arrivals of the current round; gen: rounds
 // completed.  Zero-initialised.
+// Arrivals at the software grid barrier so far (never reset: the n-th crossing
+// of a G-CTA grid completes when the count reaches n G).
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;
+    unsigned long long arrived;
 };
 
 // One problem of a batch of independent m = 1 solvers stepped in one launch.
@@ -435,27 +437,38 @@ __device__ __forceinline__ double column_element(const Problem &P, const ColList
 // of occupied spin-orbitals, then a shuffle-down tree; every lane returns the
 // same value).  An ordered same-spin pair contributes (J - K) / 2, an ordered
 // opposite-spin pair J / 2, so each unordered pair is counted once.
-__device__ __forceinline__ double diag_warp(const Problem &P, const ColLists &L) {
+// J and K may be global or shared memory (the loop kernels stage them in
+// shared memory).  A lane's pair terms t = lane + 32 r go to four partial sums
+// (r mod 4) whose loads are independent, combined pairwise.
+__device__ __forceinline__ double diag_warp(const Problem &P, const ColLists &L, const double *J, const double *K) {
     const int lane = threadIdx.x & 31;
-    const int N = P.N, n = P.na + P.nb;
+    const int N = P.N, n = P.na + P.nb, n2 = n * n;
     double x = 0.0;
     for (int t = lane; t < n; t += 32) {
         const int p = t < P.na ? L.occA[t] : L.occB[t - P.na];
         x += __ldg(P.h + p * (N + 1));
     }
-    double y = 0.0;
-    for (int t = lane; t < n * n; t += 32) {
-        const int u = t / n, w = t - u * n;
-        if (u == w) continue;
-        const bool ua = u < P.na, wa = w < P.na;
-        const int p = ua ? L.occA[u] : L.occB[u - P.na];
-        const int q = wa ? L.occA[w] : L.occB[w - P.na];
-        const double jv = __ldg(P.J + p * N + q);
-        y += (ua == wa) ? (jv - __ldg(P.K + p * N + q)) : jv;
+    double y4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t0 = lane; t0 < n2; t0 += 128) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int t = t0 + 32 * r;
+            if (t >= n2) continue;
+            const int u = t / n, w = t - u * n;
+            if (u == w) continue;
+            const bool ua = u < P.na, wa = w < P.na;
+            const int p = ua ? L.occA[u] : L.occB[u - P.na];
+            const int q = wa ? L.occA[w] : L.occB[w - P.na];
+            const double jv = J[p * N + q];
+            y4[r] += (ua == wa) ? (jv - K[p * N + q]) : jv;
+        }
     }
-    x = fma(0.5, y, x);
+    x = fma(0.5, (y4[0] + y4[1]) + (y4[2] + y4[3]), x);
     for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
     return __shfl_sync(0xffffffffu, x, 0);
+}
+__device__ __forceinline__ double diag_warp(const Problem &P, const ColLists &L) {
+    return diag_warp(P, L, P.J, P.K);
 }
 
 // ---------------------------------------------------------------------------
@@ -499,10 +512,16 @@ __device__ __forceinline__ float newton_f32(float x, float v1, float v2, float v
 
 // Step size (appendix "Determining Step Size"): the global minimiser of
 // eta^4 + v3 eta^3 + v2 eta^2 + v1 eta.  Cardano's method on the cubic
-// derivative, with the depressed cubic in single precision; each root is
+// derivative, with the depressed cubic in single precision; the chosen root is
 // polished by two single-precision Newton steps in eta and one FP64 Halley
-// step.  With three real roots the outer two are kept and the one with the
-// smaller quartic value wins, which is the root farther from the middle one.
+// step.  With three real roots x1 < x2 < x3 the minimum at x3 is lower exactly
+// when x3 - x2 > x2 - x1 (the quartic's difference between them is
+// -(x3 - x1)^3 ((x3 - x2) - (x2 - x1)) / 3), so the root farther from the
+// middle one wins, x1 on a tie.  A tie is a difference of the two distances
+// below 1e-9 of their sum (e.g. a coordinate that is the only nonzero one,
+// whose quartic is symmetric about -c_i): decided in single precision when
+// the distances differ by more than 1e-4 of their sum, else on the FP64
+// roots through the quartic's values and that identity.
 __device__ __forceinline__ double line_search(double v1, double v2, double v3) {
     const float f1 = (float)v1, f2 = (float)v2, f3 = (float)v3;
     const float b = 3.0f * f3, c = 2.0f * f2, d = f1;
@@ -520,13 +539,19 @@ __device__ __forceinline__ double line_search(double v1, double v2, double v3) {
     float arg = (3.0f * q / (2.0f * p)) * sqrtf(-3.0f / p);
     arg = fminf(1.0f, fmaxf(-1.0f, arg));
     const float th = acosf(arg) * (1.0f / 3.0f);
-    const float xhi = newton_f32(m * cosf(th) - sh, f1, f2, f3);                    // largest root
-    const float xlo = newton_f32(m * cosf(th - 4.18879020478639098f) - sh, f1, f2, f3);  // smallest root
-    const double r1 = halley_cubic((double)xlo, v1, v2, v3);
-    const double r3 = halley_cubic((double)xhi, v1, v2, v3);
+    const float x3 = m * cosf(th);                            // depressed roots x1 <= x2 <= x3
+    const float x2 = m * cosf(th - 2.09439510239319549f);
+    const float x1 = m * cosf(th - 4.18879020478639098f);
+    const float d1 = x2 - x1, d3 = x3 - x2;
+    if (d3 - d1 > 1e-4f * (d1 + d3)) return halley_cubic((double)newton_f32(x3 - sh, f1, f2, f3), v1, v2, v3);
+    if (d1 - d3 > 1e-4f * (d1 + d3)) return halley_cubic((double)newton_f32(x1 - sh, f1, f2, f3), v1, v2, v3);
+    const double r1 = halley_cubic((double)newton_f32(x1 - sh, f1, f2, f3), v1, v2, v3);
+    const double r3 = halley_cubic((double)newton_f32(x3 - sh, f1, f2, f3), v1, v2, v3);
     const double h1 = (((r1 + v3) * r1 + v2) * r1 + v1) * r1;
     const double h3 = (((r3 + v3) * r3 + v2) * r3 + v1) * r3;
-    return (h3 < h1) ? r3 : r1;
+    const double w = r3 - r1;
+    // x3 iff (d3 - d1) > 1e-9 (d1 + d3), i.e. h1 - h3 > 1e-9 / 3 (x3 - x1)^4
+    return (h1 - h3 > (1e-9 / 3.0) * (w * w) * (w * w)) ? r3 : r1;
 }
 
 }  // namespace cdfci

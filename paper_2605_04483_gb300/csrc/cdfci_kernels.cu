@@ -22,6 +22,8 @@
 // written by the thread whose excitation equals it, with the recalculated b.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "cdfci_internal.cuh"
 #include "cdfci_kernels.h"
 
@@ -122,6 +124,72 @@ __device__ __forceinline__ void build_singles(const Problem &P, const ColLists &
         e.info = (__popcll(X & between_mask(i, a)) & 1) | (i << 8) | (a << 16);
         (alpha ? tabA : tabB)[sl] = e;
     }
+}
+
+// Dynamic shared memory of the m = 1 loop kernels: the column's single-
+// excitation tables (alpha then beta), J and K, and the term table of the
+// singles a CTA evaluates term-parallel: 32-element blocks of the single
+// segment, at most as many as a thread's first round of elements covers and
+// as fit in kTermBytes, each holding 32 x (n_alpha + n_beta + 1) entries.
+constexpr int kTermBytes = 32 * 1024;
+constexpr int kCdMaxDynSmem = 200 * 1024;   // N <= 64: at most 49 KB of tables, 64 KB of J and K, 32 KB of terms
+struct CdSmem {
+    size_t off_j, off_k, off_t, bytes;
+    int tb_max;                        // blocks in the term table (the most any CTA owns, G = 1)
+};
+__host__ __device__ inline CdSmem cd_smem_layout(const Problem &P) {
+    CdSmem L;
+    const size_t tab = (size_t)(P.na * P.va + P.nb * P.vb + 1) * sizeof(SingleEnt);
+    L.off_j = (tab + 15) & ~(size_t)15;
+    L.off_k = L.off_j + (size_t)P.N * P.N * sizeof(double);
+    L.off_t = L.off_k + (size_t)P.N * P.N * sizeof(double);
+    const int nocc = P.na + P.nb;
+    const int nqs = (int)((P.seg[2] - P.seg[0] + 31) / 32);
+    const int cap = kTermBytes / (32 * (int)sizeof(double) * (nocc + 1));
+    int tb = nqs < (kCdWarps - 1) * kCdMaxE ? nqs : (kCdWarps - 1) * kCdMaxE;
+    if (tb > (cap > 1 ? cap : 1)) tb = cap > 1 ? cap : 1;
+    L.tb_max = tb;
+    L.bytes = L.off_t + (size_t)tb * 32 * (nocc + 1) * sizeof(double);
+    return L;
+}
+
+// Entry idx = ls * (nocc + 1) + kk of the CTA's term table: single ls (block
+// ls / 32 of this CTA's share, lane ls % 32); kk < nocc: the term of occupied
+// orbital kk (same spin first, then the other spin); kk = nocc: h_ia.  0.0
+// past the last single.
+__device__ __forceinline__ double single_term(const Problem &P, const ColLists &L, const SingleEnt *tabA,
+                                              const SingleEnt *tabB, int rank, int G, int nocc, long long nsing,
+                                              int idx) {
+    const int ls = idx / (nocc + 1), kk = idx - ls * (nocc + 1);
+    const long long s = 32ll * (rank + (long long)G * (ls >> 5)) + (ls & 31);
+    if (s >= nsing) return 0.0;
+    const int nsa = P.na * P.va;
+    const bool alpha = s < nsa;
+    const int info = alpha ? tabA[s].info : tabB[s - nsa].info;
+    const int i = (info >> 8) & 0xff, a = (info >> 16) & 0xff;
+    if (kk == nocc) return __ldg(P.h + i * P.N + a);
+    const int ns = alpha ? P.na : P.nb;
+    const bool same = kk < ns;
+    const int k = same ? (alpha ? L.occA[kk] : L.occB[kk]) : (alpha ? L.occB[kk - ns] : L.occA[kk - ns]);
+    return __ldg((same ? P.W3 : P.V3) + ((size_t)(i * P.N + a) * P.N + k));
+}
+
+// A single's value from its row of terms, summed in the order of
+// element_value (four partial sums by k mod 4, same spin then other spin).
+__device__ __forceinline__ double single_sum(const double *row, int ns, int no, unsigned long long sgn) {
+    const double h_ia = row[ns + no];
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k0 = 0; k0 < ns; k0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u < ns) s4[u] += row[k0 + u];
+    }
+    for (int k0 = 0; k0 < no; k0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u < no) s4[u] += row[ns + k0 + u];
+    }
+    return apply_parity(h_ia + ((s4[0] + s4[1]) + (s4[2] + s4[3])), sgn);
 }
 
 // Decode element e (singles and opposite-spin doubles from the tables) and
@@ -277,30 +345,29 @@ __device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb,
     }
 }
 
-// Grid-wide barrier for the co-resident CTAs of a cooperative launch: a
-// sense-reversing counter with fences on both sides (every CTA's table writes
-// and partial are visible after it).  The wait is bounded: on expiry the status
-// becomes CDFCI_ERR_TIMEOUT and false is returned (all CTAs then leave).
+// Grid-wide barrier for the co-resident CTAs of a cooperative launch: one
+// atomic arrival on a counter that is never reset (the crossing completes
+// when it reaches the next multiple of the CTA count), a fence before it (this
+// CTA's table writes and partial become visible) and acquire loads while
+// waiting.  The wait is bounded: on expiry the status becomes
+// CDFCI_ERR_TIMEOUT and false is returned (all CTAs then leave).
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, IterState *st) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        volatile unsigned int *gen = &bar->gen;
-        const unsigned int g0 = *gen;
+        const unsigned long long old = atomicAdd(&bar->arrived, 1ull);
+        const unsigned long long target = (old / nblocks + 1ull) * nblocks;
         int ok = 1;
-        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g0) {
-                if (++spins > (1ll << 26)) { set_status(st, kErrTimeout); ok = 0; break; }
-                __nanosleep(32);
-            }
+        long long spins = 0;
+        while (ld_acquire_gpu(&bar->arrived) < target) {
+            if (++spins > (1ll << 22)) { set_status(st, kErrTimeout); ok = 0; break; }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -369,16 +436,24 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     __shared__ int r_cnt[4][kCdWarps];
     __shared__ Sel sel;
     __shared__ int s_done;
-    LoopState ls;                                // meaningful in the control warp (warp 0) only
+    __shared__ LoopState ls;                     // written by lane 0 of the control warp (warp 0) only
     __shared__ double s_hii;
     __shared__ dd s_mu_n, s_al_n;
     __shared__ int s_err;
-    extern __shared__ SingleEnt s_tab[];         // singles of the column: alpha then beta
-    SingleEnt *tabA = s_tab, *tabB = s_tab + P.na * P.va;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    const CdSmem lay = cd_smem_layout(P);
+    SingleEnt *tabA = reinterpret_cast<SingleEnt *>(s_dyn), *tabB = tabA + P.na * P.va;
+    double *sJ = reinterpret_cast<double *>(s_dyn + lay.off_j);
+    double *sK = reinterpret_cast<double *>(s_dyn + lay.off_k);
+    double *sTerm = reinterpret_cast<double *>(s_dyn + lay.off_t);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (rec->done) return;                       // uniform: nothing has synchronised yet
-    if (warp == 0) {
+    for (int t = tid; t < P.N * P.N; t += kCdThreads) {
+        sJ[t] = __ldg(P.J + t);
+        sK[t] = __ldg(P.K + t);
+    }
+    if (tid == 0) {
         const CdRecord &R = *rec;
         ls.pA = R.a; ls.pB = R.b; ls.pslot = R.slot;
         ls.pc = R.c_new; ls.pHii = R.Hii; ls.pmu_g = R.mu_g; ls.peta = R.eta;
@@ -386,11 +461,9 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         ls.iterations = R.iterations; ls.nnz_c = R.nnz_c; ls.n_slots = R.n_slots; ls.elements = R.elements;
         ls.applied = R.applied; ls.dropped = R.dropped; ls.inserted = R.inserted; ls.last_column = R.last_column;
         ls.forced = R.forced; ls.done = 0;
-        if (lane == 0) {
-            if (!kGrid) spart[1] = gpart[rank];
-            s_err = 0;
-            s_done = 0;
-        }
+        if (!kGrid) spart[1] = gpart[rank];
+        s_err = 0;
+        s_done = 0;
     }
     if (kGrid) __syncthreads(); else cluster.sync();
 
@@ -403,6 +476,15 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     constexpr int Wp = kCdWarps - 1;
     const long long stride = (long long)G * Wp * 32;
     const long long e0 = warp == 0 ? nh : 1 + lane + 32ll * (rank + (long long)G * (warp - 1));
+    // Singles of this CTA (blocks rank, rank + G, ... of the single segment) in
+    // the term table: their O(n) sums are spread over all element threads
+    // instead of running as one thread's chain of dependent loads.
+    const int nocc = P.na + P.nb;
+    const long long nsing = P.seg[2] - P.seg[0];
+    const int nqs = (int)((nsing + 31) >> 5);
+    const int n_own = rank < nqs ? (nqs - 1 - rank) / G + 1 : 0;
+    const int tb = n_own < lay.tb_max ? n_own : lay.tb_max;
+    const int nterms = tb * 32 * (nocc + 1);
     int lastp = 1;
     for (long long it = 0; it < n_iter; ++it) {
         const int pin = lastp, pout = lastp ^ 1;
@@ -420,16 +502,20 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 double bj = 0.0, cj = 0.0, gsum = 0.0;
                 int cnt[4] = {0, 0, 0, 0};
                 int err = 0;
-                for (int r = lane; r < G; r += 32) {
-                    const CdPartial x = kGrid ? ldcg_partial(gbuf[pin] + r) : *cluster.map_shared_rank(&spart[pin], r);
-                    fold_partial(x, r == lane, bb, bj, cj, gsum, cnt, err);
+                for (int r = lane; r < G; r += 64) {           // two loads in flight per lane
+                    const bool two = r + 32 < G;
+                    const CdPartial x0 = kGrid ? ldcg_partial(gbuf[pin] + r) : *cluster.map_shared_rank(&spart[pin], r);
+                    CdPartial x1;
+                    if (two) x1 = kGrid ? ldcg_partial(gbuf[pin] + r + 32) : *cluster.map_shared_rank(&spart[pin], r + 32);
+                    fold_partial(x0, r == lane, bb, bj, cj, gsum, cnt, err);
+                    if (two) fold_partial(x1, false, bb, bj, cj, gsum, cnt, err);
                 }
                 warp_combine(bb, bj, cj, gsum, cnt, err);
-                // recalculated b of the previous coordinate (Eq. recalculate-b) and its gradient
-                const double pb = fma(ls.pHii, ls.pc, gsum);
-                const unsigned long long gp = abs_bits(fma(ls.pmu_g, ls.pc, pb));
-                const long long nslots = ls.n_slots + cnt[3];
                 if (lane == 0) {
+                    // recalculated b of the previous coordinate (Eq. recalculate-b) and its gradient
+                    const double pb = fma(ls.pHii, ls.pc, gsum);
+                    const unsigned long long gp = abs_bits(fma(ls.pmu_g, ls.pc, pb));
+                    const long long nslots = ls.n_slots + cnt[3];
                     sel.pA = ls.pA; sel.pB = ls.pB; sel.pslot = ls.pslot; sel.pb = pb; sel.pc = ls.pc;
                     sel.have_prev = 1; sel.forced = 0;
                     if (better(gp, ls.pA, ls.pB, bb.g, bb.a, bb.b)) {
@@ -440,14 +526,14 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                         sel.stop = (err != 0) || (nslots > P.max_entries) || (bb.slot < 0);
                     }
                     if (nslots > P.max_entries) set_status(st, kErrTableFull);
+                    const long long pdiag = ls.pHii != 0.0 ? 1 : 0;
+                    ls.elements += cnt[0] + pdiag;
+                    ls.applied += cnt[1] + pdiag;
+                    ls.dropped += cnt[2];
+                    ls.inserted += cnt[3];
+                    ls.n_slots = nslots;
+                    ls.last_column = cnt[0] + pdiag;
                 }
-                const long long pdiag = ls.pHii != 0.0 ? 1 : 0;
-                ls.elements += cnt[0] + pdiag;
-                ls.applied += cnt[1] + pdiag;
-                ls.dropped += cnt[2];
-                ls.inserted += cnt[3];
-                ls.n_slots = nslots;
-                ls.last_column = cnt[0] + pdiag;
             }
         }
         __syncthreads();
@@ -468,7 +554,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         unsigned long long hAc = 0ull, hBc = 0ull;
         if (warp == 0) {
             // ---- control warp: H_ii and the step size (appendix) ----
-            const double Hii = diag_warp(P, L);
+            const double Hii = diag_warp(P, L, sJ, sK);
             if (lane == 0) {
                 const double bi = sel.bi, ci = sel.ci;
                 double eta;
@@ -494,9 +580,47 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
 #pragma unroll
             for (int k = 0; k < kCdMaxE; ++k)
                 issue_elem(P, L, tabA, tabB, iA, iB, hAc, hBc, e0 + k * stride, nh, have_prev, pA, pB, el[k]);
+            // this thread's singles that the term table covers (first round: block (warp - 1) + W' k)
+            bool ts[kCdMaxE];
+#pragma unroll
+            for (int k = 0; k < kCdMaxE; ++k) ts[k] = el[k].state != 0 && el[k].ix.kind <= 1 && (warp - 1) + Wp * k < tb;
+            // the term table: loads of the first pass in flight while the doubles' values load
+            const int u = tid - 32;
+            constexpr int kU = kCdThreads - 32;
+            constexpr int kR = 2;
+            double tv[kR];
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                const int idx = u + r * kU;
+                tv[r] = idx < nterms ? single_term(P, L, tabA, tabB, rank, G, nocc, nsing, idx) : 0.0;
+            }
 #pragma unroll
             for (int k = 0; k < kCdMaxE; ++k)
-                if (el[k].state != 0) el[k].H = element_value(P, L, el[k].ix);
+                if (el[k].state != 0 && !ts[k]) el[k].H = element_value(P, L, el[k].ix);
+            if (tb > 0) {                              // uniform in the CTA
+#pragma unroll
+                for (int r = 0; r < kR; ++r)
+                    if (u + r * kU < nterms) sTerm[u + r * kU] = tv[r];
+                for (int base = u + kR * kU; base < nterms; base += kR * kU) {
+#pragma unroll
+                    for (int r = 0; r < kR; ++r) {
+                        const int idx = base + r * kU;
+                        tv[r] = idx < nterms ? single_term(P, L, tabA, tabB, rank, G, nocc, nsing, idx) : 0.0;
+                    }
+#pragma unroll
+                    for (int r = 0; r < kR; ++r)
+                        if (base + r * kU < nterms) sTerm[base + r * kU] = tv[r];
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(kCdThreads - 32) : "memory");
+#pragma unroll
+                for (int k = 0; k < kCdMaxE; ++k)
+                    if (ts[k]) {
+                        const int ls = ((warp - 1) + Wp * k) * 32 + lane;
+                        const bool alpha = el[k].ix.kind == 0;
+                        el[k].H = single_sum(sTerm + ls * (nocc + 1), alpha ? P.na : P.nb, alpha ? P.nb : P.na,
+                                             el[k].ix.sgn);
+                    }
+            }
         }
         __syncthreads();
         if (warp == 0 && lane < 2) {
@@ -581,7 +705,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         }
 
         // ---- CTA partial into this CTA's shared memory ----
-        warp_combine(best, bbest, cbest, gather, cnt, err);
+        if (warp != 0) warp_combine(best, bbest, cbest, gather, cnt, err);   // warp 0 holds no elements
         if (lane == 0) {
             r_best[warp] = best;
             r_bc[warp][0] = bbest;
@@ -615,19 +739,20 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 }
                 if (bad && rank == 0) set_status(st, kErrNonfinite);
             }
-            // every lane of the control warp keeps the same copy of the state
-            const double ci = sel.ci, ci_new = ci + sel.eta;
-            ls.pA = sel.iA; ls.pB = sel.iB; ls.pslot = sel.islot;
-            ls.pc = ci_new; ls.pHii = s_hii; ls.pmu_g = sel.mu_g; ls.peta = sel.eta;
-            ls.mu = s_mu_n; ls.alpha = s_al_n;
-            if (!sel.forced) {
-                ls.iterations += 1;
-                ls.dx = P.theta * ls.dx + (1.0 - P.theta) * fabs(sel.eta);
-                if (P.dx_threshold > 0.0 && ls.dx < P.dx_threshold) ls.done = 1;
+            if (lane == 0) {
+                const double ci = sel.ci, ci_new = ci + sel.eta;
+                ls.pA = sel.iA; ls.pB = sel.iB; ls.pslot = sel.islot;
+                ls.pc = ci_new; ls.pHii = s_hii; ls.pmu_g = sel.mu_g; ls.peta = sel.eta;
+                ls.mu = s_mu_n; ls.alpha = s_al_n;
+                if (!sel.forced) {
+                    ls.iterations += 1;
+                    ls.dx = P.theta * ls.dx + (1.0 - P.theta) * fabs(sel.eta);
+                    if (P.dx_threshold > 0.0 && ls.dx < P.dx_threshold) ls.done = 1;
+                }
+                ls.nnz_c += ((ci == 0.0 && ci_new != 0.0) ? 1 : 0) - ((ci != 0.0 && ci_new == 0.0) ? 1 : 0);
+                ls.forced = 0;
+                s_done = ls.done;
             }
-            ls.nnz_c += ((ci == 0.0 && ci_new != 0.0) ? 1 : 0) - ((ci != 0.0 && ci_new == 0.0) ? 1 : 0);
-            ls.forced = 0;
-            if (lane == 0) s_done = ls.done;
         }
         bool synced = true;
         if (kGrid) synced = grid_barrier(bar, (unsigned)G, st);     // partials and table writes visible grid-wide
@@ -916,6 +1041,19 @@ __global__ void k_jk(const double *g, int N, double *J, double *K, int *has_doub
     }
 }
 
+// Single-excitation term tables (Eq. entry, singles): for the excitation i -> a
+// an occupied orbital k of the same spin contributes (ia|kk) - (ik|ka) and one
+// of the other spin (ia|kk); W3 and V3 hold these per (i, a, k), so that the
+// terms of one single lie in two rows of N doubles.
+__global__ void k_w3v3(const double *g, int N, double *W3, double *V3) {
+    const long long n3 = (long long)N * N * N;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t % N), a = (int)((t / N) % N), i = (int)(t / N / N);
+        W3[t] = gi(g, N, i, a, k, k) - gi(g, N, i, k, k, a);
+        V3[t] = gi(g, N, i, a, k, k);
+    }
+}
+
 // Insert the start determinant and write the record that makes the next
 // iteration the initialisation: c = e_ref reached from c = 0 with eta = 1,
 // so mu = 1 and alpha = H_ref,ref.
@@ -964,7 +1102,7 @@ cudaError_t launch_cd_loop_batch(const CdInstance *inst, int n_inst, int cluster
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_cd_loop_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(k_cd_loop_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(k_cd_loop_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
@@ -1008,7 +1146,7 @@ cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, 
 int cd_max_grid(size_t smem) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_cd_loop_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(k_cd_loop_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
         attr_set = true;
     }
     int dev = 0, sms = 0, per = 0;
@@ -1020,16 +1158,14 @@ int cd_max_grid(size_t smem) {
     return sms * per;
 }
 
-size_t cd_dynamic_smem(const Problem &P) {
-    return (size_t)(P.na * P.va + P.nb * P.vb + 1) * sizeof(SingleEnt);
-}
+size_t cd_dynamic_smem(const Problem &P) { return cd_smem_layout(P).bytes; }
 
 // Smallest power-of-two cluster size >= want (at most 16) that can be resident.
 int cd_pick_cluster(int want, size_t smem) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
         attr_set = true;
     }
     int c = 1;
@@ -1089,8 +1225,8 @@ cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long lon
     return cudaGetLastError();
 }
 
-cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int *status, int *has_doubles,
-                         cudaStream_t s) {
+cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, double *W3, double *V3, int *status,
+                         int *has_doubles, cudaStream_t s) {
     long long n4 = (long long)N * N * N * N;
     int grid = (int)((n4 + 255) / 256);
     if (grid > 4096) grid = 4096;
@@ -1099,6 +1235,8 @@ cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int 
     k_symmetrize_h<<<4, 256, 0, s>>>(h, N);
     k_canonicalize_g<<<grid, 256, 0, s>>>(g, N);
     k_jk<<<grid, 256, 0, s>>>(g, N, J, K, has_doubles);
+    const long long n3 = (long long)N * N * N;
+    k_w3v3<<<(int)std::min<long long>((n3 + 255) / 256, 1024), 256, 0, s>>>(g, N, W3, V3);
     return cudaGetLastError();
 }
 

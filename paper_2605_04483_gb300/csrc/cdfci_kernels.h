@@ -20,7 +20,8 @@ cudaError_t launch_export(const Problem &P, const IterState *st, unsigned long l
                           long long cap, unsigned long long *counter, cudaStream_t s);
 cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long long cap, unsigned long long *counter,
                       double *partial, int nblocks, double *out, cudaStream_t s);
-cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, int *status, int *has_doubles,
+cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, double *W3, double *V3, int *status,
+                         int *has_doubles,
                          cudaStream_t s);
 cudaError_t launch_init_state(const Problem &P, IterState *st, CdRecord *rec, unsigned long long A,
                               unsigned long long B, cudaStream_t s);
