@@ -359,10 +359,10 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
                          (double)P.capacity * sizeof(Slot) / (1 << 30)));
     P.table = c->d_table;
     {
-        // About one column element per element thread: the loop is bound by the latency of each
-        // element's dependent chain (generate, probe, update), not by bandwidth, so spreading a
-        // column over more SMs pays until the per-iteration grid barrier dominates.
-        const long long per_cta = (long long)cd_threads();
+        // About 256 column elements per CTA (0.73 per element thread): the loop is bound by the
+        // latency of each element's dependent chain (generate, probe, update), not by bandwidth,
+        // so spreading a column over more SMs pays until the per-iteration grid barrier dominates.
+        const long long per_cta = 256;
         const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
         const long long want = prm.grid_blocks > 0 ? prm.grid_blocks : (nh_eff - 1 + per_cta - 1) / per_cta;
         const int maxg = want > 16 ? cd_max_grid(cd_dynamic_smem(P)) : 0;

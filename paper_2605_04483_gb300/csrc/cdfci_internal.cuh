@@ -510,6 +510,12 @@ __device__ __forceinline__ float newton_f32(float x, float v1, float v2, float v
     return x;
 }
 
+// Cube root to about 1e-6 relative from the special-function unit's base-2
+// logarithm and exponential (0 for 0); it only seeds the Newton steps below.
+__device__ __forceinline__ float cbrt_seed(float x) {
+    return copysignf(exp2f(__log2f(fabsf(x)) * (1.0f / 3.0f)), x);
+}
+
 // Step size (appendix "Determining Step Size"): the global minimiser of
 // eta^4 + v3 eta^3 + v2 eta^2 + v1 eta.  Cardano's method on the cubic
 // derivative, with the depressed cubic in single precision; the chosen root is
@@ -532,7 +538,7 @@ __device__ __forceinline__ double line_search(double v1, double v2, double v3) {
     const float del = hq * hq + tp * tp * tp;
     if (!(del < 0.0f) || !(p < 0.0f)) {
         const float sd = sqrtf(fmaxf(del, 0.0f));
-        const float x = cbrtf(-hq + sd) + cbrtf(-hq - sd) - sh;
+        const float x = cbrt_seed(-hq + sd) + cbrt_seed(-hq - sd) - sh;
         return halley_cubic((double)newton_f32(x, f1, f2, f3), v1, v2, v3);
     }
     const float m = 2.0f * sqrtf(-tp);

@@ -1,22 +1,29 @@
 // CUDA kernels of libcdfci (sm_103a).
 //
-// The m = 1 iteration (Algorithm 1) runs inside k_cd_loop: one thread-block
-// cluster (up to 16 CTAs, one per SM) that performs many iterations per
-// launch.  Per iteration:
-//   1. warp 0 of every CTA reads the partials of the previous iteration from
-//      every CTA's shared memory (distributed shared memory) and reduces them
-//      in a fixed order: the recalculated b of the previous coordinate
-//      (Eq. recalculate-b) and the argmax of |b_j + mu c_j| over the previous
-//      column and that coordinate (Eq. choose-i; the factor 4 does not change
-//      the argmax) -> i, identical in every CTA;
-//   2. every warp builds the orbital lists of i, decodes its share of the
-//      column (Slater-Condon, Eq. entry) and issues the 32-byte slot loads;
-//   3. meanwhile one lane computes H_ii and the step size eta (appendix);
-//      single lanes of two other warps update mu and alpha (double-double);
-//   4. every thread applies b_j += eta H_ji with the compression rule
-//      (c_j != 0 or |eta H_ji| >= tau), inserting absent keys with a 16-byte
-//      CAS, and accumulates the gather sum_j H_ji c_j and its best candidate;
-//   5. the CTA writes its partial to its own shared memory; cluster barrier.
+// The m = 1 iteration (Algorithm 1) runs inside a persistent loop kernel that
+// performs many iterations per launch on G CTAs (one per SM): k_cd_loop, a
+// thread-block cluster (G <= 16, partials exchanged through distributed shared
+// memory), or k_cd_loop_grid, a cooperative grid (G > 16, partials through
+// global memory and a software grid barrier).  Per iteration:
+//   1. warp 0 (the control warp) of every CTA reads the partials of the
+//      previous iteration of every CTA and reduces them in a fixed order: the
+//      recalculated b of the previous coordinate (Eq. recalculate-b) and the
+//      argmax of |b_j + mu c_j| over the previous column and that coordinate
+//      (Eq. choose-i; the factor 4 does not change the argmax) -> i, identical
+//      in every CTA;
+//   2. every warp builds the orbital lists of i; the element warps load the
+//      terms of the CTA's single excitations, build the single-excitation
+//      tables, decode their share of the column (Slater-Condon, Eq. entry),
+//      issue the 32-byte slot loads and evaluate the elements (the singles'
+//      O(n) sums spread over the CTA through a shared-memory term table);
+//   3. meanwhile the control warp computes H_ii (from shared-memory copies of
+//      diag(h), J and K) and one lane the step size eta (appendix);
+//   4. two lanes of the control warp update mu and alpha (double-double)
+//      while every element thread applies b_j += eta H_ji with the
+//      compression rule (c_j != 0 or |eta H_ji| >= tau), inserting absent keys
+//      with a 16-byte CAS, and accumulates the gather sum_j H_ji c_j and its
+//      best candidate;
+//   5. the CTA writes its partial; cluster or grid barrier.
 // In an m = 1 column every j occurs once, so each b_j has a single writer:
 // plain loads and stores, no atomics.  The previous coordinate's slot is
 // written by the thread whose excitation equals it, with the recalculated b.
@@ -127,23 +134,28 @@ __device__ __forceinline__ void build_singles(const Problem &P, const ColLists &
 }
 
 // Dynamic shared memory of the m = 1 loop kernels: the column's single-
-// excitation tables (alpha then beta), J and K, and the term table of the
-// singles a CTA evaluates term-parallel: 32-element blocks of the single
-// segment, at most as many as a thread's first round of elements covers and
-// as fit in kTermBytes, each holding 32 x (n_alpha + n_beta + 1) entries.
+// excitation tables (alpha then beta), J and K, the diagonal of h, the pairs
+// of occupied positions, and the term table of the singles a CTA evaluates
+// term-parallel: 32-element blocks of the single segment, at most as many as a
+// thread's first round of elements covers and as fit in kTermBytes, each
+// holding 32 x (n_alpha + n_beta + 1) entries.
 constexpr int kTermBytes = 32 * 1024;
-constexpr int kCdMaxDynSmem = 200 * 1024;   // N <= 64: at most 49 KB of tables, 64 KB of J and K, 32 KB of terms
+constexpr int kCdMaxDynSmem = 200 * 1024;   // N <= 64: <= 49 KB tables, 64 KB J and K, 16 KB pairs, 32 KB terms
 struct CdSmem {
-    size_t off_j, off_k, off_t, bytes;
+    size_t off_j, off_k, off_hd, off_pairs, off_t, bytes;
+    int npairs;                        // unordered pairs u < w of the n_alpha + n_beta occupied positions
     int tb_max;                        // blocks in the term table (the most any CTA owns, G = 1)
 };
 __host__ __device__ inline CdSmem cd_smem_layout(const Problem &P) {
     CdSmem L;
     const size_t tab = (size_t)(P.na * P.va + P.nb * P.vb + 1) * sizeof(SingleEnt);
+    const int nocc = P.na + P.nb;
+    L.npairs = nocc * (nocc - 1) / 2;
     L.off_j = (tab + 15) & ~(size_t)15;
     L.off_k = L.off_j + (size_t)P.N * P.N * sizeof(double);
-    L.off_t = L.off_k + (size_t)P.N * P.N * sizeof(double);
-    const int nocc = P.na + P.nb;
+    L.off_hd = L.off_k + (size_t)P.N * P.N * sizeof(double);
+    L.off_pairs = L.off_hd + (size_t)P.N * sizeof(double);
+    L.off_t = (L.off_pairs + (size_t)L.npairs * sizeof(unsigned short) + 15) & ~(size_t)15;
     const int nqs = (int)((P.seg[2] - P.seg[0] + 31) / 32);
     const int cap = kTermBytes / (32 * (int)sizeof(double) * (nocc + 1));
     int tb = nqs < (kCdWarps - 1) * kCdMaxE ? nqs : (kCdWarps - 1) * kCdMaxE;
@@ -153,25 +165,74 @@ __host__ __device__ inline CdSmem cd_smem_layout(const Problem &P) {
     return L;
 }
 
-// Entry idx = ls * (nocc + 1) + kk of the CTA's term table: single ls (block
-// ls / 32 of this CTA's share, lane ls % 32); kk < nocc: the term of occupied
-// orbital kk (same spin first, then the other spin); kk = nocc: h_ia.  0.0
-// past the last single.
-__device__ __forceinline__ double single_term(const Problem &P, const ColLists &L, const SingleEnt *tabA,
-                                              const SingleEnt *tabB, int rank, int G, int nocc, long long nsing,
-                                              int idx) {
+// Pair table of the occupied positions (alpha 0 .. n_alpha - 1, then beta):
+// u | w << 7 | same spin << 14 for u < w, in the order (0,1), (0,2), ...,
+// (1,2), ...; filled by the threads of a CTA, u per thread.
+__device__ __forceinline__ void fill_pairs(const Problem &P, unsigned short *pairs) {
+    const int n = P.na + P.nb;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        const int base = u * n - u * (u + 1) / 2;
+        for (int w = u + 1; w < n; ++w)
+            pairs[base + (w - u - 1)] = (unsigned short)(u | (w << 7) | (((u < P.na) == (w < P.na)) ? 1 << 14 : 0));
+    }
+}
+
+// Diagonal element (Eq. entry, i = j) by one warp from shared-memory copies of
+// diag(h), J and K: sum_p h_pp + sum over unordered occupied pairs of J - K
+// (same spin) or J (opposite spins).  Lane l takes pairs l + 32 r into four
+// partial sums (r mod 4) and the h terms of positions l, l + 32, ...; the lane
+// values are combined by a shuffle-down tree, every lane returns the result.
+__device__ __forceinline__ double diag_pairs_warp(const Problem &P, const ColLists &L, const double *sHd,
+                                                  const double *sJ, const double *sK, const unsigned short *pairs,
+                                                  int npairs) {
+    const int lane = threadIdx.x & 31, N = P.N, na = P.na, n = P.na + P.nb;
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    for (int k0 = lane; k0 < npairs; k0 += 128) {
+        double t[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = k0 + 32 * r;
+            t[r] = 0.0;
+            if (k < npairs) {
+                const unsigned pr = pairs[k];
+                const int u = pr & 0x7f, w = (pr >> 7) & 0x7f;
+                const int p = u < na ? L.occA[u] : L.occB[u - na];
+                const int q = w < na ? L.occA[w] : L.occB[w - na];
+                const double jv = sJ[p * N + q];
+                t[r] = (pr >> 14) ? jv - sK[p * N + q] : jv;
+            }
+        }
+        y0 += t[0]; y1 += t[1]; y2 += t[2]; y3 += t[3];
+    }
+    double x = 0.0;
+    for (int u = lane; u < n; u += 32) x += sHd[u < na ? L.occA[u] : L.occB[u - na]];
+    x += (y0 + y1) + (y2 + y3);
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    return __shfl_sync(0xffffffffu, x, 0);
+}
+
+// Address of entry idx = ls * (nocc + 1) + kk of the CTA's term table: single
+// ls (block ls / 32 of this CTA's share, lane ls % 32); kk < nocc: the term of
+// occupied orbital kk (same spin first, then the other spin); kk = nocc: h_ia.
+// The single's orbitals come from the lists, so the loads do not wait for the
+// singles tables.  Past the last single a valid dummy address (h_00).
+__device__ __forceinline__ const double *single_term_ptr(const Problem &P, const ColLists &L, int rank, int G,
+                                                         int nocc, long long nsing, int idx) {
     const int ls = idx / (nocc + 1), kk = idx - ls * (nocc + 1);
     const long long s = 32ll * (rank + (long long)G * (ls >> 5)) + (ls & 31);
-    if (s >= nsing) return 0.0;
+    if (s >= nsing) return P.h;
     const int nsa = P.na * P.va;
     const bool alpha = s < nsa;
-    const int info = alpha ? tabA[s].info : tabB[s - nsa].info;
-    const int i = (info >> 8) & 0xff, a = (info >> 16) & 0xff;
-    if (kk == nocc) return __ldg(P.h + i * P.N + a);
+    const unsigned sl = (unsigned)(alpha ? s : s - nsa);
+    const int o = (int)fdiv(sl, alpha ? P.mg_va : P.mg_vb);
+    const int w = (int)sl - o * (alpha ? P.va : P.vb);
+    const int i = alpha ? L.occA[o] : L.occB[o];
+    const int a = alpha ? L.virA[w] : L.virB[w];
+    if (kk == nocc) return P.h + i * P.N + a;
     const int ns = alpha ? P.na : P.nb;
     const bool same = kk < ns;
     const int k = same ? (alpha ? L.occA[kk] : L.occB[kk]) : (alpha ? L.occB[kk - ns] : L.occA[kk - ns]);
-    return __ldg((same ? P.W3 : P.V3) + ((size_t)(i * P.N + a) * P.N + k));
+    return (same ? P.W3 : P.V3) + ((size_t)(i * P.N + a) * P.N + k);
 }
 
 // A single's value from its row of terms, summed in the order of
@@ -421,7 +482,7 @@ __device__ __forceinline__ void fold_partial(const CdPartial &x, bool first, Bes
 // a cluster holds).  The partials then go through global memory (gbuf[0],
 // gbuf[1] = gpart, alternating) and a software grid barrier replaces the
 // cluster barrier.
-template <bool kGrid>
+template <bool kGrid, int kE>
 __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart,
                                              CdPartial *galt, GridBar *bar, long long n_iter) {
     namespace cg = cooperative_groups;
@@ -445,6 +506,8 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     SingleEnt *tabA = reinterpret_cast<SingleEnt *>(s_dyn), *tabB = tabA + P.na * P.va;
     double *sJ = reinterpret_cast<double *>(s_dyn + lay.off_j);
     double *sK = reinterpret_cast<double *>(s_dyn + lay.off_k);
+    double *sHd = reinterpret_cast<double *>(s_dyn + lay.off_hd);
+    unsigned short *sPairs = reinterpret_cast<unsigned short *>(s_dyn + lay.off_pairs);
     double *sTerm = reinterpret_cast<double *>(s_dyn + lay.off_t);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -453,6 +516,8 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         sJ[t] = __ldg(P.J + t);
         sK[t] = __ldg(P.K + t);
     }
+    for (int t = tid; t < P.N; t += kCdThreads) sHd[t] = __ldg(P.h + t * (P.N + 1));
+    fill_pairs(P, sPairs);
     if (tid == 0) {
         const CdRecord &R = *rec;
         ls.pA = R.a; ls.pB = R.b; ls.pslot = R.slot;
@@ -483,7 +548,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     const long long nsing = P.seg[2] - P.seg[0];
     const int nqs = (int)((nsing + 31) >> 5);
     const int n_own = rank < nqs ? (nqs - 1 - rank) / G + 1 : 0;
-    const int tb = n_own < lay.tb_max ? n_own : lay.tb_max;
+    const int tb = min(min(n_own, lay.tb_max), Wp * kE);
     const int nterms = tb * 32 * (nocc + 1);
     int lastp = 1;
     for (long long it = 0; it < n_iter; ++it) {
@@ -550,11 +615,11 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
             if ((iB >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
         }
         __syncwarp();
-        Elem el[kCdMaxE];
+        Elem el[kE];
         unsigned long long hAc = 0ull, hBc = 0ull;
         if (warp == 0) {
             // ---- control warp: H_ii and the step size (appendix) ----
-            const double Hii = diag_warp(P, L, sJ, sK);
+            const double Hii = diag_pairs_warp(P, L, sHd, sJ, sK, sPairs, lay.npairs);
             if (lane == 0) {
                 const double bi = sel.bi, ci = sel.ci;
                 double eta;
@@ -570,32 +635,32 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 s_hii = Hii;
             }
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k) el[k].state = 0;
+            for (int k = 0; k < kE; ++k) el[k].state = 0;
         } else {
-            // ---- element warps: the column's single-excitation tables, then decode, first probes, values ----
+            // ---- element warps: term loads of this CTA's singles (from the lists alone), the
+            // column's single-excitation tables, decode, first probes, values ----
+            const int u = tid - 32;
+            constexpr int kU = kCdThreads - 32;
+            constexpr int kR = 2;
+            double tv[kR] = {0.0, 0.0};
+            if (tb > 0) {                              // uniform in the CTA; nterms >= 1 then
+#pragma unroll
+                for (int r = 0; r < kR; ++r)
+                    tv[r] = __ldg(single_term_ptr(P, L, rank, G, nocc, nsing, min(u + r * kU, nterms - 1)));
+            }
             build_singles(P, L, iA, iB, tabA, tabB, tid - 32, kCdThreads - 32);
             asm volatile("bar.sync 1, %0;" ::"r"(kCdThreads - 32) : "memory");
             hAc = hash_alpha(iA);
             hBc = hash_beta(iB);
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k)
+            for (int k = 0; k < kE; ++k)
                 issue_elem(P, L, tabA, tabB, iA, iB, hAc, hBc, e0 + k * stride, nh, have_prev, pA, pB, el[k]);
             // this thread's singles that the term table covers (first round: block (warp - 1) + W' k)
-            bool ts[kCdMaxE];
+            bool ts[kE];
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k) ts[k] = el[k].state != 0 && el[k].ix.kind <= 1 && (warp - 1) + Wp * k < tb;
-            // the term table: loads of the first pass in flight while the doubles' values load
-            const int u = tid - 32;
-            constexpr int kU = kCdThreads - 32;
-            constexpr int kR = 2;
-            double tv[kR];
+            for (int k = 0; k < kE; ++k) ts[k] = el[k].state != 0 && el[k].ix.kind <= 1 && (warp - 1) + Wp * k < tb;
 #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const int idx = u + r * kU;
-                tv[r] = idx < nterms ? single_term(P, L, tabA, tabB, rank, G, nocc, nsing, idx) : 0.0;
-            }
-#pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k)
+            for (int k = 0; k < kE; ++k)
                 if (el[k].state != 0 && !ts[k]) el[k].H = element_value(P, L, el[k].ix);
             if (tb > 0) {                              // uniform in the CTA
 #pragma unroll
@@ -603,17 +668,15 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                     if (u + r * kU < nterms) sTerm[u + r * kU] = tv[r];
                 for (int base = u + kR * kU; base < nterms; base += kR * kU) {
 #pragma unroll
-                    for (int r = 0; r < kR; ++r) {
-                        const int idx = base + r * kU;
-                        tv[r] = idx < nterms ? single_term(P, L, tabA, tabB, rank, G, nocc, nsing, idx) : 0.0;
-                    }
+                    for (int r = 0; r < kR; ++r)
+                        tv[r] = __ldg(single_term_ptr(P, L, rank, G, nocc, nsing, min(base + r * kU, nterms - 1)));
 #pragma unroll
                     for (int r = 0; r < kR; ++r)
                         if (base + r * kU < nterms) sTerm[base + r * kU] = tv[r];
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(kCdThreads - 32) : "memory");
 #pragma unroll
-                for (int k = 0; k < kCdMaxE; ++k)
+                for (int k = 0; k < kE; ++k)
                     if (ts[k]) {
                         const int ls = ((warp - 1) + Wp * k) * 32 + lane;
                         const bool alpha = el[k].ix.kind == 0;
@@ -647,9 +710,9 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         int err = 0;
         for (long long eb = e0; !bad && eb < nh;) {
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k) resolve_elem(P, st, el[k], &err);
+            for (int k = 0; k < kE; ++k) resolve_elem(P, st, el[k], &err);
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k) {
+            for (int k = 0; k < kE; ++k) {
                 Elem &x = el[k];
                 if (x.state == 0) continue;
                 const double H = x.H;
@@ -694,13 +757,13 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                     cbest = cj;
                 }
             }
-            eb += kCdMaxE * stride;
+            eb += kE * stride;
             if (eb >= nh) break;
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k)
+            for (int k = 0; k < kE; ++k)
                 issue_elem(P, L, tabA, tabB, iA, iB, hAc, hBc, eb + k * stride, nh, have_prev, pA, pB, el[k]);
 #pragma unroll
-            for (int k = 0; k < kCdMaxE; ++k)
+            for (int k = 0; k < kE; ++k)
                 if (el[k].state != 0) el[k].H = element_value(P, L, el[k].ix);
         }
 
@@ -780,16 +843,20 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     }
 }
 
+// kE: element slots a thread keeps in flight; 1 when one round of the CTAs'
+// threads covers the column (the smaller loop body is faster), else kCdMaxE.
+template <int kE>
 __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState *st, CdRecord *rec,
                                                            CdPartial *gpart, long long n_iter) {
-    cd_loop_body<false>(P, st, rec, gpart, nullptr, nullptr, n_iter);
+    cd_loop_body<false, kE>(P, st, rec, gpart, nullptr, nullptr, n_iter);
 }
 
 // the loop over every CTA of a cooperative launch (see cd_loop_body)
+template <int kE>
 __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop_grid(Problem P, IterState *st, CdRecord *rec,
                                                                 CdPartial *gpart, CdPartial *galt, GridBar *bar,
                                                                 long long n_iter) {
-    cd_loop_body<true>(P, st, rec, gpart, galt, bar, n_iter);
+    cd_loop_body<true, kE>(P, st, rec, gpart, galt, bar, n_iter);
 }
 
 // Many independent problems in one launch: cluster k (blocks k*G .. k*G+G-1)
@@ -804,7 +871,7 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop_batch(const CdInstanc
     for (int t = threadIdx.x; t < (int)(sizeof(Problem) / 8); t += blockDim.x)
         reinterpret_cast<unsigned long long *>(&sP)[t] = reinterpret_cast<const unsigned long long *>(&inst[k].P)[t];
     __syncthreads();
-    cd_loop_body<false>(sP, inst[k].st, inst[k].rec, inst[k].part, nullptr, nullptr, n_iter);
+    cd_loop_body<false, kCdMaxE>(sP, inst[k].st, inst[k].rec, inst[k].part, nullptr, nullptr, n_iter);
 }
 
 // After a batch of iterations: write the pending recalculated b_i of the last
@@ -1080,6 +1147,13 @@ __global__ void k_init_state(Problem P, IterState *st, CdRecord *rec, unsigned l
 // ---------------------------------------------------------------------------
 // Launch wrappers (host)
 // ---------------------------------------------------------------------------
+// One element slot per thread suffices when the G CTAs' element threads cover
+// the column in one round.
+static bool cd_one_round(const Problem &P, int G) {
+    const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
+    return (long long)G * (kCdWarps - 1) * 32 >= nh - 1;
+}
+
 cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
                            long long n_iter, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
@@ -1094,7 +1168,8 @@ cudaError_t launch_cd_loop(const Problem &P, IterState *st, CdRecord *rec, CdPar
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cd_loop, P, st, rec, part, n_iter);
+    if (cd_one_round(P, cluster)) return cudaLaunchKernelEx(&cfg, k_cd_loop<1>, P, st, rec, part, n_iter);
+    return cudaLaunchKernelEx(&cfg, k_cd_loop<kCdMaxE>, P, st, rec, part, n_iter);
 }
 
 cudaError_t launch_cd_loop_batch(const CdInstance *inst, int n_inst, int cluster, size_t smem, long long n_iter,
@@ -1139,23 +1214,26 @@ cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cd_loop_grid, P, st, rec, gpart, galt, bar, n_iter);
+    if (cd_one_round(P, G)) return cudaLaunchKernelEx(&cfg, k_cd_loop_grid<1>, P, st, rec, gpart, galt, bar, n_iter);
+    return cudaLaunchKernelEx(&cfg, k_cd_loop_grid<kCdMaxE>, P, st, rec, gpart, galt, bar, n_iter);
 }
 
 // The largest CTA count of the grid-wide loop that can be co-resident (0 if none).
 int cd_max_grid(size_t smem) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_cd_loop_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
+        cudaFuncSetAttribute(k_cd_loop_grid<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
+        cudaFuncSetAttribute(k_cd_loop_grid<kCdMaxE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
         attr_set = true;
     }
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, per = 0, per1 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cd_loop_grid, kCdThreads, smem) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cd_loop_grid<kCdMaxE>, kCdThreads, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_cd_loop_grid<1>, kCdThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    return sms * per;
+    return sms * std::min(per, per1);
 }
 
 size_t cd_dynamic_smem(const Problem &P) { return cd_smem_layout(P).bytes; }
@@ -1164,8 +1242,10 @@ size_t cd_dynamic_smem(const Problem &P) { return cd_smem_layout(P).bytes; }
 int cd_pick_cluster(int want, size_t smem) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(k_cd_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
+        cudaFuncSetAttribute(k_cd_loop<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_cd_loop<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
+        cudaFuncSetAttribute(k_cd_loop<kCdMaxE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_cd_loop<kCdMaxE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCdMaxDynSmem);
         attr_set = true;
     }
     int c = 1;
@@ -1183,7 +1263,10 @@ int cd_pick_cluster(int want, size_t smem) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_cd_loop, &cfg) == cudaSuccess && n >= 1) return c;
+        int n1 = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_cd_loop<kCdMaxE>, &cfg) == cudaSuccess && n >= 1 &&
+            cudaOccupancyMaxActiveClusters(&n1, k_cd_loop<1>, &cfg) == cudaSuccess && n1 >= 1)
+            return c;
         cudaGetLastError();
     }
     return 1;
@@ -1194,8 +1277,6 @@ cudaError_t launch_cd_finalize(const Problem &P, IterState *st, CdRecord *rec, C
     k_cd_finalize<<<1, 32, 0, s>>>(P, st, rec, part, cluster);
     return cudaGetLastError();
 }
-int cd_threads() { return kCdThreads - 32; }
-int cd_elements_per_thread() { return kCdMaxE; }
 
 cudaError_t launch_column(const Problem &P, unsigned long long A, unsigned long long B, unsigned long long *keys,
                           double *vals, long long cap, unsigned long long *counter, cudaStream_t s) {

@@ -12,8 +12,6 @@ size_t cd_dynamic_smem(const Problem &P);
 int cd_pick_cluster(int want, size_t smem);
 cudaError_t launch_cd_finalize(const Problem &P, IterState *st, CdRecord *rec, CdPartial *part, int cluster,
                                cudaStream_t s);
-int cd_threads();
-int cd_elements_per_thread();
 cudaError_t launch_column(const Problem &P, unsigned long long A, unsigned long long B, unsigned long long *keys,
                           double *vals, long long cap, unsigned long long *counter, cudaStream_t s);
 cudaError_t launch_export(const Problem &P, const IterState *st, unsigned long long *keys, double *c, double *b,
