@@ -64,7 +64,7 @@ typedef struct {
     uint64_t ref_beta;
     int32_t  block_threads;    /* reserved (the kernels' block sizes are fixed); ignored */
     int32_t  grid_blocks;      /* m = 1: CTAs that evaluate one column (0 = sized from the column
-                                  length, about 256 elements per CTA).  Up to 16 they form one
+                                  length: about 256 elements per CTA, at most 64 CTAs).  Up to 16 they form one
                                   thread-block cluster (rounded to a size that can be resident);
                                   above 16 the loop runs as one cooperative grid of that many CTAs
                                   (at most the number that can be co-resident, clamped) whose CTAs

@@ -362,9 +362,12 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         // About 256 column elements per CTA (0.73 per element thread): the loop is bound by the
         // latency of each element's dependent chain (generate, probe, update), not by bandwidth,
         // so spreading a column over more SMs pays until the per-iteration grid barrier dominates.
+        // At most 64 CTAs by default: the control warp then folds every CTA's partial with one
+        // round of loads (two per lane).
         const long long per_cta = 256;
         const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
-        const long long want = prm.grid_blocks > 0 ? prm.grid_blocks : (nh_eff - 1 + per_cta - 1) / per_cta;
+        const long long want = prm.grid_blocks > 0 ? prm.grid_blocks
+                                                   : std::min<long long>((nh_eff - 1 + per_cta - 1) / per_cta, 64);
         const int maxg = want > 16 ? cd_max_grid(cd_dynamic_smem(P)) : 0;
         if (want > 16 && maxg > 16) {            // more CTAs than a cluster: the grid-wide loop
             c->gridmode = true;

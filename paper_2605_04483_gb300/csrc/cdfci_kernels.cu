@@ -18,12 +18,12 @@
 //      O(n) sums spread over the CTA through a shared-memory term table);
 //   3. meanwhile the control warp computes H_ii (from shared-memory copies of
 //      diag(h), J and K) and one lane the step size eta (appendix);
-//   4. two lanes of the control warp update mu and alpha (double-double)
-//      while every element thread applies b_j += eta H_ji with the
-//      compression rule (c_j != 0 or |eta H_ji| >= tau), inserting absent keys
-//      with a 16-byte CAS, and accumulates the gather sum_j H_ji c_j and its
-//      best candidate;
-//   5. the CTA writes its partial; cluster or grid barrier.
+//   4. every element thread applies b_j += eta H_ji with the compression rule
+//      (c_j != 0 or |eta H_ji| >= tau), inserting absent keys with a 16-byte
+//      CAS, and accumulates the gather sum_j H_ji c_j and its best candidate;
+//   5. the control warp combines the CTA's partial and writes it while two
+//      lanes of warp 1 update mu and alpha (double-double); cluster or grid
+//      barrier.
 // In an m = 1 column every j occurs once, so each b_j has a single writer:
 // plain loads and stores, no atomics.  The previous coordinate's slot is
 // written by the thread whose excitation equals it, with the recalculated b.
@@ -499,7 +499,6 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     __shared__ int s_done;
     __shared__ LoopState ls;                     // written by lane 0 of the control warp (warp 0) only
     __shared__ double s_hii;
-    __shared__ dd s_mu_n, s_al_n;
     __shared__ int s_err;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     const CdSmem lay = cd_smem_layout(P);
@@ -686,16 +685,6 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
             }
         }
         __syncthreads();
-        if (warp == 0 && lane < 2) {
-            // lane 0: mu += 2 eta c_i + eta^2; lane 1: alpha += 2 eta b_i + eta^2 H_ii (double-double)
-            const double eta = sel.eta;
-            const dd x0 = lane == 0 ? ls.mu : ls.alpha;
-            const double y1 = lane == 0 ? sel.ci : sel.bi;
-            const double y2 = lane == 0 ? 1.0 : s_hii;
-            const dd t = dd_add_fast(dd_two_prod(2.0 * eta, y1), dd_mul_d(dd_two_prod(eta, eta), y2));
-            const dd r = dd_add_fast(x0, t);
-            if (lane == 0) s_mu_n = r; else s_al_n = r;
-        }
         const double eta = sel.eta;
         const double mu = sel.mu_g;
         const unsigned long long tau_bits = abs_bits(P.tau);
@@ -778,6 +767,17 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
             if (err) atomicOr(&s_err, 1);
         }
         __syncthreads();
+        if (warp == 1 && lane < 2) {
+            // beside the control warp's combine, on another scheduler and with the FP64 pipe of the
+            // element warps idle: lane 0: mu += 2 eta c_i + eta^2; lane 1: alpha += 2 eta b_i +
+            // eta^2 H_ii (double-double); read by the next iteration after the barrier
+            const dd x0 = lane == 0 ? ls.mu : ls.alpha;
+            const double y1 = lane == 0 ? sel.ci : sel.bi;
+            const double y2 = lane == 0 ? 1.0 : s_hii;
+            const dd t = dd_add_fast(dd_two_prod(2.0 * eta, y1), dd_mul_d(dd_two_prod(eta, eta), y2));
+            const dd r = dd_add_fast(x0, t);
+            if (lane == 0) ls.mu = r; else ls.alpha = r;
+        }
         if (warp == 0) {
             const bool have = lane < kCdWarps;
             Best b = have ? r_best[lane] : Best{0ull, ~0ull, ~0ull, -1};
@@ -806,7 +806,6 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 const double ci = sel.ci, ci_new = ci + sel.eta;
                 ls.pA = sel.iA; ls.pB = sel.iB; ls.pslot = sel.islot;
                 ls.pc = ci_new; ls.pHii = s_hii; ls.pmu_g = sel.mu_g; ls.peta = sel.eta;
-                ls.mu = s_mu_n; ls.alpha = s_al_n;
                 if (!sel.forced) {
                     ls.iterations += 1;
                     ls.dx = P.theta * ls.dx + (1.0 - P.theta) * fabs(sel.eta);
