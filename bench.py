@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 ALGO_BYTES_PER_ELEMENT = 40      # 16 B key compare + 8 B c read + 8 B b read + 8 B b write
 WORKLOAD = dict(name="abinitio_N24_6a6b_seed2", N=24, n_alpha=6, n_beta=6, seed=2, tau=1e-5, log2_capacity=27, m=1)
 KERNEL_SOURCES = ["paper_2605_04483_gb300/csrc/cdfci_kernels.cu", "paper_2605_04483_gb300/csrc/cdfci_internal.cuh"]
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_cd_loop_abinitio_N24.txt")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_cd_loop_grid_abinitio_N24.txt")
 
 
 def kernel_hash() -> str:
