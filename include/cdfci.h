@@ -155,6 +155,78 @@ int cdfci_get_column(cdfci_handle h, const uint64_t *key, uint64_t *keys_out, do
 int cdfci_export(cdfci_handle h, uint64_t *keys, double *c, double *b, int64_t cap, int64_t *n_out);
 
 /*
+ * Start vector (optional, replaces the state): c = sum_k c[k] e_{keys k},
+ * keys 2 words per entry (A, B), n >= 1 distinct determinants with the
+ * handle's N, n_alpha, n_beta and at least one nonzero c; host or device
+ * pointers, copied.  The table is cleared and the entries are applied in the
+ * given order as steps of Algorithm 1 (m = 1) or one-coordinate block steps
+ * (m > 1) from c = 0 with the step fixed to c[k]: each column is scattered
+ * with the compression rule of Sec. 3.1, so b = Hc as that rule accumulates it,
+ * mu = c.c and alpha = c.Hc (double-double, Eq. update-var); the reference
+ * start of cdfci_create is the case n = 1, c = 1.  The next cdfci_step then
+ * chooses among the entries of the last start column and that coordinate
+ * (m = 1) or among every entry the start columns touched (m > 1).  These steps
+ * are not counted as iterations.  A sticky error status is cleared.  For m > 1
+ * at most m entries (their columns' candidates must fit the candidate list).
+ * Errors: CDFCI_ERR_ARG (a key outside N or with the wrong electron counts, a
+ * repeated key, all c zero, a NaN, n out of range), CDFCI_ERR_TABLE_FULL,
+ * CDFCI_ERR_NOMEM, CDFCI_ERR_CUDA.
+ */
+int cdfci_set_initial(cdfci_handle h, const uint64_t *keys, const double *c, int64_t n);
+
+/*
+ * Checkpoint / resume (the paper's solver can stop and later continue from
+ * a saved wavefunction, Sec. "Solvers for Ground and Excited States"; it
+ * gives no format).  A checkpoint is this
+ * header plus n_entries rows (keys: 2 words; c, b: as stored, i.e. divided by
+ * the scale s for m > 1; flags: bit 0 = a candidate of the next block
+ * selection).  cdfci_checkpoint fills *hdr and then, if cap >= n_entries, the
+ * rows (host or device pointers; flags may be NULL); a smaller cap returns
+ * CDFCI_ERR_CAPACITY with *hdr filled, so a caller can size its arrays.  The
+ * m = 1 state between steps includes the partial results of the last column
+ * (its best candidate, the gather sum behind the recalculated b of Eq.
+ * recalculate-b, counters); they are stored folded into one, in the order the
+ * next step would fold them, so on a handle with any grid_blocks the next
+ * step is the one the writer would take, and with the same grid_blocks every
+ * following step is bit for bit the same (another grid folds later columns'
+ * gather sums in another order: agreement to the last bits).  m > 1 adds
+ * several columns' contributions to one b_j with FP64 atomics, so its
+ * continuation agrees to the last bits.  cdfci_restore needs a handle with the same N, n_alpha,
+ * n_beta and the same kind of step (m = 1, or m > 1 with the candidates
+ * fitting its candidate list); it clears the table, re-inserts the rows and
+ * sets every scalar.  Errors: CDFCI_ERR_ARG (mismatch, bad header or keys,
+ * duplicates), CDFCI_ERR_TABLE_FULL (the rows exceed this handle's max_load),
+ * CDFCI_ERR_NOMEM, CDFCI_ERR_CUDA.
+ */
+typedef struct {
+    int32_t  version;          /* 1 */
+    int32_t  N, n_alpha, n_beta;
+    int32_t  num_coordinates;  /* m of the handle that wrote it */
+    int32_t  have_prev;        /* m = 1: a coordinate was processed and its column's partials are pending */
+    int32_t  done;             /* the dx stopping rule has fired */
+    int32_t  has_best;         /* m = 1: the pending column has a candidate */
+    int64_t  n_entries;        /* rows that follow */
+    double   mu[2], alpha[2];  /* double-double c.c and c.Hc (hi, lo) */
+    double   scale[2];         /* m > 1: double-double scale s of the stored values (1 for m = 1) */
+    double   dx, energy, last_gamma;
+    int64_t  iterations, nnz_c, n_slots, elements, applied, dropped, inserted, last_column, reduced_iterations;
+    /* m = 1: the coordinate processed last */
+    uint64_t prev_key[2];
+    double   prev_c, prev_Hii, prev_eta, prev_mu_g;
+    /* m = 1: the pending column folded (best candidate by |b + mu c| bits, gather sum, counters) */
+    uint64_t best_key[2];
+    uint64_t best_gbits;
+    double   best_b, best_c, gather;
+    int64_t  pending[4];       /* elements, applied, dropped, inserted of the pending column */
+    int32_t  pending_err;
+    int32_t  reserved;
+} cdfci_checkpoint_header;
+int cdfci_checkpoint(cdfci_handle h, cdfci_checkpoint_header *hdr, uint64_t *keys, double *c, double *b, uint8_t *flags,
+                     int64_t cap);
+int cdfci_restore(cdfci_handle h, const cdfci_checkpoint_header *hdr, const uint64_t *keys, const double *c, const double *b,
+                  const uint8_t *flags);
+
+/*
  * The coordinates chosen by the most recent iteration and their step sizes
  * (eta, in true units), up to cap entries; *m_out receives the count.
  */

@@ -95,6 +95,8 @@ def lib():
         L.orc_candidates.argtypes = [ctypes.c_void_p, c_u64p, ctypes.c_int64]
         L.orc_step_choice.restype = ctypes.c_int
         L.orc_step_choice.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, c_dp, c_dp]
+        L.orc_set_initial.restype = ctypes.c_int
+        L.orc_set_initial.argtypes = [ctypes.c_void_p, c_u64p, c_dp, ctypes.c_int64]
         L.orc_rdm.restype = ctypes.c_int
         L.orc_rdm.argtypes = [ctypes.c_int, ctypes.c_int64, c_u64p, c_dp, c_dp, c_dp]
         _lib = L
@@ -240,6 +242,14 @@ class CDFCI:
         r = lib().orc_step(self._p, int(n))
         if r:
             raise RuntimeError(f"oracle step failed ({r})")
+
+    def set_initial(self, keys, c):
+        """Start vector sum_k c_k e_{keys k}, applied in order as steps with the given c_k (from c = 0)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+        c = np.ascontiguousarray(c, dtype=np.float64).reshape(-1)
+        r = lib().orc_set_initial(self._p, keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _d(c), len(c))
+        if r:
+            raise RuntimeError(f"oracle set_initial failed ({r})")
 
     def step_choice(self, key):
         """One Algorithm-1 step on the given coordinate; returns (|g| of it, max |g|) before the step."""

@@ -721,6 +721,49 @@ orc_state *orc_create(int N, int na, int nb, const double *h, const double *g,
     return st;
 }
 
+/*
+ * Start vector (the reading behind cdfci_set_initial): clear the state, then
+ * for each entry k in order take coordinate D_k from its current value with
+ * the step fixed to c_k, exactly as the initialisation above takes e_ref with
+ * step 1: c_k += c_k's step, b += step H_{:,k} with the compression rule,
+ * b_k recalculated, mu and alpha by Eq. (update-var) with the pre-update c_k,
+ * b_k.  No iteration is counted.  m = 1: the candidates are those of the last
+ * start column (as after any step); m > 1: of every start column,
+ * deduplicated.  Returns 0, -1 (allocation) or -4 (a repeated key).
+ */
+int orc_set_initial(orc_state *st, const uint64_t *keys, const double *c, int64_t n) {
+    dmap_free(&st->map);
+    if (dmap_init(&st->map, 1024)) return -1;
+    st->n = 0; st->ncand = 0;
+    st->mu = 0; st->alpha = 0; st->dx = 0.0; st->iter = 0;
+    st->elements = 0; st->applied = 0; st->dropped = 0; st->last_m = 0;
+    dmap seen;
+    if (dmap_init(&seen, 1024)) return -1;
+    for (int64_t k = 0; k < n; k++) {
+        det_t Di = {keys[2 * k], keys[2 * k + 1]};
+        if (st_entry(st, Di, 0) >= 0 && st->c[st_entry(st, Di, 0)] != 0.0) { dmap_free(&seen); return -4; }
+        int64_t kk = st_entry(st, Di, 1);
+        if (kk < 0) { dmap_free(&seen); return -1; }
+        double ci = st->c[kk], bi = st->b[kk];
+        double Hii = diag_sc(st->N, st->h, st->g, Di);
+        double eta = c[k];
+        st->c[kk] = ci + eta;
+        if (st->m == 1) {                  /* candidates: the last processed column only */
+            st->ncand = 0;
+            dmap_free(&seen);
+            if (dmap_init(&seen, 1024)) return -1;
+        }
+        double rc;
+        if (scatter_column(st, Di, eta, &rc, &seen)) { dmap_free(&seen); return -1; }
+        if (dmap_get(&seen, Di) < 0) { dmap_put(&seen, Di, kk); if (cand_push(st, kk)) { dmap_free(&seen); return -1; } }
+        st->b[kk] = rc;
+        st->mu = st->mu + (quad)2.0 * (quad)eta * (quad)ci + (quad)eta * (quad)eta;
+        st->alpha = st->alpha + (quad)2.0 * (quad)eta * (quad)bi + (quad)eta * (quad)eta * (quad)Hii;
+    }
+    dmap_free(&seen);
+    return 0;
+}
+
 void orc_destroy(orc_state *st) {
     if (!st) return;
     dmap_free(&st->map);

@@ -52,6 +52,22 @@ class cdfci_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class cdfci_checkpoint_header(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int32), ("N", ctypes.c_int32), ("n_alpha", ctypes.c_int32),
+                ("n_beta", ctypes.c_int32), ("num_coordinates", ctypes.c_int32), ("have_prev", ctypes.c_int32),
+                ("done", ctypes.c_int32), ("has_best", ctypes.c_int32), ("n_entries", ctypes.c_int64),
+                ("mu", ctypes.c_double * 2), ("alpha", ctypes.c_double * 2), ("scale", ctypes.c_double * 2),
+                ("dx", ctypes.c_double), ("energy", ctypes.c_double), ("last_gamma", ctypes.c_double),
+                ("iterations", ctypes.c_int64), ("nnz_c", ctypes.c_int64), ("n_slots", ctypes.c_int64),
+                ("elements", ctypes.c_int64), ("applied", ctypes.c_int64), ("dropped", ctypes.c_int64),
+                ("inserted", ctypes.c_int64), ("last_column", ctypes.c_int64), ("reduced_iterations", ctypes.c_int64),
+                ("prev_key", ctypes.c_uint64 * 2), ("prev_c", ctypes.c_double), ("prev_Hii", ctypes.c_double),
+                ("prev_eta", ctypes.c_double), ("prev_mu_g", ctypes.c_double),
+                ("best_key", ctypes.c_uint64 * 2), ("best_gbits", ctypes.c_uint64), ("best_b", ctypes.c_double),
+                ("best_c", ctypes.c_double), ("gather", ctypes.c_double), ("pending", ctypes.c_int64 * 4),
+                ("pending_err", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class CdfciError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libcdfci error {code} ({ERRORS.get(code, '?')}): {msg}")
@@ -90,6 +106,9 @@ def lib():
         L.cdfci_column_noalloc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p, dp, i64,
                                            ctypes.POINTER(ctypes.c_int64), vp]
         L.cdfci_column_noalloc.restype = ctypes.c_int
+        L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
+        L.cdfci_checkpoint.argtypes = [vp, ctypes.POINTER(cdfci_checkpoint_header), u64p, dp, dp, ctypes.c_void_p, i64]
+        L.cdfci_restore.argtypes = [vp, ctypes.POINTER(cdfci_checkpoint_header), u64p, dp, dp, ctypes.c_void_p]
         L.cdfci_destroy.argtypes = [vp]
         L.cdfci_destroy.restype = None
         L.cdfci_last_error.argtypes = []
@@ -181,6 +200,57 @@ def cdfci_export(handle: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     return keys[:n.value], c[:n.value], b[:n.value]
 
 
+def cdfci_set_initial(handle: int, keys, c) -> None:
+    """Start vector: keys (n, 2) uint64 {A, B}, c (n,) float64 (host arrays or device tensors)."""
+    if isinstance(keys, np.ndarray):
+        keys = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+    if isinstance(c, np.ndarray):
+        c = np.ascontiguousarray(c, dtype=np.float64).reshape(-1)
+    n = int(c.shape[0])
+    _check(lib().cdfci_set_initial(handle, _ptr(keys), _ptr(c), n))
+
+
+def cdfci_checkpoint(handle: int) -> dict:
+    """The state between steps: {"header": cdfci_checkpoint_header, "keys", "c", "b", "flags"} (c, b as stored)."""
+    hdr = cdfci_checkpoint_header()
+    rc = lib().cdfci_checkpoint(handle, ctypes.byref(hdr), None, None, None, None, 0)
+    if rc not in (CDFCI_OK, -8):
+        _check(rc)
+    n = int(hdr.n_entries)
+    keys = np.zeros((max(n, 1), 2), dtype=np.uint64)
+    c = np.zeros(max(n, 1))
+    b = np.zeros(max(n, 1))
+    flags = np.zeros(max(n, 1), dtype=np.uint8)
+    _check(lib().cdfci_checkpoint(handle, ctypes.byref(hdr), _ptr(keys), _ptr(c), _ptr(b), _ptr(flags), n))
+    return {"header": hdr, "keys": keys[:n], "c": c[:n], "b": b[:n], "flags": flags[:n]}
+
+
+def cdfci_restore(handle: int, ckpt: dict) -> None:
+    keys = np.ascontiguousarray(ckpt["keys"], dtype=np.uint64)
+    c = np.ascontiguousarray(ckpt["c"], dtype=np.float64)
+    b = np.ascontiguousarray(ckpt["b"], dtype=np.float64)
+    flags = ckpt.get("flags")
+    flags = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
+    hdr = ckpt["header"]
+    _check(lib().cdfci_restore(handle, ctypes.byref(hdr), _ptr(keys), _ptr(c), _ptr(b), _ptr(flags)))
+
+
+def save_checkpoint(path: str, ckpt: dict) -> None:
+    """Writes a checkpoint as .npz: the header's raw bytes and the rows."""
+    np.savez(path, header=np.frombuffer(bytes(ckpt["header"]), dtype=np.uint8), keys=ckpt["keys"], c=ckpt["c"],
+             b=ckpt["b"], flags=ckpt["flags"])
+
+
+def load_checkpoint(path: str) -> dict:
+    with np.load(path) as z:
+        raw = z["header"].tobytes()
+        if len(raw) != ctypes.sizeof(cdfci_checkpoint_header):
+            raise ValueError("checkpoint header has the wrong size")
+        hdr = cdfci_checkpoint_header.from_buffer_copy(raw)
+        return {"header": hdr, "keys": z["keys"].copy(), "c": z["c"].copy(), "b": z["b"].copy(),
+                "flags": z["flags"].copy()}
+
+
 def cdfci_autotune(h, g, N: int, n_alpha: int, n_beta: int, seconds: float = 2.0, **params) -> Tuple[dict, dict]:
     """Picks num_coordinates by the measured energy decrease per second; returns
     (the tuned params as a dict, the report)."""
@@ -270,6 +340,15 @@ class Solver:
 
     def rdm(self, two_body: bool = True):
         return cdfci_rdm(self.handle, self.N, two_body)
+
+    def set_initial(self, keys, c):
+        cdfci_set_initial(self.handle, keys, c)
+
+    def checkpoint(self) -> dict:
+        return cdfci_checkpoint(self.handle)
+
+    def restore(self, ckpt: dict):
+        cdfci_restore(self.handle, ckpt)
 
     def gradient(self):
         return cdfci_gradient(self.handle, self.N)

@@ -187,6 +187,7 @@ int setup_block(cdfci_ctx *c, int m) {
     b.chunk = b.tpc * 16;
     b.nchunk = (int)std::max<long long>(1, (nh_eff - 1 + b.chunk - 1) / b.chunk);
     const long long cap_cand = (long long)m * nh_eff + m + 64;
+    b.cap_cand = cap_cand;
     b.cand_grid = 152 * 4;
     const long long items = (long long)m * b.nchunk, gpb = 256 / b.tpc;
     b.scatter_grid = (int)std::max<long long>(1, std::min<long long>((items + gpb - 1) / gpb, 152 * 16));
@@ -223,6 +224,70 @@ int build_block_graph(cdfci_ctx *c) {
     return CDFCI_OK;
 }
 
+}  // namespace
+
+namespace {
+// Keys (2 words per entry) within N with the handle's electron counts, none repeated.
+int check_keys(const cdfci_ctx *c, const std::vector<uint64_t> &k, int64_t n) {
+    const unsigned long long full = c->N >= 64 ? ~0ull : ((1ull << c->N) - 1ull);
+    std::vector<std::pair<uint64_t, uint64_t>> v((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t a = k[2 * i], b = k[2 * i + 1];
+        if ((a & ~full) || (b & ~full) || __builtin_popcountll(a) != c->na || __builtin_popcountll(b) != c->nb)
+            return fail(CDFCI_ERR_ARG, "entry %lld: key {%#llx, %#llx} does not match N = %d, n_alpha = %d, n_beta = %d",
+                        (long long)i, (unsigned long long)a, (unsigned long long)b, c->N, c->na, c->nb);
+        v[(size_t)i] = {a, b};
+    }
+    std::sort(v.begin(), v.end());
+    for (size_t i = 1; i < v.size(); ++i)
+        if (v[i] == v[i - 1])
+            return fail(CDFCI_ERR_ARG, "key {%#llx, %#llx} appears twice", (unsigned long long)v[i].first,
+                        (unsigned long long)v[i].second);
+    return CDFCI_OK;
+}
+
+template <typename T>
+int copy_in(std::vector<T> &dst, const T *src, size_t count) {
+    dst.resize(count);
+    if (count && cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDefault) != cudaSuccess)
+        return fail(CDFCI_ERR_ARG, "input array could not be read (not host or device memory?)");
+    return CDFCI_OK;
+}
+
+// Device copies of host arrays for one call; freed by the destructor.
+struct DevTemp {
+    std::vector<void *> p;
+    template <typename T>
+    T *put(const std::vector<T> &h, cudaStream_t s) {
+        void *d = nullptr;
+        if (cudaMalloc(&d, std::max<size_t>(h.size(), 1) * sizeof(T)) != cudaSuccess) return nullptr;
+        p.push_back(d);
+        if (!h.empty() && cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return nullptr;
+        return static_cast<T *>(d);
+    }
+    template <typename T>
+    T *alloc(size_t n) {
+        void *d = nullptr;
+        if (cudaMalloc(&d, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+        p.push_back(d);
+        return static_cast<T *>(d);
+    }
+    ~DevTemp() {
+        for (void *d : p) cudaFree(d);
+    }
+};
+
+// A fresh state word: no error, scale 1, zero counters.
+int reset_state(cdfci_ctx *c) {
+    IterState t;
+    memset(&t, 0, sizeof(t));
+    t.scale = dd_from(1.0);
+    CK(cudaMemcpyAsync(c->d_st, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->d_table, 0, (size_t)c->P.capacity * sizeof(Slot), c->stream));
+    if (c->block) CK(cudaMemsetAsync(c->mb.ms, 0, sizeof(McState), c->stream));
+    return CDFCI_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -413,7 +478,7 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         if (rc != CDFCI_OK) return bail(rc);
         if (prm.graph_chunk > 0) c->mchunk = prm.graph_chunk;
         // start vector c = e_ref, b = H e_ref (compression applied): first column with eta = 1
-        if (launch_mc_init(P, c->mb, refA, refB, s) != cudaSuccess ||
+        if (launch_mc_start(P, c->mb, refA, refB, 1.0, 1, s) != cudaSuccess ||
             launch_mc_scatter_finalize(P, c->mb, s) != cudaSuccess)
             return bail(fail(CDFCI_ERR_CUDA, "initial column launch failed"));
         rc = fill_stats(c, nullptr);
@@ -423,7 +488,7 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         *out = c;
         return CDFCI_OK;
     }
-    if (launch_init_state(P, c->d_st, c->d_rec, refA, refB, s) != cudaSuccess)
+    if (launch_init_state(c->d_st, c->d_rec, refA, refB, 1.0, s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "init launch failed"));
     // initialisation iteration: c = e_ref, b = H e_ref (compression applied)
     rc = run_iterations(c, 1);
@@ -535,6 +600,198 @@ CDFCI_API int cdfci_export(cdfci_handle c, uint64_t *keys, double *cv, double *b
     cudaFree(dk); cudaFree(dc); cudaFree(db);
     if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "export: %s", cudaGetErrorString(e));
     return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_set_initial(cdfci_handle c, const uint64_t *keys, const double *cv, int64_t n) {
+    if (!c || !keys || !cv) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (n < 1) return fail(CDFCI_ERR_ARG, "n = %lld, need at least one entry", (long long)n);
+    if (c->block && n > c->mb.m)
+        return fail(CDFCI_ERR_ARG, "%lld entries for m = %d: a block handle takes at most m start entries", (long long)n,
+                    c->mb.m);
+    if (n > c->P.max_entries) return fail(CDFCI_ERR_TABLE_FULL, "%lld entries exceed max_load of the table", (long long)n);
+    std::vector<uint64_t> hk;
+    std::vector<double> hc;
+    int rc = copy_in(hk, keys, (size_t)n * 2);
+    if (!rc) rc = copy_in(hc, cv, (size_t)n);
+    if (!rc) rc = check_keys(c, hk, n);
+    if (rc) return rc;
+    bool any = false;
+    for (double x : hc) {
+        if (!std::isfinite(x)) return fail(CDFCI_ERR_ARG, "non-finite start coefficient");
+        any = any || x != 0.0;
+    }
+    if (!any) return fail(CDFCI_ERR_ARG, "every start coefficient is zero");
+    CK(cudaStreamSynchronize(c->stream));
+    DevTemp tmp;
+    unsigned long long *dk = tmp.put(std::vector<unsigned long long>(hk.begin(), hk.end()), c->stream);
+    double *dc = tmp.put(hc, c->stream);
+    if (!dk || !dc) return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    rc = reset_state(c);
+    if (rc) return rc;
+    if (!c->block) {
+        CK(launch_init_state(c->d_st, c->d_rec, hk[0], hk[1], hc[0], c->stream));
+        rc = run_iterations(c, 1);
+        for (int64_t k = 1; !rc && k < n; ++k) {
+            CK(launch_force_next(c->d_rec, dk, dc, k, c->stream));
+            rc = run_iterations(c, 1);
+        }
+        if (rc) return rc;
+    } else {
+        for (int64_t k = 0; k < n; ++k) {
+            CK(launch_mc_start(c->P, c->mb, hk[2 * k], hk[2 * k + 1], hc[k], k == 0 ? 1 : 0, c->stream));
+            CK(launch_mc_scatter_finalize(c->P, c->mb, c->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return fill_stats(c, nullptr);
+}
+
+CDFCI_API int cdfci_checkpoint(cdfci_handle c, cdfci_checkpoint_header *hdr, uint64_t *keys, double *cv, double *bv,
+                               uint8_t *flags, int64_t cap) {
+    if (!c || !hdr) return fail(CDFCI_ERR_ARG, "NULL argument");
+    int rc = fill_stats(c, nullptr);                   // m = 1: the pending b of the last coordinate is in the table
+    if (rc) return rc;
+    cdfci_checkpoint_header h;
+    memset(&h, 0, sizeof(h));
+    h.version = 1;
+    h.N = c->N; h.n_alpha = c->na; h.n_beta = c->nb;
+    h.num_coordinates = c->block ? c->mb.m : 1;
+    h.n_entries = c->h_st->n_slots;
+    if (!c->block) {
+        CdRecord R;
+        CdPartial F;
+        DevTemp tmp;
+        CdPartial *dF = tmp.alloc<CdPartial>(1);
+        if (!dF) return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+        CK(launch_ckpt_fold(c->d_part, c->grid, dF, c->stream));
+        CK(cudaMemcpyAsync(&F, dF, sizeof(F), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(&R, c->d_rec, sizeof(R), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (R.forced) return fail(CDFCI_ERR_ARG, "a start step is pending (run cdfci_step first)");
+        h.have_prev = R.have_prev; h.done = R.done;
+        h.mu[0] = R.mu.hi; h.mu[1] = R.mu.lo; h.alpha[0] = R.alpha.hi; h.alpha[1] = R.alpha.lo;
+        h.scale[0] = 1.0; h.scale[1] = 0.0;
+        h.dx = R.dx; h.energy = R.energy; h.last_gamma = 0.0;
+        h.iterations = R.iterations; h.nnz_c = R.nnz_c; h.n_slots = R.n_slots; h.elements = R.elements;
+        h.applied = R.applied; h.dropped = R.dropped; h.inserted = R.inserted; h.last_column = R.last_column;
+        h.prev_key[0] = R.a; h.prev_key[1] = R.b;
+        h.prev_c = R.c_new; h.prev_Hii = R.Hii; h.prev_eta = R.eta; h.prev_mu_g = R.mu_g;
+        h.has_best = R.have_prev && F.slot >= 0 ? 1 : 0;
+        h.best_key[0] = F.ka; h.best_key[1] = F.kb; h.best_gbits = F.gbits;
+        h.best_b = F.bj; h.best_c = F.cj; h.gather = R.have_prev ? F.gather : 0.0;
+        h.pending[0] = R.have_prev ? F.elements : 0; h.pending[1] = R.have_prev ? F.applied : 0;
+        h.pending[2] = R.have_prev ? F.dropped : 0; h.pending[3] = R.have_prev ? F.inserted : 0;
+        h.pending_err = R.have_prev ? F.err : 0;
+    } else {
+        McState ms;
+        CK(cudaMemcpyAsync(&ms, c->mb.ms, sizeof(ms), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        h.done = ms.done;
+        h.mu[0] = ms.mu.hi; h.mu[1] = ms.mu.lo; h.alpha[0] = ms.alpha.hi; h.alpha[1] = ms.alpha.lo;
+        h.scale[0] = ms.scale.hi; h.scale[1] = ms.scale.lo;
+        h.dx = ms.dx; h.energy = ms.energy; h.last_gamma = ms.last_gamma;
+        h.iterations = ms.iterations; h.nnz_c = ms.nnz_c; h.n_slots = ms.n_slots; h.elements = ms.elements;
+        h.applied = ms.applied; h.dropped = ms.dropped; h.inserted = ms.inserted; h.last_column = ms.last_column;
+        h.reduced_iterations = ms.eig_iters_total;
+    }
+    *hdr = h;
+    const long long n = h.n_entries;
+    if (cap < n) return fail(CDFCI_ERR_CAPACITY, "%lld entries stored, cap is %lld", n, (long long)cap);
+    if (!keys || !cv || !bv) return fail(CDFCI_ERR_ARG, "NULL row array");
+    DevTemp tmp;
+    unsigned long long *dk = tmp.alloc<unsigned long long>((size_t)n * 2);
+    double *dc = tmp.alloc<double>((size_t)n), *db = tmp.alloc<double>((size_t)n);
+    unsigned char *df = tmp.alloc<unsigned char>((size_t)n);
+    if (!dk || !dc || !db || !df) return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_ckpt_export(c->P, dk, dc, db, df, n, c->d_counter, c->stream));
+    CK(cudaMemcpyAsync(keys, dk, (size_t)n * 2 * sizeof(uint64_t), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(cv, dc, (size_t)n * sizeof(double), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(bv, db, (size_t)n * sizeof(double), cudaMemcpyDefault, c->stream));
+    if (flags) CK(cudaMemcpyAsync(flags, df, (size_t)n, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_restore(cdfci_handle c, const cdfci_checkpoint_header *hdr, const uint64_t *keys, const double *cv,
+                            const double *bv, const uint8_t *flags) {
+    if (!c || !hdr || !keys || !cv || !bv) return fail(CDFCI_ERR_ARG, "NULL argument");
+    const cdfci_checkpoint_header h = *hdr;
+    if (h.version != 1) return fail(CDFCI_ERR_ARG, "checkpoint version %d, expected 1", h.version);
+    if (h.N != c->N || h.n_alpha != c->na || h.n_beta != c->nb)
+        return fail(CDFCI_ERR_ARG, "checkpoint of N = %d, %d + %d electrons; handle has N = %d, %d + %d", h.N, h.n_alpha,
+                    h.n_beta, c->N, c->na, c->nb);
+    if ((h.num_coordinates > 1) != c->block)
+        return fail(CDFCI_ERR_ARG, "checkpoint of m = %d cannot resume on a handle with m %s", h.num_coordinates,
+                    c->block ? "> 1" : "= 1");
+    const long long n = h.n_entries;
+    if (n < 1) return fail(CDFCI_ERR_ARG, "checkpoint with %lld entries", n);
+    if (n > c->P.max_entries) return fail(CDFCI_ERR_TABLE_FULL, "%lld entries exceed max_load of the table", n);
+    std::vector<uint64_t> hk;
+    std::vector<double> hc, hb;
+    std::vector<uint8_t> hf;
+    int rc = copy_in(hk, keys, (size_t)n * 2);
+    if (!rc) rc = copy_in(hc, cv, (size_t)n);
+    if (!rc) rc = copy_in(hb, bv, (size_t)n);
+    if (!rc && flags) rc = copy_in(hf, flags, (size_t)n);
+    if (!rc) rc = check_keys(c, hk, n);
+    if (rc) return rc;
+    if (c->block) {
+        long long nc = 0;
+        for (uint8_t f : hf) nc += f & 1;
+        if (nc > c->mb.cap_cand)
+            return fail(CDFCI_ERR_ARG, "%lld candidates exceed this handle's candidate list (%lld)", nc, c->mb.cap_cand);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    DevTemp tmp;
+    unsigned long long *dk = tmp.put(std::vector<unsigned long long>(hk.begin(), hk.end()), c->stream);
+    double *dc = tmp.put(hc, c->stream), *db = tmp.put(hb, c->stream);
+    unsigned char *df = hf.empty() ? nullptr : tmp.put(std::vector<unsigned char>(hf.begin(), hf.end()), c->stream);
+    if (!dk || !dc || !db || (!hf.empty() && !df)) return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    rc = reset_state(c);
+    if (rc) return rc;
+    if (!c->block) {
+        CK(launch_ckpt_import(c->P, c->d_st, dk, dc, db, nullptr, n, nullptr, nullptr, 0, c->stream));
+        CdRecord R;
+        memset(&R, 0, sizeof(R));
+        R.a = h.prev_key[0]; R.b = h.prev_key[1]; R.slot = 0;
+        R.c_new = h.prev_c; R.Hii = h.prev_Hii; R.eta = h.prev_eta; R.mu_g = h.prev_mu_g;
+        R.mu = dd{h.mu[0], h.mu[1]}; R.alpha = dd{h.alpha[0], h.alpha[1]};
+        R.dx = h.dx; R.energy = h.energy;
+        R.iterations = h.iterations; R.nnz_c = h.nnz_c; R.n_slots = h.n_slots; R.elements = h.elements;
+        R.applied = h.applied; R.dropped = h.dropped; R.inserted = h.inserted; R.last_column = h.last_column;
+        R.forced = 0; R.have_prev = h.have_prev ? 1 : 0; R.done = h.done;
+        CdPartial F;
+        memset(&F, 0, sizeof(F));
+        F.gather = h.gather; F.gbits = h.has_best ? h.best_gbits : 0ull;
+        F.ka = h.has_best ? h.best_key[0] : ~0ull; F.kb = h.has_best ? h.best_key[1] : ~0ull;
+        F.slot = h.has_best ? 0 : -1;
+        F.bj = h.best_b; F.cj = h.best_c;
+        F.elements = (int)h.pending[0]; F.applied = (int)h.pending[1]; F.dropped = (int)h.pending[2];
+        F.inserted = (int)h.pending[3]; F.err = h.pending_err;
+        CK(launch_ckpt_restore_m1(c->P, c->d_st, c->d_rec, c->d_part, c->grid, R, F, c->stream));
+    } else {
+        McState ms;
+        memset(&ms, 0, sizeof(ms));
+        ms.mu = dd{h.mu[0], h.mu[1]}; ms.alpha = dd{h.alpha[0], h.alpha[1]}; ms.scale = dd{h.scale[0], h.scale[1]};
+        ms.dx = h.dx; ms.energy = h.energy; ms.last_gamma = h.last_gamma;
+        ms.iterations = h.iterations; ms.nnz_c = h.nnz_c; ms.n_slots = h.n_slots; ms.elements = h.elements;
+        ms.applied = h.applied; ms.dropped = h.dropped; ms.inserted = h.inserted; ms.last_column = h.last_column;
+        ms.done = h.done; ms.eig_iters_total = h.reduced_iterations;
+        CK(cudaMemcpyAsync(c->mb.ms, &ms, sizeof(ms), cudaMemcpyHostToDevice, c->stream));
+        IterState t;
+        memset(&t, 0, sizeof(t));
+        t.scale = ms.scale;
+        t.iterations = ms.iterations; t.nnz_c = ms.nnz_c; t.n_slots = ms.n_slots; t.elements = ms.elements;
+        t.applied = ms.applied; t.dropped = ms.dropped; t.inserted = ms.inserted; t.last_column = ms.last_column;
+        t.mu = ms.mu; t.alpha = ms.alpha; t.dx = ms.dx; t.energy = ms.energy; t.eig_iters = ms.eig_iters_total;
+        t.done = ms.done;
+        CK(cudaMemcpyAsync(c->d_st, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
+        CK(launch_ckpt_import(c->P, c->d_st, dk, dc, db, df, n, c->mb.cand, &c->mb.ms->n_cand, c->mb.cap_cand,
+                              c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return fill_stats(c, nullptr);
 }
 
 namespace {

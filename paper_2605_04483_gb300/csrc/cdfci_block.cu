@@ -1233,17 +1233,25 @@ __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel
     }
 }
 
-// Start vector c = e_ref (as a forced first "step" with eta = 1 from c = 0).
-__global__ void k_mc_init(Problem P, McState *ms, IterState *st, McSel *sel, double *Hdiag, double *w, double *thr,
-                          double *etaout, unsigned long long A, unsigned long long B) {
+// One entry of a start vector: c_{A,B} = eta from c = 0, as a forced block step
+// of one coordinate (its column is scattered with weight eta by k_mc_scatter,
+// b_{A,B} recalculated by k_mc_finalize).  mu += eta^2, alpha += 2 eta b + eta^2
+// H (double-double), b as stored before the step.  The first entry (first = 1)
+// starts from the reset state: c = e_ref (eta = 1) is the default start of r4.
+__global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, double *Hdiag, double *w, double *thr,
+                           double *etaout, unsigned long long A, unsigned long long B, double eta, int first) {
     __shared__ ColLists L;
     __shared__ long long s_slot;
+    __shared__ double s_bold;
+    __shared__ int s_ins;
     if (threadIdx.x == 0) {
         bool ins = false;
         long long s = table_find(P, st, A, B, true, &ins);
         if (s < 0) { set_status(st, kErrTableFull); s = 0; }
         s_slot = s;
-        P.table[s].c = 1.0;
+        s_ins = ins ? 1 : 0;
+        s_bold = P.table[s].bv;
+        P.table[s].c = eta;
     }
     for (int t = threadIdx.x; t < P.N; t += blockDim.x) {
         int ra = __popcll(A & low_mask(t)), rb = __popcll(B & low_mask(t));
@@ -1254,31 +1262,38 @@ __global__ void k_mc_init(Problem P, McState *ms, IterState *st, McSel *sel, dou
     if (threadIdx.x < 32) {
         const double hd = diag_warp(P, L);
         if (threadIdx.x == 0) {
+            if (first) {
+                ms->n_cand = 0;
+                ms->mu = dd_from(0.0);
+                ms->alpha = dd_from(0.0);
+                ms->scale = dd_from(1.0);
+                st->scale = dd_from(1.0);
+                ms->dx = 0.0;
+                ms->iterations = 0;
+                ms->nnz_c = 0;
+                ms->n_slots = 0;
+                ms->inserted = 0;
+                ms->elements = 0; ms->applied = 0; ms->dropped = 0; ms->last_column = 0;
+                for (int k = 0; k < 4; ++k) ms->cnt[k] = 0;
+                ms->done = 0;
+                ms->done_pending = 0;
+                ms->n_above = 0;
+                ms->n_inbin = 0;
+            }
             McSel x;
             x.slot = s_slot; x.gkey = 0ull; x.A = A; x.B = B;
             sel[0] = x;
             Hdiag[0] = hd;
-            w[0] = 1.0;
-            thr[0] = P.tau;
-            etaout[0] = 1.0;
+            w[0] = eta;
+            thr[0] = eta != 0.0 ? P.tau / fabs(eta) : 1.0e308;
+            etaout[0] = eta;
             ms->m_sel = 1;
-            ms->n_cand = 0;
-            ms->mu = dd_from(1.0);
-            ms->alpha = dd_from(hd);
-            ms->scale = dd_from(1.0);
-            st->scale = dd_from(1.0);
-            ms->energy = hd;
-            ms->dx = 0.0;
-            ms->iterations = 0;
-            ms->nnz_c = 1;
-            ms->n_slots = 1;
-            ms->inserted = 1;
-            ms->elements = 0; ms->applied = 0; ms->dropped = 0; ms->last_column = 0;
-            for (int k = 0; k < 4; ++k) ms->cnt[k] = 0;
-            ms->done = 0;
-            ms->done_pending = 0;
-            ms->n_above = 0;
-            ms->n_inbin = 0;
+            ms->mu = dd_add(ms->mu, dd_two_prod(eta, eta));
+            ms->alpha = dd_add(ms->alpha, dd_add(dd_two_prod(2.0 * eta, s_bold), dd_mul_d(dd_two_prod(eta, eta), hd)));
+            ms->energy = ms->mu.hi != 0.0 ? dd_div_to_d(ms->alpha, ms->mu) : 0.0;
+            ms->nnz_c += eta != 0.0 ? 1 : 0;
+            ms->n_slots += s_ins;
+            ms->inserted += s_ins;
         }
     }
 }
@@ -1302,9 +1317,9 @@ cudaError_t mc_configure() {
     return cudaSuccess;
 }
 
-cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
-                           cudaStream_t s) {
-    k_mc_init<<<1, 64, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.w, b.thr, b.eta, A, B);
+cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
+                            double eta, int first, cudaStream_t s) {
+    k_mc_start<<<1, 64, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.w, b.thr, b.eta, A, B, eta, first);
     return cudaGetLastError();
 }
 

@@ -103,7 +103,10 @@ struct CdRecord {                  // written at the end of a launch, read at th
     double mu_g;                   // the mu used in the gradients of the last column
     double dx, energy;
     long long iterations, nnz_c, n_slots, elements, applied, dropped, inserted, last_column;
-    int forced;                    // 1: the next launch processes (a, b, slot) with eta = 1 (start vector)
+    unsigned long long fa, fb;     // forced coordinate of the next step (a start vector's entry) ...
+    double feta;                   // ... and its step (its c value)
+    int forced;                    // 1: the next step takes (fa, fb) with eta = feta instead of the argmax
+    int have_prev;                 // 1: (a, b, slot) was processed and the partials of its column are pending
     int done;                      // 1: dx < threshold; later launches only forward the state
 };
 

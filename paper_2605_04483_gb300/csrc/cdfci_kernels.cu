@@ -349,6 +349,7 @@ struct Sel {
     long long pslot;
     double pb, pc;
     double eta, mu_g;                  // step size; mu used in the gradients of this column
+    double feta;                       // forced step: the given eta
     int have_prev, forced, stop, bad;
 };
 
@@ -360,7 +361,9 @@ struct LoopState {
     dd mu, alpha;
     double dx;
     long long iterations, nnz_c, n_slots, elements, applied, dropped, inserted, last_column;
-    int forced, done;
+    unsigned long long fa, fb;         // forced next coordinate and its step
+    double feta;
+    int forced, have_prev, done;
 };
 
 // Warp-level combine: argmax of (gbits desc, key asc) with payload (slot, b, c),
@@ -500,6 +503,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     __shared__ LoopState ls;                     // written by lane 0 of the control warp (warp 0) only
     __shared__ double s_hii;
     __shared__ int s_err;
+    __shared__ int s_fins;                       // 1: this CTA inserted the forced coordinate of this step
     extern __shared__ __align__(16) unsigned char s_dyn[];
     const CdSmem lay = cd_smem_layout(P);
     SingleEnt *tabA = reinterpret_cast<SingleEnt *>(s_dyn), *tabB = tabA + P.na * P.va;
@@ -524,10 +528,12 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         ls.mu = R.mu; ls.alpha = R.alpha; ls.dx = R.dx;
         ls.iterations = R.iterations; ls.nnz_c = R.nnz_c; ls.n_slots = R.n_slots; ls.elements = R.elements;
         ls.applied = R.applied; ls.dropped = R.dropped; ls.inserted = R.inserted; ls.last_column = R.last_column;
-        ls.forced = R.forced; ls.done = 0;
+        ls.fa = R.fa; ls.fb = R.fb; ls.feta = R.feta;
+        ls.forced = R.forced; ls.have_prev = R.have_prev; ls.done = 0;
         if (!kGrid) spart[1] = gpart[rank];
         s_err = 0;
         s_done = 0;
+        s_fins = 0;
     }
     if (kGrid) __syncthreads(); else cluster.sync();
 
@@ -554,18 +560,13 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         const int pin = lastp, pout = lastp ^ 1;
         // ---- choice of i (Eq. choose-i), by the control warp ----
         if (warp == 0) {
-            if (ls.forced) {
-                if (lane == 0) {
-                    sel.iA = ls.pA; sel.iB = ls.pB; sel.islot = ls.pslot; sel.bi = 0.0; sel.ci = 0.0;
-                    sel.have_prev = 0; sel.forced = 1; sel.stop = 0;
-                }
-            } else {
-                // every CTA's partial of the last column: lane l folds CTAs l, l + 32, ...
-                // (all lanes take part in the combine)
-                Best bb{0ull, ~0ull, ~0ull, -1};
-                double bj = 0.0, cj = 0.0, gsum = 0.0;
-                int cnt[4] = {0, 0, 0, 0};
-                int err = 0;
+            // every CTA's partial of the last column: lane l folds CTAs l, l + 32, ...
+            // (all lanes take part in the combine)
+            Best bb{0ull, ~0ull, ~0ull, -1};
+            double bj = 0.0, cj = 0.0, gsum = 0.0;
+            int cnt[4] = {0, 0, 0, 0};
+            int err = 0;
+            if (ls.have_prev) {
                 for (int r = lane; r < G; r += 64) {           // two loads in flight per lane
                     const bool two = r + 32 < G;
                     const CdPartial x0 = kGrid ? ldcg_partial(gbuf[pin] + r) : *cluster.map_shared_rank(&spart[pin], r);
@@ -575,29 +576,54 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                     if (two) fold_partial(x1, false, bb, bj, cj, gsum, cnt, err);
                 }
                 warp_combine(bb, bj, cj, gsum, cnt, err);
-                if (lane == 0) {
+            }
+            if (lane == 0) {
+                long long nslots = ls.n_slots;
+                double pb = 0.0;
+                unsigned long long gp = 0ull;
+                if (ls.have_prev) {
                     // recalculated b of the previous coordinate (Eq. recalculate-b) and its gradient
-                    const double pb = fma(ls.pHii, ls.pc, gsum);
-                    const unsigned long long gp = abs_bits(fma(ls.pmu_g, ls.pc, pb));
-                    const long long nslots = ls.n_slots + cnt[3];
-                    sel.pA = ls.pA; sel.pB = ls.pB; sel.pslot = ls.pslot; sel.pb = pb; sel.pc = ls.pc;
-                    sel.have_prev = 1; sel.forced = 0;
-                    if (better(gp, ls.pA, ls.pB, bb.g, bb.a, bb.b)) {
-                        sel.iA = ls.pA; sel.iB = ls.pB; sel.islot = ls.pslot; sel.bi = pb; sel.ci = ls.pc;
-                        sel.stop = (err != 0) || (nslots > P.max_entries);
-                    } else {
-                        sel.iA = bb.a; sel.iB = bb.b; sel.islot = bb.slot; sel.bi = bj; sel.ci = cj;
-                        sel.stop = (err != 0) || (nslots > P.max_entries) || (bb.slot < 0);
-                    }
-                    if (nslots > P.max_entries) set_status(st, kErrTableFull);
+                    pb = fma(ls.pHii, ls.pc, gsum);
+                    gp = abs_bits(fma(ls.pmu_g, ls.pc, pb));
+                    nslots += cnt[3];
                     const long long pdiag = ls.pHii != 0.0 ? 1 : 0;
                     ls.elements += cnt[0] + pdiag;
                     ls.applied += cnt[1] + pdiag;
                     ls.dropped += cnt[2];
                     ls.inserted += cnt[3];
-                    ls.n_slots = nslots;
                     ls.last_column = cnt[0] + pdiag;
                 }
+                sel.pA = ls.pA; sel.pB = ls.pB; sel.pslot = ls.pslot; sel.pb = pb; sel.pc = ls.pc;
+                sel.have_prev = ls.have_prev;
+                if (ls.forced) {
+                    // a start vector's entry: insert it if absent; its c and b as stored now.  The
+                    // previous coordinate's recalculated b is written by the element thread that meets
+                    // it in this column; an entry more than a double excitation away has no such
+                    // element, so CTA 0 writes it here.
+                    if (ls.have_prev && rank == 0 &&
+                        __popcll(ls.pA ^ ls.fa) + __popcll(ls.pB ^ ls.fb) > 4)
+                        P.table[ls.pslot].bv = pb;
+                    // every CTA looks the entry up; the one whose insert wins counts it in its partial
+                    bool ins = false;
+                    const long long fs = table_find(P, st, ls.fa, ls.fb, true, &ins);
+                    s_fins = ins ? 1 : 0;
+                    sel.iA = ls.fa; sel.iB = ls.fb; sel.islot = fs;
+                    sel.ci = fs >= 0 ? __ldcg(&P.table[fs].c) : 0.0;
+                    sel.bi = fs >= 0 ? __ldcg(&P.table[fs].bv) : 0.0;
+                    sel.feta = ls.feta;
+                    sel.forced = 1;
+                    sel.stop = (err != 0) || (fs < 0) || (nslots > P.max_entries);
+                } else if (better(gp, ls.pA, ls.pB, bb.g, bb.a, bb.b)) {
+                    sel.iA = ls.pA; sel.iB = ls.pB; sel.islot = ls.pslot; sel.bi = pb; sel.ci = ls.pc;
+                    sel.forced = 0;
+                    sel.stop = (err != 0) || (nslots > P.max_entries);
+                } else {
+                    sel.iA = bb.a; sel.iB = bb.b; sel.islot = bb.slot; sel.bi = bj; sel.ci = cj;
+                    sel.forced = 0;
+                    sel.stop = (err != 0) || (nslots > P.max_entries) || (bb.slot < 0);
+                }
+                if (nslots > P.max_entries) set_status(st, kErrTableFull);
+                ls.n_slots = nslots;
             }
         }
         __syncthreads();
@@ -623,7 +649,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 const double bi = sel.bi, ci = sel.ci;
                 double eta;
                 if (sel.forced) {
-                    eta = 1.0;
+                    eta = sel.feta;
                 } else {
                     const double mu0 = ls.pmu_g;          // c.c within 2 ulp (the double-double value runs behind)
                     eta = line_search(4.0 * bi + 4.0 * mu0 * ci, 2.0 * Hii + 4.0 * ci * ci + 2.0 * mu0, 4.0 * ci);
@@ -791,7 +817,8 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 CdPartial pp;
                 pp.gbits = b.g; pp.ka = b.a; pp.kb = b.b; pp.slot = b.slot;
                 pp.bj = bj; pp.cj = cj; pp.gather = gs;
-                pp.elements = c4[0]; pp.applied = c4[1]; pp.dropped = c4[2]; pp.inserted = c4[3];
+                pp.elements = c4[0]; pp.applied = c4[1]; pp.dropped = c4[2]; pp.inserted = c4[3] + s_fins;
+                s_fins = 0;
                 pp.err = s_err | (bad ? 1 : 0);
                 if (kGrid) gbuf[pout][rank] = pp; else spart[pout] = pp;
                 // the coordinate's own slot: c_i += eta, b_i as used (rank 0 writes)
@@ -813,6 +840,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 }
                 ls.nnz_c += ((ci == 0.0 && ci_new != 0.0) ? 1 : 0) - ((ci != 0.0 && ci_new == 0.0) ? 1 : 0);
                 ls.forced = 0;
+                ls.have_prev = 1;
                 s_done = ls.done;
             }
         }
@@ -837,7 +865,8 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         o.energy = dd_div_to_d(ls.alpha, ls.mu);
         o.iterations = ls.iterations; o.nnz_c = ls.nnz_c; o.n_slots = ls.n_slots; o.elements = ls.elements;
         o.applied = ls.applied; o.dropped = ls.dropped; o.inserted = ls.inserted; o.last_column = ls.last_column;
-        o.forced = ls.forced; o.done = ls.done;
+        o.fa = ls.fa; o.fb = ls.fb; o.feta = ls.feta;
+        o.forced = ls.forced; o.have_prev = ls.have_prev; o.done = ls.done;
         *rec = o;
     }
 }
@@ -883,7 +912,7 @@ __device__ __forceinline__ void cd_finalize_body(const Problem &P, IterState *st
     // the same per-lane fold (CTAs lane, lane + 32, ...) and tree as the loop's choice
     double gsum = 0.0;
     long long cnt[4] = {0, 0, 0, 0};
-    if (!R.forced)
+    if (R.have_prev)
         for (int r = lane; r < G; r += 32) {
             const CdPartial x = gpart[r];
             gsum = (r == lane) ? x.gather : gsum + x.gather;
@@ -894,8 +923,8 @@ __device__ __forceinline__ void cd_finalize_body(const Problem &P, IterState *st
         for (int k = 0; k < 4; ++k) cnt[k] += __shfl_down_sync(0xffffffffu, cnt[k], off);
     }
     if (lane != 0) return;
-    const long long pdiag = (!R.forced && R.Hii != 0.0) ? 1 : 0;
-    if (!R.forced && st->status == 0) P.table[R.slot].bv = fma(R.Hii, R.c_new, gsum);
+    const long long pdiag = (R.have_prev && R.Hii != 0.0) ? 1 : 0;
+    if (R.have_prev && st->status == 0) P.table[R.slot].bv = fma(R.Hii, R.c_new, gsum);
     st->iterations = R.iterations;
     st->nnz_c = R.nnz_c;
     st->n_slots = R.n_slots + cnt[3];
@@ -903,7 +932,7 @@ __device__ __forceinline__ void cd_finalize_body(const Problem &P, IterState *st
     st->applied = R.applied + cnt[1] + pdiag;
     st->dropped = R.dropped + cnt[2];
     st->inserted = R.inserted + cnt[3];
-    st->last_column = R.forced ? 0 : cnt[0] + pdiag;
+    st->last_column = R.have_prev ? cnt[0] + pdiag : 0;
     st->mu = R.mu;
     st->alpha = R.alpha;
     st->dx = R.dx;
@@ -971,6 +1000,96 @@ __global__ void k_export(Problem P, const IterState *st, unsigned long long *key
             if (c) c[pos] = sl.c * s;
             if (b) b[pos] = sl.bv * s;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / restore
+// ---------------------------------------------------------------------------
+// Every stored entry as stored (c, b divided by the scale for m > 1); flags
+// bit 0: the entry is marked as a candidate of the next block selection.
+__global__ void k_ckpt_export(Problem P, unsigned long long *keys, double *c, double *b, unsigned char *flags,
+                              long long cap, unsigned long long *counter) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.capacity;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Slot sl = P.table[i];
+        if (sl.a == 0ull && sl.b == 0ull) continue;
+        const unsigned long long pos = atomicAdd(counter, 1ull);
+        if ((long long)pos >= cap) continue;
+        keys[2 * pos] = sl.a;
+        keys[2 * pos + 1] = sl.b & kKeyMaskB;
+        c[pos] = sl.c;
+        b[pos] = sl.bv;
+        flags[pos] = (sl.b & kMarkB) ? 1 : 0;
+    }
+}
+
+// The pending partials of the last m = 1 column folded by one warp exactly as
+// the next step's choice folds them (lane l takes CTAs l, l + 32, ...; then
+// the warp combine); lane 0 writes the result.
+__global__ void k_ckpt_fold(const CdPartial *gpart, int G, CdPartial *out) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    Best bb{0ull, ~0ull, ~0ull, -1};
+    double bj = 0.0, cj = 0.0, gsum = 0.0;
+    int cnt[4] = {0, 0, 0, 0};
+    int err = 0;
+    for (int r = lane; r < G; r += 32) fold_partial(gpart[r], r == lane, bb, bj, cj, gsum, cnt, err);
+    warp_combine(bb, bj, cj, gsum, cnt, err);
+    if (lane == 0) {
+        CdPartial x;
+        x.gather = gsum; x.gbits = bb.g; x.ka = bb.a; x.kb = bb.b; x.slot = bb.slot;
+        x.bj = bj; x.cj = cj;
+        x.elements = cnt[0]; x.applied = cnt[1]; x.dropped = cnt[2]; x.inserted = cnt[3];
+        x.err = err;
+        *out = x;
+    }
+}
+
+// Re-insert checkpoint rows (the table is empty): c and b as stored; rows with
+// flag bit 0 are marked and listed as candidates (m > 1).  A key found instead
+// of inserted (a repeated row) is a consistency error.
+__global__ void k_ckpt_import(Problem P, IterState *st, const unsigned long long *keys, const double *c,
+                              const double *b, const unsigned char *flags, long long n, long long *cand,
+                              int *n_cand, long long cap_cand) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        bool ins = false;
+        const long long s = table_find(P, st, keys[2 * i], keys[2 * i + 1], true, &ins);
+        if (s < 0) continue;                                  // table full: status set
+        if (!ins) { set_status(st, kErrInternal); continue; }
+        P.table[s].c = c[i];
+        P.table[s].bv = b[i];
+        if (flags && (flags[i] & 1) && cand) {
+            P.table[s].b = keys[2 * i + 1] | kMarkB;
+            const int pos = atomicAdd(n_cand, 1);
+            if (pos < cap_cand) cand[pos] = s;
+            else set_status(st, kErrInternal);
+        }
+    }
+}
+
+// m = 1 restore after the rows are in: the record (slots looked up by key) and
+// the pending partials, the folded one at CTA 0 and empty ones elsewhere.
+__global__ void k_ckpt_restore_m1(Problem P, IterState *st, CdRecord *rec, CdPartial *gpart, int G, CdRecord r,
+                                  CdPartial folded) {
+    if (threadIdx.x == 0) {
+        bool ins = false;
+        if (r.have_prev) {
+            r.slot = table_find(P, st, r.a, r.b, false, &ins);
+            if (r.slot < 0) { set_status(st, kErrInternal); r.slot = 0; }
+        }
+        if (folded.slot >= 0) {
+            folded.slot = table_find(P, st, folded.ka, folded.kb, false, &ins);
+            if (folded.slot < 0) set_status(st, kErrInternal);
+        }
+        *rec = r;
+        gpart[0] = folded;
+    }
+    for (int k = 1 + threadIdx.x; k < G; k += blockDim.x) {
+        CdPartial e;
+        e.gather = 0.0; e.gbits = 0ull; e.ka = ~0ull; e.kb = ~0ull; e.slot = -1; e.bj = 0.0; e.cj = 0.0;
+        e.elements = 0; e.applied = 0; e.dropped = 0; e.inserted = 0; e.err = 0;
+        gpart[k] = e;
     }
 }
 
@@ -1123,24 +1242,34 @@ __global__ void k_w3v3(const double *g, int N, double *W3, double *V3) {
 // Insert the start determinant and write the record that makes the next
 // iteration the initialisation: c = e_ref reached from c = 0 with eta = 1,
 // so mu = 1 and alpha = H_ref,ref.
-__global__ void k_init_state(Problem P, IterState *st, CdRecord *rec, unsigned long long A, unsigned long long B) {
+// The record of a fresh start: nothing processed yet, the next step forced onto
+// {A, B} with step eta (from c = 0: c = eta e_{A,B}, the start vector of r4).
+__global__ void k_init_state(IterState *st, CdRecord *rec, unsigned long long A, unsigned long long B, double eta) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    bool ins = false;
-    long long s = table_find(P, st, A, B, true, &ins);
-    if (s < 0) { set_status(st, kErrTableFull); s = 0; }
     CdRecord r;
-    r.a = A; r.b = B; r.slot = s;
+    r.a = 0ull; r.b = 0ull; r.slot = 0;
     r.c_new = 0.0; r.Hii = 0.0; r.eta = 0.0;
     r.mu = dd_from(0.0); r.alpha = dd_from(0.0);
     r.dx = 0.0; r.energy = 0.0;
-    r.iterations = 0; r.nnz_c = 0; r.n_slots = 1; r.elements = 0; r.applied = 0; r.dropped = 0;
-    r.inserted = 1; r.last_column = 0;
+    r.iterations = 0; r.nnz_c = 0; r.n_slots = 0; r.elements = 0; r.applied = 0; r.dropped = 0;
+    r.inserted = 0; r.last_column = 0;
+    r.fa = A; r.fb = B; r.feta = eta;
     r.forced = 1;
+    r.have_prev = 0;
     r.done = 0;
     r.mu_g = 0.0;
     rec[0] = r;
     st->last_parity = 0;
     st->scale = dd_from(1.0);
+}
+
+// The next step forced onto start-vector entry k (keys 2k, 2k + 1; step c[k]).
+__global__ void k_force_next(CdRecord *rec, const unsigned long long *keys, const double *c, long long k) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    rec->fa = keys[2 * k];
+    rec->fb = keys[2 * k + 1];
+    rec->feta = c[k];
+    rec->forced = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -1295,6 +1424,35 @@ cudaError_t launch_export(const Problem &P, const IterState *st, unsigned long l
     return cudaGetLastError();
 }
 
+cudaError_t launch_ckpt_export(const Problem &P, unsigned long long *keys, double *c, double *b, unsigned char *flags,
+                               long long cap, unsigned long long *counter, cudaStream_t s) {
+    long long grid = (P.capacity + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_ckpt_export<<<(int)grid, 256, 0, s>>>(P, keys, c, b, flags, cap, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ckpt_fold(const CdPartial *gpart, int G, CdPartial *out, cudaStream_t s) {
+    k_ckpt_fold<<<1, 32, 0, s>>>(gpart, G, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ckpt_import(const Problem &P, IterState *st, const unsigned long long *keys, const double *c,
+                               const double *b, const unsigned char *flags, long long n, long long *cand, int *n_cand,
+                               long long cap_cand, cudaStream_t s) {
+    long long grid = (n + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    k_ckpt_import<<<(int)grid, 256, 0, s>>>(P, st, keys, c, b, flags, n, cand, n_cand, cap_cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ckpt_restore_m1(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart, int G,
+                                   const CdRecord &r, const CdPartial &folded, cudaStream_t s) {
+    k_ckpt_restore_m1<<<1, 256, 0, s>>>(P, st, rec, gpart, G, r, folded);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long long cap, unsigned long long *counter,
                       double *partial, int nblocks, double *out, cudaStream_t s) {
     long long grid = (P.capacity + 255) / 256;
@@ -1320,9 +1478,15 @@ cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_state(const Problem &P, IterState *st, CdRecord *rec, unsigned long long A,
-                              unsigned long long B, cudaStream_t s) {
-    k_init_state<<<1, 32, 0, s>>>(P, st, rec, A, B);
+cudaError_t launch_init_state(IterState *st, CdRecord *rec, unsigned long long A, unsigned long long B, double eta,
+                              cudaStream_t s) {
+    k_init_state<<<1, 32, 0, s>>>(st, rec, A, B, eta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_next(CdRecord *rec, const unsigned long long *keys, const double *c, long long k,
+                              cudaStream_t s) {
+    k_force_next<<<1, 32, 0, s>>>(rec, keys, c, k);
     return cudaGetLastError();
 }
 

@@ -21,8 +21,19 @@ cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long lon
 cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, double *W3, double *V3, int *status,
                          int *has_doubles,
                          cudaStream_t s);
-cudaError_t launch_init_state(const Problem &P, IterState *st, CdRecord *rec, unsigned long long A,
-                              unsigned long long B, cudaStream_t s);
+cudaError_t launch_init_state(IterState *st, CdRecord *rec, unsigned long long A, unsigned long long B, double eta,
+                              cudaStream_t s);
+cudaError_t launch_force_next(CdRecord *rec, const unsigned long long *keys, const double *c, long long k,
+                              cudaStream_t s);
+// checkpoint / restore
+cudaError_t launch_ckpt_export(const Problem &P, unsigned long long *keys, double *c, double *b, unsigned char *flags,
+                               long long cap, unsigned long long *counter, cudaStream_t s);
+cudaError_t launch_ckpt_fold(const CdPartial *gpart, int G, CdPartial *out, cudaStream_t s);
+cudaError_t launch_ckpt_import(const Problem &P, IterState *st, const unsigned long long *keys, const double *c,
+                               const double *b, const unsigned char *flags, long long n, long long *cand, int *n_cand,
+                               long long cap_cand, cudaStream_t s);
+cudaError_t launch_ckpt_restore_m1(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart, int G,
+                                   const CdRecord &r, const CdPartial &folded, cudaStream_t s);
 
 // Device buffers of the multicoordinate iteration.
 struct McBuffers {
@@ -36,12 +47,13 @@ struct McBuffers {
     float *Rh, *Rl;                // reduced matrix R as float-float pairs, leading dimension ldr
     int ldr;
     int m, cand_grid, scatter_grid, tpc, nchunk, chunk;
+    long long cap_cand;            // entries of cand / gkey / ties
 };
 size_t mc_eigen_smem(int m);
 int mc_max_m();
 cudaError_t mc_configure();
-cudaError_t launch_mc_init(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
-                           cudaStream_t s);
+cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
+                            double eta, int first, cudaStream_t s);
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s);
 

@@ -37,6 +37,8 @@ def test_every_declared_symbol_is_exported(built):
 
 
 def test_struct_layouts_match_header(built, tmp_path):
+    ck = built.cdfci_checkpoint_header
+    ck_lines = "\n".join(f"  F(cdfci_checkpoint_header, {f})" for f, _ in ck._fields_)
     src = tmp_path / "layout.c"
     src.write_text("""
 #include <stdio.h>
@@ -53,6 +55,8 @@ int main(void) {
   F(cdfci_stats, grid_blocks) F(cdfci_stats, grid_wide)
   F(cdfci_tune_report, chosen) F(cdfci_tune_report, m) F(cdfci_tune_report, grid_blocks) F(cdfci_tune_report, iterations) F(cdfci_tune_report, seconds)
   F(cdfci_tune_report, energy_drop) F(cdfci_tune_report, score)
+  printf("cdfci_checkpoint_header %zu\\n", sizeof(cdfci_checkpoint_header));
+""" + ck_lines + """
   return 0;
 }
 """)
@@ -64,10 +68,11 @@ int main(void) {
     assert int(vals["cdfci_params"]) == ctypes.sizeof(P)
     assert int(vals["cdfci_stats"]) == ctypes.sizeof(S)
     assert int(vals["cdfci_tune_report"]) == ctypes.sizeof(R)
+    assert int(vals["cdfci_checkpoint_header"]) == ctypes.sizeof(ck)
     for k, v in vals.items():
         if "." in k:
             t, f = k.split(".")
-            cls = {"cdfci_params": P, "cdfci_stats": S, "cdfci_tune_report": R}[t]
+            cls = {"cdfci_params": P, "cdfci_stats": S, "cdfci_tune_report": R, "cdfci_checkpoint_header": ck}[t]
             assert getattr(cls, f).offset == int(v), k
 
 
