@@ -95,6 +95,23 @@ def lib():
         L.orc_candidates.argtypes = [ctypes.c_void_p, c_u64p, ctypes.c_int64]
         L.orc_step_choice.restype = ctypes.c_int
         L.orc_step_choice.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, c_dp, c_dp]
+        L.orx_create.restype = ctypes.c_void_p
+        L.orx_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_dp, c_u64p, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_double]
+        L.orx_destroy.restype = None
+        L.orx_destroy.argtypes = [ctypes.c_void_p]
+        L.orx_step.restype = ctypes.c_int
+        L.orx_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        L.orx_energies.restype = ctypes.c_int
+        L.orx_energies.argtypes = [ctypes.c_void_p, c_dp]
+        L.orx_info.restype = None
+        L.orx_info.argtypes = [ctypes.c_void_p, c_dp, c_dp, c_dp]
+        L.orx_export.restype = ctypes.c_int64
+        L.orx_export.argtypes = [ctypes.c_void_p, c_u64p, c_dp, c_dp, ctypes.c_int64]
+        L.orx_last_step.restype = None
+        L.orx_last_step.argtypes = [ctypes.c_void_p, c_u64p, c_dp]
+        L.orx_quartic.restype = None
+        L.orx_quartic.argtypes = [ctypes.c_int, c_dp, c_dp, c_dp, ctypes.c_double, c_dp]
         L.orc_set_initial.restype = ctypes.c_int
         L.orc_set_initial.argtypes = [ctypes.c_void_p, c_u64p, c_dp, ctypes.c_int64]
         L.orc_rdm.restype = ctypes.c_int
@@ -325,3 +342,70 @@ def orbital_gradient(h: np.ndarray, g: np.ndarray, g1: np.ndarray, g2: np.ndarra
     dE = 1/2 sum_pq G_pq dkappa_pq for an antisymmetric dkappa."""
     F = h @ g1.T + np.einsum("prst,qrst->pq", g, g2)
     return 2.0 * (F - F.T)
+
+
+def xcd_quartic(c, g, S, Hii) -> np.ndarray:
+    """w0..w4 of h(eta) = f(C + eta e_i g) - f(C) from the oracle (w0 = 0)."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    w = np.zeros(5)
+    lib().orx_quartic(len(c), _d(c), _d(g), _d(S), float(Hii), _d(w))
+    return w
+
+
+class XCDFCI:
+    """Serial Algorithm 3 (xCDFCI) for k1 = K + 1 states from start determinants keys (k1, 2)."""
+
+    def __init__(self, N, na, nb, h, g, keys, tau=0.0, theta=0.9):
+        self.h, self.g = _ints(h, g)
+        self.N, self.k1 = N, len(keys)
+        self._keys = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+        self._p = lib().orx_create(N, na, nb, _d(self.h), _d(self.g),
+                                   self._keys.ctypes.data_as(c_u64p), self.k1, float(tau), float(theta))
+        if not self._p:
+            raise ValueError("oracle xCDFCI create failed")
+
+    def step(self, n: int = 1):
+        r = lib().orx_step(self._p, int(n))
+        if r:
+            raise RuntimeError(f"oracle xCDFCI step failed ({r})")
+
+    def energies(self) -> np.ndarray:
+        E = np.zeros(self.k1)
+        if lib().orx_energies(self._p, _d(E)):
+            raise RuntimeError("S is not positive definite")
+        return E
+
+    def info(self) -> dict:
+        S = np.zeros((self.k1, self.k1))
+        M = np.zeros((self.k1, self.k1))
+        out = np.zeros(6)
+        lib().orx_info(self._p, _d(S), _d(M), _d(out))
+        return {"S": S, "M": M, "dx": out[0], "iterations": int(out[1]), "entries": int(out[2]),
+                "elements": int(out[3]), "applied": int(out[4]), "dropped": int(out[5])}
+
+    def export(self):
+        n = self.info()["entries"]
+        keys = np.zeros((n, 2), dtype=np.uint64)
+        C = np.zeros((n, self.k1))
+        B = np.zeros((n, self.k1))
+        lib().orx_export(self._p, keys.ctypes.data_as(c_u64p), _d(C), _d(B), n)
+        return keys, C, B
+
+    def last_step(self):
+        k = np.zeros(2, dtype=np.uint64)
+        e = ctypes.c_double()
+        lib().orx_last_step(self._p, k.ctypes.data_as(c_u64p), ctypes.byref(e))
+        return k, e.value
+
+    def close(self):
+        if self._p:
+            lib().orx_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1086,3 +1086,307 @@ int orc_step_choice(orc_state *st, uint64_t A, uint64_t B, double *g_choice, dou
     st->ncand = 1;
     return step_cd(st);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3 (xCDFCI): K + 1 states, one row of C per step                  */
+/* ------------------------------------------------------------------------ */
+/*
+ * State: rows C_{D,:}, B_{D,:} = (H C)_{D,:} (k1 = K + 1 values each), the
+ * (k1 x k1) matrices S = C^T C and M = C^T H C in binary128, the candidate
+ * list.  Readings (the paper leaves them open):
+ *   - start: C = [e_{D_0} ... e_{D_K}] for k1 given determinants, built as k1
+ *     forced row steps (row D_k += 1 * e_k) in order, each column scattered
+ *     with the compression rule; candidates afterwards = every start column;
+ *   - compression of B rows: row j is updated iff some C_{j,k} != 0 or
+ *     max_k |eta H_ji g_k| >= tau (an absent row only in the second case);
+ *   - h'(0) = <G, e_i g> = ||G_i||^2 (G = 4B + 4CS already holds the factor 4):
+ *     w1 = ||g||^2, and the eta^2 terms of the S and M updates are the outer
+ *     product g^T g;
+ *   - candidates after a step: the rows the column updated, plus i;
+ *   - ties of ||G_i||_inf: the smaller key; dx <- theta dx + (1 - theta) |eta| ||g||_2.
+ */
+#define XK_MAX 8
+typedef struct {
+    int N, na, nb, k1;
+    const double *h, *g;
+    double tau, theta;
+    dmap map;
+    int64_t n, cap;
+    det_t *key;
+    double *C, *B;                 /* n x k1 each */
+    quad S[XK_MAX * XK_MAX], M[XK_MAX * XK_MAX];
+    double dx;
+    int64_t iter, elements, applied, dropped;
+    int64_t ncand, candcap;
+    int64_t *cand;
+    det_t last_key;
+    double last_eta;
+} orx_state;
+
+static int64_t orx_entry(orx_state *st, det_t d, int insert) {
+    int64_t k = dmap_get(&st->map, d);
+    if (k >= 0 || !insert) return k;
+    if (st->n == st->cap) {
+        int64_t nc = 2 * st->cap;
+        det_t *nk = (det_t *)realloc(st->key, (size_t)nc * sizeof(det_t));
+        if (!nk) return -2;
+        st->key = nk;
+        double *ncc = (double *)realloc(st->C, (size_t)nc * st->k1 * sizeof(double));
+        if (!ncc) return -2;
+        st->C = ncc;
+        double *nbb = (double *)realloc(st->B, (size_t)nc * st->k1 * sizeof(double));
+        if (!nbb) return -2;
+        st->B = nbb; st->cap = nc;
+    }
+    k = st->n++;
+    st->key[k] = d;
+    for (int a = 0; a < st->k1; a++) { st->C[k * st->k1 + a] = 0.0; st->B[k * st->k1 + a] = 0.0; }
+    if (dmap_put(&st->map, d, k) < 0) return -2;
+    return k;
+}
+
+static int orx_cand_push(orx_state *st, int64_t k) {
+    if (st->ncand == st->candcap) {
+        int64_t nc = 2 * st->candcap;
+        int64_t *p = (int64_t *)realloc(st->cand, (size_t)nc * sizeof(int64_t));
+        if (!p) return -1;
+        st->cand = p; st->candcap = nc;
+    }
+    st->cand[st->ncand++] = k;
+    return 0;
+}
+
+/* B += H_{:,i} w (w = eta g, k1 values) with the row compression rule; recalc = sum_j H_ji C_{j,:} */
+static int orx_scatter(orx_state *st, det_t Di, const double *w, double *recalc, dmap *seen) {
+    const int k1 = st->k1;
+    colbuf col;
+    if (colbuf_init(&col, 1024)) return -1;
+    if (column_sc_buf(st->N, st->h, st->g, Di, &col)) { colbuf_free(&col); return -1; }
+    for (int a = 0; a < k1; a++) recalc[a] = 0.0;
+    for (int64_t t = 0; t < col.n; t++) {
+        double Hji = col.v[t];
+        if (Hji == 0.0) continue;
+        st->elements++;
+        det_t dj = col.d[t];
+        int64_t k = orx_entry(st, dj, 0);
+        int cnz = 0;
+        double vmax = 0.0;
+        double upd[XK_MAX];
+        for (int a = 0; a < k1; a++) {
+            upd[a] = Hji * w[a];
+            if (fabs(upd[a]) > vmax) vmax = fabs(upd[a]);
+            if (k >= 0 && st->C[k * k1 + a] != 0.0) cnz = 1;
+        }
+        if (cnz || vmax >= st->tau) {
+            if (k < 0) { k = orx_entry(st, dj, 1); if (k < 0) { colbuf_free(&col); return -1; } }
+            for (int a = 0; a < k1; a++) st->B[k * k1 + a] += upd[a];
+            st->applied++;
+            if (dmap_get(seen, dj) < 0) { dmap_put(seen, dj, k); if (orx_cand_push(st, k)) { colbuf_free(&col); return -1; } }
+        } else {
+            st->dropped++;
+        }
+        if (k >= 0)
+            for (int a = 0; a < k1; a++) recalc[a] += Hji * st->C[k * k1 + a];
+    }
+    colbuf_free(&col);
+    return 0;
+}
+
+/* the row update C_i += eta g with its column, the recalculated B_i and the S, M updates */
+static int orx_row_step(orx_state *st, det_t Di, double eta, const double *g, dmap *seen) {
+    const int k1 = st->k1;
+    int64_t i = orx_entry(st, Di, 1);
+    if (i < 0) return -1;
+    double c[XK_MAX], b[XK_MAX], w[XK_MAX], rc[XK_MAX];
+    for (int a = 0; a < k1; a++) { c[a] = st->C[i * k1 + a]; b[a] = st->B[i * k1 + a]; w[a] = eta * g[a]; }
+    double Hii = diag_sc(st->N, st->h, st->g, Di);
+    for (int a = 0; a < k1; a++)
+        for (int bb = 0; bb < k1; bb++) {
+            quad ga = (quad)g[a], gb = (quad)g[bb], e = (quad)eta;
+            st->S[a * k1 + bb] += e * ((quad)c[a] * gb + ga * (quad)c[bb]) + e * e * ga * gb;
+            st->M[a * k1 + bb] += e * ((quad)b[a] * gb + ga * (quad)b[bb]) + e * e * (quad)Hii * ga * gb;
+        }
+    for (int a = 0; a < k1; a++) st->C[i * k1 + a] = c[a] + w[a];
+    if (orx_scatter(st, Di, w, rc, seen)) return -1;
+    i = orx_entry(st, Di, 0);
+    for (int a = 0; a < k1; a++) st->B[i * k1 + a] = rc[a];
+    if (dmap_get(seen, Di) < 0) { dmap_put(seen, Di, i); if (orx_cand_push(st, i)) return -1; }
+    st->last_key = Di; st->last_eta = eta;
+    return 0;
+}
+
+/*
+ * Coefficients w1..w4 of h(eta) = f(C + eta e_i g) - f(C) (appendix
+ * "Determining Step Size", problem choose-eta) from the row c = C_i, g, S and
+ * H_ii; w[0] is set to 0 (f(C) itself is not needed).
+ */
+void orx_quartic(int k1, const double *c, const double *g, const double *S, double Hii, double *w) {
+    double gg = 0.0, cg = 0.0, cc = 0.0, gSg = 0.0;
+    for (int a = 0; a < k1; a++) {
+        gg += g[a] * g[a]; cg += c[a] * g[a]; cc += c[a] * c[a];
+        for (int b = 0; b < k1; b++) gSg += g[a] * S[a * k1 + b] * g[b];
+    }
+    w[0] = 0.0;
+    w[1] = gg;
+    w[2] = 2.0 * Hii * gg + 2.0 * cg * cg + 2.0 * cc * gg + 2.0 * gSg;
+    w[3] = 4.0 * gg * cg;
+    w[4] = gg * gg;
+}
+
+orx_state *orx_create(int N, int na, int nb, const double *h, const double *g, const uint64_t *keys, int k1,
+                      double tau, double theta) {
+    if (N < 1 || N > 64 || k1 < 1 || k1 > XK_MAX) return NULL;
+    orx_state *st = (orx_state *)calloc(1, sizeof(orx_state));
+    if (!st) return NULL;
+    st->N = N; st->na = na; st->nb = nb; st->k1 = k1; st->h = h; st->g = g; st->tau = tau; st->theta = theta;
+    st->cap = 1024;
+    st->key = (det_t *)malloc((size_t)st->cap * sizeof(det_t));
+    st->C = (double *)malloc((size_t)st->cap * k1 * sizeof(double));
+    st->B = (double *)malloc((size_t)st->cap * k1 * sizeof(double));
+    st->candcap = 1024;
+    st->cand = (int64_t *)malloc((size_t)st->candcap * sizeof(int64_t));
+    if (!st->key || !st->C || !st->B || !st->cand || dmap_init(&st->map, 1024)) return NULL;
+    dmap seen;
+    if (dmap_init(&seen, 1024)) return NULL;
+    for (int k = 0; k < k1; k++) {
+        det_t D = {keys[2 * k], keys[2 * k + 1]};
+        double e[XK_MAX];
+        for (int a = 0; a < k1; a++) e[a] = (a == k) ? 1.0 : 0.0;
+        if (orx_entry(st, D, 0) >= 0) {
+            int nz = 0;
+            int64_t q = orx_entry(st, D, 0);
+            for (int a = 0; a < k1; a++) nz |= st->C[q * k1 + a] != 0.0;
+            if (nz) { dmap_free(&seen); return NULL; }       /* a repeated start determinant */
+        }
+        if (orx_row_step(st, D, 1.0, e, &seen)) { dmap_free(&seen); return NULL; }
+    }
+    dmap_free(&seen);
+    st->dx = 0.0; st->iter = 0;
+    return st;
+}
+
+void orx_destroy(orx_state *st) {
+    if (!st) return;
+    dmap_free(&st->map);
+    free(st->key); free(st->C); free(st->B); free(st->cand);
+    free(st);
+}
+
+static double orx_gnorm_inf(const orx_state *st, int64_t k, const double *S, double *G) {
+    const int k1 = st->k1;
+    double m = 0.0;
+    for (int a = 0; a < k1; a++) {
+        double s = 0.0;
+        for (int b = 0; b < k1; b++) s += st->C[k * k1 + b] * S[b * k1 + a];
+        G[a] = 4.0 * st->B[k * k1 + a] + 4.0 * s;
+        if (fabs(G[a]) > m) m = fabs(G[a]);
+    }
+    return m;
+}
+
+/* one iteration of Algorithm 3 */
+static int orx_step1(orx_state *st) {
+    const int k1 = st->k1;
+    double S[XK_MAX * XK_MAX], G[XK_MAX], g[XK_MAX];
+    for (int a = 0; a < k1 * k1; a++) S[a] = (double)st->S[a];
+    int64_t best = -1;
+    double gbest = -1.0;
+    for (int64_t t = 0; t < st->ncand; t++) {
+        int64_t k = st->cand[t];
+        double gk = orx_gnorm_inf(st, k, S, G);
+        if (best < 0 || gk > gbest || (gk == gbest && det_less(st->key[k], st->key[best]))) {
+            best = k; gbest = gk;
+            for (int a = 0; a < k1; a++) g[a] = G[a];
+        }
+    }
+    if (best < 0) return -3;
+    det_t Di = st->key[best];
+    double c[XK_MAX];
+    for (int a = 0; a < k1; a++) c[a] = st->C[best * k1 + a];
+    double Hii = diag_sc(st->N, st->h, st->g, Di);
+    double w[5];
+    orx_quartic(k1, c, g, S, Hii, w);
+    double eta = 0.0;
+    if (w[4] > 0.0) eta = orc_line_search(w[1] / w[4], w[2] / w[4], w[3] / w[4]);
+    st->ncand = 0;
+    dmap seen;
+    if (dmap_init(&seen, 1024)) return -1;
+    int r = orx_row_step(st, Di, eta, g, &seen);
+    dmap_free(&seen);
+    if (r) return -1;
+    double gn = 0.0;
+    for (int a = 0; a < k1; a++) gn += g[a] * g[a];
+    st->dx = st->theta * st->dx + (1.0 - st->theta) * fabs(eta) * sqrt(gn);
+    st->iter++;
+    return 0;
+}
+
+int orx_step(orx_state *st, int64_t n) {
+    for (int64_t t = 0; t < n; t++) {
+        int r = orx_step1(st);
+        if (r) return r;
+    }
+    return 0;
+}
+
+/* energies: the k1 eigenvalues of the pencil (M, S), ascending (S = L L^T, eig of L^-1 M L^-T) */
+int orx_energies(const orx_state *st, double *E) {
+    const int k1 = st->k1;
+    double L[XK_MAX * XK_MAX] = {0}, A[XK_MAX * XK_MAX], T[XK_MAX * XK_MAX], V[XK_MAX * XK_MAX];
+    for (int i = 0; i < k1; i++)
+        for (int j = 0; j <= i; j++) {
+            double s = (double)st->S[i * k1 + j];
+            for (int k = 0; k < j; k++) s -= L[i * k1 + k] * L[j * k1 + k];
+            if (i == j) {
+                if (!(s > 0.0)) return -1;
+                L[i * k1 + i] = sqrt(s);
+            } else {
+                L[i * k1 + j] = s / L[j * k1 + j];
+            }
+        }
+    /* T = L^-1 M (forward substitution per column), A = T L^-T */
+    for (int col = 0; col < k1; col++)
+        for (int i = 0; i < k1; i++) {
+            double s = (double)st->M[i * k1 + col];
+            for (int k = 0; k < i; k++) s -= L[i * k1 + k] * T[k * k1 + col];
+            T[i * k1 + col] = s / L[i * k1 + i];
+        }
+    for (int row = 0; row < k1; row++)
+        for (int i = 0; i < k1; i++) {
+            double s = T[row * k1 + i];
+            for (int k = 0; k < i; k++) s -= L[i * k1 + k] * A[row * k1 + k];
+            A[row * k1 + i] = s / L[i * k1 + i];
+        }
+    for (int i = 0; i < k1; i++)
+        for (int j = 0; j < i; j++) {
+            double s = 0.5 * (A[i * k1 + j] + A[j * k1 + i]);
+            A[i * k1 + j] = s; A[j * k1 + i] = s;
+        }
+    jacobi_eig(k1, A, E, V);
+    for (int i = 0; i < k1; i++)
+        for (int j = i + 1; j < k1; j++)
+            if (E[j] < E[i]) { double t = E[i]; E[i] = E[j]; E[j] = t; }
+    return 0;
+}
+
+/* S, M (as doubles, k1 x k1 each), dx, iterations, entries, elements, applied, dropped */
+void orx_info(const orx_state *st, double *S, double *M, double *out) {
+    const int k1 = st->k1;
+    for (int a = 0; a < k1 * k1; a++) { S[a] = (double)st->S[a]; M[a] = (double)st->M[a]; }
+    out[0] = st->dx; out[1] = (double)st->iter; out[2] = (double)st->n;
+    out[3] = (double)st->elements; out[4] = (double)st->applied; out[5] = (double)st->dropped;
+}
+
+int64_t orx_export(const orx_state *st, uint64_t *keys, double *C, double *B, int64_t cap) {
+    const int k1 = st->k1;
+    int64_t n = st->n < cap ? st->n : cap;
+    for (int64_t k = 0; k < n; k++) {
+        keys[2 * k] = st->key[k].a; keys[2 * k + 1] = st->key[k].b;
+        for (int a = 0; a < k1; a++) { C[k * k1 + a] = st->C[k * k1 + a]; B[k * k1 + a] = st->B[k * k1 + a]; }
+    }
+    return st->n;
+}
+
+void orx_last_step(const orx_state *st, uint64_t *key, double *eta) {
+    key[0] = st->last_key.a; key[1] = st->last_key.b; *eta = st->last_eta;
+}
