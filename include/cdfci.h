@@ -76,6 +76,12 @@ typedef struct {
                                   per b_j per iteration); m > 1 adds several columns' contributions to
                                   one b_j with FP64 atomics, whose order (last-bit rounding) can vary */
     void    *cuda_stream;      /* cudaStream_t the work is queued on; NULL = a library stream */
+    int32_t  num_states;       /* K + 1: 1 = ground state; 2..8 = xCDFCI (Alg. 3, Sec. "Coordinate-Descent
+                                  Methods for Excited States") for the K + 1 lowest states, with
+                                  num_coordinates = 1.  Start rows: the reference determinant and the K
+                                  determinants of its column with the lowest diagonal H_DD (ties: the
+                                  smaller key), C = [e_{D_0} .. e_{D_K}] */
+    int32_t  reserved0;
 } cdfci_params;
 
 /* Progress report (the console row of Sec. "Expected Console Output"). */
@@ -153,6 +159,24 @@ int cdfci_get_column(cdfci_handle h, const uint64_t *key, uint64_t *keys_out, do
  * may be NULL); *n_out = number stored.  CDFCI_ERR_CAPACITY if cap is too small.
  */
 int cdfci_export(cdfci_handle h, uint64_t *keys, double *c, double *b, int64_t cap, int64_t *n_out);
+
+/*
+ * xCDFCI handles (num_states = K + 1 > 1): the K + 1 energies, ascending, from
+ * the pencil (C^T H C, C^T C) of the current rows (the generalised eigenvalue
+ * problem that closes Alg. 3); *n_out = K + 1 (1 and the Rayleigh quotient for
+ * other handles).  CDFCI_ERR_CAPACITY if cap < K + 1.
+ */
+int cdfci_energies(cdfci_handle h, double *E, int32_t cap, int32_t *n_out);
+
+/*
+ * All stored determinants with their rows C_{D,:} and B_{D,:} = (HC)_{D,:}
+ * (num_states values each, row-major), in table order; for other handles the
+ * same as cdfci_export (one value each).  CDFCI_ERR_CAPACITY if cap is too small
+ * (*n_out = number stored).  The columns of C span the K + 1 lowest eigenvectors
+ * at convergence; they are not orthonormal (Sec. "Coordinate-Descent Methods
+ * for Excited States": the pencil gives the eigenvectors).
+ */
+int cdfci_export_states(cdfci_handle h, uint64_t *keys, double *C, double *B, int64_t cap, int64_t *n_out);
 
 /*
  * Start vector (optional, replaces the state): c = sum_k c[k] e_{keys k},

@@ -29,7 +29,7 @@ class cdfci_params(ctypes.Structure):
                 ("ref_alpha", ctypes.c_uint64), ("ref_beta", ctypes.c_uint64),
                 ("block_threads", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("graph_chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("num_states", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class cdfci_tune_report(ctypes.Structure):
@@ -107,6 +107,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_int64), vp]
         L.cdfci_column_noalloc.restype = ctypes.c_int
         L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
+        L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.cdfci_export_states.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_checkpoint.argtypes = [vp, ctypes.POINTER(cdfci_checkpoint_header), u64p, dp, dp, ctypes.c_void_p, i64]
         L.cdfci_restore.argtypes = [vp, ctypes.POINTER(cdfci_checkpoint_header), u64p, dp, dp, ctypes.c_void_p]
         L.cdfci_destroy.argtypes = [vp]
@@ -198,6 +200,28 @@ def cdfci_export(handle: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     b = np.zeros(max(cap, 1))
     _check(lib().cdfci_export(handle, _ptr(keys), _ptr(c), _ptr(b), cap, ctypes.byref(n)))
     return keys[:n.value], c[:n.value], b[:n.value]
+
+
+def cdfci_energies(handle: int, cap: int = 8) -> np.ndarray:
+    """The K + 1 energies of an xCDFCI handle (ascending); one for other handles."""
+    E = np.zeros(cap)
+    n = ctypes.c_int32()
+    _check(lib().cdfci_energies(handle, _ptr(E), cap, ctypes.byref(n)))
+    return E[:n.value].copy()
+
+
+def cdfci_export_states(handle: int, k1: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Keys (n, 2) and rows C, B (n, k1) of every stored determinant."""
+    n = ctypes.c_int64()
+    rc = lib().cdfci_export_states(handle, None, None, None, 0, ctypes.byref(n))
+    if rc not in (CDFCI_OK, -8):
+        _check(rc)
+    cap = n.value
+    keys = np.zeros((max(cap, 1), 2), dtype=np.uint64)
+    C = np.zeros((max(cap, 1), k1))
+    B = np.zeros((max(cap, 1), k1))
+    _check(lib().cdfci_export_states(handle, _ptr(keys), _ptr(C), _ptr(B), cap, ctypes.byref(n)))
+    return keys[:n.value], C[:n.value], B[:n.value]
 
 
 def cdfci_set_initial(handle: int, keys, c) -> None:
@@ -343,6 +367,12 @@ class Solver:
 
     def set_initial(self, keys, c):
         cdfci_set_initial(self.handle, keys, c)
+
+    def energies(self) -> np.ndarray:
+        return cdfci_energies(self.handle)
+
+    def export_states(self):
+        return cdfci_export_states(self.handle, max(1, int(self.p.num_states)))
 
     def checkpoint(self) -> dict:
         return cdfci_checkpoint(self.handle)

@@ -97,6 +97,10 @@ struct cdfci_ctx {
     int mb_nalloc = 0;
     int mchunk = 8;                              // iterations per captured graph
     cudaGraphExec_t mgraph = nullptr;
+    // xCDFCI (num_states = K + 1 > 1)
+    bool xcd = false;
+    int k1 = 1;
+    XBuffers xb{};
 };
 
 namespace {
@@ -131,7 +135,8 @@ int run_iterations(cdfci_ctx *c, long long n) {
 int stats_from_snapshot(cdfci_ctx *c, cdfci_stats *s);
 
 int fill_stats(cdfci_ctx *c, cdfci_stats *s) {
-    if (!c->block) CK(launch_cd_finalize(c->P, c->d_st, c->d_rec, c->d_part, c->grid, c->stream));
+    if (c->xcd) CK(launch_x_energies(c->xb, c->stream));
+    else if (!c->block) CK(launch_cd_finalize(c->P, c->d_st, c->d_rec, c->d_part, c->grid, c->stream));
     CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return stats_from_snapshot(c, s);
@@ -157,7 +162,7 @@ int stats_from_snapshot(cdfci_ctx *c, cdfci_stats *s) {
         s->status = t.status;
         s->converged = t.done;
         s->reduced_iterations = t.eig_iters;
-        s->grid_blocks = c->block ? 0 : c->grid;
+        s->grid_blocks = (c->block || c->xcd) ? 0 : c->grid;
         s->grid_wide = c->gridmode ? 1 : 0;
     }
     if (t.status != 0) {
@@ -203,6 +208,80 @@ int setup_block(cdfci_ctx *c, int m) {
         mb_alloc(c, &b.gathp, (size_t)m * b.nchunk))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
     CK(mc_configure());
+    return CDFCI_OK;
+}
+
+// xCDFCI buffers and the start rows: the reference and the K determinants of
+// its column with the lowest diagonal (ties: the smaller key).
+int setup_xcd(cdfci_ctx *c, int k1, unsigned long long refA, unsigned long long refB) {
+    XBuffers &b = c->xb;
+    const Problem &P = c->P;
+    cudaStream_t s = c->stream;
+    const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
+    c->k1 = k1;
+    b.nscatter = x_scatter_blocks();
+    b.nselect = 152;
+    b.cap_cand = (long long)k1 * (nh_eff + 1) + 64;
+    if (mb_alloc(c, &b.xs, 1) || mb_alloc(c, &b.rows, (size_t)P.capacity * 2 * k1) ||
+        mb_alloc(c, &b.cand, (size_t)b.cap_cand) || mb_alloc(c, &b.gathp, (size_t)b.nscatter * k1) ||
+        mb_alloc(c, reinterpret_cast<unsigned char **>(&b.bbest), (size_t)b.nselect * x_block_bytes()) ||
+        mb_alloc(c, &b.counter, 1))
+        return fail(CDFCI_ERR_NOMEM, "device allocation of the xCDFCI buffers failed");
+    b.st = c->d_st;
+    XState x;
+    memset(&x, 0, sizeof(x));
+    x.k1 = k1;
+    CK(cudaMemcpyAsync(b.xs, &x, sizeof(x), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(b.rows, 0, (size_t)P.capacity * 2 * k1 * sizeof(double), s));
+    CK(cudaMemsetAsync(b.counter, 0, sizeof(unsigned int), s));
+    // the reference column and its diagonals
+    CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s));
+    CK(launch_column(P, refA, refB, c->d_colkeys, c->d_colvals, P.nh, c->d_counter, s));
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, c->d_counter, sizeof(n), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<unsigned long long> keys(2 * n);
+    std::vector<double> diag(n);
+    double *dd_ = nullptr;
+    if (n > 0) {
+        if (cudaMalloc(&dd_, n * sizeof(double)) != cudaSuccess) return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+        cudaError_t e = launch_x_diag_list(P, c->d_colkeys, (long long)n, dd_, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(keys.data(), c->d_colkeys, 2 * n * sizeof(unsigned long long),
+                                                  cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(diag.data(), dd_, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(dd_);
+        if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "start rows: %s", cudaGetErrorString(e));
+    }
+    struct Cand { double d; unsigned long long a, b; };
+    std::vector<Cand> cs;
+    for (unsigned long long k = 0; k < n; ++k)
+        if (!(keys[2 * k] == refA && keys[2 * k + 1] == refB)) cs.push_back({diag[k], keys[2 * k], keys[2 * k + 1]});
+    std::sort(cs.begin(), cs.end(), [](const Cand &x, const Cand &y) {
+        if (x.d != y.d) return x.d < y.d;
+        return x.b != y.b ? x.b < y.b : x.a < y.a;
+    });
+    if ((int)cs.size() < k1 - 1)
+        return fail(CDFCI_ERR_ARG, "num_states = %d: the reference column has only %d other determinants", k1,
+                    (int)cs.size());
+    CK(launch_x_start(P, b, refA, refB, 0, s));
+    for (int k = 1; k < k1; ++k) CK(launch_x_start(P, b, cs[k - 1].a, cs[k - 1].b, k, s));
+    return CDFCI_OK;
+}
+
+int build_xcd_graph(cdfci_ctx *c) {
+    cudaGraph_t got = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < c->mchunk && e == cudaSuccess; ++i) e = launch_x_iteration(c->P, c->xb, c->stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &got);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (got) cudaGraphDestroy(got);
+        return fail(CDFCI_ERR_CUDA, "capture of the xCDFCI iteration failed");
+    }
+    e = cudaGraphInstantiate(&c->mgraph, got, 0);
+    cudaGraphDestroy(got);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     return CDFCI_OK;
 }
 
@@ -303,6 +382,7 @@ CDFCI_API void cdfci_default_params(cdfci_params *p) {
     p->dx_damping = 0.9;
     p->dx_threshold = 0.0;
     p->deterministic = 1;
+    p->num_states = 1;
 }
 
 CDFCI_API const char *cdfci_last_error(void) { return g_last_error.c_str(); }
@@ -319,6 +399,11 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
     if (params) prm = *params; else cdfci_default_params(&prm);
     if (prm.num_coordinates < 1 || prm.num_coordinates > mc_max_m())
         return fail(CDFCI_ERR_ARG, "num_coordinates = %d outside [1, %d]", prm.num_coordinates, mc_max_m());
+    if (prm.num_states == 0) prm.num_states = 1;
+    if (prm.num_states < 1 || prm.num_states > kXMax)
+        return fail(CDFCI_ERR_ARG, "num_states = %d outside [1, %d]", prm.num_states, kXMax);
+    if (prm.num_states > 1 && prm.num_coordinates != 1)
+        return fail(CDFCI_ERR_ARG, "num_states = %d needs num_coordinates = 1 (Alg. 3 updates one row)", prm.num_states);
     if (prm.log2_capacity < 4 || prm.log2_capacity > 34)
         return fail(CDFCI_ERR_ARG, "log2_capacity = %d outside [4, 34]", prm.log2_capacity);
     if (!(prm.max_load > 0.0 && prm.max_load <= 0.95)) return fail(CDFCI_ERR_ARG, "max_load must be in (0, 0.95]");
@@ -472,6 +557,18 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         for (int k = 0; k < n_alpha; ++k) refA |= 1ull << order[k];
         for (int k = 0; k < n_beta; ++k) refB |= 1ull << order[k];
     }
+    if (prm.num_states > 1) {
+        c->xcd = true;
+        if (prm.graph_chunk > 0) c->mchunk = prm.graph_chunk;
+        rc = setup_xcd(c, prm.num_states, refA, refB);
+        if (rc != CDFCI_OK) return bail(rc);
+        rc = fill_stats(c, nullptr);
+        if (rc != CDFCI_OK) return bail(rc);
+        rc = build_xcd_graph(c);
+        if (rc != CDFCI_OK) return bail(rc);
+        *out = c;
+        return CDFCI_OK;
+    }
     if (prm.num_coordinates > 1) {
         c->block = true;
         rc = setup_block(c, prm.num_coordinates);
@@ -502,9 +599,10 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
 CDFCI_API int cdfci_step(cdfci_handle c, int64_t n_iter, cdfci_stats *stats) {
     if (!c) return fail(CDFCI_ERR_ARG, "handle is NULL");
     if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
-    if (c->block) {
+    if (c->block || c->xcd) {
         for (int64_t i = 0; i < n_iter / c->mchunk; ++i) CK(cudaGraphLaunch(c->mgraph, c->stream));
-        for (int64_t i = 0; i < n_iter % c->mchunk; ++i) CK(launch_mc_iteration(c->P, c->mb, c->stream));
+        for (int64_t i = 0; i < n_iter % c->mchunk; ++i)
+            CK(c->xcd ? launch_x_iteration(c->P, c->xb, c->stream) : launch_mc_iteration(c->P, c->mb, c->stream));
         return fill_stats(c, stats);
     }
     int rc = run_iterations(c, n_iter);
@@ -526,6 +624,7 @@ CDFCI_API int cdfci_energy(cdfci_handle c, int mode, double *E) {
         return CDFCI_OK;
     }
     if (mode != 1) return fail(CDFCI_ERR_ARG, "mode must be 0 or 1");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "exact recompute (mode 1) is for one state; use cdfci_energies");
     int rc = fill_stats(c, nullptr);
     if (rc) return rc;
     long long n = c->h_st->n_slots;
@@ -575,8 +674,54 @@ CDFCI_API int cdfci_get_column(cdfci_handle c, const uint64_t *key, uint64_t *ke
     return CDFCI_OK;
 }
 
+CDFCI_API int cdfci_energies(cdfci_handle c, double *E, int32_t cap, int32_t *n_out) {
+    if (!c || !E || !n_out) return fail(CDFCI_ERR_ARG, "NULL argument");
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    *n_out = c->k1;
+    if (cap < c->k1) return fail(CDFCI_ERR_CAPACITY, "%d energies, cap is %d", c->k1, (int)cap);
+    if (!c->xcd) {
+        E[0] = c->h_st->energy;
+        return CDFCI_OK;
+    }
+    XState x;
+    CK(cudaMemcpy(&x, c->xb.xs, sizeof(x), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < c->k1; ++a) E[a] = x.E[a];
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_export_states(cdfci_handle c, uint64_t *keys, double *C, double *B, int64_t cap,
+                                  int64_t *n_out) {
+    if (!c || !n_out) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (!c->xcd) return cdfci_export(c, keys, C, B, cap, n_out);
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    const long long n = c->h_st->n_slots, k1 = c->k1;
+    *n_out = n;
+    if (n > cap) return fail(CDFCI_ERR_CAPACITY, "%lld entries stored, cap is %lld", n, (long long)cap);
+    if (n == 0) return CDFCI_OK;
+    unsigned long long *dk = nullptr;
+    double *dc = nullptr, *db = nullptr;
+    if (cudaMalloc(&dk, (size_t)n * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&dc, (size_t)n * k1 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&db, (size_t)n * k1 * sizeof(double)) != cudaSuccess) {
+        cudaFree(dk); cudaFree(dc); cudaFree(db);
+        return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = launch_x_export(c->P, c->xb, c->k1, dk, dc, db, n, c->d_counter, c->stream);
+    if (e == cudaSuccess && keys) e = cudaMemcpyAsync(keys, dk, (size_t)n * 2 * sizeof(uint64_t), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && C) e = cudaMemcpyAsync(C, dc, (size_t)n * k1 * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && B) e = cudaMemcpyAsync(B, db, (size_t)n * k1 * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(dk); cudaFree(dc); cudaFree(db);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "export_states: %s", cudaGetErrorString(e));
+    return CDFCI_OK;
+}
+
 CDFCI_API int cdfci_export(cdfci_handle c, uint64_t *keys, double *cv, double *bv, int64_t cap, int64_t *n_out) {
     if (!c || !n_out) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "a num_states > 1 handle stores rows: use cdfci_export_states");
     int rc = fill_stats(c, nullptr);
     if (rc) return rc;
     long long n = c->h_st->n_slots;
@@ -604,6 +749,7 @@ CDFCI_API int cdfci_export(cdfci_handle c, uint64_t *keys, double *cv, double *b
 
 CDFCI_API int cdfci_set_initial(cdfci_handle c, const uint64_t *keys, const double *cv, int64_t n) {
     if (!c || !keys || !cv) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "start vectors are for one state (num_states = 1)");
     if (n < 1) return fail(CDFCI_ERR_ARG, "n = %lld, need at least one entry", (long long)n);
     if (c->block && n > c->mb.m)
         return fail(CDFCI_ERR_ARG, "%lld entries for m = %d: a block handle takes at most m start entries", (long long)n,
@@ -649,6 +795,7 @@ CDFCI_API int cdfci_set_initial(cdfci_handle c, const uint64_t *keys, const doub
 CDFCI_API int cdfci_checkpoint(cdfci_handle c, cdfci_checkpoint_header *hdr, uint64_t *keys, double *cv, double *bv,
                                uint8_t *flags, int64_t cap) {
     if (!c || !hdr) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "checkpoints are for one state (num_states = 1)");
     int rc = fill_stats(c, nullptr);                   // m = 1: the pending b of the last coordinate is in the table
     if (rc) return rc;
     cdfci_checkpoint_header h;
@@ -716,6 +863,7 @@ CDFCI_API int cdfci_checkpoint(cdfci_handle c, cdfci_checkpoint_header *hdr, uin
 CDFCI_API int cdfci_restore(cdfci_handle c, const cdfci_checkpoint_header *hdr, const uint64_t *keys, const double *cv,
                             const double *bv, const uint8_t *flags) {
     if (!c || !hdr || !keys || !cv || !bv) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "checkpoints are for one state (num_states = 1)");
     const cdfci_checkpoint_header h = *hdr;
     if (h.version != 1) return fail(CDFCI_ERR_ARG, "checkpoint version %d, expected 1", h.version);
     if (h.N != c->N || h.n_alpha != c->na || h.n_beta != c->nb)
@@ -817,6 +965,7 @@ int rdm_device(cdfci_ctx *c, double *g1, double *g2) {
 
 CDFCI_API int cdfci_rdm(cdfci_handle c, double *rdm1, double *rdm2) {
     if (!c || !rdm1) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "RDMs are for one state (num_states = 1)");
     int rc = fill_stats(c, nullptr);
     if (rc) return rc;
     const size_t n2 = (size_t)c->P.N * c->P.N, n4 = n2 * n2;
@@ -838,6 +987,7 @@ CDFCI_API int cdfci_rdm(cdfci_handle c, double *rdm1, double *rdm2) {
 
 CDFCI_API int cdfci_gradient(cdfci_handle c, double *dE_dh, double *dE_dg, double *dE_dkappa) {
     if (!c) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "gradients are for one state (num_states = 1)");
     int rc = fill_stats(c, nullptr);
     if (rc) return rc;
     const int N = c->P.N;
@@ -906,6 +1056,7 @@ CDFCI_API int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_hand
     for (int k = 0; k < n; ++k) {
         if (!hs[k]) return fail(CDFCI_ERR_ARG, "handle %d is NULL", k);
         if (hs[k]->block) return fail(CDFCI_ERR_ARG, "handle %d has num_coordinates > 1 (batches take m = 1 solvers)", k);
+        if (hs[k]->xcd) return fail(CDFCI_ERR_ARG, "handle %d has num_states > 1 (batches take one-state solvers)", k);
         if (hs[k]->gridmode)
             return fail(CDFCI_ERR_ARG, "handle %d runs on %d CTAs, more than a cluster (batches take grid_blocks <= 16)",
                         k, hs[k]->grid);
@@ -973,6 +1124,7 @@ CDFCI_API int cdfci_autotune(const double *h, const double *g, int N, int n_alph
                              double seconds, cdfci_tune_report *report) {
     if (!params) return fail(CDFCI_ERR_ARG, "NULL params");
     if (!(seconds > 0.0)) return fail(CDFCI_ERR_ARG, "seconds must be > 0");
+    if (params->num_states > 1) return fail(CDFCI_ERR_ARG, "the autotuner picks m for one state (num_states = 1)");
     struct Cand { int m, grid; };
     std::vector<Cand> cs;
     cs.push_back({1, params->grid_blocks});
@@ -1030,6 +1182,16 @@ CDFCI_API int cdfci_last_step(cdfci_handle c, uint64_t *keys, double *eta, int64
     if (!c || !m_out) return fail(CDFCI_ERR_ARG, "NULL argument");
     int rc = fill_stats(c, nullptr);
     if (rc) return rc;
+    if (c->xcd) {
+        XState x;
+        CK(cudaMemcpy(&x, c->xb.xs, sizeof(x), cudaMemcpyDeviceToHost));
+        *m_out = 1;
+        if (cap < 1) return fail(CDFCI_ERR_CAPACITY, "cap < 1");
+        uint64_t k[2] = {x.A, x.B};
+        if (keys) CK(cudaMemcpy(keys, k, sizeof(k), cudaMemcpyDefault));
+        if (eta) CK(cudaMemcpy(eta, &x.eta, sizeof(double), cudaMemcpyDefault));
+        return CDFCI_OK;
+    }
     if (c->block) {
         McState ms;
         CK(cudaMemcpy(&ms, c->mb.ms, sizeof(ms), cudaMemcpyDeviceToHost));

@@ -153,6 +153,24 @@ struct McState {
     long long eig_iters_total;
 };
 
+// xCDFCI (Algorithm 3, k1 = K + 1 states) iteration state, one per handle.
+// Rows of C and B live beside the table: rows[slot * 2 k1 + a] = C_{slot,a},
+// rows[slot * 2 k1 + k1 + a] = B_{slot,a}.
+constexpr int kXMax = 8;
+struct XState {
+    dd S[kXMax * kXMax], M[kXMax * kXMax];   // C^T C, C^T H C (double-double)
+    double g[kXMax];               // G_i of the chosen row (4 B_i + 4 C_i S)
+    double wv[kXMax];              // scatter weights eta g
+    double thr;                    // |H_ji| >= thr passes the compression rule: tau / max_a |eta g_a|
+    double eta, dx, Hii;
+    double E[kXMax];               // energies of the pencil (M, S), ascending (on request)
+    long long slot;                // chosen row
+    unsigned long long A, B;
+    long long iterations, nnz_c, n_slots, elements, applied, dropped, inserted, last_column;
+    unsigned long long cnt[4];     // counters of the running column
+    int n_cand, k1, done;
+};
+
 // Everything a kernel needs about the problem and the table.
 struct Problem {
     int N, na, nb, va, vb;

@@ -25,6 +25,29 @@ cudaError_t launch_init_state(IterState *st, CdRecord *rec, unsigned long long A
                               cudaStream_t s);
 cudaError_t launch_force_next(CdRecord *rec, const unsigned long long *keys, const double *c, long long k,
                               cudaStream_t s);
+// xCDFCI (Algorithm 3): k1 = K + 1 states
+struct XBuffers {
+    XState *xs;
+    IterState *st;
+    double *rows;                  // capacity x 2 k1: C row, B row
+    long long *cand;               // candidate slots (deduplicated by the mark)
+    long long cap_cand;
+    double *gathp;                 // per scatter block: k1 gather sums
+    void *bbest;                   // per select block: its best candidate
+    unsigned int *counter;         // last-block counter of the selection
+    int nscatter, nselect;
+};
+int x_scatter_blocks();
+size_t x_block_bytes();
+cudaError_t launch_x_start(const Problem &P, const XBuffers &b, unsigned long long A, unsigned long long B, int k,
+                           cudaStream_t s);
+cudaError_t launch_x_iteration(const Problem &P, const XBuffers &b, cudaStream_t s);
+cudaError_t launch_x_energies(const XBuffers &b, cudaStream_t s);
+cudaError_t launch_x_export(const Problem &P, const XBuffers &b, int k1, unsigned long long *keys, double *C,
+                            double *B, long long cap, unsigned long long *counter, cudaStream_t s);
+cudaError_t launch_x_diag_list(const Problem &P, const unsigned long long *keys, long long n, double *out,
+                               cudaStream_t s);
+
 // checkpoint / restore
 cudaError_t launch_ckpt_export(const Problem &P, unsigned long long *keys, double *c, double *b, unsigned char *flags,
                                long long cap, unsigned long long *counter, cudaStream_t s);

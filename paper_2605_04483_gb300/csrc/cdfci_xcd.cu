@@ -1,0 +1,495 @@
+// xCDFCI (Algorithm 3): K + 1 states, one row of C per iteration.
+//
+// Per iteration four launches (captured in a CUDA graph):
+//   k_x_select    argmax over the candidates of ||G_j||_inf, G_j = 4 B_j + 4 C_j S
+//                 (ties: the smaller key), by a block argmax and a last-block
+//                 reduction in block order; clears the candidates' marks;
+//   k_x_prepare   H_ii, the quartic of problem choose-eta (appendix "Determining
+//                 Step Size") and its minimiser eta, C_i += eta G_i, the S and M
+//                 updates (double-double, one entry per lane);
+//   k_x_scatter   B_j += eta H_ji G_i for the column of i with the row compression
+//                 rule, insertion of absent rows, the gather sum_j H_ji C_j per
+//                 block, the rows it updated become the next candidates;
+//   k_x_finalize  B_i = H_ii C_i + the gather (Eq. recalculate-b, per state),
+//                 counters.
+// The energies (the pencil (M, S)) are computed on request by k_x_energies.
+// Each row j occurs once in a column, so B_j is updated by plain loads and
+// stores, and every reduction has a fixed order: the iteration is
+// deterministic.
+#include <algorithm>
+
+#include "cdfci_internal.cuh"
+#include "cdfci_kernels.h"
+
+namespace cdfci {
+
+namespace {
+
+struct XBest {
+    unsigned long long gbits, a, b;
+    long long slot;
+};
+
+// |x| as its bit pattern (monotone in |x| for non-negative doubles)
+__device__ __forceinline__ unsigned long long x_abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ bool x_better(const XBest &x, const XBest &y) {
+    if (x.slot < 0) return false;
+    if (y.slot < 0) return true;
+    return x.gbits > y.gbits || (x.gbits == y.gbits && key_less(x.a, x.b, y.a, y.b));
+}
+
+__device__ __forceinline__ double x_gnorm(const double *row, const double *S, int k1, double *G) {
+    double m = 0.0;
+    for (int a = 0; a < kXMax; ++a) {
+        if (a >= k1) break;
+        double s = 0.0;
+        for (int b = 0; b < kXMax; ++b) {
+            if (b >= k1) break;
+            s = fma(row[b], S[b * k1 + a], s);
+        }
+        const double ga = 4.0 * row[k1 + a] + 4.0 * s;
+        if (G) G[a] = ga;
+        m = fmax(m, fabs(ga));
+    }
+    return m;
+}
+
+}  // namespace
+
+constexpr int kXThreads = 256;
+
+__global__ void __launch_bounds__(kXThreads) k_x_select(Problem P, XState *xs, IterState *st, const long long *cand,
+                                                        const double *rows, XBest *bbest, unsigned int *counter) {
+    __shared__ double sS[kXMax * kXMax];
+    __shared__ XBest wb[kXThreads / 32];
+    __shared__ bool s_last;
+    if (xs->done || st->status) return;
+    const int k1 = xs->k1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = tid; t < k1 * k1; t += blockDim.x) sS[t] = xs->S[t].hi + xs->S[t].lo;
+    __syncthreads();
+    const int n = xs->n_cand;
+    XBest best{0ull, ~0ull, ~0ull, -1};
+    for (int t = blockIdx.x * blockDim.x + tid; t < n; t += gridDim.x * blockDim.x) {
+        const long long s = cand[t];
+        double row[2 * kXMax];
+        for (int a = 0; a < 2 * k1; ++a) row[a] = __ldcg(rows + s * 2 * k1 + a);
+        const Slot sl = P.table[s];
+        P.table[s].b = sl.b & kKeyMaskB;                           // no longer a candidate
+        const XBest x{x_abs_bits(x_gnorm(row, sS, k1, nullptr)), sl.a, sl.b & kKeyMaskB, s};
+        if (x_better(x, best)) best = x;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        XBest y;
+        y.gbits = __shfl_down_sync(0xffffffffu, best.gbits, off);
+        y.a = __shfl_down_sync(0xffffffffu, best.a, off);
+        y.b = __shfl_down_sync(0xffffffffu, best.b, off);
+        y.slot = __shfl_down_sync(0xffffffffu, best.slot, off);
+        if (x_better(y, best)) best = y;
+    }
+    if (lane == 0) wb[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+        XBest b = wb[0];
+        for (int w = 1; w < kXThreads / 32; ++w)
+            if (x_better(wb[w], b)) b = wb[w];
+        bbest[blockIdx.x] = b;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || tid != 0) return;
+    __threadfence();
+    XBest b = bbest[0];
+    for (int k = 1; k < (int)gridDim.x; ++k) {
+        const XBest y = bbest[k];
+        if (x_better(y, b)) b = y;
+    }
+    *counter = 0u;
+    xs->n_cand = 0;
+    if (b.slot < 0) { xs->done = 1; xs->eta = 0.0; return; }     // nothing left to choose
+    double row[2 * kXMax], G[kXMax];
+    for (int a = 0; a < 2 * k1; ++a) row[a] = __ldcg(rows + b.slot * 2 * k1 + a);
+    x_gnorm(row, sS, k1, G);
+    for (int a = 0; a < k1; ++a) xs->g[a] = G[a];
+    xs->slot = b.slot; xs->A = b.a; xs->B = b.b;
+}
+
+// forced >= 0: the start step of row {fA, fB} with g = e_forced and eta = 1.
+__global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, int forced, unsigned long long fA,
+                            unsigned long long fB) {
+    __shared__ ColLists L;
+    __shared__ long long s_slot;
+    __shared__ double s_c[kXMax], s_g[kXMax], s_b[kXMax];
+    __shared__ double s_eta;
+    __shared__ int s_stop;
+    if (xs->done || st->status) return;
+    const int k1 = xs->k1, lane = threadIdx.x;
+    if (lane == 0) {
+        s_stop = 0;
+        xs->eta = 0.0;                                               // 0: no step this iteration
+        if (forced >= 0) {
+            bool ins = false;
+            const long long s = table_find(P, st, fA, fB, true, &ins);
+            if (s < 0) { s_stop = 1; } else {
+                if (ins) { xs->n_slots += 1; xs->inserted += 1; }
+                xs->slot = s; xs->A = fA; xs->B = fB;
+                for (int a = 0; a < k1; ++a) xs->g[a] = a == forced ? 1.0 : 0.0;
+            }
+        }
+        s_slot = xs->slot;
+    }
+    __syncwarp();
+    if (s_stop) return;
+    build_lists(L, P.N, xs->A, xs->B);
+    __syncwarp();
+    const double Hii = diag_warp(P, L);
+    const long long s = s_slot;
+    if (lane < k1) {
+        s_c[lane] = rows[s * 2 * k1 + lane];
+        s_b[lane] = rows[s * 2 * k1 + k1 + lane];
+        s_g[lane] = xs->g[lane];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double eta = 1.0;
+        if (forced < 0) {
+            // h(eta) = f(C + eta e_i g) - f(C) = w4 eta^4 + w3 eta^3 + w2 eta^2 + w1 eta with w4 = ||g||^4,
+            // w3 = 4 ||g||^2 c.g, w2 = 2 H_ii ||g||^2 + 2 (c.g)^2 + 2 ||c||^2 ||g||^2 + 2 g S g^T,
+            // w1 = ||g||^2 (the directional derivative)
+            double gg = 0.0, cg = 0.0, cc = 0.0, gSg = 0.0;
+            for (int a = 0; a < k1; ++a) {
+                gg = fma(s_g[a], s_g[a], gg);
+                cg = fma(s_c[a], s_g[a], cg);
+                cc = fma(s_c[a], s_c[a], cc);
+                double t = 0.0;
+                for (int b = 0; b < k1; ++b) t = fma(xs->S[a * k1 + b].hi + xs->S[a * k1 + b].lo, s_g[b], t);
+                gSg = fma(s_g[a], t, gSg);
+            }
+            // In t = eta ||g|| the quartic is monic with O(1) coefficients (w / w4 would grow like
+            // 1 / ||g||^2 near convergence and overflow the single-precision root stage):
+            // t^4 + 4 (c.u) t^3 + (2 H_ii + 2 (c.u)^2 + 2 ||c||^2 + 2 u S u^T) t^2 + ||g|| t, u = g / ||g||.
+            const double gn = sqrt(gg);
+            if (!(gn > 0.0)) { xs->done = 1; s_stop = 1; }
+            else {
+                const double cu = cg / gn;
+                const double v3 = 4.0 * cu;
+                const double v2 = 2.0 * Hii + 2.0 * cu * cu + 2.0 * cc + 2.0 * (gSg / gg);
+                eta = line_search(gn, v2, v3) / gn;
+                if (!isfinite(eta)) { set_status(st, kErrNonfinite); s_stop = 1; }
+            }
+        }
+        s_eta = eta;
+    }
+    __syncwarp();
+    if (s_stop) return;
+    const double eta = s_eta;
+    // S += eta (c^T g + g^T c) + eta^2 g^T g,  M += eta (b^T g + g^T b) + eta^2 H_ii g^T g (one entry per lane)
+    for (int t = lane; t < k1 * k1; t += 32) {
+        const int a = t / k1, b = t - a * k1;
+        const dd e2 = dd_two_prod(eta, eta);
+        const dd gab = dd_two_prod(s_g[a], s_g[b]);
+        const dd ds = dd_add(dd_mul_d(dd_add(dd_two_prod(s_c[a], s_g[b]), dd_two_prod(s_g[a], s_c[b])), eta),
+                             dd_mul(e2, gab));
+        const dd dm = dd_add(dd_mul_d(dd_add(dd_two_prod(s_b[a], s_g[b]), dd_two_prod(s_g[a], s_b[b])), eta),
+                             dd_mul_d(dd_mul(e2, gab), Hii));
+        xs->S[t] = dd_add(xs->S[t], ds);
+        xs->M[t] = dd_add(xs->M[t], dm);
+    }
+    if (lane == 0) {
+        bool was = false, now = false;
+        double wmax = 0.0;
+        for (int a = 0; a < k1; ++a) {
+            const double cn = fma(eta, s_g[a], s_c[a]);
+            was = was || s_c[a] != 0.0;
+            now = now || cn != 0.0;
+            rows[s * 2 * k1 + a] = cn;
+            xs->wv[a] = eta * s_g[a];
+            wmax = fmax(wmax, fabs(eta * s_g[a]));
+        }
+        xs->nnz_c += (now ? 1 : 0) - (was ? 1 : 0);
+        xs->thr = wmax > 0.0 ? P.tau / wmax : 1.0e308;
+        xs->eta = eta;
+        xs->Hii = Hii;
+        if (forced < 0) {
+            double gn = 0.0;
+            for (int a = 0; a < k1; ++a) gn = fma(s_g[a], s_g[a], gn);
+            xs->dx = P.theta * xs->dx + (1.0 - P.theta) * fabs(eta) * sqrt(gn);
+            xs->iterations += 1;
+            if (P.dx_threshold > 0.0 && xs->dx < P.dx_threshold) xs->done = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, IterState *st, double *rows,
+                                                         long long *cand, long long cap_cand, double *gathp) {
+    __shared__ ColLists L;
+    __shared__ double sw[kXMax];
+    __shared__ double sg[kXThreads / 32][kXMax];
+    __shared__ unsigned long long s_cnt[4];
+    if (xs->eta == 0.0 || st->status) return;                        // no step this iteration
+    const int k1 = xs->k1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long A = xs->A, B = xs->B;
+    build_lists(L, P.N, A, B);
+    if (tid < k1) sw[tid] = xs->wv[tid];
+    if (tid < 4) s_cnt[tid] = 0ull;
+    __syncthreads();
+    const double thr = xs->thr;
+    const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
+    double gat[kXMax];
+    for (int a = 0; a < kXMax; ++a) gat[a] = 0.0;
+    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    for (long long e = 1 + (long long)blockIdx.x * blockDim.x + tid; e < nh; e += (long long)gridDim.x * blockDim.x) {
+        unsigned long long oa, ob;
+        const double H = column_element(P, L, A, B, e, oa, ob);
+        if (is_zero(H)) continue;
+        ++c0;
+        bool ins = false;
+        long long s = table_find(P, st, oa, ob, false, &ins);
+        double cj[kXMax];
+        bool cnz = false;
+        for (int a = 0; a < k1; ++a) {
+            cj[a] = s >= 0 ? __ldcg(rows + s * 2 * k1 + a) : 0.0;
+            cnz = cnz || cj[a] != 0.0;
+        }
+        if (!cnz && !(fabs(H) >= thr)) { ++c2; continue; }
+        if (s < 0) {
+            s = table_find(P, st, oa, ob, true, &ins);
+            if (s < 0) continue;                                      // table full: status set
+            if (ins) ++c3;
+        }
+        ++c1;
+        double *br = rows + s * 2 * k1 + k1;
+        for (int a = 0; a < k1; ++a) {
+            br[a] = fma(H, sw[a], __ldcg(br + a));
+            gat[a] = fma(H, cj[a], gat[a]);
+        }
+        const unsigned long long kb = P.table[s].b;
+        if (!(kb & kMarkB)) {
+            P.table[s].b = kb | kMarkB;
+            const int pos = atomicAdd(&xs->n_cand, 1);
+            if (pos < cap_cand) cand[pos] = s;
+            else set_status(st, kErrInternal);
+        }
+    }
+    // gather: warp tree, then warps in order (fixed order)
+    for (int a = 0; a < k1; ++a) {
+        double v = gat[a];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sg[warp][a] = v;
+    }
+    atomicAdd(&s_cnt[0], c0); atomicAdd(&s_cnt[1], c1); atomicAdd(&s_cnt[2], c2); atomicAdd(&s_cnt[3], c3);
+    __syncthreads();
+    if (tid < k1) {
+        double v = sg[0][tid];
+        for (int w = 1; w < kXThreads / 32; ++w) v += sg[w][tid];
+        gathp[(size_t)blockIdx.x * k1 + tid] = v;
+    }
+    if (tid < 4) atomicAdd(&xs->cnt[tid], s_cnt[tid]);
+}
+
+__global__ void __launch_bounds__(kXThreads) k_x_finalize(Problem P, XState *xs, IterState *st, double *rows,
+                                                          const double *gathp, int nblocks, long long *cand,
+                                                          long long cap_cand) {
+    __shared__ double red[kXThreads];
+    if (xs->eta == 0.0 || st->status) return;                        // no step this iteration
+    const int k1 = xs->k1, tid = threadIdx.x;
+    const long long s = xs->slot;
+    const double Hii = xs->Hii;
+    for (int a = 0; a < k1; ++a) {
+        double v = 0.0;
+        for (int k = tid; k < nblocks; k += blockDim.x) v += gathp[(size_t)k * k1 + a];
+        red[tid] = v;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (tid < w) red[tid] += red[tid + w];
+            __syncthreads();
+        }
+        if (tid == 0) rows[s * 2 * k1 + k1 + a] = fma(Hii, rows[s * 2 * k1 + a], red[0]);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const unsigned long long kb = P.table[s].b;
+        if (!(kb & kMarkB)) {
+            P.table[s].b = kb | kMarkB;
+            const int pos = atomicAdd(&xs->n_cand, 1);
+            if (pos < cap_cand) cand[pos] = s;
+            else set_status(st, kErrInternal);
+        }
+        const long long nd = Hii != 0.0 ? 1 : 0;
+        xs->elements += (long long)xs->cnt[0] + nd;
+        xs->applied += (long long)xs->cnt[1] + nd;
+        xs->dropped += (long long)xs->cnt[2];
+        xs->inserted += (long long)xs->cnt[3];
+        xs->n_slots += (long long)xs->cnt[3];
+        xs->last_column = (long long)xs->cnt[0] + nd;
+        for (int k = 0; k < 4; ++k) xs->cnt[k] = 0ull;
+        if (xs->n_slots > P.max_entries) set_status(st, kErrTableFull);
+    }
+}
+
+// Energies: the k1 eigenvalues of the pencil (M, S), ascending: S = L L^T
+// (Cholesky), the symmetric A = L^-1 M L^-T, cyclic Jacobi rotations (Golub &
+// Van Loan, Sec. 8.5) until the off-diagonal mass is below 1e-30 of the total.
+// One thread; also the host-visible snapshot.
+__global__ void k_x_energies(XState *xs, IterState *st) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int n = xs->k1;
+    double L[kXMax * kXMax], T[kXMax * kXMax], A[kXMax * kXMax];
+    bool ok = true;
+    for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+    for (int i = 0; i < n && ok; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = xs->S[i * n + j].hi + xs->S[i * n + j].lo;
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(s > 0.0)) { ok = false; break; }
+                L[i * n + i] = sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    if (ok) {
+        for (int col = 0; col < n; ++col)
+            for (int i = 0; i < n; ++i) {
+                double s = xs->M[i * n + col].hi + xs->M[i * n + col].lo;
+                for (int k = 0; k < i; ++k) s -= L[i * n + k] * T[k * n + col];
+                T[i * n + col] = s / L[i * n + i];
+            }
+        for (int row = 0; row < n; ++row)
+            for (int i = 0; i < n; ++i) {
+                double s = T[row * n + i];
+                for (int k = 0; k < i; ++k) s -= L[i * n + k] * A[row * n + k];
+                A[row * n + i] = s / L[i * n + i];
+            }
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < i; ++j) {
+                const double v = 0.5 * (A[i * n + j] + A[j * n + i]);
+                A[i * n + j] = v; A[j * n + i] = v;
+            }
+        for (int sweep = 0; sweep < 64; ++sweep) {
+            double off = 0.0, tot = 0.0;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    tot += A[i * n + j] * A[i * n + j];
+                    if (i != j) off += A[i * n + j] * A[i * n + j];
+                }
+            if (off <= 1e-30 * tot) break;
+            for (int p = 0; p < n; ++p)
+                for (int q = p + 1; q < n; ++q) {
+                    const double apq = A[p * n + q];
+                    if (apq == 0.0) continue;
+                    const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                    for (int k = 0; k < n; ++k) {
+                        const double akp = A[k * n + p], akq = A[k * n + q];
+                        A[k * n + p] = c * akp - sn * akq;
+                        A[k * n + q] = sn * akp + c * akq;
+                    }
+                    for (int k = 0; k < n; ++k) {
+                        const double apk = A[p * n + k], aqk = A[q * n + k];
+                        A[p * n + k] = c * apk - sn * aqk;
+                        A[q * n + k] = sn * apk + c * aqk;
+                    }
+                }
+        }
+        double E[kXMax];
+        for (int i = 0; i < n; ++i) E[i] = A[i * n + i];
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j)
+                if (E[j] < E[i]) { const double t = E[i]; E[i] = E[j]; E[j] = t; }
+        for (int i = 0; i < n; ++i) xs->E[i] = E[i];
+    } else {
+        for (int i = 0; i < n; ++i) xs->E[i] = nan("");
+    }
+    st->iterations = xs->iterations; st->nnz_c = xs->nnz_c; st->n_slots = xs->n_slots;
+    st->elements = xs->elements; st->applied = xs->applied; st->dropped = xs->dropped; st->inserted = xs->inserted;
+    st->last_column = xs->last_column;
+    st->mu = xs->S[0]; st->alpha = xs->M[0];
+    st->dx = xs->dx; st->energy = xs->E[0]; st->last_eta = xs->eta;
+    st->last_a = xs->A; st->last_b = xs->B; st->done = xs->done;
+}
+
+// Diagonal elements H_DD of a list of determinants (one warp each): picks the
+// start rows of xCDFCI.
+__global__ void k_x_diag_list(Problem P, const unsigned long long *keys, long long n, double *out) {
+    __shared__ ColLists Ls[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ColLists &L = Ls[warp];
+    for (long long k = (long long)blockIdx.x * 8 + warp; k < n; k += (long long)gridDim.x * 8) {
+        const unsigned long long A = keys[2 * k], B = keys[2 * k + 1];
+        for (int t = lane; t < P.N; t += 32) {
+            const int ra = __popcll(A & low_mask(t)), rb = __popcll(B & low_mask(t));
+            if ((A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+            if ((B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+        }
+        __syncwarp();
+        const double d = diag_warp(P, L);
+        if (lane == 0) out[k] = d;
+        __syncwarp();
+    }
+}
+
+// Every stored determinant with its rows (k1 values of C and of B).
+__global__ void k_x_export(Problem P, const double *rows, int k1, unsigned long long *keys, double *C, double *B,
+                           long long cap, unsigned long long *counter) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.capacity;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Slot sl = P.table[i];
+        if (sl.a == 0ull && sl.b == 0ull) continue;
+        const unsigned long long pos = atomicAdd(counter, 1ull);
+        if ((long long)pos >= cap) continue;
+        keys[2 * pos] = sl.a;
+        keys[2 * pos + 1] = sl.b & kKeyMaskB;
+        for (int a = 0; a < k1; ++a) {
+            C[pos * k1 + a] = rows[i * 2 * k1 + a];
+            B[pos * k1 + a] = rows[i * 2 * k1 + k1 + a];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+cudaError_t launch_x_export(const Problem &P, const XBuffers &b, int k1, unsigned long long *keys, double *C,
+                            double *B, long long cap, unsigned long long *counter, cudaStream_t s) {
+    long long grid = (P.capacity + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_x_export<<<(int)grid, 256, 0, s>>>(P, b.rows, k1, keys, C, B, cap, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_x_diag_list(const Problem &P, const unsigned long long *keys, long long n, double *out,
+                               cudaStream_t s) {
+    const long long blocks = std::min<long long>((n + 7) / 8, 1024);
+    k_x_diag_list<<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(P, keys, n, out);
+    return cudaGetLastError();
+}
+
+int x_scatter_blocks() { return 152 * 2; }
+
+size_t x_block_bytes() { return sizeof(XBest); }
+
+cudaError_t launch_x_start(const Problem &P, const XBuffers &b, unsigned long long A, unsigned long long B, int k,
+                           cudaStream_t s) {
+    k_x_prepare<<<1, 32, 0, s>>>(P, b.xs, b.st, b.rows, k, A, B);
+    k_x_scatter<<<b.nscatter, kXThreads, 0, s>>>(P, b.xs, b.st, b.rows, b.cand, b.cap_cand, b.gathp);
+    k_x_finalize<<<1, kXThreads, 0, s>>>(P, b.xs, b.st, b.rows, b.gathp, b.nscatter, b.cand, b.cap_cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_x_iteration(const Problem &P, const XBuffers &b, cudaStream_t s) {
+    k_x_select<<<b.nselect, kXThreads, 0, s>>>(P, b.xs, b.st, b.cand, b.rows, static_cast<XBest *>(b.bbest),
+                                              b.counter);
+    return launch_x_start(P, b, 0ull, 0ull, -1, s);
+}
+
+cudaError_t launch_x_energies(const XBuffers &b, cudaStream_t s) {
+    k_x_energies<<<1, 32, 0, s>>>(b.xs, b.st);
+    return cudaGetLastError();
+}
+
+}  // namespace cdfci
