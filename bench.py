@@ -224,6 +224,26 @@ def timed_block_run(api, w, m, tau, log2_capacity, warm_iters, iters, **kw) -> d
             "energy": st["energy"], "load": st["load"]}
 
 
+def timed_xcd_run(api, w, k1, tau, log2_capacity, warm_iters, iters) -> dict:
+    """xCDFCI (Algorithm 3, K + 1 = k1 states) throughput: elements/s (one column of k1-wide
+    updates per iteration) over `iters` iterations after `warm_iters`, and the energies."""
+    s = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, num_states=k1, z_threshold=tau,
+                   log2_capacity=log2_capacity, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]))
+    try:
+        s.step(warm_iters)
+        st0 = s.stats()
+        t0 = time.perf_counter()
+        st = s.step(iters)
+        dt = time.perf_counter() - t0
+        E = [float(x) for x in s.energies()]
+    finally:
+        s.close()
+    el = st["elements"] - st0["elements"]
+    return {"value": el / dt, "unit": "elements/s", "us_per_iteration": dt / iters * 1e6,
+            "elements_per_iteration": el / iters, "iterations": iters, "after_warmup_iterations": warm_iters,
+            "energies": E, "load": st["load"]}
+
+
 def fci_dim(N: int, na: int, nb: int) -> int:
     import math
     return math.comb(N, na) * math.comb(N, nb)
@@ -359,8 +379,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the device-timed value (for profiling)")
     ap.add_argument("--log2-capacity", type=int, default=WORKLOAD["log2_capacity"],
                     help="hash table size (smaller only for profiling captures)")
-    ap.add_argument("--only", choices=["mcdfci"], default=None,
-                    help="run only the m = 128 block leg on the same workload (for profiling captures)")
+    ap.add_argument("--only", choices=["mcdfci", "xcdfci"], default=None,
+                    help="run only the m = 128 block leg or the K + 1 = 4 xCDFCI leg on the same workload "
+                         "(for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -375,6 +396,14 @@ def main():
         r = timed_block_run(api, inputs.config2(), 128, WORKLOAD["tau"], args.log2_capacity, args.warmup * 10,
                             args.iters_per_step)
         print(json.dumps({"mcdfci_m128": r}))
+        return
+    if args.only == "xcdfci":
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2605_04483_gb300 import api, inputs
+        r = timed_xcd_run(api, inputs.config2(), 4, WORKLOAD["tau"], args.log2_capacity, args.warmup * 10,
+                          args.iters_per_step)
+        print(json.dumps({"xcdfci_k4": r}))
         return
 
     import numpy as np
@@ -507,6 +536,9 @@ def main():
         # ---- batched coordinate updates (mCDFCI, Algorithm 2) on the same workload ------------
         line["mcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=128, 2^27-slot table",
                               **timed_block_run(api, w, 128, WORKLOAD["tau"], 27, 200, 200))
+        # ---- excited states (xCDFCI, Algorithm 3), K + 1 = 4, same workload -------------------
+        line["xcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, K+1=4 states, 2^26-slot table",
+                              **timed_xcd_run(api, w, 4, WORKLOAD["tau"], 26, 500, 2000))
         # ---- 2D Hubbard 4x4 periodic, U=8, 8+8 (FCI dim 165,636,900), m=256, 2^28 slots ------------
         line["hubbard_4x4"] = dict(workload="hubbard_4x4_pbc_U8 (dim 1.66e8, column <= 65), m=256, 2^28-slot table",
                                    **timed_block_run(api, inputs.config3(8.0), 256, 0.0, 28, 100, 200))

@@ -100,13 +100,23 @@ __global__ void __launch_bounds__(kXThreads) k_x_select(Problem P, XState *xs, I
         s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || tid != 0) return;
+    if (!s_last || warp != 0) return;
     __threadfence();
-    XBest b = bbest[0];
-    for (int k = 1; k < (int)gridDim.x; ++k) {
+    // the last block's warp 0 reduces the blocks' winners: lane l takes blocks l, l + 32, ...
+    XBest b{0ull, ~0ull, ~0ull, -1};
+    for (int k = lane; k < (int)gridDim.x; k += 32) {
         const XBest y = bbest[k];
         if (x_better(y, b)) b = y;
     }
+    for (int off = 16; off > 0; off >>= 1) {
+        XBest y;
+        y.gbits = __shfl_down_sync(0xffffffffu, b.gbits, off);
+        y.a = __shfl_down_sync(0xffffffffu, b.a, off);
+        y.b = __shfl_down_sync(0xffffffffu, b.b, off);
+        y.slot = __shfl_down_sync(0xffffffffu, b.slot, off);
+        if (x_better(y, b)) b = y;
+    }
+    if (lane != 0) return;
     *counter = 0u;
     xs->n_cand = 0;
     if (b.slot < 0) { xs->done = 1; xs->eta = 0.0; return; }     // nothing left to choose
