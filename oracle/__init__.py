@@ -409,3 +409,74 @@ class XCDFCI:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# OptOrbFCI (Algorithm 4): the orbital subproblem and the outer loop
+# ---------------------------------------------------------------------------
+def optorb_transform(h: np.ndarray, g: np.ndarray, U: np.ndarray):
+    """Integrals in the orbitals (phi) = (psi) U, U of size M x N with orthonormal
+    columns (Sec. "Optimal Orbital Selections"): h' = U^T h U, g'_pqrs = sum U_ap U_bq U_cr U_ds g_abcd."""
+    return U.T @ h @ U, np.einsum("ap,bq,cr,ds,abcd->pqrs", U, U, U, U, g, optimize=True)
+
+
+def optorb_objective(h, g, U, g1, g2) -> float:
+    """P4(U) of the subproblem (eq. subopt) in the RDM convention E = sum h gamma + 1/2 sum (pq|rs) Gamma."""
+    h2, gg = optorb_transform(h, g, U)
+    return float(np.sum(h2 * g1) + 0.5 * np.sum(gg * g2))
+
+
+def optorb_gradient(h, g, U, g1, g2) -> np.ndarray:
+    """Euclidean gradient of P4 with respect to U (M x N): 2 h U gamma + 2 sum g''_pbcd Gamma_abcd,
+    g''_pbcd = sum_jkl g_pjkl U_jb U_kc U_ld (the symmetries of g and Gamma make the four
+    positions of U contribute alike)."""
+    g3 = np.einsum("pjkl,jb,kc,ld->pbcd", g, U, U, U, optimize=True)
+    return 2.0 * h @ U @ g1 + 2.0 * np.einsum("pbcd,abcd->pa", g3, g2, optimize=True)
+
+
+def polar(X: np.ndarray) -> np.ndarray:
+    """orth(X): the orthonormal factor of the polar decomposition (closest matrix with orthonormal columns)."""
+    W, _, Vt = np.linalg.svd(X, full_matrices=False)
+    return W @ Vt
+
+
+def optorb_subproblem(h, g, U, g1, g2, steps: int):
+    """Projected gradient with alternating Barzilai-Borwein steps (Algorithm 4, eq. projBB):
+    U <- orth(U - t_k grad P4(U)), t_k = <S,S>/|<S,Y>| on odd and |<S,Y>|/<Y,Y> on even k
+    (S, Y the last differences of U and of the gradient), t_0 = 0.1 / max(1, ||grad||_F).
+    Returns the U with the lowest P4 met and the P4 history."""
+    best_U, best_P = U, optorb_objective(h, g, U, g1, g2)
+    hist = [best_P]
+    G = optorb_gradient(h, g, U, g1, g2)
+    t = 0.1 / max(1.0, np.linalg.norm(G))
+    Uo, Go = None, None
+    for k in range(steps):
+        if Uo is not None:
+            S, Y = U - Uo, G - Go
+            ss, sy, yy = np.sum(S * S), np.sum(S * Y), np.sum(Y * Y)
+            if abs(sy) > 0.0 and yy > 0.0:
+                t = ss / abs(sy) if k % 2 == 1 else abs(sy) / yy
+            t = min(max(t, 1e-10), 1e10)
+        Uo, Go = U, G
+        U = polar(U - t * G)
+        G = optorb_gradient(h, g, U, g1, g2)
+        P = optorb_objective(h, g, U, g1, g2)
+        hist.append(P)
+        if P < best_P:
+            best_U, best_P = U, P
+    return best_U, hist
+
+
+def optorb_run(h, g, M: int, N: int, na: int, nb: int, outer: int, bb_steps: int, U0=None):
+    """Algorithm 4 with the exact FCI solution of each basis (dense diagonalisation):
+    returns the energies E_0 per outer iteration and the final U."""
+    U = np.eye(M)[:, :N] if U0 is None else np.asarray(U0, dtype=np.float64)
+    dets = fci_dets(N, na, nb)
+    energies = []
+    for _ in range(outer):
+        h2, g2 = optorb_transform(h, g, U)
+        w, V = np.linalg.eigh(dense_H(N, na, nb, h2, g2))
+        energies.append(float(w[0]))
+        r1, r2 = rdm(N, dets, V[:, 0].copy())
+        U, _ = optorb_subproblem(h, g, U, r1, r2, bb_steps)
+    return np.array(energies), U
