@@ -179,6 +179,33 @@ int cdfci_energies(cdfci_handle h, double *E, int32_t cap, int32_t *n_out);
 int cdfci_export_states(cdfci_handle h, uint64_t *keys, double *C, double *B, int64_t cap, int64_t *n_out);
 
 /*
+ * OptOrbFCI (Alg. 4, Sec. "Optimal Orbital Selections"): N orbitals phi = psi U
+ * chosen from M >= N by alternating the FCI problem in the current basis
+ * (this library's solver with p->fci, p->inner_iterations steps) with the
+ * orbital subproblem (eq. subopt): P4(U) = sum h'gamma + 1/2 sum g'Gamma over
+ * the M x N matrices with orthonormal columns, the RDMs of the current FCI
+ * state fixed, by p->bb_steps projected-gradient steps (eq. projBB)
+ * U <- orth(U - t_k grad P4(U)) with alternating Barzilai-Borwein steps t_k =
+ * <S,S>/|<S,Y>| (odd k) and |<S,Y>|/<Y,Y> (even k), t_0 = 0.1 / max(1, ||grad||_F),
+ * orth = the polar factor (Newton-Schulz on the device); the U with the lowest
+ * P4 met is kept.  h (M x M), g (M^4, (pq|rs)) and U (M x N, row-major, in: a
+ * start with orthonormal columns, out: the last basis) are host or device
+ * pointers; energies (host) receives E_0 of each outer iteration's FCI solve
+ * (p->outer values).  Every step runs on the device (integral transformation,
+ * gradient, projection, reductions); the host only sequences them.  Errors:
+ * CDFCI_ERR_ARG (sizes, U not orthonormal to 1e-10, num_states > 1), and those
+ * of cdfci_create / cdfci_step.
+ */
+typedef struct {
+    int32_t      outer;             /* outer iterations of Alg. 4 */
+    int32_t      bb_steps;          /* projected-gradient steps of the orbital subproblem per outer iteration */
+    int64_t      inner_iterations;  /* solver iterations per FCI problem */
+    cdfci_params fci;               /* the inner solver (num_states = 1) */
+} cdfci_optorb_params;
+int cdfci_optorb(const double *h, const double *g, int M, int N, int n_alpha, int n_beta, double *U,
+                 const cdfci_optorb_params *p, double *energies);
+
+/*
  * Start vector (optional, replaces the state): c = sum_k c[k] e_{keys k},
  * keys 2 words per entry (A, B), n >= 1 distinct determinants with the
  * handle's N, n_alpha, n_beta and at least one nonzero c; host or device

@@ -32,6 +32,11 @@ class cdfci_params(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("num_states", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
+class cdfci_optorb_params(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int32), ("bb_steps", ctypes.c_int32), ("inner_iterations", ctypes.c_int64),
+                ("fci", cdfci_params)]
+
+
 class cdfci_tune_report(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("chosen", ctypes.c_int32), ("m", ctypes.c_int32 * 16),
                 ("grid_blocks", ctypes.c_int32 * 16), ("iterations", ctypes.c_int64 * 16),
@@ -108,6 +113,8 @@ def lib():
         L.cdfci_column_noalloc.restype = ctypes.c_int
         L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
         L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.cdfci_optorb.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                   ctypes.POINTER(cdfci_optorb_params), dp]
         L.cdfci_export_states.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_checkpoint.argtypes = [vp, ctypes.POINTER(cdfci_checkpoint_header), u64p, dp, dp, ctypes.c_void_p, i64]
         L.cdfci_restore.argtypes = [vp, ctypes.POINTER(cdfci_checkpoint_header), u64p, dp, dp, ctypes.c_void_p]
@@ -200,6 +207,20 @@ def cdfci_export(handle: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     b = np.zeros(max(cap, 1))
     _check(lib().cdfci_export(handle, _ptr(keys), _ptr(c), _ptr(b), cap, ctypes.byref(n)))
     return keys[:n.value], c[:n.value], b[:n.value]
+
+
+def cdfci_optorb(h, g, M: int, N: int, n_alpha: int, n_beta: int, U0=None, outer: int = 4, bb_steps: int = 20,
+                 inner_iterations: int = 20000, **fci) -> Tuple[np.ndarray, np.ndarray]:
+    """OptOrbFCI (Algorithm 4): returns the final U (M x N) and E_0 of each outer iteration."""
+    p = cdfci_optorb_params()
+    p.outer, p.bb_steps, p.inner_iterations = outer, bb_steps, inner_iterations
+    p.fci = cdfci_default_params(**fci)
+    U = np.ascontiguousarray(np.eye(M)[:, :N] if U0 is None else U0, dtype=np.float64).copy()
+    E = np.zeros(outer)
+    h = np.ascontiguousarray(h, dtype=np.float64) if isinstance(h, np.ndarray) else h
+    g = np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g
+    _check(lib().cdfci_optorb(_ptr(h), _ptr(g), M, N, n_alpha, n_beta, _ptr(U), ctypes.byref(p), _ptr(E)))
+    return U, E
 
 
 def cdfci_energies(handle: int, cap: int = 8) -> np.ndarray:

@@ -674,6 +674,137 @@ CDFCI_API int cdfci_get_column(cdfci_handle c, const uint64_t *key, uint64_t *ke
     return CDFCI_OK;
 }
 
+CDFCI_API int cdfci_optorb(const double *h, const double *g, int M, int N, int n_alpha, int n_beta, double *U,
+                           const cdfci_optorb_params *p, double *energies) {
+    if (!h || !g || !U || !p || !energies) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (M < 1 || M > kMaxN || N < 1 || N > M) return fail(CDFCI_ERR_ARG, "need 1 <= N <= M <= %d", kMaxN);
+    if (p->outer < 1 || p->bb_steps < 0 || p->inner_iterations < 0)
+        return fail(CDFCI_ERR_ARG, "outer >= 1, bb_steps >= 0 and inner_iterations >= 0 required");
+    if (p->fci.num_states > 1) return fail(CDFCI_ERR_ARG, "the inner FCI solves one state (num_states = 1)");
+    const long long MN = (long long)M * N, M2 = (long long)M * M, N2 = (long long)N * N;
+    const long long M4 = M2 * M2, N3 = N2 * N, N4 = N2 * N2;
+    std::vector<double> hU0;
+    int rc = copy_in(hU0, U, (size_t)MN);
+    if (rc) return rc;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            double x = 0.0;
+            for (int q = 0; q < M; ++q) x += hU0[(size_t)q * N + a] * hU0[(size_t)q * N + b];
+            if (std::fabs(x - (a == b ? 1.0 : 0.0)) > 1e-10) return fail(CDFCI_ERR_ARG, "U has no orthonormal columns");
+        }
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); } } sg{s};
+    DevTemp tmp;
+    double *dh = tmp.alloc<double>(M2), *dg = tmp.alloc<double>(M4), *dU = tmp.alloc<double>(MN);
+    double *t1 = tmp.alloc<double>(M2 * M * N), *t2 = tmp.alloc<double>(M2 * N2), *g3 = tmp.alloc<double>(M * N3);
+    double *g4 = tmp.alloc<double>(N4), *hU = tmp.alloc<double>(MN), *h2 = tmp.alloc<double>(N2);
+    double *r1 = tmp.alloc<double>(N2), *r2 = tmp.alloc<double>(N4), *G = tmp.alloc<double>(MN);
+    double *Uo = tmp.alloc<double>(MN), *Go = tmp.alloc<double>(MN), *X = tmp.alloc<double>(MN);
+    double *Xn = tmp.alloc<double>(MN), *Gm = tmp.alloc<double>(N2), *Ub = tmp.alloc<double>(MN);
+    double *sc = tmp.alloc<double>(8);
+    if (!dh || !dg || !dU || !t1 || !t2 || !g3 || !g4 || !hU || !h2 || !r1 || !r2 || !G || !Uo || !Go || !X || !Xn ||
+        !Gm || !Ub || !sc)
+        return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    CK(cudaMemcpyAsync(dh, h, M2 * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(dg, g, M4 * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(dU, hU0.data(), MN * sizeof(double), cudaMemcpyHostToDevice, s));
+    const size_t bMN = MN * sizeof(double);
+    // h' = U^T h U, g' (all four indices), and g'' (three) for the gradient
+    auto transform = [&](const double *Uc) -> cudaError_t {
+        cudaError_t e = oo_contract(dg, Uc, t1, M2 * M, M, N, 1, s);
+        if (e == cudaSuccess) e = oo_contract(t1, Uc, t2, M2, M, N, N, s);
+        if (e == cudaSuccess) e = oo_contract(t2, Uc, g3, M, M, N, N2, s);
+        if (e == cudaSuccess) e = oo_contract(g3, Uc, g4, 1, M, N, N3, s);
+        if (e == cudaSuccess) e = oo_contract(dh, Uc, hU, M, M, N, 1, s);
+        if (e == cudaSuccess) e = oo_contract(hU, Uc, h2, 1, M, N, N, s);
+        return e;
+    };
+    auto read = [&](int k, double *out) -> int {
+        CK(cudaMemcpyAsync(out, sc, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return CDFCI_OK;
+    };
+    auto objective = [&](double *P) -> int {                       // P4 from h', g' and the RDMs
+        CK(oo_dot(h2, r1, N2, sc, s));
+        CK(oo_dot(g4, r2, N4, sc + 1, s));
+        double v[2];
+        int r = read(2, v);
+        *P = v[0] + 0.5 * v[1];
+        return r;
+    };
+    auto polar = [&]() -> int {                                    // X <- orth(X) (Newton-Schulz on X / ||X||_F)
+        CK(oo_dot(X, X, MN, sc, s));
+        CK(oo_scale(X, sc, MN, s));
+        std::vector<double> gm((size_t)N2);
+        for (int k = 0; k < 200; ++k) {
+            CK(oo_gram(X, Gm, M, N, s));
+            CK(cudaMemcpyAsync(gm.data(), Gm, N2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            double err = 0.0;
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b) err = std::max(err, std::fabs(gm[(size_t)a * N + b] - (a == b ? 1.0 : 0.0)));
+            if (err < 4e-16 * N) return CDFCI_OK;
+            CK(oo_ns(X, Gm, Xn, M, N, s));
+            std::swap(X, Xn);
+        }
+        return fail(CDFCI_ERR_INTERNAL, "the orthogonal projection did not converge");
+    };
+    for (int it = 0; it < p->outer; ++it) {
+        CK(transform(dU));
+        cdfci_params fp = p->fci;
+        fp.cuda_stream = s;
+        cdfci_handle hd = nullptr;
+        rc = cdfci_create(h2, g4, N, n_alpha, n_beta, &fp, &hd);
+        if (rc) return rc;
+        cdfci_stats st;
+        rc = cdfci_step(hd, p->inner_iterations, &st);
+        if (!rc) rc = cdfci_rdm(hd, r1, r2);
+        cdfci_destroy(hd);
+        if (rc) return rc;
+        energies[it] = st.energy;
+        // the orbital subproblem with these RDMs
+        double P = 0.0, best = 0.0;
+        if ((rc = objective(&P))) return rc;
+        best = P;
+        CK(cudaMemcpyAsync(Ub, dU, bMN, cudaMemcpyDeviceToDevice, s));
+        CK(oo_grad(hU, r1, g3, r2, G, M, N, s));
+        CK(oo_dot(G, G, MN, sc, s));
+        double gg = 0.0;
+        if ((rc = read(1, &gg))) return rc;
+        double t = 0.1 / std::max(1.0, std::sqrt(gg));
+        for (int k = 0; k < p->bb_steps; ++k) {
+            if (k > 0) {
+                CK(oo_axpy(dU, Uo, 1.0, X, MN, s));                  // S = U - U_old
+                CK(oo_axpy(G, Go, 1.0, Xn, MN, s));                  // Y = G - G_old
+                CK(oo_dot(X, X, MN, sc, s));
+                CK(oo_dot(X, Xn, MN, sc + 1, s));
+                CK(oo_dot(Xn, Xn, MN, sc + 2, s));
+                double d[3];
+                if ((rc = read(3, d))) return rc;
+                if (std::fabs(d[1]) > 0.0 && d[2] > 0.0) t = (k % 2 == 1) ? d[0] / std::fabs(d[1]) : std::fabs(d[1]) / d[2];
+                t = std::min(std::max(t, 1e-10), 1e10);
+            }
+            CK(cudaMemcpyAsync(Uo, dU, bMN, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(Go, G, bMN, cudaMemcpyDeviceToDevice, s));
+            CK(oo_axpy(dU, G, t, X, MN, s));                         // X = U - t grad
+            if ((rc = polar())) return rc;
+            CK(cudaMemcpyAsync(dU, X, bMN, cudaMemcpyDeviceToDevice, s));
+            CK(transform(dU));
+            CK(oo_grad(hU, r1, g3, r2, G, M, N, s));
+            if ((rc = objective(&P))) return rc;
+            if (P < best) {
+                best = P;
+                CK(cudaMemcpyAsync(Ub, dU, bMN, cudaMemcpyDeviceToDevice, s));
+            }
+        }
+        CK(cudaMemcpyAsync(dU, Ub, bMN, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaMemcpyAsync(U, dU, bMN, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return CDFCI_OK;
+}
+
 CDFCI_API int cdfci_energies(cdfci_handle c, double *E, int32_t cap, int32_t *n_out) {
     if (!c || !E || !n_out) return fail(CDFCI_ERR_ARG, "NULL argument");
     int rc = fill_stats(c, nullptr);

@@ -48,6 +48,17 @@ cudaError_t launch_x_export(const Problem &P, const XBuffers &b, int k1, unsigne
 cudaError_t launch_x_diag_list(const Problem &P, const unsigned long long *keys, long long n, double *out,
                                cudaStream_t s);
 
+// OptOrbFCI (Algorithm 4): orbital subproblem kernels
+cudaError_t oo_contract(const double *in, const double *U, double *out, long long A, int M, int N, long long B,
+                        cudaStream_t s);
+cudaError_t oo_grad(const double *hU, const double *g1, const double *g3, const double *g2, double *G, int M, int N,
+                    cudaStream_t s);
+cudaError_t oo_dot(const double *x, const double *y, long long n, double *out, cudaStream_t s);
+cudaError_t oo_axpy(const double *x, const double *z, double t, double *y, long long n, cudaStream_t s);
+cudaError_t oo_scale(double *x, const double *sq, long long n, cudaStream_t s);
+cudaError_t oo_gram(const double *X, double *Gm, int M, int N, cudaStream_t s);
+cudaError_t oo_ns(const double *X, const double *Gm, double *Xn, int M, int N, cudaStream_t s);
+
 // checkpoint / restore
 cudaError_t launch_ckpt_export(const Problem &P, unsigned long long *keys, double *c, double *b, unsigned char *flags,
                                long long cap, unsigned long long *counter, cudaStream_t s);

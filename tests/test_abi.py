@@ -56,6 +56,9 @@ int main(void) {
   F(cdfci_tune_report, chosen) F(cdfci_tune_report, m) F(cdfci_tune_report, grid_blocks) F(cdfci_tune_report, iterations) F(cdfci_tune_report, seconds)
   F(cdfci_tune_report, energy_drop) F(cdfci_tune_report, score)
   printf("cdfci_checkpoint_header %zu\\n", sizeof(cdfci_checkpoint_header));
+  printf("cdfci_optorb_params %zu\\n", sizeof(cdfci_optorb_params));
+  F(cdfci_optorb_params, inner_iterations) F(cdfci_optorb_params, fci)
+  F(cdfci_params, num_states)
 """ + ck_lines + """
   return 0;
 }
@@ -69,10 +72,12 @@ int main(void) {
     assert int(vals["cdfci_stats"]) == ctypes.sizeof(S)
     assert int(vals["cdfci_tune_report"]) == ctypes.sizeof(R)
     assert int(vals["cdfci_checkpoint_header"]) == ctypes.sizeof(ck)
+    assert int(vals["cdfci_optorb_params"]) == ctypes.sizeof(built.cdfci_optorb_params)
     for k, v in vals.items():
         if "." in k:
             t, f = k.split(".")
-            cls = {"cdfci_params": P, "cdfci_stats": S, "cdfci_tune_report": R, "cdfci_checkpoint_header": ck}[t]
+            cls = {"cdfci_params": P, "cdfci_stats": S, "cdfci_tune_report": R, "cdfci_checkpoint_header": ck,
+                   "cdfci_optorb_params": built.cdfci_optorb_params}[t]
             assert getattr(cls, f).offset == int(v), k
 
 
