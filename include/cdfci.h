@@ -81,7 +81,14 @@ typedef struct {
                                   num_coordinates = 1.  Start rows: the reference determinant and the K
                                   determinants of its column with the lowest diagonal H_DD (ties: the
                                   smaller key), C = [e_{D_0} .. e_{D_K}] */
-    int32_t  reserved0;
+    int32_t  z_threshold_search; /* 1: the r-th tenfold raise of tau comes when the stored determinants
+                                  pass 1 - 2^-(r+1) of max_load * capacity (50 %, 75 %, 87.5 %, ...),
+                                  the first from at least 1e-6 |E|; checked between launches, so a run
+                                  that would fill the table continues with stronger compression (Sec.
+                                  "Example Usage": adjust compression to fit the memory); tau never
+                                  decreases; the current tau is in cdfci_stats.z_threshold */
+    double   max_memory;       /* > 0: GiB for the wavefunction's table (and xCDFCI rows): log2_capacity
+                                  becomes the largest that fits; 0 = use log2_capacity */
 } cdfci_params;
 
 /* Progress report (the console row of Sec. "Expected Console Output"). */
@@ -104,6 +111,7 @@ typedef struct {
     int64_t reduced_iterations;/* m > 1: cumulative iterations of the reduced eigensolver (0 for m = 1) */
     int32_t grid_blocks;       /* m = 1: CTAs that evaluate a column (as resolved); 0 for m > 1 */
     int32_t grid_wide;         /* m = 1: 1 if they run as a cooperative grid (more than a cluster holds) */
+    double  z_threshold;       /* the tau in force (changes only under z_threshold_search) */
 } cdfci_stats;
 
 /* Fills *p with the defaults (m = 1, 2^22 slots, tau = 0, max_load = 0.79,

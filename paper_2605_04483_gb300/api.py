@@ -29,7 +29,8 @@ class cdfci_params(ctypes.Structure):
                 ("ref_alpha", ctypes.c_uint64), ("ref_beta", ctypes.c_uint64),
                 ("block_threads", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("graph_chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p), ("num_states", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("cuda_stream", ctypes.c_void_p), ("num_states", ctypes.c_int32),
+                ("z_threshold_search", ctypes.c_int32), ("max_memory", ctypes.c_double)]
 
 
 class cdfci_optorb_params(ctypes.Structure):
@@ -51,7 +52,7 @@ class cdfci_stats(ctypes.Structure):
                 ("applied", ctypes.c_int64), ("dropped", ctypes.c_int64), ("inserted", ctypes.c_int64),
                 ("load", ctypes.c_double), ("status", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("reduced_iterations", ctypes.c_int64), ("grid_blocks", ctypes.c_int32),
-                ("grid_wide", ctypes.c_int32)]
+                ("grid_wide", ctypes.c_int32), ("z_threshold", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -69,7 +69,7 @@ std::vector<unsigned short> pair_table(int n) {
 void cdfci::set_last_error_message(const char *msg) { g_last_error = msg; }
 
 struct cdfci_ctx {
-    cdfci_params prm;
+    cdfci_params prm;                            // as given (log2_capacity resolved from max_memory)
     int N, na, nb;
     Problem P;
     cudaStream_t stream = nullptr;
@@ -97,6 +97,7 @@ struct cdfci_ctx {
     int mb_nalloc = 0;
     int mchunk = 8;                              // iterations per captured graph
     cudaGraphExec_t mgraph = nullptr;
+    int tau_raises = 0;                          // z_threshold_search: tenfold raises so far
     // xCDFCI (num_states = K + 1 > 1)
     bool xcd = false;
     int k1 = 1;
@@ -119,9 +120,33 @@ void free_ctx(cdfci_ctx *c) {
     delete c;
 }
 
+int fill_stats(cdfci_ctx *c, cdfci_stats *s);
+
+// z_threshold_search: the r-th tenfold raise of tau comes when the stored determinants pass
+// 1 - 2^-(r+1) of max_entries (50 %, 75 %, 87.5 %, ...), so each raise leaves half of the
+// remaining room; the first raise starts from at least 1e-6 |E| (the scale of H) or 1e-10.
+// Reads the snapshot first; *changed tells whether tau moved.
+int maybe_raise_tau(cdfci_ctx *c, bool *changed) {
+    *changed = false;
+    if (!c->prm.z_threshold_search) return CDFCI_OK;
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    const double frac = 1.0 - std::ldexp(1.0, -(c->tau_raises + 1));
+    if ((double)c->h_st->n_slots >= frac * (double)c->P.max_entries) {
+        c->P.tau = std::max({10.0 * c->P.tau, 1e-6 * std::fabs(c->h_st->energy), 1e-10});
+        c->tau_raises += 1;
+        *changed = true;
+    }
+    return CDFCI_OK;
+}
+
 int run_iterations(cdfci_ctx *c, long long n) {
+    const long long chunk = c->prm.z_threshold_search ? std::min<long long>(c->chunk, 1024) : c->chunk;
     while (n > 0) {
-        long long k = std::min(n, c->chunk);
+        bool changed = false;
+        int rc = maybe_raise_tau(c, &changed);
+        if (rc) return rc;
+        long long k = std::min(n, chunk);
         if (c->gridmode)
             CK(launch_cd_loop_grid(c->P, c->d_st, c->d_rec, c->d_part, c->d_part + c->grid, c->d_bar, c->grid, k,
                                    c->stream));
@@ -164,6 +189,7 @@ int stats_from_snapshot(cdfci_ctx *c, cdfci_stats *s) {
         s->reduced_iterations = t.eig_iters;
         s->grid_blocks = (c->block || c->xcd) ? 0 : c->grid;
         s->grid_wide = c->gridmode ? 1 : 0;
+        s->z_threshold = c->P.tau;
     }
     if (t.status != 0) {
         const char *what = t.status == CDFCI_ERR_TABLE_FULL ? "hash table full (raise log2_capacity or z_threshold)"
@@ -404,6 +430,16 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         return fail(CDFCI_ERR_ARG, "num_states = %d outside [1, %d]", prm.num_states, kXMax);
     if (prm.num_states > 1 && prm.num_coordinates != 1)
         return fail(CDFCI_ERR_ARG, "num_states = %d needs num_coordinates = 1 (Alg. 3 updates one row)", prm.num_states);
+    if (!(prm.max_memory >= 0.0) || !std::isfinite(prm.max_memory)) return fail(CDFCI_ERR_ARG, "max_memory invalid");
+    if (prm.max_memory > 0.0) {
+        // the largest table whose slots (plus xCDFCI rows) fit in max_memory GiB
+        const double per_slot = (double)sizeof(Slot) + (prm.num_states > 1 ? 16.0 * prm.num_states : 0.0);
+        const double slots = prm.max_memory * 1073741824.0 / per_slot;
+        int lc = 0;
+        while (lc < 34 && std::ldexp(1.0, lc + 1) <= slots) ++lc;
+        if (lc < 4) return fail(CDFCI_ERR_ARG, "max_memory = %g GiB holds fewer than 16 slots", prm.max_memory);
+        prm.log2_capacity = lc;
+    }
     if (prm.log2_capacity < 4 || prm.log2_capacity > 34)
         return fail(CDFCI_ERR_ARG, "log2_capacity = %d outside [4, 34]", prm.log2_capacity);
     if (!(prm.max_load > 0.0 && prm.max_load <= 0.95)) return fail(CDFCI_ERR_ARG, "max_load must be in (0, 0.95]");
@@ -600,7 +636,18 @@ CDFCI_API int cdfci_step(cdfci_handle c, int64_t n_iter, cdfci_stats *stats) {
     if (!c) return fail(CDFCI_ERR_ARG, "handle is NULL");
     if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
     if (c->block || c->xcd) {
-        for (int64_t i = 0; i < n_iter / c->mchunk; ++i) CK(cudaGraphLaunch(c->mgraph, c->stream));
+        for (int64_t i = 0; i < n_iter / c->mchunk; ++i) {
+            bool changed = false;
+            int rc = maybe_raise_tau(c, &changed);
+            if (rc) return rc;
+            if (changed) {                                       // tau is a launch parameter of the graph
+                cudaGraphExecDestroy(c->mgraph);
+                c->mgraph = nullptr;
+                rc = c->xcd ? build_xcd_graph(c) : build_block_graph(c);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(c->mgraph, c->stream));
+        }
         for (int64_t i = 0; i < n_iter % c->mchunk; ++i)
             CK(c->xcd ? launch_x_iteration(c->P, c->xb, c->stream) : launch_mc_iteration(c->P, c->mb, c->stream));
         return fill_stats(c, stats);

@@ -58,7 +58,8 @@ int main(void) {
   printf("cdfci_checkpoint_header %zu\\n", sizeof(cdfci_checkpoint_header));
   printf("cdfci_optorb_params %zu\\n", sizeof(cdfci_optorb_params));
   F(cdfci_optorb_params, inner_iterations) F(cdfci_optorb_params, fci)
-  F(cdfci_params, num_states)
+  F(cdfci_params, num_states) F(cdfci_params, z_threshold_search) F(cdfci_params, max_memory)
+  F(cdfci_stats, z_threshold)
 """ + ck_lines + """
   return 0;
 }

@@ -228,3 +228,34 @@ def test_error_bad_integrals():
     with pytest.raises(api.CdfciError) as e:
         api.Solver(w.h, g, 6, 2, 2)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("m", [1, 8])
+def test_threshold_search_keeps_the_table_from_filling(m):
+    """z_threshold_search: a table of 4096 slots (3,235 entries at max_load) cannot hold the 8-site
+    chain's 4,900 determinants at tau = 0 (TABLE_FULL); with the search tau rises and the run
+    completes, with the table below max_load; the exact Rayleigh quotient of the compressed vector
+    is variational and within 5e-2 Ha of exact diagonalisation (a third of the space is cut away)."""
+    from paper_2605_04483_gb300 import api
+    w = inputs.config1()
+    E0 = oracle.ground_energy(8, 4, 4, w.h, w.g, dense_limit=5000)
+    n = 60000 if m == 1 else 3000
+    s = solver(w, log2_capacity=12, num_coordinates=m)
+    with pytest.raises(api.CdfciError) as e:
+        s.step(n)
+    assert e.value.code == -3
+    s.close()
+    s = solver(w, log2_capacity=12, num_coordinates=m, z_threshold_search=1)
+    st = s.step(n)
+    assert st["z_threshold"] > 0.0 and st["n_slots"] <= 0.79 * 4096
+    E1 = s.energy(1) if m == 1 else st["energy"]
+    assert E0 - 1e-10 <= E1 < E0 + 5e-2, (E1, E0, st["z_threshold"], st["n_slots"])
+    s.close()
+
+
+def test_max_memory_sets_the_capacity():
+    w = inputs.config1()
+    s = solver(w, max_memory=1.0 / 1024)                 # 1 MiB: 2^15 slots of 32 bytes
+    st = s.stats()
+    assert round(st["n_slots"] / st["load"]) == 1 << 15
+    s.close()
