@@ -214,14 +214,11 @@ int setup_block(cdfci_ctx *c, int m) {
     const Problem &P = c->P;
     const long long nh_eff = P.doubles_vanish ? P.seg[2] : P.seg[5];
     b.m = m;
-    b.tpc = nh_eff >= 4096 ? 256 : (nh_eff >= 512 ? 128 : 32);
-    b.chunk = b.tpc * 16;
-    b.nchunk = (int)std::max<long long>(1, (nh_eff - 1 + b.chunk - 1) / b.chunk);
     const long long cap_cand = (long long)m * nh_eff + m + 64;
     b.cap_cand = cap_cand;
     b.cand_grid = 152 * 4;
-    const long long items = (long long)m * b.nchunk, gpb = 256 / b.tpc;
-    b.scatter_grid = (int)std::max<long long>(1, std::min<long long>((items + gpb - 1) / gpb, 152 * 16));
+    b.scatter_grid = mc_scatter_grid();
+    if (b.scatter_grid <= 0) return fail(CDFCI_ERR_CUDA, "occupancy query of the scatter failed");
     b.st = c->d_st;
     const size_t n1 = (size_t)m + 1;
     b.ldr = (int)(32 * ((n1 + 31) / 32));
@@ -231,8 +228,14 @@ int setup_block(cdfci_ctx *c, int m) {
         mb_alloc(c, &b.HIIc, (size_t)m) || mb_alloc(c, &b.Rh, n1 * (size_t)b.ldr) ||
         mb_alloc(c, &b.Rl, n1 * (size_t)b.ldr) ||
         mb_alloc(c, &b.w, (size_t)m) || mb_alloc(c, &b.thr, (size_t)m) || mb_alloc(c, &b.eta, (size_t)m) ||
-        mb_alloc(c, &b.gathp, (size_t)m * b.nchunk))
+        mb_alloc(c, &b.gathp, (size_t)mc_gath_entries(m, b.scatter_grid)))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
+    // c != 0 filter: one bit per table slot, between 2^16 and 2^27 bits (16 MB, L2-resident)
+    const unsigned long long nbits =
+        (unsigned long long)std::min<long long>(std::max<long long>(P.capacity, 1ll << 16), 1ll << 27);
+    if (mb_alloc(c, &c->P.cnz, (size_t)(nbits / 32)))
+        return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
+    c->P.cnz_mask = nbits - 1;
     CK(mc_configure());
     return CDFCI_OK;
 }
@@ -391,6 +394,7 @@ int reset_state(cdfci_ctx *c) {
     CK(cudaMemcpyAsync(c->d_st, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->d_table, 0, (size_t)c->P.capacity * sizeof(Slot), c->stream));
     if (c->block) CK(cudaMemsetAsync(c->mb.ms, 0, sizeof(McState), c->stream));
+    if (c->P.cnz) CK(cudaMemsetAsync(c->P.cnz, 0, (size_t)(c->P.cnz_mask + 1) / 8, c->stream));
     return CDFCI_OK;
 }
 }  // namespace

@@ -22,6 +22,8 @@
 // c <- gamma c costs O(1): s <- gamma s.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "cdfci_internal.cuh"
 #include "cdfci_kernels.h"
 
@@ -966,7 +968,10 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         etaout[tid] = eta;
         w[tid] = eta * rsc;
         thr[tid] = eta != 0.0 ? P.tau / fabs(eta) : 1.0e308;
-        if (!bad) P.table[sel[tid].slot].c = zn * rsc;
+        if (!bad) {
+            P.table[sel[tid].slot].c = zn * rsc;
+            cnz_set(P, sel[tid].A, sel[tid].B);
+        }
         nz_from = (ci != 0.0 && zn == 0.0) ? 1 : 0;
         nz_to = (ci == 0.0 && zn != 0.0) ? 1 : 0;
     }
@@ -1039,9 +1044,31 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
 
 // ---------------------------------------------------------------------------
 // b += H_{:,I} eta for the m columns (stored units), gather, candidates.
-// A group of TPC threads handles one (column, chunk) work item.
+// The m columns' off-diagonal elements form one index space f = i (nh - 1) +
+// (e - 1) of T = m (nh - 1) elements; block k of the G blocks takes the
+// contiguous range [floor(k T / G), floor((k + 1) T / G)), so every block
+// has the same share (no second wave) and a column spans a few consecutive
+// blocks, each leaving one gather partial for it.
 // ---------------------------------------------------------------------------
-constexpr int kScatterBuf = 4096;   // new candidates of one block pass (groups x chunk elements)
+constexpr int kScatterBuf = 4096;   // new candidates of one block pass (<= kScatterSub)
+constexpr int kScatterSub = 4096;   // elements of one block pass (16 per thread)
+constexpr int kScatterMinRange = 256;
+
+// blocks in use for T elements on a grid of G: every range holds at least kScatterMinRange elements
+__host__ __device__ __forceinline__ long long mc_scatter_blocks(long long T, int G) {
+    const long long g = T / kScatterMinRange;
+    return g < 1 ? 1 : (g < G ? g : G);
+}
+// the block whose range holds element f (ranges as above)
+__device__ __forceinline__ long long mc_block_of(long long f, long long T, long long G) {
+    return ((f + 1) * G + T - 1) / T - 1;
+}
+// gather partials per column: blocks hold at least r = floor(T / G) elements, so a
+// column of Lc elements meets at most floor((Lc - 2) / r) + 2 <= Lc / r + 2 of them
+// (m columns: at most 2 G + 2 m partials, as r >= T / (2 G))
+__host__ __device__ __forceinline__ long long mc_gath_per_col(long long Lc, long long T, long long G) {
+    return Lc / (T / G) + 2;
+}
 
 // Probe for {a, b}: the key and the value halves of the slot are read by two
 // independent 16-byte loads.  A new key is inserted with the candidate mark
@@ -1049,9 +1076,9 @@ constexpr int kScatterBuf = 4096;   // new candidates of one block pass (groups 
 // or -1 (absent, not inserted) / -2 (error, status set).  c: the slot's
 // stored c; marked: the slot carried the mark when it was read.
 __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, unsigned long long a,
-                                              unsigned long long b, bool insert, bool &inserted, double &c,
-                                              bool &marked) {
-    unsigned long long pos = key_hash(a, b) & P.mask;
+                                              unsigned long long b, unsigned long long h, bool insert,
+                                              bool &inserted, double &c, bool &marked) {
+    unsigned long long pos = h & P.mask;
     const bool both_nonzero = (P.na > 0) && (P.nb > 0);
     for (int probe = 0; probe < P.max_probe; ++probe) {
         Slot *s = P.table + pos;
@@ -1089,90 +1116,103 @@ __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, u
     return -2;
 }
 
-__global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
+__global__ void __launch_bounds__(256, 4) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                     const double *w, const double *thr, long long *cand,
-                                                    double *gathp, int tpc, int nchunk, int chunk) {
-    __shared__ ColLists Lg[8];
-    __shared__ double sred[256];
+                                                    double *gathp) {
+    __shared__ ColLists L;
+    __shared__ double swarp[8];
     __shared__ long long s_cand[kScatterBuf];
     __shared__ int s_ncand, s_base;
     __shared__ unsigned long long scnt[4];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
-    const int gpb = 256 / tpc;                          // groups per block
-    const int grp = tid / tpc, gt = tid - grp * tpc;
     const int m = ms->m_sel;
     const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
-    const long long items = (long long)m * nchunk;
+    const long long Lc = nh - 1, T = (long long)m * Lc;
+    const long long G = mc_scatter_blocks(T, gridDim.x);
+    if (T <= 0 || blockIdx.x >= G) return;
+    const long long K = mc_gath_per_col(Lc, T, G);
+    const long long f_beg = (long long)blockIdx.x * T / G, f_end = ((long long)blockIdx.x + 1) * T / G;
     if (tid < 4) scnt[tid] = 0;
     long long c_el = 0, c_app = 0, c_drop = 0, c_ins = 0;
-    for (long long base = (long long)blockIdx.x * gpb; base < items; base += (long long)gridDim.x * gpb) {
-        const long long item = base + grp;
-        const bool act = item < items;
-        const int col = act ? (int)(item / nchunk) : 0;
-        const int ck = act ? (int)(item - (long long)col * nchunk) : 0;
-        const McSel xs = sel[col];
-        ColLists &L = Lg[grp];
-        if (act)
-            for (int t = gt; t < P.N; t += tpc) {
+    int cur = -1;
+    double gsum = 0.0;                                  // thread 0: this block's gather for column cur
+    McSel xs = {};
+    double wi = 0.0, ti = 0.0;
+    for (long long f0 = f_beg; f0 < f_end;) {
+        const int col = (int)(f0 / Lc);
+        const long long cend = (long long)(col + 1) * Lc;
+        const long long f1 = min(f_end, min(cend, f0 + kScatterSub));
+        if (col != cur) {
+            if (cur >= 0 && tid == 0)
+                gathp[(size_t)cur * K + (blockIdx.x - mc_block_of((long long)cur * Lc, T, G))] = gsum;
+            gsum = 0.0;
+            cur = col;
+            xs = sel[col];
+            wi = w[col];
+            ti = thr[col];
+            for (int t = tid; t < P.N; t += 256) {
                 int ra = __popcll(xs.A & low_mask(t)), rb = __popcll(xs.B & low_mask(t));
                 if ((xs.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
                 if ((xs.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
             }
+        }
         if (tid == 0) s_ncand = 0;
         __syncthreads();
         double gather = 0.0;
-        if (act) {
-            const double wi = w[col], ti = thr[col];
-            const long long e_beg = 1 + (long long)ck * chunk;
-            const long long e_end = e_beg + chunk < nh ? e_beg + chunk : nh;
-            for (long long e = e_beg + gt; e < e_end; e += tpc) {
-                unsigned long long oa, ob;
-                const double H = column_element(P, L, xs.A, xs.B, e, oa, ob);
-                if (is_zero(H)) continue;
-                ++c_el;
-                const bool big = fabs(H) >= ti;
-                bool ins = false, marked = false;
-                double cj = 0.0;
-                const long long s = mc_probe(P, st, oa, ob, big, ins, cj, marked);
-                if (s == -2) break;
-                if (s < 0) { ++c_drop; continue; }
-                if (!(!is_zero(cj) || big)) { ++c_drop; continue; }
-                Slot *sj = P.table + s;
-                atomicAdd(&sj->bv, wi * H);
-                ++c_app;
-                c_ins += ins ? 1 : 0;
-                gather = fma(H, cj, gather);
-                // the thread that marks a slot appends it
-                bool first = ins;
-                if (!ins && !marked) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
-                const unsigned int fm = __ballot_sync(__activemask(), first);
-                if (first) {
-                    const int leader = __ffs(fm) - 1;
-                    int pos = 0;
-                    if (lane == leader) pos = atomicAdd(&s_ncand, __popc(fm));
-                    pos = __shfl_sync(fm, pos, leader);
-                    const int at = pos + __popc(fm & ((1u << lane) - 1u));
-                    if (at < kScatterBuf) s_cand[at] = s;
-                    else set_status(st, kErrInternal);
-                }
+        const long long e_off = 1 - (long long)col * Lc;
+        for (long long f = f0 + tid; f < f1; f += 256) {
+            const long long e = f + e_off;
+            unsigned long long oa, ob;
+            const double H = column_element(P, L, xs.A, xs.B, e, oa, ob);
+            if (is_zero(H)) continue;
+            ++c_el;
+            const bool big = fabs(H) >= ti;
+            const unsigned long long hk = key_hash(oa, ob);
+            if (!big && !cnz_maybe(P, hk)) { ++c_drop; continue; }       // c_j = 0: the rule drops it
+            bool ins = false, marked = false;
+            double cj = 0.0;
+            const long long s = mc_probe(P, st, oa, ob, hk, big, ins, cj, marked);
+            if (s == -2) break;
+            if (s < 0) { ++c_drop; continue; }
+            if (!(!is_zero(cj) || big)) { ++c_drop; continue; }
+            Slot *sj = P.table + s;
+            atomicAdd(&sj->bv, wi * H);
+            ++c_app;
+            c_ins += ins ? 1 : 0;
+            gather = fma(H, cj, gather);
+            // the thread that marks a slot appends it
+            bool first = ins;
+            if (!ins && !marked) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
+            const unsigned int fm = __ballot_sync(__activemask(), first);
+            if (first) {
+                const int leader = __ffs(fm) - 1;
+                int pos = 0;
+                if (lane == leader) pos = atomicAdd(&s_ncand, __popc(fm));
+                pos = __shfl_sync(fm, pos, leader);
+                const int at = pos + __popc(fm & ((1u << lane) - 1u));
+                if (at < kScatterBuf) s_cand[at] = s;
+                else set_status(st, kErrInternal);
             }
         }
-        // fixed-order group sum of the gather
-        sred[tid] = gather;
+        // the pass's gather: a fixed tree in each warp, the warps in order
+        for (int o = 16; o > 0; o >>= 1) gather += __shfl_down_sync(0xffffffffu, gather, o);
+        if (lane == 0) swarp[warp] = gather;
         __syncthreads();
-        if (act && gt == 0) {
-            double t = 0.0;
-            for (int q = 0; q < tpc; ++q) t += sred[grp * tpc + q];
-            gathp[(size_t)col * nchunk + ck] = t;
+        if (tid == 0) {
+            double t = swarp[0];
+            for (int q = 1; q < 8; ++q) t += swarp[q];
+            gsum += t;
         }
         // this pass's new candidates: one reservation per block
         const int nb = min(s_ncand, kScatterBuf);
         if (tid == 0) s_base = nb > 0 ? atomicAdd(&ms->n_cand, nb) : 0;
         __syncthreads();
         for (int i = tid; i < nb; i += 256) cand[s_base + i] = s_cand[i];
+        f0 = f1;
         __syncthreads();
     }
+    if (cur >= 0 && tid == 0) gathp[(size_t)cur * K + (blockIdx.x - mc_block_of((long long)cur * Lc, T, G))] = gsum;
     atomicAdd((unsigned long long *)&scnt[0], (unsigned long long)c_el);
     atomicAdd((unsigned long long *)&scnt[1], (unsigned long long)c_app);
     atomicAdd((unsigned long long *)&scnt[2], (unsigned long long)c_drop);
@@ -1184,13 +1224,20 @@ __global__ void __launch_bounds__(256) k_mc_scatter(Problem P, McState *ms, Iter
 // b_I recalculated (Eq. recalculate-b), the chosen coordinates join the
 // candidates, counters and the host snapshot.
 __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel *sel, const double *Hdiag,
-                              const double *gathp, long long *cand, const double *etaout, int nchunk) {
+                              const double *gathp, long long *cand, const double *etaout, int grid) {
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
+    const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
+    const long long Lc = nh - 1, T = (long long)m * Lc;
+    const long long G = mc_scatter_blocks(T, grid), K = T > 0 ? mc_gath_per_col(Lc, T, G) : 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const long long slot = sel[i].slot;
         double t = 0.0;
-        for (int k = 0; k < nchunk; ++k) t += gathp[(size_t)i * nchunk + k];
+        if (T > 0) {
+            // the column's blocks in order
+            const long long nb = mc_block_of((long long)(i + 1) * Lc - 1, T, G) - mc_block_of((long long)i * Lc, T, G);
+            for (long long k = 0; k <= nb; ++k) t += gathp[(size_t)i * K + k];
+        }
         Slot *s = P.table + slot;
         s->bv = fma(Hdiag[i], s->c, t);
         const unsigned long long kb = s->b;
@@ -1252,6 +1299,7 @@ __global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, do
         s_ins = ins ? 1 : 0;
         s_bold = P.table[s].bv;
         P.table[s].c = eta;
+        cnz_set(P, A, B);
     }
     for (int t = threadIdx.x; t < P.N; t += blockDim.x) {
         int ra = __popcll(A & low_mask(t)), rb = __popcll(B & low_mask(t));
@@ -1310,6 +1358,18 @@ size_t mc_eigen_smem(int m) {
 int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
 int mc_max_m() { return kEigMaxN - 1; }
 
+// the scatter's grid: the blocks that are resident at once on this device
+int mc_scatter_grid() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_scatter, 256, 0) != cudaSuccess)
+        return 0;
+    return sms * std::max(per, 1);
+}
+// gather partials for m columns on a grid of `grid` blocks (any m_sel <= m)
+long long mc_gath_entries(int m, int grid) { return 2ll * grid + 2ll * m + 8; }
+
 cudaError_t mc_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)mc_eigen_smem(kEigSmemN - 1));
@@ -1324,9 +1384,8 @@ cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long 
 }
 
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s) {
-    k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp, b.tpc, b.nchunk,
-                                                b.chunk);
-    k_mc_finalize<<<1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.nchunk);
+    k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp);
+    k_mc_finalize<<<1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.scatter_grid);
     return cudaGetLastError();
 }
 

@@ -189,6 +189,8 @@ struct Problem {
     double tau;
     double theta, dx_threshold;
     unsigned long long mg_va, mg_vb, mg_nsb, mg_cva2, mg_cvb2;   // fdiv multipliers
+    unsigned int *cnz;             // m > 1: filter of determinants whose c may be nonzero (NULL: none)
+    unsigned long long cnz_mask;   // its bit count - 1
 };
 
 // ---------------------------------------------------------------------------
@@ -222,6 +224,21 @@ __host__ __device__ __forceinline__ unsigned long long hash_beta(unsigned long l
 }
 __host__ __device__ __forceinline__ unsigned long long key_hash(unsigned long long a, unsigned long long b) {
     return hash_alpha(a) ^ hash_beta(b);
+}
+
+// Filter of determinants whose c may be nonzero: one bit per bucket of the
+// high half of the key's hash (the table's slot comes from the low bits).  A
+// clear bit proves c = 0; bits are set wherever a c becomes nonzero and never
+// cleared, so a set bit only means "look it up".
+__device__ __forceinline__ void cnz_set(const Problem &P, unsigned long long a, unsigned long long b) {
+    if (!P.cnz) return;
+    const unsigned long long i = (key_hash(a, b) >> 32) & P.cnz_mask;
+    atomicOr(P.cnz + (i >> 5), 1u << (unsigned)(i & 31));
+}
+__device__ __forceinline__ bool cnz_maybe(const Problem &P, unsigned long long h) {
+    if (!P.cnz) return true;
+    const unsigned long long i = (h >> 32) & P.cnz_mask;
+    return (__ldg(P.cnz + (i >> 5)) >> (unsigned)(i & 31)) & 1u;
 }
 
 // floor(n / d) for n < 2^24, d < 2^16 with M = floor(2^40 / d) + 1 (the

@@ -1059,6 +1059,7 @@ __global__ void k_ckpt_import(Problem P, IterState *st, const unsigned long long
         if (!ins) { set_status(st, kErrInternal); continue; }
         P.table[s].c = c[i];
         P.table[s].bv = b[i];
+        if (c[i] != 0.0) cnz_set(P, keys[2 * i], keys[2 * i + 1]);
         if (flags && (flags[i] & 1) && cand) {
             P.table[s].b = keys[2 * i + 1] | kMarkB;
             const int pos = atomicAdd(n_cand, 1);

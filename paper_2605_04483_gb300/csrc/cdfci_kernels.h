@@ -80,11 +80,13 @@ struct McBuffers {
     double *cI, *bI, *Hdiag, *HIIc, *w, *thr, *eta, *gathp;
     float *Rh, *Rl;                // reduced matrix R as float-float pairs, leading dimension ldr
     int ldr;
-    int m, cand_grid, scatter_grid, tpc, nchunk, chunk;
+    int m, cand_grid, scatter_grid;
     long long cap_cand;            // entries of cand / gkey / ties
 };
 size_t mc_eigen_smem(int m);
 int mc_max_m();
+int mc_scatter_grid();
+long long mc_gath_entries(int m, int grid);
 cudaError_t mc_configure();
 cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
                             double eta, int first, cudaStream_t s);
