@@ -217,7 +217,8 @@ int setup_block(cdfci_ctx *c, int m) {
     const long long cap_cand = (long long)m * nh_eff + m + 64;
     b.cap_cand = cap_cand;
     b.cand_grid = 152 * 4;
-    b.scatter_grid = mc_scatter_grid();
+    CK(mc_configure());
+    b.scatter_grid = mc_scatter_grid(P);
     if (b.scatter_grid <= 0) return fail(CDFCI_ERR_CUDA, "occupancy query of the scatter failed");
     b.st = c->d_st;
     const size_t n1 = (size_t)m + 1;
@@ -236,7 +237,6 @@ int setup_block(cdfci_ctx *c, int m) {
     if (mb_alloc(c, &c->P.cnz, (size_t)(nbits / 32)))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
     c->P.cnz_mask = nbits - 1;
-    CK(mc_configure());
     return CDFCI_OK;
 }
 

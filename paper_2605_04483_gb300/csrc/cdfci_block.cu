@@ -1050,8 +1050,8 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
 // has the same share (no second wave) and a column spans a few consecutive
 // blocks, each leaving one gather partial for it.
 // ---------------------------------------------------------------------------
-constexpr int kScatterBuf = 4096;   // new candidates of one block pass (<= kScatterSub)
-constexpr int kScatterSub = 4096;   // elements of one block pass (16 per thread)
+constexpr int kScatterQ = 96;       // per-warp queue of elements that need a table lookup (31 + 2 x 32)
+constexpr int kWarpCand = 256;      // per-warp buffer of new candidates (flushed above kWarpCand - 32)
 constexpr int kScatterMinRange = 256;
 
 // blocks in use for T elements on a grid of G: every range holds at least kScatterMinRange elements
@@ -1116,14 +1116,101 @@ __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, u
     return -2;
 }
 
+// One element of the scatter's column (flat index e): its determinant, the hash,
+// H, and whether c_j may be nonzero.  The integral and filter loads are
+// independent, so both are in flight together.
+__device__ __forceinline__ void mc_elem(const Problem &P, const ColLists &L, const SingleEnt *tabA,
+                                        const SingleEnt *tabB, const volatile unsigned long long &A,
+                                        const volatile unsigned long long &B, const volatile unsigned long long &hA,
+                                        const volatile unsigned long long &hB, long long e,
+                                        unsigned long long &oa, unsigned long long &ob, unsigned long long &hk,
+                                        double &H, bool &maybe) {
+    if (e >= P.seg[4]) {                                // opposite-spin double: two single-excitation entries
+        const unsigned idx = (unsigned)(e - P.seg[4]);
+        const unsigned sa = fdiv(idx, P.mg_nsb), sb = idx - sa * (unsigned)(P.nb * P.vb);
+        const SingleEnt ea = tabA[sa], eb = tabB[sb];
+        oa = ea.key;
+        ob = eb.key;
+        hk = ea.h ^ eb.h;
+        const double gv = __ldg(P.g + ea.goff + eb.goff);
+        maybe = cnz_maybe(P, hk);
+        H = apply_parity(gv, (unsigned long long)((ea.info ^ eb.info) & 1));
+    } else {
+        ElemIdx x;
+        decode_element(P, L, A, B, e, oa, ob, x);
+        hk = (x.kind == 0 || x.kind == 2) ? (hash_alpha(oa) ^ hB) : (hA ^ hash_beta(ob));
+        maybe = cnz_maybe(P, hk);
+        H = element_value(P, L, x);
+    }
+}
+
+// The warp's candidate buffer to the global list (one reservation).
+__device__ __forceinline__ void mc_flush_cand(McState *ms, long long *wcand, int &nwc, long long *cand) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    int base = 0;
+    if (lane == 0 && nwc > 0) base = atomicAdd(&ms->n_cand, nwc);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < nwc; i += 32) cand[base + i] = wcand[i];
+    nwc = 0;
+    __syncwarp();
+}
+
+// One queued element of the scatter: look up its slot (insert when it passes
+// the compression rule), add w H to b, gather H c, mark the slot as a
+// candidate of the next selection (its marker appends it to the warp's
+// candidate buffer wc, which goes to the global list, one reservation per
+// flush, when it fills).  Called by a whole warp; `has` = this lane holds an
+// element.  Returns true on a table error (status set).
+__device__ __forceinline__ bool mc_apply(const Problem &P, McState *ms, IterState *st, bool has,
+                                         unsigned long long oa, unsigned long long ob, unsigned long long hk,
+                                         double H, unsigned long long tib, double wi, double &gather, int &c_app,
+                                         int &c_drop, int &c_ins, long long *wcand, int &nwc, long long *cand) {
+    const int lane = threadIdx.x & 31;
+    bool err = false, first = false;
+    long long s = -1;
+    if (has) {
+        const bool big = abs_bits(H) >= tib;
+        bool ins = false, marked = false;
+        double cj = 0.0;
+        s = mc_probe(P, st, oa, ob, hk, big, ins, cj, marked);
+        if (s == -2) {
+            err = true;
+        } else if (s < 0 || !(!is_zero(cj) || big)) {
+            ++c_drop;
+        } else {
+            Slot *sj = P.table + s;
+            atomicAdd(&sj->bv, wi * H);
+            ++c_app;
+            c_ins += ins ? 1 : 0;
+            gather = fma(H, cj, gather);
+            first = ins;
+            if (!ins && !marked) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
+        }
+    }
+    const unsigned int fm = __ballot_sync(0xffffffffu, first);
+    if (first) wcand[nwc + __popc(fm & ((1u << lane) - 1u))] = s;
+    nwc += __popc(fm);
+    if (nwc > kWarpCand - 32) mc_flush_cand(ms, wcand, nwc, cand);
+    return __any_sync(0xffffffffu, err);
+}
+
 __global__ void __launch_bounds__(256, 4) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                     const double *w, const double *thr, long long *cand,
                                                     double *gathp) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    SingleEnt *tabA = reinterpret_cast<SingleEnt *>(s_dyn), *tabB = tabA + P.na * P.va;
     __shared__ ColLists L;
     __shared__ double swarp[8];
-    __shared__ long long s_cand[kScatterBuf];
-    __shared__ int s_ncand, s_base;
-    __shared__ unsigned long long scnt[4];
+    __shared__ int s_cnt[4][8];
+    // the current column: determinant, weight, |H| threshold bits, string hashes (read
+    // through volatile loads, which keeps them out of the loop's registers)
+    __shared__ unsigned long long s_colA, s_colB, s_tib, s_hA, s_hB;
+    __shared__ double s_wi;
+    // per-warp queues of elements that need a lookup (key, hash, H) and candidate buffers
+    __shared__ unsigned long long q_a[8][kScatterQ], q_b[8][kScatterQ], q_h[8][kScatterQ];
+    __shared__ double q_H[8][kScatterQ];
+    __shared__ long long w_cand[8][kWarpCand];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
@@ -1133,92 +1220,106 @@ __global__ void __launch_bounds__(256, 4) k_mc_scatter(Problem P, McState *ms, I
     if (T <= 0 || blockIdx.x >= G) return;
     const long long K = mc_gath_per_col(Lc, T, G);
     const long long f_beg = (long long)blockIdx.x * T / G, f_end = ((long long)blockIdx.x + 1) * T / G;
-    if (tid < 4) scnt[tid] = 0;
-    long long c_el = 0, c_app = 0, c_drop = 0, c_ins = 0;
-    int cur = -1;
-    double gsum = 0.0;                                  // thread 0: this block's gather for column cur
-    McSel xs = {};
-    double wi = 0.0, ti = 0.0;
+    int c_el = 0, c_app = 0, c_drop = 0, c_ins = 0;
+    int nwc = 0;                                        // warp-uniform: entries in w_cand[warp]
+    bool err = false;                                   // warp-uniform
+    const volatile unsigned long long &vA = s_colA, &vB = s_colB, &vtib = s_tib, &vhA = s_hA, &vhB = s_hB;
+    const volatile double &vwi = s_wi;
+    // one pass per column segment of the block's range
     for (long long f0 = f_beg; f0 < f_end;) {
         const int col = (int)(f0 / Lc);
-        const long long cend = (long long)(col + 1) * Lc;
-        const long long f1 = min(f_end, min(cend, f0 + kScatterSub));
-        if (col != cur) {
-            if (cur >= 0 && tid == 0)
-                gathp[(size_t)cur * K + (blockIdx.x - mc_block_of((long long)cur * Lc, T, G))] = gsum;
-            gsum = 0.0;
-            cur = col;
-            xs = sel[col];
-            wi = w[col];
-            ti = thr[col];
-            for (int t = tid; t < P.N; t += 256) {
-                int ra = __popcll(xs.A & low_mask(t)), rb = __popcll(xs.B & low_mask(t));
-                if ((xs.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
-                if ((xs.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
-            }
+        const long long f1 = min(f_end, (long long)(col + 1) * Lc);
+        const McSel xs = sel[col];
+        __syncthreads();                                // the previous segment's lists and tables are done
+        if (tid == 0) {
+            s_colA = xs.A;
+            s_colB = xs.B;
+            s_wi = w[col];
+            s_tib = abs_bits(thr[col]);
+            s_hA = hash_alpha(xs.A);
+            s_hB = hash_beta(xs.B);
         }
-        if (tid == 0) s_ncand = 0;
+        for (int t = tid; t < P.N; t += 256) {
+            int ra = __popcll(xs.A & low_mask(t)), rb = __popcll(xs.B & low_mask(t));
+            if ((xs.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+            if ((xs.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+        }
+        __syncthreads();
+        build_singles(P, L, xs.A, xs.B, tabA, tabB, tid, 256);
         __syncthreads();
         double gather = 0.0;
         const long long e_off = 1 - (long long)col * Lc;
-        for (long long f = f0 + tid; f < f1; f += 256) {
-            const long long e = f + e_off;
-            unsigned long long oa, ob;
-            const double H = column_element(P, L, xs.A, xs.B, e, oa, ob);
-            if (is_zero(H)) continue;
-            ++c_el;
-            const bool big = fabs(H) >= ti;
-            const unsigned long long hk = key_hash(oa, ob);
-            if (!big && !cnz_maybe(P, hk)) { ++c_drop; continue; }       // c_j = 0: the rule drops it
-            bool ins = false, marked = false;
-            double cj = 0.0;
-            const long long s = mc_probe(P, st, oa, ob, hk, big, ins, cj, marked);
-            if (s == -2) break;
-            if (s < 0) { ++c_drop; continue; }
-            if (!(!is_zero(cj) || big)) { ++c_drop; continue; }
-            Slot *sj = P.table + s;
-            atomicAdd(&sj->bv, wi * H);
-            ++c_app;
-            c_ins += ins ? 1 : 0;
-            gather = fma(H, cj, gather);
-            // the thread that marks a slot appends it
-            bool first = ins;
-            if (!ins && !marked) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
-            const unsigned int fm = __ballot_sync(__activemask(), first);
-            if (first) {
-                const int leader = __ffs(fm) - 1;
-                int pos = 0;
-                if (lane == leader) pos = atomicAdd(&s_ncand, __popc(fm));
-                pos = __shfl_sync(fm, pos, leader);
-                const int at = pos + __popc(fm & ((1u << lane) - 1u));
-                if (at < kScatterBuf) s_cand[at] = s;
-                else set_status(st, kErrInternal);
+        const unsigned long long tib = vtib;
+        // Phase 1, every lane: the element and the c != 0 filter; elements that need the
+        // table go to the warp's queue.  Phase 2, whenever 32 are queued: the warp looks
+        // them up together, one per lane, so that no lane waits on another's round trips.
+        int qn = 0;                                     // warp-uniform
+        for (long long fb = f0 + warp * 32; fb < f1 && !err; fb += 512) {
+            // two elements per lane: f and f + 256
+            bool need[2] = {false, false};
+            unsigned long long oa[2] = {0ull, 0ull}, ob[2] = {0ull, 0ull}, hk[2] = {0ull, 0ull};
+            double H[2] = {0.0, 0.0};
+            bool maybe[2] = {false, false};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const long long f = fb + lane + 256 * u;
+                if (f < f1) mc_elem(P, L, tabA, tabB, vA, vB, vhA, vhB, f + e_off, oa[u], ob[u], hk[u], H[u], maybe[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (fb + lane + 256 * u < f1 && !is_zero(H[u])) {
+                    ++c_el;
+                    // |H| >= thr (non-negative doubles order like their bits) or c_j may be nonzero;
+                    // otherwise c_j = 0 and the rule drops it
+                    need[u] = maybe[u] || abs_bits(H[u]) >= tib;
+                    if (!need[u]) ++c_drop;
+                }
+                const unsigned int nm = __ballot_sync(0xffffffffu, need[u]);
+                if (need[u]) {
+                    const int at = qn + __popc(nm & ((1u << lane) - 1u));
+                    q_a[warp][at] = oa[u]; q_b[warp][at] = ob[u]; q_h[warp][at] = hk[u]; q_H[warp][at] = H[u];
+                }
+                qn += __popc(nm);
+            }
+            while (qn >= 32 && !err) {
+                __syncwarp();
+                qn -= 32;
+                const int at = qn + lane;
+                err = mc_apply(P, ms, st, true, q_a[warp][at], q_b[warp][at], q_h[warp][at], q_H[warp][at], tib, vwi,
+                               gather, c_app, c_drop, c_ins, w_cand[warp], nwc, cand);
+                __syncwarp();
             }
         }
-        // the pass's gather: a fixed tree in each warp, the warps in order
+        if (qn > 0 && !err) {                           // the rest of the queue
+            __syncwarp();
+            const bool has = lane < qn;
+            err = mc_apply(P, ms, st, has, has ? q_a[warp][lane] : 0ull, has ? q_b[warp][lane] : 0ull,
+                           has ? q_h[warp][lane] : 0ull, has ? q_H[warp][lane] : 0.0, tib, vwi, gather, c_app,
+                           c_drop, c_ins, w_cand[warp], nwc, cand);
+            __syncwarp();
+        }
+        // the segment's gather: a fixed tree in each warp, the warps in order
         for (int o = 16; o > 0; o >>= 1) gather += __shfl_down_sync(0xffffffffu, gather, o);
         if (lane == 0) swarp[warp] = gather;
         __syncthreads();
         if (tid == 0) {
             double t = swarp[0];
             for (int q = 1; q < 8; ++q) t += swarp[q];
-            gsum += t;
+            gathp[(size_t)col * K + (blockIdx.x - mc_block_of((long long)col * Lc, T, G))] = t;
         }
-        // this pass's new candidates: one reservation per block
-        const int nb = min(s_ncand, kScatterBuf);
-        if (tid == 0) s_base = nb > 0 ? atomicAdd(&ms->n_cand, nb) : 0;
-        __syncthreads();
-        for (int i = tid; i < nb; i += 256) cand[s_base + i] = s_cand[i];
         f0 = f1;
-        __syncthreads();
     }
-    if (cur >= 0 && tid == 0) gathp[(size_t)cur * K + (blockIdx.x - mc_block_of((long long)cur * Lc, T, G))] = gsum;
-    atomicAdd((unsigned long long *)&scnt[0], (unsigned long long)c_el);
-    atomicAdd((unsigned long long *)&scnt[1], (unsigned long long)c_app);
-    atomicAdd((unsigned long long *)&scnt[2], (unsigned long long)c_drop);
-    atomicAdd((unsigned long long *)&scnt[3], (unsigned long long)c_ins);
+    mc_flush_cand(ms, w_cand[warp], nwc, cand);
+    // counters: warp sums, then the warps in order
+    const int r0 = __reduce_add_sync(0xffffffffu, c_el), r1 = __reduce_add_sync(0xffffffffu, c_app);
+    const int r2 = __reduce_add_sync(0xffffffffu, c_drop), r3 = __reduce_add_sync(0xffffffffu, c_ins);
+    if (lane == 0) { s_cnt[0][warp] = r0; s_cnt[1][warp] = r1; s_cnt[2][warp] = r2; s_cnt[3][warp] = r3; }
     __syncthreads();
-    if (tid < 4) atomicAdd((unsigned long long *)&ms->cnt[tid], (unsigned long long)scnt[tid]);
+    if (tid < 4) {
+        unsigned long long t = 0;
+        for (int q = 0; q < 8; ++q) t += (unsigned long long)s_cnt[tid][q];
+        atomicAdd((unsigned long long *)&ms->cnt[tid], t);
+    }
 }
 
 // b_I recalculated (Eq. recalculate-b), the chosen coordinates join the
@@ -1358,12 +1459,14 @@ size_t mc_eigen_smem(int m) {
 int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
 int mc_max_m() { return kEigMaxN - 1; }
 
+// the scatter's dynamic shared memory: the column's single-excitation tables
+size_t mc_scatter_smem(const Problem &P) { return (size_t)(P.na * P.va + P.nb * P.vb + 1) * sizeof(SingleEnt); }
 // the scatter's grid: the blocks that are resident at once on this device
-int mc_scatter_grid() {
+int mc_scatter_grid(const Problem &P) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_scatter, 256, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_scatter, 256, mc_scatter_smem(P)) != cudaSuccess)
         return 0;
     return sms * std::max(per, 1);
 }
@@ -1373,6 +1476,10 @@ long long mc_gath_entries(int m, int grid) { return 2ll * grid + 2ll * m + 8; }
 cudaError_t mc_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)mc_eigen_smem(kEigSmemN - 1));
+    if (e != cudaSuccess) return e;
+    // N <= 64: at most 2 x 32 x 32 single-excitation entries
+    e = cudaFuncSetAttribute(k_mc_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((2 * 32 * 32 + 1) * sizeof(SingleEnt)));
     if (e != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -1384,7 +1491,7 @@ cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long 
 }
 
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s) {
-    k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp);
+    k_mc_scatter<<<b.scatter_grid, 256, mc_scatter_smem(P), s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp);
     k_mc_finalize<<<1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.scatter_grid);
     return cudaGetLastError();
 }

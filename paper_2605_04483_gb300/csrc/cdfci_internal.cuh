@@ -460,6 +460,41 @@ __device__ __forceinline__ double element_value(const Problem &P, const ColLists
     return apply_parity(v, x.sgn);
 }
 
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// One single excitation of the column determinant (per-iteration table): the
+// changed string, its hash, the offset of its orbital pair in g, the sign and
+// the orbitals (info = sign | i << 8 | a << 16).
+struct SingleEnt {
+    unsigned long long key, h;
+    int goff;                          // alpha table: (i N + a) N^2;  beta table: j N + b
+    int info;
+};
+
+__device__ __forceinline__ int j_b_off(int N, int j, int b) { return j * N + b; }
+
+__device__ __forceinline__ void build_singles(const Problem &P, const ColLists &L, unsigned long long iA,
+                                              unsigned long long iB, SingleEnt *tabA, SingleEnt *tabB, int t0, int nt) {
+    const int na_va = P.na * P.va, nb_vb = P.nb * P.vb, N = P.N;
+    for (int s = t0; s < na_va + nb_vb; s += nt) {
+        const bool alpha = s < na_va;
+        const int sl = alpha ? s : s - na_va;
+        const int o = (int)fdiv((unsigned)sl, alpha ? P.mg_va : P.mg_vb);
+        const int w = sl - o * (alpha ? P.va : P.vb);
+        const int i = alpha ? L.occA[o] : L.occB[o];
+        const int a = alpha ? L.virA[w] : L.virB[w];
+        const unsigned long long X = alpha ? iA : iB;
+        SingleEnt e;
+        e.key = X ^ (1ull << i) ^ (1ull << a);
+        e.h = alpha ? hash_alpha(e.key) : hash_beta(e.key);
+        e.goff = alpha ? (i * N + a) * N * N : j_b_off(N, i, a);
+        e.info = (__popcll(X & between_mask(i, a)) & 1) | (i << 8) | (a << 16);
+        (alpha ? tabA : tabB)[sl] = e;
+    }
+}
+
 // One element of the column of {A, B}: flat index e in [1, nh).  Returns the
 // value H_{D',D} (0.0 when the Slater-Condon element vanishes) and the key D'.
 __device__ __forceinline__ double column_element(const Problem &P, const ColLists &L, unsigned long long A,

@@ -85,7 +85,7 @@ struct McBuffers {
 };
 size_t mc_eigen_smem(int m);
 int mc_max_m();
-int mc_scatter_grid();
+int mc_scatter_grid(const Problem &P);
 long long mc_gath_entries(int m, int grid);
 cudaError_t mc_configure();
 cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
