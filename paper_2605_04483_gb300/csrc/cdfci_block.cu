@@ -712,36 +712,85 @@ __device__ __forceinline__ float f_row(const float *Ah, int ld, int n, int row, 
 __host__ __device__ __forceinline__ int eig_tpr(int n1) { return n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1); }
 __host__ __device__ __forceinline__ int eig_lds(int ldr, int tpr) { return ldr + 32 / tpr; }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// FP64 sums of K values over the first nw warps of the block (fixed trees);
+// every lane of warp 0 gets them after the caller's barrier via red_sum.
+template <int K>
+__device__ __forceinline__ void red_warp(double (&v)[K], double *scr, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp >= nw) return;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) scr[warp * K + k] = v[k];
+}
+template <int K>
+__device__ __forceinline__ void red_sum(double (&v)[K], const double *scr, int nw) {   // warp 0, after the barrier
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double t = lane < nw ? scr[lane * K + k] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        v[k] = t;
+    }
+}
+
 __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                        const double *cI, const double *bI, const double *HIIc,
                                                        float *Rh, float *Rl, int ldr, int tpr, int use_smem,
                                                        double *w, double *thr, double *etaout) {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     __shared__ float s_rf[2 * 32 * 16];
     __shared__ ff s_rff[2 * 32 * 2];
-    __shared__ double s_sc[4];
+    __shared__ double s_red[32 * 4];
+    __shared__ double s_sc[8];
+    __shared__ dd s_snew;
+    __shared__ int s_nzr[2][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
+    const int wm = (m + 31) >> 5;                       // warps holding a coordinate of I (thread t: coordinate t)
     int hf = 0, hff = 0;
-
-    // 1. scalars over I (warp 0, FP64): nonzeros, c.c, c.b, c.H_II c; the
-    //    degenerate case (c has no support outside I); nu = |c - E_I c_I|; R_00
-    if (warp == 0) {
-        int nz = 0;
-        double cc = 0.0, cb = 0.0, chc = 0.0;
-        for (int i = lane; i < m; i += 32) {
-            const double c = cI[i];
-            nz += (c != 0.0) ? 1 : 0;
-            cc = fma(c, c, cc);
-            cb = fma(c, bI[i], cb);
-            chc = fma(c, HIIc[i], chc);
+    const int lds = eig_lds(ldr, tpr);
+    float *sh = sm, *sl = sm + (size_t)(m + 1) * lds;
+    // 0. start the copy of R (rows 0..m) into shared memory; it completes behind step 1
+    if (use_smem) {
+        const float4 *gh = reinterpret_cast<const float4 *>(Rh), *gl = reinterpret_cast<const float4 *>(Rl);
+        const int q = ldr / 4, nv = (m + 1) * q;
+        for (int t = tid; t < nv; t += blockDim.x) {
+            const int r = t / q, c = 4 * (t - r * q);
+            cp_async16(sh + r * lds + c, gh + t);
+            cp_async16(sl + r * lds + c, gl + t);
         }
-        nz = __reduce_add_sync(0xffffffffu, nz);
-        cc = wsum_d(cc);
-        cb = wsum_d(cb);
-        chc = wsum_d(chc);
+    }
+    float *vec = use_smem ? sm + 2 * (size_t)(m + 1) * lds : sm;
+    double *s_cI = reinterpret_cast<double *>(vec + 4 * ((3 * (m + 1) + 3) / 4) + 2 * (m + 1));   // m doubles
+
+    // 1. scalars over I (FP64): nonzeros, c.c, c.b, c.H_II c; the degenerate case
+    //    (c has no support outside I); nu = |c - E_I c_I|; R_00
+    double ct = 0.0, bt = 0.0, ht = 0.0;
+    if (tid < m) { ct = cI[tid]; bt = bI[tid]; ht = HIIc[tid]; s_cI[tid] = ct; }
+    {
+        double v[3] = {ct * ct, ct * bt, ct * ht};
+        red_warp<3>(v, s_red, wm);
+        const int nzw = __reduce_add_sync(0xffffffffu, (tid < m && ct != 0.0) ? 1 : 0);
+        if (lane == 0) s_nzr[0][warp] = nzw;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double v[3];
+        red_sum<3>(v, s_red, wm);
+        int nz = 0;
+        for (int q = 0; q < wm; ++q) nz += s_nzr[0][q];
         if (lane == 0) {
+            const double cc = v[0], cb = v[1], chc = v[2];
             const dd nu2 = dd_add(ms->mu, dd{-cc, 0.0});
             const bool deg = (nz >= ms->nnz_c) || !(nu2.hi > 0.0);
             s_sc[0] = deg ? 1.0 : 0.0;
@@ -750,60 +799,41 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             s_sc[3] = cc;
         }
     }
-    __syncthreads();
+    if (use_smem) cp_async_wait_all();
+    __syncthreads();                                    // scalars, and this block's copy of R, complete
     const bool deg = s_sc[0] != 0.0;
     const double nu = s_sc[1];
     const int off = deg ? 1 : 0;
     const int n = m + 1 - off;                          // active size
     const int k0 = 1 - off;                             // active index of coordinate 0
+    // row and column 0 of R: R_0i = (b_i - (H_II c_I)_i) / nu
     if (!deg) {
-        for (int i = tid; i < m; i += blockDim.x) {
-            const ff r0 = ff_from_double((bI[i] - HIIc[i]) / nu);
-            Rh[i + 1] = r0.hi; Rl[i + 1] = r0.lo;
-            Rh[(size_t)(i + 1) * ldr] = r0.hi; Rl[(size_t)(i + 1) * ldr] = r0.lo;
+        if (tid < m) {
+            const ff r0 = ff_from_double((bt - ht) / nu);
+            if (use_smem) {
+                sh[tid + 1] = r0.hi; sl[tid + 1] = r0.lo;
+                sh[(tid + 1) * lds] = r0.hi; sl[(tid + 1) * lds] = r0.lo;
+            } else {
+                Rh[tid + 1] = r0.hi; Rl[tid + 1] = r0.lo;
+                Rh[(size_t)(tid + 1) * ldr] = r0.hi; Rl[(size_t)(tid + 1) * ldr] = r0.lo;
+            }
         }
         if (tid == 0) {
             const ff r00 = ff_from_double(s_sc[2]);
-            Rh[0] = r00.hi; Rl[0] = r00.lo;
+            if (use_smem) { sh[0] = r00.hi; sl[0] = r00.lo; }
+            else { Rh[0] = r00.hi; Rl[0] = r00.lo; }
         }
     }
-    __syncthreads();
     const float *Ah, *Al;
     int ld;
-    float *vec;
     if (use_smem) {
-        // rows 0..m of R into shared memory with the row stride lds (no bank
-        // conflicts for the groups' reads); 16-byte loads, eight in flight per thread
-        const int lds = eig_lds(ldr, tpr);
-        float *sh = sm, *sl = sm + (size_t)(m + 1) * lds;
-        const float4 *gh = reinterpret_cast<const float4 *>(Rh), *gl = reinterpret_cast<const float4 *>(Rl);
-        const int q = ldr / 4, nv = (m + 1) * q;
-        for (int t0 = tid; t0 < nv; t0 += 4 * (int)blockDim.x) {
-            float4 a[4], b[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int t = t0 + u * (int)blockDim.x;
-                if (t < nv) { a[u] = __ldcg(gh + t); b[u] = __ldcg(gl + t); }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int t = t0 + u * (int)blockDim.x;
-                if (t < nv) {
-                    const int r = t / q, c = 4 * (t - r * q);
-                    *reinterpret_cast<float4 *>(sh + r * lds + c) = a[u];
-                    *reinterpret_cast<float4 *>(sl + r * lds + c) = b[u];
-                }
-            }
-        }
         Ah = sh + off * lds + off;
         Al = sl + off * lds + off;
         ld = lds;
-        vec = sm + 2 * (size_t)(m + 1) * lds;
     } else {
         Ah = Rh + (size_t)off * ldr + off;
         Al = Rl + (size_t)off * ldr + off;
         ld = ldr;
-        vec = sm;
     }
     float *xs = vec;                                    // float-float x (2 n floats)
     float *ws = vec + 2 * n;                            // FP32 w (n floats)
@@ -817,10 +847,10 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     const double inv0 = zz0 > 0.0 ? 1.0 / sqrt(zz0) : 0.0;
     ff x = {0.0f, 0.0f};
     if (act) {
-        const double v0 = (row < k0) ? nu : cI[row - k0];
+        const double v0 = (row < k0) ? nu : s_cI[row - k0];
         x = ff_from_double(zz0 > 0.0 ? v0 * inv0 : (row == 0 ? 1.0 : 0.0));
     }
-    __syncthreads();                                    // the copy of A is complete
+    __syncthreads();                                    // row and column 0 of A are in place
     const float d = act ? Ah[row * ld + row] : 0.0f;
     float pv = 0.0f, apv = 0.0f;                        // search direction p and A p
     bool have_p = false;
@@ -937,34 +967,37 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         if (tid == 0) set_status(st, kErrNotNegative);
         return;
     }
-    const double zs = sqrt(-lamd / ff_to_double(xx));
-    if (lead) zd[row] = ff_to_double(x) * zs;
+    if (lead) zd[row] = ff_to_double(x);
     __syncthreads();
-    // sign (Eq. def-z wants gamma >= 0): z_0 >= 0; degenerate or z_0 = 0: z . [nu; c_I] >= 0
+    // sign (Eq. def-z wants gamma >= 0): z_0 >= 0; degenerate or z_0 = 0: z . [nu; c_I] >= 0;
+    // gamma, the new scale and its reciprocal (warp 0; the scaling by |z| / |x| > 0 keeps the signs)
     if (warp == 0) {
         double dot = 0.0;
-        for (int i = lane; i < m; i += 32) dot = fma(zd[i + k0], cI[i], dot);
+        for (int i = lane; i < m; i += 32) dot = fma(zd[i + k0], s_cI[i], dot);
         dot = wsum_d(dot);
         if (lane == 0) {
-            const double z0 = deg ? 0.0 : zd[0];
+            const double zs = sqrt(-lamd / ff_to_double(xx));
+            const double z0 = deg ? 0.0 : zd[0] * zs;
             const double sgn = (z0 < 0.0 || (z0 == 0.0 && dot < 0.0)) ? -1.0 : 1.0;
             const double gamma = deg ? 1.0 : sgn * z0 / nu;
-            s_sc[0] = sgn;
-            s_sc[1] = gamma;
+            const dd s_new = dd_mul_d(ms->scale, gamma);
+            s_sc[4] = sgn;
+            s_sc[5] = gamma;
+            s_sc[6] = zs;
+            s_sc[7] = 1.0 / s_new.hi;
+            s_snew = s_new;
         }
     }
     __syncthreads();
-    const double sgn = s_sc[0], gamma = s_sc[1];
+    const double sgn = s_sc[4], gamma = s_sc[5], zs = s_sc[6], rsc = s_sc[7];
     const bool bad = !isfinite(gamma) || !(gamma > 1e-200);
-    const dd s_new = dd_mul_d(ms->scale, gamma);
-    const double rsc = 1.0 / s_new.hi;
-    // 4. eta (Eq. def-z), the new stored c_I, the scatter weights (thread i: coordinate i)
+    // 4. eta (Eq. def-z), the new stored c_I, the scatter weights (thread i: coordinate i);
+    //    eta also goes to x in the active indexing (float-float) for eta^T H_II eta
     double eta = 0.0;
     int nz_from = 0, nz_to = 0;
     if (tid < m) {
-        const double zn = sgn * zd[tid + k0];
-        const double ci = cI[tid];
-        eta = zn - gamma * ci;
+        const double zn = sgn * (zd[tid + k0] * zs);
+        eta = zn - gamma * ct;
         etaout[tid] = eta;
         w[tid] = eta * rsc;
         thr[tid] = eta != 0.0 ? P.tau / fabs(eta) : 1.0e308;
@@ -972,45 +1005,32 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             P.table[sel[tid].slot].c = zn * rsc;
             cnz_set(P, sel[tid].A, sel[tid].B);
         }
-        nz_from = (ci != 0.0 && zn == 0.0) ? 1 : 0;
-        nz_to = (ci == 0.0 && zn != 0.0) ? 1 : 0;
+        nz_from = (ct != 0.0 && zn == 0.0) ? 1 : 0;
+        nz_to = (ct == 0.0 && zn != 0.0) ? 1 : 0;
+        const ff e = ff_from_double(eta);
+        xs[2 * (tid + k0)] = e.hi;
+        xs[2 * (tid + k0) + 1] = e.lo;
     }
-    // eta in the active indexing (float-float) for eta^T H_II eta
-    __syncthreads();                                    // zd reads are done
-    if (lead) {
-        const ff e = (row >= k0) ? ff_from_double(sgn * zd[row] - gamma * cI[row - k0]) : ff{0.0f, 0.0f};
-        xs[2 * row] = e.hi;
-        xs[2 * row + 1] = e.lo;
+    if (tid == 0 && k0 == 1) { xs[0] = 0.0f; xs[1] = 0.0f; }
+    // eta . c_I, eta . b_I, eta . eta and the nonzero changes: warp partials
+    {
+        double v[3] = {eta * ct, eta * bt, eta * eta};
+        red_warp<3>(v, s_red, wm);
+        const int a = __reduce_add_sync(0xffffffffu, nz_from), b = __reduce_add_sync(0xffffffffu, nz_to);
+        if (lane == 0) { s_nzr[0][warp] = a; s_nzr[1][warp] = b; }
     }
     __syncthreads();
     {
         const ff he = ff_row(Ah, Al, ld, n, row, kk, tpr, act, xs);
         ff t[1] = {lead ? ff_mul(ff{xs[2 * row], xs[2 * row + 1]}, he) : ff{0.0f, 0.0f}};
         bsum_ff<1>(t, s_rff, hff);
-        if (tid == 0) s_sc[2] = ff_to_double(t[0]);
-    }
-    // eta . c_I, eta . b_I, eta . eta (warp 0, FP64) and the nonzero changes
-    if (tid < m) zd[tid] = eta;
-    {
-        int a = __reduce_add_sync(0xffffffffu, nz_from), b = __reduce_add_sync(0xffffffffu, nz_to);
-        __shared__ int s_nz[2][32];
-        if (lane == 0) { s_nz[0][warp] = a; s_nz[1][warp] = b; }
-        __syncthreads();
         if (warp == 0) {
-            const int nw = blockDim.x >> 5;
+            const double eHe = ff_to_double(t[0]);
+            double v[3];
+            red_sum<3>(v, s_red, wm);
+            const double ec = v[0], eb = v[1], ee = v[2];
             int fa = 0, fb = 0;
-            for (int q = 0; q < nw; ++q) { fa += s_nz[0][q]; fb += s_nz[1][q]; }
-            double ec = 0.0, eb = 0.0, ee = 0.0;
-            for (int i = lane; i < m; i += 32) {
-                const double e = zd[i];
-                ec = fma(e, cI[i], ec);
-                eb = fma(e, bI[i], eb);
-                ee = fma(e, e, ee);
-            }
-            ec = wsum_d(ec);
-            eb = wsum_d(eb);
-            ee = wsum_d(ee);
-            const double eHe = s_sc[2];
+            for (int q = 0; q < wm; ++q) { fa += s_nzr[0][q]; fb += s_nzr[1][q]; }
             // mu and alpha (Alg. 2 update of c) in double-double: lane 0 mu, lane 1 alpha
             const dd g2 = dd_two_prod(gamma, gamma);
             dd out = {0.0, 0.0};
@@ -1024,8 +1044,8 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
                 } else {
                     ms->mu = mu_n;
                     ms->alpha = al_n;
-                    ms->scale = s_new;
-                    st->scale = s_new;
+                    ms->scale = s_snew;
+                    st->scale = s_snew;
                 }
                 ms->energy = dd_div_to_d(ms->alpha, ms->mu);
                 ms->iterations += 1;
@@ -1453,7 +1473,8 @@ __global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, do
 size_t mc_eigen_smem(int m) {
     const int n1 = m + 1, ldr = 32 * ((n1 + 31) / 32);
     const size_t lds = (size_t)eig_lds(ldr, eig_tpr(n1));
-    const size_t vec = 4 * ((3 * (size_t)n1 + 3) / 4) + 2 * (size_t)n1;   // x (float-float), w, eta (FP64)
+    // x (float-float), w, z / eta (FP64), c_I (FP64)
+    const size_t vec = 4 * ((3 * (size_t)n1 + 3) / 4) + 2 * (size_t)n1 + 2 * (size_t)m;
     return ((n1 <= kEigSmemN ? 2 * (size_t)n1 * lds : 0) + vec) * sizeof(float);
 }
 int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
