@@ -218,7 +218,7 @@ int setup_block(cdfci_ctx *c, int m) {
     b.cap_cand = cap_cand;
     b.cand_grid = 152 * 4;
     CK(mc_configure());
-    b.scatter_grid = mc_scatter_grid(P);
+    b.scatter_grid = 2 * mc_scatter_grid(P);         // twice the resident blocks: late blocks even out the SMs
     if (b.scatter_grid <= 0) return fail(CDFCI_ERR_CUDA, "occupancy query of the scatter failed");
     b.st = c->d_st;
     const size_t n1 = (size_t)m + 1;

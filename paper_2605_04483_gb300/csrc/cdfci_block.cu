@@ -757,6 +757,14 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
     const int wm = (m + 31) >> 5;                       // warps holding a coordinate of I (thread t: coordinate t)
+    // the state scalars, loaded (thread 0) ahead of the sums; read after the barriers below
+    __shared__ dd s_mu0, s_al0, s_sc0;
+    __shared__ long long s_nnz0, s_its0, s_eit0;
+    __shared__ double s_dx0;
+    if (tid == 0) {
+        s_mu0 = ms->mu; s_al0 = ms->alpha; s_sc0 = ms->scale;
+        s_nnz0 = ms->nnz_c; s_its0 = ms->iterations; s_eit0 = ms->eig_iters_total; s_dx0 = ms->dx;
+    }
     int hf = 0, hff = 0;
     const int lds = eig_lds(ldr, tpr);
     float *sh = sm, *sl = sm + (size_t)(m + 1) * lds;
@@ -791,11 +799,11 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         for (int q = 0; q < wm; ++q) nz += s_nzr[0][q];
         if (lane == 0) {
             const double cc = v[0], cb = v[1], chc = v[2];
-            const dd nu2 = dd_add(ms->mu, dd{-cc, 0.0});
-            const bool deg = (nz >= ms->nnz_c) || !(nu2.hi > 0.0);
+            const dd nu2 = dd_add(s_mu0, dd{-cc, 0.0});
+            const bool deg = (nz >= s_nnz0) || !(nu2.hi > 0.0);
             s_sc[0] = deg ? 1.0 : 0.0;
             s_sc[1] = deg ? 0.0 : sqrt(nu2.hi);
-            s_sc[2] = deg ? 0.0 : dd_div_to_d(dd_add(dd_add(ms->alpha, dd{-2.0 * cb, 0.0}), dd{chc, 0.0}), nu2);
+            s_sc[2] = deg ? 0.0 : dd_div_to_d(dd_add(dd_add(s_al0, dd{-2.0 * cb, 0.0}), dd{chc, 0.0}), nu2);
             s_sc[3] = cc;
         }
     }
@@ -980,7 +988,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             const double z0 = deg ? 0.0 : zd[0] * zs;
             const double sgn = (z0 < 0.0 || (z0 == 0.0 && dot < 0.0)) ? -1.0 : 1.0;
             const double gamma = deg ? 1.0 : sgn * z0 / nu;
-            const dd s_new = dd_mul_d(ms->scale, gamma);
+            const dd s_new = dd_mul_d(s_sc0, gamma);
             s_sc[4] = sgn;
             s_sc[5] = gamma;
             s_sc[6] = zs;
@@ -1034,12 +1042,14 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             // mu and alpha (Alg. 2 update of c) in double-double: lane 0 mu, lane 1 alpha
             const dd g2 = dd_two_prod(gamma, gamma);
             dd out = {0.0, 0.0};
-            if (lane == 0) out = dd_add(dd_add(dd_mul(g2, ms->mu), dd_two_prod(2.0 * gamma, ec)), dd{ee, 0.0});
-            if (lane == 1) out = dd_add(dd_add(dd_mul(g2, ms->alpha), dd_two_prod(2.0 * gamma, eb)), dd{eHe, 0.0});
+            if (lane == 0) out = dd_add(dd_add(dd_mul(g2, s_mu0), dd_two_prod(2.0 * gamma, ec)), dd{ee, 0.0});
+            if (lane == 1) out = dd_add(dd_add(dd_mul(g2, s_al0), dd_two_prod(2.0 * gamma, eb)), dd{eHe, 0.0});
             const dd al_n = {__shfl_sync(0xffffffffu, out.hi, 1), __shfl_sync(0xffffffffu, out.lo, 1)};
             if (lane == 0) {
                 const dd mu_n = out;
-                if (bad || !isfinite(mu_n.hi) || !isfinite(al_n.hi)) {
+                const bool ok = !(bad || !isfinite(mu_n.hi) || !isfinite(al_n.hi));
+                const dd mu_k = ok ? mu_n : s_mu0, al_k = ok ? al_n : s_al0;
+                if (!ok) {
                     set_status(st, kErrNonfinite);
                 } else {
                     ms->mu = mu_n;
@@ -1047,15 +1057,16 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
                     ms->scale = s_snew;
                     st->scale = s_snew;
                 }
-                ms->energy = dd_div_to_d(ms->alpha, ms->mu);
-                ms->iterations += 1;
-                ms->dx = P.theta * ms->dx + (1.0 - P.theta) * sqrt(ee);
-                if (P.dx_threshold > 0.0 && ms->dx < P.dx_threshold) ms->done_pending = 1;
-                ms->nnz_c += fb - fa;
+                const double dxn = P.theta * s_dx0 + (1.0 - P.theta) * sqrt(ee);
+                ms->energy = dd_div_to_d(al_k, mu_k);
+                ms->iterations = s_its0 + 1;
+                ms->dx = dxn;
+                if (P.dx_threshold > 0.0 && dxn < P.dx_threshold) ms->done_pending = 1;
+                ms->nnz_c = s_nnz0 + (fb - fa);
                 ms->degenerate = deg ? 1 : 0;
                 ms->last_gamma = gamma;
                 ms->eig_iters = it;
-                ms->eig_iters_total += it;
+                ms->eig_iters_total = s_eit0 + it;
                 ms->n_cand = 0;                         // the scatter builds the next candidate list
             }
         }
@@ -1348,56 +1359,86 @@ __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel
                               const double *gathp, long long *cand, const double *etaout, int grid) {
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
+    const int lane = threadIdx.x & 31;
     const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
     const long long Lc = nh - 1, T = (long long)m * Lc;
     const long long G = mc_scatter_blocks(T, grid), K = T > 0 ? mc_gath_per_col(Lc, T, G) : 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const long long slot = sel[i].slot;
-        double t = 0.0;
-        if (T > 0) {
-            // the column's blocks in order
-            const long long nb = mc_block_of((long long)(i + 1) * Lc - 1, T, G) - mc_block_of((long long)i * Lc, T, G);
-            for (long long k = 0; k <= nb; ++k) t += gathp[(size_t)i * K + k];
+    int nd = 0;                                         // this thread's nonzero diagonals
+    for (int i0 = 0; i0 < m; i0 += blockDim.x) {        // block-uniform rounds
+        const int i = i0 + (int)threadIdx.x;
+        bool append = false;
+        long long slot = 0;
+        if (i < m) {
+            slot = sel[i].slot;
+            const double hd = Hdiag[i];
+            nd += hd != 0.0 ? 1 : 0;
+            double t = 0.0;
+            if (T > 0) {
+                // the column's blocks in order
+                const long long nb = mc_block_of((long long)(i + 1) * Lc - 1, T, G) - mc_block_of((long long)i * Lc, T, G);
+                for (long long k = 0; k <= nb; ++k) t += gathp[(size_t)i * K + k];
+            }
+            Slot *s = P.table + slot;
+            s->bv = fma(hd, s->c, t);
+            const unsigned long long kb = s->b;
+            if (!(kb & kMarkB)) {
+                s->b = kb | kMarkB;
+                append = true;
+            }
         }
-        Slot *s = P.table + slot;
-        s->bv = fma(Hdiag[i], s->c, t);
-        const unsigned long long kb = s->b;
-        if (!(kb & kMarkB)) {
-            s->b = kb | kMarkB;
-            const int pos = atomicAdd(&ms->n_cand, 1);
-            cand[pos] = slot;
+        // the chosen coordinates join the candidates: one reservation per warp
+        const unsigned int am = __ballot_sync(0xffffffffu, append);
+        if (am) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&ms->n_cand, __popc(am));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (append) cand[base + __popc(am & ((1u << lane) - 1u))] = slot;
         }
     }
+    __shared__ int s_nd;
+    if (threadIdx.x == 0) s_nd = 0;
+    __syncthreads();
+    if (nd) atomicAdd(&s_nd, nd);
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long nd = 0;
-        for (int i = 0; i < m; ++i) nd += Hdiag[i] != 0.0 ? 1 : 0;
-        ms->elements += ms->cnt[0] + nd;
-        ms->applied += ms->cnt[1] + nd;
-        ms->dropped += ms->cnt[2];
-        ms->inserted += ms->cnt[3];
-        ms->n_slots += ms->cnt[3];
-        ms->last_column = ms->cnt[0] + nd;
+        // every field read first (independent loads), then written
+        const long long nd_all = s_nd;
+        const unsigned long long c0 = ms->cnt[0], c1 = ms->cnt[1], c2 = ms->cnt[2], c3 = ms->cnt[3];
+        const long long el = ms->elements + (long long)c0 + nd_all, ap = ms->applied + (long long)c1 + nd_all;
+        const long long dr = ms->dropped + (long long)c2, in = ms->inserted + (long long)c3;
+        const long long ns = ms->n_slots + (long long)c3;
+        const long long its = ms->iterations, nnz = ms->nnz_c, eit = ms->eig_iters_total;
+        const dd mu = ms->mu, al = ms->alpha;
+        const double dx = ms->dx, en = ms->energy;
+        const int done = ms->done_pending ? 1 : ms->done;
+        const double eta0 = m > 0 ? etaout[0] : 0.0;
+        const unsigned long long la = m > 0 ? sel[0].A : 0ull, lb = m > 0 ? sel[0].B : 0ull;
+        ms->elements = el;
+        ms->applied = ap;
+        ms->dropped = dr;
+        ms->inserted = in;
+        ms->n_slots = ns;
+        ms->last_column = (long long)c0 + nd_all;
         for (int k = 0; k < 4; ++k) ms->cnt[k] = 0;
-        if (ms->n_slots > P.max_entries) set_status(st, kErrTableFull);
-        st->iterations = ms->iterations;
-        st->nnz_c = ms->nnz_c;
-        st->n_slots = ms->n_slots;
-        st->elements = ms->elements;
-        st->applied = ms->applied;
-        st->dropped = ms->dropped;
-        st->inserted = ms->inserted;
-        st->last_column = ms->last_column;
-        st->eig_iters = ms->eig_iters_total;
-        st->mu = ms->mu;
-        st->alpha = ms->alpha;
-        st->dx = ms->dx;
-        st->energy = ms->energy;
-        st->last_eta = m > 0 ? etaout[0] : 0.0;
-        st->last_a = m > 0 ? sel[0].A : 0ull;
-        st->last_b = m > 0 ? sel[0].B : 0ull;
-        if (ms->done_pending) ms->done = 1;
-        st->done = ms->done;
+        ms->done = done;
+        if (ns > P.max_entries) set_status(st, kErrTableFull);
+        st->iterations = its;
+        st->nnz_c = nnz;
+        st->n_slots = ns;
+        st->elements = el;
+        st->applied = ap;
+        st->dropped = dr;
+        st->inserted = in;
+        st->last_column = (long long)c0 + nd_all;
+        st->eig_iters = eit;
+        st->mu = mu;
+        st->alpha = al;
+        st->dx = dx;
+        st->energy = en;
+        st->last_eta = eta0;
+        st->last_a = la;
+        st->last_b = lb;
+        st->done = done;
     }
 }
 
