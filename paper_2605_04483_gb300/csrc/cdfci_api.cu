@@ -237,6 +237,9 @@ int setup_block(cdfci_ctx *c, int m) {
     if (mb_alloc(c, &c->P.cnz, (size_t)(nbits / 32)))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
     c->P.cnz_mask = nbits - 1;
+    // candidate marks: one bit per slot
+    if (mb_alloc(c, &c->P.mark, (size_t)((P.capacity + 31) / 32)))
+        return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
     return CDFCI_OK;
 }
 
@@ -395,6 +398,7 @@ int reset_state(cdfci_ctx *c) {
     CK(cudaMemsetAsync(c->d_table, 0, (size_t)c->P.capacity * sizeof(Slot), c->stream));
     if (c->block) CK(cudaMemsetAsync(c->mb.ms, 0, sizeof(McState), c->stream));
     if (c->P.cnz) CK(cudaMemsetAsync(c->P.cnz, 0, (size_t)(c->P.cnz_mask + 1) / 8, c->stream));
+    if (c->P.mark) CK(cudaMemsetAsync(c->P.mark, 0, (size_t)((c->P.capacity + 31) / 32) * 4, c->stream));
     return CDFCI_OK;
 }
 }  // namespace

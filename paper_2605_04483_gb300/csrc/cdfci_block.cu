@@ -371,12 +371,11 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterSt
             set_status(st, kErrInternal);                  // a candidate outside the table: skip it
             gkey[t] = 0ull;
         } else if (ok) {
-            Slot *s = P.table + cand[t];
-            const ulonglong2 key = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
-            const double2 v = __ldcg(reinterpret_cast<const double2 *>(&s->c));
+            const long long slot = cand[t];
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(&P.table[slot].c));
             k = (unsigned long long)__double_as_longlong(fma(mu, v.x, v.y)) & 0x7fffffffffffffffull;
             gkey[t] = k;
-            if (key.y & kMarkB) s->b = key.y & kKeyMaskB;     // clear the candidate mark
+            mark_clear(P, slot);                           // clear the candidate mark
         }
         if (count) sel_bin_add(sh, ok, sel_digit(k, 0));
     }
@@ -597,6 +596,8 @@ __global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, co
     }
 }
 
+constexpr int kEigMaxN = 1024;      // m + 1 <= 1024: one thread per row of the reduced problem
+
 // ---------------------------------------------------------------------------
 // c_I, b_I, H_II, H_II c_I: one warp per selected row.  H_II goes to rows and
 // columns 1..m of R as float-float pairs (Rh, Rl; leading dimension ldr).
@@ -605,35 +606,42 @@ __global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, cons
                                                     double *bI, double *Hdiag, double *HIIc, float *Rh, float *Rl,
                                                     int ldr) {
     __shared__ ColLists Lw[8];
+    // the chosen determinants and their c (true units), staged once per block
+    __shared__ unsigned long long s_A[kEigMaxN], s_B[kEigMaxN];
+    __shared__ double s_c[kEigMaxN];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (ms->done) return;
     const int m = ms->m_sel;
     const double s = ms->scale.hi;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const McSel x = sel[i];
+        s_A[i] = x.A;
+        s_B[i] = x.B;
+        s_c[i] = P.table[x.slot].c * s;
+    }
+    __syncthreads();
     for (int r = blockIdx.x * 8 + warp; r < m; r += gridDim.x * 8) {
-        const McSel xr = sel[r];
+        const unsigned long long rA = s_A[r], rB = s_B[r];
         ColLists &L = Lw[warp];
         for (int t = lane; t < P.N; t += 32) {
-            int ra = __popcll(xr.A & low_mask(t)), rb = __popcll(xr.B & low_mask(t));
-            if ((xr.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
-            if ((xr.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+            int ra = __popcll(rA & low_mask(t)), rb = __popcll(rB & low_mask(t));
+            if ((rA >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+            if ((rB >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
         }
         __syncwarp();
         const double hd = diag_warp(P, L);
         double acc = 0.0;
         for (int c = lane; c < m; c += 32) {
-            const McSel xc = sel[c];
-            const double h = (c == r) ? hd : hij_pair(P, xr.A, xr.B, xc.A, xc.B);
+            const double h = (c == r) ? hd : hij_pair(P, rA, rB, s_A[c], s_B[c]);
             const ff hf = ff_from_double(h);
             Rh[(size_t)(r + 1) * ldr + (c + 1)] = hf.hi;
             Rl[(size_t)(r + 1) * ldr + (c + 1)] = hf.lo;
-            const double cc = P.table[xc.slot].c * s;
-            acc = fma(h, cc, acc);
+            acc = fma(h, s_c[c], acc);
         }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
         if (lane == 0) {
-            const Slot sl = P.table[xr.slot];
-            cI[r] = sl.c * s;
-            bI[r] = sl.bv * s;
+            cI[r] = s_c[r];
+            bI[r] = P.table[sel[r].slot].bv * s;
             Hdiag[r] = hd;
             HIIc[r] = acc;
         }
@@ -656,7 +664,6 @@ __global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, cons
 // vector arithmetic on the FP32 pipe.
 // ---------------------------------------------------------------------------
 constexpr int kEigSmemN = 160;      // A in shared memory (hi and lo) up to this size
-constexpr int kEigMaxN = 1024;      // m + 1 <= 1024: one thread per row
 constexpr int kEigMaxIt = 200;
 
 // Row `row` of A times a vector: this thread's share, the columns j = k,
@@ -1102,13 +1109,11 @@ __host__ __device__ __forceinline__ long long mc_gath_per_col(long long Lc, long
 }
 
 // Probe for {a, b}: the key and the value halves of the slot are read by two
-// independent 16-byte loads.  A new key is inserted with the candidate mark
-// already set (its inserter is the one that appends it).  Returns the slot,
-// or -1 (absent, not inserted) / -2 (error, status set).  c: the slot's
-// stored c; marked: the slot carried the mark when it was read.
+// independent 16-byte loads.  Returns the slot, or -1 (absent, not inserted) /
+// -2 (error, status set).  c: the slot's stored c.
 __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, unsigned long long a,
                                               unsigned long long b, unsigned long long h, bool insert,
-                                              bool &inserted, double &c, bool &marked) {
+                                              bool &inserted, double &c) {
     unsigned long long pos = h & P.mask;
     const bool both_nonzero = (P.na > 0) && (P.nb > 0);
     for (int probe = 0; probe < P.max_probe; ++probe) {
@@ -1122,22 +1127,19 @@ __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, u
         }
         if (k.x == a && (k.y & kKeyMaskB) == b) {
             c = v.x;
-            marked = (k.y & kMarkB) != 0ull;
             return (long long)pos;
         }
         if (k.x == 0ull && k.y == 0ull) {
             if (!insert) return -1;
             unsigned long long oa, ob;
-            cas128(&s->a, 0ull, 0ull, a, b | kMarkB, oa, ob);
+            cas128(&s->a, 0ull, 0ull, a, b, oa, ob);
             if (oa == 0ull && ob == 0ull) {
                 inserted = true;
                 c = 0.0;
-                marked = false;                          // marked by this thread
                 return (long long)pos;
             }
             if (oa == a && (ob & kKeyMaskB) == b) {      // lost to an insert of the same key
                 c = __ldcg(&s->c);
-                marked = true;
                 return (long long)pos;
             }
         }
@@ -1202,9 +1204,9 @@ __device__ __forceinline__ bool mc_apply(const Problem &P, McState *ms, IterStat
     long long s = -1;
     if (has) {
         const bool big = abs_bits(H) >= tib;
-        bool ins = false, marked = false;
+        bool ins = false;
         double cj = 0.0;
-        s = mc_probe(P, st, oa, ob, hk, big, ins, cj, marked);
+        s = mc_probe(P, st, oa, ob, hk, big, ins, cj);
         if (s == -2) {
             err = true;
         } else if (s < 0 || !(!is_zero(cj) || big)) {
@@ -1215,8 +1217,7 @@ __device__ __forceinline__ bool mc_apply(const Problem &P, McState *ms, IterStat
             ++c_app;
             c_ins += ins ? 1 : 0;
             gather = fma(H, cj, gather);
-            first = ins;
-            if (!ins && !marked) first = !(atomicOr(&sj->b, kMarkB) & kMarkB);
+            first = mark_set(P, s);                     // the marker appends it
         }
     }
     const unsigned int fm = __ballot_sync(0xffffffffu, first);
@@ -1380,11 +1381,7 @@ __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel
             }
             Slot *s = P.table + slot;
             s->bv = fma(hd, s->c, t);
-            const unsigned long long kb = s->b;
-            if (!(kb & kMarkB)) {
-                s->b = kb | kMarkB;
-                append = true;
-            }
+            append = mark_set(P, slot);
         }
         // the chosen coordinates join the candidates: one reservation per warp
         const unsigned int am = __ballot_sync(0xffffffffu, append);

@@ -191,6 +191,7 @@ struct Problem {
     unsigned long long mg_va, mg_vb, mg_nsb, mg_cva2, mg_cvb2;   // fdiv multipliers
     unsigned int *cnz;             // m > 1: filter of determinants whose c may be nonzero (NULL: none)
     unsigned long long cnz_mask;   // its bit count - 1
+    unsigned int *mark;            // m > 1: candidate marks, one bit per slot (NULL: bit 63 of the slot's B)
 };
 
 // ---------------------------------------------------------------------------
@@ -239,6 +240,18 @@ __device__ __forceinline__ bool cnz_maybe(const Problem &P, unsigned long long h
     if (!P.cnz) return true;
     const unsigned long long i = (h >> 32) & P.cnz_mask;
     return (__ldg(P.cnz + (i >> 5)) >> (unsigned)(i & 31)) & 1u;
+}
+
+// Candidate mark of slot s in the m > 1 bitmap: set (returns true if this call set it), test, clear.
+__device__ __forceinline__ bool mark_set(const Problem &P, long long s) {
+    const unsigned bit = 1u << (unsigned)(s & 31);
+    return !(atomicOr(P.mark + (s >> 5), bit) & bit);
+}
+__device__ __forceinline__ bool mark_test(const Problem &P, long long s) {
+    return (P.mark[s >> 5] >> (unsigned)(s & 31)) & 1u;
+}
+__device__ __forceinline__ void mark_clear(const Problem &P, long long s) {
+    atomicAnd(P.mark + (s >> 5), ~(1u << (unsigned)(s & 31)));
 }
 
 // floor(n / d) for n < 2^24, d < 2^16 with M = floor(2^40 / d) + 1 (the

@@ -985,7 +985,7 @@ __global__ void k_ckpt_export(Problem P, unsigned long long *keys, double *c, do
         keys[2 * pos + 1] = sl.b & kKeyMaskB;
         c[pos] = sl.c;
         b[pos] = sl.bv;
-        flags[pos] = (sl.b & kMarkB) ? 1 : 0;
+        flags[pos] = (P.mark ? mark_test(P, i) : (sl.b & kMarkB) != 0ull) ? 1 : 0;
     }
 }
 
@@ -1026,7 +1026,8 @@ __global__ void k_ckpt_import(Problem P, IterState *st, const unsigned long long
         P.table[s].bv = b[i];
         if (c[i] != 0.0) cnz_set(P, keys[2 * i], keys[2 * i + 1]);
         if (flags && (flags[i] & 1) && cand) {
-            P.table[s].b = keys[2 * i + 1] | kMarkB;
+            if (P.mark) mark_set(P, s);
+            else P.table[s].b = keys[2 * i + 1] | kMarkB;
             const int pos = atomicAdd(n_cand, 1);
             if (pos < cap_cand) cand[pos] = s;
             else set_status(st, kErrInternal);
