@@ -416,6 +416,64 @@ __global__ void __launch_bounds__(256) k_mc_hist(McState *ms, const unsigned lon
     if (sel_merge(sh, hist, hist + kSelBins)) sel_scan(ms, hist, hist + kSelBins, level, need);
 }
 
+// Levels 2.. on one CTA of 1024 threads (one launch instead of one per level):
+// it returns at once when the selection is resolved, which is the common case;
+// otherwise it counts the keys on the prefix in a shared-memory histogram and
+// scans it, level by level, exactly as k_mc_hist and sel_scan do.
+__global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsigned long long *gkey) {
+    __shared__ unsigned int sh[kSelBins];
+    __shared__ unsigned int s_warp[32];
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int level = 2; level < kSelLevels; ++level) {
+        if (tid == 0) s_stop = (ms->done || ms->sel_resolved) ? 1 : 0;
+        for (int d = tid; d < kSelBins; d += blockDim.x) sh[d] = 0u;
+        __syncthreads();
+        if (s_stop) return;
+        const int n = ms->n_cand;
+        const unsigned long long prefix = ms->sel_prefix;
+        const int need = ms->sel_need;
+        for (int base = 0; base < n; base += blockDim.x) {
+            const int t = base + tid;
+            const unsigned long long k = t < n ? gkey[t] : 0ull;
+            const bool ok = t < n && sel_top(k, level) == prefix;
+            sel_bin_add(sh, ok, sel_digit(k, level));
+        }
+        __syncthreads();
+        // the digit of rank `need` from the top (thread t owns bins top - t per .. top - t per - per + 1)
+        const int per = kSelBins / blockDim.x;
+        const int top = kSelBins - 1 - tid * per;
+        unsigned int loc = 0;
+        for (int q = 0; q < per; ++q) loc += sh[top - q];
+        unsigned int inc = loc;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned int v = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += v;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        unsigned int before = inc - loc;
+        for (int w2 = 0; w2 < warp; ++w2) before += s_warp[w2];
+        if (before < (unsigned int)need && (unsigned int)need <= before + loc) {
+            unsigned int acc = before;
+            for (int q = 0; q < per; ++q) {
+                const unsigned int c = sh[top - q];
+                if (acc + c >= (unsigned int)need) {
+                    ms->sel_prefix = (ms->sel_prefix << sel_bits(level)) | (unsigned long long)(top - q);
+                    ms->sel_need = need - (int)acc;
+                    ms->sel_level = level + 1;
+                    ms->sel_nbin = (int)c;
+                    ms->sel_resolved = (c <= (unsigned int)kInBin || level == kSelLevels - 1) ? 1 : 0;
+                    break;
+                }
+                acc += c;
+            }
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+}
+
 __global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, const unsigned long long *gkey,
                              McSel *sel, McSel *inbin) {
     if (ms->done) return;
@@ -1557,7 +1615,8 @@ cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cud
 
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s) {
     k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.st, b.cand, b.gkey, b.hist, b.m);
-    for (int level = 1; level < kSelLevels; ++level) k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, level);
+    k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, 1);
+    k_mc_hist_tail<<<1, 1024, 0, s>>>(b.ms, b.gkey);
     k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
     k_mc_ties<<<1, 1024, 0, s>>>(P, b.ms, b.cand, b.gkey, b.ties, b.inbin);
     k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
