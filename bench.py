@@ -205,23 +205,42 @@ def run_reference_arm(args) -> None:
     print(json.dumps(line))
 
 
-def timed_block_run(api, w, m, tau, log2_capacity, warm_iters, iters, **kw) -> dict:
-    """mCDFCI (Algorithm 2) throughput: elements/s over `iters` block iterations after `warm_iters`."""
+def timed_block_run(api, w, m, tau, log2_capacity, warm_iters, iters, kernel_iters=0, **kw) -> dict:
+    """mCDFCI (Algorithm 2) throughput: elements/s over `iters` block iterations after `warm_iters`.
+    With kernel_iters > 0, then that many more iterations launch by launch with CUDA events around each
+    kernel (cdfci_time_kernels): the per-kernel split and the scatter's achieved bandwidth."""
     s = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, num_coordinates=m, z_threshold=tau,
                    log2_capacity=log2_capacity, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]), **kw)
+    kt = None
     try:
         s.step(warm_iters)
         st0 = s.stats()
         t0 = time.perf_counter()
         st = s.step(iters)
         dt = time.perf_counter() - t0
+        if kernel_iters > 0:
+            k0 = s.stats()
+            t = s.time_kernels(kernel_iters)
+            k1 = s.stats()
+            kt = (t, (k1["elements"] - k0["elements"]) / kernel_iters)
     finally:
         s.close()
     el = st["elements"] - st0["elements"]
-    return {"value": el / dt, "unit": "elements/s", "us_per_iteration": dt / iters * 1e6,
-            "elements_per_iteration": el / iters, "iterations": iters, "after_warmup_iterations": warm_iters,
-            "reduced_eig_iterations_per_iteration": (st["reduced_iterations"] - st0["reduced_iterations"]) / iters,
-            "energy": st["energy"], "load": st["load"]}
+    out = {"value": el / dt, "unit": "elements/s", "us_per_iteration": dt / iters * 1e6,
+           "elements_per_iteration": el / iters, "iterations": iters, "after_warmup_iterations": warm_iters,
+           "reduced_eig_iterations_per_iteration": (st["reduced_iterations"] - st0["reduced_iterations"]) / iters,
+           "energy": st["energy"], "load": st["load"]}
+    if kt is not None:
+        t, el_k = kt
+        us = {k: v * 1e3 / kernel_iters for k, v in t.items()}
+        peak, kind = measured_peaks()
+        achieved = el_k * ALGO_BYTES_PER_ELEMENT / (us["scatter"] * 1e-6) / 1e9
+        out["us_per_kernel"] = {k: round(v, 2) for k, v in us.items()}
+        out["scatter_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": kind,
+                                   "unit": "GB/s", "frac": achieved / peak,
+                                   "algorithmic_bytes_per_element": ALGO_BYTES_PER_ELEMENT,
+                                   "elements_per_iteration": el_k, "iterations_timed": kernel_iters}
+    return out
 
 
 def timed_xcd_run(api, w, k1, tau, log2_capacity, warm_iters, iters) -> dict:
@@ -394,7 +413,7 @@ def main():
         __graft_entry__.build()
         from paper_2605_04483_gb300 import api, inputs
         r = timed_block_run(api, inputs.config2(), 128, WORKLOAD["tau"], args.log2_capacity, args.warmup * 10,
-                            args.iters_per_step)
+                            args.iters_per_step, kernel_iters=min(200, args.iters_per_step))
         print(json.dumps({"mcdfci_m128": r}))
         return
     if args.only == "xcdfci":
@@ -535,13 +554,13 @@ def main():
         line["time_to_E_batched_vs_plain"] = time_to_e_batched_vs_plain(api, inputs)
         # ---- batched coordinate updates (mCDFCI, Algorithm 2) on the same workload ------------
         line["mcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=128, 2^27-slot table",
-                              **timed_block_run(api, w, 128, WORKLOAD["tau"], 27, 200, 200))
+                              **timed_block_run(api, w, 128, WORKLOAD["tau"], 27, 200, 200, kernel_iters=100))
         # ---- excited states (xCDFCI, Algorithm 3), K + 1 = 4, same workload -------------------
         line["xcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, K+1=4 states, 2^26-slot table",
                               **timed_xcd_run(api, w, 4, WORKLOAD["tau"], 26, 500, 2000))
         # ---- 2D Hubbard 4x4 periodic, U=8, 8+8 (FCI dim 165,636,900), m=256, 2^28 slots ------------
         line["hubbard_4x4"] = dict(workload="hubbard_4x4_pbc_U8 (dim 1.66e8, column <= 65), m=256, 2^28-slot table",
-                                   **timed_block_run(api, inputs.config3(8.0), 256, 0.0, 28, 100, 200))
+                                   **timed_block_run(api, inputs.config3(8.0), 256, 0.0, 28, 100, 200, kernel_iters=50))
         # ---- uneven batch of 96 problems in one launch --------------------------------------
         sweep = {gb: batch_c4(api, inputs, 200, gb) for gb in (1, 2, 4, 8, 16)}
         best = max(sweep, key=lambda gb: sweep[gb]["value"])

@@ -177,6 +177,21 @@ int cdfci_export(cdfci_handle h, uint64_t *keys, double *c, double *b, int64_t c
 int cdfci_energies(cdfci_handle h, double *E, int32_t cap, int32_t *n_out);
 
 /*
+ * Per-kernel device time of the mCDFCI iteration (Alg. 2; handles with
+ * num_coordinates > 1): runs n_iter iterations of the solve (they advance it
+ * like cdfci_step) launch by launch instead of as a graph, with a CUDA event
+ * recorded before every launch on the handle's stream, and writes into ms the
+ * milliseconds spent from each launch to the next, summed over the
+ * iterations, in launch order: 0 choice keys + level-0 histogram, 1 level-1
+ * histogram, 2 levels 2.., 3 collect, 4 exact ties, 5 sort of the chosen set,
+ * 6 c_I / b_I / H_II, 7 reduced problem, 8 scatter of the m columns,
+ * 9 b_I recalculated.  *n_kernels = 10 (host pointer); ms holds up to cap
+ * values (host pointer).  CDFCI_ERR_CAPACITY if cap < 10,
+ * CDFCI_ERR_UNIMPLEMENTED for other handles.
+ */
+int cdfci_time_kernels(cdfci_handle h, int64_t n_iter, double *ms, int32_t cap, int32_t *n_kernels);
+
+/*
  * All stored determinants with their rows C_{D,:} and B_{D,:} = (HC)_{D,:}
  * (num_states values each, row-major), in table order; for other handles the
  * same as cdfci_export (one value each).  CDFCI_ERR_CAPACITY if cap is too small

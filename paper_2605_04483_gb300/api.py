@@ -114,6 +114,7 @@ def lib():
         L.cdfci_column_noalloc.restype = ctypes.c_int
         L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
         L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.cdfci_time_kernels.argtypes = [vp, i64, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.cdfci_optorb.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                    ctypes.POINTER(cdfci_optorb_params), dp]
         L.cdfci_export_states.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
@@ -222,6 +223,18 @@ def cdfci_optorb(h, g, M: int, N: int, n_alpha: int, n_beta: int, U0=None, outer
     g = np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g
     _check(lib().cdfci_optorb(_ptr(h), _ptr(g), M, N, n_alpha, n_beta, _ptr(U), ctypes.byref(p), _ptr(E)))
     return U, E
+
+
+MC_KERNELS = ["gkeys", "hist_level1", "hist_tail", "collect", "ties", "sortsel", "prepare", "eigen", "scatter",
+              "finalize"]
+
+
+def cdfci_time_kernels(handle: int, n_iter: int) -> dict:
+    """Milliseconds per launch of the mCDFCI iteration, summed over n_iter iterations (which advance the solve)."""
+    ms = np.zeros(len(MC_KERNELS), dtype=np.float64)
+    n = ctypes.c_int32(0)
+    _check(lib().cdfci_time_kernels(handle, int(n_iter), _ptr(ms), len(MC_KERNELS), ctypes.byref(n)))
+    return dict(zip(MC_KERNELS, ms.tolist()))
 
 
 def cdfci_energies(handle: int, cap: int = 8) -> np.ndarray:
@@ -392,6 +405,9 @@ class Solver:
 
     def energies(self) -> np.ndarray:
         return cdfci_energies(self.handle)
+
+    def time_kernels(self, n_iter: int) -> dict:
+        return cdfci_time_kernels(self.handle, n_iter)
 
     def export_states(self):
         return cdfci_export_states(self.handle, max(1, int(self.p.num_states)))

@@ -876,6 +876,35 @@ CDFCI_API int cdfci_energies(cdfci_handle c, double *E, int32_t cap, int32_t *n_
     return CDFCI_OK;
 }
 
+CDFCI_API int cdfci_time_kernels(cdfci_handle c, int64_t n_iter, double *ms, int32_t cap, int32_t *n_kernels) {
+    if (!c || !ms || !n_kernels) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
+    if (!c->block || c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "per-kernel times are for mCDFCI handles");
+    *n_kernels = kMcKernels;
+    if (cap < kMcKernels) return fail(CDFCI_ERR_CAPACITY, "%d kernels, cap is %d", kMcKernels, (int)cap);
+    for (int k = 0; k < kMcKernels; ++k) ms[k] = 0.0;
+    cudaEvent_t ev[kMcKernels + 1];
+    int made = 0;
+    for (; made <= kMcKernels; ++made)
+        if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+    int rc = made <= kMcKernels ? fail(CDFCI_ERR_CUDA, "cudaEventCreate failed") : CDFCI_OK;
+    for (int64_t i = 0; i < n_iter && rc == CDFCI_OK; ++i) {
+        if (launch_mc_iteration(c->P, c->mb, c->stream, ev) != cudaSuccess ||
+            cudaEventSynchronize(ev[kMcKernels]) != cudaSuccess) {
+            rc = fail(CDFCI_ERR_CUDA, "timed iteration failed");
+            break;
+        }
+        for (int k = 0; k < kMcKernels; ++k) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) != cudaSuccess) { rc = fail(CDFCI_ERR_CUDA, "event timing failed"); break; }
+            ms[k] += t;
+        }
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    if (rc != CDFCI_OK) return rc;
+    return fill_stats(c, nullptr);
+}
+
 CDFCI_API int cdfci_export_states(cdfci_handle c, uint64_t *keys, double *C, double *B, int64_t cap,
                                   int64_t *n_out) {
     if (!c || !n_out) return fail(CDFCI_ERR_ARG, "NULL argument");

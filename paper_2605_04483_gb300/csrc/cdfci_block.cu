@@ -1613,19 +1613,38 @@ cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s) {
+cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s, cudaEvent_t *ev) {
+    // ev (optional): kMcKernels + 1 events, recorded before every launch and after the last
+    int k = 0;
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(ev[k], s);
+        ++k;
+    };
+    mark();
     k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.st, b.cand, b.gkey, b.hist, b.m);
+    mark();
     k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, 1);
+    mark();
     k_mc_hist_tail<<<1, 1024, 0, s>>>(b.ms, b.gkey);
+    mark();
     k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
+    mark();
     k_mc_ties<<<1, 1024, 0, s>>>(P, b.ms, b.cand, b.gkey, b.ties, b.inbin);
+    mark();
     k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
+    mark();
     k_mc_prepare<<<(b.m + 7) / 8, 256, 0, s>>>(P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr);
+    mark();
     k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Rh,
                                                                     b.Rl, b.ldr, eig_tpr(b.m + 1),
                                                                     b.m + 1 <= kEigSmemN ? 1 : 0,
                                                                     b.w, b.thr, b.eta);
-    return launch_mc_scatter_finalize(P, b, s);
+    mark();
+    k_mc_scatter<<<b.scatter_grid, 256, mc_scatter_smem(P), s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp);
+    mark();
+    k_mc_finalize<<<1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.scatter_grid);
+    mark();
+    return cudaGetLastError();
 }
 
 }  // namespace cdfci

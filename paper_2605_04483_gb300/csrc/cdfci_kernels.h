@@ -91,7 +91,8 @@ cudaError_t mc_configure();
 cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
                             double eta, int first, cudaStream_t s);
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
-cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s);
+constexpr int kMcKernels = 10;      // launches of one mCDFCI iteration
+cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // the m = 1 loop over more CTAs than a cluster holds (cooperative launch)
 cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart, CdPartial *galt,

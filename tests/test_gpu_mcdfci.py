@@ -125,6 +125,33 @@ def test_block_compression_and_counters():
         g.close()
 
 
+def test_block_kernel_times():
+    """cdfci_time_kernels runs real iterations launch by launch: the same
+    trajectory as graph steps, ten non-negative per-launch times, and an
+    UNIMPLEMENTED error for an m = 1 handle."""
+    from paper_2605_04483_gb300 import api
+    w = inputs.ab_initio(10, 4, 4, seed=8)
+    a, b = solver(w, 8), solver(w, 8)
+    try:
+        a.step(40)
+        t = a.time_kernels(20)
+        b.step(60)
+        assert list(t) == api.MC_KERNELS and all(v >= 0.0 for v in t.values()) and t["scatter"] > 0.0
+        sa, sb = a.stats(), b.stats()
+        # the same iterations (b's atomic sums may round in another order)
+        assert sa["iterations"] == sb["iterations"]
+        assert abs(sa["energy"] - sb["energy"]) <= 1e-10 * abs(sb["energy"])
+    finally:
+        a.close()
+        b.close()
+    one = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta)
+    try:
+        with pytest.raises(api.CdfciError):
+            one.time_kernels(1)
+    finally:
+        one.close()
+
+
 def open_reference(name):
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "reference_energies.txt")
