@@ -89,6 +89,15 @@ typedef struct {
                                   decreases; the current tau is in cdfci_stats.z_threshold */
     double   max_memory;       /* > 0: GiB for the wavefunction's table (and xCDFCI rows): log2_capacity
                                   becomes the largest that fits; 0 = use log2_capacity */
+    int32_t  integral_symmetry; /* 8 (or 0, the default): real orbitals, g has the 8-fold symmetry and every
+                                  image is canonicalised; 4: g is real with (pq|rs) = (rs|pq) = (qp|sr)
+                                  only, as for the plane-wave orbitals of the k-space Hubbard model
+                                  (HamiltonianHubbardK of Sec. "The Hamiltonian Class": (pq|rs) =
+                                  (U/L) delta(k_q - k_p + k_s - k_r)); g is then validated against those
+                                  two symmetries and used as given.  The kernels read doubles as
+                                  (ia|jb) with i, j occupied in the column's determinant and a, b in the
+                                  row's, and diagonals as J_pq = (pp|qq), K_pq = (pq|qp), so both forms
+                                  give Eq. (entry).  cdfci_gradient's dE/dg assumes the 8-fold form */
 } cdfci_params;
 
 /* Progress report (the console row of Sec. "Expected Console Output"). */
@@ -190,6 +199,25 @@ int cdfci_energies(cdfci_handle h, double *E, int32_t cap, int32_t *n_out);
  * CDFCI_ERR_UNIMPLEMENTED for other handles.
  */
 int cdfci_time_kernels(cdfci_handle h, int64_t n_iter, double *ms, int32_t cap, int32_t *n_kernels);
+
+/*
+ * Degenerate-subspace start (the k-space Hubbard example of the paper's
+ * numerical section: when the lowest one-body configurations are degenerate,
+ * H restricted to all of them is diagonalised and its lowest eigenvector is
+ * the start).  The one-body energies are the diagonal h_pp; per spin the
+ * lowest shells are filled, and the last, partly filled shell (levels within
+ * tol * max(1, |level|), tol <= 0: 1e-10) contributes every choice of its
+ * remaining electrons.  The set S (alpha choices x beta choices, ordered by the
+ * 128-bit key (B << 64) | A) must hold at most cap determinants (cap <= 0:
+ * 1024); H_SS comes from this handle's columns, its lowest eigenpair from
+ * cyclic Jacobi rotations on the host, the vector normalised with its largest
+ * component positive (ties: the first in S).  The vector then replaces the
+ * state as cdfci_set_initial would (zero components skipped).  *n_det = |S|,
+ * *E_sub = the lowest eigenvalue (host pointers; E_sub may be NULL).
+ * CDFCI_ERR_CAPACITY if |S| > cap (*n_det set), CDFCI_ERR_UNIMPLEMENTED for
+ * xCDFCI handles.
+ */
+int cdfci_set_initial_degenerate(cdfci_handle h, double tol, int64_t cap, int64_t *n_det, double *E_sub);
 
 /*
  * All stored determinants with their rows C_{D,:} and B_{D,:} = (HC)_{D,:}

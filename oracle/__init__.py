@@ -14,6 +14,8 @@ scalars), loaded with ctypes:
   * ``ground_energy``   - smallest eigenvalue of H (LAPACK ``eigh`` on the dense
     matrix, or ARPACK ``eigsh`` on the sparse one: library eigensolvers used
     as one step).
+  * ``degenerate_start`` - the lowest eigenvector of H on the degenerate
+    lowest one-body configurations (the k-space Hubbard start).
   * ``CDFCI``           - Algorithm 1 (m = 1) and Algorithm 2 (m > 1), serial.
   * ``line_search``     - the appendix's Cardano + Newton step.
   * ``rdm``             - spin-summed 1- and 2-RDMs by literal operator
@@ -215,6 +217,51 @@ def ground_energy(N, na, nb, h, g, dense_limit: int = 2500) -> float:
     w = eigsh(Hs, k=1, which="SA", tol=1e-14, ncv=min(dim - 1, 64), maxiter=100000,
               v0=np.ones(dim) / np.sqrt(dim))[0]
     return float(w[0])
+
+
+def degenerate_start(N, na, nb, h, g, tol: float = 1e-10, cap: int = 1024):
+    """The degenerate-subspace start of the paper's k-space Hubbard example (numerical section, 4x4
+    lattice: the configurations of lowest one-body energy, the Hamiltonian restricted to them, its
+    lowest eigenvector).  Per spin the orbitals below the ne-th lowest level h_pp are filled and
+    every choice of the remaining electrons in that level's shell (levels within tol * max(1, |level|))
+    is listed.  S = alpha x beta choices ordered by the 128-bit key (B << 64) | A; H_SS from
+    column_sc; the lowest eigenpair from numpy's eigh; the vector normalised, its largest component
+    positive (ties: the first in S).  Returns (keys (|S|, 2), c, lowest eigenvalue)."""
+    import itertools
+    eps = np.diag(np.asarray(h, dtype=np.float64))
+
+    def strings(ne):
+        if ne == 0:
+            return [0]
+        top = sorted(eps)[ne - 1]
+        band = tol * max(1.0, abs(top))
+        below = [p for p in range(N) if eps[p] < top - band]
+        shell = [p for p in range(N) if top - band <= eps[p] <= top + band]
+        r = ne - len(below)
+        base = sum(1 << p for p in below)
+        return [base | sum(1 << p for p in pick) for pick in itertools.combinations(shell, r)]
+
+    sa, sb = strings(na), strings(nb)
+    if len(sa) * len(sb) > cap:
+        raise ValueError(f"degenerate set of {len(sa) * len(sb)} determinants exceeds cap = {cap}")
+    S = sorted((b, a) for a in sa for b in sb)
+    index = {k: i for i, k in enumerate(S)}
+    n = len(S)
+    H = np.zeros((n, n))
+    for i, (b, a) in enumerate(S):
+        keys, vals = column_sc(N, h, g, (a, b))
+        for (ka, kb), v in zip(keys, vals):
+            j = index.get((int(kb), int(ka)))
+            if j is not None:
+                H[j, i] = v
+    H = 0.5 * (H + H.T)
+    w, V = np.linalg.eigh(H)
+    v = V[:, 0] / np.linalg.norm(V[:, 0])
+    big = int(np.argmax(np.abs(v)))
+    if v[big] < 0:
+        v = -v
+    keys = np.array([[a, b] for (b, a) in S], dtype=np.uint64)
+    return keys, v, float(w[0])
 
 
 def line_search(v1: float, v2: float, v3: float) -> float:

@@ -30,7 +30,8 @@ class cdfci_params(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("graph_chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("num_states", ctypes.c_int32),
-                ("z_threshold_search", ctypes.c_int32), ("max_memory", ctypes.c_double)]
+                ("z_threshold_search", ctypes.c_int32), ("max_memory", ctypes.c_double),
+                ("integral_symmetry", ctypes.c_int32)]
 
 
 class cdfci_optorb_params(ctypes.Structure):
@@ -115,6 +116,8 @@ def lib():
         L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
         L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.cdfci_time_kernels.argtypes = [vp, i64, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.cdfci_set_initial_degenerate.argtypes = [vp, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int64),
+                                                   ctypes.POINTER(ctypes.c_double)]
         L.cdfci_optorb.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                    ctypes.POINTER(cdfci_optorb_params), dp]
         L.cdfci_export_states.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
@@ -223,6 +226,14 @@ def cdfci_optorb(h, g, M: int, N: int, n_alpha: int, n_beta: int, U0=None, outer
     g = np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g
     _check(lib().cdfci_optorb(_ptr(h), _ptr(g), M, N, n_alpha, n_beta, _ptr(U), ctypes.byref(p), _ptr(E)))
     return U, E
+
+
+def cdfci_set_initial_degenerate(handle: int, tol: float = 0.0, cap: int = 0) -> Tuple[int, float]:
+    """Degenerate-subspace start; returns (number of degenerate determinants, lowest eigenvalue on them)."""
+    n = ctypes.c_int64(0)
+    E = ctypes.c_double(0.0)
+    _check(lib().cdfci_set_initial_degenerate(handle, float(tol), int(cap), ctypes.byref(n), ctypes.byref(E)))
+    return int(n.value), float(E.value)
 
 
 MC_KERNELS = ["gkeys", "hist_level1", "hist_tail", "collect", "ties", "sortsel", "prepare", "eigen", "scatter",
@@ -408,6 +419,9 @@ class Solver:
 
     def time_kernels(self, n_iter: int) -> dict:
         return cdfci_time_kernels(self.handle, n_iter)
+
+    def set_initial_degenerate(self, tol: float = 0.0, cap: int = 0) -> Tuple[int, float]:
+        return cdfci_set_initial_degenerate(self.handle, tol, cap)
 
     def export_states(self):
         return cdfci_export_states(self.handle, max(1, int(self.p.num_states)))

@@ -9,6 +9,7 @@
 #include <chrono>
 #include <new>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/cdfci.h"
@@ -216,6 +217,7 @@ int setup_block(cdfci_ctx *c, int m) {
     b.m = m;
     const long long cap_cand = (long long)m * nh_eff + m + 64;
     b.cap_cand = cap_cand;
+    c->P.cap_cand = cap_cand;
     b.cand_grid = 152 * 4;
     CK(mc_configure());
     b.scatter_grid = 2 * mc_scatter_grid(P);         // twice the resident blocks: late blocks even out the SMs
@@ -231,9 +233,10 @@ int setup_block(cdfci_ctx *c, int m) {
         mb_alloc(c, &b.w, (size_t)m) || mb_alloc(c, &b.thr, (size_t)m) || mb_alloc(c, &b.eta, (size_t)m) ||
         mb_alloc(c, &b.gathp, (size_t)mc_gath_entries(m, b.scatter_grid)))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
-    // c != 0 filter: one bit per table slot, between 2^16 and 2^27 bits (16 MB, L2-resident)
+    // c != 0 filter: one bit per table slot, between 2^16 and 2^25 bits (4 MB: it stays in L2 while the
+    // scatter's random slot traffic streams through)
     const unsigned long long nbits =
-        (unsigned long long)std::min<long long>(std::max<long long>(P.capacity, 1ll << 16), 1ll << 27);
+        (unsigned long long)std::min<long long>(std::max<long long>(P.capacity, 1ll << 16), 1ll << 25);
     if (mb_alloc(c, &c->P.cnz, (size_t)(nbits / 32)))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
     c->P.cnz_mask = nbits - 1;
@@ -335,6 +338,40 @@ int build_block_graph(cdfci_ctx *c) {
     return CDFCI_OK;
 }
 
+// Candidate buffers (list, choice keys, tie scratch) of at least `need` entries: a start of more
+// than m columns can touch more slots than one iteration.  The iteration graph holds the old
+// buffers and Problem, so it is captured again.
+int grow_candidates(cdfci_ctx *c, long long need) {
+    McBuffers &b = c->mb;
+    if (need <= b.cap_cand) return CDFCI_OK;
+    long long *cand = nullptr;
+    unsigned long long *gkey = nullptr;
+    McSel *ties = nullptr;
+    if (cudaMalloc(&cand, (size_t)need * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&gkey, (size_t)need * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ties, (size_t)need * sizeof(McSel)) != cudaSuccess) {
+        cudaFree(cand); cudaFree(gkey); cudaFree(ties);
+        return fail(CDFCI_ERR_NOMEM, "candidate list of %lld entries does not fit", need);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->mb_nalloc; ++i) {
+        void *&q = c->mb_alloc[i];
+        if (q == (void *)b.cand) { cudaFree(q); q = cand; }
+        else if (q == (void *)b.gkey) { cudaFree(q); q = gkey; }
+        else if (q == (void *)b.ties) { cudaFree(q); q = ties; }
+    }
+    b.cand = cand;
+    b.gkey = gkey;
+    b.ties = ties;
+    b.cap_cand = need;
+    c->P.cap_cand = need;
+    if (c->mgraph) {
+        cudaGraphExecDestroy(c->mgraph);
+        c->mgraph = nullptr;
+    }
+    return build_block_graph(c);
+}
+
 }  // namespace
 
 namespace {
@@ -417,6 +454,7 @@ CDFCI_API void cdfci_default_params(cdfci_params *p) {
     p->dx_threshold = 0.0;
     p->deterministic = 1;
     p->num_states = 1;
+    p->integral_symmetry = 8;
 }
 
 CDFCI_API const char *cdfci_last_error(void) { return g_last_error.c_str(); }
@@ -434,6 +472,9 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
     if (prm.num_coordinates < 1 || prm.num_coordinates > mc_max_m())
         return fail(CDFCI_ERR_ARG, "num_coordinates = %d outside [1, %d]", prm.num_coordinates, mc_max_m());
     if (prm.num_states == 0) prm.num_states = 1;
+    if (prm.integral_symmetry == 0) prm.integral_symmetry = 8;
+    if (prm.integral_symmetry != 8 && prm.integral_symmetry != 4)
+        return fail(CDFCI_ERR_ARG, "integral_symmetry = %d (8 or 4)", prm.integral_symmetry);
     if (prm.num_states < 1 || prm.num_states > kXMax)
         return fail(CDFCI_ERR_ARG, "num_states = %d outside [1, %d]", prm.num_states, kXMax);
     if (prm.num_states > 1 && prm.num_coordinates != 1)
@@ -514,7 +555,8 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         cudaMemcpyAsync(c->d_g, g, n4 * sizeof(double), kind_to_device(g), s) != cudaSuccess ||
         cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "copy of the integrals failed"));
-    if (launch_setup(c->d_h, c->d_g, N, c->d_J, c->d_K, c->d_W3, c->d_V3, c->d_flags, c->d_flags + 1, s) !=
+    if (launch_setup(c->d_h, c->d_g, N, c->d_J, c->d_K, c->d_W3, c->d_V3, c->d_flags, c->d_flags + 1,
+                     prm.integral_symmetry == 4 ? 1 : 0, s) !=
         cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "set-up kernels failed to launch"));
     int flags[4];
@@ -522,7 +564,8 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
         cudaStreamSynchronize(s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "set-up failed"));
     if (flags[0] == CDFCI_ERR_NONFINITE) return bail(fail(CDFCI_ERR_NONFINITE, "h or g holds NaN/Inf"));
-    if (flags[0] != 0) return bail(fail(CDFCI_ERR_ARG, "h is not symmetric or g is not 8-fold symmetric"));
+    if (flags[0] != 0)
+        return bail(fail(CDFCI_ERR_ARG, "h is not symmetric or g lacks the %d-fold symmetry", prm.integral_symmetry));
     P.doubles_vanish = flags[1] ? 0 : 1;
 
     // pair tables: occupied alpha, occupied beta, virtual alpha, virtual beta
@@ -876,6 +919,169 @@ CDFCI_API int cdfci_energies(cdfci_handle c, double *E, int32_t cap, int32_t *n_
     return CDFCI_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// The strings of ne electrons with the lowest one-body energy: the shells below
+// the ne-th level filled, every choice of the rest in the last shell.
+std::vector<uint64_t> lowest_strings(const std::vector<double> &eps, int ne, double tol, int64_t cap, bool &over) {
+    const int N = (int)eps.size();
+    std::vector<uint64_t> out;
+    over = false;
+    if (ne == 0) { out.push_back(0); return out; }
+    std::vector<int> order(N);
+    for (int p = 0; p < N; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return eps[x] < eps[y]; });
+    const double top = eps[order[ne - 1]], band = tol * std::max(1.0, std::fabs(top));
+    uint64_t below = 0;
+    std::vector<int> shell;
+    for (int p = 0; p < N; ++p) {
+        if (eps[p] < top - band) below |= 1ull << p;
+        else if (eps[p] <= top + band) shell.push_back(p);
+    }
+    const int r = ne - __builtin_popcountll(below);
+    // C(|shell|, r) choices, bounded before they are listed
+    double count = 1.0;
+    for (int k = 0; k < r; ++k) count = count * (double)(shell.size() - k) / (double)(k + 1);
+    if (count > (double)cap) { over = true; return out; }
+    std::vector<int> pick(r);
+    for (int k = 0; k < r; ++k) pick[k] = k;
+    while (true) {
+        uint64_t m = below;
+        for (int k = 0; k < r; ++k) m |= 1ull << shell[pick[k]];
+        out.push_back(m);
+        int k = r - 1;
+        while (k >= 0 && pick[k] == (int)shell.size() - r + k) --k;
+        if (k < 0) break;
+        ++pick[k];
+        for (int j = k + 1; j < r; ++j) pick[j] = pick[j - 1] + 1;
+    }
+    return out;
+}
+
+// Lowest eigenpair of the symmetric n x n matrix A (row-major, destroyed) by
+// cyclic Jacobi rotations: each rotation zeroes A_pq with tan = t, t the
+// smaller root of t^2 + 2 theta t - 1 = 0, theta = (A_qq - A_pp) / (2 A_pq).
+void jacobi_lowest(int n, std::vector<double> &A, double &lam, std::vector<double> &v) {
+    std::vector<double> V((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    double norm2 = 0.0;
+    for (double x : A) norm2 += x * x;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off <= 1e-32 * norm2 || off == 0.0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {               // columns p, q
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = cs * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {               // rows p, q
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = cs * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = cs * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    int lo = 0;
+    for (int i = 1; i < n; ++i)
+        if (A[(size_t)i * n + i] < A[(size_t)lo * n + lo]) lo = i;
+    lam = A[(size_t)lo * n + lo];
+    v.assign(n, 0.0);
+    double nrm = 0.0;
+    for (int k = 0; k < n; ++k) { v[k] = V[(size_t)k * n + lo]; nrm += v[k] * v[k]; }
+    nrm = std::sqrt(nrm);
+    int big = 0;
+    for (int k = 0; k < n; ++k) {
+        v[k] /= nrm;
+        if (std::fabs(v[k]) > std::fabs(v[big])) big = k;
+    }
+    if (v[big] < 0.0)
+        for (double &x : v) x = -x;
+}
+}  // namespace
+
+extern "C" {
+
+CDFCI_API int cdfci_set_initial_degenerate(cdfci_handle c, double tol, int64_t cap, int64_t *n_det, double *E_sub) {
+    if (!c || !n_det) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "start vectors are for one state (num_states = 1)");
+    if (!(tol > 0.0)) tol = 1e-10;
+    if (cap <= 0) cap = 1024;
+    const int N = c->N;
+    std::vector<double> hd((size_t)N * N);
+    CK(cudaMemcpy(hd.data(), c->d_h, hd.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> eps(N);
+    for (int p = 0; p < N; ++p) eps[p] = hd[(size_t)p * N + p];
+    bool overA = false, overB = false;
+    const std::vector<uint64_t> sa = lowest_strings(eps, c->na, tol, cap, overA), sb = lowest_strings(eps, c->nb, tol, cap, overB);
+    const double total = (double)sa.size() * (double)sb.size();
+    if (overA || overB || total > (double)cap) {
+        *n_det = (overA || overB) ? cap + 1 : (int64_t)total;
+        return fail(CDFCI_ERR_CAPACITY, "the degenerate set exceeds cap = %lld", (long long)cap);
+    }
+    std::vector<std::pair<uint64_t, uint64_t>> S;                // (B, A): the 128-bit key order
+    for (uint64_t b : sb)
+        for (uint64_t a : sa) S.push_back({b, a});
+    std::sort(S.begin(), S.end());
+    const int n = (int)S.size();
+    *n_det = n;
+    std::map<std::pair<uint64_t, uint64_t>, int> index;
+    for (int i = 0; i < n; ++i) index[S[i]] = i;
+    // H_SS from the columns: column i holds H_{D', D_i}
+    std::vector<double> H((size_t)n * n, 0.0);
+    std::vector<uint64_t> ck((size_t)c->P.nh * 2);
+    std::vector<double> cv((size_t)c->P.nh);
+    for (int i = 0; i < n; ++i) {
+        CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+        CK(launch_column(c->P, S[i].second, S[i].first, c->d_colkeys, c->d_colvals, c->P.nh, c->d_counter, c->stream));
+        unsigned long long cnt = 0;
+        CK(cudaMemcpyAsync(&cnt, c->d_counter, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if ((long long)cnt > c->P.nh) return fail(CDFCI_ERR_INTERNAL, "column longer than its enumeration");
+        if (cnt > 0) {
+            CK(cudaMemcpyAsync(ck.data(), c->d_colkeys, cnt * 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(cv.data(), c->d_colvals, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        for (unsigned long long e = 0; e < cnt; ++e) {
+            const auto it = index.find({ck[2 * e + 1], ck[2 * e]});
+            if (it != index.end()) H[(size_t)it->second * n + i] = cv[e];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const double x = 0.5 * (H[(size_t)i * n + j] + H[(size_t)j * n + i]);
+            H[(size_t)i * n + j] = H[(size_t)j * n + i] = x;
+        }
+    double lam = 0.0;
+    std::vector<double> v;
+    jacobi_lowest(n, H, lam, v);
+    if (E_sub) *E_sub = lam;
+    std::vector<uint64_t> keys;
+    std::vector<double> cvals;
+    for (int i = 0; i < n; ++i)
+        if (v[i] != 0.0) {
+            keys.push_back(S[i].second);
+            keys.push_back(S[i].first);
+            cvals.push_back(v[i]);
+        }
+    return cdfci_set_initial(c, keys.data(), cvals.data(), (int64_t)cvals.size());
+}
+
 CDFCI_API int cdfci_time_kernels(cdfci_handle c, int64_t n_iter, double *ms, int32_t cap, int32_t *n_kernels) {
     if (!c || !ms || !n_kernels) return fail(CDFCI_ERR_ARG, "NULL argument");
     if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
@@ -966,9 +1172,6 @@ CDFCI_API int cdfci_set_initial(cdfci_handle c, const uint64_t *keys, const doub
     if (!c || !keys || !cv) return fail(CDFCI_ERR_ARG, "NULL argument");
     if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "start vectors are for one state (num_states = 1)");
     if (n < 1) return fail(CDFCI_ERR_ARG, "n = %lld, need at least one entry", (long long)n);
-    if (c->block && n > c->mb.m)
-        return fail(CDFCI_ERR_ARG, "%lld entries for m = %d: a block handle takes at most m start entries", (long long)n,
-                    c->mb.m);
     if (n > c->P.max_entries) return fail(CDFCI_ERR_TABLE_FULL, "%lld entries exceed max_load of the table", (long long)n);
     std::vector<uint64_t> hk;
     std::vector<double> hc;
@@ -998,6 +1201,10 @@ CDFCI_API int cdfci_set_initial(cdfci_handle c, const uint64_t *keys, const doub
         }
         if (rc) return rc;
     } else {
+        // the candidates of every start column: at most n columns' elements and the n entries
+        const long long nh_eff = c->P.doubles_vanish ? c->P.seg[2] : c->P.seg[5];
+        rc = grow_candidates(c, (long long)n * nh_eff + n + 64);
+        if (rc) return rc;
         for (int64_t k = 0; k < n; ++k) {
             CK(launch_mc_start(c->P, c->mb, hk[2 * k], hk[2 * k + 1], hc[k], k == 0 ? 1 : 0, c->stream));
             CK(launch_mc_scatter_finalize(c->P, c->mb, c->stream));

@@ -271,6 +271,13 @@ __device__ __forceinline__ void sym2_lowest(float a00, float a01, float a11, flo
 // one or two levels; later levels return at once.
 // ---------------------------------------------------------------------------
 constexpr int kSelBins = 4096;
+
+// Candidates in the list: the count, clamped to the list's capacity (a count
+// above it only occurs after an overflow, which set the status).
+__device__ __forceinline__ int mc_ncand(const McState *ms, long long cap) {
+    const long long n = ms->n_cand;
+    return (int)(n < cap ? n : cap);
+}
 constexpr int kSelLevels = 6;
 
 __device__ __forceinline__ int sel_bits(int level) { return level < 5 ? 12 : 4; }
@@ -357,7 +364,7 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterSt
                                                   unsigned long long *gkey, unsigned int *hist, int m) {
     __shared__ unsigned int sh[kSelBins];
     if (ms->done) return;
-    const int n = ms->n_cand;
+    const int n = mc_ncand(ms, P.cap_cand);
     const double mu = ms->mu.hi;
     const bool count = n > m;
     for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
@@ -398,10 +405,10 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterSt
 
 // level >= 1: the keys on the current prefix
 __global__ void __launch_bounds__(256) k_mc_hist(McState *ms, const unsigned long long *gkey, unsigned int *hist,
-                                                 int level) {
+                                                 int level, long long cap) {
     __shared__ unsigned int sh[kSelBins];
     if (ms->done || ms->sel_resolved) return;
-    const int n = ms->n_cand;
+    const int n = mc_ncand(ms, cap);
     const unsigned long long prefix = ms->sel_prefix;
     const int need = ms->sel_need;
     for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
@@ -420,7 +427,7 @@ __global__ void __launch_bounds__(256) k_mc_hist(McState *ms, const unsigned lon
 // it returns at once when the selection is resolved, which is the common case;
 // otherwise it counts the keys on the prefix in a shared-memory histogram and
 // scans it, level by level, exactly as k_mc_hist and sel_scan do.
-__global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsigned long long *gkey) {
+__global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsigned long long *gkey, long long cap) {
     __shared__ unsigned int sh[kSelBins];
     __shared__ unsigned int s_warp[32];
     __shared__ int s_stop;
@@ -430,7 +437,7 @@ __global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsign
         for (int d = tid; d < kSelBins; d += blockDim.x) sh[d] = 0u;
         __syncthreads();
         if (s_stop) return;
-        const int n = ms->n_cand;
+        const int n = mc_ncand(ms, cap);
         const unsigned long long prefix = ms->sel_prefix;
         const int need = ms->sel_need;
         for (int base = 0; base < n; base += blockDim.x) {
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsign
 __global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, const unsigned long long *gkey,
                              McSel *sel, McSel *inbin) {
     if (ms->done) return;
-    const int n = ms->n_cand;
+    const int n = mc_ncand(ms, P.cap_cand);
     const bool all = ms->sel_level == 0;                 // n_cand <= m: every candidate is selected
     const int L = ms->sel_level;
     const unsigned long long prefix = ms->sel_prefix;
@@ -517,7 +524,7 @@ __global__ void __launch_bounds__(1024) k_mc_ties(Problem P, McState *ms, const 
     __shared__ int s_n, s_out, s_digit;
     __shared__ unsigned int s_below;
     if (ms->done || ms->sel_level < kSelLevels || ms->n_inbin <= kInBin) return;
-    const int n = ms->n_cand, tid = threadIdx.x;
+    const int n = mc_ncand(ms, P.cap_cand), tid = threadIdx.x;
     const unsigned long long g = ms->sel_prefix;
     int need = ms->sel_need;
     if (tid == 0) { s_n = 0; s_out = 0; }
@@ -1235,14 +1242,19 @@ __device__ __forceinline__ void mc_elem(const Problem &P, const ColLists &L, con
     }
 }
 
-// The warp's candidate buffer to the global list (one reservation).
-__device__ __forceinline__ void mc_flush_cand(McState *ms, long long *wcand, int &nwc, long long *cand) {
+// The warp's candidate buffer to the global list (one reservation); entries
+// beyond the list's capacity are not written and set the status.
+__device__ __forceinline__ void mc_flush_cand(const Problem &P, McState *ms, IterState *st, long long *wcand, int &nwc,
+                                              long long *cand) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     int base = 0;
     if (lane == 0 && nwc > 0) base = atomicAdd(&ms->n_cand, nwc);
     base = __shfl_sync(0xffffffffu, base, 0);
-    for (int i = lane; i < nwc; i += 32) cand[base + i] = wcand[i];
+    for (int i = lane; i < nwc; i += 32) {
+        if ((long long)base + i < P.cap_cand) cand[base + i] = wcand[i];
+        else set_status(st, kErrInternal);
+    }
     nwc = 0;
     __syncwarp();
 }
@@ -1281,7 +1293,7 @@ __device__ __forceinline__ bool mc_apply(const Problem &P, McState *ms, IterStat
     const unsigned int fm = __ballot_sync(0xffffffffu, first);
     if (first) wcand[nwc + __popc(fm & ((1u << lane) - 1u))] = s;
     nwc += __popc(fm);
-    if (nwc > kWarpCand - 32) mc_flush_cand(ms, wcand, nwc, cand);
+    if (nwc > kWarpCand - 32) mc_flush_cand(P, ms, st, wcand, nwc, cand);
     return __any_sync(0xffffffffu, err);
 }
 
@@ -1399,7 +1411,7 @@ __global__ void __launch_bounds__(256, 4) k_mc_scatter(Problem P, McState *ms, I
         }
         f0 = f1;
     }
-    mc_flush_cand(ms, w_cand[warp], nwc, cand);
+    mc_flush_cand(P, ms, st, w_cand[warp], nwc, cand);
     // counters: warp sums, then the warps in order
     const int r0 = __reduce_add_sync(0xffffffffu, c_el), r1 = __reduce_add_sync(0xffffffffu, c_app);
     const int r2 = __reduce_add_sync(0xffffffffu, c_drop), r3 = __reduce_add_sync(0xffffffffu, c_ins);
@@ -1447,7 +1459,11 @@ __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel
             int base = 0;
             if (lane == 0) base = atomicAdd(&ms->n_cand, __popc(am));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (append) cand[base + __popc(am & ((1u << lane) - 1u))] = slot;
+            const long long at = (long long)base + __popc(am & ((1u << lane) - 1u));
+            if (append) {
+                if (at < P.cap_cand) cand[at] = slot;
+                else set_status(st, kErrInternal);
+            }
         }
     }
     __shared__ int s_nd;
@@ -1623,9 +1639,9 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
     mark();
     k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.st, b.cand, b.gkey, b.hist, b.m);
     mark();
-    k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, 1);
+    k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, 1, b.cap_cand);
     mark();
-    k_mc_hist_tail<<<1, 1024, 0, s>>>(b.ms, b.gkey);
+    k_mc_hist_tail<<<1, 1024, 0, s>>>(b.ms, b.gkey, b.cap_cand);
     mark();
     k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
     mark();

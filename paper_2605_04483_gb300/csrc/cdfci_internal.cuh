@@ -192,6 +192,7 @@ struct Problem {
     unsigned int *cnz;             // m > 1: filter of determinants whose c may be nonzero (NULL: none)
     unsigned long long cnz_mask;   // its bit count - 1
     unsigned int *mark;            // m > 1: candidate marks, one bit per slot (NULL: bit 63 of the slot's B)
+    long long cap_cand;            // m > 1: entries of the candidate list
 };
 
 // ---------------------------------------------------------------------------

@@ -1150,6 +1150,18 @@ __global__ void k_validate_g(double *g, int N, double tol, int *status) {
         if (fabs(x - y) > tol * fmax(1.0, fabs(y))) atomicCAS(status, 0, kErrArg);
     }
 }
+// 4-fold form (complex orbitals with real integrals): (pq|rs) = (rs|pq) = (qp|sr)
+__global__ void k_validate_g4(const double *g, int N, double tol, int *status) {
+    const long long n4 = (long long)N * N * N * N;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t % N), r = (int)((t / N) % N), q = (int)((t / N / N) % N), p = (int)(t / N / N / N);
+        const double x = g[t];
+        const double y1 = g[(((long long)r * N + s) * N + p) * N + q], y2 = g[(((long long)q * N + p) * N + s) * N + r];
+        if (!isfinite(x)) { atomicCAS(status, 0, kErrNonfinite); continue; }
+        if (fabs(x - y1) > tol * fmax(1.0, fabs(y1)) || fabs(x - y2) > tol * fmax(1.0, fabs(y2)))
+            atomicCAS(status, 0, kErrArg);
+    }
+}
 __global__ void k_canonicalize_g(double *g, int N) {
     const long long n4 = (long long)N * N * N * N;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (long long)gridDim.x * blockDim.x) {
@@ -1431,14 +1443,18 @@ cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long lon
 }
 
 cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, double *W3, double *V3, int *status,
-                         int *has_doubles, cudaStream_t s) {
+                         int *has_doubles, int sym4, cudaStream_t s) {
     long long n4 = (long long)N * N * N * N;
     int grid = (int)((n4 + 255) / 256);
     if (grid > 4096) grid = 4096;
     k_validate_h<<<4, 256, 0, s>>>(h, N, 1e-12, status);
-    k_validate_g<<<grid, 256, 0, s>>>(g, N, 1e-12, status);
+    if (sym4) {
+        k_validate_g4<<<grid, 256, 0, s>>>(g, N, 1e-12, status);
+    } else {
+        k_validate_g<<<grid, 256, 0, s>>>(g, N, 1e-12, status);
+    }
     k_symmetrize_h<<<4, 256, 0, s>>>(h, N);
-    k_canonicalize_g<<<grid, 256, 0, s>>>(g, N);
+    if (!sym4) k_canonicalize_g<<<grid, 256, 0, s>>>(g, N);
     k_jk<<<grid, 256, 0, s>>>(g, N, J, K, has_doubles);
     const long long n3 = (long long)N * N * N;
     k_w3v3<<<(int)std::min<long long>((n3 + 255) / 256, 1024), 256, 0, s>>>(g, N, W3, V3);

@@ -19,8 +19,7 @@ cudaError_t launch_export(const Problem &P, const IterState *st, unsigned long l
 cudaError_t launch_rq(const Problem &P, IterState *st, long long *list, long long cap, unsigned long long *counter,
                       double *partial, int nblocks, double *out, cudaStream_t s);
 cudaError_t launch_setup(double *h, double *g, int N, double *J, double *K, double *W3, double *V3, int *status,
-                         int *has_doubles,
-                         cudaStream_t s);
+                         int *has_doubles, int sym4, cudaStream_t s);
 cudaError_t launch_init_state(IterState *st, CdRecord *rec, unsigned long long A, unsigned long long B, double eta,
                               cudaStream_t s);
 cudaError_t launch_force_next(CdRecord *rec, const unsigned long long *keys, const double *c, long long k,

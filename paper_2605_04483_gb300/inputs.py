@@ -110,6 +110,51 @@ def hubbard(shape: Sequence[int], n_alpha: int, n_beta: int, t: float = 1.0, U: 
                     dict(kind="hubbard", shape=list(shape), t=t, U=U, periodic=periodic))
 
 
+def momenta(shape: Sequence[int]) -> np.ndarray:
+    """Integer momentum indices n (row-major, one row per plane wave); k_d = 2 pi n_d / L_d."""
+    return np.array(list(np.ndindex(*tuple(int(x) for x in shape))), dtype=np.int64).reshape(-1, len(shape))
+
+
+def hubbard_k_integrals(shape: Sequence[int], t: float, U: float) -> Tuple[np.ndarray, np.ndarray]:
+    """The periodic Hubbard model in the plane-wave basis phi_k(x) = exp(i k.x) / sqrt(L), one orbital per
+    momentum (the row order of momenta()).  h is diagonal: eps_k = sum_xy conj(phi_k(x)) h_xy phi_k(y) of the
+    real-space hopping (so a length-2 direction keeps its single bond); the on-site U gives
+    (pq|rs) = sum_x U conj(phi_p) phi_q conj(phi_r) phi_s = (U/L) delta(k_q - k_p + k_s - k_r), real, with
+    only the symmetries (pq|rs) = (rs|pq) = (qp|sr)."""
+    shape = tuple(int(x) for x in shape)
+    L = int(np.prod(shape))
+    n = momenta(shape)
+    hr, _ = hubbard_integrals(shape, t, U, True)
+    x = momenta(shape)                                  # site coordinates, same row-major order
+    phase = 2.0 * np.pi * (x / np.array(shape, dtype=float)) @ n.T     # [site, k]
+    P = np.exp(1j * phase) / np.sqrt(L)
+    hk = P.conj().T @ hr @ P
+    off = hk - np.diag(np.diag(hk))
+    if np.max(np.abs(off)) > 1e-12 or np.max(np.abs(hk.imag)) > 1e-12:
+        raise AssertionError("the hopping is not diagonal in the plane waves")
+    # rounded to 12 decimals so that equal levels (the degenerate shells) are exactly equal
+    h = np.diag(np.round(np.diag(hk).real, 12) + 0.0)
+    dk = (-n[:, None, None, None, :] + n[None, :, None, None, :] - n[None, None, :, None, :]
+          + n[None, None, None, :, :]) % np.array(shape)
+    g = np.where(np.all(dk == 0, axis=-1), U / L, 0.0)
+    return h, g
+
+
+def hubbard_k(shape: Sequence[int], n_alpha: int, n_beta: int, t: float = 1.0, U: float = 4.0,
+              name: str | None = None) -> Workload:
+    """The k-space Hubbard model (HamiltonianHubbardK, periodic boundaries); a handle needs
+    integral_symmetry = 4.  Start: aufbau on eps_k, or the degenerate-subspace start."""
+    h, g = hubbard_k_integrals(shape, t, U)
+    return Workload(name or f"hubbardk_{'x'.join(map(str, shape))}_U{U:g}", int(np.prod(shape)),
+                    n_alpha, n_beta, h, g, (0, 0),
+                    dict(kind="hubbard_k", shape=list(shape), t=t, U=U, periodic=True, integral_symmetry=4))
+
+
+def config3_k(U: float = 4.0, n_alpha: int = 8, n_beta: int = 8) -> Workload:
+    """The paper's own Hubbard setting: 4x4 periodic lattice in momentum space, t = 1 (half filling: 8 + 8)."""
+    return hubbard_k((4, 4), n_alpha, n_beta, t=1.0, U=U, name=f"hubbardk_4x4_pbc_U{U:g}_{n_alpha}a{n_beta}b")
+
+
 # ---------------------------------------------------------------------------
 # Synthetic ab initio integrals
 # ---------------------------------------------------------------------------

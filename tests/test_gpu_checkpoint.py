@@ -116,11 +116,24 @@ def test_start_vector_errors():
         with pytest.raises(api.CdfciError) as e:
             g.set_initial(bad_keys, bad_c)
         assert e.value.code == -1
+    g.close()
+
+
+def test_start_vector_longer_than_the_block():
+    """m = 4 with a start of 5 entries: the candidates of all start columns fit the list
+    (its capacity bounds every write on the device), the state matches the oracle's."""
+    w = inputs.ab_initio(8, 3, 3, seed=7)
+    keys, c = start_vector(w, 5, seed=3)
     h4 = solver(w, num_coordinates=4)
-    with pytest.raises(api.CdfciError) as e:
-        h4.set_initial(keys, c)                         # 5 > m = 4
-    assert e.value.code == -1
-    g.close(); h4.close()
+    o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, w.ref, 0.0, 4)
+    h4.set_initial(keys, c)
+    o.set_initial(keys, c)
+    assert abs(h4.stats()["energy"] - o.energy()) <= 1e-11 * abs(o.energy())
+    assert_same_vectors(h4, o, tol=1e-11)
+    h4.step(10)
+    o.step(10)
+    assert abs(h4.stats()["energy"] - o.energy()) <= 1e-9 * abs(o.energy())
+    h4.close(); o.close()
 
 
 @pytest.mark.parametrize("grid_a, grid_b", [(24, 24), (4, 4), (24, 4)])

@@ -1,0 +1,185 @@
+"""GPU k-space Hubbard model (HamiltonianHubbardK of Sec. "The Hamiltonian Class": plane-wave
+orbitals, (pq|rs) = (U/L) delta of the momenta, integral_symmetry = 4) against the oracle:
+the symmetry check at create, columns, an Algorithm-1 trajectory, Algorithm-2 convergence to
+exact diagonalisation, and the degenerate-subspace start of the paper's 4x4 example."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_04483_gb300 import inputs
+from gpu_util import require_gpu, vec_by_key
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def ksolver(w, **kw):
+    from paper_2605_04483_gb300 import api
+    kw.setdefault("log2_capacity", 16)
+    return api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]),
+                      integral_symmetry=4, **kw)
+
+
+def random_dets(N, na, nb, n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        a = sum(1 << int(p) for p in rng.choice(N, na, replace=False))
+        b = sum(1 << int(p) for p in rng.choice(N, nb, replace=False))
+        out.append((a, b))
+    return out
+
+
+def test_create_checks_the_symmetry():
+    """The plane-wave g lacks the 8-fold symmetry, so the default create rejects it; with
+    integral_symmetry = 4 it is accepted, and a g that breaks (pq|rs) = (rs|pq) is not."""
+    from paper_2605_04483_gb300 import api
+    w = inputs.hubbard_k((2, 3), 3, 2, U=2.0)
+    with pytest.raises(api.CdfciError) as e:
+        api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, log2_capacity=12)
+    assert e.value.code == -1
+    ksolver(w, log2_capacity=12).close()
+    g2 = w.g.copy()
+    g2[0, 1, 2, 3] += 0.01
+    with pytest.raises(api.CdfciError) as e:
+        api.Solver(w.h, g2, w.N, w.n_alpha, w.n_beta, log2_capacity=12, integral_symmetry=4)
+    assert e.value.code == -1
+    with pytest.raises(api.CdfciError) as e:
+        api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, log2_capacity=12, integral_symmetry=3)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("w", [inputs.hubbard_k((2, 3), 3, 2, U=2.0), inputs.config3_k(4.0)],
+                         ids=["2x3", "4x4"])
+def test_columns_match_the_oracle(w):
+    """Keys exact and values to 1e-12 for every entry above 1e-12 (a diagonal whose true value
+    is 0 may round to a few 1e-16 on either side)."""
+    s = ksolver(w)
+    try:
+        for d in random_dets(w.N, w.n_alpha, w.n_beta, 6, seed=5):
+            kg, vg = s.column(d)
+            ko, vo = oracle.column_sc(w.N, w.h, w.g, d)
+            mg = {k: v for k, v in vec_by_key(kg, vg).items() if abs(v) > 1e-12}
+            mo = {k: v for k, v in vec_by_key(ko, vo).items() if abs(v) > 1e-12}
+            assert set(mg) == set(mo)
+            assert all(abs(mg[k] - mo[k]) <= 1e-12 * max(1.0, abs(mo[k])) for k in mo)
+    finally:
+        s.close()
+
+
+def test_trajectory_matches_oracle():
+    """Algorithm 1 on a 2x4 ring of 4 + 4 electrons in momentum space: the GPU's choice is an
+    argmax of the oracle's |gradient| (lattice symmetry makes exact ties, broken either way),
+    eta and the energy agree each step."""
+    w = inputs.hubbard_k((2, 4), 4, 4, U=4.0)
+    g = ksolver(w)
+    o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, w.ref, 0.0, 1)
+    try:
+        for it in range(300):
+            st = g.step(1)
+            (kg,), (eg,) = g.last_step()
+            gc, gm = o.step_choice(kg)
+            assert gc >= gm * (1 - 1e-12), (it, gc, gm)
+            (ko,), (eo,) = o.last_step()
+            assert abs(eg - eo) <= 1e-10 * max(1.0, abs(eo)), (it, eg, eo)
+            assert abs(st["energy"] - o.energy()) <= 1e-11 * max(1.0, abs(o.energy())), it
+    finally:
+        g.close()
+        o.close()
+
+
+@pytest.mark.parametrize("m", [1, 16])
+def test_converges_to_exact_diagonalisation(m):
+    """2x4 ring, 4 + 4 electrons (FCI dim 4,900): within 1e-8 of the oracle's exact energy."""
+    w = inputs.hubbard_k((2, 4), 4, 4, U=4.0)
+    E0 = oracle.ground_energy(w.N, 4, 4, w.h, w.g)
+    s = ksolver(w, num_coordinates=m)
+    try:
+        for _ in range(400):
+            s.step(2000 if m == 1 else 100)
+            if abs(s.energy(mode=1) - E0) <= 1e-9:
+                break
+        assert abs(s.energy(mode=1) - E0) <= 1e-8
+        assert abs(s.stats()["energy"] - E0) <= 1e-8
+    finally:
+        s.close()
+
+
+def test_degenerate_start_matches_oracle():
+    """6-site ring, 2 + 2: four degenerate configurations; the start's eigenvalue and vector equal
+    the oracle's, and the state's Rayleigh quotient is that eigenvalue.  Then 100 steps of
+    Algorithm 1 from it agree with the oracle started from the same vector."""
+    w = inputs.hubbard_k((6,), 2, 2, U=4.0)
+    keys, c, E = oracle.degenerate_start(w.N, 2, 2, w.h, w.g)
+    s = ksolver(w)
+    try:
+        n, Eg = s.set_initial_degenerate()
+        assert n == len(keys) == 4 and abs(Eg - E) <= 1e-12 * max(1.0, abs(E))
+        assert abs(s.energy(mode=1) - E) <= 1e-12 * max(1.0, abs(E))
+        kg, cg, _ = s.export()
+        mg = vec_by_key(kg, cg)
+        for k, v in zip(keys, c):
+            assert abs(mg.get((int(k[0]), int(k[1])), 0.0) - v) <= 1e-12
+        o = oracle.CDFCI(w.N, 2, 2, w.h, w.g, (0, 0), 0.0, 1)
+        o.set_initial(keys[c != 0], c[c != 0])
+        for it in range(100):
+            s.step(1)
+            (kk,), (eg,) = s.last_step()
+            gc, gm = o.step_choice(kk)
+            assert gc >= gm * (1 - 1e-12), (it, gc, gm)
+            assert abs(s.stats()["energy"] - o.energy()) <= 1e-10 * abs(o.energy()), it
+        o.close()
+    finally:
+        s.close()
+
+
+def test_degenerate_start_4x4_paper_count():
+    """The paper's 4x4 example at half filling: 400 = C(6, 3)^2 degenerate configurations; the
+    lowest eigenvalue on them agrees with the oracle's (numpy eigh on the same submatrix)."""
+    w = inputs.config3_k(4.0)
+    keys, c, E = oracle.degenerate_start(w.N, 8, 8, w.h, w.g)
+    for m in (1, 128):
+        s = ksolver(w, num_coordinates=m, log2_capacity=23)
+        try:
+            n, Eg = s.set_initial_degenerate()
+            assert n == 400 == math.comb(6, 3) ** 2
+            assert abs(Eg - E) <= 1e-10 * abs(E)
+            assert abs(s.energy(mode=1) - E) <= 1e-10 * abs(E)
+            if m > 1:
+                # alpha / mu is not monotone while |c| grows from 1 towards sqrt(-E0); after 100
+                # block iterations it is well below the start's Rayleigh quotient
+                s.step(100)
+                assert s.stats()["energy"] < E - 1.0
+        finally:
+            s.close()
+
+
+def test_paper_4x4_weak_coupling_energy():
+    """The paper's 4x4 half-filled lattice at U/t = 0.5 from the degenerate start (its table
+    "hubbard-ut", exact diagonalisation -22.34023 Ha to five decimals): m = 128 reaches it
+    within 1e-5 Ha."""
+    ref = None
+    import os
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_hubbard_ed.txt")):
+        f = line.split()
+        if f and not line.startswith("#") and (f[0], f[1], f[2]) == ("8", "8", "0.5"):
+            ref = float(f[3])
+    assert ref == -22.34023
+    w = inputs.config3_k(0.5)
+    s = ksolver(w, num_coordinates=128, log2_capacity=24)
+    try:
+        s.set_initial_degenerate()
+        for _ in range(60):
+            s.step(200)
+            if abs(s.stats()["energy"] - ref) < 1e-5:
+                break
+        assert abs(s.stats()["energy"] - ref) < 1e-5
+        assert abs(s.energy(mode=1) - ref) < 1e-5
+    finally:
+        s.close()
