@@ -781,7 +781,11 @@ __device__ __forceinline__ float f_row(const float *Ah, int ld, int n, int row, 
 
 // Threads per row of the reduced problem and the shared-memory row stride for
 // a problem of size n1 = m + 1 (columns padded to ldr).
-__host__ __device__ __forceinline__ int eig_tpr(int n1) { return n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1); }
+// 2 threads per row up to 150 rows (cheaper block sums, measured faster; with the wider row padding R
+// still fits in shared memory), 4 up to 256, then 2, then 1.
+__host__ __device__ __forceinline__ int eig_tpr(int n1) {
+    return n1 <= 150 ? 2 : (n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1));
+}
 __host__ __device__ __forceinline__ int eig_lds(int ldr, int tpr) { return ldr + 32 / tpr; }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -1608,7 +1612,7 @@ long long mc_gath_entries(int m, int grid) { return 2ll * grid + 2ll * m + 8; }
 
 cudaError_t mc_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)mc_eigen_smem(kEigSmemN - 1));
+                                         (int)std::max(mc_eigen_smem(kEigSmemN - 1), mc_eigen_smem(149)));
     if (e != cudaSuccess) return e;
     // N <= 64: at most 2 x 32 x 32 single-excitation entries
     e = cudaFuncSetAttribute(k_mc_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
