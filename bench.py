@@ -164,16 +164,16 @@ def paper_hubbard_ed(na: int, nb: int, U: float) -> float:
 
 
 def hubbard_k_leg(api, inputs) -> dict:
-    """The paper's own lattice setting: the 4x4 periodic Hubbard model in momentum space (integral_symmetry
-    = 4), half filling, from the degenerate-subspace start, m = 128, 2^24 slots: seconds until the running
+    """The paper's own lattice setting: the 4x4 periodic Hubbard model in momentum space built by the library
+    (cdfci_create_hubbard_k: momentum-conserving enumeration), half filling, from the degenerate-subspace
+    start, m = 128, 2^24 slots: seconds until the running
     energy is within 1e-5 Ha of the paper's exact value at U/t = 0.5 (its table: CDFCI there took 13 s), and
     the energy reached in a 20 s budget at U/t = 4 (its table: 9 minutes to the exact value)."""
     out = {}
     for U, budget in ((0.5, 30.0), (4.0, 20.0)):
         ref = paper_hubbard_ed(8, 8, U)
-        w = inputs.config3_k(U)
-        s = api.Solver(w.h, w.g, w.N, 8, 8, num_coordinates=128, log2_capacity=24, integral_symmetry=4,
-                       z_threshold_search=1)
+        s = api.Solver.hubbard_k((4, 4), 8, 8, t=1.0, U=U, num_coordinates=128, log2_capacity=24,
+                                 z_threshold_search=1)
         try:
             t0 = time.perf_counter()
             n_det, E_start = s.set_initial_degenerate()

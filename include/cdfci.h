@@ -143,6 +143,22 @@ int cdfci_create(const double *h, const double *g, int N, int n_alpha, int n_bet
                  const cdfci_params *params, cdfci_handle *out);
 
 /*
+ * The k-space Hubbard model (HamiltonianHubbardK of Sec. "The Hamiltonian
+ * Class": a D-dimensional periodic orthogonal lattice, nearest-neighbour
+ * hopping t, on-site U) in plane-wave orbitals, one per momentum (row-major
+ * momentum indices n, the last direction fastest; k_d = 2 pi n_d / shape[d]).
+ * h = diag(eps_k), eps_k = sum_d -2t cos k_d over directions of extent >= 3,
+ * -t cos k_d for extent 2 (a single bond), rounded to 12 decimals; (pq|rs) =
+ * U/L when k_q - k_p + k_s - k_r = 0, else 0 (integral_symmetry = 4 is
+ * implied).  The handle also keeps the lattice's momentum tables, so the
+ * column enumeration drops the opposite-spin doubles that do not conserve
+ * momentum before any integral or table access.  shape: D extents (host),
+ * prod(shape) <= 64 orbitals; otherwise as cdfci_create.
+ */
+int cdfci_create_hubbard_k(const int32_t *shape, int32_t D, double t, double U, int n_alpha, int n_beta,
+                           const cdfci_params *params, cdfci_handle *out);
+
+/*
  * Run n_iter iterations of Algorithm 1 (m = 1: Gauss-Southwell choice over the
  * last column, Eq. choose-i; exact line search, appendix; Eq. update-var with
  * compression; recalculation of b_i, Eq. recalculate-b) or Algorithm 2

@@ -116,6 +116,9 @@ def lib():
         L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
         L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.cdfci_time_kernels.argtypes = [vp, i64, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.cdfci_create_hubbard_k.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(cdfci_params),
+                                             ctypes.POINTER(vp)]
         L.cdfci_set_initial_degenerate.argtypes = [vp, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int64),
                                                    ctypes.POINTER(ctypes.c_double)]
         L.cdfci_optorb.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
@@ -166,6 +169,17 @@ def cdfci_create(h, g, N: int, n_alpha: int, n_beta: int, params: Optional[cdfci
     handle = ctypes.c_void_p()
     p = params if params is not None else cdfci_default_params()
     _check(lib().cdfci_create(_ptr(h), _ptr(g), N, n_alpha, n_beta, ctypes.byref(p), ctypes.byref(handle)))
+    return handle.value
+
+
+def cdfci_create_hubbard_k(shape, t: float, U: float, n_alpha: int, n_beta: int,
+                           params: Optional[cdfci_params] = None) -> int:
+    """The k-space Hubbard model built by the library (plane waves, momentum tables)."""
+    dims = np.ascontiguousarray(shape, dtype=np.int32).reshape(-1)
+    handle = ctypes.c_void_p()
+    p = params if params is not None else cdfci_default_params()
+    _check(lib().cdfci_create_hubbard_k(dims.ctypes.data, len(dims), float(t), float(U), int(n_alpha), int(n_beta),
+                                        ctypes.byref(p), ctypes.byref(handle)))
     return handle.value
 
 
@@ -389,6 +403,15 @@ class Solver:
         self.handle = cdfci_create(np.ascontiguousarray(h, dtype=np.float64) if isinstance(h, np.ndarray) else h,
                                    np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g,
                                    N, n_alpha, n_beta, self.p)
+
+    @classmethod
+    def hubbard_k(cls, shape, n_alpha: int, n_beta: int, t: float = 1.0, U: float = 4.0, **params) -> "Solver":
+        """A solver of the k-space Hubbard model built by the library (cdfci_create_hubbard_k)."""
+        self = cls.__new__(cls)
+        self.N = int(np.prod(shape))
+        self.p = cdfci_default_params(**params)
+        self.handle = cdfci_create_hubbard_k(shape, t, U, n_alpha, n_beta, self.p)
+        return self
 
     def step(self, n: int) -> dict:
         return cdfci_step(self.handle, n)

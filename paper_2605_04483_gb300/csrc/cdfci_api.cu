@@ -78,6 +78,7 @@ struct cdfci_ctx {
     // device buffers
     double *d_h = nullptr, *d_g = nullptr, *d_J = nullptr, *d_K = nullptr, *d_W3 = nullptr, *d_V3 = nullptr;
     unsigned short *d_pairs = nullptr;
+    unsigned char *d_ktab = nullptr;   // k-space handles: ksub then kadd (N x N each)
     Slot *d_table = nullptr;
     IterState *d_st = nullptr;
     CdRecord *d_rec = nullptr;                   // state between launches of the cluster loop
@@ -113,7 +114,7 @@ void free_ctx(cdfci_ctx *c) {
     if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
     for (int i = 0; i < c->mb_nalloc; ++i) cudaFree(c->mb_alloc[i]);
     cudaFree(c->d_h); cudaFree(c->d_g); cudaFree(c->d_J); cudaFree(c->d_K); cudaFree(c->d_W3); cudaFree(c->d_V3);
-    cudaFree(c->d_pairs); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part); cudaFree(c->d_rec);
+    cudaFree(c->d_pairs); cudaFree(c->d_ktab); cudaFree(c->d_table); cudaFree(c->d_st); cudaFree(c->d_part); cudaFree(c->d_rec);
     cudaFree(c->d_bar);
     cudaFree(c->d_flags); cudaFree(c->d_counter); cudaFree(c->d_colkeys); cudaFree(c->d_colvals);
     if (c->h_st) cudaFreeHost(c->h_st);
@@ -459,8 +460,13 @@ CDFCI_API void cdfci_default_params(cdfci_params *p) {
 
 CDFCI_API const char *cdfci_last_error(void) { return g_last_error.c_str(); }
 
-CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha, int n_beta, const cdfci_params *params,
-                 cdfci_handle *out) {
+}  // extern "C"
+
+namespace {
+// cdfci_create, with the momentum tables of a k-space handle (host, ksub then kadd, N x N bytes
+// each) or NULL.
+int create_impl(const double *h, const double *g, int N, int n_alpha, int n_beta, const cdfci_params *params,
+                const unsigned char *ktab, cdfci_handle *out) {
     if (!out) return fail(CDFCI_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!h || !g) return fail(CDFCI_ERR_ARG, "h or g is NULL");
@@ -589,6 +595,14 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
     P.pair_va = P.pair_ob + pob.size();
     P.pair_vb = P.pair_va + pva.size();
     P.h = c->d_h; P.g = c->d_g; P.J = c->d_J; P.K = c->d_K; P.W3 = c->d_W3; P.V3 = c->d_V3;
+    if (ktab) {
+        if (cudaMalloc(&c->d_ktab, 2 * (size_t)N * N) != cudaSuccess)
+            return bail(fail(CDFCI_ERR_NOMEM, "device allocation failed"));
+        if (cudaMemcpyAsync(c->d_ktab, ktab, 2 * (size_t)N * N, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return bail(fail(CDFCI_ERR_CUDA, "copy of the momentum tables failed"));
+        P.ksub = c->d_ktab;
+        P.kadd = c->d_ktab + (size_t)N * N;
+    }
 
     // table, state, partials, scratch
     if (cudaMalloc(&c->d_table, (size_t)P.capacity * sizeof(Slot)) != cudaSuccess)
@@ -681,6 +695,74 @@ CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha,
     if (rc != CDFCI_OK) return bail(rc);
     *out = c;
     return CDFCI_OK;
+}
+}  // namespace
+
+extern "C" {
+
+CDFCI_API int cdfci_create(const double *h, const double *g, int N, int n_alpha, int n_beta, const cdfci_params *params,
+                 cdfci_handle *out) {
+    return create_impl(h, g, N, n_alpha, n_beta, params, nullptr, out);
+}
+
+CDFCI_API int cdfci_create_hubbard_k(const int32_t *shape, int32_t D, double t, double U, int n_alpha, int n_beta,
+                                     const cdfci_params *params, cdfci_handle *out) {
+    if (!out) return fail(CDFCI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!shape || D < 1 || D > 8) return fail(CDFCI_ERR_ARG, "lattice dimension D = %d outside [1, 8]", (int)D);
+    long long L = 1;
+    for (int d = 0; d < D; ++d) {
+        if (shape[d] < 1) return fail(CDFCI_ERR_ARG, "extent %d of direction %d", (int)shape[d], d);
+        L *= shape[d];
+        if (L > kMaxN) return fail(CDFCI_ERR_ARG, "%lld sites exceed %d orbitals", L, kMaxN);
+    }
+    if (!std::isfinite(t) || !std::isfinite(U)) return fail(CDFCI_ERR_ARG, "t or U is not finite");
+    const int N = (int)L;
+    // momentum indices n_p, row-major (the last direction fastest)
+    std::vector<int> mom((size_t)N * D);
+    for (int p = 0; p < N; ++p) {
+        int r = p;
+        for (int d = D - 1; d >= 0; --d) { mom[(size_t)p * D + d] = r % shape[d]; r /= shape[d]; }
+    }
+    auto index_of = [&](const int *m) {
+        int p = 0;
+        for (int d = 0; d < D; ++d) p = p * shape[d] + (((m[d] % shape[d]) + shape[d]) % shape[d]);
+        return p;
+    };
+    // eps_k of the nearest-neighbour hopping: -2t cos k_d per direction of extent >= 3 (two bonds),
+    // -t cos k_d for extent 2 (one bond), none for extent 1; rounded to 12 decimals
+    std::vector<double> h((size_t)N * N, 0.0);
+    for (int p = 0; p < N; ++p) {
+        double e = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double k = 2.0 * M_PI * mom[(size_t)p * D + d] / shape[d];
+            if (shape[d] >= 3) e += -2.0 * t * std::cos(k);
+            else if (shape[d] == 2) e += -t * std::cos(k);
+        }
+        h[(size_t)p * N + p] = std::nearbyint(e * 1e12) / 1e12 + 0.0;
+    }
+    // (pq|rs) = U/L when k_q - k_p + k_s - k_r = 0; momentum tables
+    std::vector<unsigned char> ktab(2 * (size_t)N * N);
+    std::vector<int> m(D);
+    for (int p = 0; p < N; ++p)
+        for (int q = 0; q < N; ++q) {
+            for (int d = 0; d < D; ++d) m[d] = mom[(size_t)q * D + d] - mom[(size_t)p * D + d];
+            ktab[(size_t)p * N + q] = (unsigned char)index_of(m.data());
+            for (int d = 0; d < D; ++d) m[d] = mom[(size_t)p * D + d] + mom[(size_t)q * D + d];
+            ktab[(size_t)N * N + (size_t)p * N + q] = (unsigned char)index_of(m.data());
+        }
+    std::vector<double> g((size_t)N * N * N * N, 0.0);
+    const double v = U / (double)N;
+    for (int p = 0; p < N; ++p)
+        for (int q = 0; q < N; ++q)
+            for (int r = 0; r < N; ++r)
+                for (int s2 = 0; s2 < N; ++s2)
+                    if (ktab[(size_t)N * N + (size_t)ktab[(size_t)p * N + q] * N + ktab[(size_t)r * N + s2]] == 0)
+                        g[(((size_t)p * N + q) * N + r) * N + s2] = v;
+    cdfci_params prm;
+    if (params) prm = *params; else cdfci_default_params(&prm);
+    prm.integral_symmetry = 4;
+    return create_impl(h.data(), g.data(), N, n_alpha, n_beta, &prm, ktab.data(), out);
 }
 
 CDFCI_API int cdfci_step(cdfci_handle c, int64_t n_iter, cdfci_stats *stats) {

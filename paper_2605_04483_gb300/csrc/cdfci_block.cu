@@ -1234,6 +1234,11 @@ __device__ __forceinline__ void mc_elem(const Problem &P, const ColLists &L, con
         oa = ea.key;
         ob = eb.key;
         hk = ea.h ^ eb.h;
+        if (!k_conserved(P, (ea.info >> 24) & 0xff, (eb.info >> 24) & 0xff)) {   // momentum not conserved
+            H = 0.0;
+            maybe = false;
+            return;
+        }
         const double gv = __ldg(P.g + ea.goff + eb.goff);
         maybe = cnz_maybe(P, hk);
         H = apply_parity(gv, (unsigned long long)((ea.info ^ eb.info) & 1));

@@ -193,7 +193,16 @@ struct Problem {
     unsigned long long cnz_mask;   // its bit count - 1
     unsigned int *mark;            // m > 1: candidate marks, one bit per slot (NULL: bit 63 of the slot's B)
     long long cap_cand;            // m > 1: entries of the candidate list
+    // k-space Hubbard handles (cdfci_create_hubbard_k), else NULL: the index of the momentum
+    // k_q - k_p (ksub[p N + q]) and of k_x + k_y (kadd[x N + y]); index 0 is k = 0
+    const unsigned char *ksub, *kadd;
 };
+
+// k-space handles: an opposite-spin double with momentum transfers dA (alpha) and dB
+// (beta) conserves momentum iff dA + dB = 0; the others are zero without an integral load.
+__device__ __forceinline__ bool k_conserved(const Problem &P, int dA, int dB) {
+    return !P.kadd || __ldg(P.kadd + dA * P.N + dB) == 0;
+}
 
 // ---------------------------------------------------------------------------
 // Bits and hashing
@@ -479,8 +488,9 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 }
 
 // One single excitation of the column determinant (per-iteration table): the
-// changed string, its hash, the offset of its orbital pair in g, the sign and
-// the orbitals (info = sign | i << 8 | a << 16).
+// changed string, its hash, the offset of its orbital pair in g, the sign, the
+// orbitals and, for k-space handles, the momentum transfer k_a - k_i
+// (info = sign | i << 8 | a << 16 | transfer << 24).
 struct SingleEnt {
     unsigned long long key, h;
     int goff;                          // alpha table: (i N + a) N^2;  beta table: j N + b
@@ -504,7 +514,8 @@ __device__ __forceinline__ void build_singles(const Problem &P, const ColLists &
         e.key = X ^ (1ull << i) ^ (1ull << a);
         e.h = alpha ? hash_alpha(e.key) : hash_beta(e.key);
         e.goff = alpha ? (i * N + a) * N * N : j_b_off(N, i, a);
-        e.info = (__popcll(X & between_mask(i, a)) & 1) | (i << 8) | (a << 16);
+        e.info = (__popcll(X & between_mask(i, a)) & 1) | (i << 8) | (a << 16) |
+                 (P.ksub ? (int)__ldg(P.ksub + i * N + a) << 24 : 0);
         (alpha ? tabA : tabB)[sl] = e;
     }
 }

@@ -232,6 +232,7 @@ __device__ __forceinline__ void issue_elem(const Problem &P, const ColLists &L, 
         const unsigned sa = fdiv(idx, P.mg_nsb);
         const unsigned sb = idx - sa * (unsigned)(P.nb * P.vb);
         const SingleEnt ea = tabA[sa], eb = tabB[sb];
+        if (!k_conserved(P, (ea.info >> 24) & 0xff, (eb.info >> 24) & 0xff)) return;   // zero: momentum
         x.ka = ea.key;
         x.kb = eb.key;
         h = ea.h ^ eb.h;

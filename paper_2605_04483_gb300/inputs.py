@@ -132,8 +132,19 @@ def hubbard_k_integrals(shape: Sequence[int], t: float, U: float) -> Tuple[np.nd
     off = hk - np.diag(np.diag(hk))
     if np.max(np.abs(off)) > 1e-12 or np.max(np.abs(hk.imag)) > 1e-12:
         raise AssertionError("the hopping is not diagonal in the plane waves")
-    # rounded to 12 decimals so that equal levels (the degenerate shells) are exactly equal
-    h = np.diag(np.round(np.diag(hk).real, 12) + 0.0)
+    # eps_k in closed form (-2t cos k_d per direction of extent >= 3, -t cos k_d for extent 2, the single
+    # bond), equal to the transform above; rounded to 12 decimals so that equal levels (the degenerate
+    # shells) are exactly equal
+    eps = np.zeros(L)
+    for d, Ld in enumerate(shape):
+        k = 2.0 * np.pi * n[:, d] / Ld
+        if Ld >= 3:
+            eps += -2.0 * t * np.cos(k)
+        elif Ld == 2:
+            eps += -t * np.cos(k)
+    if np.max(np.abs(eps - np.diag(hk).real)) > 1e-12:
+        raise AssertionError("closed-form band differs from the transformed hopping")
+    h = np.diag(np.round(eps, 12) + 0.0)
     dk = (-n[:, None, None, None, :] + n[None, :, None, None, :] - n[None, None, :, None, :]
           + n[None, None, None, :, :]) % np.array(shape)
     g = np.where(np.all(dk == 0, axis=-1), U / L, 0.0)
