@@ -1391,8 +1391,9 @@ CDFCI_API int cdfci_restore(cdfci_handle c, const cdfci_checkpoint_header *hdr, 
     if (c->block) {
         long long nc = 0;
         for (uint8_t f : hf) nc += f & 1;
-        if (nc > c->mb.cap_cand)
-            return fail(CDFCI_ERR_ARG, "%lld candidates exceed this handle's candidate list (%lld)", nc, c->mb.cap_cand);
+        // a checkpoint written after a long start vector may list more candidates than one iteration makes
+        rc = grow_candidates(c, nc + c->mb.m + 64);
+        if (rc) return rc;
     }
     CK(cudaStreamSynchronize(c->stream));
     DevTemp tmp;
