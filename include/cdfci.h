@@ -41,7 +41,7 @@ extern "C" {
 #define CDFCI_ERR_TABLE_FULL    -3   /* stored determinants exceed max_load * capacity, or probe limit hit */
 #define CDFCI_ERR_TIMEOUT       -4   /* a bounded device wait gave up */
 #define CDFCI_ERR_CUDA          -5   /* a CUDA runtime call failed */
-#define CDFCI_ERR_UNIMPLEMENTED -6   /* entry point not available in this build */
+#define CDFCI_ERR_UNIMPLEMENTED -6   /* entry point not available for this kind of handle */
 #define CDFCI_ERR_NOMEM         -7   /* host or device allocation failed */
 #define CDFCI_ERR_CAPACITY      -8   /* caller's output buffer too small (required size returned) */
 #define CDFCI_ERR_NOT_NEGATIVE  -9   /* reduced problem has no negative eigenvalue (needs E0 < 0) */
