@@ -187,6 +187,16 @@ int cdfci_get_column(cdfci_handle h, const uint64_t *key, uint64_t *keys_out, do
                      int64_t cap, int64_t *n_out);
 
 /*
+ * get_entry and get_diagonal of Sec. "The Hamiltonian Class": one element
+ * H_{row, col} of Eq. (entry) (0.0 beyond a double excitation) and the
+ * diagonal H_{key, key}.  Keys are {A, B} (host or device, 2 words each) with
+ * the handle's N and electron counts (else CDFCI_ERR_ARG); *value is a host
+ * pointer.  H is symmetric, so the order of the two keys does not matter.
+ */
+int cdfci_get_entry(cdfci_handle h, const uint64_t *row_key, const uint64_t *col_key, double *value);
+int cdfci_get_diagonal(cdfci_handle h, const uint64_t *key, double *value);
+
+/*
  * All stored determinants with their true (unscaled) c and b values, in
  * table order.  keys (2 words per entry), c, b hold up to cap entries (c or b
  * may be NULL); *n_out = number stored.  CDFCI_ERR_CAPACITY if cap is too small.

@@ -116,6 +116,8 @@ def lib():
         L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
         L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.cdfci_time_kernels.argtypes = [vp, i64, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.cdfci_get_entry.argtypes = [vp, u64p, u64p, ctypes.POINTER(ctypes.c_double)]
+        L.cdfci_get_diagonal.argtypes = [vp, u64p, ctypes.POINTER(ctypes.c_double)]
         L.cdfci_create_hubbard_k.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(cdfci_params),
                                              ctypes.POINTER(vp)]
@@ -181,6 +183,22 @@ def cdfci_create_hubbard_k(shape, t: float, U: float, n_alpha: int, n_beta: int,
     _check(lib().cdfci_create_hubbard_k(dims.ctypes.data, len(dims), float(t), float(U), int(n_alpha), int(n_beta),
                                         ctypes.byref(p), ctypes.byref(handle)))
     return handle.value
+
+
+def cdfci_get_entry(handle: int, row_key, col_key) -> float:
+    """H_{row, col} (Eq. entry), the get_entry of the Hamiltonian interface."""
+    r = np.ascontiguousarray(np.asarray(row_key, dtype=np.uint64).reshape(2))
+    c = np.ascontiguousarray(np.asarray(col_key, dtype=np.uint64).reshape(2))
+    v = ctypes.c_double()
+    _check(lib().cdfci_get_entry(handle, r.ctypes.data, c.ctypes.data, ctypes.byref(v)))
+    return v.value
+
+
+def cdfci_get_diagonal(handle: int, key) -> float:
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64).reshape(2))
+    v = ctypes.c_double()
+    _check(lib().cdfci_get_diagonal(handle, k.ctypes.data, ctypes.byref(v)))
+    return v.value
 
 
 def cdfci_step(handle: int, n_iter: int) -> dict:
@@ -421,6 +439,12 @@ class Solver:
 
     def energy(self, mode: int = 0) -> float:
         return cdfci_energy(self.handle, mode)
+
+    def entry(self, row_key, col_key) -> float:
+        return cdfci_get_entry(self.handle, row_key, col_key)
+
+    def diagonal(self, key) -> float:
+        return cdfci_get_diagonal(self.handle, key)
 
     def column(self, key):
         return cdfci_get_column(self.handle, key)

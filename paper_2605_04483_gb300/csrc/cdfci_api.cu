@@ -854,6 +854,36 @@ CDFCI_API int cdfci_get_column(cdfci_handle c, const uint64_t *key, uint64_t *ke
     return CDFCI_OK;
 }
 
+CDFCI_API int cdfci_get_entry(cdfci_handle c, const uint64_t *row_key, const uint64_t *col_key, double *value) {
+    if (!c || !row_key || !col_key || !value) return fail(CDFCI_ERR_ARG, "NULL argument");
+    uint64_t k[4];
+    for (int t = 0; t < 2; ++t) {
+        const uint64_t *src = t == 0 ? row_key : col_key;
+        if (is_device_ptr(src)) {
+            CK(cudaMemcpy(k + 2 * t, src, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        } else {
+            k[2 * t] = src[0];
+            k[2 * t + 1] = src[1];
+        }
+    }
+    const unsigned long long full = c->N >= 64 ? ~0ull : ((1ull << c->N) - 1ull);
+    for (int t = 0; t < 2; ++t)
+        if ((k[2 * t] & ~full) || (k[2 * t + 1] & ~full) || __builtin_popcountll(k[2 * t]) != c->na ||
+            __builtin_popcountll(k[2 * t + 1]) != c->nb)
+            return fail(CDFCI_ERR_ARG, "key does not match N, n_alpha, n_beta");
+    DevTemp tmp;
+    double *d = tmp.put(std::vector<double>(1, 0.0), c->stream);
+    if (!d) return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+    CK(launch_entry(c->P, k[0], k[1], k[2], k[3], d, c->stream));
+    CK(cudaMemcpyAsync(value, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CDFCI_OK;
+}
+
+CDFCI_API int cdfci_get_diagonal(cdfci_handle c, const uint64_t *key, double *value) {
+    return cdfci_get_entry(c, key, key, value);
+}
+
 CDFCI_API int cdfci_optorb(const double *h, const double *g, int M, int N, int n_alpha, int n_beta, double *U,
                            const cdfci_optorb_params *p, double *energies) {
     if (!h || !g || !U || !p || !energies) return fail(CDFCI_ERR_ARG, "NULL argument");

@@ -1626,6 +1626,32 @@ cudaError_t mc_configure() {
     return cudaSuccess;
 }
 
+// One matrix element H_{D'D} (Eq. entry; the get_entry / get_diagonal of Sec. "The Hamiltonian Class"):
+// the diagonal by diag_warp, any other pair by hij_pair (zero beyond a double excitation).  One warp.
+__global__ void k_entry(Problem P, unsigned long long A1, unsigned long long B1, unsigned long long A2,
+                        unsigned long long B2, double *out) {
+    __shared__ ColLists L;
+    const int lane = threadIdx.x & 31;
+    if (A1 == A2 && B1 == B2) {
+        for (int t = lane; t < P.N; t += 32) {
+            int ra = __popcll(A2 & low_mask(t)), rb = __popcll(B2 & low_mask(t));
+            if ((A2 >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
+            if ((B2 >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
+        }
+        __syncwarp();
+        const double d = diag_warp(P, L);
+        if (lane == 0) *out = d;
+    } else if (lane == 0) {
+        *out = hij_pair(P, A1, B1, A2, B2);
+    }
+}
+
+cudaError_t launch_entry(const Problem &P, unsigned long long A1, unsigned long long B1, unsigned long long A2,
+                         unsigned long long B2, double *out, cudaStream_t s) {
+    k_entry<<<1, 32, 0, s>>>(P, A1, B1, A2, B2, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
                             double eta, int first, cudaStream_t s) {
     k_mc_start<<<1, 64, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.w, b.thr, b.eta, A, B, eta, first);

@@ -87,6 +87,8 @@ int mc_max_m();
 int mc_scatter_grid(const Problem &P);
 long long mc_gath_entries(int m, int grid);
 cudaError_t mc_configure();
+cudaError_t launch_entry(const Problem &P, unsigned long long A1, unsigned long long B1, unsigned long long A2,
+                         unsigned long long B2, double *out, cudaStream_t s);
 cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
                             double eta, int first, cudaStream_t s);
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
