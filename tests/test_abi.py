@@ -100,3 +100,25 @@ def test_defaults_and_errors_without_gpu(built):
     with pytest.raises(built.CdfciError) as e:
         built.cdfci_create(h, g, 4, 2, 1, bad_ref)
     assert e.value.code == -1
+
+
+def test_new_entry_points_check_arguments_without_gpu(built):
+    """integral_symmetry, the k-space lattice's shape and parameters, and NULL handles are
+    rejected with CDFCI_ERR_ARG before any device work."""
+    import numpy as np
+    h = np.zeros((4, 4))
+    g = np.zeros((4, 4, 4, 4))
+    with pytest.raises(built.CdfciError) as e:
+        built.cdfci_create(h, g, 4, 2, 1, built.cdfci_default_params(integral_symmetry=3))
+    assert e.value.code == -1
+    assert built.cdfci_default_params().integral_symmetry == 8
+    for shape, t, U in [([], 1.0, 4.0), ([0, 4], 1.0, 4.0), ([9, 8], 1.0, 4.0), ([2] * 9, 1.0, 4.0),
+                        ([4, 4], float("inf"), 4.0), ([4, 4], 1.0, float("nan"))]:
+        with pytest.raises(built.CdfciError) as e:
+            built.cdfci_create_hubbard_k(shape, t, U, 2, 2)
+        assert e.value.code == -1, (shape, t, U)
+    L = built.lib()
+    assert L.cdfci_get_entry(None, None, None, None) == -1
+    assert L.cdfci_get_diagonal(None, None, None) == -1
+    assert L.cdfci_time_kernels(None, 1, None, 0, None) == -1
+    assert L.cdfci_set_initial_degenerate(None, 0.0, 0, None, None) == -1
