@@ -246,6 +246,17 @@ int cdfci_time_kernels(cdfci_handle h, int64_t n_iter, double *ms, int32_t cap, 
 int cdfci_set_initial_degenerate(cdfci_handle h, double tol, int64_t cap, int64_t *n_det, double *E_sub);
 
 /*
+ * The degenerate set alone (host only, no handle, no device work): the
+ * determinants of lowest one-body energy for the levels eps[0..N) (host),
+ * built and ordered as cdfci_set_initial_degenerate builds S.  keys (host, 2
+ * words per determinant, {A, B}) receives them when not NULL (room for cap);
+ * *n_det = |S|.  CDFCI_ERR_CAPACITY if |S| > cap (cap <= 0: 1024),
+ * CDFCI_ERR_ARG for N, electron counts or levels out of range.
+ */
+int cdfci_degenerate_set(const double *eps, int N, int n_alpha, int n_beta, double tol, int64_t cap,
+                         uint64_t *keys, int64_t *n_det);
+
+/*
  * All stored determinants with their rows C_{D,:} and B_{D,:} = (HC)_{D,:}
  * (num_states values each, row-major), in table order; for other handles the
  * same as cdfci_export (one value each).  CDFCI_ERR_CAPACITY if cap is too small

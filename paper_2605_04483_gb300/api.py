@@ -117,6 +117,8 @@ def lib():
         L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.cdfci_time_kernels.argtypes = [vp, i64, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.cdfci_get_entry.argtypes = [vp, u64p, u64p, ctypes.POINTER(ctypes.c_double)]
+        L.cdfci_degenerate_set.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, i64, u64p,
+                                           ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_get_diagonal.argtypes = [vp, u64p, ctypes.POINTER(ctypes.c_double)]
         L.cdfci_create_hubbard_k.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(cdfci_params),
@@ -183,6 +185,17 @@ def cdfci_create_hubbard_k(shape, t: float, U: float, n_alpha: int, n_beta: int,
     _check(lib().cdfci_create_hubbard_k(dims.ctypes.data, len(dims), float(t), float(U), int(n_alpha), int(n_beta),
                                         ctypes.byref(p), ctypes.byref(handle)))
     return handle.value
+
+
+def cdfci_degenerate_set(eps, n_alpha: int, n_beta: int, tol: float = 0.0, cap: int = 0) -> np.ndarray:
+    """The determinants of lowest one-body energy (host only): (n, 2) keys {A, B} in the library's order."""
+    e = np.ascontiguousarray(eps, dtype=np.float64).reshape(-1)
+    n = ctypes.c_int64(0)
+    cap = int(cap) if cap > 0 else 1024
+    keys = np.zeros((cap, 2), dtype=np.uint64)
+    _check(lib().cdfci_degenerate_set(e.ctypes.data, len(e), int(n_alpha), int(n_beta), float(tol), cap,
+                                      keys.ctypes.data, ctypes.byref(n)))
+    return keys[:n.value].copy()
 
 
 def cdfci_get_entry(handle: int, row_key, col_key) -> float:

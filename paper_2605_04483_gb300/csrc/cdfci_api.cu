@@ -1071,6 +1071,25 @@ std::vector<uint64_t> lowest_strings(const std::vector<double> &eps, int ne, dou
     return out;
 }
 
+// The degenerate set S = alpha choices x beta choices, ordered by the 128-bit key; *n_det = |S|
+// (cap + 1 when a spin's choices alone exceed cap).
+int degenerate_configurations(const std::vector<double> &eps, int na, int nb, double tol, int64_t cap,
+                              std::vector<std::pair<uint64_t, uint64_t>> &S, int64_t *n_det) {
+    bool overA = false, overB = false;
+    const std::vector<uint64_t> sa = lowest_strings(eps, na, tol, cap, overA), sb = lowest_strings(eps, nb, tol, cap, overB);
+    const double total = (double)sa.size() * (double)sb.size();
+    if (overA || overB || total > (double)cap) {
+        *n_det = (overA || overB) ? cap + 1 : (int64_t)total;
+        return fail(CDFCI_ERR_CAPACITY, "the degenerate set exceeds cap = %lld", (long long)cap);
+    }
+    S.clear();
+    for (uint64_t b : sb)
+        for (uint64_t a : sa) S.push_back({b, a});
+    std::sort(S.begin(), S.end());
+    *n_det = (int64_t)S.size();
+    return CDFCI_OK;
+}
+
 // Lowest eigenpair of the symmetric n x n matrix A (row-major, destroyed) by
 // cyclic Jacobi rotations: each rotation zeroes A_pq with tan = t, t the
 // smaller root of t^2 + 2 theta t - 1 = 0, theta = (A_qq - A_pp) / (2 A_pq).
@@ -1128,6 +1147,28 @@ void jacobi_lowest(int n, std::vector<double> &A, double &lam, std::vector<doubl
 
 extern "C" {
 
+CDFCI_API int cdfci_degenerate_set(const double *eps, int N, int n_alpha, int n_beta, double tol, int64_t cap,
+                                   uint64_t *keys, int64_t *n_det) {
+    if (!eps || !n_det) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (N < 1 || N > kMaxN) return fail(CDFCI_ERR_ARG, "N = %d outside [1, %d]", N, kMaxN);
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N)
+        return fail(CDFCI_ERR_ARG, "electron counts (%d, %d) invalid for N = %d", n_alpha, n_beta, N);
+    if (!(tol > 0.0)) tol = 1e-10;
+    if (cap <= 0) cap = 1024;
+    std::vector<double> e(eps, eps + N);
+    for (double x : e)
+        if (!std::isfinite(x)) return fail(CDFCI_ERR_ARG, "a one-body level is not finite");
+    std::vector<std::pair<uint64_t, uint64_t>> S;
+    const int rc = degenerate_configurations(e, n_alpha, n_beta, tol, cap, S, n_det);
+    if (rc) return rc;
+    if (keys)
+        for (size_t i = 0; i < S.size(); ++i) {
+            keys[2 * i] = S[i].second;
+            keys[2 * i + 1] = S[i].first;
+        }
+    return CDFCI_OK;
+}
+
 CDFCI_API int cdfci_set_initial_degenerate(cdfci_handle c, double tol, int64_t cap, int64_t *n_det, double *E_sub) {
     if (!c || !n_det) return fail(CDFCI_ERR_ARG, "NULL argument");
     if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "start vectors are for one state (num_states = 1)");
@@ -1138,19 +1179,10 @@ CDFCI_API int cdfci_set_initial_degenerate(cdfci_handle c, double tol, int64_t c
     CK(cudaMemcpy(hd.data(), c->d_h, hd.size() * sizeof(double), cudaMemcpyDeviceToHost));
     std::vector<double> eps(N);
     for (int p = 0; p < N; ++p) eps[p] = hd[(size_t)p * N + p];
-    bool overA = false, overB = false;
-    const std::vector<uint64_t> sa = lowest_strings(eps, c->na, tol, cap, overA), sb = lowest_strings(eps, c->nb, tol, cap, overB);
-    const double total = (double)sa.size() * (double)sb.size();
-    if (overA || overB || total > (double)cap) {
-        *n_det = (overA || overB) ? cap + 1 : (int64_t)total;
-        return fail(CDFCI_ERR_CAPACITY, "the degenerate set exceeds cap = %lld", (long long)cap);
-    }
     std::vector<std::pair<uint64_t, uint64_t>> S;                // (B, A): the 128-bit key order
-    for (uint64_t b : sb)
-        for (uint64_t a : sa) S.push_back({b, a});
-    std::sort(S.begin(), S.end());
+    int rc = degenerate_configurations(eps, c->na, c->nb, tol, cap, S, n_det);
+    if (rc) return rc;
     const int n = (int)S.size();
-    *n_det = n;
     std::map<std::pair<uint64_t, uint64_t>, int> index;
     for (int i = 0; i < n; ++i) index[S[i]] = i;
     // H_SS from the columns: column i holds H_{D', D_i}
