@@ -250,8 +250,9 @@ int cdfci_set_initial_degenerate(cdfci_handle h, double tol, int64_t cap, int64_
  * determinants of lowest one-body energy for the levels eps[0..N) (host),
  * built and ordered as cdfci_set_initial_degenerate builds S.  keys (host, 2
  * words per determinant, {A, B}) receives them when not NULL (room for cap);
- * *n_det = |S|.  CDFCI_ERR_CAPACITY if |S| > cap (cap <= 0: 1024),
- * CDFCI_ERR_ARG for N, electron counts or levels out of range.
+ * *n_det = |S|.  CDFCI_ERR_CAPACITY if |S| > cap (with keys NULL, cap <= 0
+ * means 1024), CDFCI_ERR_ARG for N, electron counts or levels out of range,
+ * or for keys given with cap <= 0.
  */
 int cdfci_degenerate_set(const double *eps, int N, int n_alpha, int n_beta, double tol, int64_t cap,
                          uint64_t *keys, int64_t *n_det);
@@ -451,23 +452,34 @@ int cdfci_get_stats(cdfci_handle h, cdfci_stats *stats);
  * or a framework that forbids allocation on its hot path).  The paper has no
  * counterpart: it is the cdfci_get_column operation without a handle.
  *
- * h (N*N) and g (N^4, exactly 8-fold symmetric for bit-for-bit agreement with
- * cdfci_get_column, which canonicalises its copy) must be device memory, as
- * must keys_out (2 words per entry) and vals_out when cap > 0; key ({A, B})
- * may be host or device memory; *n_out (host) receives the column length.
+ * h (N*N) and g (N^4) must be device memory, as must keys_out (2 words per
+ * entry) and vals_out when cap > 0; key ({A, B}) may be host or device memory;
+ * *n_out (host) receives the column length.  h and g are used exactly as
+ * given: h must be symmetric and g exactly 8-fold symmetric for bit-for-bit
+ * agreement with cdfci_get_column (whose handle symmetrises h and
+ * canonicalises g at creation), and neither is checked for symmetry or for
+ * NaN/Inf entries.
  * Work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
- * stream) and the call returns after it finished.
+ * stream) and the call waits for it: it reads the key and the column length
+ * back to the host.  On a stream that is being captured it therefore returns
+ * CDFCI_ERR_ARG before touching the stream, so the caller's capture stays
+ * valid.
  * Scratch: a fixed array of about 80 KB inside the library image (counter,
  * J/K tables, pair tables), held by every GPU that loads the library until
  * the process exits.  Limit: N <= 63 orbitals; larger N is rejected with
  * CDFCI_ERR_ARG.  The first call on a device looks up the array's device
- * address; make that first call before any stream capture.  All calls on a
- * device share the array: calls that overlap on the GPU (other streams,
- * other host threads) race and must be serialised by the caller.
+ * address and keeps it for that device; make that first call before any
+ * stream capture.  The kept address belongs to the device context of that
+ * first call: after cudaDeviceReset on that device it is stale, so the
+ * function must not be called again in that process.  All calls on a device
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Every call clears the
+ * counter and rewrites the tables it reads, so nothing of an earlier call's
+ * contents reaches its result.
  * Errors: CDFCI_ERR_ARG (sizes, host memory where device memory is needed,
- * a key with the wrong electron counts), CDFCI_ERR_CAPACITY (*n_out holds the
- * required size; the buffers then hold an unspecified part of the column),
- * CDFCI_ERR_CUDA.
+ * a key with the wrong electron counts, a capturing stream),
+ * CDFCI_ERR_CAPACITY (*n_out holds the required size; the buffers then hold
+ * an unspecified part of the column), CDFCI_ERR_CUDA.
  */
 int cdfci_column_noalloc(const double *h, const double *g, int N, int n_alpha, int n_beta, const uint64_t *key,
                          uint64_t *keys_out, double *vals_out, int64_t cap, int64_t *n_out, void *cuda_stream);

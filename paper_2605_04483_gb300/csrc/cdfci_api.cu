@@ -1154,6 +1154,7 @@ CDFCI_API int cdfci_degenerate_set(const double *eps, int N, int n_alpha, int n_
     if (n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N)
         return fail(CDFCI_ERR_ARG, "electron counts (%d, %d) invalid for N = %d", n_alpha, n_beta, N);
     if (!(tol > 0.0)) tol = 1e-10;
+    if (keys && cap <= 0) return fail(CDFCI_ERR_ARG, "cap must be > 0 when keys is given");
     if (cap <= 0) cap = 1024;
     std::vector<double> e(eps, eps + N);
     for (double x : e)

@@ -46,17 +46,21 @@ __device__ double hij_pair(const Problem &P, unsigned long long A1, unsigned lon
     const double *g = P.g;
     if (la + lb == 2) {                                  // single
         const bool alpha = la == 2;
-        const unsigned long long X2 = alpha ? A2 : B2, X1 = alpha ? A1 : B1, Y2 = alpha ? B2 : A2;
+        const unsigned long long X2 = alpha ? A2 : B2, X1 = alpha ? A1 : B1;
         const int i = __ffsll((long long)(X2 & (alpha ? dA : dB))) - 1;
         const int a = __ffsll((long long)(X1 & (alpha ? dA : dB))) - 1;
+        // h_ia, then the occupied spin-orbitals of the column determinant in
+        // spin-orbital order (alpha, then beta), one running sum (element_value's order)
         double v = __ldg(P.h + i * N + a);
-        for (unsigned long long m = X2; m; m &= m - 1) {
+        for (unsigned long long m = A2; m; m &= m - 1) {
             const int k = __ffsll((long long)m) - 1;
-            v += gi(g, N, i, a, k, k) - gi(g, N, i, k, k, a);
+            const double t = gi(g, N, i, a, k, k);
+            v += alpha ? t - gi(g, N, i, k, k, a) : t;
         }
-        for (unsigned long long m = Y2; m; m &= m - 1) {
+        for (unsigned long long m = B2; m; m &= m - 1) {
             const int k = __ffsll((long long)m) - 1;
-            v += gi(g, N, i, a, k, k);
+            const double t = gi(g, N, i, a, k, k);
+            v += alpha ? t : t - gi(g, N, i, k, k, a);
         }
         return apply_parity(v, X2 & between_mask(i, a));
     }

@@ -442,9 +442,13 @@ __device__ __forceinline__ void decode_element(const Problem &P, const ColLists 
     ob = B ^ (1ull << j) ^ (1ull << b);
 }
 
-// Value part (Eq. entry): singles h_ia + sum_{k in occ same spin} [(ia|kk) - (ik|ka)]
-// + sum_{k in occ other spin} (ia|kk); same-spin doubles (ia|jb) - (ib|ja);
-// opposite-spin doubles (ia|jb); all times the sign.
+// Value part (Eq. entry): singles h_ia + sum over the occupied spin-orbitals k
+// of the column determinant, taken in spin-orbital order (alpha ascending, then
+// beta ascending), of (ia|kk) - (ik|ka) for k of the single's spin and (ia|kk)
+// for the other spin, one running sum in exactly that order (so the value does
+// not depend on the kernel or on which of the two determinants is the column);
+// same-spin doubles (ia|jb) - (ib|ja); opposite-spin doubles (ia|jb); all times
+// the sign.
 __device__ __forceinline__ double element_value(const Problem &P, const ColLists &L, const ElemIdx &x) {
     const int N = P.N;
     const double *g = P.g;
@@ -452,29 +456,17 @@ __device__ __forceinline__ double element_value(const Problem &P, const ColLists
     if (x.kind <= 1) {
         const bool alpha = x.kind == 0;
         const int i = x.i, a = x.a;
-        const unsigned char *os = alpha ? L.occA : L.occB;
-        const unsigned char *oo = alpha ? L.occB : L.occA;
-        const int ns = alpha ? P.na : P.nb, no = alpha ? P.nb : P.na;
-        // sum in a fixed order: four interleaved partial sums (k mod 4), combined pairwise
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k0 = 0; k0 < ns; k0 += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = k0 + u;
-                if (k < ns) {
-                    const int kk = os[k];
-                    s4[u] += gi(g, N, i, a, kk, kk) - gi(g, N, i, kk, kk, a);
-                }
-            }
+        v = __ldg(P.h + i * N + a);
+        for (int k = 0; k < P.na; ++k) {
+            const int kk = L.occA[k];
+            const double t = gi(g, N, i, a, kk, kk);
+            v += alpha ? t - gi(g, N, i, kk, kk, a) : t;
         }
-        for (int k0 = 0; k0 < no; k0 += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = k0 + u;
-                if (k < no) s4[u] += gi(g, N, i, a, oo[k], oo[k]);
-            }
+        for (int k = 0; k < P.nb; ++k) {
+            const int kk = L.occB[k];
+            const double t = gi(g, N, i, a, kk, kk);
+            v += alpha ? t : t - gi(g, N, i, kk, kk, a);
         }
-        v = __ldg(P.h + i * N + a) + ((s4[0] + s4[1]) + (s4[2] + s4[3]));
     } else if (x.kind <= 3) {
         v = gi(g, N, x.i, x.a, x.j, x.b) - gi(g, N, x.i, x.b, x.j, x.a);
     } else {

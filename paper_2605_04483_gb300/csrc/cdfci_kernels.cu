@@ -178,9 +178,11 @@ __device__ __forceinline__ double diag_pairs_warp(const Problem &P, const ColLis
 
 // Address of entry idx = ls * (nocc + 1) + kk of the CTA's term table: single
 // ls (block ls / 32 of this CTA's share, lane ls % 32); kk < nocc: the term of
-// occupied orbital kk (same spin first, then the other spin); kk = nocc: h_ia.
-// The single's orbitals come from the lists, so the loads do not wait for the
-// singles tables.  Past the last single a valid dummy address (h_00).
+// occupied spin-orbital kk in spin-orbital order (the n_alpha alpha orbitals,
+// then the n_beta beta ones; W3 for the single's own spin, V3 for the other);
+// kk = nocc: h_ia.  The single's orbitals come from the lists, so the loads do
+// not wait for the singles tables.  Past the last single a valid dummy address
+// (h_00).
 __device__ __forceinline__ const double *single_term_ptr(const Problem &P, const ColLists &L, int rank, int G,
                                                          int nocc, long long nsing, int idx) {
     const int ls = idx / (nocc + 1), kk = idx - ls * (nocc + 1);
@@ -194,28 +196,17 @@ __device__ __forceinline__ const double *single_term_ptr(const Problem &P, const
     const int i = alpha ? L.occA[o] : L.occB[o];
     const int a = alpha ? L.virA[w] : L.virB[w];
     if (kk == nocc) return P.h + i * P.N + a;
-    const int ns = alpha ? P.na : P.nb;
-    const bool same = kk < ns;
-    const int k = same ? (alpha ? L.occA[kk] : L.occB[kk]) : (alpha ? L.occB[kk - ns] : L.occA[kk - ns]);
-    return (same ? P.W3 : P.V3) + ((size_t)(i * P.N + a) * P.N + k);
+    const bool k_alpha = kk < P.na;
+    const int k = k_alpha ? L.occA[kk] : L.occB[kk - P.na];
+    return (k_alpha == alpha ? P.W3 : P.V3) + ((size_t)(i * P.N + a) * P.N + k);
 }
 
-// A single's value from its row of terms, summed in the order of
-// element_value (four partial sums by k mod 4, same spin then other spin).
-__device__ __forceinline__ double single_sum(const double *row, int ns, int no, unsigned long long sgn) {
-    const double h_ia = row[ns + no];
-    double s4[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int k0 = 0; k0 < ns; k0 += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (k0 + u < ns) s4[u] += row[k0 + u];
-    }
-    for (int k0 = 0; k0 < no; k0 += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (k0 + u < no) s4[u] += row[ns + k0 + u];
-    }
-    return apply_parity(h_ia + ((s4[0] + s4[1]) + (s4[2] + s4[3])), sgn);
+// A single's value from its row of terms: h_ia, then the nocc terms in the
+// row's order, one running sum (the order of element_value).
+__device__ __forceinline__ double single_sum(const double *row, int nocc, unsigned long long sgn) {
+    double v = row[nocc];
+    for (int k = 0; k < nocc; ++k) v += row[k];
+    return apply_parity(v, sgn);
 }
 
 // Decode element e (singles and opposite-spin doubles from the tables) and
@@ -670,9 +661,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 for (int k = 0; k < kE; ++k)
                     if (ts[k]) {
                         const int ls = ((warp - 1) + Wp * k) * 32 + lane;
-                        const bool alpha = el[k].ix.kind == 0;
-                        el[k].H = single_sum(sTerm + ls * (nocc + 1), alpha ? P.na : P.nb, alpha ? P.nb : P.na,
-                                             el[k].ix.sgn);
+                        el[k].H = single_sum(sTerm + ls * (nocc + 1), nocc, el[k].ix.sgn);
                     }
             }
         }

@@ -116,6 +116,17 @@ extern "C" __attribute__((visibility("default"))) int cdfci_column_noalloc(
     double *vals_out, int64_t cap, int64_t *n_out, void *cuda_stream) {
     if (!h || !g || !key || !n_out || (cap > 0 && (!keys_out || !vals_out)))
         return nfail(CDFCI_ERR_ARG, "cdfci_column_noalloc: NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the call waits on the stream (key and count read back), which a capturing
+    // stream does not allow: refuse before anything is queued on it
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return nfail(CDFCI_ERR_ARG, "cdfci_column_noalloc: stream state unavailable (%s)", cudaGetErrorString(ce));
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+        return nfail(CDFCI_ERR_ARG, "cdfci_column_noalloc: the stream is being captured; this call waits on it");
     if (N < 1 || N > kNoallocMaxN)
         return nfail(CDFCI_ERR_ARG, "cdfci_column_noalloc: N = %d exceeds the scratch limit of %d orbitals", N,
                      kNoallocMaxN);
@@ -125,7 +136,6 @@ extern "C" __attribute__((visibility("default"))) int cdfci_column_noalloc(
     if (cap < 0) return nfail(CDFCI_ERR_ARG, "cdfci_column_noalloc: cap < 0");
     if (!on_device(h) || !on_device(g) || (cap > 0 && (!on_device(keys_out) || !on_device(vals_out))))
         return nfail(CDFCI_ERR_ARG, "cdfci_column_noalloc: h, g and the outputs must be device memory");
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     uint64_t k[2];
     if (cudaMemcpyAsync(k, key, sizeof(k), cudaMemcpyDefault, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return nfail(CDFCI_ERR_CUDA, "cdfci_column_noalloc: reading the key failed");

@@ -122,3 +122,31 @@ def test_new_entry_points_check_arguments_without_gpu(built):
     assert L.cdfci_get_diagonal(None, None, None) == -1
     assert L.cdfci_time_kernels(None, 1, None, 0, None) == -1
     assert L.cdfci_set_initial_degenerate(None, 0.0, 0, None, None) == -1
+
+
+def test_degenerate_set_requires_a_capacity_with_a_buffer(built):
+    """With a keys buffer, cap <= 0 is an argument error (no default capacity that could overrun a
+    smaller buffer); without one, cap <= 0 only asks for the count."""
+    import ctypes
+    import numpy as np
+    L = built.lib()
+    eps = np.array([-2.0, 0.0, 0.0, 0.0, 0.0, 2.0])        # 1 + 4 degenerate levels + 1
+    n = ctypes.c_int64(-1)
+    keys = np.zeros((2, 2), dtype=np.uint64)
+    assert L.cdfci_degenerate_set(eps.ctypes.data, 6, 2, 2, 0.0, 0, keys.ctypes.data, ctypes.byref(n)) == -1
+    assert (keys == 0).all()
+    assert L.cdfci_degenerate_set(eps.ctypes.data, 6, 2, 2, 0.0, 0, None, ctypes.byref(n)) == 0
+    assert n.value == 16                                     # 4 choices per spin
+
+
+def test_noalloc_source_allocates_nothing():
+    """The allocation-free entry point's translation unit calls no allocating CUDA routine."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2605_04483_gb300", "csrc", "cdfci_noalloc.cu")).read()
+    code = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", src), flags=re.S)
+    for call in ("cudaMalloc", "cudaMallocAsync", "cudaMallocManaged", "cudaMallocHost", "cudaHostAlloc",
+                 "cudaFree", "cuMemAlloc", "malloc(", "new "):
+        assert call not in code, call
+    assert "static __device__ __align__(256)" in code and "cudaGetSymbolAddress" in code

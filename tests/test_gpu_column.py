@@ -1,5 +1,5 @@
 """GPU column enumeration (get_column) against the oracle: the key set (excitations,
-hence determinants) bit-exact, signs exact, values within the FP64 bound."""
+hence determinants) bit-exact, signs exact, values within 1e-12 relative of the oracle's."""
 import math
 
 import numpy as np
@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_2605_04483_gb300 import inputs
-from gpu_util import colmap, element_tol, require_gpu
+from gpu_util import ElementCheck, colmap, order_tol, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -19,6 +19,7 @@ def _gpu():
 
 def check_columns(w, dets, literal=False):
     from paper_2605_04483_gb300 import api
+    chk = ElementCheck(f"get_column N={w.N} {w.n_alpha}+{w.n_beta}")
     va, vb = w.N - w.n_alpha, w.N - w.n_beta
     nh = 1 + w.n_alpha * va + w.n_beta * vb + math.comb(w.n_alpha, 2) * math.comb(va, 2) + \
         math.comb(w.n_beta, 2) * math.comb(vb, 2) + w.n_alpha * va * w.n_beta * vb
@@ -28,15 +29,22 @@ def check_columns(w, dets, literal=False):
     try:
         for d in dets:
             k1, v1 = s.column(d)
-            k2, v2 = (oracle.column_literal if literal else oracle.column_sc)(w.N, w.h, w.g, d)
-            m1, m2 = colmap(k1, v1), colmap(k2, v2)
+            m1 = colmap(k1, v1)
             assert len(m1) == len(k1), "duplicate determinant in a GPU column"
+            m2 = colmap(*oracle.column_sc(w.N, w.h, w.g, d))
             assert set(m1) == set(m2), f"key sets differ for det {d}: {len(set(m1) ^ set(m2))} keys"
             for k, v in m2.items():
-                assert abs(m1[k] - v) <= element_tol(w, v), (k, m1[k], v)
+                chk(w, m1[k], v, k)
                 assert np.sign(m1[k]) == np.sign(v)
+            if literal:                  # the definition itself: keys and signs exact, values to the order bound
+                m3 = colmap(*oracle.column_literal(w.N, w.h, w.g, d))
+                assert set(m1) == set(m3)
+                for k, v in m3.items():
+                    assert abs(m1[k] - v) <= order_tol(w, v), (k, m1[k], v)
+                    assert np.sign(m1[k]) == np.sign(v)
     finally:
         s.close()
+    chk.report()
 
 
 def test_column_config1_hubbard_chain():

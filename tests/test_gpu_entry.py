@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2605_04483_gb300 import inputs
-from gpu_util import colmap, element_tol, require_gpu
+from gpu_util import ElementCheck, colmap, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +27,7 @@ def test_entry_and_diagonal_match_the_oracle(kind):
     else:
         w, sym = inputs.hubbard_k((2, 3), 3, 2, U=2.0), 4
     s = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, log2_capacity=12, integral_symmetry=sym)
+    chk = ElementCheck(f"get_entry/get_diagonal {kind}")
     try:
         dets = oracle.fci_dets(w.N, w.n_alpha, w.n_beta)
         rng = np.random.default_rng(4)
@@ -34,11 +35,11 @@ def test_entry_and_diagonal_match_the_oracle(kind):
             ko, vo = oracle.column_sc(w.N, w.h, w.g, d)
             col = colmap(ko, vo)
             dv = col.get((int(d[0]), int(d[1])), 0.0)
-            assert abs(s.diagonal(d) - dv) <= element_tol(w, dv)
+            chk(w, s.diagonal(d), dv, "diagonal")
             for k in list(col)[:: max(1, len(col) // 10)]:
                 kk = np.array(k, dtype=np.uint64)
-                assert abs(s.entry(kk, d) - col[k]) <= element_tol(w, col[k])
-                assert abs(s.entry(d, kk) - col[k]) <= element_tol(w, col[k])
+                chk(w, s.entry(kk, d), col[k], k)
+                chk(w, s.entry(d, kk), col[k], k)
         ref = dets[0]
         far = [x for x in dets if bin(int(x[0]) ^ int(ref[0])).count("1") + bin(int(x[1]) ^ int(ref[1])).count("1") > 4]
         assert far and s.entry(ref, far[0]) == 0.0
@@ -47,3 +48,4 @@ def test_entry_and_diagonal_match_the_oracle(kind):
         assert e.value.code == -1
     finally:
         s.close()
+    chk.report()
