@@ -41,52 +41,56 @@ ALGO_BYTES_PER_ELEMENT = 40      # 16 B key compare + 8 B c read + 8 B b read + 
 WORKLOAD = dict(name="abinitio_N24_6a6b_seed2", N=24, n_alpha=6, n_beta=6, seed=2, tau=1e-5, log2_capacity=27, m=1)
 KERNEL_SOURCES = ["paper_2605_04483_gb300/csrc/cdfci_kernels.cu", "paper_2605_04483_gb300/csrc/cdfci_internal.cuh"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_cd_loop_grid_abinitio_N24.txt")
+SCATTER_SOURCES = ["paper_2605_04483_gb300/csrc/cdfci_block.cu", "paper_2605_04483_gb300/csrc/cdfci_internal.cuh"]
+SCATTER_PROFILE = os.path.join(ROOT, "profiles", "k_mc_scatter_abinitio_N24_m128.txt")
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """dram bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+def profiled_traffic(path, sources, key):
+    """A DRAM figure from a committed ncu summary, if it was taken on the current kernel sources."""
     try:
         vals = {}
-        for line in open(PROFILE_SUMMARY):
+        for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("kernel_source_hash") != kernel_hash():
+        if vals.get("kernel_source_hash") != kernel_hash(sources):
             return None
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (OSError, KeyError, ValueError):
         return None
 
 
-def random_sector_peak(torch, seconds: float = 0.5) -> float:
-    """GB/s of DRAM sectors moved by scattered 8-byte reads (each read costs one
-    32-byte sector) over a 4 GiB buffer: the ceiling of random hash-slot traffic,
-    measured with torch's gather kernel beside the copy peak."""
-    x = torch.empty(1 << 29, dtype=torch.float64, device="cuda")
-    x.fill_(1.0)
-    idx = torch.randint(0, 1 << 29, (1 << 24,), device="cuda")
-    for _ in range(3):
-        y = x[idx]
-    torch.cuda.synchronize()
+def slot_probe(torch, api, log2_slots: int = 27, n_ops: int = 1 << 26, reps: int = 5) -> dict:
+    """The hash scatter's access pattern at its ceiling (cdfci_probe_slots, a hand-written kernel of the
+    library): independent random 32-byte slots of a 2^27-slot (4 GiB > L2) table, each a 16-byte key load,
+    a 16-byte {c, b} load and an FP64 add to b, several in flight per lane.  Reported per operation as the
+    scatter's 40 algorithmic bytes and as the 64 bytes of DRAM sectors it moves (read + write-back)."""
+    table = torch.zeros((1 << log2_slots) * 4, dtype=torch.float64, device="cuda")
+    st = torch.cuda.Stream()
+    for r in range(2):
+        api.cdfci_probe_slots(table, log2_slots, n_ops, seed=r + 1, stream=st.cuda_stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 10
-    e0.record()
-    for _ in range(reps):
-        y = x[idx]
-    e1.record()
+    e0.record(st)
+    for r in range(reps):
+        api.cdfci_probe_slots(table, log2_slots, n_ops, seed=100 + r, stream=st.cuda_stream)
+    e1.record(st)
     e1.synchronize()
     dt = e0.elapsed_time(e1) * 1e-3 / reps
-    del x, idx, y
+    del table
     torch.cuda.empty_cache()
-    return (1 << 24) * 32 / dt / 1e9
+    ops = n_ops / dt
+    peak, _ = measured_peaks()
+    return {"ops_per_s": ops, "gbs_40B": ops * ALGO_BYTES_PER_ELEMENT / 1e9,
+            "frac_40B": ops * ALGO_BYTES_PER_ELEMENT / 1e9 / peak, "sector_gbs_64B": ops * 64 / 1e9,
+            "frac_64B": ops * 64 / 1e9 / peak, "ops": n_ops, "table_gib": (1 << log2_slots) * 32 / 2 ** 30}
 
 
 def measured_peaks():
@@ -194,6 +198,28 @@ def hubbard_k_leg(api, inputs) -> dict:
     return out
 
 
+def host_info() -> dict:
+    """The host the CPU numbers were taken on: online cores and CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": os.uname().machine}
+
+
 def cpu_baseline(seconds: float) -> dict:
     """The CPU oracle's serial CDFCI on the same workload, one host core, bounded sample."""
     import oracle
@@ -210,9 +236,13 @@ def cpu_baseline(seconds: float) -> dict:
     dt = time.perf_counter() - t0
     el = o.info()["elements"] - e0
     o.close()
-    return {"value": el / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+    return {"value": el / dt, "unit": "elements/s", "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": f"{it} CDFCI iterations of the same workload after 20 warm-up iterations "
                       f"({dt:.1f} s, serial C oracle, 1 thread)"}
+
+
+def workload_name(log2_capacity: int) -> str:
+    return WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=1, 2^{log2_capacity}-slot table"
 
 
 def run_reference_arm(args) -> None:
@@ -237,9 +267,9 @@ def run_reference_arm(args) -> None:
             "unit": "elements/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=1",
-                       "iters_per_step": iters, "note": "CPU oracle (serial C), bounded sample per step"},
-            "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "config": {"workload": workload_name(args.log2_capacity),
+                       "iters_per_step": iters, "note": "CPU oracle (serial C, its own hash map), bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": f"{args.steps} steps x {iters} iterations after {args.warmup} warm-up steps"},
             "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -413,6 +443,32 @@ def time_to_e_batched_vs_plain(api, inputs) -> list:
     return out
 
 
+def batched_summary(line: dict, probe: dict) -> dict:
+    """The m = 128 scatter's roofline and the batched-vs-plain figures in a few scalars."""
+    out = {}
+    mc = line.get("mcdfci", {})
+    sr = mc.get("scatter_roofline")
+    if sr:
+        out["mcdfci_scatter"] = {
+            "workload": f"config 2 (N=24, 6+6, tau=1e-5), m=128, iterations {mc['after_warmup_iterations'] + mc['iterations']}.."
+                        f"{mc['after_warmup_iterations'] + mc['iterations'] + sr['iterations_timed']}",
+            "elements_per_iteration": round(sr["elements_per_iteration"]),
+            "scatter_us": mc["us_per_kernel"]["scatter"], "iteration_us": round(mc["us_per_iteration"], 2),
+            "achieved": round(sr["achieved"], 1), "frac": round(sr["frac"], 4),
+            "frac_of_slot_probe": round(sr["achieved"] / probe["gbs_40B"], 4),
+            "dram_bytes_per_element": profiled_traffic(SCATTER_PROFILE, SCATTER_SOURCES, "dram_bytes_per_element"),
+            "kernel_source_hash": kernel_hash(SCATTER_SOURCES)}
+    b = line.get("batch_96")
+    if b:
+        out["batch_96"] = {k: b.get(k) for k in ("value", "m", "problems", "ms_per_batch_step", "scatter_frac")
+                           if b.get(k) is not None}
+    tt = line.get("time_to_E_batched_vs_plain")
+    if tt:
+        out["time_to_E_s"] = [[x["workload"].split(" ")[0], x["plain_m1"].get("seconds"),
+                               x["batched"].get("seconds"), x["batched"].get("m")] for x in tt]
+    return out
+
+
 def aggregate_ranks(ms: float, elements: float, dist=None, device: str = "cpu"):
     """Replicas: the slowest rank's time and all ranks' elements (weak scaling,
     no data-path collective; this reduction only reports)."""
@@ -536,10 +592,13 @@ def main():
     avg_launch_s = ms * 1e-3 / loop_launches
     el_per_launch = elements / loop_launches
     achieved = el_per_launch * ALGO_BYTES_PER_ELEMENT / avg_launch_s / 1e9
-    traffic = profiled_traffic()
-    rs_peak = random_sector_peak(torch)
+    # DRAM bytes per iteration from the committed small-case capture (same column length per
+    # iteration, so a launch's traffic grows in proportion to its iterations), times this launch's
+    per_it = profiled_traffic(PROFILE_SUMMARY, KERNEL_SOURCES, "dram_bytes_per_iteration")
+    traffic = None if per_it is None else per_it * ips
+    probe = slot_probe(torch, api)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "random_sector_peak_gbs": rs_peak, "frac_of_random_sector_peak": achieved / rs_peak,
+                "slot_probe": {k: probe[k] for k in ("gbs_40B", "frac_40B", "sector_gbs_64B")},
                 "traffic": traffic, "kernel": loop_kernel_name(st, ips),
                 "algorithmic_bytes_per_launch": el_per_launch * ALGO_BYTES_PER_ELEMENT,
                 "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
@@ -548,7 +607,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=1, 2^{args.log2_capacity}-slot table",
+            "config": {"workload": workload_name(args.log2_capacity),
                        "iters_per_step": ips, "column_length": 16471,
                        "l2": "inputs larger than L2 (4 GiB hash table), no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -558,21 +617,25 @@ def main():
 
     if not args.no_extras:
         # ---- end to end through the C-ABI from pinned host buffers ----------------------
-        # each step: create from host h, g (H2D copy, table set-up, initial column), ips
-        # iterations, the stats (energy) read back to the host; elements counted as above
-        nrep = 3
-        e_el = 0
+        # the job as a user runs it: create from host h, g (H2D copy, table set-up, initial column),
+        # then the same W + K steps of ips iterations as the device-timed run, the stats (energy) read
+        # back to the host after every step; it covers iterations 0 .. (W + K) ips, the device-timed
+        # window and the W warm-up steps before it
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(nrep):
-            s2 = api.Solver(h_host, g_host, w.N, w.n_alpha, w.n_beta, **params)
+        s2 = api.Solver(h_host, g_host, w.N, w.n_alpha, w.n_beta, **params)
+        for _ in range(args.warmup + args.steps):
             st2 = s2.step(ips)
-            e_el += st2["elements"]
-            s2.close()
         e_dt = time.perf_counter() - t0
+        e_el = st2["elements"]
+        s2.close()
+        nst = args.warmup + args.steps
         line["e2e"] = {"value": e_el / e_dt, "unit": "elements/s",
-                       "h2d_bytes_per_step": int(h_host.numel() * 8 + g_host.numel() * 8),
+                       "h2d_bytes_per_step": int((h_host.numel() * 8 + g_host.numel() * 8) / nst),
                        "d2h_bytes_per_step": int(__import__("ctypes").sizeof(api.cdfci_stats)),
-                       "note": f"{nrep} steps of create(host h, g) + {ips} iterations + stats read; wall clock"}
+                       "iterations": [0, nst * ips],
+                       "note": f"create(host h, g) once ({int(h_host.numel() * 8 + g_host.numel() * 8)} B H2D) "
+                               f"+ {nst} steps of {ips} iterations with a stats read each; wall clock"}
         # ---- time to E within 1e-6 Ha on the 8-site chain (stored exact energy) ------------
         wc = inputs.config1()
         E_ref = load_reference_energy("config1_hubbard_chain8_obc_U4")
@@ -594,7 +657,7 @@ def main():
         line["time_to_E_batched_vs_plain"] = time_to_e_batched_vs_plain(api, inputs)
         # ---- batched coordinate updates (mCDFCI, Algorithm 2) on the same workload ------------
         line["mcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, m=128, 2^27-slot table",
-                              **timed_block_run(api, w, 128, WORKLOAD["tau"], 27, 200, 200, kernel_iters=100))
+                              **timed_block_run(api, w, 128, WORKLOAD["tau"], 27, 1000, 500, kernel_iters=200))
         # ---- excited states (xCDFCI, Algorithm 3), K + 1 = 4, same workload -------------------
         line["xcdfci"] = dict(workload=WORKLOAD["name"] + f", tau={WORKLOAD['tau']}, K+1=4 states, 2^26-slot table",
                               **timed_xcd_run(api, w, 4, WORKLOAD["tau"], 26, 500, 2000))
@@ -615,6 +678,8 @@ def main():
                                 **sweep[best], by_cluster_ctas={gb: v["value"] for gb, v in sweep.items()})
         # ---- adjoint: RDMs and energy derivatives ----------------------------------------------
         line["adjoint"] = adjoint_c5(api, inputs, 128, 300)
+        # ---- compact copies of the batched paths' figures inside the roofline object ------------
+        roofline.update(batched_summary(line, probe))
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line))

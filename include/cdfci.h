@@ -227,6 +227,25 @@ int cdfci_energies(cdfci_handle h, double *E, int32_t cap, int32_t *n_out);
 int cdfci_time_kernels(cdfci_handle h, int64_t n_iter, double *ms, int32_t cap, int32_t *n_kernels);
 
 /*
+ * Measurement only; the paper has no counterpart.  The memory system's rate
+ * for the hash scatter's access pattern (Sec. "Parallelization Support": the
+ * update is bound by irregular hash-table accesses): n_ops operations, each
+ * on a pseudo-random slot (SplitMix64 of seed + op) of a table of
+ * 2^log2_slots 32-byte slots {A, B, c, b}: one 32-byte load of the slot and
+ * an FP64 add to b whose result is not read (the scatter's lookup of an
+ * existing key).
+ * Operations are independent, so every lane keeps several in flight: the rate
+ * bounds any lookup sequence of random slots from above.  table (device, 32-byte
+ * aligned, 2^log2_slots * 32 bytes, caller-owned) must be larger than L2 for
+ * the rate to be DRAM's; its b fields are changed, nothing else is written.
+ * The launch is queued on cuda_stream (a cudaStream_t, NULL = legacy default)
+ * and the call returns at once; time it with events on that stream.
+ * Errors: CDFCI_ERR_ARG (NULL or misaligned table, log2_slots outside
+ * [10, 34], n_ops < 0), CDFCI_ERR_CUDA.
+ */
+int cdfci_probe_slots(void *table, int log2_slots, int64_t n_ops, uint64_t seed, void *cuda_stream);
+
+/*
  * Degenerate-subspace start (the k-space Hubbard example of the paper's
  * numerical section: when the lowest one-body configurations are degenerate,
  * H restricted to all of them is diagonalised and its lowest eigenvector is
@@ -483,6 +502,31 @@ int cdfci_get_stats(cdfci_handle h, cdfci_stats *stats);
  */
 int cdfci_column_noalloc(const double *h, const double *g, int N, int n_alpha, int n_beta, const uint64_t *key,
                          uint64_t *keys_out, double *vals_out, int64_t cap, int64_t *n_out, void *cuda_stream);
+
+/*
+ * FCIDUMP ingestion (Sec. "Example Usage": the molecular Hamiltonian is read
+ * from an FCIDUMP file, "fcidump_path", with a "threshold" below which
+ * integral values are neglected).  Host code only; no device work.
+ *
+ * cdfci_fcidump_header reads the namelist header "&FCI NORB=.., NELEC=..,
+ * MS2=.., ... &END" (or "/" as the end): *norb = N, *nelec, *ms2 = 2 S_z
+ * (0 when absent), so n_alpha = (nelec + ms2) / 2, n_beta = (nelec - ms2) / 2.
+ *
+ * cdfci_fcidump_read fills h (N*N, row-major, host) and g (N^4, (pq|rs)
+ * row-major, host) from the integral lines "value i j k l" (1-based): i j k l
+ * all > 0 set (ij|kl) and its 8 symmetric images; k = l = 0 sets h_ij and h_ji;
+ * i = j = k = l = 0 gives the core energy (*e_core, host, may be NULL; a
+ * constant that the solver's energies do not include); i > 0, j = k = l = 0
+ * lines (orbital energies) are skipped.  Entries absent from the file are 0.
+ * A value with |value| < threshold is stored as 0 (threshold = 0 keeps all;
+ * the core energy is never truncated).  Fortran exponents (1.0D-03) are
+ * accepted.  norb must equal the header's NORB.  The caller owns h and g.
+ * Errors: CDFCI_ERR_ARG (unreadable file, malformed header or line, an index
+ * outside [0, N], N outside [1, 63], inconsistent NELEC/MS2, norb mismatch),
+ * CDFCI_ERR_NONFINITE (a NaN or infinite value).
+ */
+int cdfci_fcidump_header(const char *path, int *norb, int *nelec, int *ms2);
+int cdfci_fcidump_read(const char *path, double threshold, int norb, double *h, double *g, double *e_core);
 
 /* Frees everything the handle owns (safe on NULL). */
 void cdfci_destroy(cdfci_handle h);

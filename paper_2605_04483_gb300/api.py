@@ -116,6 +116,11 @@ def lib():
         L.cdfci_set_initial.argtypes = [vp, u64p, dp, i64]
         L.cdfci_energies.argtypes = [vp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.cdfci_time_kernels.argtypes = [vp, i64, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.cdfci_probe_slots.argtypes = [ctypes.c_void_p, ctypes.c_int, i64, ctypes.c_uint64, ctypes.c_void_p]
+        L.cdfci_fcidump_header.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]
+        L.cdfci_fcidump_read.argtypes = [ctypes.c_char_p, ctypes.c_double, ctypes.c_int, dp, dp,
+                                         ctypes.POINTER(ctypes.c_double)]
         L.cdfci_get_entry.argtypes = [vp, u64p, u64p, ctypes.POINTER(ctypes.c_double)]
         L.cdfci_degenerate_set.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, i64, u64p,
                                            ctypes.POINTER(ctypes.c_int64)]
@@ -283,6 +288,30 @@ def cdfci_set_initial_degenerate(handle: int, tol: float = 0.0, cap: int = 0) ->
 
 MC_KERNELS = ["gkeys", "hist_level1", "hist_tail", "collect", "ties", "sortsel", "prepare", "eigen", "scatter",
               "finalize"]
+
+
+def cdfci_fcidump_header(path: str) -> Tuple[int, int, int]:
+    """(NORB, NELEC, MS2) of an FCIDUMP file's header."""
+    n, ne, m2 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().cdfci_fcidump_header(os.fsencode(path), ctypes.byref(n), ctypes.byref(ne), ctypes.byref(m2)))
+    return n.value, ne.value, m2.value
+
+
+def cdfci_fcidump_read(path: str, threshold: float = 0.0) -> dict:
+    """An FCIDUMP file as {h, g, N, n_alpha, n_beta, e_core} (values below `threshold` in magnitude
+    stored as 0)."""
+    N, ne, m2 = cdfci_fcidump_header(path)
+    h = np.zeros((N, N))
+    g = np.zeros((N, N, N, N))
+    core = ctypes.c_double()
+    _check(lib().cdfci_fcidump_read(os.fsencode(path), float(threshold), N, h.ctypes.data, g.ctypes.data,
+                                    ctypes.byref(core)))
+    return {"h": h, "g": g, "N": N, "n_alpha": (ne + m2) // 2, "n_beta": (ne - m2) // 2, "e_core": core.value}
+
+
+def cdfci_probe_slots(table, log2_slots: int, n_ops: int, seed: int = 1, stream: int = 0) -> None:
+    """Queue the random-slot probe on `stream` over the caller's device table (measurement only)."""
+    _check(lib().cdfci_probe_slots(_ptr(table), int(log2_slots), int(n_ops), int(seed), stream))
 
 
 def cdfci_time_kernels(handle: int, n_iter: int) -> dict:

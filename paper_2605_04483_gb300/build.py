@@ -10,7 +10,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libcdfci.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["cdfci_kernels.cu", "cdfci_block.cu", "cdfci_rdm.cu", "cdfci_xcd.cu", "cdfci_optorb.cu", "cdfci_api.cu", "cdfci_noalloc.cu"]
+SOURCES = ["cdfci_kernels.cu", "cdfci_block.cu", "cdfci_rdm.cu", "cdfci_xcd.cu", "cdfci_optorb.cu", "cdfci_api.cu", "cdfci_noalloc.cu", "cdfci_probe.cu", "cdfci_fcidump.cu"]
 HEADERS = ["cdfci_internal.cuh", "cdfci_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -95,7 +95,7 @@ struct cdfci_ctx {
     // multicoordinate (m > 1) iteration
     bool block = false;
     McBuffers mb;
-    void *mb_alloc[20] = {};
+    void *mb_alloc[32] = {};
     int mb_nalloc = 0;
     int mchunk = 8;                              // iterations per captured graph
     cudaGraphExec_t mgraph = nullptr;
@@ -221,8 +221,10 @@ int setup_block(cdfci_ctx *c, int m) {
     c->P.cap_cand = cap_cand;
     b.cand_grid = 152 * 4;
     CK(mc_configure());
-    b.scatter_grid = 2 * mc_scatter_grid(P);         // twice the resident blocks: late blocks even out the SMs
+    b.scatter_grid = mc_scatter_grid(P);             // the resident blocks; their warps take items from a counter
     if (b.scatter_grid <= 0) return fail(CDFCI_ERR_CUDA, "occupancy query of the scatter failed");
+    b.geom = mc_geometry(P);
+    const size_t ns = (size_t)b.geom.nsA + (size_t)b.geom.nsB;
     b.st = c->d_st;
     const size_t n1 = (size_t)m + 1;
     b.ldr = (int)(32 * ((n1 + 31) / 32));
@@ -232,7 +234,8 @@ int setup_block(cdfci_ctx *c, int m) {
         mb_alloc(c, &b.HIIc, (size_t)m) || mb_alloc(c, &b.Rh, n1 * (size_t)b.ldr) ||
         mb_alloc(c, &b.Rl, n1 * (size_t)b.ldr) ||
         mb_alloc(c, &b.w, (size_t)m) || mb_alloc(c, &b.thr, (size_t)m) || mb_alloc(c, &b.eta, (size_t)m) ||
-        mb_alloc(c, &b.gathp, (size_t)mc_gath_entries(m, b.scatter_grid)))
+        mb_alloc(c, &b.gathp, (size_t)m * (size_t)b.geom.per_col) || mb_alloc(c, &b.coltab, (size_t)m * ns) ||
+        mb_alloc(c, &b.collists, (size_t)m) || mb_alloc(c, &b.work, 1))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
     // c != 0 filter: one bit per table slot, between 2^16 and 2^25 bits (4 MB: it stays in L2 while the
     // scatter's random slot traffic streams through)

@@ -667,13 +667,37 @@ __global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, co
 
 constexpr int kEigMaxN = 1024;      // m + 1 <= 1024: one thread per row of the reduced problem
 
+// The entries of the column of {A, B} into tab, threads t0, t0 + nt, ...
+__device__ __forceinline__ void mc_build_coltab(const Problem &P, const ColLists &L, unsigned long long A,
+                                                unsigned long long B, ColEnt *tab, int t0, int nt) {
+    const int na_va = P.na * P.va, nb_vb = P.nb * P.vb, N = P.N;
+    for (int s = t0; s < na_va + nb_vb; s += nt) {
+        const bool alpha = s < na_va;
+        const int sl = alpha ? s : s - na_va;
+        const int o = (int)fdiv((unsigned)sl, alpha ? P.mg_va : P.mg_vb);
+        const int w = sl - o * (alpha ? P.va : P.vb);
+        const int i = alpha ? L.occA[o] : L.occB[o];
+        const int a = alpha ? L.virA[w] : L.virB[w];
+        const unsigned long long X = alpha ? A : B;
+        ColEnt e;
+        e.key = X ^ (1ull << i) ^ (1ull << a);
+        e.h = alpha ? hash_alpha(e.key) : hash_beta(e.key);
+        e.goff = alpha ? (i * N + a) * N * N : i * N + a;
+        e.info = (__popcll(X & between_mask(i, a)) & 1) | (i << 8) | (a << 16) |
+                 (P.ksub ? (int)__ldg(P.ksub + i * N + a) << 24 : 0);
+        e.pad0 = 0;
+        e.pad1 = 0;
+        tab[s] = e;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // c_I, b_I, H_II, H_II c_I: one warp per selected row.  H_II goes to rows and
 // columns 1..m of R as float-float pairs (Rh, Rl; leading dimension ldr).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, const McSel *sel, double *cI,
                                                     double *bI, double *Hdiag, double *HIIc, float *Rh, float *Rl,
-                                                    int ldr) {
+                                                    int ldr, ColEnt *coltab, ColLists *collists, int ns) {
     __shared__ ColLists Lw[8];
     // the chosen determinants and their c (true units), staged once per block
     __shared__ unsigned long long s_A[kEigMaxN], s_B[kEigMaxN];
@@ -698,6 +722,9 @@ __global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, cons
             if ((rB >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
         }
         __syncwarp();
+        // the column's single excitations and orbital lists for the scatter
+        mc_build_coltab(P, L, rA, rB, coltab + (size_t)r * ns, lane, 32);
+        reinterpret_cast<uint2 *>(collists + r)[lane] = reinterpret_cast<const uint2 *>(&L)[lane];
         const double hd = diag_warp(P, L);
         double acc = 0.0;
         for (int c = lane; c < m; c += 32) {
@@ -1155,35 +1182,42 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
 
 // ---------------------------------------------------------------------------
 // b += H_{:,I} eta for the m columns (stored units), gather, candidates.
-// The m columns' off-diagonal elements form one index space f = i (nh - 1) +
-// (e - 1) of T = m (nh - 1) elements; block k of the G blocks takes the
-// contiguous range [floor(k T / G), floor((k + 1) T / G)), so every block
-// has the same share (no second wave) and a column spans a few consecutive
-// blocks, each leaving one gather partial for it.
+//
+// Work items of one warp each.  The off-diagonal elements of a column are
+// products of single excitations of its determinant: an opposite-spin double
+// is an alpha single times a beta single, a same-spin double an occupied pair
+// times a virtual pair of one string.  An item gives every lane one factor,
+// kept in registers, and runs the other factor over a short range, one
+// uniform (broadcast) load per step:
+//   AB item: 32 beta singles (one per lane) x kAbChunk alpha singles; the
+//            element is the integral at the sum of the two entries' offsets,
+//            its key the two changed strings, its hash the xor of their hashes;
+//   AA / BB: 32 virtual pairs x kSsChunk occupied pairs of one string;
+//   S item:  32 singles, each summing its terms in the order of Eq. (entry).
+// The column's single-excitation entries and orbital lists are built once per
+// iteration (k_mc_prepare, k_mc_start).  Warps take items of all columns from
+// a global counter; each item leaves one gather partial (sum_j H_ji c_j over
+// its elements), which k_mc_finalize adds per column in item order.  Elements
+// that need the table (|H| at or above the column's threshold, or c_j possibly
+// nonzero by the filter) go to the warp's queue; whenever it holds 32 the warp
+// looks them up together, one per lane.
 // ---------------------------------------------------------------------------
-constexpr int kScatterQ = 96;       // per-warp queue of elements that need a table lookup (31 + 2 x 32)
+constexpr int kScatterQ = 64;       // per-warp queue of elements that need a table lookup (31 + 32)
 constexpr int kWarpCand = 256;      // per-warp buffer of new candidates (flushed above kWarpCand - 32)
-constexpr int kScatterMinRange = 256;
 
-// blocks in use for T elements on a grid of G: every range holds at least kScatterMinRange elements
-__host__ __device__ __forceinline__ long long mc_scatter_blocks(long long T, int G) {
-    const long long g = T / kScatterMinRange;
-    return g < 1 ? 1 : (g < G ? g : G);
-}
-// the block whose range holds element f (ranges as above)
-__device__ __forceinline__ long long mc_block_of(long long f, long long T, long long G) {
-    return ((f + 1) * G + T - 1) / T - 1;
-}
-// gather partials per column: blocks hold at least r = floor(T / G) elements, so a
-// column of Lc elements meets at most floor((Lc - 2) / r) + 2 <= Lc / r + 2 of them
-// (m columns: at most 2 G + 2 m partials, as r >= T / (2 G))
-__host__ __device__ __forceinline__ long long mc_gath_per_col(long long Lc, long long T, long long G) {
-    return Lc / (T / G) + 2;
+// The whole 32-byte slot {A, B, c, b} in one load: one DRAM access for the key
+// and the values (two 16-byte loads of one slot cost two accesses of random
+// slots on this memory system).  L2 only, re-read on every call.
+__device__ __forceinline__ void ld_slot(const Slot *s, unsigned long long &ka, unsigned long long &kb, double &c) {
+    unsigned long long cb, bb;
+    asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(ka), "=l"(kb), "=l"(cb), "=l"(bb)
+                 : "l"(s));
+    c = __longlong_as_double((long long)cb);
 }
 
-// Probe for {a, b}: the key and the value halves of the slot are read by two
-// independent 16-byte loads.  Returns the slot, or -1 (absent, not inserted) /
-// -2 (error, status set).  c: the slot's stored c.
+// Probe for {a, b}.  Returns the slot, or -1 (absent, not inserted) / -2
+// (error, status set).  c: the slot's stored c.
 __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, unsigned long long a,
                                               unsigned long long b, unsigned long long h, bool insert,
                                               bool &inserted, double &c) {
@@ -1191,18 +1225,19 @@ __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, u
     const bool both_nonzero = (P.na > 0) && (P.nb > 0);
     for (int probe = 0; probe < P.max_probe; ++probe) {
         Slot *s = P.table + pos;
-        ulonglong2 k = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
-        const double2 v = __ldcg(reinterpret_cast<const double2 *>(&s->c));
+        unsigned long long ka, kb;
+        double sc;
+        ld_slot(s, ka, kb, sc);
         int spins = 0;
-        while (both_nonzero && ((k.x == 0ull) != (k.y == 0ull))) {     // an insert in flight
+        while (both_nonzero && ((ka == 0ull) != (kb == 0ull))) {     // an insert in flight
             if (++spins > (1 << 20)) { set_status(st, kErrTimeout); return -2; }
-            k = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
+            ld_slot(s, ka, kb, sc);
         }
-        if (k.x == a && (k.y & kKeyMaskB) == b) {
-            c = v.x;
+        if (ka == a && (kb & kKeyMaskB) == b) {
+            c = sc;
             return (long long)pos;
         }
-        if (k.x == 0ull && k.y == 0ull) {
+        if (ka == 0ull && kb == 0ull) {
             if (!insert) return -1;
             unsigned long long oa, ob;
             cas128(&s->a, 0ull, 0ull, a, b, oa, ob);
@@ -1220,39 +1255,6 @@ __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, u
     }
     set_status(st, kErrTableFull);
     return -2;
-}
-
-// One element of the scatter's column (flat index e): its determinant, the hash,
-// H, and whether c_j may be nonzero.  The integral and filter loads are
-// independent, so both are in flight together.
-__device__ __forceinline__ void mc_elem(const Problem &P, const ColLists &L, const SingleEnt *tabA,
-                                        const SingleEnt *tabB, const volatile unsigned long long &A,
-                                        const volatile unsigned long long &B, const volatile unsigned long long &hA,
-                                        const volatile unsigned long long &hB, long long e,
-                                        unsigned long long &oa, unsigned long long &ob, unsigned long long &hk,
-                                        double &H, bool &maybe) {
-    if (e >= P.seg[4]) {                                // opposite-spin double: two single-excitation entries
-        const unsigned idx = (unsigned)(e - P.seg[4]);
-        const unsigned sa = fdiv(idx, P.mg_nsb), sb = idx - sa * (unsigned)(P.nb * P.vb);
-        const SingleEnt ea = tabA[sa], eb = tabB[sb];
-        oa = ea.key;
-        ob = eb.key;
-        hk = ea.h ^ eb.h;
-        if (!k_conserved(P, (ea.info >> 24) & 0xff, (eb.info >> 24) & 0xff)) {   // momentum not conserved
-            H = 0.0;
-            maybe = false;
-            return;
-        }
-        const double gv = __ldg(P.g + ea.goff + eb.goff);
-        maybe = cnz_maybe(P, hk);
-        H = apply_parity(gv, (unsigned long long)((ea.info ^ eb.info) & 1));
-    } else {
-        ElemIdx x;
-        decode_element(P, L, A, B, e, oa, ob, x);
-        hk = (x.kind == 0 || x.kind == 2) ? (hash_alpha(oa) ^ hB) : (hA ^ hash_beta(ob));
-        maybe = cnz_maybe(P, hk);
-        H = element_value(P, L, x);
-    }
 }
 
 // The warp's candidate buffer to the global list (one reservation); entries
@@ -1310,124 +1312,247 @@ __device__ __forceinline__ bool mc_apply(const Problem &P, McState *ms, IterStat
     return __any_sync(0xffffffffu, err);
 }
 
-__global__ void __launch_bounds__(256, 4) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
+// Per-warp scatter context: the column's constants and the lookup queue.
+struct McWarp {
+    const Problem &P;
+    McState *ms;
+    IterState *st;
+    long long *cand;
+    unsigned long long *qa, *qb, *qh;
+    double *qH;
+    long long *wcand;
+    unsigned long long tib;
+    double wi, gather;
+    int qn, nwc, c_el, c_app, c_drop, c_ins;
+    bool err;
+
+    // filter word of hash h (the c != 0 bit is bit (h >> 32) & 31 of it); all ones without a filter
+    __device__ __forceinline__ unsigned cnz_word(unsigned long long h) const {
+        return P.cnz ? __ldg(P.cnz + (((h >> 32) & P.cnz_mask) >> 5)) : 0xffffffffu;
+    }
+    // element (oa, ob) with hash hk and value H, `ok` = this lane holds one; filter word cw
+    __device__ __forceinline__ void push(bool ok, unsigned long long oa, unsigned long long ob, unsigned long long hk,
+                                         double H, unsigned cw) {
+        const int lane = threadIdx.x & 31;
+        bool need = false;
+        if (ok && !is_zero(H)) {
+            ++c_el;
+            // |H| >= thr (non-negative doubles order like their bits) or c_j may be nonzero;
+            // otherwise c_j = 0 and the rule drops it
+            need = ((cw >> (unsigned)((hk >> 32) & 31)) & 1u) || abs_bits(H) >= tib;
+            if (!need) ++c_drop;
+        }
+        const unsigned int nm = __ballot_sync(0xffffffffu, need);
+        if (need) {
+            const int at = qn + __popc(nm & ((1u << lane) - 1u));
+            qa[at] = oa; qb[at] = ob; qh[at] = hk; qH[at] = H;
+        }
+        qn += __popc(nm);
+        if (qn >= 32 && !err) {
+            __syncwarp();
+            qn -= 32;
+            const int at = qn + lane;
+            err = mc_apply(P, ms, st, true, qa[at], qb[at], qh[at], qH[at], tib, wi, gather, c_app, c_drop, c_ins,
+                           wcand, nwc, cand);
+            __syncwarp();
+        }
+    }
+    // the rest of the queue
+    __device__ __forceinline__ void drain() {
+        const int lane = threadIdx.x & 31;
+        if (qn > 0 && !err) {
+            __syncwarp();
+            const bool has = lane < qn;
+            err = mc_apply(P, ms, st, has, has ? qa[lane] : 0ull, has ? qb[lane] : 0ull, has ? qh[lane] : 0ull,
+                           has ? qH[lane] : 0.0, tib, wi, gather, c_app, c_drop, c_ins, wcand, nwc, cand);
+            __syncwarp();
+        }
+        qn = 0;
+    }
+};
+
+constexpr int kAbChunk = 8;         // alpha singles per opposite-spin item
+constexpr int kSsChunk = 8;         // occupied pairs per same-spin item
+constexpr int kAbU = 4;             // opposite-spin elements in flight per lane
+
+// Opposite-spin doubles: lane = beta single sb, alpha singles [sa0, sa1).
+__device__ __forceinline__ void mc_item_ab(McWarp &W, const ColEnt *tA, const ColEnt *tB, int nsB, int sb, int sa0,
+                                           int sa1) {
+    const Problem &P = W.P;
+    const bool lane_ok = sb < nsB;
+    ColEnt eb;
+    if (lane_ok) {
+        eb = tB[sb];
+    } else {
+        eb.key = 0ull; eb.h = 0ull; eb.goff = 0; eb.info = 0;
+    }
+    const int kb = (eb.info >> 24) & 0xff;
+    for (int sa = sa0; sa < sa1; sa += kAbU) {
+        unsigned long long ka[kAbU], hk[kAbU];
+        double H[kAbU];
+        unsigned cw[kAbU];
+        bool ok[kAbU];
+#pragma unroll
+        for (int u = 0; u < kAbU; ++u) {
+            ok[u] = false;
+            H[u] = 0.0;
+            ka[u] = 0ull;
+            hk[u] = 0ull;
+            cw[u] = 0u;
+            if (sa + u < sa1) {
+                const ColEnt ea = tA[sa + u];             // uniform: one broadcast load
+                ka[u] = ea.key;
+                hk[u] = ea.h ^ eb.h;
+                ok[u] = lane_ok && k_conserved(P, (ea.info >> 24) & 0xff, kb);
+                if (ok[u]) {
+                    H[u] = apply_parity(__ldg(P.g + ea.goff + eb.goff), (unsigned long long)((ea.info ^ eb.info) & 1));
+                    cw[u] = W.cnz_word(hk[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kAbU; ++u) W.push(ok[u], ka[u], eb.key, hk[u], H[u], cw[u]);
+        if (W.err) return;
+    }
+}
+
+// Same-spin doubles of one string X (the other string Y with hash hY): lane =
+// virtual pair vp, occupied pairs [op0, op1); the element of Eq. (entry) with
+// i < j occupied, a < b empty: (ia|jb) - (ib|ja) times the sign of i -> a then
+// j -> b.
+__device__ __forceinline__ void mc_item_ss(McWarp &W, bool alpha, unsigned long long X, unsigned long long Y,
+                                           unsigned long long hY, const ColLists &L, int vp, int op0, int op1) {
+    const Problem &P = W.P;
+    const int N = P.N, N2 = N * N;
+    const int cv2 = alpha ? P.cva2 : P.cvb2;
+    const bool lane_ok = vp < cv2;
+    const unsigned char *occ = alpha ? L.occA : L.occB;
+    const unsigned char *vir = alpha ? L.virA : L.virB;
+    int a = 0, b = 0;
+    if (lane_ok) {
+        const unsigned short pv = __ldg((alpha ? P.pair_va : P.pair_vb) + vp);
+        a = vir[pv & 0xff];
+        b = vir[pv >> 8];
+    }
+    const unsigned short *po_t = alpha ? P.pair_oa : P.pair_ob;
+    const int aN2 = a * N2, bN2 = b * N2;
+    for (int op = op0; op < op1; op += 2) {
+        unsigned long long key[2], hk[2];
+        double H[2];
+        unsigned cw[2];
+        bool ok[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            ok[u] = false;
+            key[u] = 0ull;
+            hk[u] = 0ull;
+            H[u] = 0.0;
+            cw[u] = 0u;
+            if (op + u < op1 && lane_ok) {
+                const unsigned short po = __ldg(po_t + op + u);      // uniform
+                const int i = occ[po & 0xff], j = occ[po >> 8];
+                const unsigned long long m1 = X & between_mask(i, a);
+                const unsigned long long X1 = X ^ (1ull << i) ^ (1ull << a);
+                const unsigned long long m2 = X1 & between_mask(j, b);
+                key[u] = X1 ^ (1ull << j) ^ (1ull << b);
+                hk[u] = (alpha ? hash_alpha(key[u]) : hash_beta(key[u])) ^ hY;
+                const int base = i * N * N2 + j * N;
+                H[u] = apply_parity(__ldg(P.g + base + aN2 + b) - __ldg(P.g + base + bN2 + a), m1 ^ m2);
+                cw[u] = W.cnz_word(hk[u]);
+                ok[u] = true;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            W.push(ok[u], alpha ? key[u] : Y, alpha ? Y : key[u], hk[u], H[u], cw[u]);
+        if (W.err) return;
+    }
+}
+
+// Singles: lane = single s of the column (alpha entries first); the value is
+// h_ia plus the terms of the occupied spin-orbitals in spin-orbital order
+// (W3 for the single's spin, V3 for the other), one running sum.
+__device__ __forceinline__ void mc_item_s(McWarp &W, const ColEnt *tA, int nsA, int ns, int s, unsigned long long A,
+                                          unsigned long long B, unsigned long long hA, unsigned long long hB) {
+    const Problem &P = W.P;
+    const int N = P.N;
+    bool ok = false;
+    unsigned long long oa = 0ull, ob = 0ull, hk = 0ull;
+    double H = 0.0;
+    unsigned cw = 0u;
+    if (s < ns) {
+        const ColEnt e = tA[s];
+        const bool alpha = s < nsA;
+        const int i = (e.info >> 8) & 0xff, a = (e.info >> 16) & 0xff;
+        const size_t row = (size_t)(i * N + a) * N;
+        const double *tA_row = (alpha ? P.W3 : P.V3) + row, *tB_row = (alpha ? P.V3 : P.W3) + row;
+        double v = __ldg(P.h + i * N + a);
+        for (unsigned long long m = A; m; m &= m - 1) v += __ldg(tA_row + (__ffsll((long long)m) - 1));
+        for (unsigned long long m = B; m; m &= m - 1) v += __ldg(tB_row + (__ffsll((long long)m) - 1));
+        H = apply_parity(v, (unsigned long long)(e.info & 1));
+        oa = alpha ? e.key : A;
+        ob = alpha ? B : e.key;
+        hk = alpha ? (e.h ^ hB) : (hA ^ e.h);
+        cw = W.cnz_word(hk);
+        ok = true;
+    }
+    W.push(ok, oa, ob, hk, H, cw);
+}
+
+__global__ void __launch_bounds__(256, 3) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
+                                                    const ColEnt *coltab, const ColLists *collists, McGeom Gm,
                                                     const double *w, const double *thr, long long *cand,
-                                                    double *gathp) {
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    SingleEnt *tabA = reinterpret_cast<SingleEnt *>(s_dyn), *tabB = tabA + P.na * P.va;
-    __shared__ ColLists L;
-    __shared__ double swarp[8];
-    __shared__ int s_cnt[4][8];
-    // the current column: determinant, weight, |H| threshold bits, string hashes (read
-    // through volatile loads, which keeps them out of the loop's registers)
-    __shared__ unsigned long long s_colA, s_colB, s_tib, s_hA, s_hB;
-    __shared__ double s_wi;
-    // per-warp queues of elements that need a lookup (key, hash, H) and candidate buffers
+                                                    double *gathp, unsigned int *work) {
     __shared__ unsigned long long q_a[8][kScatterQ], q_b[8][kScatterQ], q_h[8][kScatterQ];
     __shared__ double q_H[8][kScatterQ];
     __shared__ long long w_cand[8][kWarpCand];
+    __shared__ int s_cnt[4][8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
-    const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
-    const long long Lc = nh - 1, T = (long long)m * Lc;
-    const long long G = mc_scatter_blocks(T, gridDim.x);
-    if (T <= 0 || blockIdx.x >= G) return;
-    const long long K = mc_gath_per_col(Lc, T, G);
-    const long long f_beg = (long long)blockIdx.x * T / G, f_end = ((long long)blockIdx.x + 1) * T / G;
-    int c_el = 0, c_app = 0, c_drop = 0, c_ins = 0;
-    int nwc = 0;                                        // warp-uniform: entries in w_cand[warp]
-    bool err = false;                                   // warp-uniform
-    const volatile unsigned long long &vA = s_colA, &vB = s_colB, &vtib = s_tib, &vhA = s_hA, &vhB = s_hB;
-    const volatile double &vwi = s_wi;
-    // one pass per column segment of the block's range
-    for (long long f0 = f_beg; f0 < f_end;) {
-        const int col = (int)(f0 / Lc);
-        const long long f1 = min(f_end, (long long)(col + 1) * Lc);
+    const int total = m * Gm.per_col;
+    const int ns = Gm.nsA + Gm.nsB;
+    McWarp W{P, ms, st, cand, q_a[warp], q_b[warp], q_h[warp], q_H[warp], w_cand[warp], 0ull, 0.0, 0.0,
+             0, 0, 0, 0, 0, 0, false};
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(work, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total || W.err) break;
+        const int col = t / Gm.per_col, k = t - col * Gm.per_col;
         const McSel xs = sel[col];
-        __syncthreads();                                // the previous segment's lists and tables are done
-        if (tid == 0) {
-            s_colA = xs.A;
-            s_colB = xs.B;
-            s_wi = w[col];
-            s_tib = abs_bits(thr[col]);
-            s_hA = hash_alpha(xs.A);
-            s_hB = hash_beta(xs.B);
+        W.wi = w[col];
+        W.tib = abs_bits(thr[col]);
+        W.gather = 0.0;
+        W.qn = 0;
+        const ColEnt *tA = coltab + (size_t)col * ns;
+        if (k < Gm.n_ab) {
+            const int lg = k / Gm.ab_ch, ch = k - lg * Gm.ab_ch;
+            mc_item_ab(W, tA, tA + Gm.nsA, Gm.nsB, 32 * lg + lane, ch * kAbChunk, min(Gm.nsA, (ch + 1) * kAbChunk));
+        } else if (k < Gm.n_ab + Gm.n_aa + Gm.n_bb) {
+            const bool alpha = k < Gm.n_ab + Gm.n_aa;
+            const int kk = k - (alpha ? Gm.n_ab : Gm.n_ab + Gm.n_aa);
+            const int chn = alpha ? Gm.aa_ch : Gm.bb_ch;
+            const int lg = kk / chn, ch = kk - lg * chn;
+            const int co2 = alpha ? P.ca2 : P.cb2;
+            const unsigned long long X = alpha ? xs.A : xs.B, Y = alpha ? xs.B : xs.A;
+            const unsigned long long hY = alpha ? hash_beta(xs.B) : hash_alpha(xs.A);
+            mc_item_ss(W, alpha, X, Y, hY, collists[col], 32 * lg + lane, ch * kSsChunk,
+                       min(co2, (ch + 1) * kSsChunk));
+        } else {
+            const int lg = k - (Gm.n_ab + Gm.n_aa + Gm.n_bb);
+            mc_item_s(W, tA, Gm.nsA, ns, 32 * lg + lane, xs.A, xs.B, hash_alpha(xs.A), hash_beta(xs.B));
         }
-        for (int t = tid; t < P.N; t += 256) {
-            int ra = __popcll(xs.A & low_mask(t)), rb = __popcll(xs.B & low_mask(t));
-            if ((xs.A >> t) & 1ull) L.occA[ra] = (unsigned char)t; else L.virA[t - ra] = (unsigned char)t;
-            if ((xs.B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
-        }
-        __syncthreads();
-        build_singles(P, L, xs.A, xs.B, tabA, tabB, tid, 256);
-        __syncthreads();
-        double gather = 0.0;
-        const long long e_off = 1 - (long long)col * Lc;
-        const unsigned long long tib = vtib;
-        // Phase 1, every lane: the element and the c != 0 filter; elements that need the
-        // table go to the warp's queue.  Phase 2, whenever 32 are queued: the warp looks
-        // them up together, one per lane, so that no lane waits on another's round trips.
-        int qn = 0;                                     // warp-uniform
-        for (long long fb = f0 + warp * 32; fb < f1 && !err; fb += 512) {
-            // two elements per lane: f and f + 256
-            bool need[2] = {false, false};
-            unsigned long long oa[2] = {0ull, 0ull}, ob[2] = {0ull, 0ull}, hk[2] = {0ull, 0ull};
-            double H[2] = {0.0, 0.0};
-            bool maybe[2] = {false, false};
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const long long f = fb + lane + 256 * u;
-                if (f < f1) mc_elem(P, L, tabA, tabB, vA, vB, vhA, vhB, f + e_off, oa[u], ob[u], hk[u], H[u], maybe[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                if (fb + lane + 256 * u < f1 && !is_zero(H[u])) {
-                    ++c_el;
-                    // |H| >= thr (non-negative doubles order like their bits) or c_j may be nonzero;
-                    // otherwise c_j = 0 and the rule drops it
-                    need[u] = maybe[u] || abs_bits(H[u]) >= tib;
-                    if (!need[u]) ++c_drop;
-                }
-                const unsigned int nm = __ballot_sync(0xffffffffu, need[u]);
-                if (need[u]) {
-                    const int at = qn + __popc(nm & ((1u << lane) - 1u));
-                    q_a[warp][at] = oa[u]; q_b[warp][at] = ob[u]; q_h[warp][at] = hk[u]; q_H[warp][at] = H[u];
-                }
-                qn += __popc(nm);
-            }
-            while (qn >= 32 && !err) {
-                __syncwarp();
-                qn -= 32;
-                const int at = qn + lane;
-                err = mc_apply(P, ms, st, true, q_a[warp][at], q_b[warp][at], q_h[warp][at], q_H[warp][at], tib, vwi,
-                               gather, c_app, c_drop, c_ins, w_cand[warp], nwc, cand);
-                __syncwarp();
-            }
-        }
-        if (qn > 0 && !err) {                           // the rest of the queue
-            __syncwarp();
-            const bool has = lane < qn;
-            err = mc_apply(P, ms, st, has, has ? q_a[warp][lane] : 0ull, has ? q_b[warp][lane] : 0ull,
-                           has ? q_h[warp][lane] : 0ull, has ? q_H[warp][lane] : 0.0, tib, vwi, gather, c_app,
-                           c_drop, c_ins, w_cand[warp], nwc, cand);
-            __syncwarp();
-        }
-        // the segment's gather: a fixed tree in each warp, the warps in order
-        for (int o = 16; o > 0; o >>= 1) gather += __shfl_down_sync(0xffffffffu, gather, o);
-        if (lane == 0) swarp[warp] = gather;
-        __syncthreads();
-        if (tid == 0) {
-            double t = swarp[0];
-            for (int q = 1; q < 8; ++q) t += swarp[q];
-            gathp[(size_t)col * K + (blockIdx.x - mc_block_of((long long)col * Lc, T, G))] = t;
-        }
-        f0 = f1;
+        W.drain();
+        // the item's gather: a fixed tree over the warp
+        double gsum = W.gather;
+        for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(0xffffffffu, gsum, o);
+        if (lane == 0) gathp[(size_t)col * Gm.per_col + k] = gsum;
     }
-    mc_flush_cand(P, ms, st, w_cand[warp], nwc, cand);
+    mc_flush_cand(P, ms, st, w_cand[warp], W.nwc, cand);
     // counters: warp sums, then the warps in order
-    const int r0 = __reduce_add_sync(0xffffffffu, c_el), r1 = __reduce_add_sync(0xffffffffu, c_app);
-    const int r2 = __reduce_add_sync(0xffffffffu, c_drop), r3 = __reduce_add_sync(0xffffffffu, c_ins);
+    const int r0 = __reduce_add_sync(0xffffffffu, W.c_el), r1 = __reduce_add_sync(0xffffffffu, W.c_app);
+    const int r2 = __reduce_add_sync(0xffffffffu, W.c_drop), r3 = __reduce_add_sync(0xffffffffu, W.c_ins);
     if (lane == 0) { s_cnt[0][warp] = r0; s_cnt[1][warp] = r1; s_cnt[2][warp] = r2; s_cnt[3][warp] = r3; }
     __syncthreads();
     if (tid < 4) {
@@ -1440,13 +1565,21 @@ __global__ void __launch_bounds__(256, 4) k_mc_scatter(Problem P, McState *ms, I
 // b_I recalculated (Eq. recalculate-b), the chosen coordinates join the
 // candidates, counters and the host snapshot.
 __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel *sel, const double *Hdiag,
-                              const double *gathp, long long *cand, const double *etaout, int grid) {
+                              const double *gathp, long long *cand, const double *etaout, int per_col,
+                              unsigned int *work) {
+    __shared__ double s_gsum[kEigMaxN];
+    if (threadIdx.x == 0) *work = 0u;                   // the next scatter's item counter
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
-    const int lane = threadIdx.x & 31;
-    const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
-    const long long Lc = nh - 1, T = (long long)m * Lc;
-    const long long G = mc_scatter_blocks(T, grid), K = T > 0 ? mc_gath_per_col(Lc, T, G) : 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // each column's gather: its item partials, lane-strided in item order, then a fixed tree
+    for (int i = warp; i < m; i += nwarp) {
+        double t = 0.0;
+        for (int k = lane; k < per_col; k += 32) t += gathp[(size_t)i * per_col + k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) s_gsum[i] = t;
+    }
+    __syncthreads();
     int nd = 0;                                         // this thread's nonzero diagonals
     for (int i0 = 0; i0 < m; i0 += blockDim.x) {        // block-uniform rounds
         const int i = i0 + (int)threadIdx.x;
@@ -1456,14 +1589,8 @@ __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel
             slot = sel[i].slot;
             const double hd = Hdiag[i];
             nd += hd != 0.0 ? 1 : 0;
-            double t = 0.0;
-            if (T > 0) {
-                // the column's blocks in order
-                const long long nb = mc_block_of((long long)(i + 1) * Lc - 1, T, G) - mc_block_of((long long)i * Lc, T, G);
-                for (long long k = 0; k <= nb; ++k) t += gathp[(size_t)i * K + k];
-            }
             Slot *s = P.table + slot;
-            s->bv = fma(hd, s->c, t);
+            s->bv = fma(hd, s->c, s_gsum[i]);
             append = mark_set(P, slot);
         }
         // the chosen coordinates join the candidates: one reservation per warp
@@ -1532,7 +1659,8 @@ __global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel
 // H (double-double), b as stored before the step.  The first entry (first = 1)
 // starts from the reset state: c = e_ref (eta = 1) is the default start of r4.
 __global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, double *Hdiag, double *w, double *thr,
-                           double *etaout, unsigned long long A, unsigned long long B, double eta, int first) {
+                           double *etaout, unsigned long long A, unsigned long long B, double eta, int first,
+                           ColEnt *coltab, ColLists *collists) {
     __shared__ ColLists L;
     __shared__ long long s_slot;
     __shared__ double s_bold;
@@ -1553,6 +1681,9 @@ __global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, do
         if ((B >> t) & 1ull) L.occB[rb] = (unsigned char)t; else L.virB[t - rb] = (unsigned char)t;
     }
     __syncthreads();
+    // the column's single excitations and orbital lists for the scatter (column 0)
+    mc_build_coltab(P, L, A, B, coltab, threadIdx.x, blockDim.x);
+    if (threadIdx.x < 32) reinterpret_cast<uint2 *>(collists)[threadIdx.x] = reinterpret_cast<const uint2 *>(&L)[threadIdx.x];
     if (threadIdx.x < 32) {
         const double hd = diag_warp(P, L);
         if (threadIdx.x == 0) {
@@ -1605,27 +1736,37 @@ size_t mc_eigen_smem(int m) {
 int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
 int mc_max_m() { return kEigMaxN - 1; }
 
-// the scatter's dynamic shared memory: the column's single-excitation tables
-size_t mc_scatter_smem(const Problem &P) { return (size_t)(P.na * P.va + P.nb * P.vb + 1) * sizeof(SingleEnt); }
-// the scatter's grid: the blocks that are resident at once on this device
+// the scatter's grid: the blocks that are resident at once on this device (warps take items from a counter)
 int mc_scatter_grid(const Problem &P) {
+    (void)P;
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_scatter, 256, mc_scatter_smem(P)) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mc_scatter, 256, 0) != cudaSuccess)
         return 0;
     return sms * std::max(per, 1);
 }
-// gather partials for m columns on a grid of `grid` blocks (any m_sel <= m)
-long long mc_gath_entries(int m, int grid) { return 2ll * grid + 2ll * m + 8; }
+// the scatter's work items per column (see k_mc_scatter)
+McGeom mc_geometry(const Problem &P) {
+    McGeom g{};
+    g.nsA = P.na * P.va;
+    g.nsB = P.nb * P.vb;
+    if (!P.doubles_vanish) {
+        g.ab_ch = (g.nsA + kAbChunk - 1) / kAbChunk;
+        g.n_ab = g.nsB > 0 ? ((g.nsB + 31) / 32) * g.ab_ch : 0;
+        g.aa_ch = (P.ca2 + kSsChunk - 1) / kSsChunk;
+        g.n_aa = P.cva2 > 0 ? ((P.cva2 + 31) / 32) * g.aa_ch : 0;
+        g.bb_ch = (P.cb2 + kSsChunk - 1) / kSsChunk;
+        g.n_bb = P.cvb2 > 0 ? ((P.cvb2 + 31) / 32) * g.bb_ch : 0;
+    }
+    g.n_s = (g.nsA + g.nsB + 31) / 32;
+    g.per_col = g.n_ab + g.n_aa + g.n_bb + g.n_s;
+    return g;
+}
 
 cudaError_t mc_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max(mc_eigen_smem(kEigSmemN - 1), mc_eigen_smem(149)));
-    if (e != cudaSuccess) return e;
-    // N <= 64: at most 2 x 32 x 32 single-excitation entries
-    e = cudaFuncSetAttribute(k_mc_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((2 * 32 * 32 + 1) * sizeof(SingleEnt)));
     if (e != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -1658,13 +1799,15 @@ cudaError_t launch_entry(const Problem &P, unsigned long long A1, unsigned long 
 
 cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
                             double eta, int first, cudaStream_t s) {
-    k_mc_start<<<1, 64, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.w, b.thr, b.eta, A, B, eta, first);
+    k_mc_start<<<1, 64, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.w, b.thr, b.eta, A, B, eta, first, b.coltab,
+                                b.collists);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s) {
-    k_mc_scatter<<<b.scatter_grid, 256, mc_scatter_smem(P), s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp);
-    k_mc_finalize<<<1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.scatter_grid);
+    k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.coltab, b.collists, b.geom, b.w, b.thr,
+                                                 b.cand, b.gathp, b.work);
+    k_mc_finalize<<<1, 1024, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.geom.per_col, b.work);
     return cudaGetLastError();
 }
 
@@ -1688,16 +1831,18 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
     mark();
     k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
     mark();
-    k_mc_prepare<<<(b.m + 7) / 8, 256, 0, s>>>(P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr);
+    k_mc_prepare<<<(b.m + 7) / 8, 256, 0, s>>>(P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr,
+                                               b.coltab, b.collists, b.geom.nsA + b.geom.nsB);
     mark();
     k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Rh,
                                                                     b.Rl, b.ldr, eig_tpr(b.m + 1),
                                                                     b.m + 1 <= kEigSmemN ? 1 : 0,
                                                                     b.w, b.thr, b.eta);
     mark();
-    k_mc_scatter<<<b.scatter_grid, 256, mc_scatter_smem(P), s>>>(P, b.ms, b.st, b.sel, b.w, b.thr, b.cand, b.gathp);
+    k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.coltab, b.collists, b.geom, b.w, b.thr,
+                                                 b.cand, b.gathp, b.work);
     mark();
-    k_mc_finalize<<<1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.scatter_grid);
+    k_mc_finalize<<<1, 1024, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.geom.per_col, b.work);
     mark();
     return cudaGetLastError();
 }

@@ -69,6 +69,21 @@ cudaError_t launch_ckpt_restore_m1(const Problem &P, IterState *st, CdRecord *re
                                    const CdRecord &r, const CdPartial &folded, cudaStream_t s);
 
 // Device buffers of the multicoordinate iteration.
+// One column's single excitations in global memory (built once per iteration for the
+// scatter): alpha entries [0, nsA), beta entries [nsA, nsA + nsB).
+struct __align__(16) ColEnt {
+    unsigned long long key, h;     // the changed string and its hash (hash_alpha / hash_beta)
+    int goff;                      // alpha: (i N + a) N^2; beta: j N + b
+    int info;                      // sign | i << 8 | a << 16 | momentum transfer << 24
+    int pad0, pad1;
+};
+// The scatter's work items per column: opposite-spin (ab), same-spin (aa, bb) and singles (s)
+// items; *_ch = chunks of the looped factor per lane group of 32.
+struct McGeom {
+    int nsA, nsB;
+    int n_ab, ab_ch, n_aa, aa_ch, n_bb, bb_ch, n_s;
+    int per_col;
+};
 struct McBuffers {
     McState *ms;
     IterState *st;
@@ -76,7 +91,11 @@ struct McBuffers {
     unsigned long long *gkey;      // their choice keys
     unsigned int *hist;            // 4096-bin radix histogram, then the last-block counter
     McSel *sel, *inbin, *ties;     // chosen set, threshold-digit candidates, exact-tie scratch
-    double *cI, *bI, *Hdiag, *HIIc, *w, *thr, *eta, *gathp;
+    double *cI, *bI, *Hdiag, *HIIc, *w, *thr, *eta, *gathp;   // gathp: m x geom.per_col item partials
+    ColEnt *coltab;                // m columns x (nsA + nsB) single excitations
+    ColLists *collists;            // m columns' orbital lists
+    unsigned int *work;            // the scatter's item counter (reset by k_mc_finalize)
+    McGeom geom;
     float *Rh, *Rl;                // reduced matrix R as float-float pairs, leading dimension ldr
     int ldr;
     int m, cand_grid, scatter_grid;
@@ -85,7 +104,7 @@ struct McBuffers {
 size_t mc_eigen_smem(int m);
 int mc_max_m();
 int mc_scatter_grid(const Problem &P);
-long long mc_gath_entries(int m, int grid);
+McGeom mc_geometry(const Problem &P);
 cudaError_t mc_configure();
 cudaError_t launch_entry(const Problem &P, unsigned long long A1, unsigned long long B1, unsigned long long A2,
                          unsigned long long B2, double *out, cudaStream_t s);

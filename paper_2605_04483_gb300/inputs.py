@@ -281,3 +281,36 @@ def random_determinants(N: int, n_alpha: int, n_beta: int, count: int, seed: int
         out[k, 0] = np.uint64(sum(1 << int(p) for p in a))
         out[k, 1] = np.uint64(sum(1 << int(p) for p in b))
     return out
+
+
+def write_fcidump(path: str, w: Workload, e_core: float = 0.0, fortran: bool = False) -> None:
+    """w's integrals as FCIDUMP text (Knowles-Handy format): the namelist header, one line per
+    unique nonzero (ij|kl) with i >= j, k >= l, (i, j) >= (k, l) (1-based), one per h_ij with
+    i >= j, then the core energy.  Values are written with 17 significant digits, so they read
+    back to the same doubles; `fortran` writes D exponents."""
+    N = w.N
+    ms2 = w.n_alpha - w.n_beta
+
+    def fmt(x: float) -> str:
+        t = f"{x:.16E}"
+        return t.replace("E", "D") if fortran else t
+
+    lines = [f" &FCI NORB={N:3d},NELEC={w.n_alpha + w.n_beta:3d},MS2={ms2:2d},",
+             "  ORBSYM=" + ",".join(["1"] * N) + ",", "  ISYM=1,", " &END"]
+    for i in range(N):
+        for j in range(i + 1):
+            for k in range(N):
+                for l in range(k + 1):
+                    if i * (i + 1) // 2 + j < k * (k + 1) // 2 + l:
+                        continue
+                    v = float(w.g[i, j, k, l])
+                    if v != 0.0:
+                        lines.append(f"{fmt(v)} {i + 1:3d} {j + 1:3d} {k + 1:3d} {l + 1:3d}")
+    for i in range(N):
+        for j in range(i + 1):
+            v = float(w.h[i, j])
+            if v != 0.0:
+                lines.append(f"{fmt(v)} {i + 1:3d} {j + 1:3d}   0   0")
+    lines.append(f"{fmt(e_core)}   0   0   0   0")
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
