@@ -345,25 +345,62 @@ def loop_kernel_name(st: dict, ips: int) -> str:
     return f"k_cd_loop (persistent {st['grid_blocks']}-CTA cluster, {ips} iterations per launch)"
 
 
-def batch_c4(api, inputs, iters: int, grid_blocks: int = 1) -> dict:
-    """The uneven batch (64 ab initio + 32 Hubbard problems) stepped in one launch, one
-    thread-block cluster of grid_blocks CTAs per problem."""
+def c4_tables(w):
+    """Table size and tau of a config-4 instance: the next power of two >= dim / 0.6, capped at 2^24;
+    tau = 0 where the FCI space fits, else 1e-5."""
     import math
+    dim = fci_dim(w.N, w.n_alpha, w.n_beta)
+    need = dim / 0.6
+    lc = max(10, min(24, math.ceil(math.log2(need))))
+    return lc, (0.0 if need <= 2 ** 24 else 1e-5)
+
+
+def column_length(w) -> int:
+    import math
+    va, vb = w.N - w.n_alpha, w.N - w.n_beta
+    return (1 + w.n_alpha * va + w.n_beta * vb + math.comb(w.n_alpha, 2) * math.comb(va, 2) +
+            math.comb(w.n_beta, 2) * math.comb(vb, 2) + w.n_alpha * va * w.n_beta * vb)
+
+
+def c4_block_sizes(api, ws, seconds: float = 0.6) -> tuple:
+    """m for every config-4 instance from cdfci_autotune: the tuner runs on the instances with the
+    shortest, the median and the longest column, and every instance takes the choice of the nearest
+    of them in column length."""
+    order = sorted(range(len(ws)), key=lambda i: column_length(ws[i]))
+    reps = sorted({order[0], order[len(order) // 2], order[-1]})
+    chosen = {}
+    for i in reps:
+        w = ws[i]
+        lc, tau = c4_tables(w)
+        p, _ = api.cdfci_autotune(w.h, w.g, w.N, w.n_alpha, w.n_beta, seconds=seconds, log2_capacity=lc,
+                                  z_threshold=tau, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]))
+        chosen[i] = max(p["num_coordinates"], 4)           # the batch's m > 1 path
+    ms = []
+    for w in ws:
+        L = column_length(w)
+        near = min(reps, key=lambda i: abs(column_length(ws[i]) - L))
+        ms.append(chosen[near])
+    return ms, {column_length(ws[i]): chosen[i] for i in reps}
+
+
+def batch_c4(api, inputs, iters: int, grid_blocks: int = 1, ms=None) -> dict:
+    """The uneven batch (64 ab initio + 32 Hubbard problems) stepped together: with ms = None every
+    problem runs Algorithm 1 (one thread-block cluster of grid_blocks CTAs per problem, one persistent
+    launch); otherwise problem k runs Algorithm 2 with m = ms[k], all problems as branches of one
+    captured graph."""
     ws = inputs.config4_instances()
     solvers = []
     total_bytes = 0
     try:
-        for w in ws:
-            dim = fci_dim(w.N, w.n_alpha, w.n_beta)
-            need = dim / 0.6
-            lc = max(10, min(24, math.ceil(math.log2(need))))
-            tau = 0.0 if need <= 2 ** 24 else 1e-5
+        for k, w in enumerate(ws):
+            lc, tau = c4_tables(w)
             total_bytes += (1 << lc) * 32
+            kw = dict(grid_blocks=grid_blocks) if ms is None else dict(num_coordinates=ms[k])
             solvers.append(api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, log2_capacity=lc, z_threshold=tau,
-                                      grid_blocks=grid_blocks, ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1])))
+                                      ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]), **kw))
         b = api.Batch(solvers)
         try:
-            b.step(20)
+            b.step(20 if ms is None else 16)
             st0 = [s.stats() for s in solvers]
             t0 = time.perf_counter()
             st = b.step(iters)
@@ -371,10 +408,18 @@ def batch_c4(api, inputs, iters: int, grid_blocks: int = 1) -> dict:
         finally:
             b.close()
         el = sum(x["elements"] - y["elements"] for x, y in zip(st, st0))
-        return {"value": el / dt, "unit": "elements/s", "problems": len(ws), "iterations_each": iters,
-                "ms_per_batch_step": dt * 1e3, "gpu_launches_timed": 2, "cluster_ctas_per_problem": grid_blocks,
-                "tables_gib": total_bytes / 2 ** 30,
-                "column_lengths": [min(x["last_column"] for x in st), max(x["last_column"] for x in st)]}
+        peak, _ = measured_peaks()
+        out = {"value": el / dt, "unit": "elements/s", "problems": len(ws), "iterations_each": iters,
+               "ms_per_batch_step": dt * 1e3, "tables_gib": total_bytes / 2 ** 30,
+               "algorithmic_frac": el * ALGO_BYTES_PER_ELEMENT / dt / 1e9 / peak,
+               "column_lengths": [min(x["last_column"] for x in st), max(x["last_column"] for x in st)],
+               "energies": [round(x["energy"], 10) for x in st]}
+        if ms is None:
+            out.update(cluster_ctas_per_problem=grid_blocks, m=1, gpu_launches_timed=2)
+        else:
+            out.update(m=sorted(set(ms)), m_counts={m: ms.count(m) for m in sorted(set(ms))},
+                       graph_launches_timed=iters // 8)
+        return out
     finally:
         for s in solvers:
             s.close()
@@ -460,8 +505,11 @@ def batched_summary(line: dict, probe: dict) -> dict:
             "kernel_source_hash": kernel_hash(SCATTER_SOURCES)}
     b = line.get("batch_96")
     if b:
-        out["batch_96"] = {k: b.get(k) for k in ("value", "m", "problems", "ms_per_batch_step", "scatter_frac")
-                           if b.get(k) is not None}
+        out["batch_96"] = {k: b.get(k) for k in ("value", "m_counts", "problems", "ms_per_batch_step",
+                                                 "algorithmic_frac") if b.get(k) is not None}
+        b1 = line.get("batch_96_m1")
+        if b1:
+            out["batch_96"]["m1_value"] = b1.get("value")
     tt = line.get("time_to_E_batched_vs_plain")
     if tt:
         out["time_to_E_s"] = [[x["workload"].split(" ")[0], x["plain_m1"].get("seconds"),
@@ -671,11 +719,14 @@ def main():
             kleg = {"error": f"{type(e).__name__}: {e}"}
         line["hubbard_k_4x4"] = dict(workload="hubbardk_4x4_pbc_8a8b (momentum basis, dim 1.66e8), m=128, 2^24 slots",
                                      **kleg)
-        # ---- uneven batch of 96 problems in one launch --------------------------------------
-        sweep = {gb: batch_c4(api, inputs, 200, gb) for gb in (1, 2, 4, 8, 16)}
-        best = max(sweep, key=lambda gb: sweep[gb]["value"])
-        line["batch_96"] = dict(workload="64 ab initio (N 12..32, 3..8 electrons per spin) + 32 Hubbard problems, m=1",
-                                **sweep[best], by_cluster_ctas={gb: v["value"] for gb, v in sweep.items()})
+        # ---- uneven batch of 96 problems: Algorithm 2 with autotuned m, one graph; and at m = 1 ----
+        ws4 = inputs.config4_instances()
+        ms, tuned = c4_block_sizes(api, ws4)
+        line["batch_96"] = dict(workload="64 ab initio (N 12..32, 3..8 electrons per spin) + 32 Hubbard problems, "
+                                         "Algorithm 2 per problem (m autotuned), one graph per 8 iterations",
+                                **batch_c4(api, inputs, 200, ms=ms), autotuned_m_by_column_length=tuned)
+        line["batch_96_m1"] = dict(workload="the same 96 problems, m=1, one persistent launch (8-CTA cluster each)",
+                                   **batch_c4(api, inputs, 200, 8))
         # ---- adjoint: RDMs and energy derivatives ----------------------------------------------
         line["adjoint"] = adjoint_c5(api, inputs, 128, 300)
         # ---- compact copies of the batched paths' figures inside the roofline object ------------

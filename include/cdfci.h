@@ -416,16 +416,26 @@ int cdfci_rdm(cdfci_handle h, double *rdm1, double *rdm2);
 int cdfci_gradient(cdfci_handle h, double *dE_dh, double *dE_dg, double *dE_dkappa);
 
 /*
- * Batches: many independent m = 1 solvers (problems of different sizes:
- * molecules, lattices) stepped together.  One persistent launch (replayed from
- * a captured CUDA graph) runs every problem, one thread-block cluster per
- * problem, each cluster executing Algorithm 1 on its own problem with no
- * communication between clusters.  The batch does not own the handles, which
- * must outlive it, have num_coordinates = 1 and the same grid_blocks (CTAs per
- * problem, at most 16: a grid-wide handle is rejected), and are queued on the first handle's stream while batched.  A
- * handle stays usable on its own: cdfci_step continues from the batch's state.
- * stats (n entries, or NULL) receives every problem's report; the return code
- * is the first problem's error, if any.
+ * Batches: many independent solvers (problems of different sizes: molecules,
+ * lattices) stepped together; cdfci_batch_step(n_iter) runs n_iter iterations
+ * of every problem (Algorithm 1 for num_coordinates = 1, Algorithm 2 with its
+ * own m otherwise).
+ *   m = 1 solvers: one persistent launch (replayed from a captured CUDA
+ *   graph) runs them all, one thread-block cluster per problem, with no
+ *   communication between clusters; they need the same grid_blocks (CTAs per
+ *   problem, at most 16: a grid-wide handle is rejected).
+ *   m > 1 solvers: one captured CUDA graph holds graph_chunk iterations of
+ *   every such problem, each problem's iteration kernels (with its own launch
+ *   shapes and block size m) on a branch of its own, forked from the batch's
+ *   stream and joined back, so that the problems run side by side; one graph
+ *   launch advances them all.  z_threshold_search is applied per problem
+ *   between graph launches (the graph is captured again when a tau moves).
+ * Each problem's arithmetic is exactly its solo step's.  The batch does not
+ * own the handles, which must outlive it and not be num_states > 1; while
+ * batched they are queued on the first handle's stream.  A handle stays usable
+ * on its own: cdfci_step continues from the batch's state.  stats (n entries,
+ * in the order of hs, or NULL) receives every problem's report; the return
+ * code is the first error, if any.
  */
 typedef struct cdfci_batch *cdfci_batch_handle;
 int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_handle *out);

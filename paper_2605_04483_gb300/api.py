@@ -537,7 +537,8 @@ class Solver:
 
 
 class Batch:
-    """Many m = 1 solvers stepped in one launch (cdfci_batch_*); does not own them."""
+    """Many solvers stepped together (cdfci_batch_*): the m = 1 ones in one persistent launch, the
+    m > 1 ones as branches of one graph; does not own them."""
 
     def __init__(self, solvers):
         self.solvers = list(solvers)

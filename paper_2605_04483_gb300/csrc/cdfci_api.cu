@@ -1588,14 +1588,23 @@ CDFCI_API int cdfci_gradient(cdfci_handle c, double *dE_dh, double *dE_dg, doubl
 }  // extern "C"
 
 struct cdfci_batch {
-    std::vector<cdfci_ctx *> hs;
+    std::vector<cdfci_ctx *> hs;       // every handle, in the caller's order
+    std::vector<cdfci_ctx *> one;      // m = 1 handles: one persistent launch, a cluster per problem
+    std::vector<int> one_at;           // their positions in hs
+    std::vector<cdfci_ctx *> blk;      // m > 1 handles: one graph branch each
+    std::vector<int> blk_at;
     CdInstance *d_inst = nullptr;
     int cluster = 1;
     size_t smem = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;     // the batch's stream (handle 0's)
     long long chunk = 1 << 16;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;   // the m = 1 group's launch of graph_iters iterations
     long long graph_iters = 0;
+    std::vector<cudaStream_t> br;      // the m > 1 group: a branch stream per handle ...
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t mgraph = nullptr;  // ... and one graph of mchunk iterations of every branch
+    int mchunk = 8;
 };
 
 namespace {
@@ -1604,7 +1613,7 @@ int batch_graph(cdfci_batch *b, long long k) {
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_cd_loop_batch(b->d_inst, (int)b->hs.size(), b->cluster, b->smem, k, b->stream);
+    cudaError_t e = launch_cd_loop_batch(b->d_inst, (int)b->one.size(), b->cluster, b->smem, k, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -1616,6 +1625,42 @@ int batch_graph(cdfci_batch *b, long long k) {
     b->graph_iters = k;
     return CDFCI_OK;
 }
+
+// The m > 1 group: one graph in which every handle's mchunk iterations (its own
+// kernels and launch shapes) form a branch of their own, forked from the batch
+// stream and joined back, so that the problems' iterations run side by side.
+int batch_mgraph(cdfci_batch *b) {
+    if (b->mgraph) { cudaGraphExecDestroy(b->mgraph); b->mgraph = nullptr; }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (size_t i = 0; i < b->blk.size() && e == cudaSuccess; ++i) {
+        cdfci_ctx *c = b->blk[i];
+        e = cudaStreamWaitEvent(b->br[i], b->fork, 0);
+        for (int it = 0; it < b->mchunk && e == cudaSuccess; ++it) e = launch_mc_iteration(c->P, c->mb, b->br[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[i], b->br[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(CDFCI_ERR_CUDA, "capture of the batched multicoordinate iteration failed");
+    }
+    e = cudaGraphInstantiate(&b->mgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return CDFCI_OK;
+}
+
+void batch_free(cdfci_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->mgraph) cudaGraphExecDestroy(b->mgraph);
+    for (cudaStream_t s : b->br) if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    cudaFree(b->d_inst);
+    delete b;
+}
 }  // namespace
 
 extern "C" {
@@ -1624,37 +1669,61 @@ CDFCI_API int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_hand
     if (!out) return fail(CDFCI_ERR_ARG, "NULL argument");
     *out = nullptr;
     if (!hs || n < 1) return fail(CDFCI_ERR_ARG, "empty batch");
+    int first_one = -1;
     for (int k = 0; k < n; ++k) {
         if (!hs[k]) return fail(CDFCI_ERR_ARG, "handle %d is NULL", k);
-        if (hs[k]->block) return fail(CDFCI_ERR_ARG, "handle %d has num_coordinates > 1 (batches take m = 1 solvers)", k);
         if (hs[k]->xcd) return fail(CDFCI_ERR_ARG, "handle %d has num_states > 1 (batches take one-state solvers)", k);
+        for (int q = 0; q < k; ++q)
+            if (hs[q] == hs[k]) return fail(CDFCI_ERR_ARG, "handle %d appears twice", k);
+        if (hs[k]->block) continue;
         if (hs[k]->gridmode)
             return fail(CDFCI_ERR_ARG, "handle %d runs on %d CTAs, more than a cluster (batches take grid_blocks <= 16)",
                         k, hs[k]->grid);
-        if (hs[k]->grid != hs[0]->grid)
-            return fail(CDFCI_ERR_ARG, "handle %d uses %d CTAs per problem, handle 0 uses %d (create all with the same grid_blocks)",
-                        k, hs[k]->grid, hs[0]->grid);
-        for (int q = 0; q < k; ++q)
-            if (hs[q] == hs[k]) return fail(CDFCI_ERR_ARG, "handle %d appears twice", k);
+        if (first_one < 0) first_one = k;
+        if (hs[k]->grid != hs[first_one]->grid)
+            return fail(CDFCI_ERR_ARG, "handle %d uses %d CTAs per problem, handle %d uses %d (create the m = 1 "
+                        "solvers with the same grid_blocks)", k, hs[k]->grid, first_one, hs[first_one]->grid);
     }
     cdfci_batch *b = new (std::nothrow) cdfci_batch;
     if (!b) return fail(CDFCI_ERR_NOMEM, "host allocation failed");
     b->hs.assign(hs, hs + n);
-    b->cluster = hs[0]->grid;
-    b->stream = hs[0]->stream;
-    b->chunk = hs[0]->chunk;
-    std::vector<CdInstance> inst(n);
     for (int k = 0; k < n; ++k) {
-        inst[k] = CdInstance{hs[k]->P, hs[k]->d_st, hs[k]->d_rec, hs[k]->d_part};
-        b->smem = std::max(b->smem, cd_dynamic_smem(hs[k]->P));
+        if (hs[k]->block) { b->blk.push_back(hs[k]); b->blk_at.push_back(k); }
+        else { b->one.push_back(hs[k]); b->one_at.push_back(k); }
     }
+    b->stream = hs[0]->stream;
     // every handle's queued work is complete before the batch touches its state
     for (int k = 0; k < n; ++k)
-        if (cudaStreamSynchronize(hs[k]->stream) != cudaSuccess) { delete b; return fail(CDFCI_ERR_CUDA, "stream sync failed"); }
-    if (cudaMalloc(&b->d_inst, n * sizeof(CdInstance)) != cudaSuccess) { delete b; return fail(CDFCI_ERR_NOMEM, "device allocation failed"); }
-    if (cudaMemcpy(b->d_inst, inst.data(), n * sizeof(CdInstance), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(b->d_inst); delete b;
-        return fail(CDFCI_ERR_CUDA, "copy of the instance table failed");
+        if (cudaStreamSynchronize(hs[k]->stream) != cudaSuccess) { batch_free(b); return fail(CDFCI_ERR_CUDA, "stream sync failed"); }
+    if (!b->one.empty()) {
+        b->cluster = b->one[0]->grid;
+        b->chunk = b->one[0]->chunk;
+        std::vector<CdInstance> inst(b->one.size());
+        for (size_t k = 0; k < b->one.size(); ++k) {
+            cdfci_ctx *c = b->one[k];
+            inst[k] = CdInstance{c->P, c->d_st, c->d_rec, c->d_part};
+            b->smem = std::max(b->smem, cd_dynamic_smem(c->P));
+        }
+        if (cudaMalloc(&b->d_inst, inst.size() * sizeof(CdInstance)) != cudaSuccess) {
+            batch_free(b);
+            return fail(CDFCI_ERR_NOMEM, "device allocation failed");
+        }
+        if (cudaMemcpy(b->d_inst, inst.data(), inst.size() * sizeof(CdInstance), cudaMemcpyHostToDevice) != cudaSuccess) {
+            batch_free(b);
+            return fail(CDFCI_ERR_CUDA, "copy of the instance table failed");
+        }
+    }
+    if (!b->blk.empty()) {
+        b->mchunk = b->blk[0]->mchunk;
+        b->br.assign(b->blk.size(), nullptr);
+        b->join.assign(b->blk.size(), nullptr);
+        bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (size_t i = 0; i < b->blk.size() && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&b->br[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) { batch_free(b); return fail(CDFCI_ERR_CUDA, "stream or event creation failed"); }
+        const int rc = batch_mgraph(b);
+        if (rc) { batch_free(b); return rc; }
     }
     *out = b;
     return CDFCI_OK;
@@ -1663,8 +1732,11 @@ CDFCI_API int cdfci_batch_create(const cdfci_handle *hs, int n, cdfci_batch_hand
 CDFCI_API int cdfci_batch_step(cdfci_batch_handle b, int64_t n_iter, cdfci_stats *stats) {
     if (!b) return fail(CDFCI_ERR_ARG, "NULL batch");
     if (n_iter < 0) return fail(CDFCI_ERR_ARG, "n_iter < 0");
-    const int n = (int)b->hs.size();
-    long long left = n_iter;
+    // work a handle queued on its own stream (a solo step) completes first
+    for (cdfci_ctx *c : b->hs)
+        if (c->stream != b->stream) CK(cudaStreamSynchronize(c->stream));
+    // m = 1 group: the persistent batch launch
+    long long left = b->one.empty() ? 0 : n_iter;
     while (left > 0) {
         const long long k = std::min(left, b->chunk);
         int rc = batch_graph(b, k);
@@ -1672,13 +1744,38 @@ CDFCI_API int cdfci_batch_step(cdfci_batch_handle b, int64_t n_iter, cdfci_stats
         CK(cudaGraphLaunch(b->graph, b->stream));
         left -= k;
     }
-    CK(launch_cd_finalize_batch(b->d_inst, n, b->cluster, b->stream));
-    for (int k = 0; k < n; ++k)
-        CK(cudaMemcpyAsync(b->hs[k]->h_st, b->hs[k]->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, b->stream));
+    if (!b->one.empty()) CK(launch_cd_finalize_batch(b->d_inst, (int)b->one.size(), b->cluster, b->stream));
+    // m > 1 group: graphs of mchunk iterations of every problem side by side, then the rest
+    if (!b->blk.empty()) {
+        for (int64_t i = 0; i < n_iter / b->mchunk; ++i) {
+            bool rebuild = false;
+            for (cdfci_ctx *c : b->blk) {
+                if (!c->prm.z_threshold_search) continue;
+                CK(cudaStreamSynchronize(b->stream));
+                bool changed = false;
+                const int rc = maybe_raise_tau(c, &changed);      // tau is a launch parameter of the graph
+                if (rc) return rc;
+                rebuild = rebuild || changed;
+            }
+            if (rebuild) {
+                const int rc = batch_mgraph(b);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(b->mgraph, b->stream));
+        }
+        for (cdfci_ctx *c : b->blk)
+            for (int64_t r = 0; r < n_iter % b->mchunk; ++r) CK(launch_mc_iteration(c->P, c->mb, b->stream));
+    }
+    for (size_t k = 0; k < b->one.size(); ++k)
+        CK(cudaMemcpyAsync(b->one[k]->h_st, b->one[k]->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
     int first = CDFCI_OK;
-    for (int k = 0; k < n; ++k) {
-        const int rc = stats_from_snapshot(b->hs[k], stats ? stats + k : nullptr);
+    for (size_t k = 0; k < b->one.size(); ++k) {
+        const int rc = stats_from_snapshot(b->one[k], stats ? stats + b->one_at[k] : nullptr);
+        if (rc && !first) first = rc;
+    }
+    for (size_t k = 0; k < b->blk.size(); ++k) {
+        const int rc = fill_stats(b->blk[k], stats ? stats + b->blk_at[k] : nullptr);
         if (rc && !first) first = rc;
     }
     return first;
@@ -1686,9 +1783,7 @@ CDFCI_API int cdfci_batch_step(cdfci_batch_handle b, int64_t n_iter, cdfci_stats
 
 CDFCI_API void cdfci_batch_destroy(cdfci_batch_handle b) {
     if (!b) return;
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    cudaFree(b->d_inst);
-    delete b;
+    batch_free(b);
 }
 
 CDFCI_API int cdfci_autotune(const double *h, const double *g, int N, int n_alpha, int n_beta, cdfci_params *params,

@@ -374,6 +374,8 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterSt
     for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
     __syncthreads();
     const int stride = gridDim.x * blockDim.x;
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
         const int t = base + threadIdx.x;
         const bool ok = t < n;
@@ -383,7 +385,10 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterSt
             gkey[t] = 0ull;
         } else if (ok) {
             const long long slot = cand[t];
-            const double2 v = __ldcg(reinterpret_cast<const double2 *>(&P.table[slot].c));
+            double2 v;                                     // c and b of a random slot: evict first from L2
+            asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                         : "=d"(v.x), "=d"(v.y)
+                         : "l"(&P.table[slot].c), "l"(pol));
             k = (unsigned long long)__double_as_longlong(fma(mu, v.x, v.y)) & 0x7fffffffffffffffull;
             gkey[t] = k;
             mark_clear(P, slot);                           // clear the candidate mark
@@ -1197,13 +1202,53 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
 // The column's single-excitation entries and orbital lists are built once per
 // iteration (k_mc_prepare, k_mc_start).  Warps take items of all columns from
 // a global counter; each item leaves one gather partial (sum_j H_ji c_j over
-// its elements), which k_mc_finalize adds per column in item order.  Elements
-// that need the table (|H| at or above the column's threshold, or c_j possibly
-// nonzero by the filter) go to the warp's queue; whenever it holds 32 the warp
-// looks them up together, one per lane.
+// its elements), which k_mc_finalize adds per column in item order.  An item
+// first evaluates its elements; those that need the table (|H| at or above
+// the column's threshold, or c_j possibly nonzero by the filter) go to the
+// warp's queue, which the warp then looks up 64 at a time, two per lane with
+// both first slots in flight (one call site of the lookup routine for every
+// item kind keeps the kernel's code small).
 // ---------------------------------------------------------------------------
-constexpr int kScatterQ = 64;       // per-warp queue of elements that need a table lookup (31 + 32)
-constexpr int kWarpCand = 256;      // per-warp buffer of new candidates (flushed above kWarpCand - 32)
+constexpr int kWarpCand = 192;      // per-warp buffer of new candidates (flushed above kWarpCand - 64)
+
+// L2 eviction priorities for the scatter: a table slot's last touch in a lookup
+// is the add to b (evict first after it; the slot's load keeps the normal
+// priority so that the line is still in L2 when the add arrives), while the
+// integrals, the c != 0 filter and the candidate marks are read by every
+// element and must stay in L2 (evict last).
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double ldg_keep(const double *p, unsigned long long pol) {
+    double x;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(x) : "l"(p), "l"(pol));
+    return x;
+}
+__device__ __forceinline__ unsigned ldg_keep(const unsigned *p, unsigned long long pol) {
+    unsigned x;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(x) : "l"(p), "l"(pol));
+    return x;
+}
+__device__ __forceinline__ void red_add_hint(double *p, double v, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+// candidate mark of slot s (true if this call set it), kept in L2
+__device__ __forceinline__ bool mark_set_keep(const Problem &P, long long s, unsigned long long pol) {
+    const unsigned bit = 1u << (unsigned)(s & 31);
+    unsigned old;
+    asm volatile("atom.global.or.L2::cache_hint.b32 %0, [%1], %2, %3;"
+                 : "=r"(old)
+                 : "l"(P.mark + (s >> 5)), "r"(bit), "l"(pol)
+                 : "memory");
+    return !(old & bit);
+}
 
 // The whole 32-byte slot {A, B, c, b} in one load: one DRAM access for the key
 // and the values (two 16-byte loads of one slot cost two accesses of random
@@ -1216,18 +1261,17 @@ __device__ __forceinline__ void ld_slot(const Slot *s, unsigned long long &ka, u
     c = __longlong_as_double((long long)cb);
 }
 
-// Probe for {a, b}.  Returns the slot, or -1 (absent, not inserted) / -2
-// (error, status set).  c: the slot's stored c.
-__device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, unsigned long long a,
-                                              unsigned long long b, unsigned long long h, bool insert,
-                                              bool &inserted, double &c) {
-    unsigned long long pos = h & P.mask;
+// Probe for {a, b} whose first slot (at pos) the caller has loaded: key (ka,
+// kb) and c (sc).  Returns the slot, or -1 (absent, not inserted) / -2 (error,
+// status set).  c: the slot's stored c.
+__device__ __forceinline__ long long mc_resolve(const Problem &P, IterState *st, unsigned long long a,
+                                                unsigned long long b, unsigned long long pos, unsigned long long ka,
+                                                unsigned long long kb, double sc, bool insert, bool &inserted,
+                                                double &c) {
     const bool both_nonzero = (P.na > 0) && (P.nb > 0);
     for (int probe = 0; probe < P.max_probe; ++probe) {
         Slot *s = P.table + pos;
-        unsigned long long ka, kb;
-        double sc;
-        ld_slot(s, ka, kb, sc);
+        if (probe > 0) ld_slot(s, ka, kb, sc);
         int spins = 0;
         while (both_nonzero && ((ka == 0ull) != (kb == 0ull))) {     // an insert in flight
             if (++spins > (1 << 20)) { set_status(st, kErrTimeout); return -2; }
@@ -1257,6 +1301,43 @@ __device__ __forceinline__ long long mc_probe(const Problem &P, IterState *st, u
     return -2;
 }
 
+// Per-warp scatter context: the column's constants, counters and the lookup queue.
+struct McWarp {
+    unsigned long long *qa, *qb, *qh;
+    double *qH;
+    long long *wcand;
+    unsigned long long pol_first, pol_last;        // L2 eviction policies: table slots / hot structures
+    unsigned long long tib;
+    double wi, gather;
+    int qn, nwc, c_el, c_app, c_drop, c_ins;
+    bool err;
+};
+
+// filter word of hash h (the c != 0 bit is bit (h >> 32) & 31 of it); all ones without a filter
+__device__ __forceinline__ unsigned cnz_word(const Problem &P, unsigned long long h, unsigned long long pol) {
+    return P.cnz ? ldg_keep(P.cnz + (((h >> 32) & P.cnz_mask) >> 5), pol) : 0xffffffffu;
+}
+
+// Element (oa, ob) with hash hk and value H (`ok`: this lane holds one) with its filter word cw:
+// counted, and queued when it needs the table (|H| >= thr, compared as bit patterns, or c_j
+// possibly nonzero); otherwise c_j = 0 and the compression rule drops it here.
+__device__ __forceinline__ void mc_push(McWarp &W, bool ok, unsigned long long oa, unsigned long long ob,
+                                        unsigned long long hk, double H, unsigned cw) {
+    const int lane = threadIdx.x & 31;
+    bool need = false;
+    if (ok && !is_zero(H)) {
+        ++W.c_el;
+        need = ((cw >> (unsigned)((hk >> 32) & 31)) & 1u) || abs_bits(H) >= W.tib;
+        if (!need) ++W.c_drop;
+    }
+    const unsigned int nm = __ballot_sync(0xffffffffu, need);
+    if (need) {
+        const int at = W.qn + __popc(nm & ((1u << lane) - 1u));
+        W.qa[at] = oa; W.qb[at] = ob; W.qh[at] = hk; W.qH[at] = H;
+    }
+    W.qn += __popc(nm);
+}
+
 // The warp's candidate buffer to the global list (one reservation); entries
 // beyond the list's capacity are not written and set the status.
 __device__ __forceinline__ void mc_flush_cand(const Problem &P, McState *ms, IterState *st, long long *wcand, int &nwc,
@@ -1274,111 +1355,72 @@ __device__ __forceinline__ void mc_flush_cand(const Problem &P, McState *ms, Ite
     __syncwarp();
 }
 
-// One queued element of the scatter: look up its slot (insert when it passes
-// the compression rule), add w H to b, gather H c, mark the slot as a
-// candidate of the next selection (its marker appends it to the warp's
-// candidate buffer wc, which goes to the global list, one reservation per
-// flush, when it fills).  Called by a whole warp; `has` = this lane holds an
-// element.  Returns true on a table error (status set).
-__device__ __forceinline__ bool mc_apply(const Problem &P, McState *ms, IterState *st, bool has,
-                                         unsigned long long oa, unsigned long long ob, unsigned long long hk,
-                                         double H, unsigned long long tib, double wi, double &gather, int &c_app,
-                                         int &c_drop, int &c_ins, long long *wcand, int &nwc, long long *cand) {
+// The queue's lookups, two per lane at a time (both first slots loaded
+// together): find the slot (insert when the rule passes), add w H to b, gather
+// H c, mark the slot as a candidate of the next selection; the lane that marks
+// it appends it to the warp's candidate buffer.
+__device__ __forceinline__ void mc_drain(const Problem &P, McState *ms, IterState *st, long long *cand, McWarp &W) {
     const int lane = threadIdx.x & 31;
-    bool err = false, first = false;
-    long long s = -1;
-    if (has) {
-        const bool big = abs_bits(H) >= tib;
-        bool ins = false;
-        double cj = 0.0;
-        s = mc_probe(P, st, oa, ob, hk, big, ins, cj);
-        if (s == -2) {
-            err = true;
-        } else if (s < 0 || !(!is_zero(cj) || big)) {
-            ++c_drop;
-        } else {
-            Slot *sj = P.table + s;
-            atomicAdd(&sj->bv, wi * H);
-            ++c_app;
-            c_ins += ins ? 1 : 0;
-            gather = fma(H, cj, gather);
-            first = mark_set(P, s);                     // the marker appends it
+    while (W.qn > 0 && !W.err) {
+        __syncwarp();
+        const int n = min(W.qn, 64), base = W.qn - n;
+        bool has[2];
+        unsigned long long oa[2], ob[2], pos[2], ka[2], kb[2];
+        double H[2], sc[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            has[u] = lane + 32 * u < n;
+            const int at = base + lane + 32 * u;
+            oa[u] = has[u] ? W.qa[at] : 0ull;
+            ob[u] = has[u] ? W.qb[at] : 0ull;
+            pos[u] = has[u] ? (W.qh[at] & P.mask) : 0ull;
+            H[u] = has[u] ? W.qH[at] : 0.0;
+            ka[u] = kb[u] = 0ull;
+            sc[u] = 0.0;
+            if (has[u]) ld_slot(P.table + pos[u], ka[u], kb[u], sc[u]);
         }
+        __syncwarp();
+        W.qn = base;
+        bool first[2] = {false, false};
+        long long s[2] = {-1, -1};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!has[u]) continue;
+            const bool big = abs_bits(H[u]) >= W.tib;
+            bool ins = false;
+            double cj = 0.0;
+            s[u] = mc_resolve(P, st, oa[u], ob[u], pos[u], ka[u], kb[u], sc[u], big, ins, cj);
+            if (s[u] == -2) {
+                W.err = true;
+            } else if (s[u] < 0 || !(!is_zero(cj) || big)) {
+                ++W.c_drop;
+            } else {
+                red_add_hint(&P.table[s[u]].bv, W.wi * H[u], W.pol_first);
+                ++W.c_app;
+                W.c_ins += ins ? 1 : 0;
+                W.gather = fma(H[u], cj, W.gather);
+                first[u] = mark_set_keep(P, s[u], W.pol_last);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const unsigned int fm = __ballot_sync(0xffffffffu, first[u]);
+            if (first[u]) W.wcand[W.nwc + __popc(fm & ((1u << lane) - 1u))] = s[u];
+            W.nwc += __popc(fm);
+        }
+        if (W.nwc > kWarpCand - 64) mc_flush_cand(P, ms, st, W.wcand, W.nwc, cand);
+        W.err = __any_sync(0xffffffffu, W.err);
     }
-    const unsigned int fm = __ballot_sync(0xffffffffu, first);
-    if (first) wcand[nwc + __popc(fm & ((1u << lane) - 1u))] = s;
-    nwc += __popc(fm);
-    if (nwc > kWarpCand - 32) mc_flush_cand(P, ms, st, wcand, nwc, cand);
-    return __any_sync(0xffffffffu, err);
+    W.qn = 0;
 }
 
-// Per-warp scatter context: the column's constants and the lookup queue.
-struct McWarp {
-    const Problem &P;
-    McState *ms;
-    IterState *st;
-    long long *cand;
-    unsigned long long *qa, *qb, *qh;
-    double *qH;
-    long long *wcand;
-    unsigned long long tib;
-    double wi, gather;
-    int qn, nwc, c_el, c_app, c_drop, c_ins;
-    bool err;
+constexpr int kAbChunk = 4;         // alpha singles per opposite-spin item
+constexpr int kSsChunk = 4;         // occupied pairs per same-spin item
+constexpr int kScatterQ = 32 * 4;   // per-warp queue: one item's elements at most
 
-    // filter word of hash h (the c != 0 bit is bit (h >> 32) & 31 of it); all ones without a filter
-    __device__ __forceinline__ unsigned cnz_word(unsigned long long h) const {
-        return P.cnz ? __ldg(P.cnz + (((h >> 32) & P.cnz_mask) >> 5)) : 0xffffffffu;
-    }
-    // element (oa, ob) with hash hk and value H, `ok` = this lane holds one; filter word cw
-    __device__ __forceinline__ void push(bool ok, unsigned long long oa, unsigned long long ob, unsigned long long hk,
-                                         double H, unsigned cw) {
-        const int lane = threadIdx.x & 31;
-        bool need = false;
-        if (ok && !is_zero(H)) {
-            ++c_el;
-            // |H| >= thr (non-negative doubles order like their bits) or c_j may be nonzero;
-            // otherwise c_j = 0 and the rule drops it
-            need = ((cw >> (unsigned)((hk >> 32) & 31)) & 1u) || abs_bits(H) >= tib;
-            if (!need) ++c_drop;
-        }
-        const unsigned int nm = __ballot_sync(0xffffffffu, need);
-        if (need) {
-            const int at = qn + __popc(nm & ((1u << lane) - 1u));
-            qa[at] = oa; qb[at] = ob; qh[at] = hk; qH[at] = H;
-        }
-        qn += __popc(nm);
-        if (qn >= 32 && !err) {
-            __syncwarp();
-            qn -= 32;
-            const int at = qn + lane;
-            err = mc_apply(P, ms, st, true, qa[at], qb[at], qh[at], qH[at], tib, wi, gather, c_app, c_drop, c_ins,
-                           wcand, nwc, cand);
-            __syncwarp();
-        }
-    }
-    // the rest of the queue
-    __device__ __forceinline__ void drain() {
-        const int lane = threadIdx.x & 31;
-        if (qn > 0 && !err) {
-            __syncwarp();
-            const bool has = lane < qn;
-            err = mc_apply(P, ms, st, has, has ? qa[lane] : 0ull, has ? qb[lane] : 0ull, has ? qh[lane] : 0ull,
-                           has ? qH[lane] : 0.0, tib, wi, gather, c_app, c_drop, c_ins, wcand, nwc, cand);
-            __syncwarp();
-        }
-        qn = 0;
-    }
-};
-
-constexpr int kAbChunk = 8;         // alpha singles per opposite-spin item
-constexpr int kSsChunk = 8;         // occupied pairs per same-spin item
-constexpr int kAbU = 4;             // opposite-spin elements in flight per lane
-
-// Opposite-spin doubles: lane = beta single sb, alpha singles [sa0, sa1).
-__device__ __forceinline__ void mc_item_ab(McWarp &W, const ColEnt *tA, const ColEnt *tB, int nsB, int sb, int sa0,
-                                           int sa1) {
-    const Problem &P = W.P;
+// Opposite-spin doubles: lane = beta single sb, alpha singles [sa0, sa1), all in flight together.
+__device__ __forceinline__ void mc_item_ab(const Problem &P, McWarp &W, const ColEnt *tA, const ColEnt *tB, int nsB,
+                                           int sb, int sa0, int sa1) {
     const bool lane_ok = sb < nsB;
     ColEnt eb;
     if (lane_ok) {
@@ -1387,42 +1429,40 @@ __device__ __forceinline__ void mc_item_ab(McWarp &W, const ColEnt *tA, const Co
         eb.key = 0ull; eb.h = 0ull; eb.goff = 0; eb.info = 0;
     }
     const int kb = (eb.info >> 24) & 0xff;
-    for (int sa = sa0; sa < sa1; sa += kAbU) {
-        unsigned long long ka[kAbU], hk[kAbU];
-        double H[kAbU];
-        unsigned cw[kAbU];
-        bool ok[kAbU];
+    unsigned long long ka[kAbChunk], hk[kAbChunk];
+    double H[kAbChunk];
+    unsigned cw[kAbChunk];
+    bool ok[kAbChunk];
 #pragma unroll
-        for (int u = 0; u < kAbU; ++u) {
-            ok[u] = false;
-            H[u] = 0.0;
-            ka[u] = 0ull;
-            hk[u] = 0ull;
-            cw[u] = 0u;
-            if (sa + u < sa1) {
-                const ColEnt ea = tA[sa + u];             // uniform: one broadcast load
-                ka[u] = ea.key;
-                hk[u] = ea.h ^ eb.h;
-                ok[u] = lane_ok && k_conserved(P, (ea.info >> 24) & 0xff, kb);
-                if (ok[u]) {
-                    H[u] = apply_parity(__ldg(P.g + ea.goff + eb.goff), (unsigned long long)((ea.info ^ eb.info) & 1));
-                    cw[u] = W.cnz_word(hk[u]);
-                }
+    for (int u = 0; u < kAbChunk; ++u) {
+        ok[u] = false;
+        H[u] = 0.0;
+        ka[u] = 0ull;
+        hk[u] = 0ull;
+        cw[u] = 0u;
+        if (sa0 + u < sa1) {
+            const ColEnt ea = tA[sa0 + u];                 // uniform: one broadcast load
+            ka[u] = ea.key;
+            hk[u] = ea.h ^ eb.h;
+            ok[u] = lane_ok && k_conserved(P, (ea.info >> 24) & 0xff, kb);
+            if (ok[u]) {
+                H[u] = apply_parity(ldg_keep(P.g + ea.goff + eb.goff, W.pol_last),
+                                    (unsigned long long)((ea.info ^ eb.info) & 1));
+                cw[u] = cnz_word(P, hk[u], W.pol_last);
             }
         }
-#pragma unroll
-        for (int u = 0; u < kAbU; ++u) W.push(ok[u], ka[u], eb.key, hk[u], H[u], cw[u]);
-        if (W.err) return;
     }
+#pragma unroll
+    for (int u = 0; u < kAbChunk; ++u) mc_push(W, ok[u], ka[u], eb.key, hk[u], H[u], cw[u]);
 }
 
 // Same-spin doubles of one string X (the other string Y with hash hY): lane =
 // virtual pair vp, occupied pairs [op0, op1); the element of Eq. (entry) with
 // i < j occupied, a < b empty: (ia|jb) - (ib|ja) times the sign of i -> a then
 // j -> b.
-__device__ __forceinline__ void mc_item_ss(McWarp &W, bool alpha, unsigned long long X, unsigned long long Y,
-                                           unsigned long long hY, const ColLists &L, int vp, int op0, int op1) {
-    const Problem &P = W.P;
+__device__ __forceinline__ void mc_item_ss(const Problem &P, McWarp &W, bool alpha, unsigned long long X,
+                                           unsigned long long Y, unsigned long long hY, const ColLists &L, int vp,
+                                           int op0, int op1) {
     const int N = P.N, N2 = N * N;
     const int cv2 = alpha ? P.cva2 : P.cvb2;
     const bool lane_ok = vp < cv2;
@@ -1436,45 +1476,43 @@ __device__ __forceinline__ void mc_item_ss(McWarp &W, bool alpha, unsigned long 
     }
     const unsigned short *po_t = alpha ? P.pair_oa : P.pair_ob;
     const int aN2 = a * N2, bN2 = b * N2;
-    for (int op = op0; op < op1; op += 2) {
-        unsigned long long key[2], hk[2];
-        double H[2];
-        unsigned cw[2];
-        bool ok[2];
+    unsigned long long key[kSsChunk], hk[kSsChunk];
+    double H[kSsChunk];
+    unsigned cw[kSsChunk];
+    bool ok[kSsChunk];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            ok[u] = false;
-            key[u] = 0ull;
-            hk[u] = 0ull;
-            H[u] = 0.0;
-            cw[u] = 0u;
-            if (op + u < op1 && lane_ok) {
-                const unsigned short po = __ldg(po_t + op + u);      // uniform
-                const int i = occ[po & 0xff], j = occ[po >> 8];
-                const unsigned long long m1 = X & between_mask(i, a);
-                const unsigned long long X1 = X ^ (1ull << i) ^ (1ull << a);
-                const unsigned long long m2 = X1 & between_mask(j, b);
-                key[u] = X1 ^ (1ull << j) ^ (1ull << b);
-                hk[u] = (alpha ? hash_alpha(key[u]) : hash_beta(key[u])) ^ hY;
-                const int base = i * N * N2 + j * N;
-                H[u] = apply_parity(__ldg(P.g + base + aN2 + b) - __ldg(P.g + base + bN2 + a), m1 ^ m2);
-                cw[u] = W.cnz_word(hk[u]);
-                ok[u] = true;
-            }
+    for (int u = 0; u < kSsChunk; ++u) {
+        ok[u] = false;
+        key[u] = 0ull;
+        hk[u] = 0ull;
+        H[u] = 0.0;
+        cw[u] = 0u;
+        if (op0 + u < op1 && lane_ok) {
+            const unsigned short po = __ldg(po_t + op0 + u);      // uniform
+            const int i = occ[po & 0xff], j = occ[po >> 8];
+            const unsigned long long m1 = X & between_mask(i, a);
+            const unsigned long long X1 = X ^ (1ull << i) ^ (1ull << a);
+            const unsigned long long m2 = X1 & between_mask(j, b);
+            key[u] = X1 ^ (1ull << j) ^ (1ull << b);
+            hk[u] = (alpha ? hash_alpha(key[u]) : hash_beta(key[u])) ^ hY;
+            const int base = i * N * N2 + j * N;
+            H[u] = apply_parity(ldg_keep(P.g + base + aN2 + b, W.pol_last) - ldg_keep(P.g + base + bN2 + a, W.pol_last),
+                                m1 ^ m2);
+            cw[u] = cnz_word(P, hk[u], W.pol_last);
+            ok[u] = true;
         }
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-            W.push(ok[u], alpha ? key[u] : Y, alpha ? Y : key[u], hk[u], H[u], cw[u]);
-        if (W.err) return;
     }
+#pragma unroll
+    for (int u = 0; u < kSsChunk; ++u)
+        mc_push(W, ok[u], alpha ? key[u] : Y, alpha ? Y : key[u], hk[u], H[u], cw[u]);
 }
 
 // Singles: lane = single s of the column (alpha entries first); the value is
 // h_ia plus the terms of the occupied spin-orbitals in spin-orbital order
 // (W3 for the single's spin, V3 for the other), one running sum.
-__device__ __forceinline__ void mc_item_s(McWarp &W, const ColEnt *tA, int nsA, int ns, int s, unsigned long long A,
-                                          unsigned long long B, unsigned long long hA, unsigned long long hB) {
-    const Problem &P = W.P;
+__device__ __forceinline__ void mc_item_s(const Problem &P, McWarp &W, const ColEnt *tA, int nsA, int ns, int s,
+                                          unsigned long long A, unsigned long long B, unsigned long long hA,
+                                          unsigned long long hB) {
     const int N = P.N;
     bool ok = false;
     unsigned long long oa = 0ull, ob = 0ull, hk = 0ull;
@@ -1493,10 +1531,10 @@ __device__ __forceinline__ void mc_item_s(McWarp &W, const ColEnt *tA, int nsA, 
         oa = alpha ? e.key : A;
         ob = alpha ? B : e.key;
         hk = alpha ? (e.h ^ hB) : (hA ^ e.h);
-        cw = W.cnz_word(hk);
+        cw = cnz_word(P, hk, W.pol_last);
         ok = true;
     }
-    W.push(ok, oa, ob, hk, H, cw);
+    mc_push(W, ok, oa, ob, hk, H, cw);
 }
 
 __global__ void __launch_bounds__(256, 3) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
@@ -1512,23 +1550,26 @@ __global__ void __launch_bounds__(256, 3) k_mc_scatter(Problem P, McState *ms, I
     const int m = ms->m_sel;
     const int total = m * Gm.per_col;
     const int ns = Gm.nsA + Gm.nsB;
-    McWarp W{P, ms, st, cand, q_a[warp], q_b[warp], q_h[warp], q_H[warp], w_cand[warp], 0ull, 0.0, 0.0,
-             0, 0, 0, 0, 0, 0, false};
+    McWarp W{q_a[warp], q_b[warp], q_h[warp], q_H[warp], w_cand[warp], l2_evict_first(), l2_evict_last(),
+             0ull, 0.0, 0.0, 0, 0, 0, 0, 0, 0, false};
+    // the next item's index is fetched while the current one runs
+    int t_next = 0;
+    if (lane == 0) t_next = (int)atomicAdd(work, 1u);
+    t_next = __shfl_sync(0xffffffffu, t_next, 0);
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = (int)atomicAdd(work, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        const int t = t_next;
         if (t >= total || W.err) break;
+        unsigned int fetched = 0u;
+        if (lane == 0) fetched = atomicAdd(work, 1u);
         const int col = t / Gm.per_col, k = t - col * Gm.per_col;
         const McSel xs = sel[col];
         W.wi = w[col];
         W.tib = abs_bits(thr[col]);
         W.gather = 0.0;
-        W.qn = 0;
         const ColEnt *tA = coltab + (size_t)col * ns;
         if (k < Gm.n_ab) {
             const int lg = k / Gm.ab_ch, ch = k - lg * Gm.ab_ch;
-            mc_item_ab(W, tA, tA + Gm.nsA, Gm.nsB, 32 * lg + lane, ch * kAbChunk, min(Gm.nsA, (ch + 1) * kAbChunk));
+            mc_item_ab(P, W, tA, tA + Gm.nsA, Gm.nsB, 32 * lg + lane, ch * kAbChunk, min(Gm.nsA, (ch + 1) * kAbChunk));
         } else if (k < Gm.n_ab + Gm.n_aa + Gm.n_bb) {
             const bool alpha = k < Gm.n_ab + Gm.n_aa;
             const int kk = k - (alpha ? Gm.n_ab : Gm.n_ab + Gm.n_aa);
@@ -1537,17 +1578,18 @@ __global__ void __launch_bounds__(256, 3) k_mc_scatter(Problem P, McState *ms, I
             const int co2 = alpha ? P.ca2 : P.cb2;
             const unsigned long long X = alpha ? xs.A : xs.B, Y = alpha ? xs.B : xs.A;
             const unsigned long long hY = alpha ? hash_beta(xs.B) : hash_alpha(xs.A);
-            mc_item_ss(W, alpha, X, Y, hY, collists[col], 32 * lg + lane, ch * kSsChunk,
+            mc_item_ss(P, W, alpha, X, Y, hY, collists[col], 32 * lg + lane, ch * kSsChunk,
                        min(co2, (ch + 1) * kSsChunk));
         } else {
             const int lg = k - (Gm.n_ab + Gm.n_aa + Gm.n_bb);
-            mc_item_s(W, tA, Gm.nsA, ns, 32 * lg + lane, xs.A, xs.B, hash_alpha(xs.A), hash_beta(xs.B));
+            mc_item_s(P, W, tA, Gm.nsA, ns, 32 * lg + lane, xs.A, xs.B, hash_alpha(xs.A), hash_beta(xs.B));
         }
-        W.drain();
+        mc_drain(P, ms, st, cand, W);
         // the item's gather: a fixed tree over the warp
         double gsum = W.gather;
         for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(0xffffffffu, gsum, o);
         if (lane == 0) gathp[(size_t)col * Gm.per_col + k] = gsum;
+        t_next = __shfl_sync(0xffffffffu, (int)fetched, 0);
     }
     mc_flush_cand(P, ms, st, w_cand[warp], W.nwc, cand);
     // counters: warp sums, then the warps in order

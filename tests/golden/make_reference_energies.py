@@ -16,6 +16,7 @@ CASES = [
     ("abinitio_N12_3a3b_seed2", inputs.ab_initio(12, 3, 3, seed=2)),
     ("hubbard_chain10_obc_U4_5a5b", inputs.hubbard((10,), 5, 5, U=4.0, periodic=False)),
     ("abinitio_N10_4a4b_seed7", inputs.ab_initio(10, 4, 4, seed=7)),
+    ("abinitio_N12_4a4b_seed2", inputs.ab_initio(12, 4, 4, seed=2)),
 ]
 
 if __name__ == "__main__":

@@ -1,5 +1,6 @@
-"""Batches of independent m = 1 problems of different sizes in one launch:
-every problem follows exactly the trajectory it follows alone, and converges."""
+"""Batches of independent problems of different sizes: m = 1 problems in one launch follow exactly
+the trajectory they follow alone; m > 1 problems (Algorithm 2, one graph branch each) follow theirs up
+to the order of the FP64 atomics on b; every problem converges to the oracle's exact energy."""
 import numpy as np
 import pytest
 
@@ -71,19 +72,72 @@ def test_batch_converges_every_problem():
             s.close()
 
 
-def test_batch_rejects_mixed_problems():
+def test_batch_rejects_invalid_sets():
     from paper_2605_04483_gb300 import api
     ws = problems()[:2]
     a = make(ws[:1])[0]
-    m4 = api.Solver(ws[1].h, ws[1].g, ws[1].N, ws[1].n_alpha, ws[1].n_beta, num_coordinates=4, log2_capacity=14)
     g2 = make(ws[1:2], grid_blocks=2)[0]
+    x2 = api.Solver(ws[1].h, ws[1].g, ws[1].N, ws[1].n_alpha, ws[1].n_beta, num_states=2, log2_capacity=14)
     try:
         with pytest.raises(api.CdfciError):
-            api.Batch([a, m4])
-        with pytest.raises(api.CdfciError):
-            api.Batch([a, g2])
+            api.Batch([a, g2])                        # m = 1 solvers with different CTAs per problem
         with pytest.raises(api.CdfciError):
             api.Batch([a, a])
+        with pytest.raises(api.CdfciError):
+            api.Batch([a, x2])                        # excited states
     finally:
-        for s in (a, m4, g2):
+        for s in (a, g2, x2):
+            s.close()
+
+
+def block_problems():
+    """Ab initio problems without exact ties of |g| (the chosen blocks do not depend on rounding)."""
+    return [inputs.ab_initio(6, 2, 2, seed=31), inputs.ab_initio(8, 3, 2, seed=32),
+            inputs.ab_initio(10, 3, 3, seed=11), inputs.ab_initio(7, 3, 3, seed=33),
+            inputs.ab_initio(12, 3, 3, seed=2)]
+
+
+def test_block_batch_follows_the_single_runs():
+    """m > 1 problems with different m and sizes in one graph: the same chosen blocks (element counts)
+    and energies as alone, below, at and above the graph chunk of 8 iterations; m = 1 problems in
+    the same batch follow theirs exactly."""
+    from paper_2605_04483_gb300 import api
+    ws = block_problems()
+    ms = [4, 16, 8, 32, 64]
+    alone = [make([w], num_coordinates=m)[0] for w, m in zip(ws, ms)] + make(problems()[2:3])
+    batched = [make([w], num_coordinates=m)[0] for w, m in zip(ws, ms)] + make(problems()[2:3])
+    b = api.Batch(batched)
+    try:
+        for n in (3, 8, 21, 40):
+            st_b = b.step(n)
+            st_a = [s.step(n) for s in alone]
+            for k, (x, y) in enumerate(zip(st_a, st_b)):
+                assert x["iterations"] == y["iterations"], k
+                assert x["elements"] == y["elements"], (k, x["elements"], y["elements"])
+                assert abs(x["energy"] - y["energy"]) <= 1e-10 * abs(x["energy"]), (k, x["energy"], y["energy"])
+                if k == len(ws):                          # the m = 1 problem: bit for bit
+                    for f in ("energy", "mu", "alpha", "dx", "nnz_c", "n_slots", "applied"):
+                        assert x[f] == y[f], (f, x[f], y[f])
+        x, y = alone[0].step(8), batched[0].step(8)       # a batched handle goes on alone
+        assert abs(x["energy"] - y["energy"]) <= 1e-10 * abs(x["energy"])
+    finally:
+        b.close()
+        for s in alone + batched:
+            s.close()
+
+
+def test_block_batch_converges_every_problem():
+    from paper_2605_04483_gb300 import api
+    ws = block_problems()[:4] + [inputs.config1()]
+    ms = [8, 16, 64, 64, 128]
+    ss = [make([w], num_coordinates=m)[0] for w, m in zip(ws, ms)]
+    b = api.Batch(ss)
+    try:
+        st = b.step(12000)
+        for w, x in zip(ws, st):
+            E0 = oracle.ground_energy(w.N, w.n_alpha, w.n_beta, w.h, w.g, dense_limit=5000)
+            assert abs(x["energy"] - E0) < 1e-8, (w.N, x["energy"] - E0)
+    finally:
+        b.close()
+        for s in ss:
             s.close()

@@ -208,3 +208,27 @@ def test_restore_errors():
     assert e.value.code == -3
     for s in (a, b, m4, small):
         s.close()
+
+
+def test_restore_grows_the_candidate_list():
+    """A checkpoint whose candidate list is longer than one iteration makes (a start vector of 12
+    columns at m = 4) restored into a fresh m = 4 handle: the restore grows the handle's list to hold
+    every flagged candidate, and the continuation follows the writer's and the oracle's."""
+    w = inputs.ab_initio(8, 3, 3, seed=7)
+    keys, c = start_vector(w, 12, seed=5)
+    a = solver(w, num_coordinates=4)
+    o = oracle.CDFCI(w.N, w.n_alpha, w.n_beta, w.h, w.g, w.ref, 0.0, 4)
+    a.set_initial(keys, c)
+    o.set_initial(keys, c)
+    ck = a.checkpoint()
+    n_h = 1 + 2 * 3 * 5 + 2 * 3 * 10 + 15 * 15              # column length of N = 8, 3 + 3
+    assert ck["flags"].sum() > 4 * n_h + 4 + 64               # more than a fresh m = 4 handle's list
+    b = solver(w, num_coordinates=4)
+    b.restore(ck)
+    assert b.stats()["energy"] == a.stats()["energy"]
+    sa, sb = a.step(12), b.step(12)
+    o.step(12)
+    assert sa["iterations"] == sb["iterations"]
+    assert abs(sb["energy"] - sa["energy"]) <= 1e-10 * abs(sa["energy"])
+    assert abs(sb["energy"] - o.energy()) <= 1e-9 * abs(o.energy())
+    a.close(); b.close(); o.close()

@@ -100,6 +100,29 @@ def test_block_converges_ab_initio(m, n_iter):
         g.close()
 
 
+@pytest.mark.parametrize("name,shape,m,n_max", [("abinitio_N12_3a3b_seed2", (12, 3, 3, 2), 128, 20000),
+                                                 ("abinitio_N12_4a4b_seed2", (12, 4, 4, 2), 256, 20000)])
+def test_block_converges_config2_companions(name, shape, m, n_max):
+    """The config-2 generator's companions small enough for the oracle's exact diagonalisation
+    (dims 48,400 and 245,025): Algorithm 2 at tau = 0 reaches the stored exact energy within 1e-8 Ha,
+    running and exact Rayleigh quotient alike."""
+    N, na, nb, seed = shape
+    w = inputs.ab_initio(N, na, nb, seed=seed)
+    E0 = float(open_reference(name))
+    g = solver(w, m, log2_capacity=20)
+    try:
+        it = 0
+        st = g.stats()
+        while it < n_max and abs(st["energy"] - E0) > 2e-9:
+            st = g.step(200)
+            it += 200
+        print(f"[{name}] m={m}: |E - E0| = {abs(st['energy'] - E0):.2e} after {it} iterations")
+        assert abs(st["energy"] - E0) < 1e-8, (it, st["energy"] - E0)
+        assert abs(g.energy(1) - E0) < 1e-8
+    finally:
+        g.close()
+
+
 def test_block_converges_hubbard_chain():
     w = inputs.config1()
     E0 = float(open_reference("config1_hubbard_chain8_obc_U4"))
