@@ -21,10 +21,12 @@ CASES = [
 
 if __name__ == "__main__":
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "reference_energies.txt")
-    with open(out, "w") as f:
+    tmp = out + ".tmp"
+    with open(tmp, "w") as f:
         f.write("# Exact ground-state energies (Hartree) from the CPU oracle's H; written by\n"
                 "# make_reference_energies.py.  name N n_alpha n_beta fci_dim E0\n")
         for name, w in CASES:
             E = oracle.ground_energy(w.N, w.n_alpha, w.n_beta, w.h, w.g, dense_limit=5000)
             f.write(f"{name} {w.N} {w.n_alpha} {w.n_beta} {w.fci_dim} {E:.15f}\n")
             print(name, w.fci_dim, repr(E))
+    os.replace(tmp, out)
