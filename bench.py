@@ -170,27 +170,28 @@ def paper_hubbard_ed(na: int, nb: int, U: float) -> float:
 def hubbard_k_leg(api, inputs) -> dict:
     """The paper's own lattice setting: the 4x4 periodic Hubbard model in momentum space built by the library
     (cdfci_create_hubbard_k: momentum-conserving enumeration), half filling, from the degenerate-subspace
-    start, m = 128, 2^24 slots: seconds until the running
-    energy is within 1e-5 Ha of the paper's exact value at U/t = 0.5 (its table: CDFCI there took 13 s), and
-    the energy reached in a 20 s budget at U/t = 4 (its table: 9 minutes to the exact value)."""
+    start, m = 128: seconds until the running energy is within 1e-5 Ha of the paper's exact value, at
+    U/t = 0.5 (2^24 slots with z_threshold_search; the paper's CDFCI run took 13 s) and at U/t = 4 (2^26
+    slots, tau = 0; the paper's run took 9 minutes), and the exact Rayleigh quotient reached."""
     out = {}
-    for U, budget in ((0.5, 30.0), (4.0, 20.0)):
+    for U, budget, kw in ((0.5, 30.0, dict(log2_capacity=24, z_threshold_search=1)),
+                          (4.0, 60.0, dict(log2_capacity=26))):
         ref = paper_hubbard_ed(8, 8, U)
-        s = api.Solver.hubbard_k((4, 4), 8, 8, t=1.0, U=U, num_coordinates=128, log2_capacity=24,
-                                 z_threshold_search=1)
+        s = api.Solver.hubbard_k((4, 4), 8, 8, t=1.0, U=U, num_coordinates=128, **kw)
         try:
             t0 = time.perf_counter()
             n_det, E_start = s.set_initial_degenerate()
             t_start = time.perf_counter() - t0
             reached = None
             while time.perf_counter() - t0 < budget:
-                st = s.step(100)
+                st = s.step(200)
                 if abs(st["energy"] - ref) < 1e-5:
                     reached = time.perf_counter() - t0
                     break
             st = s.stats()
             out[f"U{U:g}"] = {"E_paper_ed": ref, "seconds_to_1e-5": reached, "energy": st["energy"],
-                              "gap_ha": st["energy"] - ref, "seconds": time.perf_counter() - t0,
+                              "exact_rq": s.energy(1), "gap_ha": st["energy"] - ref,
+                              "seconds": time.perf_counter() - t0,
                               "iterations": st["iterations"], "determinants": st["n_slots"],
                               "degenerate_start": {"determinants": n_det, "E": E_start, "seconds": t_start}}
         finally:
@@ -426,10 +427,25 @@ def batch_c4(api, inputs, iters: int, grid_blocks: int = 1, ms=None) -> dict:
 
 
 def adjoint_c5(api, inputs, m: int, iters: int) -> dict:
-    """RDMs and dE/dh, dE/dg, dE/dkappa of a config-5 mCDFCI vector (after `iters` iterations)."""
+    """RDMs and dE/dh, dE/dg, dE/dkappa of a config-5 mCDFCI vector after `iters` iterations, and the
+    largest relative difference from central differences (step 1e-5) of the vector's exact Rayleigh
+    quotient under perturbed integrals (cdfci_energy_with), one random direction each for h, g, kappa."""
+    import numpy as np
+    import scipy.linalg
     w = inputs.config5()
     s = api.Solver(w.h, w.g, w.N, w.n_alpha, w.n_beta, num_coordinates=m, log2_capacity=25,
                    ref_alpha=int(w.ref[0]), ref_beta=int(w.ref[1]))
+
+    def sym8(G):
+        return (G + G.transpose(1, 0, 2, 3) + G.transpose(0, 1, 3, 2) + G.transpose(1, 0, 3, 2) +
+                G.transpose(2, 3, 0, 1) + G.transpose(3, 2, 0, 1) + G.transpose(2, 3, 1, 0) +
+                G.transpose(3, 2, 1, 0)) / 8
+
+    def rotated(K):
+        U = scipy.linalg.expm(K)
+        h2 = U.T @ w.h @ U
+        return 0.5 * (h2 + h2.T), sym8(np.einsum("ap,bq,cr,ds,abcd->pqrs", U, U, U, U, w.g, optimize=True))
+
     try:
         t0 = time.perf_counter()
         st = s.step(iters)
@@ -438,13 +454,26 @@ def adjoint_c5(api, inputs, m: int, iters: int) -> dict:
         dh, dg, dk = s.gradient()
         t_grad = time.perf_counter() - t0
         nnz = st["nnz_c"]
+        rng = np.random.default_rng(7)
+        eps = 1e-5
+        D = rng.normal(size=(16, 16)); D = D + D.T
+        G = sym8(rng.normal(size=(16, 16, 16, 16)))
+        K = rng.normal(size=(16, 16)); K = K - K.T
+        t0 = time.perf_counter()
+        fd = {"h": (s.energy_with(w.h + eps * D, w.g) - s.energy_with(w.h - eps * D, w.g)) / (2 * eps),
+              "g": (s.energy_with(w.h, w.g + eps * G) - s.energy_with(w.h, w.g - eps * G)) / (2 * eps),
+              "kappa": (s.energy_with(*rotated(eps * K)) - s.energy_with(*rotated(-eps * K))) / (2 * eps)}
+        t_fd = time.perf_counter() - t0
+        an = {"h": float(np.sum(D * dh)), "g": float(np.sum(G * dg)), "kappa": 0.5 * float(np.sum(dk * K))}
+        err = {k: abs(fd[k] - an[k]) / max(1.0, abs(fd[k])) for k in fd}
     finally:
         s.close()
     return {"workload": "abinitio_N16_5a5b_seed5 (FCI dim 19,079,424, column 4,236), m=%d" % m,
             "solve_iterations": iters, "solve_seconds": t_solve, "energy": st["energy"],
             "nonzeros_c": nnz, "gradient_seconds": t_grad,
             "rdm_lookups_per_s": nnz * 4236 / t_grad, "dE_dkappa_norm": float((dk ** 2).sum() ** 0.5),
-            "trace_dE_dh": float(dh.trace())}
+            "trace_dE_dh": float(dh.trace()), "central_difference_rel_err": err,
+            "central_difference_seconds": t_fd}
 
 
 def time_to_energy(api, w, E_ref: float, m: int, check_every: int, log2_capacity: int, cap_s: float = 30.0):
@@ -510,6 +539,12 @@ def batched_summary(line: dict, probe: dict) -> dict:
         b1 = line.get("batch_96_m1")
         if b1:
             out["batch_96"]["m1_value"] = b1.get("value")
+    ad = line.get("adjoint")
+    if ad and "central_difference_rel_err" in ad:
+        out["adjoint_c5_max_rel_err_vs_central_difference"] = max(ad["central_difference_rel_err"].values())
+    hk = line.get("hubbard_k_4x4")
+    if hk and "U4" in hk:
+        out["hubbard_4x4_U4_seconds_to_paper_ed"] = hk["U4"].get("seconds_to_1e-5")
     tt = line.get("time_to_E_batched_vs_plain")
     if tt:
         out["time_to_E_s"] = [[x["workload"].split(" ")[0], x["plain_m1"].get("seconds"),
@@ -717,8 +752,7 @@ def main():
             kleg = hubbard_k_leg(api, inputs)
         except Exception as e:                       # an informational leg: report, keep the line
             kleg = {"error": f"{type(e).__name__}: {e}"}
-        line["hubbard_k_4x4"] = dict(workload="hubbardk_4x4_pbc_8a8b (momentum basis, dim 1.66e8), m=128, 2^24 slots",
-                                     **kleg)
+        line["hubbard_k_4x4"] = dict(workload="hubbardk_4x4_pbc_8a8b (momentum basis, dim 1.66e8), m=128", **kleg)
         # ---- uneven batch of 96 problems: Algorithm 2 with autotuned m, one graph; and at m = 1 ----
         ws4 = inputs.config4_instances()
         ms, tuned = c4_block_sizes(api, ws4)
@@ -728,7 +762,7 @@ def main():
         line["batch_96_m1"] = dict(workload="the same 96 problems, m=1, one persistent launch (8-CTA cluster each)",
                                    **batch_c4(api, inputs, 200, 8))
         # ---- adjoint: RDMs and energy derivatives ----------------------------------------------
-        line["adjoint"] = adjoint_c5(api, inputs, 128, 300)
+        line["adjoint"] = adjoint_c5(api, inputs, 512, 8000)
         # ---- compact copies of the batched paths' figures inside the roofline object ------------
         roofline.update(batched_summary(line, probe))
         if world == 1:

@@ -177,6 +177,19 @@ int cdfci_step(cdfci_handle h, int64_t n_iter, cdfci_stats *stats);
 int cdfci_energy(cdfci_handle h, int mode, double *E);
 
 /*
+ * The exact Rayleigh quotient c^T H' c / c^T c of the handle's stored vector c
+ * under other integrals h1 (N*N) and g2 (N^4, (pq|rs)) of the same orbital
+ * space and electron counts (host or device pointers, copied; validated as by
+ * cdfci_create with the handle's integral_symmetry): the energy of a fixed
+ * state in another Hamiltonian, as the orbital subproblem of Sec. "Optimal
+ * Orbital Selections" evaluates the fixed FCI state in rotated orbitals.  Used
+ * for central differences of the energy along any integral direction; the
+ * handle's state is not changed.  E: host.  Errors: CDFCI_ERR_ARG,
+ * CDFCI_ERR_NONFINITE, CDFCI_ERR_NOMEM, CDFCI_ERR_UNIMPLEMENTED (xCDFCI).
+ */
+int cdfci_energy_with(cdfci_handle h, const double *h1, const double *g2, double *E);
+
+/*
  * get_column of Sec. "The Hamiltonian Class": all (D', H_{D',D}) with a
  * nonzero FP64 value (Eq. entry), diagonal included, as an unordered list.
  * key = {A, B} (host or device, 2 words).  keys_out (2 words per entry) and
@@ -254,9 +267,17 @@ int cdfci_probe_slots(void *table, int log2_slots, int64_t n_ops, uint64_t seed,
  * tol * max(1, |level|), tol <= 0: 1e-10) contributes every choice of its
  * remaining electrons.  The set S (alpha choices x beta choices, ordered by the
  * 128-bit key (B << 64) | A) must hold at most cap determinants (cap <= 0:
- * 1024); H_SS comes from this handle's columns, its lowest eigenpair from
- * cyclic Jacobi rotations on the host, the vector normalised with its largest
- * component positive (ties: the first in S).  The vector then replaces the
+ * 1024); H_SS comes from this handle's columns, its eigenpairs from cyclic
+ * Jacobi rotations on the host (a one-time start, |S| x |S| dense).  When the
+ * lowest eigenvalue is degenerate (eigenvalues within 1e-9 of it, relative;
+ * 4-fold at the paper's 4x4 half filling, over two total-momentum sectors)
+ * every vector of its eigenspace is an eigenvector: the start is the
+ * projection onto that eigenspace of the ramp r_s = 1 + s / |S| (s = position
+ * in S), which has a component in every momentum sector of it (one basis
+ * vector may lie in a single sector, and H conserves momentum, so the
+ * iteration could never reach the ground state's sector).  For a simple
+ * eigenvalue this is its eigenvector.  The vector is normalised with its
+ * largest component positive (ties: the first in S).  The vector then replaces the
  * state as cdfci_set_initial would (zero components skipped).  *n_det = |S|,
  * *E_sub = the lowest eigenvalue (host pointers; E_sub may be NULL).
  * CDFCI_ERR_CAPACITY if |S| > cap (*n_det set), CDFCI_ERR_UNIMPLEMENTED for

@@ -225,8 +225,12 @@ def degenerate_start(N, na, nb, h, g, tol: float = 1e-10, cap: int = 1024):
     lowest eigenvector).  Per spin the orbitals below the ne-th lowest level h_pp are filled and
     every choice of the remaining electrons in that level's shell (levels within tol * max(1, |level|))
     is listed.  S = alpha x beta choices ordered by the 128-bit key (B << 64) | A; H_SS from
-    column_sc; the lowest eigenpair from numpy's eigh; the vector normalised, its largest component
-    positive (ties: the first in S).  Returns (keys (|S|, 2), c, lowest eigenvalue)."""
+    column_sc; its eigenpairs from numpy's eigh.  When the lowest eigenvalue is degenerate (the 4x4
+    lattice: 4-fold, over two total-momentum sectors) "the" eigenvector is any vector of its
+    eigenspace; the start is the projection onto that eigenspace of the ramp r_s = 1 + s / |S|, which
+    has a component in every sector of it (an arbitrary basis vector can lie in one sector only, and H
+    conserves momentum).  The vector normalised, its largest component positive (ties: the first in
+    S).  Returns (keys (|S|, 2), c, lowest eigenvalue)."""
     import itertools
     eps = np.diag(np.asarray(h, dtype=np.float64))
 
@@ -256,12 +260,19 @@ def degenerate_start(N, na, nb, h, g, tol: float = 1e-10, cap: int = 1024):
                 H[j, i] = v
     H = 0.5 * (H + H.T)
     w, V = np.linalg.eigh(H)
-    v = V[:, 0] / np.linalg.norm(V[:, 0])
+    # the lowest eigenvalue's whole eigenspace (eigenvalues within 1e-9 of it, relative): the start
+    # is the projection onto it of the ramp r_s = 1 + s / |S| (s = position in S); for a simple
+    # eigenvalue that is the eigenvector itself
+    lo = w[0]
+    k = int(np.sum(w <= lo + 1e-9 * max(1.0, abs(lo))))
+    ramp = 1.0 + np.arange(n) / n
+    v = V[:, :k] @ (V[:, :k].T @ ramp)
+    v = v / np.linalg.norm(v)
     big = int(np.argmax(np.abs(v)))
     if v[big] < 0:
         v = -v
     keys = np.array([[a, b] for (b, a) in S], dtype=np.uint64)
-    return keys, v, float(w[0])
+    return keys, v, float(lo)
 
 
 def line_search(v1: float, v2: float, v3: float) -> float:

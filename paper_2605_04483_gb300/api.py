@@ -99,6 +99,7 @@ def lib():
         L.cdfci_step.argtypes = [vp, i64, ctypes.POINTER(cdfci_stats)]
         L.cdfci_get_stats.argtypes = [vp, ctypes.POINTER(cdfci_stats)]
         L.cdfci_energy.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        L.cdfci_energy_with.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_double)]
         L.cdfci_get_column.argtypes = [vp, u64p, u64p, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_export.argtypes = [vp, u64p, dp, dp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.cdfci_rdm.argtypes = [vp, dp, dp]
@@ -229,6 +230,15 @@ def cdfci_get_stats(handle: int) -> dict:
     s = cdfci_stats()
     _check(lib().cdfci_get_stats(handle, ctypes.byref(s)))
     return s.as_dict()
+
+
+def cdfci_energy_with(handle: int, h, g) -> float:
+    """Exact Rayleigh quotient of the stored vector under the integrals h, g (same space)."""
+    h = np.ascontiguousarray(h, dtype=np.float64) if isinstance(h, np.ndarray) else h
+    g = np.ascontiguousarray(g, dtype=np.float64) if isinstance(g, np.ndarray) else g
+    E = ctypes.c_double()
+    _check(lib().cdfci_energy_with(handle, _ptr(h), _ptr(g), ctypes.byref(E)))
+    return E.value
 
 
 def cdfci_energy(handle: int, mode: int = 0) -> float:
@@ -481,6 +491,9 @@ class Solver:
 
     def energy(self, mode: int = 0) -> float:
         return cdfci_energy(self.handle, mode)
+
+    def energy_with(self, h, g) -> float:
+        return cdfci_energy_with(self.handle, h, g)
 
     def entry(self, row_key, col_key) -> float:
         return cdfci_get_entry(self.handle, row_key, col_key)

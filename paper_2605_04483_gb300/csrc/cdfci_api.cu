@@ -123,6 +123,7 @@ void free_ctx(cdfci_ctx *c) {
 }
 
 int fill_stats(cdfci_ctx *c, cdfci_stats *s);
+int exact_rq(cdfci_ctx *c, const Problem &P, double *E);
 
 // z_threshold_search: the r-th tenfold raise of tau comes when the stored determinants pass
 // 1 - 2^-(r+1) of max_entries (50 %, 75 %, 87.5 %, ...), so each raise leaves half of the
@@ -810,6 +811,58 @@ CDFCI_API int cdfci_energy(cdfci_handle c, int mode, double *E) {
     if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "exact recompute (mode 1) is for one state; use cdfci_energies");
     int rc = fill_stats(c, nullptr);
     if (rc) return rc;
+    return exact_rq(c, c->P, E);
+}
+
+CDFCI_API int cdfci_energy_with(cdfci_handle c, const double *h, const double *g, double *E) {
+    if (!c || !h || !g || !E) return fail(CDFCI_ERR_ARG, "NULL argument");
+    if (c->xcd) return fail(CDFCI_ERR_UNIMPLEMENTED, "the Rayleigh quotient under other integrals is for one state");
+    int rc = fill_stats(c, nullptr);
+    if (rc) return rc;
+    const int N = c->N;
+    const size_t n2 = (size_t)N * N, n4 = n2 * n2;
+    double *dh = nullptr, *dg = nullptr, *dJ = nullptr, *dK = nullptr, *dW3 = nullptr, *dV3 = nullptr;
+    int *dflags = nullptr;
+    auto release = [&]() {
+        cudaFree(dh); cudaFree(dg); cudaFree(dJ); cudaFree(dK); cudaFree(dW3); cudaFree(dV3); cudaFree(dflags);
+    };
+    if (cudaMalloc(&dh, n2 * sizeof(double)) != cudaSuccess || cudaMalloc(&dg, n4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dJ, n2 * sizeof(double)) != cudaSuccess || cudaMalloc(&dK, n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dW3, (size_t)N * n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dV3, (size_t)N * n2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dflags, 4 * sizeof(int)) != cudaSuccess) {
+        release();
+        return fail(CDFCI_ERR_NOMEM, "device allocation of the integrals failed");
+    }
+    int flags[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(dh, h, n2 * sizeof(double), kind_to_device(h), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dg, g, n4 * sizeof(double), kind_to_device(g), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflags, 0, 4 * sizeof(int), c->stream);
+    if (e == cudaSuccess)
+        e = launch_setup(dh, dg, N, dJ, dK, dW3, dV3, dflags, dflags + 1, c->prm.integral_symmetry == 4 ? 1 : 0,
+                         c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flags, dflags, sizeof(flags), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { release(); return fail(CDFCI_ERR_CUDA, "set-up of the integrals: %s", cudaGetErrorString(e)); }
+    if (flags[0] == CDFCI_ERR_NONFINITE) { release(); return fail(CDFCI_ERR_NONFINITE, "h or g holds NaN/Inf"); }
+    if (flags[0] != 0) {
+        release();
+        return fail(CDFCI_ERR_ARG, "h is not symmetric or g lacks the %d-fold symmetry", c->prm.integral_symmetry);
+    }
+    Problem P = c->P;
+    P.h = dh; P.g = dg; P.J = dJ; P.K = dK; P.W3 = dW3; P.V3 = dV3;
+    P.doubles_vanish = flags[1] ? 0 : 1;
+    rc = exact_rq(c, P, E);
+    release();
+    return rc;
+}
+
+}  // extern "C"
+
+namespace {
+// c^T H c / c^T c of the handle's stored vector with H from P's integrals: every stored i with
+// c_i != 0 gets (Hc)_i from a fresh column (lookups only), partial sums reduced in a fixed order.
+int exact_rq(cdfci_ctx *c, const Problem &P, double *E) {
     long long n = c->h_st->n_slots;
     long long *list = nullptr;
     double *partial = nullptr, *dE = nullptr;
@@ -821,13 +874,16 @@ CDFCI_API int cdfci_energy(cdfci_handle c, int mode, double *E) {
         return fail(CDFCI_ERR_NOMEM, "device allocation failed");
     }
     cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
-    if (e == cudaSuccess) e = launch_rq(c->P, c->d_st, list, n, c->d_counter, partial, nblocks, dE, c->stream);
+    if (e == cudaSuccess) e = launch_rq(P, c->d_st, list, n, c->d_counter, partial, nblocks, dE, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(list); cudaFree(partial); cudaFree(dE);
     if (e != cudaSuccess) return fail(CDFCI_ERR_CUDA, "energy: %s", cudaGetErrorString(e));
     return fill_stats(c, nullptr);
 }
+}  // namespace
+
+extern "C" {
 
 CDFCI_API int cdfci_get_column(cdfci_handle c, const uint64_t *key, uint64_t *keys_out, double *vals_out, int64_t cap,
                      int64_t *n_out) {
@@ -1093,9 +1149,15 @@ int degenerate_configurations(const std::vector<double> &eps, int na, int nb, do
     return CDFCI_OK;
 }
 
-// Lowest eigenpair of the symmetric n x n matrix A (row-major, destroyed) by
-// cyclic Jacobi rotations: each rotation zeroes A_pq with tan = t, t the
-// smaller root of t^2 + 2 theta t - 1 = 0, theta = (A_qq - A_pp) / (2 A_pq).
+// The start vector of the degenerate subspace: the eigenpairs of the symmetric
+// n x n matrix A (row-major, destroyed) by cyclic Jacobi rotations (each zeroes
+// A_pq with tan = t, t the smaller root of t^2 + 2 theta t - 1 = 0, theta =
+// (A_qq - A_pp) / (2 A_pq)); lam = the lowest eigenvalue; v = the projection
+// onto its whole eigenspace (eigenvalues within 1e-9 of it, relative) of the
+// ramp r_s = 1 + s / n, normalised with its largest component positive (ties:
+// the first).  For a simple eigenvalue v is its eigenvector; for a degenerate
+// one the projection has a component in every momentum sector of the
+// eigenspace, where a single basis vector may lie in one sector only.
 void jacobi_lowest(int n, std::vector<double> &A, double &lam, std::vector<double> &v) {
     std::vector<double> V((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
@@ -1134,9 +1196,16 @@ void jacobi_lowest(int n, std::vector<double> &A, double &lam, std::vector<doubl
     for (int i = 1; i < n; ++i)
         if (A[(size_t)i * n + i] < A[(size_t)lo * n + lo]) lo = i;
     lam = A[(size_t)lo * n + lo];
+    const double band = 1e-9 * std::max(1.0, std::fabs(lam));
     v.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        if (!(A[(size_t)j * n + j] <= lam + band)) continue;
+        double dot = 0.0;                                   // (eigenvector j) . ramp
+        for (int k = 0; k < n; ++k) dot += V[(size_t)k * n + j] * (1.0 + (double)k / (double)n);
+        for (int k = 0; k < n; ++k) v[k] += dot * V[(size_t)k * n + j];
+    }
     double nrm = 0.0;
-    for (int k = 0; k < n; ++k) { v[k] = V[(size_t)k * n + lo]; nrm += v[k] * v[k]; }
+    for (int k = 0; k < n; ++k) nrm += v[k] * v[k];
     nrm = std::sqrt(nrm);
     int big = 0;
     for (int k = 0; k < n; ++k) {

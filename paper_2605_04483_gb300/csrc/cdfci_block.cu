@@ -983,12 +983,23 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         bsum_f<1>(t, s_rf, hf);
         drms = sqrtf(t[0] / (float)n);
     }
+    // A x in float-float for the start; afterwards A x follows x implicitly (x <- yx x + yw w + yp p
+    // gives A x <- yx A x + yw A w + yp A p, the last two in FP32) and is recomputed exactly each time
+    // the residual falls below `refresh` (relative), and always before convergence is accepted:
+    // an implicit A x drifts by about the FP32 rounding of the steps taken since the last exact one.
+    ff ax = {0.0f, 0.0f};
+    bool exact = false, want_exact = true;
+    float refresh = 1e-6f;
     for (;; ++it) {
-        // (a) A x in float-float
-        if (lead) { xs[2 * row] = x.hi; xs[2 * row + 1] = x.lo; }
-        __syncthreads();
-        const ff ax = ff_row(Ah, Al, ld, n, row, kk, tpr, act, xs);
-        // (b) theta = x.Ax / x.x, r = A x - theta x
+        // A x recomputed exactly for the current x when asked for
+        if (want_exact) {
+            if (lead) { xs[2 * row] = x.hi; xs[2 * row + 1] = x.lo; }
+            __syncthreads();
+            ax = ff_row(Ah, Al, ld, n, row, kk, tpr, act, xs);
+            exact = true;
+            want_exact = false;
+        }
+        // (a) theta = x.Ax / x.x, r = A x - theta x
         {
             ff t[2] = {lead ? ff_mul(x, ax) : ff{0.0f, 0.0f}, lead ? ff_mul(x, x) : ff{0.0f, 0.0f}};
             bsum_ff<2>(t, s_rff, hff);
@@ -998,80 +1009,99 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         const float r = act ? ff_to_float(ff_add(ax, ff_neg(ff_mul(theta, x)))) : 0.0f;
         const float th = ff_to_float(theta);
         const float scale = fmaxf(fabsf(th), drms);
-        // (c) preconditioned residual w = r / |A_ii - theta|: the absolute value
-        //     keeps the preconditioner positive definite while theta is still
-        //     above some diagonal entries (an indefinite one stalls the iteration)
+        // (b) preconditioned residual w = r / |A_ii - theta| (the absolute value keeps the
+        //     preconditioner positive definite while theta is still above some diagonal entries;
+        //     an indefinite one stalls the iteration)
         const float den = fmaxf(fabsf(d - th), 1e-4f * fmaxf(scale, 1e-30f));
         float wv = act ? r / den : 0.0f;
         const float xh = x.hi;
         float red[3] = {lead ? r * r : 0.0f, lead ? xh * wv : 0.0f, lead ? xh * pv : 0.0f};
         bsum_f<3>(red, s_rf, hf);
-        const float rr = red[0];
+        const float nres = sqrtf(red[0]);
         const float tol = 1e-14f * scale;
-        const float nres = sqrtf(rr);
-        // stop at the float-float floor, at the cap, or when progress has ended well below it
+        // stop at the float-float floor, at the cap, or when progress has ended well below it;
+        // only a residual of an exact A x ends the iteration: with an implicit one the step below
+        // is taken and A x is recomputed at the start of the next iteration (likewise once the
+        // residual is below `refresh`, which then moves down three decades)
         if (nres < best * 0.7f) { best = nres; stall = 0; } else ++stall;
-        if (!(nres > tol * sqrtf((float)n)) || it >= kEigMaxIt || (stall >= 4 && nres < 1e-11f * scale)) break;
-        // orthogonalise w and p against x (x.x ~ 1)
+        const bool stop = !(nres > tol * sqrtf((float)n)) || it >= kEigMaxIt || (stall >= 4 && nres < 1e-11f * scale);
+        if (stop && exact) break;
+        if (!exact && (stop || nres < refresh * scale)) {
+            want_exact = true;
+            refresh = fminf(refresh, nres / fmaxf(scale, 1e-30f)) * 1e-3f;
+            if (stop) { best = 3.0e38f; stall = 0; }
+        }
+        // w and p orthogonalised against x (x.x ~ 1)
         const float ixx = 1.0f / ff_to_float(xx);
         wv -= red[1] * ixx * xh;
         if (have_p) {
             pv -= red[2] * ixx * xh;
             apv -= red[2] * ixx * ff_to_float(ax);
         }
-        // (d) A w
+        // (c) A w
         if (lead) ws[row] = wv;
         __syncthreads();
         const float awv = f_row(Ah, ld, n, row, kk, tpr, act, ws);
-        // (e) projections on span{x, w, p}
-        float pr[8] = {r * wv, r * pv, wv * awv, wv * apv, pv * apv, wv * wv, wv * pv, pv * pv};
+        // (d) projections on span{x, w, p}, the pencil shifted by theta: its x row is
+        //     (A x - theta x) . [x, w, p] = [0, r.w, r.p]
+        const float aws = awv - th * wv, aps = apv - th * pv;
+        float pr[8] = {r * wv, r * pv, wv * aws, wv * aps, pv * aps, wv * wv, wv * pv, pv * pv};
         if (!lead)
 #pragma unroll
             for (int q = 0; q < 8; ++q) pr[q] = 0.0f;
         bsum_f<8>(pr, s_rf, hf);
-        const float rw = pr[0], rp = pr[1], waw = pr[2], wap = pr[3], pap = pr[4], ww = pr[5], wp = pr[6], pp = pr[7];
-        // (f) Rayleigh-Ritz with the pencil shifted by theta, in the basis
-        //     x / |x|, w / |w|, and p orthogonalised against w
-        const float ix = sqrtf(ixx);
+        // Rayleigh-Ritz: the lowest eigenpair of (P - mu G) y = 0 with P = [0 rw rp; rw sww swp;
+        // rp swp spp] and the Gram matrix G (x orthogonal to w and p), by the Cholesky factor L of
+        // G: C = L^-1 P L^-T, y = L^-T v
+        const float rw = pr[0], rp = pr[1], sww = pr[2], swp = pr[3], spp = pr[4];
+        const float gxx = ff_to_float(xx), gxw = 0.0f, gxp = 0.0f, gww = pr[5], gwp = pr[6], gpp = pr[7];
         float yx = 1.0f, yw = 0.0f, yp = 0.0f;
-        if (ww > 0.0f) {
-            const float l11 = sqrtf(ww);
-            const float il11 = 1.0f / l11;
-            const float a0 = rw * il11 * ix;
-            const float hww = (waw - th * ww) * il11 * il11;
-            float l21 = 0.0f, l22sq = 0.0f;
-            bool use_p = have_p && pp > 0.0f;
+        const float l00 = sqrtf(gxx), il00 = 1.0f / l00;
+        const float l10 = gxw * il00, l20 = gxp * il00;
+        const float d11 = gww - l10 * l10;
+        if (d11 > 1e-12f * gww && gww > 0.0f) {
+            const float l11 = sqrtf(d11), il11 = 1.0f / l11;
+            bool use_p = have_p && gpp > 0.0f;
+            float l21 = 0.0f, l22 = 0.0f, il22 = 0.0f;
             if (use_p) {
-                l21 = wp * il11;
-                l22sq = pp - l21 * l21;
-                use_p = l22sq > 1e-6f * pp;
+                l21 = (gwp - l20 * l10) * il11;
+                const float d22 = gpp - l20 * l20 - l21 * l21;
+                use_p = d22 > 1e-6f * gpp;
+                if (use_p) { l22 = sqrtf(d22); il22 = 1.0f / l22; }
             }
+            // M = L^-1 P (rows), then C = M L^-T
+            const float m00 = 0.0f, m01 = rw * il00, m02 = rp * il00;
+            const float m10 = (rw - l10 * m00) * il11, m11 = (sww - l10 * m01) * il11, m12 = (swp - l10 * m02) * il11;
+            const float c00 = m00 * il00;
+            const float c01 = (m01 - l10 * c00) * il11;
+            const float c11 = (m11 - l10 * (m10 * il00)) * il11;
+            float v0, v1, v2 = 0.0f, lam;
             if (use_p) {
-                const float il22 = rsqrtf(l22sq);
-                // L^-1 [rw rp]^T and L^-1 H' L^-T for L = [l11 0; l21 l22]
-                const float a1 = (rp * ix - l21 * a0) * il22;
-                const float hwp = ((wap - th * wp) * il11 - l21 * hww) * il22;
-                const float hpp = ((pap - th * pp) - 2.0f * l21 * (wap - th * wp) * il11 + l21 * l21 * hww) * il22 * il22;
-                float lam, v0, v1, v2;
-                sym3_lowest(0.0f, a0, a1, hww, hwp, hpp, lam, v0, v1, v2);
-                if (v0 < 0.0f) { v0 = -v0; v1 = -v1; v2 = -v2; }
-                yx = v0 * ix;
+                const float m20 = (rp - l20 * m00 - l21 * m10) * il22;
+                const float m21 = (swp - l20 * m01 - l21 * m11) * il22;
+                const float m22 = (spp - l20 * m02 - l21 * m12) * il22;
+                const float c02 = (m02 - l20 * c00 - l21 * c01) * il22;
+                const float c12 = (m12 - l20 * (m10 * il00) - l21 * c11) * il22;
+                const float c22 = (m22 - l20 * (m20 * il00) - l21 * ((m21 - l10 * (m20 * il00)) * il11)) * il22;
+                sym3_lowest(c00, c01, c02, c11, c12, c22, lam, v0, v1, v2);
                 yp = v2 * il22;
                 yw = (v1 - l21 * yp) * il11;
+                yx = (v0 - l10 * yw - l20 * yp) * il00;
             } else {
-                float lam, v0, v1;
-                sym2_lowest(0.0f, a0, hww, lam, v0, v1);
-                if (v0 < 0.0f) { v0 = -v0; v1 = -v1; }
-                yx = v0 * ix;
+                sym2_lowest(c00, c01, c11, lam, v0, v1);
                 yw = v1 * il11;
+                yx = (v0 - l10 * yw) * il00;
                 yp = 0.0f;
             }
+            if (yx < 0.0f) { yx = -yx; yw = -yw; yp = -yp; }
         }
-        // (g) x <- yx x + yw w + yp p, p <- yw w + yp p (unit length), A p likewise
+        // (e) x <- yx x + yw w + yp p, A x likewise; p <- yw w + yp p (unit length), A p likewise
         const float np = yw * wv + yp * pv;
         const float nap = yw * awv + yp * apv;
-        const float pn2 = yw * yw * ww + 2.0f * yw * yp * wp + yp * yp * pp;
+        const float pn2 = yw * yw * gww + 2.0f * yw * yp * gwp + yp * yp * gpp;
         x = ff_add(ff_mul_f(x, yx), ff{np, 0.0f});
+        ax = ff_add(ff_mul_f(ax, yx), ff{nap, 0.0f});
+        exact = false;
         if (pn2 > 0.0f) {
             const float ip = rsqrtf(pn2);
             pv = np * ip;
@@ -1254,7 +1284,8 @@ __device__ __forceinline__ bool mark_set_keep(const Problem &P, long long s, uns
 // and the values (two 16-byte loads of one slot cost two accesses of random
 // slots on this memory system).  L2 only, re-read on every call.
 __device__ __forceinline__ void ld_slot(const Slot *s, unsigned long long &ka, unsigned long long &kb, double &c) {
-    unsigned long long cb, bb;
+    unsigned long long cb;
+    [[maybe_unused]] unsigned long long bb;
     asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
                  : "=l"(ka), "=l"(kb), "=l"(cb), "=l"(bb)
                  : "l"(s));

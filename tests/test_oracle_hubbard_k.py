@@ -105,6 +105,17 @@ def test_degenerate_start_4x4_half_filling():
     assert np.max(np.abs(H - H.T)) <= 1e-14
     assert np.linalg.norm(H @ c - E * c) <= 1e-10 and abs(np.linalg.norm(c) - 1.0) <= 1e-14
     assert E <= np.min(np.diag(H)) and c[np.argmax(np.abs(c))] > 0
+    # the lowest eigenvalue is 4-fold degenerate over total momenta (0, 0) and (pi, pi); the start
+    # (the ramp projected onto the eigenspace) has a component in both sectors
+    ev = np.linalg.eigvalsh(H)
+    assert np.sum(ev <= E + 1e-9 * abs(E)) == 4
+    km = inputs.momenta((4, 4))
+    weight = {}
+    for (a, b), x in zip(keys, c):
+        K = sum(km[p] for p in range(16) if (int(a) >> p) & 1) + sum(km[p] for p in range(16) if (int(b) >> p) & 1)
+        weight[tuple(int(q) for q in np.asarray(K) % 4)] = weight.get(tuple(int(q) for q in np.asarray(K) % 4), 0.0) + x * x
+    assert set(k for k, v in weight.items() if v > 1e-12) == {(0, 0), (2, 2)}
+    assert min(v for v in weight.values() if v > 1e-12) > 0.1
 
 
 def test_degenerate_start_small_and_unique():
