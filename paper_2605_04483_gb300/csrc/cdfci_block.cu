@@ -1239,7 +1239,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
 // both first slots in flight (one call site of the lookup routine for every
 // item kind keeps the kernel's code small).
 // ---------------------------------------------------------------------------
-constexpr int kWarpCand = 192;      // per-warp buffer of new candidates (flushed above kWarpCand - 64)
+constexpr int kWarpCand = 192;      // per-warp buffer of new candidates (flushed above kWarpCand - 32 kDrainU)
 
 // L2 eviction priorities for the scatter: a table slot's last touch in a lookup
 // is the add to b (evict first after it; the slot's load keeps the normal
@@ -1386,20 +1386,21 @@ __device__ __forceinline__ void mc_flush_cand(const Problem &P, McState *ms, Ite
     __syncwarp();
 }
 
-// The queue's lookups, two per lane at a time (both first slots loaded
-// together): find the slot (insert when the rule passes), add w H to b, gather
-// H c, mark the slot as a candidate of the next selection; the lane that marks
-// it appends it to the warp's candidate buffer.
+// The queue's lookups, kDrainU per lane at a time (all their first slots in
+// flight together): find the slot (insert when the rule passes), add w H to b,
+// gather H c, mark the slot as a candidate of the next selection; the lane that
+// marks it appends it to the warp's candidate buffer.
+constexpr int kDrainU = 2;
 __device__ __forceinline__ void mc_drain(const Problem &P, McState *ms, IterState *st, long long *cand, McWarp &W) {
     const int lane = threadIdx.x & 31;
     while (W.qn > 0 && !W.err) {
         __syncwarp();
-        const int n = min(W.qn, 64), base = W.qn - n;
-        bool has[2];
-        unsigned long long oa[2], ob[2], pos[2], ka[2], kb[2];
-        double H[2], sc[2];
+        const int n = min(W.qn, 32 * kDrainU), base = W.qn - n;
+        bool has[kDrainU];
+        unsigned long long oa[kDrainU], ob[kDrainU], pos[kDrainU], ka[kDrainU], kb[kDrainU];
+        double H[kDrainU], sc[kDrainU];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kDrainU; ++u) {
             has[u] = lane + 32 * u < n;
             const int at = base + lane + 32 * u;
             oa[u] = has[u] ? W.qa[at] : 0ull;
@@ -1412,10 +1413,12 @@ __device__ __forceinline__ void mc_drain(const Problem &P, McState *ms, IterStat
         }
         __syncwarp();
         W.qn = base;
-        bool first[2] = {false, false};
-        long long s[2] = {-1, -1};
+        bool first[kDrainU];
+        long long s[kDrainU];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kDrainU; ++u) {
+            first[u] = false;
+            s[u] = -1;
             if (!has[u]) continue;
             const bool big = abs_bits(H[u]) >= W.tib;
             bool ins = false;
@@ -1434,12 +1437,12 @@ __device__ __forceinline__ void mc_drain(const Problem &P, McState *ms, IterStat
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kDrainU; ++u) {
             const unsigned int fm = __ballot_sync(0xffffffffu, first[u]);
             if (first[u]) W.wcand[W.nwc + __popc(fm & ((1u << lane) - 1u))] = s[u];
             W.nwc += __popc(fm);
         }
-        if (W.nwc > kWarpCand - 64) mc_flush_cand(P, ms, st, W.wcand, W.nwc, cand);
+        if (W.nwc > kWarpCand - 32 * kDrainU) mc_flush_cand(P, ms, st, W.wcand, W.nwc, cand);
         W.err = __any_sync(0xffffffffu, W.err);
     }
     W.qn = 0;
