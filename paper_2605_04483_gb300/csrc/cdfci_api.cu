@@ -220,11 +220,16 @@ int setup_block(cdfci_ctx *c, int m) {
     const long long cap_cand = (long long)m * nh_eff + m + 64;
     b.cap_cand = cap_cand;
     c->P.cap_cand = cap_cand;
-    b.cand_grid = 152 * 4;
     CK(mc_configure());
-    b.scatter_grid = mc_scatter_grid(P);             // the resident blocks; their warps take items from a counter
-    if (b.scatter_grid <= 0) return fail(CDFCI_ERR_CUDA, "occupancy query of the scatter failed");
     b.geom = mc_geometry(P);
+    // grids sized to the problem's work (a small problem leaves the rest of the GPU to the other
+    // problems of a batch): the scatter's warps take about two items each, at most the resident
+    // blocks; the candidate passes give every thread at least eight candidates, at most 4 blocks per SM
+    const int resident = mc_scatter_grid(P);
+    if (resident <= 0) return fail(CDFCI_ERR_CUDA, "occupancy query of the scatter failed");
+    const long long items = (long long)m * b.geom.per_col;
+    b.scatter_grid = (int)std::max<long long>(1, std::min<long long>(resident, (items + 15) / 16));
+    b.cand_grid = (int)std::max<long long>(1, std::min<long long>(152 * 4, (cap_cand + 2047) / 2048));
     const size_t ns = (size_t)b.geom.nsA + (size_t)b.geom.nsB;
     b.st = c->d_st;
     const size_t n1 = (size_t)m + 1;
