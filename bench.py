@@ -300,7 +300,7 @@ def timed_block_run(api, w, m, tau, log2_capacity, warm_iters, iters, kernel_ite
             k0 = s.stats()
             t = s.time_kernels(kernel_iters)
             k1 = s.stats()
-            kt = (t, (k1["elements"] - k0["elements"]) / kernel_iters)
+            kt = (t, (k1["elements"] - k0["elements"]) / kernel_iters, (k1["applied"] - k0["applied"]) / kernel_iters)
     finally:
         s.close()
     el = st["elements"] - st0["elements"]
@@ -309,7 +309,7 @@ def timed_block_run(api, w, m, tau, log2_capacity, warm_iters, iters, kernel_ite
            "reduced_eig_iterations_per_iteration": (st["reduced_iterations"] - st0["reduced_iterations"]) / iters,
            "energy": st["energy"], "load": st["load"]}
     if kt is not None:
-        t, el_k = kt
+        t, el_k, app_k = kt
         us = {k: v * 1e3 / kernel_iters for k, v in t.items()}
         peak, kind = measured_peaks()
         achieved = el_k * ALGO_BYTES_PER_ELEMENT / (us["scatter"] * 1e-6) / 1e9
@@ -317,7 +317,9 @@ def timed_block_run(api, w, m, tau, log2_capacity, warm_iters, iters, kernel_ite
         out["scatter_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": kind,
                                    "unit": "GB/s", "frac": achieved / peak,
                                    "algorithmic_bytes_per_element": ALGO_BYTES_PER_ELEMENT,
-                                   "elements_per_iteration": el_k, "iterations_timed": kernel_iters}
+                                   "elements_per_iteration": el_k, "iterations_timed": kernel_iters,
+                                   "applied_per_iteration": app_k,
+                                   "applied_per_s": app_k / (us["scatter"] * 1e-6)}
     return out
 
 
@@ -546,7 +548,10 @@ def batched_summary(line: dict, probe: dict) -> dict:
             "elements_per_iteration": round(sr["elements_per_iteration"]),
             "scatter_us": mc["us_per_kernel"]["scatter"], "iteration_us": round(mc["us_per_iteration"], 2),
             "achieved": round(sr["achieved"], 1), "frac": round(sr["frac"], 4),
-            "frac_of_slot_probe": round(sr["achieved"] / probe["gbs_40B"], 4),
+            "applied_per_iteration": round(sr["applied_per_iteration"]),
+            # elements that reach the table (applied: a slot read and an add each) per second of the
+            # scatter, against the probe's independent random slots per second
+            "applied_frac_of_slot_probe": round(sr["applied_per_s"] / probe["ops_per_s"], 4),
             "dram_bytes_per_element": profiled_traffic(SCATTER_PROFILE, SCATTER_SOURCES, "dram_bytes_per_element"),
             "kernel_source_hash": kernel_hash(SCATTER_SOURCES)}
     b = line.get("batch_96")

@@ -376,24 +376,40 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterSt
     const int stride = gridDim.x * blockDim.x;
     unsigned long long pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int t = base + threadIdx.x;
-        const bool ok = t < n;
-        unsigned long long k = 0ull;
-        if (ok && (unsigned long long)cand[t] >= (unsigned long long)P.capacity) {
-            set_status(st, kErrInternal);                  // a candidate outside the table: skip it
-            gkey[t] = 0ull;
-        } else if (ok) {
-            const long long slot = cand[t];
-            double2 v;                                     // c and b of a random slot: evict first from L2
-            asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
-                         : "=d"(v.x), "=d"(v.y)
-                         : "l"(&P.table[slot].c), "l"(pol));
-            k = (unsigned long long)__double_as_longlong(fma(mu, v.x, v.y)) & 0x7fffffffffffffffull;
-            gkey[t] = k;
-            mark_clear(P, slot);                           // clear the candidate mark
+    // kGkU candidates per thread and round, all their slot loads in flight together
+    constexpr int kGkU = 4;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += kGkU * stride) {
+        long long slot[kGkU];
+        bool ok[kGkU];
+        double2 v[kGkU];
+#pragma unroll
+        for (int u = 0; u < kGkU; ++u) {
+            const int t = base + u * stride + threadIdx.x;
+            ok[u] = t < n;
+            slot[u] = ok[u] ? cand[t] : 0;
         }
-        if (count) sel_bin_add(sh, ok, sel_digit(k, 0));
+#pragma unroll
+        for (int u = 0; u < kGkU; ++u) {
+            v[u] = make_double2(0.0, 0.0);
+            if (ok[u] && (unsigned long long)slot[u] < (unsigned long long)P.capacity)
+                asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"   // c and b of a random
+                             : "=d"(v[u].x), "=d"(v[u].y)                                   // slot: evict first
+                             : "l"(&P.table[slot[u]].c), "l"(pol));
+        }
+#pragma unroll
+        for (int u = 0; u < kGkU; ++u) {
+            const int t = base + u * stride + threadIdx.x;
+            unsigned long long k = 0ull;
+            if (ok[u] && (unsigned long long)slot[u] >= (unsigned long long)P.capacity) {
+                set_status(st, kErrInternal);              // a candidate outside the table: skip it
+                gkey[t] = 0ull;
+            } else if (ok[u]) {
+                k = (unsigned long long)__double_as_longlong(fma(mu, v[u].x, v[u].y)) & 0x7fffffffffffffffull;
+                gkey[t] = k;
+                mark_clear(P, slot[u]);                    // clear the candidate mark
+            }
+            if (count) sel_bin_add(sh, ok[u], sel_digit(k, 0));
+        }
     }
     if (!count) {                                      // every candidate is chosen
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -700,10 +716,12 @@ __device__ __forceinline__ void mc_build_coltab(const Problem &P, const ColLists
 // c_I, b_I, H_II, H_II c_I: one warp per selected row.  H_II goes to rows and
 // columns 1..m of R as float-float pairs (Rh, Rl; leading dimension ldr).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, const McSel *sel, double *cI,
+constexpr int kPrepWarps = 8;       // rows (warps) per block
+
+__global__ void __launch_bounds__(32 * kPrepWarps) k_mc_prepare(Problem P, McState *ms, const McSel *sel, double *cI,
                                                     double *bI, double *Hdiag, double *HIIc, float *Rh, float *Rl,
                                                     int ldr, ColEnt *coltab, ColLists *collists, int ns) {
-    __shared__ ColLists Lw[8];
+    __shared__ ColLists Lw[kPrepWarps];
     // the chosen determinants and their c (true units), staged once per block
     __shared__ unsigned long long s_A[kEigMaxN], s_B[kEigMaxN];
     __shared__ double s_c[kEigMaxN];
@@ -718,8 +736,9 @@ __global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, cons
         s_c[i] = P.table[x.slot].c * s;
     }
     __syncthreads();
-    for (int r = blockIdx.x * 8 + warp; r < m; r += gridDim.x * 8) {
+    for (int r = blockIdx.x * kPrepWarps + warp; r < m; r += gridDim.x * kPrepWarps) {
         const unsigned long long rA = s_A[r], rB = s_B[r];
+        const double b_r = lane == 0 ? P.table[sel[r].slot].bv : 0.0;     // issued early: a random slot
         ColLists &L = Lw[warp];
         for (int t = lane; t < P.N; t += 32) {
             int ra = __popcll(rA & low_mask(t)), rb = __popcll(rB & low_mask(t));
@@ -742,7 +761,7 @@ __global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, cons
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
         if (lane == 0) {
             cI[r] = s_c[r];
-            bI[r] = P.table[sel[r].slot].bv * s;
+            bI[r] = b_r * s;
             Hdiag[r] = hd;
             HIIc[r] = acc;
         }
@@ -753,46 +772,110 @@ __global__ void __launch_bounds__(256) k_mc_prepare(Problem P, McState *ms, cons
 // ---------------------------------------------------------------------------
 // The reduced problem: the lowest eigenpair of the active block A of
 // R = Q^T H Q, Q = [c~ / nu, E_I] (rows/columns 1.. only when c lies in
-// span(E_I)), on one CTA with one thread per row.
+// span(E_I)), on one CTA with one thread group per row.
 //
 // LOBPCG (Knyazev's locally optimal block preconditioned conjugate gradient)
 // for one vector, with the diagonal (Davidson) preconditioner, started from
-// the current point [nu; c_I].  x and A x are float-float; the search vectors
-// w, p and their images are FP32.  The Rayleigh-Ritz step on span{x, w, p}
-// uses the float-float residual r = A x - theta x for the x-couplings
-// (x^T A w = r^T w once w is orthogonal to x), so the iteration converges to
-// the accuracy of the float-float residual, about 1e-14 relative, with all
-// vector arithmetic on the FP32 pipe.
+// the current point x = [nu; c_I], whose image is known without a product:
+// (A x)_i = nu R_i0 + (H_II c_I)_i = b_i and (A x)_0 = (alpha - c_I.b_I) / nu.
+// x and A x are float-float; the search vectors w, p and their images are
+// FP32.  The Rayleigh-Ritz step on span{x, w, p} uses the float-float residual
+// r = A x - theta x for the x-couplings (x^T A w = r^T w once w is orthogonal
+// to x), so the iteration converges to the accuracy of the float-float
+// residual, about 1e-14 relative, with all vector arithmetic on the FP32 pipe.
+// FP64 is kept to the few scalars that need its range or its cancellation-free
+// sums; on this part a dependent FP64 operation costs far more than an FP32 one.
+//
+// Vectors are held in the absolute indexing of R (entry 0 is the direction
+// c~ / nu, zero when it is not active) and padded with zeros to a multiple of
+// 4 entries, so that a row of A times a vector reads 16 bytes per load along
+// the row (R is symmetric).
 // ---------------------------------------------------------------------------
 constexpr int kEigSmemN = 160;      // A in shared memory (hi and lo) up to this size
 constexpr int kEigMaxIt = 200;
 
-// Row `row` of A times a vector: this thread's share, the columns j = k,
-// k + tpr, ... (k = its rank in the row's group of tpr threads); A(i, j) is
-// read at j * ld + i (A is symmetric), so a warp's groups read consecutive i.
-__device__ __forceinline__ ff ff_row_part(const float *Ah, const float *Al, int ld, int n, int row, int k, int tpr,
-                                          const float *xs) {
-    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
-    int j = k;
-    for (; j + tpr < n; j += 2 * tpr) {
-        ff_mac(h0, l0, Ah[j * ld + row], Al[j * ld + row], ff{xs[2 * j], xs[2 * j + 1]});
-        const int j2 = j + tpr;
-        ff_mac(h1, l1, Ah[j2 * ld + row], Al[j2 * ld + row], ff{xs[2 * j2], xs[2 * j2 + 1]});
-    }
-    if (j < n) ff_mac(h0, l0, Ah[j * ld + row], Al[j * ld + row], ff{xs[2 * j], xs[2 * j + 1]});
-    return ff_add(ff_norm(h0, l0), ff_norm(h1, l1));
+// Threads per row of the reduced problem and the shared-memory row stride for
+// a problem of size n1 = m + 1 (columns padded to ldr, a multiple of 32).
+// 2 threads per row up to 160 rows (cheaper block sums; R in shared memory),
+// 4 up to 256, then 2, then 1.  The stride ldr + 4 tpr puts the 16-byte loads
+// of a quarter warp (8 lanes: 8 / tpr rows, tpr chunks each) on distinct banks.
+__host__ __device__ __forceinline__ int eig_tpr(int n1) {
+    return n1 <= kEigSmemN ? 2 : (n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1));
 }
-__device__ __forceinline__ float f_row_part(const float *Ah, int ld, int n, int row, int k, int tpr, const float *ws) {
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    int j = k;
-    for (; j + 3 * tpr < n; j += 4 * tpr) {
-        a0 = fmaf(Ah[j * ld + row], ws[j], a0);
-        a1 = fmaf(Ah[(j + tpr) * ld + row], ws[j + tpr], a1);
-        a2 = fmaf(Ah[(j + 2 * tpr) * ld + row], ws[j + 2 * tpr], a2);
-        a3 = fmaf(Ah[(j + 3 * tpr) * ld + row], ws[j + 3 * tpr], a3);
+__host__ __device__ __forceinline__ int eig_lds(int ldr, int tpr) { return ldr + 4 * tpr; }
+// entries of a vector in absolute indexing, a multiple of 4
+__host__ __device__ __forceinline__ int eig_len(int n1) { return 4 * ((n1 + 3) / 4); }
+
+// Row ra of R times a vector v (absolute indexing, nq chunks of 4 entries):
+// this thread's share, the chunks q = k, k + tpr, ... (k = its rank in the
+// row's group of tpr threads), U chunks of A in flight per round.
+template <int U>
+__device__ __forceinline__ float f_row_part(const float *A, int ld, int nq, int ra, int k, int tpr, const float *v) {
+    const float4 *a4 = reinterpret_cast<const float4 *>(A + (size_t)ra * ld);
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+    float acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0f;
+    int q = k;
+    for (; q + (U - 1) * tpr < nq; q += U * tpr) {
+        float4 av[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) av[u] = a4[q + u * tpr];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float4 x = v4[q + u * tpr];
+            acc[u] = fmaf(av[u].x, x.x, acc[u]);
+            acc[u] = fmaf(av[u].y, x.y, acc[u]);
+            acc[u] = fmaf(av[u].z, x.z, acc[u]);
+            acc[u] = fmaf(av[u].w, x.w, acc[u]);
+        }
     }
-    for (; j < n; j += tpr) a0 = fmaf(Ah[j * ld + row], ws[j], a0);
-    return (a0 + a1) + (a2 + a3);
+    for (; q < nq; q += tpr) {
+        const float4 a = a4[q], x = v4[q];
+        acc[0] = fmaf(a.x, x.x, acc[0]);
+        acc[0] = fmaf(a.y, x.y, acc[0]);
+        acc[0] = fmaf(a.z, x.z, acc[0]);
+        acc[0] = fmaf(a.w, x.w, acc[0]);
+    }
+    float t = acc[0];
+#pragma unroll
+    for (int u = 1; u < U; ++u) t += acc[u];
+    return t;
+}
+// the same for float-float A (hi, lo) and x (pairs x[2 j], x[2 j + 1])
+template <int U>
+__device__ __forceinline__ ff ff_row_part(const float *Ah, const float *Al, int ld, int nq, int ra, int k, int tpr,
+                                          const float *x) {
+    const float4 *h4 = reinterpret_cast<const float4 *>(Ah + (size_t)ra * ld);
+    const float4 *l4 = reinterpret_cast<const float4 *>(Al + (size_t)ra * ld);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float sh[2] = {0.0f, 0.0f}, sl[2] = {0.0f, 0.0f};
+    int q = k;
+    for (; q + (U - 1) * tpr < nq; q += U * tpr) {
+        float4 hv[U], lv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            hv[u] = h4[q + u * tpr];
+            lv[u] = l4[q + u * tpr];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = q + u * tpr, a = u & 1;
+            const float4 xa = x4[2 * c], xb = x4[2 * c + 1];
+            ff_mac(sh[a], sl[a], hv[u].x, lv[u].x, ff{xa.x, xa.y});
+            ff_mac(sh[a], sl[a], hv[u].y, lv[u].y, ff{xa.z, xa.w});
+            ff_mac(sh[a], sl[a], hv[u].z, lv[u].z, ff{xb.x, xb.y});
+            ff_mac(sh[a], sl[a], hv[u].w, lv[u].w, ff{xb.z, xb.w});
+        }
+    }
+    for (; q < nq; q += tpr) {
+        const float4 h = h4[q], l = l4[q], xa = x4[2 * q], xb = x4[2 * q + 1];
+        ff_mac(sh[0], sl[0], h.x, l.x, ff{xa.x, xa.y});
+        ff_mac(sh[0], sl[0], h.y, l.y, ff{xa.z, xa.w});
+        ff_mac(sh[0], sl[0], h.z, l.z, ff{xb.x, xb.y});
+        ff_mac(sh[0], sl[0], h.w, l.w, ff{xb.z, xb.w});
+    }
+    return ff_add(ff_norm(sh[0], sl[0]), ff_norm(sh[1], sl[1]));
 }
 // sums over the tpr lanes of a row's group (xor butterfly: sums of commutative
 // pairs, identical in every lane of the group)
@@ -805,24 +888,35 @@ __device__ __forceinline__ float f_group_sum(float v, int tpr) {
     for (int o = 1; o < tpr; o <<= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-// A x (float-float) and A w (FP32) for the row; every lane of the group holds it
-__device__ __forceinline__ ff ff_row(const float *Ah, const float *Al, int ld, int n, int row, int k, int tpr,
-                                     bool act, const float *xs) {
-    return ff_group_sum(act ? ff_row_part(Ah, Al, ld, n, row, k, tpr, xs) : ff{0.0f, 0.0f}, tpr);
+// A x (float-float) and A w (FP32) for the row; every lane of the group holds
+// it.  R in shared memory: 2 (float-float) or 4 (FP32) chunks per round; in
+// global memory (L2): 4 or 8, for more loads in flight.
+__device__ __forceinline__ ff ff_row(const float *Ah, const float *Al, int ld, int nq, int ra, int k, int tpr,
+                                     bool act, bool smem, const float *x) {
+    ff v = {0.0f, 0.0f};
+    if (act) v = smem ? ff_row_part<2>(Ah, Al, ld, nq, ra, k, tpr, x) : ff_row_part<4>(Ah, Al, ld, nq, ra, k, tpr, x);
+    return ff_group_sum(v, tpr);
 }
-__device__ __forceinline__ float f_row(const float *Ah, int ld, int n, int row, int k, int tpr, bool act,
-                                       const float *ws) {
-    return f_group_sum(act ? f_row_part(Ah, ld, n, row, k, tpr, ws) : 0.0f, tpr);
+__device__ __forceinline__ float f_row(const float *Ah, int ld, int nq, int ra, int k, int tpr, bool act, bool smem,
+                                       const float *w) {
+    float v = 0.0f;
+    if (act) v = smem ? f_row_part<4>(Ah, ld, nq, ra, k, tpr, w) : f_row_part<8>(Ah, ld, nq, ra, k, tpr, w);
+    return f_group_sum(v, tpr);
 }
 
-// Threads per row of the reduced problem and the shared-memory row stride for
-// a problem of size n1 = m + 1 (columns padded to ldr).
-// 2 threads per row up to 150 rows (cheaper block sums, measured faster; with the wider row padding R
-// still fits in shared memory), 4 up to 256, then 2, then 1.
-__host__ __device__ __forceinline__ int eig_tpr(int n1) {
-    return n1 <= 150 ? 2 : (n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1));
+// float-float 1 / sqrt(a), a > 0 and normal in FP32: the FP32 estimate and two
+// Newton steps y <- y + y (1 - a y^2) / 2 (Newton's iteration for the inverse
+// square root), the residual 1 - a y^2 formed in float-float; each step about
+// doubles the correct bits, up to the format's ~48.
+__device__ __forceinline__ ff ff_rsqrt(ff a) {
+    ff y = {rsqrtf(a.hi), 0.0f};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const ff e = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul(a, ff_mul(y, y))));
+        y = ff_add(y, ff_mul_f(y, 0.5f * e.hi));
+    }
+    return y;
 }
-__host__ __device__ __forceinline__ int eig_lds(int ldr, int tpr) { return ldr + 32 / tpr; }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -843,42 +937,50 @@ __device__ __forceinline__ void red_warp(double (&v)[K], double *scr, int nw) {
 #pragma unroll
         for (int k = 0; k < K; ++k) scr[warp * K + k] = v[k];
 }
+// (warp 0, after the barrier) the xor butterfly over the nw partials; its
+// levels at and above the next power of two of nw only add zeros to lane 0,
+// so they are skipped, and lane 0's sum goes to every lane
 template <int K>
-__device__ __forceinline__ void red_sum(double (&v)[K], const double *scr, int nw) {   // warp 0, after the barrier
+__device__ __forceinline__ void red_sum(double (&v)[K], const double *scr, int nw) {
     const int lane = threadIdx.x & 31;
+    int top = 1;
+    while (top < nw) top <<= 1;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         double t = lane < nw ? scr[lane * K + k] : 0.0;
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        v[k] = t;
+        for (int off = top >> 1; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        v[k] = __shfl_sync(0xffffffffu, t, 0);
     }
 }
 
+// Dynamic shared memory of k_mc_eigen, in floats: A (hi, lo) when it fits,
+// then x (float-float), w, z (FP64) and a staging area, each of eig_len(m + 1)
+// entries in absolute indexing.
+__host__ __device__ __forceinline__ size_t eig_vec_floats(int n1) { return 7 * (size_t)eig_len(n1); }
+
 __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                        const double *cI, const double *bI, const double *HIIc,
-                                                       float *Rh, float *Rl, int ldr, int tpr, int use_smem,
-                                                       double *w, double *thr, double *etaout) {
+                                                       const double *Hdiag, float *Rh, float *Rl, int ldr, int tpr,
+                                                       int use_smem, double *w, double *thr, double *etaout) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float s_rf[2 * 32 * 16];
     __shared__ ff s_rff[2 * 32 * 2];
     __shared__ double s_red[32 * 4];
+    __shared__ ff s_row0[4];                            // nu, R_00, (A x)_0 of the start, 1 / nu
     __shared__ double s_sc[8];
-    __shared__ dd s_snew;
-    __shared__ int s_nzr[2][32];
+    __shared__ float s_drms;
+    __shared__ int s_nzr[32], s_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
     const int wm = (m + 31) >> 5;                       // warps holding a coordinate of I (thread t: coordinate t)
     // the state scalars, loaded (thread 0) ahead of the sums; read after the barriers below
     __shared__ dd s_mu0, s_al0, s_sc0;
-    __shared__ long long s_nnz0, s_its0, s_eit0;
-    __shared__ double s_dx0;
-    if (tid == 0) {
-        s_mu0 = ms->mu; s_al0 = ms->alpha; s_sc0 = ms->scale;
-        s_nnz0 = ms->nnz_c; s_its0 = ms->iterations; s_eit0 = ms->eig_iters_total; s_dx0 = ms->dx;
-    }
+    __shared__ long long s_nnz0;
+    if (tid == 0) { s_mu0 = ms->mu; s_al0 = ms->alpha; s_sc0 = ms->scale; s_nnz0 = ms->nnz_c; }
     int hf = 0, hff = 0;
     const int lds = eig_lds(ldr, tpr);
+    const int L = eig_len(m + 1), nq = L / 4;
     float *sh = sm, *sl = sm + (size_t)(m + 1) * lds;
     // 0. start the copy of R (rows 0..m) into shared memory; it completes behind step 1
     if (use_smem) {
@@ -891,111 +993,127 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         }
     }
     float *vec = use_smem ? sm + 2 * (size_t)(m + 1) * lds : sm;
-    double *s_cI = reinterpret_cast<double *>(vec + 4 * ((3 * (m + 1) + 3) / 4) + 2 * (m + 1));   // m doubles
+    float *xs = vec;                                    // float-float x (2 L floats)
+    float *ws = vec + 2 * L;                            // FP32 w (L floats)
+    double *zd = reinterpret_cast<double *>(vec + 3 * L);   // z (L doubles); first the start's A x (float-float)
+    float *hs = vec + 5 * L;                            // the start's H_II c_I (float-float, 2 L floats)
+    const float *Ah = use_smem ? sh : Rh, *Al = use_smem ? sl : Rl;
+    const int ld = use_smem ? lds : ldr;
 
-    // 1. scalars over I (FP64): nonzeros, c.c, c.b, c.H_II c; the degenerate case
-    //    (c has no support outside I); nu = |c - E_I c_I|; R_00
-    double ct = 0.0, bt = 0.0, ht = 0.0;
-    if (tid < m) { ct = cI[tid]; bt = bI[tid]; ht = HIIc[tid]; s_cI[tid] = ct; }
+    // 1. sums over I (FP64): c.c, c.b, c.H_II c, |diag H_II|^2, nonzeros; the
+    //    coordinates' start values staged at their absolute index i + 1
+    double ct = 0.0, bt = 0.0, ht = 0.0, hd = 0.0;
+    if (tid < m) { ct = cI[tid]; bt = bI[tid]; ht = HIIc[tid]; hd = Hdiag[tid]; }
     {
-        double v[3] = {ct * ct, ct * bt, ct * ht};
-        red_warp<3>(v, s_red, wm);
+        double v[4] = {ct * ct, ct * bt, ct * ht, hd * hd};
+        red_warp<4>(v, s_red, wm);
         const int nzw = __reduce_add_sync(0xffffffffu, (tid < m && ct != 0.0) ? 1 : 0);
-        if (lane == 0) s_nzr[0][warp] = nzw;
+        if (lane == 0) s_nzr[warp] = nzw;
     }
+    const ff bh_f = ff_from_double(bt - ht);            // nu R_0i = b_i - (H_II c_I)_i
+    if (tid < m) {
+        const ff c_f = ff_from_double(ct), b_f = ff_from_double(bt), h_f = ff_from_double(ht);
+        const int a = tid + 1;
+        xs[2 * a] = c_f.hi; xs[2 * a + 1] = c_f.lo;
+        float *az = reinterpret_cast<float *>(zd);
+        az[2 * a] = b_f.hi; az[2 * a + 1] = b_f.lo;
+        hs[2 * a] = h_f.hi; hs[2 * a + 1] = h_f.lo;
+    }
+    for (int t = m + 1 + tid; t < L; t += blockDim.x) { xs[2 * t] = 0.0f; xs[2 * t + 1] = 0.0f; ws[t] = 0.0f; }
+    if (tid == 0) { xs[0] = 0.0f; xs[1] = 0.0f; ws[0] = 0.0f; }
     __syncthreads();
+    // 2. warp 0: nu^2 = mu - c.c (lane 0), nu^2 R_00 = alpha - 2 c.b + c.H c (lane 1) and
+    //    nu (A x)_0 = alpha - c.b (lane 2) as compensated sums (TwoSum), all three in the same
+    //    instructions; the degenerate case (c has no support outside I); 1 / nu (FP64 rsqrt),
+    //    then nu, R_00 and (A x)_0 (float-float)
     if (warp == 0) {
-        double v[3];
-        red_sum<3>(v, s_red, wm);
+        double v[4];
+        red_sum<4>(v, s_red, wm);
         int nz = 0;
-        for (int q = 0; q < wm; ++q) nz += s_nzr[0][q];
+        for (int q = 0; q < wm; ++q) nz += s_nzr[q];
+        const dd a = lane == 0 ? s_mu0 : s_al0;
+        const double p = lane == 0 ? -v[0] : (lane == 1 ? -2.0 * v[1] : -v[1]);
+        const double q = lane == 1 ? v[2] : 0.0;
+        const dd s1 = dd_two_sum(a.hi, p), s2 = dd_two_sum(s1.hi, q);
+        const double r = s2.hi + ((s1.lo + s2.lo) + a.lo);
+        const double nu2 = __shfl_sync(0xffffffffu, r, 0);
+        const bool deg = (nz >= s_nnz0) || !(nu2 > 0.0);
+        const double inu = deg ? 0.0 : rsqrt(nu2);
+        const double y = (lane == 3 ? 1.0 : r) * inu * (lane == 1 ? inu : 1.0);   // nu, R_00, (A x)_0, 1 / nu
+        const ff yf = ff_from_double(y);
+        if (lane < 4) s_row0[lane] = yf;
+        const float r00 = __shfl_sync(0xffffffffu, yf.hi, 1);
         if (lane == 0) {
-            const double cc = v[0], cb = v[1], chc = v[2];
-            const dd nu2 = dd_add(s_mu0, dd{-cc, 0.0});
-            const bool deg = (nz >= s_nnz0) || !(nu2.hi > 0.0);
             s_sc[0] = deg ? 1.0 : 0.0;
-            s_sc[1] = deg ? 0.0 : sqrt(nu2.hi);
-            s_sc[2] = deg ? 0.0 : dd_div_to_d(dd_add(dd_add(s_al0, dd{-2.0 * cb, 0.0}), dd{chc, 0.0}), nu2);
-            s_sc[3] = cc;
+            s_sc[1] = inu;
+            s_sc[2] = v[0];
+            const float n = (float)(m + (deg ? 0 : 1));
+            s_drms = sqrtf((__double2float_rn(v[3]) + (deg ? 0.0f : r00 * r00)) / n);
         }
     }
     if (use_smem) cp_async_wait_all();
     __syncthreads();                                    // scalars, and this block's copy of R, complete
     const bool deg = s_sc[0] != 0.0;
-    const double nu = s_sc[1];
     const int off = deg ? 1 : 0;
     const int n = m + 1 - off;                          // active size
-    const int k0 = 1 - off;                             // active index of coordinate 0
-    // row and column 0 of R: R_0i = (b_i - (H_II c_I)_i) / nu
-    if (!deg) {
-        if (tid < m) {
-            const ff r0 = ff_from_double((bt - ht) / nu);
-            if (use_smem) {
-                sh[tid + 1] = r0.hi; sl[tid + 1] = r0.lo;
-                sh[(tid + 1) * lds] = r0.hi; sl[(tid + 1) * lds] = r0.lo;
-            } else {
-                Rh[tid + 1] = r0.hi; Rl[tid + 1] = r0.lo;
-                Rh[(size_t)(tid + 1) * ldr] = r0.hi; Rl[(size_t)(tid + 1) * ldr] = r0.lo;
-            }
-        }
-        if (tid == 0) {
-            const ff r00 = ff_from_double(s_sc[2]);
-            if (use_smem) { sh[0] = r00.hi; sl[0] = r00.lo; }
-            else { Rh[0] = r00.hi; Rl[0] = r00.lo; }
-        }
+    // row and column 0 of R: R_0i = (b_i - (H_II c_I)_i) / nu (zero when not active); they are
+    // first read by the product A w after the barriers of the first sums below
+    if (tid < m) {
+        const ff r0 = deg ? ff{0.0f, 0.0f} : ff_mul(bh_f, s_row0[3]);
+        float *Wh = use_smem ? sh : Rh, *Wl = use_smem ? sl : Rl;
+        const int ldw = use_smem ? lds : ldr;
+        Wh[tid + 1] = r0.hi; Wl[tid + 1] = r0.lo;
+        Wh[(size_t)(tid + 1) * ldw] = r0.hi; Wl[(size_t)(tid + 1) * ldw] = r0.lo;
     }
-    const float *Ah, *Al;
-    int ld;
-    if (use_smem) {
-        Ah = sh + off * lds + off;
-        Al = sl + off * lds + off;
-        ld = lds;
-    } else {
-        Ah = Rh + (size_t)off * ldr + off;
-        Al = Rl + (size_t)off * ldr + off;
-        ld = ldr;
+    if (tid == 0) {
+        const ff r00 = deg ? ff{0.0f, 0.0f} : s_row0[1];
+        if (use_smem) { sh[0] = r00.hi; sl[0] = r00.lo; }
+        else { Rh[0] = r00.hi; Rl[0] = r00.lo; }
     }
-    float *xs = vec;                                    // float-float x (2 n floats)
-    float *ws = vec + 2 * n;                            // FP32 w (n floats)
-    double *zd = reinterpret_cast<double *>(vec + 4 * ((3 * n + 3) / 4));   // n doubles
 
-    // 2. start: x = [nu; c_I] / |.|; one row per group of tpr threads, the
-    //    group's first lane (lead) speaks for the row in sums
+    // 3. the start: row group `row` (active index), absolute index ra = row + off; the group's
+    //    first lane (lead) speaks for the row in sums.  x = [nu; c_I] (not normalised) and A x in
+    //    closed form; degenerate: x = c_I, A x = H_II c_I; c = 0 (not reached in practice):
+    //    x = e_0 with A x computed
     const int row = tid / tpr, kk = tid - row * tpr;
     const bool act = row < n, lead = act && kk == 0;
-    const double zz0 = (deg ? 0.0 : nu * nu) + s_sc[3];
-    const double inv0 = zz0 > 0.0 ? 1.0 / sqrt(zz0) : 0.0;
-    ff x = {0.0f, 0.0f};
+    const int ra = row + off;
+    const bool zero_start = deg && !(s_sc[2] > 0.0);
+    ff x = {0.0f, 0.0f}, ax = {0.0f, 0.0f};
+    float d = 0.0f;
     if (act) {
-        const double v0 = (row < k0) ? nu : s_cI[row - k0];
-        x = ff_from_double(zz0 > 0.0 ? v0 * inv0 : (row == 0 ? 1.0 : 0.0));
+        if (zero_start) {
+            x = ff{row == 0 ? 1.0f : 0.0f, 0.0f};
+        } else if (ra == 0) {
+            x = s_row0[0];
+            ax = s_row0[2];
+        } else {
+            x = ff{xs[2 * ra], xs[2 * ra + 1]};
+            const float *az = deg ? hs : reinterpret_cast<const float *>(zd);
+            ax = ff{az[2 * ra], az[2 * ra + 1]};
+        }
+        d = ra == 0 ? s_row0[1].hi : Ah[(size_t)ra * ld + ra];
     }
-    __syncthreads();                                    // row and column 0 of A are in place
-    const float d = act ? Ah[row * ld + row] : 0.0f;
+    const bool smem = use_smem != 0;
     float pv = 0.0f, apv = 0.0f;                        // search direction p and A p
     bool have_p = false;
     ff theta = {0.0f, 0.0f}, xx = {1.0f, 0.0f};
     float best = 3.0e38f;
     int stall = 0, it = 0;
-    float drms;                                         // RMS of diag A, a scale for the tests below
-    {
-        float t[1] = {lead ? d * d : 0.0f};
-        bsum_f<1>(t, s_rf, hf);
-        drms = sqrtf(t[0] / (float)n);
-    }
-    // A x in float-float for the start; afterwards A x follows x implicitly (x <- yx x + yw w + yp p
-    // gives A x <- yx A x + yw A w + yp A p, the last two in FP32) and is recomputed exactly each time
-    // the residual falls below `refresh` (relative), and always before convergence is accepted:
-    // an implicit A x drifts by about the FP32 rounding of the steps taken since the last exact one.
-    ff ax = {0.0f, 0.0f};
-    bool exact = false, want_exact = true;
+    const float drms = s_drms;                          // RMS of diag A, a scale for the tests below
+    // A x follows x implicitly (x <- yx x + yw w + yp p gives A x <- yx A x + yw A w + yp A p, the
+    // last two in FP32) and is recomputed exactly each time the residual falls below `refresh`
+    // (relative), and always before convergence is accepted: an implicit A x drifts by about the
+    // FP32 rounding of the steps taken since the last exact one (and the closed-form start's by
+    // the float-float rounding of R)
+    bool exact = false, want_exact = zero_start;
     float refresh = 1e-6f;
     for (;; ++it) {
         // A x recomputed exactly for the current x when asked for
         if (want_exact) {
-            if (lead) { xs[2 * row] = x.hi; xs[2 * row + 1] = x.lo; }
+            if (lead) { xs[2 * ra] = x.hi; xs[2 * ra + 1] = x.lo; }
             __syncthreads();
-            ax = ff_row(Ah, Al, ld, n, row, kk, tpr, act, xs);
+            ax = ff_row(Ah, Al, ld, nq, ra, kk, tpr, act, smem, xs);
             exact = true;
             want_exact = false;
         }
@@ -1031,7 +1149,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             refresh = fminf(refresh, nres / fmaxf(scale, 1e-30f)) * 1e-3f;
             if (stop) { best = 3.0e38f; stall = 0; }
         }
-        // w and p orthogonalised against x (x.x ~ 1)
+        // w and p orthogonalised against x
         const float ixx = 1.0f / ff_to_float(xx);
         wv -= red[1] * ixx * xh;
         if (have_p) {
@@ -1039,9 +1157,9 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             apv -= red[2] * ixx * ff_to_float(ax);
         }
         // (c) A w
-        if (lead) ws[row] = wv;
+        if (lead) ws[ra] = wv;
         __syncthreads();
-        const float awv = f_row(Ah, ld, n, row, kk, tpr, act, ws);
+        const float awv = f_row(Ah, ld, nq, ra, kk, tpr, act, smem, ws);
         // (d) projections on span{x, w, p}, the pencil shifted by theta: its x row is
         //     (A x - theta x) . [x, w, p] = [0, r.w, r.p]
         const float aws = awv - th * wv, aps = apv - th * pv;
@@ -1111,108 +1229,161 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             pv = 0.0f; apv = 0.0f; have_p = false;
         }
     }
-    // 3. z = sqrt(-lambda) x / |x| (FP64); the reduced problem needs lambda < 0
-    const double lamd = ff_to_double(theta);
-    if (!(lamd < 0.0)) {
+    // 4. z = zs x, zs = sqrt(-lambda / x.x) (float-float); the reduced problem needs lambda < 0
+    if (!(theta.hi < 0.0f || (theta.hi == 0.0f && theta.lo < 0.0f))) {
         if (tid == 0) set_status(st, kErrNotNegative);
         return;
     }
-    if (lead) zd[row] = ff_to_double(x);
-    __syncthreads();
-    // sign (Eq. def-z wants gamma >= 0): z_0 >= 0; degenerate or z_0 = 0: z . [nu; c_I] >= 0;
-    // gamma, the new scale and its reciprocal (warp 0; the scaling by |z| / |x| > 0 keeps the signs)
-    if (warp == 0) {
-        double dot = 0.0;
-        for (int i = lane; i < m; i += 32) dot = fma(zd[i + k0], s_cI[i], dot);
-        dot = wsum_d(dot);
-        if (lane == 0) {
-            const double zs = sqrt(-lamd / ff_to_double(xx));
-            const double z0 = deg ? 0.0 : zd[0] * zs;
-            const double sgn = (z0 < 0.0 || (z0 == 0.0 && dot < 0.0)) ? -1.0 : 1.0;
-            const double gamma = deg ? 1.0 : sgn * z0 / nu;
-            const dd s_new = dd_mul_d(s_sc0, gamma);
-            s_sc[4] = sgn;
-            s_sc[5] = gamma;
-            s_sc[6] = zs;
-            s_sc[7] = 1.0 / s_new.hi;
-            s_snew = s_new;
-        }
+    const ff q = ff_div(ff_neg(theta), xx);
+    const ff zs_f = ff_mul(q, ff_rsqrt(q));
+    if (lead) zd[ra] = ff_to_double(x);
+    // sign (Eq. def-z wants gamma >= 0): z_0 >= 0 (thread 0 holds row 0); degenerate or z_0 = 0:
+    // z . c_I >= 0, the FP64 dot taken only then; gamma = z_0 / nu
+    if (tid == 0) {
+        const ff z0 = deg ? ff{0.0f, 0.0f} : ff_mul(zs_f, x);
+        s_flag = (deg || z0.hi == 0.0f) ? 1 : 0;
+        s_sc[3] = z0.hi < 0.0f ? -1.0 : 1.0;
+        const ff g = ff_mul(ff{fabsf(z0.hi), z0.hi < 0.0f ? -z0.lo : z0.lo}, s_row0[3]);
+        s_sc[4] = deg ? 1.0 : ff_to_double(g);
+        s_sc[5] = ff_to_double(zs_f);
     }
     __syncthreads();
-    const double sgn = s_sc[4], gamma = s_sc[5], zs = s_sc[6], rsc = s_sc[7];
+    if (s_flag && warp == 0) {                          // block-uniform: s_flag is shared
+        double dot = 0.0;
+        for (int i = lane; i < m; i += 32) dot = fma(zd[i + 1], cI[i], dot);
+        dot = wsum_d(dot);
+        if (lane == 0) s_sc[3] = dot < 0.0 ? -1.0 : 1.0;
+    }
+    if (s_flag) __syncthreads();
+    const double sgn = s_sc[3], gamma = s_sc[4], zs = s_sc[5];
     const bool bad = !isfinite(gamma) || !(gamma > 1e-200);
-    // 4. eta (Eq. def-z), the new stored c_I, the scatter weights (thread i: coordinate i);
-    //    eta also goes to x in the active indexing (float-float) for eta^T H_II eta
-    double eta = 0.0;
-    int nz_from = 0, nz_to = 0;
+    // 5. eta (Eq. def-z) and the compression thresholds (thread i: coordinate i), while thread 0
+    //    forms the new scale s' = s gamma (double-double) and 1 / s'
+    double eta = 0.0, zn = 0.0;
     if (tid < m) {
-        const double zn = sgn * (zd[tid + k0] * zs);
+        zn = sgn * (zd[tid + 1] * zs);
         eta = zn - gamma * ct;
         etaout[tid] = eta;
-        w[tid] = eta * rsc;
         thr[tid] = eta != 0.0 ? P.tau / fabs(eta) : 1.0e308;
+    }
+    if (tid == 0) {
+        const dd s_new = dd_mul_d(s_sc0, gamma);
+        s_sc[6] = 1.0 / s_new.hi;
+        ms->pend_scale = s_new;
+        ms->pend_gamma = gamma;
+        ms->pend_it = it;
+        ms->pend_deg = deg ? 1 : 0;
+        ms->n_cand = 0;                                 // the scatter builds the next candidate list
+        if (bad) set_status(st, kErrNonfinite);
+    }
+    __syncthreads();
+    // 6. the scatter weights and the new stored c_I; the change in nonzeros of c
+    const double rsc = s_sc[6];
+    bool to = false, from = false;
+    if (tid < m) {
+        w[tid] = eta * rsc;
         if (!bad) {
             P.table[sel[tid].slot].c = zn * rsc;
             cnz_set(P, sel[tid].A, sel[tid].B);
         }
-        nz_from = (ct != 0.0 && zn == 0.0) ? 1 : 0;
-        nz_to = (ct == 0.0 && zn != 0.0) ? 1 : 0;
-        const ff e = ff_from_double(eta);
-        xs[2 * (tid + k0)] = e.hi;
-        xs[2 * (tid + k0) + 1] = e.lo;
+        from = ct != 0.0 && zn == 0.0;
+        to = ct == 0.0 && zn != 0.0;
     }
-    if (tid == 0 && k0 == 1) { xs[0] = 0.0f; xs[1] = 0.0f; }
-    // eta . c_I, eta . b_I, eta . eta and the nonzero changes: warp partials
-    {
-        double v[3] = {eta * ct, eta * bt, eta * eta};
-        red_warp<3>(v, s_red, wm);
-        const int a = __reduce_add_sync(0xffffffffu, nz_from), b = __reduce_add_sync(0xffffffffu, nz_to);
-        if (lane == 0) { s_nzr[0][warp] = a; s_nzr[1][warp] = b; }
+    const int dn = __popc(__ballot_sync(0xffffffffu, to)) - __popc(__ballot_sync(0xffffffffu, from));
+    if (lane == 0 && dn != 0 && !bad) atomicAdd(reinterpret_cast<unsigned long long *>(&ms->nnz_c),
+                                                (unsigned long long)(long long)dn);
+}
+
+// ---------------------------------------------------------------------------
+// The scalars of Alg. 2's update of c (one block, inside the scatter's launch,
+// so that it runs beside the scatter): with gamma and eta from k_mc_eigen,
+//   mu'    = gamma^2 mu + 2 gamma eta.c_I + eta.eta,
+//   alpha' = gamma^2 alpha + 2 gamma eta.b_I + eta^T H_II eta   (double-double),
+// eta^T H_II eta in float-float from R's rows and columns 1..m; the energy
+// alpha / mu, the dx rule, the new scale, the counters.
+// ---------------------------------------------------------------------------
+struct McUpdate {
+    const double *cI, *bI, *eta;
+    const float *Rh, *Rl;
+    int ldr, on;                    // on = 0: no update block (the scatter of a start vector)
+};
+__device__ void mc_update_block(const Problem &P, McState *ms, IterState *st, const double *cI, const double *bI,
+                                const double *etaout, const float *Rh, const float *Rl, int ldr, int m,
+                                float *s_eta, double *s_red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int i = tid; i < m; i += blockDim.x) {
+        const ff e = ff_from_double(etaout[i]);
+        s_eta[2 * i] = e.hi;
+        s_eta[2 * i + 1] = e.lo;
+    }
+    // FP64 sums eta.c_I, eta.b_I, eta.eta (threads over coordinates)
+    double ec = 0.0, eb = 0.0, ee = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) {
+        const double e = etaout[i];
+        ec = fma(e, cI[i], ec);
+        eb = fma(e, bI[i], eb);
+        ee = fma(e, e, ee);
     }
     __syncthreads();
-    {
-        const ff he = ff_row(Ah, Al, ld, n, row, kk, tpr, act, xs);
-        ff t[1] = {lead ? ff_mul(ff{xs[2 * row], xs[2 * row + 1]}, he) : ff{0.0f, 0.0f}};
-        bsum_ff<1>(t, s_rff, hff);
-        if (warp == 0) {
-            const double eHe = ff_to_double(t[0]);
-            double v[3];
-            red_sum<3>(v, s_red, wm);
-            const double ec = v[0], eb = v[1], ee = v[2];
-            int fa = 0, fb = 0;
-            for (int q = 0; q < wm; ++q) { fa += s_nzr[0][q]; fb += s_nzr[1][q]; }
-            // mu and alpha (Alg. 2 update of c) in double-double: lane 0 mu, lane 1 alpha
-            const dd g2 = dd_two_prod(gamma, gamma);
-            dd out = {0.0, 0.0};
-            if (lane == 0) out = dd_add(dd_add(dd_mul(g2, s_mu0), dd_two_prod(2.0 * gamma, ec)), dd{ee, 0.0});
-            if (lane == 1) out = dd_add(dd_add(dd_mul(g2, s_al0), dd_two_prod(2.0 * gamma, eb)), dd{eHe, 0.0});
-            const dd al_n = {__shfl_sync(0xffffffffu, out.hi, 1), __shfl_sync(0xffffffffu, out.lo, 1)};
-            if (lane == 0) {
-                const dd mu_n = out;
-                const bool ok = !(bad || !isfinite(mu_n.hi) || !isfinite(al_n.hi));
-                const dd mu_k = ok ? mu_n : s_mu0, al_k = ok ? al_n : s_al0;
-                if (!ok) {
-                    set_status(st, kErrNonfinite);
-                } else {
-                    ms->mu = mu_n;
-                    ms->alpha = al_n;
-                    ms->scale = s_snew;
-                    st->scale = s_snew;
-                }
-                const double dxn = P.theta * s_dx0 + (1.0 - P.theta) * sqrt(ee);
-                ms->energy = dd_div_to_d(al_k, mu_k);
-                ms->iterations = s_its0 + 1;
-                ms->dx = dxn;
-                if (P.dx_threshold > 0.0 && dxn < P.dx_threshold) ms->done_pending = 1;
-                ms->nnz_c = s_nnz0 + (fb - fa);
-                ms->degenerate = deg ? 1 : 0;
-                ms->last_gamma = gamma;
-                ms->eig_iters = it;
-                ms->eig_iters_total = s_eit0 + it;
-                ms->n_cand = 0;                         // the scatter builds the next candidate list
-            }
-        }
+    // eta^T H_II eta: warp w takes rows w, w + nw, ...; lane l the columns l, l + 32, ... of each
+    float ah = 0.0f, al = 0.0f;
+    for (int i = warp; i < m; i += nw) {
+        const float *rh = Rh + (size_t)(i + 1) * ldr + 1, *rl = Rl + (size_t)(i + 1) * ldr + 1;
+        float th = 0.0f, tl = 0.0f;
+        for (int k = lane; k < m; k += 32) ff_mac(th, tl, rh[k], rl[k], ff{s_eta[2 * k], s_eta[2 * k + 1]});
+        const ff t = ff_mul(ff_norm(th, tl), ff{s_eta[2 * i], s_eta[2 * i + 1]});
+        const ff s = ff_two_sum(ah, t.hi);
+        ah = s.hi;
+        al = __fadd_rn(al, __fadd_rn(s.lo, t.lo));
     }
+    ff eh = ff_norm(ah, al);
+    for (int o = 16; o > 0; o >>= 1)
+        eh = ff_add(eh, ff{__shfl_down_sync(0xffffffffu, eh.hi, o), __shfl_down_sync(0xffffffffu, eh.lo, o)});
+    for (int o = 16; o > 0; o >>= 1) {
+        ec += __shfl_down_sync(0xffffffffu, ec, o);
+        eb += __shfl_down_sync(0xffffffffu, eb, o);
+        ee += __shfl_down_sync(0xffffffffu, ee, o);
+    }
+    if (lane == 0) {
+        s_red[4 * warp] = ec; s_red[4 * warp + 1] = eb; s_red[4 * warp + 2] = ee;
+        reinterpret_cast<ff *>(s_red + 4 * warp + 3)[0] = eh;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    double sc = 0.0, sb = 0.0, se = 0.0;
+    ff sh = {0.0f, 0.0f};
+    for (int q = 0; q < nw; ++q) {
+        sc += s_red[4 * q]; sb += s_red[4 * q + 1]; se += s_red[4 * q + 2];
+        sh = ff_add(sh, reinterpret_cast<const ff *>(s_red + 4 * q + 3)[0]);
+    }
+    const double eHe = ff_to_double(sh);
+    const dd mu0 = ms->mu, al0 = ms->alpha, s_new = ms->pend_scale;
+    const double gamma = ms->pend_gamma, dx0 = ms->dx;
+    const long long its = ms->iterations, eit = ms->eig_iters_total;
+    const int it = ms->pend_it, deg = ms->pend_deg;
+    // mu and alpha (Alg. 2 update of c) in double-double
+    const dd g2 = dd_two_prod(gamma, gamma);
+    const dd mu_n = dd_add(dd_add(dd_mul(g2, mu0), dd_two_prod(2.0 * gamma, sc)), dd{se, 0.0});
+    const dd al_n = dd_add(dd_add(dd_mul(g2, al0), dd_two_prod(2.0 * gamma, sb)), dd{eHe, 0.0});
+    const bool ok = isfinite(mu_n.hi) && isfinite(al_n.hi);
+    const dd mu_k = ok ? mu_n : mu0, al_k = ok ? al_n : al0;
+    if (!ok) {
+        set_status(st, kErrNonfinite);
+    } else {
+        ms->mu = mu_n;
+        ms->alpha = al_n;
+        ms->scale = s_new;
+        st->scale = s_new;
+    }
+    const double dxn = P.theta * dx0 + (1.0 - P.theta) * sqrt(se);
+    ms->energy = dd_div_to_d(al_k, mu_k);
+    ms->iterations = its + 1;
+    ms->dx = dxn;
+    if (P.dx_threshold > 0.0 && dxn < P.dx_threshold) ms->done_pending = 1;
+    ms->degenerate = deg;
+    ms->last_gamma = gamma;
+    ms->eig_iters = it;
+    ms->eig_iters_total = eit + it;
 }
 
 // ---------------------------------------------------------------------------
@@ -1574,7 +1745,7 @@ __device__ __forceinline__ void mc_item_s(const Problem &P, McWarp &W, const Col
 __global__ void __launch_bounds__(256, 3) k_mc_scatter(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                     const ColEnt *coltab, const ColLists *collists, McGeom Gm,
                                                     const double *w, const double *thr, long long *cand,
-                                                    double *gathp, unsigned int *work) {
+                                                    double *gathp, unsigned int *work, McUpdate U) {
     __shared__ unsigned long long q_a[8][kScatterQ], q_b[8][kScatterQ], q_h[8][kScatterQ];
     __shared__ double q_H[8][kScatterQ];
     __shared__ long long w_cand[8][kWarpCand];
@@ -1582,6 +1753,11 @@ __global__ void __launch_bounds__(256, 3) k_mc_scatter(Problem P, McState *ms, I
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
+    if (U.on && blockIdx.x == 0) {                      // the first block: mu, alpha and the scale, beside the scatter
+        mc_update_block(P, ms, st, U.cI, U.bI, U.eta, U.Rh, U.Rl, U.ldr, m, reinterpret_cast<float *>(&q_H[0][0]),
+                        reinterpret_cast<double *>(&q_a[0][0]));
+        return;
+    }
     const int total = m * Gm.per_col;
     const int ns = Gm.nsA + Gm.nsB;
     McWarp W{q_a[warp], q_b[warp], q_h[warp], q_H[warp], w_cand[warp], l2_evict_first(), l2_evict_last(),
@@ -1805,9 +1981,7 @@ __global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, do
 size_t mc_eigen_smem(int m) {
     const int n1 = m + 1, ldr = 32 * ((n1 + 31) / 32);
     const size_t lds = (size_t)eig_lds(ldr, eig_tpr(n1));
-    // x (float-float), w, z / eta (FP64), c_I (FP64)
-    const size_t vec = 4 * ((3 * (size_t)n1 + 3) / 4) + 2 * (size_t)n1 + 2 * (size_t)m;
-    return ((n1 <= kEigSmemN ? 2 * (size_t)n1 * lds : 0) + vec) * sizeof(float);
+    return ((n1 <= kEigSmemN ? 2 * (size_t)n1 * lds : 0) + eig_vec_floats(n1)) * sizeof(float);
 }
 int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
 int mc_max_m() { return kEigMaxN - 1; }
@@ -1841,8 +2015,9 @@ McGeom mc_geometry(const Problem &P) {
 }
 
 cudaError_t mc_configure() {
-    cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max(mc_eigen_smem(kEigSmemN - 1), mc_eigen_smem(149)));
+    size_t most = 0;
+    for (int m = 1; m < kEigMaxN; ++m) most = std::max(most, mc_eigen_smem(m));
+    cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     if (e != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -1882,7 +2057,7 @@ cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long 
 
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s) {
     k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.coltab, b.collists, b.geom, b.w, b.thr,
-                                                 b.cand, b.gathp, b.work);
+                                                 b.cand, b.gathp, b.work, McUpdate{});
     k_mc_finalize<<<1, 1024, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.geom.per_col, b.work);
     return cudaGetLastError();
 }
@@ -1907,16 +2082,18 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
     mark();
     k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
     mark();
-    k_mc_prepare<<<(b.m + 7) / 8, 256, 0, s>>>(P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr,
-                                               b.coltab, b.collists, b.geom.nsA + b.geom.nsB);
+    k_mc_prepare<<<(b.m + kPrepWarps - 1) / kPrepWarps, 32 * kPrepWarps, 0, s>>>(
+        P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr, b.coltab, b.collists, b.geom.nsA + b.geom.nsB);
     mark();
-    k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Rh,
-                                                                    b.Rl, b.ldr, eig_tpr(b.m + 1),
+    k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc,
+                                                                    b.Hdiag, b.Rh, b.Rl, b.ldr, eig_tpr(b.m + 1),
                                                                     b.m + 1 <= kEigSmemN ? 1 : 0,
                                                                     b.w, b.thr, b.eta);
     mark();
-    k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.coltab, b.collists, b.geom, b.w, b.thr,
-                                                 b.cand, b.gathp, b.work);
+    // one more block than the scatter's own: block 0 updates mu, alpha and the scale meanwhile
+    k_mc_scatter<<<b.scatter_grid + 1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.coltab, b.collists, b.geom, b.w, b.thr,
+                                                     b.cand, b.gathp, b.work,
+                                                     McUpdate{b.cI, b.bI, b.eta, b.Rh, b.Rl, b.ldr, 1});
     mark();
     k_mc_finalize<<<1, 1024, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.geom.per_col, b.work);
     mark();

@@ -151,6 +151,10 @@ struct McState {
     int n_above, n_inbin;
     int eig_iters;                 // LOBPCG iterations of the last reduced problem
     long long eig_iters_total;
+    // from the reduced solve to the update of mu and alpha that runs beside the scatter
+    dd pend_scale;                 // s gamma
+    double pend_gamma;
+    int pend_it, pend_deg;
 };
 
 // xCDFCI (Algorithm 3, k1 = K + 1 states) iteration state, one per handle.
