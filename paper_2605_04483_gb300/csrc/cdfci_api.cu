@@ -233,7 +233,7 @@ int setup_block(cdfci_ctx *c, int m) {
     const size_t ns = (size_t)b.geom.nsA + (size_t)b.geom.nsB;
     b.st = c->d_st;
     const size_t n1 = (size_t)m + 1;
-    b.ldr = (int)(32 * ((n1 + 31) / 32));
+    b.ldr = mc_ldr(m);
     if (mb_alloc(c, &b.ms, 1) || mb_alloc(c, &b.cand, (size_t)cap_cand) || mb_alloc(c, &b.gkey, (size_t)cap_cand) ||
         mb_alloc(c, &b.hist, 4096 + 1) || mb_alloc(c, &b.sel, (size_t)m) || mb_alloc(c, &b.inbin, 4096) || mb_alloc(c, &b.ties, (size_t)cap_cand) ||
         mb_alloc(c, &b.cI, (size_t)m) || mb_alloc(c, &b.bI, (size_t)m) || mb_alloc(c, &b.Hdiag, (size_t)m) ||
@@ -241,7 +241,7 @@ int setup_block(cdfci_ctx *c, int m) {
         mb_alloc(c, &b.Rl, n1 * (size_t)b.ldr) ||
         mb_alloc(c, &b.w, (size_t)m) || mb_alloc(c, &b.thr, (size_t)m) || mb_alloc(c, &b.eta, (size_t)m) ||
         mb_alloc(c, &b.gathp, (size_t)m * (size_t)b.geom.per_col) || mb_alloc(c, &b.coltab, (size_t)m * ns) ||
-        mb_alloc(c, &b.collists, (size_t)m) || mb_alloc(c, &b.work, 1))
+        mb_alloc(c, &b.collists, (size_t)m) || mb_alloc(c, &b.work, 1) || mb_alloc(c, &b.rowf, 2 * (size_t)m))
         return fail(CDFCI_ERR_NOMEM, "allocation of the multicoordinate buffers failed");
     // c != 0 filter: one bit per table slot, between 2^16 and 2^25 bits (4 MB: it stays in L2 while the
     // scatter's random slot traffic streams through)

@@ -149,13 +149,15 @@ __device__ __forceinline__ void ff_mac(float &sh, float &sl, float ah, float al,
 // lane 0 stores the warp's value, and after the barrier every thread adds the
 // warps' values in warp order, so all threads hold bit-identical results.  Two
 // scratch halves alternate: a half is rewritten only after the barrier of the
-// following reduction, which every reader of it has passed.
+// following reduction, which every reader of it has passed.  (The trees have
+// a fixed depth, fully unrolled, so that the K sums' shuffles interleave.)
 // ---------------------------------------------------------------------------
 template <int K>
 __device__ __forceinline__ void bsum_f(float (&v)[K], float *scr, int &half) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k)
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[k] = __fadd_rn(v[k], __shfl_down_sync(0xffffffffu, v[k], off));
     float *s = scr + half * 32 * 16;                     // fixed stride: K <= 16
     if (lane == 0)
@@ -167,6 +169,7 @@ __device__ __forceinline__ void bsum_f(float (&v)[K], float *scr, int &half) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float t = lane < nw ? s[lane * K + k] : 0.0f;
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
         v[k] = t;
     }
@@ -178,6 +181,7 @@ __device__ __forceinline__ void bsum_ff(ff (&v)[K], ff *scr, int &half) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k)
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const ff o = {__shfl_down_sync(0xffffffffu, v[k].hi, off), __shfl_down_sync(0xffffffffu, v[k].lo, off)};
             v[k] = ff_add(v[k], o);
@@ -192,6 +196,7 @@ __device__ __forceinline__ void bsum_ff(ff (&v)[K], ff *scr, int &half) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         ff t = lane < nw ? s[lane * K + k] : ff{0.0f, 0.0f};
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1)
             t = ff_add(t, ff{__shfl_xor_sync(0xffffffffu, t.hi, off), __shfl_xor_sync(0xffffffffu, t.lo, off)});
         v[k] = t;
@@ -217,19 +222,18 @@ __device__ __forceinline__ void sym3_lowest(float a00, float a01, float a02, flo
         lam = 0.0f; v0 = 1.0f; v1 = 0.0f; v2 = 0.0f;
         return;
     }
-    const float is = 1.0f / sc;
+    const float is = __fdividef(1.0f, sc);
     a00 *= is; a01 *= is; a02 *= is; a11 *= is; a12 *= is; a22 *= is;
     const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
     const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
     const float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * (a01 * a01 + a02 * a02 + a12 * a12);
     float l = q;
     if (p2 > 0.0f) {
-        const float p = sqrtf(p2 * (1.0f / 6.0f));
-        const float ip = 1.0f / p;
+        const float ip = rsqrtf(p2 * (1.0f / 6.0f)), p = p2 * (1.0f / 6.0f) * ip;
         const float c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
         float r = 0.5f * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
         r = fminf(1.0f, fmaxf(-1.0f, r));
-        l = q + 2.0f * p * cosf(acosf(r) * (1.0f / 3.0f) + 2.0943951023931953f);
+        l = q + 2.0f * p * __cosf(acosf(r) * (1.0f / 3.0f) + 2.0943951023931953f);
     }
     const float m00 = a00 - l, m11 = a11 - l, m22 = a22 - l;
     float x0 = a01 * a12 - a02 * m11, x1 = a02 * a01 - m00 * a12, x2 = m00 * m11 - a01 * a01;   // r0 x r1
@@ -719,8 +723,8 @@ __device__ __forceinline__ void mc_build_coltab(const Problem &P, const ColLists
 constexpr int kPrepWarps = 8;       // rows (warps) per block
 
 __global__ void __launch_bounds__(32 * kPrepWarps) k_mc_prepare(Problem P, McState *ms, const McSel *sel, double *cI,
-                                                    double *bI, double *Hdiag, double *HIIc, float *Rh, float *Rl,
-                                                    int ldr, ColEnt *coltab, ColLists *collists, int ns) {
+                                                    double *bI, double *Hdiag, double *HIIc, float4 *rowf, float *Rh,
+                                                    float *Rl, int ldr, ColEnt *coltab, ColLists *collists, int ns) {
     __shared__ ColLists Lw[kPrepWarps];
     // the chosen determinants and their c (true units), staged once per block
     __shared__ unsigned long long s_A[kEigMaxN], s_B[kEigMaxN];
@@ -759,12 +763,19 @@ __global__ void __launch_bounds__(32 * kPrepWarps) k_mc_prepare(Problem P, McSta
             acc = fma(h, s_c[c], acc);
         }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        // the row's values, and for the reduced solve c_r, b_r, (H_II c_I)_r, b_r - (H_II c_I)_r as
+        // float-float pairs (lanes 0..3, one conversion each)
+        const double hc = __shfl_sync(0xffffffffu, acc, 0), br = __shfl_sync(0xffffffffu, b_r, 0) * s;
         if (lane == 0) {
             cI[r] = s_c[r];
-            bI[r] = b_r * s;
+            bI[r] = br;
             Hdiag[r] = hd;
-            HIIc[r] = acc;
+            HIIc[r] = hc;
         }
+        const double cv = lane == 0 ? s_c[r] : (lane == 1 ? br : (lane == 2 ? hc : br - hc));
+        const ff f = ff_from_double(cv);
+        const float fh1 = __shfl_sync(0xffffffffu, f.hi, lane | 1), fl1 = __shfl_sync(0xffffffffu, f.lo, lane | 1);
+        if (lane == 0 || lane == 2) rowf[2 * r + (lane >> 1)] = make_float4(f.hi, f.lo, fh1, fl1);
         __syncwarp();
     }
 }
@@ -794,15 +805,20 @@ __global__ void __launch_bounds__(32 * kPrepWarps) k_mc_prepare(Problem P, McSta
 constexpr int kEigSmemN = 160;      // A in shared memory (hi and lo) up to this size
 constexpr int kEigMaxIt = 200;
 
-// Threads per row of the reduced problem and the shared-memory row stride for
-// a problem of size n1 = m + 1 (columns padded to ldr, a multiple of 32).
-// 2 threads per row up to 160 rows (cheaper block sums; R in shared memory),
-// 4 up to 256, then 2, then 1.  The stride ldr + 4 tpr puts the 16-byte loads
-// of a quarter warp (8 lanes: 8 / tpr rows, tpr chunks each) on distinct banks.
+// Threads per row of the reduced problem and R's row stride (in global and,
+// for n1 <= kEigSmemN, in shared memory) for a problem of size n1 = m + 1.
+// 2 threads per row while R is in shared memory (n1 <= 160), else 1 (the
+// products then stream R through shared memory with all threads on every
+// block of rows, independent of the row groups).  The stride is a multiple of 32 floats, plus
+// 4 tpr when R is copied to shared memory: that puts the 16-byte loads of a
+// quarter warp (8 lanes: 8 / tpr rows, tpr chunks each) on distinct banks,
+// and the copy is one bulk transfer per array.
 __host__ __device__ __forceinline__ int eig_tpr(int n1) {
-    return n1 <= kEigSmemN ? 2 : (n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1));
+    return n1 <= kEigSmemN ? 2 : 1;
 }
-__host__ __device__ __forceinline__ int eig_lds(int ldr, int tpr) { return ldr + 4 * tpr; }
+__host__ __device__ __forceinline__ int eig_ldr(int n1) {
+    return 32 * ((n1 + 31) / 32) + (n1 <= kEigSmemN ? 4 * eig_tpr(n1) : 0);
+}
 // entries of a vector in absolute indexing, a multiple of 4
 __host__ __device__ __forceinline__ int eig_len(int n1) { return 4 * ((n1 + 3) / 4); }
 
@@ -889,19 +905,15 @@ __device__ __forceinline__ float f_group_sum(float v, int tpr) {
     return v;
 }
 // A x (float-float) and A w (FP32) for the row; every lane of the group holds
-// it.  R in shared memory: 2 (float-float) or 4 (FP32) chunks per round; in
-// global memory (L2): 4 or 8, for more loads in flight.
+// it.  2 (float-float) or 4 (FP32) chunks of the row in flight per round
+// (more would spill at the 64 registers of a 1024-thread block).
 __device__ __forceinline__ ff ff_row(const float *Ah, const float *Al, int ld, int nq, int ra, int k, int tpr,
-                                     bool act, bool smem, const float *x) {
-    ff v = {0.0f, 0.0f};
-    if (act) v = smem ? ff_row_part<2>(Ah, Al, ld, nq, ra, k, tpr, x) : ff_row_part<4>(Ah, Al, ld, nq, ra, k, tpr, x);
-    return ff_group_sum(v, tpr);
+                                     bool act, const float *x) {
+    return ff_group_sum(act ? ff_row_part<2>(Ah, Al, ld, nq, ra, k, tpr, x) : ff{0.0f, 0.0f}, tpr);
 }
-__device__ __forceinline__ float f_row(const float *Ah, int ld, int nq, int ra, int k, int tpr, bool act, bool smem,
+__device__ __forceinline__ float f_row(const float *Ah, int ld, int nq, int ra, int k, int tpr, bool act,
                                        const float *w) {
-    float v = 0.0f;
-    if (act) v = smem ? f_row_part<4>(Ah, ld, nq, ra, k, tpr, w) : f_row_part<8>(Ah, ld, nq, ra, k, tpr, w);
-    return f_group_sum(v, tpr);
+    return f_group_sum(act ? f_row_part<4>(Ah, ld, nq, ra, k, tpr, w) : 0.0f, tpr);
 }
 
 // float-float 1 / sqrt(a), a > 0 and normal in FP32: the FP32 estimate and two
@@ -918,50 +930,154 @@ __device__ __forceinline__ ff ff_rsqrt(ff a) {
     return y;
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+// Bulk copies global -> shared by the TMA unit (cp.async.bulk), completed on an
+// mbarrier by transaction bytes: one thread arms the barrier with the total,
+// the lanes of one warp issue one copy per row, every thread later waits for
+// the barrier's phase 0.  Addresses 16-byte aligned, sizes multiples of 16.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init_arm(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// FP64 sums of K values over the first nw warps of the block (fixed trees);
-// every lane of warp 0 gets them after the caller's barrier via red_sum.
-template <int K>
-__device__ __forceinline__ void red_warp(double (&v)[K], double *scr, int nw) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp >= nw) return;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) scr[warp * K + k] = v[k];
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// (warp 0, after the barrier) the xor butterfly over the nw partials; its
-// levels at and above the next power of two of nw only add zeros to lane 0,
-// so they are skipped, and lane 0's sum goes to every lane
-template <int K>
-__device__ __forceinline__ void red_sum(double (&v)[K], const double *scr, int nw) {
-    const int lane = threadIdx.x & 31;
-    int top = 1;
-    while (top < nw) top <<= 1;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double t = lane < nw ? scr[lane * K + k] : 0.0;
-        for (int off = top >> 1; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        v[k] = __shfl_sync(0xffffffffu, t, 0);
+// true once the barrier's phase of the given parity has completed; gives up after `limit` polls
+__device__ __forceinline__ bool mbar_wait_parity(unsigned long long *bar, unsigned parity, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        unsigned ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (ok) return true;
     }
+    return false;
+}
+// true once phase 0 of the barrier has completed; gives up after `limit` polls
+__device__ __forceinline__ bool mbar_wait0(unsigned long long *bar, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        unsigned ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok) : "r"(smem_u32(bar)) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// FP64 sums over a warp of four values at once (a butterfly that halves the
+// values while it halves the lanes: 6 dependent adds instead of 4 x 5); lane l
+// ends with the sum of value l >> 3, in a fixed order
+__device__ __forceinline__ double wsum4(double a, double b, double c, double d) {
+    const int lane = threadIdx.x & 31;
+    const bool up = lane & 16;
+    double x0 = up ? c : a, x1 = up ? d : b;
+    x0 += __shfl_xor_sync(0xffffffffu, up ? a : c, 16);
+    x1 += __shfl_xor_sync(0xffffffffu, up ? b : d, 16);
+    const bool up2 = lane & 8;
+    double z = up2 ? x1 : x0;
+    z += __shfl_xor_sync(0xffffffffu, up2 ? x0 : x1, 8);
+    z += __shfl_xor_sync(0xffffffffu, z, 4);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    return z;
 }
 
 // Dynamic shared memory of k_mc_eigen, in floats: A (hi, lo) when it fits,
 // then x (float-float), w, z (FP64) and a staging area, each of eig_len(m + 1)
 // entries in absolute indexing.
 __host__ __device__ __forceinline__ size_t eig_vec_floats(int n1) { return 7 * (size_t)eig_len(n1); }
+// R in global memory: the rows per stage buffer (two buffers, each hi and lo rows x ldr floats, about
+// 160 KB in all) and the product results (2 eig_len floats) after the vectors
+constexpr size_t kEigStageBytes = 160 * 1024;
+__host__ __device__ __forceinline__ int eig_stage_rows(int n1) {
+    const int ldr = eig_ldr(n1), r = (int)(kEigStageBytes / (16 * (size_t)ldr));
+    return r < 1 ? 1 : (r > n1 ? n1 : r);
+}
+
+// R in global memory: y = R v for rows 0..m, R passing through two stage
+// buffers in shared memory (TMA bulk copies of contiguous row blocks, one
+// mbarrier per buffer, issued by thread 0 two blocks ahead); every thread
+// works on every staged block, g threads per row (a power of two), and the
+// row's sum goes to y (FP32 y[r], or float-float y[2 r], y[2 r + 1]).  v is
+// in absolute indexing (float-float pairs for FF), nq chunks of 4 entries.
+// par[b] is the parity of buffer b's next phase; a wait that gives up sets
+// the status (the copies are then waited for once more, bounded, at the end).
+template <bool FF>
+__device__ void eig_stream(const float *Rh, const float *Rl, int ldr, int n1, int nq, float *buf, int rows,
+                           unsigned long long *bar, unsigned (&par)[2], const float *v, float *y, IterState *st) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int g = 1;
+    while (g < 32 && 2 * g * rows <= nt) g <<= 1;
+    const int nch = (n1 + rows - 1) / rows;
+    const size_t stage = 2 * (size_t)rows * ldr;      // floats per buffer (hi rows, then lo rows)
+    auto issue = [&](int c) {
+        const int r0 = c * rows, nr = min(rows, n1 - r0), b = c & 1;
+        const unsigned bytes = (unsigned)nr * (unsigned)ldr * 4u;
+        float *dst = buf + b * stage;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(smem_u32(bar + b)), "r"(FF ? 2u * bytes : bytes) : "memory");
+        bulk_g2s(dst, Rh + (size_t)r0 * ldr, bytes, bar + b);
+        if (FF) bulk_g2s(dst + (size_t)rows * ldr, Rl + (size_t)r0 * ldr, bytes, bar + b);
+    };
+    if (tid == 0) {
+        issue(0);
+        if (nch > 1) issue(1);
+    }
+    bool late = false;
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1, r0 = c * rows, nr = min(rows, n1 - r0);
+        late |= !mbar_wait_parity(bar + b, par[b], 1 << 22);
+        par[b] ^= 1u;
+        const float *bh = buf + b * stage, *bl = bh + (size_t)rows * ldr;
+        const int rr = tid / g, k = tid - rr * g;
+        if (FF) {
+            float sh0 = 0.0f, sl0 = 0.0f;
+            if (rr < nr) {
+                const float4 *h4 = reinterpret_cast<const float4 *>(bh + (size_t)rr * ldr);
+                const float4 *l4 = reinterpret_cast<const float4 *>(bl + (size_t)rr * ldr);
+                const float4 *x4 = reinterpret_cast<const float4 *>(v);
+                for (int q = k; q < nq; q += g) {
+                    const float4 h = h4[q], l = l4[q], xa = x4[2 * q], xb = x4[2 * q + 1];
+                    ff_mac(sh0, sl0, h.x, l.x, ff{xa.x, xa.y});
+                    ff_mac(sh0, sl0, h.y, l.y, ff{xa.z, xa.w});
+                    ff_mac(sh0, sl0, h.z, l.z, ff{xb.x, xb.y});
+                    ff_mac(sh0, sl0, h.w, l.w, ff{xb.z, xb.w});
+                }
+            }
+            ff t = ff_norm(sh0, sl0);
+            for (int o = 1; o < g; o <<= 1)
+                t = ff_add(t, ff{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)});
+            if (rr < nr && k == 0) { y[2 * (r0 + rr)] = t.hi; y[2 * (r0 + rr) + 1] = t.lo; }
+        } else {
+            float a0 = 0.0f, a1 = 0.0f;
+            if (rr < nr) {
+                const float4 *h4 = reinterpret_cast<const float4 *>(bh + (size_t)rr * ldr);
+                const float4 *w4 = reinterpret_cast<const float4 *>(v);
+                for (int q = k; q < nq; q += g) {
+                    const float4 h = h4[q], x = w4[q];
+                    a0 = fmaf(h.x, x.x, a0);
+                    a1 = fmaf(h.y, x.y, a1);
+                    a0 = fmaf(h.z, x.z, a0);
+                    a1 = fmaf(h.w, x.w, a1);
+                }
+            }
+            float t = a0 + a1;
+            for (int o = 1; o < g; o <<= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
+            if (rr < nr && k == 0) y[r0 + rr] = t;
+        }
+        __syncthreads();                                // buffer b read by every thread; y complete at the end
+        if (tid == 0 && c + 2 < nch) issue(c + 2);
+    }
+    if (late) set_status(st, kErrTimeout);
+}
 
 __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                        const double *cI, const double *bI, const double *HIIc,
-                                                       const double *Hdiag, float *Rh, float *Rl, int ldr, int tpr,
-                                                       int use_smem, double *w, double *thr, double *etaout) {
+                                                       const double *Hdiag, const float4 *rowf, float *Rh, float *Rl,
+                                                       int ldr, int tpr, int use_smem, double *w, double *thr,
+                                                       double *etaout) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float s_rf[2 * 32 * 16];
     __shared__ ff s_rff[2 * 32 * 2];
@@ -969,7 +1085,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     __shared__ ff s_row0[4];                            // nu, R_00, (A x)_0 of the start, 1 / nu
     __shared__ double s_sc[8];
     __shared__ float s_drms;
-    __shared__ int s_nzr[32], s_flag;
+    __shared__ int s_nzr[32], s_flag, s_zero;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
     const int m = ms->m_sel;
@@ -979,80 +1095,113 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     __shared__ long long s_nnz0;
     if (tid == 0) { s_mu0 = ms->mu; s_al0 = ms->alpha; s_sc0 = ms->scale; s_nnz0 = ms->nnz_c; }
     int hf = 0, hff = 0;
-    const int lds = eig_lds(ldr, tpr);
+    const int lds = ldr;                                // R's stride in shared memory too
     const int L = eig_len(m + 1), nq = L / 4;
     float *sh = sm, *sl = sm + (size_t)(m + 1) * lds;
-    // 0. start the copy of R (rows 0..m) into shared memory; it completes behind step 1
-    if (use_smem) {
-        const float4 *gh = reinterpret_cast<const float4 *>(Rh), *gl = reinterpret_cast<const float4 *>(Rl);
-        const int q = ldr / 4, nv = (m + 1) * q;
-        for (int t = tid; t < nv; t += blockDim.x) {
-            const int r = t / q, c = 4 * (t - r * q);
-            cp_async16(sh + r * lds + c, gh + t);
-            cp_async16(sl + r * lds + c, gl + t);
-        }
+    // 0. start the copy of R (rows 0..m, hi and lo) into shared memory: one bulk copy per array,
+    //    issued by thread 0 after arming the barrier; it completes behind steps 1 and 2
+    __shared__ unsigned long long s_bar;
+    if (use_smem && tid == 0) {
+        const unsigned bytes = (unsigned)(m + 1) * (unsigned)ldr * 4u;
+        mbar_init_arm(&s_bar, 2u * bytes);
+        bulk_g2s(sh, Rh, bytes, &s_bar);
+        bulk_g2s(sl, Rl, bytes, &s_bar);
+    }
+    // R in global memory: two stage buffers for the streamed products, their barriers armed later
+    __shared__ unsigned long long s_sbar[2];
+    unsigned spar[2] = {0u, 0u};
+    if (!use_smem && tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_sbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_sbar[1])) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     float *vec = use_smem ? sm + 2 * (size_t)(m + 1) * lds : sm;
     float *xs = vec;                                    // float-float x (2 L floats)
     float *ws = vec + 2 * L;                            // FP32 w (L floats)
     double *zd = reinterpret_cast<double *>(vec + 3 * L);   // z (L doubles); first the start's A x (float-float)
     float *hs = vec + 5 * L;                            // the start's H_II c_I (float-float, 2 L floats)
+    float *ys = vec + 7 * L;                            // streamed products' results (2 L floats)
+    float *stg = vec + 9 * L;                           // stage buffers
+    const int srows = eig_stage_rows(m + 1);
     const float *Ah = use_smem ? sh : Rh, *Al = use_smem ? sl : Rl;
     const int ld = use_smem ? lds : ldr;
 
-    // 1. sums over I (FP64): c.c, c.b, c.H_II c, |diag H_II|^2, nonzeros; the
-    //    coordinates' start values staged at their absolute index i + 1
-    double ct = 0.0, bt = 0.0, ht = 0.0, hd = 0.0;
-    if (tid < m) { ct = cI[tid]; bt = bI[tid]; ht = HIIc[tid]; hd = Hdiag[tid]; }
-    {
-        double v[4] = {ct * ct, ct * bt, ct * ht, hd * hd};
-        red_warp<4>(v, s_red, wm);
-        const int nzw = __reduce_add_sync(0xffffffffu, (tid < m && ct != 0.0) ? 1 : 0);
+    // 1. sums over I (FP64): c.c, c.b, c.H_II c, |diag H_II|^2, nonzeros (warps holding I);
+    //    the coordinates' start values (float-float, from k_mc_prepare) staged at their absolute
+    //    index i + 1
+    double c0 = 0.0, bt = 0.0, ht = 0.0, hd = 0.0;
+    float4 f0 = {0.0f, 0.0f, 0.0f, 0.0f}, f1 = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (tid < m) {
+        c0 = cI[tid]; bt = bI[tid]; ht = HIIc[tid]; hd = Hdiag[tid];
+        f0 = rowf[2 * tid]; f1 = rowf[2 * tid + 1];
+    }
+    if (warp < wm) {
+        const double t = wsum4(c0 * c0, c0 * bt, c0 * ht, hd * hd);
+        const int nzw = __reduce_add_sync(0xffffffffu, (__double_as_longlong(c0) << 1) != 0 ? 1 : 0);
+        if ((lane & 7) == 0) s_red[warp * 4 + (lane >> 3)] = t;
         if (lane == 0) s_nzr[warp] = nzw;
     }
-    const ff bh_f = ff_from_double(bt - ht);            // nu R_0i = b_i - (H_II c_I)_i
+    const ff bh_f = {f1.z, f1.w};                       // nu R_0i = b_i - (H_II c_I)_i
     if (tid < m) {
-        const ff c_f = ff_from_double(ct), b_f = ff_from_double(bt), h_f = ff_from_double(ht);
         const int a = tid + 1;
-        xs[2 * a] = c_f.hi; xs[2 * a + 1] = c_f.lo;
+        xs[2 * a] = f0.x; xs[2 * a + 1] = f0.y;         // c_i
         float *az = reinterpret_cast<float *>(zd);
-        az[2 * a] = b_f.hi; az[2 * a + 1] = b_f.lo;
-        hs[2 * a] = h_f.hi; hs[2 * a + 1] = h_f.lo;
+        az[2 * a] = f0.z; az[2 * a + 1] = f0.w;         // b_i
+        hs[2 * a] = f1.x; hs[2 * a + 1] = f1.y;         // (H_II c_I)_i
     }
     for (int t = m + 1 + tid; t < L; t += blockDim.x) { xs[2 * t] = 0.0f; xs[2 * t + 1] = 0.0f; ws[t] = 0.0f; }
     if (tid == 0) { xs[0] = 0.0f; xs[1] = 0.0f; ws[0] = 0.0f; }
     __syncthreads();
-    // 2. warp 0: nu^2 = mu - c.c (lane 0), nu^2 R_00 = alpha - 2 c.b + c.H c (lane 1) and
-    //    nu (A x)_0 = alpha - c.b (lane 2) as compensated sums (TwoSum), all three in the same
-    //    instructions; the degenerate case (c has no support outside I); 1 / nu (FP64 rsqrt),
-    //    then nu, R_00 and (A x)_0 (float-float)
+    // 2. warp 0: the four sums (lane 8 k + j adds value k of warps j, j + 8, ..., then a
+    //    three-level butterfly); nu^2 = mu - c.c (lane 0), nu^2 R_00 = alpha - 2 c.b + c.H c
+    //    (lane 1) and nu (A x)_0 = alpha - c.b (lane 2) as compensated sums (TwoSum), all three
+    //    in the same instructions; the degenerate case (c has no support outside I); 1 / nu in
+    //    float-float (Newton) while nu^2 is a normal FP32 number, else by the FP64 rsqrt; then
+    //    nu, R_00 and (A x)_0 (float-float).  Tests on FP64 values are integer tests of their bits.
     if (warp == 0) {
-        double v[4];
-        red_sum<4>(v, s_red, wm);
+        double t = 0.0;
+        for (int q = lane & 7; q < wm; q += 8) t += s_red[q * 4 + (lane >> 3)];
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        const double cc = __shfl_sync(0xffffffffu, t, 0), cb = __shfl_sync(0xffffffffu, t, 8);
+        const double chc = __shfl_sync(0xffffffffu, t, 16), hh = __shfl_sync(0xffffffffu, t, 24);
         int nz = 0;
         for (int q = 0; q < wm; ++q) nz += s_nzr[q];
         const dd a = lane == 0 ? s_mu0 : s_al0;
-        const double p = lane == 0 ? -v[0] : (lane == 1 ? -2.0 * v[1] : -v[1]);
-        const double q = lane == 1 ? v[2] : 0.0;
+        const double p = lane == 0 ? -cc : (lane == 1 ? -2.0 * cb : -cb);
+        const double q = lane == 1 ? chc : 0.0;
         const dd s1 = dd_two_sum(a.hi, p), s2 = dd_two_sum(s1.hi, q);
         const double r = s2.hi + ((s1.lo + s2.lo) + a.lo);
         const double nu2 = __shfl_sync(0xffffffffu, r, 0);
-        const bool deg = (nz >= s_nnz0) || !(nu2 > 0.0);
-        const double inu = deg ? 0.0 : rsqrt(nu2);
-        const double y = (lane == 3 ? 1.0 : r) * inu * (lane == 1 ? inu : 1.0);   // nu, R_00, (A x)_0, 1 / nu
-        const ff yf = ff_from_double(y);
+        const long long nb = __double_as_longlong(nu2);
+        const bool deg = (nz >= s_nnz0) || nb <= 0;     // nu^2 <= 0
+        const int ex = (int)((nb >> 52) & 0x7ff) - 1023;
+        const ff rf = ff_from_double(r), n2f = {__shfl_sync(0xffffffffu, rf.hi, 0), __shfl_sync(0xffffffffu, rf.lo, 0)};
+        ff inu_f = {0.0f, 0.0f};
+        if (!deg) {
+            if (ex > -120 && ex < 120) inu_f = ff_rsqrt(n2f);
+            else inu_f = ff_from_double(rsqrt(nu2));
+        }
+        // lane 0: nu = nu^2 / nu, lane 1: R_00, lane 2: (A x)_0, lane 3: 1 / nu
+        const ff yf = lane == 3 ? inu_f : ff_mul(ff_mul(rf, inu_f), lane == 1 ? inu_f : ff{1.0f, 0.0f});
         if (lane < 4) s_row0[lane] = yf;
         const float r00 = __shfl_sync(0xffffffffu, yf.hi, 1);
         if (lane == 0) {
             s_sc[0] = deg ? 1.0 : 0.0;
-            s_sc[1] = inu;
-            s_sc[2] = v[0];
-            const float n = (float)(m + (deg ? 0 : 1));
-            s_drms = sqrtf((__double2float_rn(v[3]) + (deg ? 0.0f : r00 * r00)) / n);
+            s_zero = (deg && __double_as_longlong(cc) <= 0) ? 1 : 0;   // c = 0: no start vector
+            const float nf = (float)(m + (deg ? 0 : 1));
+            s_drms = sqrtf((__double2float_rn(hh) + (deg ? 0.0f : r00 * r00)) / nf);
         }
     }
-    if (use_smem) cp_async_wait_all();
-    __syncthreads();                                    // scalars, and this block's copy of R, complete
+    // the copy of R: a bounded wait; a copy that never lands is an error (its bytes may still be in
+    // flight: the threads that gave up wait once more, bounded, before the block leaves)
+    const bool late = use_smem && !mbar_wait0(&s_bar, 1 << 22);
+    if (__syncthreads_or(late)) {                       // scalars, and this block's copy of R, complete
+        if (tid == 0) set_status(st, kErrTimeout);
+        if (late) mbar_wait0(&s_bar, 1 << 22);
+        return;
+    }
     const bool deg = s_sc[0] != 0.0;
     const int off = deg ? 1 : 0;
     const int n = m + 1 - off;                          // active size
@@ -1070,6 +1219,9 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         if (use_smem) { sh[0] = r00.hi; sl[0] = r00.lo; }
         else { Rh[0] = r00.hi; Rl[0] = r00.lo; }
     }
+    // (in global memory, the streamed products read them through the TMA unit: order these writes
+    // before its reads; a barrier follows before the first product)
+    if (!use_smem) asm volatile("fence.proxy.async.global;" ::: "memory");
 
     // 3. the start: row group `row` (active index), absolute index ra = row + off; the group's
     //    first lane (lead) speaks for the row in sums.  x = [nu; c_I] (not normalised) and A x in
@@ -1078,7 +1230,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     const int row = tid / tpr, kk = tid - row * tpr;
     const bool act = row < n, lead = act && kk == 0;
     const int ra = row + off;
-    const bool zero_start = deg && !(s_sc[2] > 0.0);
+    const bool zero_start = s_zero != 0;
     ff x = {0.0f, 0.0f}, ax = {0.0f, 0.0f};
     float d = 0.0f;
     if (act) {
@@ -1094,7 +1246,6 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         }
         d = ra == 0 ? s_row0[1].hi : Ah[(size_t)ra * ld + ra];
     }
-    const bool smem = use_smem != 0;
     float pv = 0.0f, apv = 0.0f;                        // search direction p and A p
     bool have_p = false;
     ff theta = {0.0f, 0.0f}, xx = {1.0f, 0.0f};
@@ -1107,13 +1258,18 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     // FP32 rounding of the steps taken since the last exact one (and the closed-form start's by
     // the float-float rounding of R)
     bool exact = false, want_exact = zero_start;
-    float refresh = 1e-6f;
+    float refresh = 1e-12f;                             // (relative |r|^2: |r| below 1e-6 of the scale)
     for (;; ++it) {
         // A x recomputed exactly for the current x when asked for
         if (want_exact) {
             if (lead) { xs[2 * ra] = x.hi; xs[2 * ra + 1] = x.lo; }
             __syncthreads();
-            ax = ff_row(Ah, Al, ld, nq, ra, kk, tpr, act, smem, xs);
+            if (use_smem) {
+                ax = ff_row(Ah, Al, ld, nq, ra, kk, tpr, act, xs);
+            } else {
+                eig_stream<true>(Rh, Rl, ldr, m + 1, nq, stg, srows, s_sbar, spar, xs, ys, st);
+                ax = act ? ff{ys[2 * ra], ys[2 * ra + 1]} : ff{0.0f, 0.0f};
+            }
             exact = true;
             want_exact = false;
         }
@@ -1131,26 +1287,27 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         //     preconditioner positive definite while theta is still above some diagonal entries;
         //     an indefinite one stalls the iteration)
         const float den = fmaxf(fabsf(d - th), 1e-4f * fmaxf(scale, 1e-30f));
-        float wv = act ? r / den : 0.0f;
+        float wv = act ? __fdividef(r, den) : 0.0f;
         const float xh = x.hi;
         float red[3] = {lead ? r * r : 0.0f, lead ? xh * wv : 0.0f, lead ? xh * pv : 0.0f};
         bsum_f<3>(red, s_rf, hf);
-        const float nres = sqrtf(red[0]);
-        const float tol = 1e-14f * scale;
+        const float nres2 = red[0];                     // |r|^2; the tests below compare squares
+        const float sc2 = scale * scale;
         // stop at the float-float floor, at the cap, or when progress has ended well below it;
         // only a residual of an exact A x ends the iteration: with an implicit one the step below
         // is taken and A x is recomputed at the start of the next iteration (likewise once the
-        // residual is below `refresh`, which then moves down three decades)
-        if (nres < best * 0.7f) { best = nres; stall = 0; } else ++stall;
-        const bool stop = !(nres > tol * sqrtf((float)n)) || it >= kEigMaxIt || (stall >= 4 && nres < 1e-11f * scale);
+        // residual is below `refresh`, which then moves down five decades: the steps after a
+        // refresh are about the residual's size, so the implicit A x drifts by about 1e-7 of it)
+        if (nres2 < best * 0.49f) { best = nres2; stall = 0; } else ++stall;
+        const bool stop = !(nres2 > 1e-28f * sc2 * (float)n) || it >= kEigMaxIt || (stall >= 4 && nres2 < 1e-22f * sc2);
         if (stop && exact) break;
-        if (!exact && (stop || nres < refresh * scale)) {
+        if (!exact && (stop || nres2 < refresh * sc2)) {
             want_exact = true;
-            refresh = fminf(refresh, nres / fmaxf(scale, 1e-30f)) * 1e-3f;
+            refresh = fminf(refresh, __fdividef(nres2, fmaxf(sc2, 1e-30f))) * 1e-10f;   // five decades of |r|
             if (stop) { best = 3.0e38f; stall = 0; }
         }
-        // w and p orthogonalised against x
-        const float ixx = 1.0f / ff_to_float(xx);
+        // w and p orthogonalised against x (A p likewise, with A x as held)
+        const float ixx = __fdividef(1.0f, ff_to_float(xx));
         wv -= red[1] * ixx * xh;
         if (have_p) {
             pv -= red[2] * ixx * xh;
@@ -1159,7 +1316,13 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         // (c) A w
         if (lead) ws[ra] = wv;
         __syncthreads();
-        const float awv = f_row(Ah, ld, nq, ra, kk, tpr, act, smem, ws);
+        float awv;
+        if (use_smem) {
+            awv = f_row(Ah, ld, nq, ra, kk, tpr, act, ws);
+        } else {
+            eig_stream<false>(Rh, Rl, ldr, m + 1, nq, stg, srows, s_sbar, spar, ws, ys, st);
+            awv = act ? ys[ra] : 0.0f;
+        }
         // (d) projections on span{x, w, p}, the pencil shifted by theta: its x row is
         //     (A x - theta x) . [x, w, p] = [0, r.w, r.p]
         const float aws = awv - th * wv, aps = apv - th * pv;
@@ -1174,18 +1337,18 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         const float rw = pr[0], rp = pr[1], sww = pr[2], swp = pr[3], spp = pr[4];
         const float gxx = ff_to_float(xx), gxw = 0.0f, gxp = 0.0f, gww = pr[5], gwp = pr[6], gpp = pr[7];
         float yx = 1.0f, yw = 0.0f, yp = 0.0f;
-        const float l00 = sqrtf(gxx), il00 = 1.0f / l00;
+        const float il00 = rsqrtf(gxx);                 // L = [l00 0 0; l10 l11 0; l20 l21 l22], inverses of its diagonal
         const float l10 = gxw * il00, l20 = gxp * il00;
         const float d11 = gww - l10 * l10;
         if (d11 > 1e-12f * gww && gww > 0.0f) {
-            const float l11 = sqrtf(d11), il11 = 1.0f / l11;
+            const float il11 = rsqrtf(d11);
             bool use_p = have_p && gpp > 0.0f;
-            float l21 = 0.0f, l22 = 0.0f, il22 = 0.0f;
+            float l21 = 0.0f, il22 = 0.0f;
             if (use_p) {
                 l21 = (gwp - l20 * l10) * il11;
                 const float d22 = gpp - l20 * l20 - l21 * l21;
                 use_p = d22 > 1e-6f * gpp;
-                if (use_p) { l22 = sqrtf(d22); il22 = 1.0f / l22; }
+                if (use_p) il22 = rsqrtf(d22);
             }
             // M = L^-1 P (rows), then C = M L^-T
             const float m00 = 0.0f, m01 = rw * il00, m02 = rp * il00;
@@ -1259,8 +1422,9 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     const bool bad = !isfinite(gamma) || !(gamma > 1e-200);
     // 5. eta (Eq. def-z) and the compression thresholds (thread i: coordinate i), while thread 0
     //    forms the new scale s' = s gamma (double-double) and 1 / s'
-    double eta = 0.0, zn = 0.0;
+    double eta = 0.0, zn = 0.0, ct = 0.0;
     if (tid < m) {
+        ct = cI[tid];                                   // reloaded: nothing of step 1 stays live in the loop
         zn = sgn * (zd[tid + 1] * zs);
         eta = zn - gamma * ct;
         etaout[tid] = eta;
@@ -1311,10 +1475,12 @@ __device__ void mc_update_block(const Problem &P, McState *ms, IterState *st, co
                                 const double *etaout, const float *Rh, const float *Rl, int ldr, int m,
                                 float *s_eta, double *s_red) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int i = tid; i < m; i += blockDim.x) {
-        const ff e = ff_from_double(etaout[i]);
-        s_eta[2 * i] = e.hi;
-        s_eta[2 * i + 1] = e.lo;
+    const int L = eig_len(m + 1), nq = L / 4;
+    // eta as float-float in R's absolute indexing (entry 0 and the padding are zero)
+    for (int a = tid; a < L; a += blockDim.x) {
+        const ff e = (a >= 1 && a <= m) ? ff_from_double(etaout[a - 1]) : ff{0.0f, 0.0f};
+        s_eta[2 * a] = e.hi;
+        s_eta[2 * a + 1] = e.lo;
     }
     // FP64 sums eta.c_I, eta.b_I, eta.eta (threads over coordinates)
     double ec = 0.0, eb = 0.0, ee = 0.0;
@@ -1325,21 +1491,39 @@ __device__ void mc_update_block(const Problem &P, McState *ms, IterState *st, co
         ee = fma(e, e, ee);
     }
     __syncthreads();
-    // eta^T H_II eta: warp w takes rows w, w + nw, ...; lane l the columns l, l + 32, ... of each
+    // eta^T H_II eta over R's rows and columns 1..m: warp w takes the row pairs (a, a + nw),
+    // a = 1 + w, 1 + w + 2 nw, ...; lane l the 4-column chunks l, l + 32, ... of both rows
+    const float4 *e4 = reinterpret_cast<const float4 *>(s_eta);
     float ah = 0.0f, al = 0.0f;
-    for (int i = warp; i < m; i += nw) {
-        const float *rh = Rh + (size_t)(i + 1) * ldr + 1, *rl = Rl + (size_t)(i + 1) * ldr + 1;
-        float th = 0.0f, tl = 0.0f;
-        for (int k = lane; k < m; k += 32) ff_mac(th, tl, rh[k], rl[k], ff{s_eta[2 * k], s_eta[2 * k + 1]});
-        const ff t = ff_mul(ff_norm(th, tl), ff{s_eta[2 * i], s_eta[2 * i + 1]});
-        const ff s = ff_two_sum(ah, t.hi);
-        ah = s.hi;
-        al = __fadd_rn(al, __fadd_rn(s.lo, t.lo));
+    for (int a = 1 + warp; a <= m; a += 2 * nw) {
+        const int b = a + nw;
+        const bool two = b <= m;
+        const float4 *h0 = reinterpret_cast<const float4 *>(Rh + (size_t)a * ldr);
+        const float4 *l0 = reinterpret_cast<const float4 *>(Rl + (size_t)a * ldr);
+        const float4 *h1 = reinterpret_cast<const float4 *>(Rh + (size_t)(two ? b : a) * ldr);
+        const float4 *l1 = reinterpret_cast<const float4 *>(Rl + (size_t)(two ? b : a) * ldr);
+        float th0 = 0.0f, tl0 = 0.0f, th1 = 0.0f, tl1 = 0.0f;
+        for (int q = lane; q < nq; q += 32) {
+            const float4 hv0 = h0[q], lv0 = l0[q], hv1 = h1[q], lv1 = l1[q];
+            const float4 xa = e4[2 * q], xb = e4[2 * q + 1];
+            ff_mac(th0, tl0, hv0.x, lv0.x, ff{xa.x, xa.y});
+            ff_mac(th0, tl0, hv0.y, lv0.y, ff{xa.z, xa.w});
+            ff_mac(th0, tl0, hv0.z, lv0.z, ff{xb.x, xb.y});
+            ff_mac(th0, tl0, hv0.w, lv0.w, ff{xb.z, xb.w});
+            ff_mac(th1, tl1, hv1.x, lv1.x, ff{xa.x, xa.y});
+            ff_mac(th1, tl1, hv1.y, lv1.y, ff{xa.z, xa.w});
+            ff_mac(th1, tl1, hv1.z, lv1.z, ff{xb.x, xb.y});
+            ff_mac(th1, tl1, hv1.w, lv1.w, ff{xb.z, xb.w});
+        }
+        ff t = ff_mul(ff_norm(th0, tl0), ff{s_eta[2 * a], s_eta[2 * a + 1]});
+        if (two) t = ff_add(t, ff_mul(ff_norm(th1, tl1), ff{s_eta[2 * b], s_eta[2 * b + 1]}));
+        const ff u = ff_two_sum(ah, t.hi);
+        ah = u.hi;
+        al = __fadd_rn(al, __fadd_rn(u.lo, t.lo));
     }
     ff eh = ff_norm(ah, al);
-    for (int o = 16; o > 0; o >>= 1)
-        eh = ff_add(eh, ff{__shfl_down_sync(0xffffffffu, eh.hi, o), __shfl_down_sync(0xffffffffu, eh.lo, o)});
     for (int o = 16; o > 0; o >>= 1) {
+        eh = ff_add(eh, ff{__shfl_down_sync(0xffffffffu, eh.hi, o), __shfl_down_sync(0xffffffffu, eh.lo, o)});
         ec += __shfl_down_sync(0xffffffffu, ec, o);
         eb += __shfl_down_sync(0xffffffffu, eb, o);
         ee += __shfl_down_sync(0xffffffffu, ee, o);
@@ -1349,22 +1533,28 @@ __device__ void mc_update_block(const Problem &P, McState *ms, IterState *st, co
         reinterpret_cast<ff *>(s_red + 4 * warp + 3)[0] = eh;
     }
     __syncthreads();
-    if (tid != 0) return;
+    if (warp != 0) return;
+    // warp 0: the warps' sums in order (every lane), then mu' (lane 0) and alpha' (lane 1) in the same
+    // instructions, double-double
     double sc = 0.0, sb = 0.0, se = 0.0;
     ff sh = {0.0f, 0.0f};
     for (int q = 0; q < nw; ++q) {
         sc += s_red[4 * q]; sb += s_red[4 * q + 1]; se += s_red[4 * q + 2];
         sh = ff_add(sh, reinterpret_cast<const ff *>(s_red + 4 * q + 3)[0]);
     }
-    const double eHe = ff_to_double(sh);
-    const dd mu0 = ms->mu, al0 = ms->alpha, s_new = ms->pend_scale;
-    const double gamma = ms->pend_gamma, dx0 = ms->dx;
+    const dd mu0 = ms->mu, al0 = ms->alpha;
+    const double gamma = ms->pend_gamma;
+    const bool a1 = lane == 1;
+    const dd g2 = dd_two_prod(gamma, gamma);
+    const dd out = dd_add(dd_add(dd_mul(g2, a1 ? al0 : mu0), dd_two_prod(2.0 * gamma, a1 ? sb : sc)),
+                          dd{a1 ? ff_to_double(sh) : se, 0.0});
+    const dd al_n = {__shfl_sync(0xffffffffu, out.hi, 1), __shfl_sync(0xffffffffu, out.lo, 1)};
+    const double dxr = sqrt(se);
+    if (lane != 0) return;
+    const dd mu_n = out, s_new = ms->pend_scale;
+    const double dx0 = ms->dx;
     const long long its = ms->iterations, eit = ms->eig_iters_total;
     const int it = ms->pend_it, deg = ms->pend_deg;
-    // mu and alpha (Alg. 2 update of c) in double-double
-    const dd g2 = dd_two_prod(gamma, gamma);
-    const dd mu_n = dd_add(dd_add(dd_mul(g2, mu0), dd_two_prod(2.0 * gamma, sc)), dd{se, 0.0});
-    const dd al_n = dd_add(dd_add(dd_mul(g2, al0), dd_two_prod(2.0 * gamma, sb)), dd{eHe, 0.0});
     const bool ok = isfinite(mu_n.hi) && isfinite(al_n.hi);
     const dd mu_k = ok ? mu_n : mu0, al_k = ok ? al_n : al0;
     if (!ok) {
@@ -1375,7 +1565,7 @@ __device__ void mc_update_block(const Problem &P, McState *ms, IterState *st, co
         ms->scale = s_new;
         st->scale = s_new;
     }
-    const double dxn = P.theta * dx0 + (1.0 - P.theta) * sqrt(se);
+    const double dxn = P.theta * dx0 + (1.0 - P.theta) * dxr;
     ms->energy = dd_div_to_d(al_k, mu_k);
     ms->iterations = its + 1;
     ms->dx = dxn;
@@ -1979,10 +2169,12 @@ __global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, do
 // host wrappers
 // ---------------------------------------------------------------------------
 size_t mc_eigen_smem(int m) {
-    const int n1 = m + 1, ldr = 32 * ((n1 + 31) / 32);
-    const size_t lds = (size_t)eig_lds(ldr, eig_tpr(n1));
-    return ((n1 <= kEigSmemN ? 2 * (size_t)n1 * lds : 0) + eig_vec_floats(n1)) * sizeof(float);
+    const int n1 = m + 1;
+    const size_t r = n1 <= kEigSmemN ? 2 * (size_t)n1 * (size_t)eig_ldr(n1)
+                                     : 2 * (size_t)eig_len(n1) + 4 * (size_t)eig_stage_rows(n1) * eig_ldr(n1);
+    return (r + eig_vec_floats(n1)) * sizeof(float);
 }
+int mc_ldr(int m) { return eig_ldr(m + 1); }
 int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
 int mc_max_m() { return kEigMaxN - 1; }
 
@@ -2083,10 +2275,12 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
     k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
     mark();
     k_mc_prepare<<<(b.m + kPrepWarps - 1) / kPrepWarps, 32 * kPrepWarps, 0, s>>>(
-        P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.Rh, b.Rl, b.ldr, b.coltab, b.collists, b.geom.nsA + b.geom.nsB);
+        P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.rowf, b.Rh, b.Rl, b.ldr, b.coltab, b.collists,
+        b.geom.nsA + b.geom.nsB);
     mark();
     k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc,
-                                                                    b.Hdiag, b.Rh, b.Rl, b.ldr, eig_tpr(b.m + 1),
+                                                                    b.Hdiag, b.rowf, b.Rh, b.Rl, b.ldr,
+                                                                    eig_tpr(b.m + 1),
                                                                     b.m + 1 <= kEigSmemN ? 1 : 0,
                                                                     b.w, b.thr, b.eta);
     mark();

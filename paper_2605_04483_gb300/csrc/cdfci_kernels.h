@@ -92,6 +92,7 @@ struct McBuffers {
     unsigned int *hist;            // 4096-bin radix histogram, then the last-block counter
     McSel *sel, *inbin, *ties;     // chosen set, threshold-digit candidates, exact-tie scratch
     double *cI, *bI, *Hdiag, *HIIc, *w, *thr, *eta, *gathp;   // gathp: m x geom.per_col item partials
+    float4 *rowf;                  // per chosen row: (c, b), (H_II c_I, b - H_II c_I) as float-float pairs
     ColEnt *coltab;                // m columns x (nsA + nsB) single excitations
     ColLists *collists;            // m columns' orbital lists
     unsigned int *work;            // the scatter's item counter (reset by k_mc_finalize)
@@ -102,6 +103,7 @@ struct McBuffers {
     long long cap_cand;            // entries of cand / gkey / ties
 };
 size_t mc_eigen_smem(int m);
+int mc_ldr(int m);                  // row stride of R for a block of m coordinates
 int mc_max_m();
 int mc_scatter_grid(const Problem &P);
 McGeom mc_geometry(const Problem &P);
