@@ -20,6 +20,7 @@
 //   k_mc_finalize  the recalculated b_I, counters, snapshot.
 // Stored values are c_j / s and b_j / s for a global scale s, so that
 // c <- gamma c costs O(1): s <- gamma s.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +29,8 @@
 #include "cdfci_kernels.h"
 
 namespace cdfci {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -144,31 +147,40 @@ __device__ __forceinline__ void ff_mac(float &sh, float &sl, float ah, float al,
     sl = __fadd_rn(sl, __fadd_rn(s.lo, e));
 }
 
-// ---------------------------------------------------------------------------
-// Block reductions with one barrier each.  Every warp reduces in a fixed tree,
-// lane 0 stores the warp's value, and after the barrier every thread adds the
-// warps' values in warp order, so all threads hold bit-identical results.  Two
-// scratch halves alternate: a half is rewritten only after the barrier of the
-// following reduction, which every reader of it has passed.  (The trees have
-// a fixed depth, fully unrolled, so that the K sums' shuffles interleave.)
-// ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void bsum_f(float (&v)[K], float *scr, int &half) {
+// Block or cluster sums of K values held by the row leads (the other threads
+// hold zero): every warp reduces in a fixed tree, lane 0 of every warp writes
+// its K partials into slot (rank * warps + warp) of the scratch of every CTA
+// of the cluster (CL; else its own block's), one barrier, and every thread
+// adds the slots in a fixed xor butterfly, so all threads of all CTAs hold
+// bit-identical sums.  Two scratch halves alternate: a half is rewritten only
+// after the barrier of the following sum, which every reader of it has passed.
+// The trees have a fixed depth, fully unrolled, so that the K sums interleave.
+template <bool CL, int K>
+__device__ __forceinline__ void bsum_f(float (&v)[K], float *scr, int &half, unsigned rank, unsigned C) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[k] = __fadd_rn(v[k], __shfl_down_sync(0xffffffffu, v[k], off));
-    float *s = scr + half * 32 * 16;                     // fixed stride: K <= 16
-    if (lane == 0)
+    float *s = scr + half * 32 * 16;                     // fixed stride: K <= 16, slots <= 32
+    const int slot = (int)rank * nw + warp, ns = (int)C * nw;
+    if (lane == 0) {
+        if (CL) {
+            cg::cluster_group cl = cg::this_cluster();
+            for (unsigned r = 0; r < C; ++r) {
+                float *d = cl.map_shared_rank(s, r);
 #pragma unroll
-        for (int k = 0; k < K; ++k) s[warp * K + k] = v[k];
-    __syncthreads();
-    // every warp sums the warps' values with an xor butterfly: each step adds
-    // commutative pairs, so all lanes of all warps end with the same bits
+                for (int k = 0; k < K; ++k) d[slot * K + k] = v[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) s[slot * K + k] = v[k];
+        }
+    }
+    if (CL) cg::this_cluster().sync(); else __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float t = lane < nw ? s[lane * K + k] : 0.0f;
+        float t = lane < ns ? s[lane * K + k] : 0.0f;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
         v[k] = t;
@@ -176,8 +188,8 @@ __device__ __forceinline__ void bsum_f(float (&v)[K], float *scr, int &half) {
     half ^= 1;
 }
 
-template <int K>
-__device__ __forceinline__ void bsum_ff(ff (&v)[K], ff *scr, int &half) {
+template <bool CL, int K>
+__device__ __forceinline__ void bsum_ff(ff (&v)[K], ff *scr, int &half, unsigned rank, unsigned C) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -186,22 +198,54 @@ __device__ __forceinline__ void bsum_ff(ff (&v)[K], ff *scr, int &half) {
             const ff o = {__shfl_down_sync(0xffffffffu, v[k].hi, off), __shfl_down_sync(0xffffffffu, v[k].lo, off)};
             v[k] = ff_add(v[k], o);
         }
-    ff *s = scr + half * 32 * 2;                         // fixed stride: K <= 2
-    if (lane == 0)
+    ff *s = scr + half * 32 * 2;                         // fixed stride: K <= 2, slots <= 32
+    const int slot = (int)rank * nw + warp, ns = (int)C * nw;
+    if (lane == 0) {
+        if (CL) {
+            cg::cluster_group cl = cg::this_cluster();
+            for (unsigned r = 0; r < C; ++r) {
+                ff *d = cl.map_shared_rank(s, r);
 #pragma unroll
-        for (int k = 0; k < K; ++k) s[warp * K + k] = v[k];
-    __syncthreads();
-    // xor butterfly over the warps' values (ff_add is commutative bit for bit:
-    // TwoSum's error term is exact), identical in every lane and warp
+                for (int k = 0; k < K; ++k) d[slot * K + k] = v[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) s[slot * K + k] = v[k];
+        }
+    }
+    if (CL) cg::this_cluster().sync(); else __syncthreads();
+    // xor butterfly over the slots (ff_add is commutative bit for bit: TwoSum's error term is exact)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        ff t = lane < nw ? s[lane * K + k] : ff{0.0f, 0.0f};
+        ff t = lane < ns ? s[lane * K + k] : ff{0.0f, 0.0f};
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
             t = ff_add(t, ff{__shfl_xor_sync(0xffffffffu, t.hi, off), __shfl_xor_sync(0xffffffffu, t.lo, off)});
         v[k] = t;
     }
     half ^= 1;
+}
+
+// an FP64 sum over the cluster (or block) of one value per thread, in every thread (fixed order)
+template <bool CL>
+__device__ __forceinline__ double csum_d(double v, double *scr, unsigned rank, unsigned C) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int slot = (int)rank * nw + warp, ns = (int)C * nw;
+    if (lane == 0) {
+        if (CL) {
+            cg::cluster_group cl = cg::this_cluster();
+            for (unsigned r = 0; r < C; ++r) cl.map_shared_rank(scr, r)[slot] = v;
+        } else {
+            scr[slot] = v;
+        }
+    }
+    if (CL) cg::this_cluster().sync(); else __syncthreads();
+    double t = lane < ns ? scr[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    return t;
 }
 
 // FP64 warp sum, result in every lane (fixed tree, broadcast from lane 0)
@@ -805,20 +849,35 @@ __global__ void __launch_bounds__(32 * kPrepWarps) k_mc_prepare(Problem P, McSta
 constexpr int kEigSmemN = 160;      // A in shared memory (hi and lo) up to this size
 constexpr int kEigMaxIt = 200;
 
-// Threads per row of the reduced problem and R's row stride (in global and,
-// for n1 <= kEigSmemN, in shared memory) for a problem of size n1 = m + 1.
-// 2 threads per row while R is in shared memory (n1 <= 160), else 1 (the
-// products then stream R through shared memory with all threads on every
-// block of rows, independent of the row groups).  The stride is a multiple of 32 floats, plus
-// 4 tpr when R is copied to shared memory: that puts the 16-byte loads of a
-// quarter warp (8 lanes: 8 / tpr rows, tpr chunks each) on distinct banks,
-// and the copy is one bulk transfer per array.
-__host__ __device__ __forceinline__ int eig_tpr(int n1) {
-    return n1 <= kEigSmemN ? 2 : 1;
+// How the reduced problem of size n1 = m + 1 is laid out:
+//   n1 <= kEigSmemN: one CTA, R in its shared memory, 2 threads per row;
+//   else a cluster of C = 2, 4 or 8 CTAs, each holding a block of `crows` rows
+//   of R (hi and lo) in its shared memory, tpr threads per row, when such a
+//   split fits (at most 32 warps in the cluster, the rows within
+//   kEigClusterBytes per CTA);
+//   else one CTA streaming R from global memory (C = 0), 1 thread per row.
+constexpr size_t kEigClusterBytes = 192 * 1024;
+struct EigCfg {
+    int C, tpr, crows;
+};
+__host__ __device__ __forceinline__ EigCfg eig_cfg(int n1) {
+    if (n1 <= kEigSmemN) return EigCfg{1, 2, n1};
+    for (int C = 2; C <= 8; C *= 2) {
+        const int crows = (n1 + C - 1) / C;
+        for (int tpr = 2; tpr >= 1; --tpr) {
+            const int nw = tpr * ((crows + 31) / 32);
+            const size_t ldr = 32 * (size_t)((n1 + 31) / 32) + 4 * (size_t)tpr;
+            if (C * nw <= 32 && 8 * (size_t)crows * ldr <= kEigClusterBytes) return EigCfg{C, tpr, crows};
+        }
+    }
+    return EigCfg{0, 1, n1};
 }
-__host__ __device__ __forceinline__ int eig_ldr(int n1) {
-    return 32 * ((n1 + 31) / 32) + (n1 <= kEigSmemN ? 4 * eig_tpr(n1) : 0);
-}
+// threads per row and R's row stride: a multiple of 32 floats plus 4 tpr, which
+// puts the 16-byte loads of a quarter warp (8 lanes: 8 / tpr rows, tpr chunks
+// each) on distinct banks; the same stride in global and shared memory makes
+// each CTA's block of rows one contiguous bulk copy
+__host__ __device__ __forceinline__ int eig_tpr(int n1) { return eig_cfg(n1).tpr; }
+__host__ __device__ __forceinline__ int eig_ldr(int n1) { return 32 * ((n1 + 31) / 32) + 4 * eig_tpr(n1); }
 // entries of a vector in absolute indexing, a multiple of 4
 __host__ __device__ __forceinline__ int eig_len(int n1) { return 4 * ((n1 + 3) / 4); }
 
@@ -1073,83 +1132,99 @@ __device__ void eig_stream(const float *Rh, const float *Rl, int ldr, int n1, in
     if (late) set_status(st, kErrTimeout);
 }
 
+// CL = false: one CTA holds the whole problem (R in its shared memory when
+// use_smem, else streamed from global memory); CL = true: a cluster of C CTAs,
+// CTA r holding rows [r crows, (r + 1) crows) of R in its shared memory, the
+// vectors x and w gathered in full in every CTA before each product, the sums
+// taken over the cluster.  Every CTA computes the scalar steps itself, from
+// the same sums in the same order, so they agree bit for bit.
+template <bool CL>
 __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                        const double *cI, const double *bI, const double *HIIc,
                                                        const double *Hdiag, const float4 *rowf, float *Rh, float *Rl,
-                                                       int ldr, int tpr, int use_smem, double *w, double *thr,
-                                                       double *etaout) {
+                                                       int ldr, int tpr, int use_smem, int crows, double *w,
+                                                       double *thr, double *etaout) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float s_rf[2 * 32 * 16];
     __shared__ ff s_rff[2 * 32 * 2];
     __shared__ double s_red[32 * 4];
     __shared__ ff s_row0[4];                            // nu, R_00, (A x)_0 of the start, 1 / nu
+    __shared__ ff s_x0;                                 // x_0 at the end (CL: from CTA 0)
     __shared__ double s_sc[8];
     __shared__ float s_drms;
-    __shared__ int s_nzr[32], s_flag, s_zero;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int s_nzr[32], s_flag, s_zero, s_late[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwb = blockDim.x >> 5;
     if (ms->done || st->status) return;
-    const int m = ms->m_sel;
-    const int wm = (m + 31) >> 5;                       // warps holding a coordinate of I (thread t: coordinate t)
+    unsigned rank = 0, C = 1;
+    if (CL) {
+        rank = cg::this_cluster().block_rank();
+        C = cg::this_cluster().num_blocks();
+    }
+    const int m = ms->m_sel, n1 = m + 1;
+    // this CTA's rows of R (absolute indices [a0, a1)); one CTA: all
+    const int a0 = CL ? (int)rank * crows : 0, a1 = CL ? min(a0 + crows, n1) : n1;
+    const bool in_smem = CL || use_smem;
     // the state scalars, loaded (thread 0) ahead of the sums; read after the barriers below
     __shared__ dd s_mu0, s_al0, s_sc0;
     __shared__ long long s_nnz0;
     if (tid == 0) { s_mu0 = ms->mu; s_al0 = ms->alpha; s_sc0 = ms->scale; s_nnz0 = ms->nnz_c; }
     int hf = 0, hff = 0;
-    const int lds = ldr;                                // R's stride in shared memory too
-    const int L = eig_len(m + 1), nq = L / 4;
-    float *sh = sm, *sl = sm + (size_t)(m + 1) * lds;
-    // 0. start the copy of R (rows 0..m, hi and lo) into shared memory: one bulk copy per array,
-    //    issued by thread 0 after arming the barrier; it completes behind steps 1 and 2
+    const int L = eig_len(n1), nq = L / 4;
+    const int nown = a1 > a0 ? a1 - a0 : 0;             // rows held here
+    // (the layout uses crows, the same in every CTA of a cluster, so that an array's offset, which
+    // the other CTAs' writes address, does not depend on this CTA's own number of rows)
+    float *sh = sm, *sl = sm + (size_t)crows * ldr;
+    // 0. start the copy of this CTA's rows of R (hi and lo) into shared memory: one bulk copy per
+    //    array (R is row-major with stride ldr), issued by thread 0 after arming the barrier; it
+    //    completes behind steps 1 and 2
     __shared__ unsigned long long s_bar;
-    if (use_smem && tid == 0) {
-        const unsigned bytes = (unsigned)(m + 1) * (unsigned)ldr * 4u;
+    if (in_smem && tid == 0 && nown > 0) {
+        const unsigned bytes = (unsigned)nown * (unsigned)ldr * 4u;
         mbar_init_arm(&s_bar, 2u * bytes);
-        bulk_g2s(sh, Rh, bytes, &s_bar);
-        bulk_g2s(sl, Rl, bytes, &s_bar);
+        bulk_g2s(sh, Rh + (size_t)a0 * ldr, bytes, &s_bar);
+        bulk_g2s(sl, Rl + (size_t)a0 * ldr, bytes, &s_bar);
     }
     // R in global memory: two stage buffers for the streamed products, their barriers armed later
     __shared__ unsigned long long s_sbar[2];
     unsigned spar[2] = {0u, 0u};
-    if (!use_smem && tid == 0) {
+    if (!in_smem && tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_sbar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_sbar[1])) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    float *vec = use_smem ? sm + 2 * (size_t)(m + 1) * lds : sm;
+    float *vec = in_smem ? sm + 2 * (size_t)crows * ldr : sm;
     float *xs = vec;                                    // float-float x (2 L floats)
     float *ws = vec + 2 * L;                            // FP32 w (L floats)
     double *zd = reinterpret_cast<double *>(vec + 3 * L);   // z (L doubles); first the start's A x (float-float)
     float *hs = vec + 5 * L;                            // the start's H_II c_I (float-float, 2 L floats)
     float *ys = vec + 7 * L;                            // streamed products' results (2 L floats)
     float *stg = vec + 9 * L;                           // stage buffers
-    const int srows = eig_stage_rows(m + 1);
-    const float *Ah = use_smem ? sh : Rh, *Al = use_smem ? sl : Rl;
-    const int ld = use_smem ? lds : ldr;
+    const int srows = eig_stage_rows(n1);
 
-    // 1. sums over I (FP64): c.c, c.b, c.H_II c, |diag H_II|^2, nonzeros (warps holding I);
-    //    the coordinates' start values (float-float, from k_mc_prepare) staged at their absolute
-    //    index i + 1
-    double c0 = 0.0, bt = 0.0, ht = 0.0, hd = 0.0;
-    float4 f0 = {0.0f, 0.0f, 0.0f, 0.0f}, f1 = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (tid < m) {
-        c0 = cI[tid]; bt = bI[tid]; ht = HIIc[tid]; hd = Hdiag[tid];
-        f0 = rowf[2 * tid]; f1 = rowf[2 * tid + 1];
-    }
-    if (warp < wm) {
-        const double t = wsum4(c0 * c0, c0 * bt, c0 * ht, hd * hd);
-        const int nzw = __reduce_add_sync(0xffffffffu, (__double_as_longlong(c0) << 1) != 0 ? 1 : 0);
-        if ((lane & 7) == 0) s_red[warp * 4 + (lane >> 3)] = t;
-        if (lane == 0) s_nzr[warp] = nzw;
-    }
-    const ff bh_f = {f1.z, f1.w};                       // nu R_0i = b_i - (H_II c_I)_i
-    if (tid < m) {
-        const int a = tid + 1;
+    // 1. sums over I (FP64): c.c, c.b, c.H_II c, |diag H_II|^2, nonzeros (thread t: coordinates
+    //    t, t + blockDim, ...; the warps holding one); the coordinates' start values (float-float,
+    //    from k_mc_prepare) staged at their absolute index i + 1
+    const int nsw = (min(m, (int)blockDim.x) + 31) >> 5;
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    int nzc = 0;
+    for (int t = tid; t < m; t += blockDim.x) {
+        const double c0 = cI[t], bt = bI[t], ht = HIIc[t], hd = Hdiag[t];
+        p0 = fma(c0, c0, p0); p1 = fma(c0, bt, p1); p2 = fma(c0, ht, p2); p3 = fma(hd, hd, p3);
+        nzc += (__double_as_longlong(c0) << 1) != 0 ? 1 : 0;
+        const float4 f0 = rowf[2 * t], f1 = rowf[2 * t + 1];
+        const int a = t + 1;
         xs[2 * a] = f0.x; xs[2 * a + 1] = f0.y;         // c_i
         float *az = reinterpret_cast<float *>(zd);
         az[2 * a] = f0.z; az[2 * a + 1] = f0.w;         // b_i
         hs[2 * a] = f1.x; hs[2 * a + 1] = f1.y;         // (H_II c_I)_i
     }
-    for (int t = m + 1 + tid; t < L; t += blockDim.x) { xs[2 * t] = 0.0f; xs[2 * t + 1] = 0.0f; ws[t] = 0.0f; }
+    if (warp < nsw) {
+        const double t = wsum4(p0, p1, p2, p3);
+        const int nzw = __reduce_add_sync(0xffffffffu, nzc);
+        if ((lane & 7) == 0) s_red[warp * 4 + (lane >> 3)] = t;
+        if (lane == 0) s_nzr[warp] = nzw;
+    }
+    for (int t = n1 + tid; t < L; t += blockDim.x) { xs[2 * t] = 0.0f; xs[2 * t + 1] = 0.0f; ws[t] = 0.0f; }
     if (tid == 0) { xs[0] = 0.0f; xs[1] = 0.0f; ws[0] = 0.0f; }
     __syncthreads();
     // 2. warp 0: the four sums (lane 8 k + j adds value k of warps j, j + 8, ..., then a
@@ -1160,14 +1235,14 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     //    nu, R_00 and (A x)_0 (float-float).  Tests on FP64 values are integer tests of their bits.
     if (warp == 0) {
         double t = 0.0;
-        for (int q = lane & 7; q < wm; q += 8) t += s_red[q * 4 + (lane >> 3)];
+        for (int q = lane & 7; q < nsw; q += 8) t += s_red[q * 4 + (lane >> 3)];
         t += __shfl_xor_sync(0xffffffffu, t, 4);
         t += __shfl_xor_sync(0xffffffffu, t, 2);
         t += __shfl_xor_sync(0xffffffffu, t, 1);
         const double cc = __shfl_sync(0xffffffffu, t, 0), cb = __shfl_sync(0xffffffffu, t, 8);
         const double chc = __shfl_sync(0xffffffffu, t, 16), hh = __shfl_sync(0xffffffffu, t, 24);
         int nz = 0;
-        for (int q = 0; q < wm; ++q) nz += s_nzr[q];
+        for (int q = 0; q < nsw; ++q) nz += s_nzr[q];
         const dd a = lane == 0 ? s_mu0 : s_al0;
         const double p = lane == 0 ? -cc : (lane == 1 ? -2.0 * cb : -cb);
         const double q = lane == 1 ? chc : 0.0;
@@ -1195,47 +1270,64 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         }
     }
     // the copy of R: a bounded wait; a copy that never lands is an error (its bytes may still be in
-    // flight: the threads that gave up wait once more, bounded, before the block leaves)
-    const bool late = use_smem && !mbar_wait0(&s_bar, 1 << 22);
-    if (__syncthreads_or(late)) {                       // scalars, and this block's copy of R, complete
+    // flight: the threads that gave up wait once more, bounded, before the block leaves).  In a
+    // cluster the decision is shared, so that every CTA leaves or none.
+    const bool late = in_smem && nown > 0 && !mbar_wait0(&s_bar, 1 << 22);
+    bool any_late = __syncthreads_or(late);             // scalars, and this block's copy of R, complete
+    if (CL) {
+        if (tid == 0) {
+            cg::cluster_group cl = cg::this_cluster();
+            for (unsigned r = 0; r < C; ++r) cl.map_shared_rank(s_late, r)[rank] = any_late ? 1 : 0;
+        }
+        cg::this_cluster().sync();
+        any_late = false;
+        for (unsigned r = 0; r < C; ++r) any_late |= s_late[r] != 0;
+    }
+    if (any_late) {
         if (tid == 0) set_status(st, kErrTimeout);
         if (late) mbar_wait0(&s_bar, 1 << 22);
         return;
     }
     const bool deg = s_sc[0] != 0.0;
     const int off = deg ? 1 : 0;
-    const int n = m + 1 - off;                          // active size
-    // row and column 0 of R: R_0i = (b_i - (H_II c_I)_i) / nu (zero when not active); they are
-    // first read by the product A w after the barriers of the first sums below
-    if (tid < m) {
-        const ff r0 = deg ? ff{0.0f, 0.0f} : ff_mul(bh_f, s_row0[3]);
-        float *Wh = use_smem ? sh : Rh, *Wl = use_smem ? sl : Rl;
-        const int ldw = use_smem ? lds : ldr;
-        Wh[tid + 1] = r0.hi; Wl[tid + 1] = r0.lo;
-        Wh[(size_t)(tid + 1) * ldw] = r0.hi; Wl[(size_t)(tid + 1) * ldw] = r0.lo;
-    }
-    if (tid == 0) {
-        const ff r00 = deg ? ff{0.0f, 0.0f} : s_row0[1];
-        if (use_smem) { sh[0] = r00.hi; sl[0] = r00.lo; }
-        else { Rh[0] = r00.hi; Rl[0] = r00.lo; }
+    const int n = n1 - off;                             // active size
+    // row and column 0 of R: R_0i = (b_i - (H_II c_I)_i) / nu (zero when not active); column 0 for
+    // this CTA's rows, row 0 where it is held.  They are first read by the product A w after the
+    // barriers of the first sums below.
+    {
+        float *Wh = in_smem ? sh : Rh, *Wl = in_smem ? sl : Rl;
+        const ff inu = s_row0[3];
+        for (int t = tid; t < m; t += blockDim.x) {
+            const int a = t + 1;
+            const bool col = a >= a0 && a < a1, row = a0 == 0 && nown > 0;
+            if (!col && !row) continue;
+            const float4 f1 = rowf[2 * t + 1];
+            const ff r0 = deg ? ff{0.0f, 0.0f} : ff_mul(ff{f1.z, f1.w}, inu);
+            if (row) { Wh[a] = r0.hi; Wl[a] = r0.lo; }
+            if (col) { Wh[(size_t)(a - a0) * ldr] = r0.hi; Wl[(size_t)(a - a0) * ldr] = r0.lo; }
+        }
+        if (tid == 0 && a0 == 0 && nown > 0) {
+            const ff r00 = deg ? ff{0.0f, 0.0f} : s_row0[1];
+            Wh[0] = r00.hi; Wl[0] = r00.lo;
+        }
     }
     // (in global memory, the streamed products read them through the TMA unit: order these writes
     // before its reads; a barrier follows before the first product)
-    if (!use_smem) asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (!in_smem) asm volatile("fence.proxy.async.global;" ::: "memory");
 
-    // 3. the start: row group `row` (active index), absolute index ra = row + off; the group's
-    //    first lane (lead) speaks for the row in sums.  x = [nu; c_I] (not normalised) and A x in
-    //    closed form; degenerate: x = c_I, A x = H_II c_I; c = 0 (not reached in practice):
-    //    x = e_0 with A x computed
-    const int row = tid / tpr, kk = tid - row * tpr;
-    const bool act = row < n, lead = act && kk == 0;
-    const int ra = row + off;
+    // 3. the start: thread group `lr` of tpr threads takes absolute row ra = a0 + lr (active from
+    //    off); the group's first lane (lead) speaks for the row in sums.  x = [nu; c_I] (not
+    //    normalised) and A x in closed form; degenerate: x = c_I, A x = H_II c_I; c = 0 (not
+    //    reached in practice): x = e_off with A x computed
+    const int lr = tid / tpr, kk = tid - lr * tpr;
+    const int ra = a0 + lr;
+    const bool act = ra >= off && ra < a1, lead = act && kk == 0;
     const bool zero_start = s_zero != 0;
     ff x = {0.0f, 0.0f}, ax = {0.0f, 0.0f};
     float d = 0.0f;
     if (act) {
         if (zero_start) {
-            x = ff{row == 0 ? 1.0f : 0.0f, 0.0f};
+            x = ff{ra == off ? 1.0f : 0.0f, 0.0f};
         } else if (ra == 0) {
             x = s_row0[0];
             ax = s_row0[2];
@@ -1244,7 +1336,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             const float *az = deg ? hs : reinterpret_cast<const float *>(zd);
             ax = ff{az[2 * ra], az[2 * ra + 1]};
         }
-        d = ra == 0 ? s_row0[1].hi : Ah[(size_t)ra * ld + ra];
+        d = ra == 0 ? s_row0[1].hi : (in_smem ? sh[(size_t)lr * ldr + ra] : Rh[(size_t)ra * ldr + ra]);
     }
     float pv = 0.0f, apv = 0.0f;                        // search direction p and A p
     bool have_p = false;
@@ -1260,14 +1352,24 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     bool exact = false, want_exact = zero_start;
     float refresh = 1e-12f;                             // (relative |r|^2: |r| below 1e-6 of the scale)
     for (;; ++it) {
-        // A x recomputed exactly for the current x when asked for
+        // A x recomputed exactly for the current x when asked for (x gathered in full first)
         if (want_exact) {
-            if (lead) { xs[2 * ra] = x.hi; xs[2 * ra + 1] = x.lo; }
-            __syncthreads();
-            if (use_smem) {
-                ax = ff_row(Ah, Al, ld, nq, ra, kk, tpr, act, xs);
+            if (lead) {
+                if (CL) {
+                    cg::cluster_group cl = cg::this_cluster();
+                    for (unsigned r = 0; r < C; ++r) {
+                        float *d2 = cl.map_shared_rank(xs, r);
+                        d2[2 * ra] = x.hi; d2[2 * ra + 1] = x.lo;
+                    }
+                } else {
+                    xs[2 * ra] = x.hi; xs[2 * ra + 1] = x.lo;
+                }
+            }
+            if (CL) cg::this_cluster().sync(); else __syncthreads();
+            if (in_smem) {
+                ax = ff_row(sh, sl, ldr, nq, lr, kk, tpr, act, xs);
             } else {
-                eig_stream<true>(Rh, Rl, ldr, m + 1, nq, stg, srows, s_sbar, spar, xs, ys, st);
+                eig_stream<true>(Rh, Rl, ldr, n1, nq, stg, srows, s_sbar, spar, xs, ys, st);
                 ax = act ? ff{ys[2 * ra], ys[2 * ra + 1]} : ff{0.0f, 0.0f};
             }
             exact = true;
@@ -1276,7 +1378,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         // (a) theta = x.Ax / x.x, r = A x - theta x
         {
             ff t[2] = {lead ? ff_mul(x, ax) : ff{0.0f, 0.0f}, lead ? ff_mul(x, x) : ff{0.0f, 0.0f}};
-            bsum_ff<2>(t, s_rff, hff);
+            bsum_ff<CL, 2>(t, s_rff, hff, rank, C);
             xx = t[1];
             theta = ff_div(t[0], t[1]);
         }
@@ -1290,7 +1392,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         float wv = act ? __fdividef(r, den) : 0.0f;
         const float xh = x.hi;
         float red[3] = {lead ? r * r : 0.0f, lead ? xh * wv : 0.0f, lead ? xh * pv : 0.0f};
-        bsum_f<3>(red, s_rf, hf);
+        bsum_f<CL, 3>(red, s_rf, hf, rank, C);
         const float nres2 = red[0];                     // |r|^2; the tests below compare squares
         const float sc2 = scale * scale;
         // stop at the float-float floor, at the cap, or when progress has ended well below it;
@@ -1313,14 +1415,21 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
             pv -= red[2] * ixx * xh;
             apv -= red[2] * ixx * ff_to_float(ax);
         }
-        // (c) A w
-        if (lead) ws[ra] = wv;
-        __syncthreads();
+        // (c) A w (w gathered in full first)
+        if (lead) {
+            if (CL) {
+                cg::cluster_group cl = cg::this_cluster();
+                for (unsigned r2 = 0; r2 < C; ++r2) cl.map_shared_rank(ws, r2)[ra] = wv;
+            } else {
+                ws[ra] = wv;
+            }
+        }
+        if (CL) cg::this_cluster().sync(); else __syncthreads();
         float awv;
-        if (use_smem) {
-            awv = f_row(Ah, ld, nq, ra, kk, tpr, act, ws);
+        if (in_smem) {
+            awv = f_row(sh, ldr, nq, lr, kk, tpr, act, ws);
         } else {
-            eig_stream<false>(Rh, Rl, ldr, m + 1, nq, stg, srows, s_sbar, spar, ws, ys, st);
+            eig_stream<false>(Rh, Rl, ldr, n1, nq, stg, srows, s_sbar, spar, ws, ys, st);
             awv = act ? ys[ra] : 0.0f;
         }
         // (d) projections on span{x, w, p}, the pencil shifted by theta: its x row is
@@ -1330,7 +1439,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         if (!lead)
 #pragma unroll
             for (int q = 0; q < 8; ++q) pr[q] = 0.0f;
-        bsum_f<8>(pr, s_rf, hf);
+        bsum_f<CL, 8>(pr, s_rf, hf, rank, C);
         // Rayleigh-Ritz: the lowest eigenpair of (P - mu G) y = 0 with P = [0 rw rp; rw sww swp;
         // rp swp spp] and the Gram matrix G (x orthogonal to w and p), by the Cholesky factor L of
         // G: C = L^-1 P L^-T, y = L^-T v
@@ -1393,17 +1502,28 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         }
     }
     // 4. z = zs x, zs = sqrt(-lambda / x.x) (float-float); the reduced problem needs lambda < 0
+    //    (theta is the same in every CTA, so all return together)
     if (!(theta.hi < 0.0f || (theta.hi == 0.0f && theta.lo < 0.0f))) {
-        if (tid == 0) set_status(st, kErrNotNegative);
+        if (tid == 0 && rank == 0) set_status(st, kErrNotNegative);
         return;
     }
     const ff q = ff_div(ff_neg(theta), xx);
     const ff zs_f = ff_mul(q, ff_rsqrt(q));
     if (lead) zd[ra] = ff_to_double(x);
-    // sign (Eq. def-z wants gamma >= 0): z_0 >= 0 (thread 0 holds row 0); degenerate or z_0 = 0:
-    // z . c_I >= 0, the FP64 dot taken only then; gamma = z_0 / nu
+    // x_0 (row 0, with CTA 0's thread 0) to every CTA
+    if (tid == 0 && rank == 0) {
+        if (CL) {
+            cg::cluster_group cl = cg::this_cluster();
+            for (unsigned r = 0; r < C; ++r) *cl.map_shared_rank(&s_x0, r) = x;
+        } else {
+            s_x0 = x;
+        }
+    }
+    if (CL) cg::this_cluster().sync(); else __syncthreads();
+    // sign (Eq. def-z wants gamma >= 0): z_0 >= 0; degenerate or z_0 = 0: z . c_I >= 0, the FP64 dot
+    // taken only then; gamma = z_0 / nu (every CTA the same)
     if (tid == 0) {
-        const ff z0 = deg ? ff{0.0f, 0.0f} : ff_mul(zs_f, x);
+        const ff z0 = deg ? ff{0.0f, 0.0f} : ff_mul(zs_f, s_x0);
         s_flag = (deg || z0.hi == 0.0f) ? 1 : 0;
         s_sc[3] = z0.hi < 0.0f ? -1.0 : 1.0;
         const ff g = ff_mul(ff{fabsf(z0.hi), z0.hi < 0.0f ? -z0.lo : z0.lo}, s_row0[3]);
@@ -1411,44 +1531,46 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         s_sc[5] = ff_to_double(zs_f);
     }
     __syncthreads();
-    if (s_flag && warp == 0) {                          // block-uniform: s_flag is shared
-        double dot = 0.0;
-        for (int i = lane; i < m; i += 32) dot = fma(zd[i + 1], cI[i], dot);
-        dot = wsum_d(dot);
-        if (lane == 0) s_sc[3] = dot < 0.0 ? -1.0 : 1.0;
+    if (s_flag) {                                       // uniform over the cluster: s_flag agrees
+        const double dot = csum_d<CL>(lead && ra >= 1 ? zd[ra] * cI[ra - 1] : 0.0, s_red, rank, C);
+        if (tid == 0) s_sc[3] = dot < 0.0 ? -1.0 : 1.0;
+        __syncthreads();
     }
-    if (s_flag) __syncthreads();
     const double sgn = s_sc[3], gamma = s_sc[4], zs = s_sc[5];
     const bool bad = !isfinite(gamma) || !(gamma > 1e-200);
-    // 5. eta (Eq. def-z) and the compression thresholds (thread i: coordinate i), while thread 0
-    //    forms the new scale s' = s gamma (double-double) and 1 / s'
+    // 5. eta (Eq. def-z) and the compression thresholds (the lead of row i + 1: coordinate i), while
+    //    thread 0 forms the new scale s' = s gamma (double-double) and 1 / s'
+    const bool coord = lead && ra >= 1;
+    const int ic = ra - 1;
     double eta = 0.0, zn = 0.0, ct = 0.0;
-    if (tid < m) {
-        ct = cI[tid];                                   // reloaded: nothing of step 1 stays live in the loop
-        zn = sgn * (zd[tid + 1] * zs);
+    if (coord) {
+        ct = cI[ic];                                    // reloaded: nothing of step 1 stays live in the loop
+        zn = sgn * (zd[ra] * zs);
         eta = zn - gamma * ct;
-        etaout[tid] = eta;
-        thr[tid] = eta != 0.0 ? P.tau / fabs(eta) : 1.0e308;
+        etaout[ic] = eta;
+        thr[ic] = eta != 0.0 ? P.tau / fabs(eta) : 1.0e308;
     }
     if (tid == 0) {
         const dd s_new = dd_mul_d(s_sc0, gamma);
         s_sc[6] = 1.0 / s_new.hi;
-        ms->pend_scale = s_new;
-        ms->pend_gamma = gamma;
-        ms->pend_it = it;
-        ms->pend_deg = deg ? 1 : 0;
-        ms->n_cand = 0;                                 // the scatter builds the next candidate list
-        if (bad) set_status(st, kErrNonfinite);
+        if (rank == 0) {
+            ms->pend_scale = s_new;
+            ms->pend_gamma = gamma;
+            ms->pend_it = it;
+            ms->pend_deg = deg ? 1 : 0;
+            ms->n_cand = 0;                             // the scatter builds the next candidate list
+            if (bad) set_status(st, kErrNonfinite);
+        }
     }
     __syncthreads();
     // 6. the scatter weights and the new stored c_I; the change in nonzeros of c
     const double rsc = s_sc[6];
     bool to = false, from = false;
-    if (tid < m) {
-        w[tid] = eta * rsc;
+    if (coord) {
+        w[ic] = eta * rsc;
         if (!bad) {
-            P.table[sel[tid].slot].c = zn * rsc;
-            cnz_set(P, sel[tid].A, sel[tid].B);
+            P.table[sel[ic].slot].c = zn * rsc;
+            cnz_set(P, sel[ic].A, sel[ic].B);
         }
         from = ct != 0.0 && zn == 0.0;
         to = ct == 0.0 && zn != 0.0;
@@ -2170,12 +2292,19 @@ __global__ void k_mc_start(Problem P, McState *ms, IterState *st, McSel *sel, do
 // ---------------------------------------------------------------------------
 size_t mc_eigen_smem(int m) {
     const int n1 = m + 1;
-    const size_t r = n1 <= kEigSmemN ? 2 * (size_t)n1 * (size_t)eig_ldr(n1)
-                                     : 2 * (size_t)eig_len(n1) + 4 * (size_t)eig_stage_rows(n1) * eig_ldr(n1);
+    const EigCfg g = eig_cfg(n1);
+    size_t r;
+    if (g.C == 1) r = 2 * (size_t)n1 * (size_t)eig_ldr(n1);          // R in one CTA
+    else if (g.C > 1) r = 2 * (size_t)g.crows * (size_t)eig_ldr(n1);  // this CTA's rows of R
+    else r = 2 * (size_t)eig_len(n1) + 4 * (size_t)eig_stage_rows(n1) * eig_ldr(n1);   // streamed
     return (r + eig_vec_floats(n1)) * sizeof(float);
 }
+int mc_eigen_threads(int m) {
+    const EigCfg g = eig_cfg(m + 1);
+    return g.tpr * 32 * ((g.crows + 31) / 32);
+}
+int mc_eigen_cluster(int m) { return eig_cfg(m + 1).C; }
 int mc_ldr(int m) { return eig_ldr(m + 1); }
-int mc_eigen_threads(int m) { return eig_tpr(m + 1) * 32 * ((m + 1 + 31) / 32); }
 int mc_max_m() { return kEigMaxN - 1; }
 
 // the scatter's grid: the blocks that are resident at once on this device (warps take items from a counter)
@@ -2207,9 +2336,14 @@ McGeom mc_geometry(const Problem &P) {
 }
 
 cudaError_t mc_configure() {
-    size_t most = 0;
-    for (int m = 1; m < kEigMaxN; ++m) most = std::max(most, mc_eigen_smem(m));
-    cudaError_t e = cudaFuncSetAttribute(k_mc_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    size_t most = 0, most_cl = 0;
+    for (int m = 1; m < kEigMaxN; ++m) {
+        if (eig_cfg(m + 1).C > 1) most_cl = std::max(most_cl, mc_eigen_smem(m));
+        else most = std::max(most, mc_eigen_smem(m));
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_mc_eigen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_mc_eigen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most_cl);
     if (e != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -2278,11 +2412,30 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
         P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.rowf, b.Rh, b.Rl, b.ldr, b.coltab, b.collists,
         b.geom.nsA + b.geom.nsB);
     mark();
-    k_mc_eigen<<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc,
-                                                                    b.Hdiag, b.rowf, b.Rh, b.Rl, b.ldr,
-                                                                    eig_tpr(b.m + 1),
-                                                                    b.m + 1 <= kEigSmemN ? 1 : 0,
-                                                                    b.w, b.thr, b.eta);
+    {
+        const EigCfg g = eig_cfg(b.m + 1);
+        if (g.C > 1) {                                  // a cluster holding R's rows
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)g.C);
+            cfg.blockDim = dim3((unsigned)mc_eigen_threads(b.m));
+            cfg.dynamicSmemBytes = mc_eigen_smem(b.m);
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)g.C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, k_mc_eigen<true>, P, b.ms, b.st, (const McSel *)b.sel, (const double *)b.cI,
+                               (const double *)b.bI, (const double *)b.HIIc, (const double *)b.Hdiag,
+                               (const float4 *)b.rowf, b.Rh, b.Rl, b.ldr, g.tpr, 1, g.crows, b.w, b.thr, b.eta);
+        } else {
+            k_mc_eigen<false><<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(
+                P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Hdiag, b.rowf, b.Rh, b.Rl, b.ldr, g.tpr, g.C == 1 ? 1 : 0,
+                b.m + 1, b.w, b.thr, b.eta);
+        }
+    }
     mark();
     // one more block than the scatter's own: block 0 updates mu, alpha and the scale meanwhile
     k_mc_scatter<<<b.scatter_grid + 1, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.coltab, b.collists, b.geom, b.w, b.thr,
