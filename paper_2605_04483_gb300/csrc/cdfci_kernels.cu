@@ -360,7 +360,7 @@ __device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb,
     for (int k = 0; k < 4; ++k) cnt[k] = __reduce_add_sync(0xffffffffu, (unsigned)cnt[k]);
     err = (int)__reduce_or_sync(0xffffffffu, (unsigned)err);
     // gather: a fixed shuffle-down tree (skipped when every lane holds 0)
-    if (__any_sync(0xffffffffu, gather != 0.0)) {
+    if (__any_sync(0xffffffffu, !is_zero(gather))) {
         for (int off = 16; off > 0; off >>= 1) gather += __shfl_down_sync(0xffffffffu, gather, off);
         gather = __shfl_sync(0xffffffffu, gather, 0);
     }
@@ -543,7 +543,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                     pb = fma(ls.pHii, ls.pc, gsum);
                     gp = abs_bits(fma(ls.pmu_g, ls.pc, pb));
                     nslots += cnt[3];
-                    const long long pdiag = ls.pHii != 0.0 ? 1 : 0;
+                    const long long pdiag = is_zero(ls.pHii) ? 0 : 1;
                     ls.elements += cnt[0] + pdiag;
                     ls.applied += cnt[1] + pdiag;
                     ls.dropped += cnt[2];
@@ -613,7 +613,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 }
                 sel.eta = eta;
                 sel.mu_g = ls.mu.hi + fma(2.0 * eta, ci, eta * eta);
-                sel.bad = !isfinite(eta);
+                sel.bad = ((__double_as_longlong(eta) >> 52) & 0x7ff) == 0x7ff;   // not finite
                 s_hii = Hii;
             }
 #pragma unroll
@@ -791,9 +791,12 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 if (!sel.forced) {
                     ls.iterations += 1;
                     ls.dx = P.theta * ls.dx + (1.0 - P.theta) * fabs(sel.eta);
-                    if (P.dx_threshold > 0.0 && ls.dx < P.dx_threshold) ls.done = 1;
+                    // (dx >= 0: the bit patterns of non-negative doubles order like their values)
+                    const long long dxb = __double_as_longlong(ls.dx), thb = __double_as_longlong(P.dx_threshold);
+                    if (thb > 0 && dxb < thb) ls.done = 1;
                 }
-                ls.nnz_c += ((ci == 0.0 && ci_new != 0.0) ? 1 : 0) - ((ci != 0.0 && ci_new == 0.0) ? 1 : 0);
+                const bool z0 = is_zero(ci), z1 = is_zero(ci_new);
+                ls.nnz_c += ((z0 && !z1) ? 1 : 0) - ((!z0 && z1) ? 1 : 0);
                 ls.forced = 0;
                 ls.have_prev = 1;
                 s_done = ls.done;
