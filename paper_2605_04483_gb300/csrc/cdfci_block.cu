@@ -53,17 +53,28 @@ __device__ double hij_pair(const Problem &P, unsigned long long A1, unsigned lon
         const int i = __ffsll((long long)(X2 & (alpha ? dA : dB))) - 1;
         const int a = __ffsll((long long)(X1 & (alpha ? dA : dB))) - 1;
         // h_ia, then the occupied spin-orbitals of the column determinant in
-        // spin-orbital order (alpha, then beta), one running sum (element_value's order)
+        // spin-orbital order (alpha, then beta), one running sum (element_value's order); the
+        // terms (ia|kk) - (ik|ka) (same spin as the excitation) and (ia|kk) come from the
+        // single-excitation tables W3 and V3, eight loads in flight before their adds
+        const double *rw = P.W3 + ((size_t)i * N + a) * N, *rv = P.V3 + ((size_t)i * N + a) * N;
+        const double *tA = alpha ? rw : rv, *tB = alpha ? rv : rw;
         double v = __ldg(P.h + i * N + a);
-        for (unsigned long long m = A2; m; m &= m - 1) {
-            const int k = __ffsll((long long)m) - 1;
-            const double t = gi(g, N, i, a, k, k);
-            v += alpha ? t - gi(g, N, i, k, k, a) : t;
-        }
-        for (unsigned long long m = B2; m; m &= m - 1) {
-            const int k = __ffsll((long long)m) - 1;
-            const double t = gi(g, N, i, a, k, k);
-            v += alpha ? t : t - gi(g, N, i, k, k, a);
+        unsigned long long mA = A2, mB = B2;
+        while (mA | mB) {
+            double t[8];
+            bool ok[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool fa = mA != 0ull;
+                const unsigned long long mm = fa ? mA : mB;
+                ok[u] = mm != 0ull;
+                const int k = ok[u] ? __ffsll((long long)mm) - 1 : 0;
+                t[u] = ok[u] ? __ldg((fa ? tA : tB) + k) : 0.0;
+                if (fa) mA &= mA - 1; else mB &= mB - 1;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (ok[u]) v += t[u];
         }
         return apply_parity(v, X2 & between_mask(i, a));
     }
@@ -248,11 +259,6 @@ __device__ __forceinline__ double csum_d(double v, double *scr, unsigned rank, u
     return t;
 }
 
-// FP64 warp sum, result in every lane (fixed tree, broadcast from lane 0)
-__device__ __forceinline__ double wsum_d(double v) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    return __shfl_sync(0xffffffffu, v, 0);
-}
 
 // Lowest eigenpair of the symmetric 3 x 3 matrix [a00 a01 a02; . a11 a12; . . a22]
 // in FP32: the trigonometric form of the three real roots of the characteristic
@@ -1153,7 +1159,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     __shared__ double s_sc[8];
     __shared__ float s_drms;
     __shared__ int s_nzr[32], s_flag, s_zero, s_late[8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwb = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ms->done || st->status) return;
     unsigned rank = 0, C = 1;
     if (CL) {
