@@ -717,11 +717,16 @@ __global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, co
     const int need = ms->sel_level == 0 ? 0 : ms->sel_need;
     int p2 = 1;
     while (p2 < n_in) p2 <<= 1;
-    for (int i = tid; i < p2; i += blockDim.x) sk[i] = SelKey{i < n_in ? inbin[i].gkey : 0ull, i < n_in ? i : -1, 0};
+    // the in-bin candidates in shared memory first: the sort's tie-breaks (equal |g|, the common
+    // case on lattices) read their keys there
+    for (int i = tid; i < p2; i += blockDim.x) {
+        if (i < n_in) tmp[i] = inbin[i];
+        sk[i] = SelKey{i < n_in ? inbin[i].gkey : 0ull, i < n_in ? i : -1, 0};
+    }
     __syncthreads();
-    if (n_in > 1) bitonic_sk(sk, p2, inbin);
+    if (n_in > 1) bitonic_sk(sk, p2, tmp);
     const int take = need < n_in ? need : n_in;
-    for (int i = tid; i < take; i += blockDim.x) sel[n_above + i] = inbin[sk[i].i];
+    for (int i = tid; i < take; i += blockDim.x) sel[n_above + i] = tmp[sk[i].i];
     __syncthreads();
     const int msel = n_above + take;
     int q2 = 1;
@@ -2133,94 +2138,100 @@ __global__ void __launch_bounds__(256, 3) k_mc_scatter(Problem P, McState *ms, I
 }
 
 // b_I recalculated (Eq. recalculate-b), the chosen coordinates join the
-// candidates, counters and the host snapshot.
-__global__ void k_mc_finalize(Problem P, McState *ms, IterState *st, const McSel *sel, const double *Hdiag,
-                              const double *gathp, long long *cand, const double *etaout, int per_col,
-                              unsigned int *work) {
-    __shared__ double s_gsum[kEigMaxN];
-    if (threadIdx.x == 0) *work = 0u;                   // the next scatter's item counter
-    if (ms->done || st->status) return;
+// candidates, counters and the host snapshot.  One warp per chosen column (8
+// per block): its gather from the item partials (lane-strided in item order,
+// then a fixed tree), b_i = H_ii c_i + gather, the candidate mark; the block's
+// new candidates in one reservation.  The last block to finish (a counter in
+// McState, reset by that block) writes the counters and the snapshot.
+constexpr int kFinWarps = 8;
+__global__ void __launch_bounds__(32 * kFinWarps) k_mc_finalize(Problem P, McState *ms, IterState *st,
+                                                                const McSel *sel, const double *Hdiag,
+                                                                const double *gathp, long long *cand,
+                                                                const double *etaout, int per_col, unsigned int *work) {
+    __shared__ long long s_slot[kFinWarps];
+    __shared__ int s_app[kFinWarps], s_nd[kFinWarps];
+    __shared__ bool s_last;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *work = 0u;   // the next scatter's item counter
+    if (ms->done) return;                               // read-only here: uniform over the blocks
+    const bool skip = st->status != 0;
     const int m = ms->m_sel;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    // each column's gather: its item partials, lane-strided in item order, then a fixed tree
-    for (int i = warp; i < m; i += nwarp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kFinWarps + warp;
+    if (lane == 0) { s_app[warp] = 0; s_nd[warp] = 0; }
+    if (!skip && i < m) {                               // warp-uniform
         double t = 0.0;
         for (int k = lane; k < per_col; k += 32) t += gathp[(size_t)i * per_col + k];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) s_gsum[i] = t;
-    }
-    __syncthreads();
-    int nd = 0;                                         // this thread's nonzero diagonals
-    for (int i0 = 0; i0 < m; i0 += blockDim.x) {        // block-uniform rounds
-        const int i = i0 + (int)threadIdx.x;
-        bool append = false;
-        long long slot = 0;
-        if (i < m) {
-            slot = sel[i].slot;
+        if (lane == 0) {
+            const long long slot = sel[i].slot;
             const double hd = Hdiag[i];
-            nd += hd != 0.0 ? 1 : 0;
-            Slot *s = P.table + slot;
-            s->bv = fma(hd, s->c, s_gsum[i]);
-            append = mark_set(P, slot);
-        }
-        // the chosen coordinates join the candidates: one reservation per warp
-        const unsigned int am = __ballot_sync(0xffffffffu, append);
-        if (am) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&ms->n_cand, __popc(am));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const long long at = (long long)base + __popc(am & ((1u << lane) - 1u));
-            if (append) {
-                if (at < P.cap_cand) cand[at] = slot;
-                else set_status(st, kErrInternal);
-            }
+            Slot *sp = P.table + slot;
+            sp->bv = fma(hd, sp->c, t);
+            s_nd[warp] = is_zero(hd) ? 0 : 1;
+            s_slot[warp] = slot;
+            s_app[warp] = mark_set(P, slot) ? 1 : 0;
         }
     }
-    __shared__ int s_nd;
-    if (threadIdx.x == 0) s_nd = 0;
-    __syncthreads();
-    if (nd) atomicAdd(&s_nd, nd);
     __syncthreads();
     if (threadIdx.x == 0) {
-        // every field read first (independent loads), then written
-        const long long nd_all = s_nd;
-        const unsigned long long c0 = ms->cnt[0], c1 = ms->cnt[1], c2 = ms->cnt[2], c3 = ms->cnt[3];
-        const long long el = ms->elements + (long long)c0 + nd_all, ap = ms->applied + (long long)c1 + nd_all;
-        const long long dr = ms->dropped + (long long)c2, in = ms->inserted + (long long)c3;
-        const long long ns = ms->n_slots + (long long)c3;
-        const long long its = ms->iterations, nnz = ms->nnz_c, eit = ms->eig_iters_total;
-        const dd mu = ms->mu, al = ms->alpha;
-        const double dx = ms->dx, en = ms->energy;
-        const int done = ms->done_pending ? 1 : ms->done;
-        const double eta0 = m > 0 ? etaout[0] : 0.0;
-        const unsigned long long la = m > 0 ? sel[0].A : 0ull, lb = m > 0 ? sel[0].B : 0ull;
-        ms->elements = el;
-        ms->applied = ap;
-        ms->dropped = dr;
-        ms->inserted = in;
-        ms->n_slots = ns;
-        ms->last_column = (long long)c0 + nd_all;
-        for (int k = 0; k < 4; ++k) ms->cnt[k] = 0;
-        ms->done = done;
-        if (ns > P.max_entries) set_status(st, kErrTableFull);
-        st->iterations = its;
-        st->nnz_c = nnz;
-        st->n_slots = ns;
-        st->elements = el;
-        st->applied = ap;
-        st->dropped = dr;
-        st->inserted = in;
-        st->last_column = (long long)c0 + nd_all;
-        st->eig_iters = eit;
-        st->mu = mu;
-        st->alpha = al;
-        st->dx = dx;
-        st->energy = en;
-        st->last_eta = eta0;
-        st->last_a = la;
-        st->last_b = lb;
-        st->done = done;
+        // the block's new candidates (warp order) in one reservation, its nonzero diagonals
+        int na = 0, nd = 0;
+        for (int w = 0; w < kFinWarps; ++w) { na += s_app[w]; nd += s_nd[w]; }
+        if (na) {
+            const int base = atomicAdd(&ms->n_cand, na);
+            for (int w = 0, at = base; w < kFinWarps; ++w)
+                if (s_app[w]) {
+                    if (at < P.cap_cand) cand[at] = s_slot[w];
+                    else set_status(st, kErrInternal);
+                    ++at;
+                }
+        }
+        if (nd) atomicAdd(&ms->fin_nd, nd);
+        __threadfence();
+        s_last = atomicAdd(&ms->fin_blocks, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    // every field read first (independent loads), then written
+    const long long nd_all = (long long)atomicExch(&ms->fin_nd, 0);
+    ms->fin_blocks = 0u;
+    const unsigned long long c0 = ms->cnt[0], c1 = ms->cnt[1], c2 = ms->cnt[2], c3 = ms->cnt[3];
+    const long long el = ms->elements + (long long)c0 + nd_all, ap = ms->applied + (long long)c1 + nd_all;
+    const long long dr = ms->dropped + (long long)c2, in = ms->inserted + (long long)c3;
+    const long long ns = ms->n_slots + (long long)c3;
+    const long long its = ms->iterations, nnz = ms->nnz_c, eit = ms->eig_iters_total;
+    const dd mu = ms->mu, al = ms->alpha;
+    const double dx = ms->dx, en = ms->energy;
+    const int done = ms->done_pending ? 1 : ms->done;
+    const double eta0 = m > 0 ? etaout[0] : 0.0;
+    const unsigned long long la = m > 0 ? sel[0].A : 0ull, lb = m > 0 ? sel[0].B : 0ull;
+    ms->elements = el;
+    ms->applied = ap;
+    ms->dropped = dr;
+    ms->inserted = in;
+    ms->n_slots = ns;
+    ms->last_column = (long long)c0 + nd_all;
+    for (int k = 0; k < 4; ++k) ms->cnt[k] = 0;
+    ms->done = done;
+    if (ns > P.max_entries) set_status(st, kErrTableFull);
+    st->iterations = its;
+    st->nnz_c = nnz;
+    st->n_slots = ns;
+    st->elements = el;
+    st->applied = ap;
+    st->dropped = dr;
+    st->inserted = in;
+    st->last_column = (long long)c0 + nd_all;
+    st->eig_iters = eit;
+    st->mu = mu;
+    st->alpha = al;
+    st->dx = dx;
+    st->energy = en;
+    st->last_eta = eta0;
+    st->last_a = la;
+    st->last_b = lb;
+    st->done = done;
 }
 
 // One entry of a start vector: c_{A,B} = eta from c = 0, as a forced block step
@@ -2390,7 +2401,8 @@ cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long 
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s) {
     k_mc_scatter<<<b.scatter_grid, 256, 0, s>>>(P, b.ms, b.st, b.sel, b.coltab, b.collists, b.geom, b.w, b.thr,
                                                  b.cand, b.gathp, b.work, McUpdate{});
-    k_mc_finalize<<<1, 1024, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.geom.per_col, b.work);
+    k_mc_finalize<<<(b.m + kFinWarps - 1) / kFinWarps, 32 * kFinWarps, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp,
+                                                                              b.cand, b.eta, b.geom.per_col, b.work);
     return cudaGetLastError();
 }
 
@@ -2448,7 +2460,8 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
                                                      b.cand, b.gathp, b.work,
                                                      McUpdate{b.cI, b.bI, b.eta, b.Rh, b.Rl, b.ldr, 1});
     mark();
-    k_mc_finalize<<<1, 1024, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp, b.cand, b.eta, b.geom.per_col, b.work);
+    k_mc_finalize<<<(b.m + kFinWarps - 1) / kFinWarps, 32 * kFinWarps, 0, s>>>(P, b.ms, b.st, b.sel, b.Hdiag, b.gathp,
+                                                                              b.cand, b.eta, b.geom.per_col, b.work);
     mark();
     return cudaGetLastError();
 }

@@ -155,6 +155,9 @@ struct McState {
     dd pend_scale;                 // s gamma
     double pend_gamma;
     int pend_it, pend_deg;
+    // the finalisation's last-block counter and nonzero diagonals (zero between iterations)
+    unsigned int fin_blocks;
+    int fin_nd;
 };
 
 // xCDFCI (Algorithm 3, k1 = K + 1 states) iteration state, one per handle.
