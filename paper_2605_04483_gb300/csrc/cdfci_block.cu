@@ -673,39 +673,54 @@ __global__ void __launch_bounds__(1024) k_mc_ties(Problem P, McState *ms, const 
 // Bitonic sort, in shared memory, of (choice key, index) pairs into the choice
 // order: |g| descending, then the determinant key ascending (looked up in src
 // for exact ties only).  Padding entries (index -1) sort last.
-struct SelKey {
-    unsigned long long g;
-    int i, pad;
+// One element of a sort, held in registers: the choice key and the determinant
+// (a strict total order: keys are unique); padding sorts last.
+struct SelE {
+    unsigned long long g, A, B;
+    long long slot;
 };
-__device__ __forceinline__ bool sk_before(const SelKey &x, const SelKey &y, const McSel *src) {
-    if (y.i < 0) return x.i >= 0;
-    if (x.i < 0) return false;
+__device__ __forceinline__ bool sel_first(const SelE &x, const SelE &y) {   // x before y in the choice order
     if (x.g != y.g) return x.g > y.g;
-    return key_less(src[x.i].A, src[x.i].B, src[y.i].A, src[y.i].B);
+    return key_less(x.A, x.B, y.A, y.B);
 }
-__device__ void bitonic_sk(SelKey *a, int n_pow2, const McSel *src) {
+__device__ __forceinline__ SelE sel_pad() { return SelE{0ull, ~0ull, ~0ull, -1}; }
+// Bitonic sort into the choice order of n_pow2 elements, one per thread (thread
+// t holds element t; n_pow2 a power of two).  Only the first max(n_pow2, 32)
+// threads take part (the caller's other threads skip it): a stage whose
+// partners lie in one warp (distance < 32) exchanges by shuffles, the others
+// through buf between two barriers of the taking-part warps (named barrier 1).
+__device__ void bitonic_reg(SelE &e, int n_pow2, SelE *buf) {
+    const int t = threadIdx.x;
+    const int nact = n_pow2 < 32 ? 32 : n_pow2;
     for (int k = 2; k <= n_pow2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n_pow2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const SelKey x = a[i], y = a[l];
-                    const bool y_first = sk_before(y, x, src);
-                    if (((i & k) == 0) ? y_first : !y_first) { a[i] = y; a[l] = x; }
-                }
+            SelE o;
+            if (j >= 32) {                              // uniform
+                buf[t] = e;
+                asm volatile("bar.sync 1, %0;" ::"r"(nact) : "memory");
+                o = buf[t ^ j];
+                asm volatile("bar.sync 1, %0;" ::"r"(nact) : "memory");
+            } else {
+                o.g = __shfl_xor_sync(0xffffffffu, e.g, j);
+                o.A = __shfl_xor_sync(0xffffffffu, e.A, j);
+                o.B = __shfl_xor_sync(0xffffffffu, e.B, j);
+                o.slot = __shfl_xor_sync(0xffffffffu, e.slot, j);
             }
-            __syncthreads();
+            // the lower position of an ascending pair (and the upper of a descending one) keeps the
+            // first of the two
+            const bool keep_first = ((t & j) == 0) == ((t & k) == 0);
+            const bool o_first = sel_first(o, e), e_first = sel_first(e, o);
+            if (keep_first ? o_first : e_first) e = o;
         }
     }
 }
 
 // The in-bin candidates sorted, the first sel_need of them join the chosen
 // set; then the chosen set in the choice order (a canonical order for the
-// reduced problem's rows).
+// reduced problem's rows).  1024 threads, one element each.
 __global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, const McSel *inbin, int m,
                                                       IterState *st) {
-    __shared__ SelKey sk[kInBin];
-    __shared__ McSel tmp[kInBin];
+    __shared__ SelE buf[kInBin];
     const int tid = threadIdx.x;
     if (ms->done) return;
     const int n_above = ms->n_above;
@@ -715,29 +730,25 @@ __global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, co
         n_in = kInBin;
     }
     const int need = ms->sel_level == 0 ? 0 : ms->sel_need;
-    int p2 = 1;
-    while (p2 < n_in) p2 <<= 1;
-    // the in-bin candidates in shared memory first: the sort's tie-breaks (equal |g|, the common
-    // case on lattices) read their keys there
-    for (int i = tid; i < p2; i += blockDim.x) {
-        if (i < n_in) tmp[i] = inbin[i];
-        sk[i] = SelKey{i < n_in ? inbin[i].gkey : 0ull, i < n_in ? i : -1, 0};
-    }
-    __syncthreads();
-    if (n_in > 1) bitonic_sk(sk, p2, tmp);
     const int take = need < n_in ? need : n_in;
-    for (int i = tid; i < take; i += blockDim.x) sel[n_above + i] = tmp[sk[i].i];
-    __syncthreads();
-    const int msel = n_above + take;
-    int q2 = 1;
-    while (q2 < msel) q2 <<= 1;
-    for (int i = tid; i < q2; i += blockDim.x) {
-        if (i < msel) tmp[i] = sel[i];
-        sk[i] = SelKey{i < msel ? sel[i].gkey : 0ull, i < msel ? i : -1, 0};
+    if (take > 0) {                                     // uniform
+        int p2 = 1;
+        while (p2 < n_in) p2 <<= 1;
+        SelE e = sel_pad();
+        if (tid < n_in) { const McSel x = inbin[tid]; e = SelE{x.gkey, x.A, x.B, x.slot}; }
+        if (n_in > 1 && tid < (p2 < 32 ? 32 : p2)) bitonic_reg(e, p2, buf);
+        if (tid < take) sel[n_above + tid] = McSel{e.slot, e.g, e.A, e.B};
+        __syncthreads();                                // sel visible to the block
     }
-    __syncthreads();
-    if (msel > 1) bitonic_sk(sk, q2, tmp);
-    for (int i = tid; i < msel; i += blockDim.x) sel[i] = tmp[sk[i].i];
+    const int msel = n_above + take;
+    if (msel > 1) {
+        int q2 = 1;
+        while (q2 < msel) q2 <<= 1;
+        SelE e = sel_pad();
+        if (tid < msel) { const McSel x = sel[tid]; e = SelE{x.gkey, x.A, x.B, x.slot}; }
+        if (tid < (q2 < 32 ? 32 : q2)) bitonic_reg(e, q2, buf);
+        if (tid < msel) sel[tid] = McSel{e.slot, e.g, e.A, e.B};
+    }
     if (tid == 0) {
         ms->m_sel = msel;
         ms->n_above = 0;
