@@ -820,13 +820,23 @@ __global__ void __launch_bounds__(32 * kPrepWarps) k_mc_prepare(Problem P, McSta
         mc_build_coltab(P, L, rA, rB, coltab + (size_t)r * ns, lane, 32);
         reinterpret_cast<uint2 *>(collists + r)[lane] = reinterpret_cast<const uint2 *>(&L)[lane];
         const double hd = diag_warp(P, L);
+        // (pairs more than a double excitation apart, or doubles when every double vanishes, are zero:
+        // no FP64 work for them; a zero term leaves acc unchanged)
+        const int dmax = P.doubles_vanish ? 2 : 4;
         double acc = 0.0;
         for (int c = lane; c < m; c += 32) {
-            const double h = (c == r) ? hd : hij_pair(P, rA, rB, s_A[c], s_B[c]);
-            const ff hf = ff_from_double(h);
-            Rh[(size_t)(r + 1) * ldr + (c + 1)] = hf.hi;
-            Rl[(size_t)(r + 1) * ldr + (c + 1)] = hf.lo;
-            acc = fma(h, s_c[c], acc);
+            const unsigned long long cA = s_A[c], cB = s_B[c];
+            const int dd2 = __popcll(rA ^ cA) + __popcll(rB ^ cB);
+            float hh = 0.0f, hl = 0.0f;
+            if (c == r || (dd2 > 0 && dd2 <= dmax)) {
+                const double h = (c == r) ? hd : hij_pair(P, rA, rB, cA, cB);
+                const ff hf = ff_from_double(h);
+                hh = hf.hi;
+                hl = hf.lo;
+                acc = fma(h, s_c[c], acc);
+            }
+            Rh[(size_t)(r + 1) * ldr + (c + 1)] = hh;
+            Rl[(size_t)(r + 1) * ldr + (c + 1)] = hl;
         }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
         // the row's values, and for the reduced solve c_r, b_r, (H_II c_I)_r, b_r - (H_II c_I)_r as
