@@ -1165,16 +1165,18 @@ __device__ void eig_stream(const float *Rh, const float *Rl, int ldr, int n1, in
 }
 
 // CL = false: one CTA holds the whole problem (R in its shared memory when
-// use_smem, else streamed from global memory); CL = true: a cluster of C CTAs,
+// SM, else streamed from global memory); CL = true (with SM): a cluster of C CTAs,
 // CTA r holding rows [r crows, (r + 1) crows) of R in its shared memory, the
 // vectors x and w gathered in full in every CTA before each product, the sums
 // taken over the cluster.  Every CTA computes the scalar steps itself, from
 // the same sums in the same order, so they agree bit for bit.
-template <bool CL>
+// (SM is a template parameter so that each instantiation holds only the code it runs: the kernel runs
+// once per iteration on whichever SM is free, its instructions fetched from L2 each time.)
+template <bool CL, bool SM>
 __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, IterState *st, const McSel *sel,
                                                        const double *cI, const double *bI, const double *HIIc,
                                                        const double *Hdiag, const float4 *rowf, float *Rh, float *Rl,
-                                                       int ldr, int tpr, int use_smem, int crows, double *w,
+                                                       int ldr, int tpr, int crows, double *w,
                                                        double *thr, double *etaout) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float s_rf[2 * 32 * 16];
@@ -1195,7 +1197,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
     const int m = ms->m_sel, n1 = m + 1;
     // this CTA's rows of R (absolute indices [a0, a1)); one CTA: all
     const int a0 = CL ? (int)rank * crows : 0, a1 = CL ? min(a0 + crows, n1) : n1;
-    const bool in_smem = CL || use_smem;
+    constexpr bool in_smem = CL || SM;
     // the state scalars, loaded (thread 0) ahead of the sums; read after the barriers below
     __shared__ dd s_mu0, s_al0, s_sc0;
     __shared__ long long s_nnz0;
@@ -1398,7 +1400,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
                 }
             }
             if (CL) cg::this_cluster().sync(); else __syncthreads();
-            if (in_smem) {
+            if constexpr (in_smem) {
                 ax = ff_row(sh, sl, ldr, nq, lr, kk, tpr, act, xs);
             } else {
                 eig_stream<true>(Rh, Rl, ldr, n1, nq, stg, srows, s_sbar, spar, xs, ys, st);
@@ -1458,7 +1460,7 @@ __global__ void __launch_bounds__(kEigMaxN) k_mc_eigen(Problem P, McState *ms, I
         }
         if (CL) cg::this_cluster().sync(); else __syncthreads();
         float awv;
-        if (in_smem) {
+        if constexpr (in_smem) {
             awv = f_row(sh, ldr, nq, lr, kk, tpr, act, ws);
         } else {
             eig_stream<false>(Rh, Rl, ldr, n1, nq, stg, srows, s_sbar, spar, ws, ys, st);
@@ -2374,14 +2376,18 @@ McGeom mc_geometry(const Problem &P) {
 }
 
 cudaError_t mc_configure() {
-    size_t most = 0, most_cl = 0;
+    size_t most1 = 0, most0 = 0, most_cl = 0;
     for (int m = 1; m < kEigMaxN; ++m) {
-        if (eig_cfg(m + 1).C > 1) most_cl = std::max(most_cl, mc_eigen_smem(m));
-        else most = std::max(most, mc_eigen_smem(m));
+        const int C = eig_cfg(m + 1).C;
+        size_t &t = C > 1 ? most_cl : (C == 1 ? most1 : most0);
+        t = std::max(t, mc_eigen_smem(m));
     }
-    cudaError_t e = cudaFuncSetAttribute(k_mc_eigen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    cudaError_t e = cudaFuncSetAttribute(k_mc_eigen<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)most1);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_mc_eigen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most_cl);
+    e = cudaFuncSetAttribute(k_mc_eigen<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most0);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_mc_eigen<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most_cl);
     if (e != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -2466,13 +2472,18 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            cudaLaunchKernelEx(&cfg, k_mc_eigen<true>, P, b.ms, b.st, (const McSel *)b.sel, (const double *)b.cI,
-                               (const double *)b.bI, (const double *)b.HIIc, (const double *)b.Hdiag,
-                               (const float4 *)b.rowf, b.Rh, b.Rl, b.ldr, g.tpr, 1, g.crows, b.w, b.thr, b.eta);
-        } else {
-            k_mc_eigen<false><<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(
-                P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Hdiag, b.rowf, b.Rh, b.Rl, b.ldr, g.tpr, g.C == 1 ? 1 : 0,
-                b.m + 1, b.w, b.thr, b.eta);
+            cudaLaunchKernelEx(&cfg, k_mc_eigen<true, true>, P, b.ms, b.st, (const McSel *)b.sel,
+                               (const double *)b.cI, (const double *)b.bI, (const double *)b.HIIc,
+                               (const double *)b.Hdiag, (const float4 *)b.rowf, b.Rh, b.Rl, b.ldr, g.tpr, g.crows,
+                               b.w, b.thr, b.eta);
+        } else if (g.C == 1) {                          // one CTA, R in its shared memory
+            k_mc_eigen<false, true><<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(
+                P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Hdiag, b.rowf, b.Rh, b.Rl, b.ldr, g.tpr, b.m + 1, b.w,
+                b.thr, b.eta);
+        } else {                                        // one CTA streaming R from L2
+            k_mc_eigen<false, false><<<1, mc_eigen_threads(b.m), mc_eigen_smem(b.m), s>>>(
+                P, b.ms, b.st, b.sel, b.cI, b.bI, b.HIIc, b.Hdiag, b.rowf, b.Rh, b.Rl, b.ldr, g.tpr, b.m + 1, b.w,
+                b.thr, b.eta);
         }
     }
     mark();
