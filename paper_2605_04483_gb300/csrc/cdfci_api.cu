@@ -83,7 +83,7 @@ struct cdfci_ctx {
     IterState *d_st = nullptr;
     CdRecord *d_rec = nullptr;                   // state between launches of the cluster loop
     CdPartial *d_part = nullptr;                 // one partial per CTA of the cluster (two sets in grid mode)
-    GridBar *d_bar = nullptr;                    // grid mode: the software grid barrier
+    GridRound *d_bar = nullptr;                  // grid mode: rounds of the partial exchange so far
     bool gridmode = false;                       // m = 1 over more CTAs than a cluster holds
     int *d_flags = nullptr;                      // [0] status, [1] has_doubles
     unsigned long long *d_counter = nullptr;     // scratch counter for compaction kernels
@@ -151,7 +151,8 @@ int run_iterations(cdfci_ctx *c, long long n) {
         if (rc) return rc;
         long long k = std::min(n, chunk);
         if (c->gridmode)
-            CK(launch_cd_loop_grid(c->P, c->d_st, c->d_rec, c->d_part, c->d_part + c->grid, c->d_bar, c->grid, k,
+            CK(launch_cd_loop_grid(c->P, c->d_st, c->d_rec, c->d_part,
+                                   reinterpret_cast<unsigned long long *>(c->d_part + c->grid), c->d_bar, c->grid, k,
                                    c->stream));
         else
             CK(launch_cd_loop(c->P, c->d_st, c->d_rec, c->d_part, c->grid, k, c->stream));
@@ -636,12 +637,14 @@ int create_impl(const double *h, const double *g, int N, int n_alpha, int n_beta
             c->grid = cd_pick_cluster((int)std::max<long long>(1, std::min<long long>(want, 16)), cd_dynamic_smem(P));
         }
     }
-    const size_t nparts = (size_t)c->grid * (c->gridmode ? 2 : 1);
+    // grid mode: after the G partials, the two exchange buffers of G x kXchgWords words (4 G CdPartials' worth)
+    static_assert(2 * kXchgWords * sizeof(unsigned long long) == 4 * sizeof(CdPartial), "exchange buffer size");
+    const size_t nparts = (size_t)c->grid * (c->gridmode ? 5 : 1);
     if (prm.graph_chunk > 0) c->chunk = prm.graph_chunk;
     if (cudaMemsetAsync(c->d_table, 0, (size_t)P.capacity * sizeof(Slot), s) != cudaSuccess ||
         cudaMalloc(&c->d_st, sizeof(IterState)) != cudaSuccess ||
         cudaMalloc(&c->d_part, nparts * sizeof(CdPartial)) != cudaSuccess ||
-        cudaMalloc(&c->d_bar, sizeof(GridBar)) != cudaSuccess ||
+        cudaMalloc(&c->d_bar, sizeof(GridRound)) != cudaSuccess ||
         cudaMalloc(&c->d_rec, sizeof(CdRecord)) != cudaSuccess ||
         cudaMalloc(&c->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_colkeys, (size_t)P.nh * 2 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -651,7 +654,7 @@ int create_impl(const double *h, const double *g, int N, int n_alpha, int n_beta
     if (cudaMemsetAsync(c->d_st, 0, sizeof(IterState), s) != cudaSuccess ||
         cudaMemsetAsync(c->d_rec, 0, sizeof(CdRecord), s) != cudaSuccess ||
         cudaMemsetAsync(c->d_part, 0, nparts * sizeof(CdPartial), s) != cudaSuccess ||
-        cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), s) != cudaSuccess)
+        cudaMemsetAsync(c->d_bar, 0, sizeof(GridRound), s) != cudaSuccess)
         return bail(fail(CDFCI_ERR_CUDA, "memset failed"));
 
     // start determinant: given, or aufbau on h_pp (smallest first, ties to the lower index)

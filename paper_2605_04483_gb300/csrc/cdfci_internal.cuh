@@ -342,14 +342,20 @@ __device__ __forceinline__ long long table_find(const Problem &P, IterState *st,
     return -2;
 }
 
-// Software grid barrier of the grid-wide m = 1 loop (all CTAs co-resident:
-// cooperative launch).  count: arrivals of the current round; gen: rounds
-// completed.  Zero-initialised.
-// Arrivals at the software grid barrier so far (never reset: the n-th crossing
-// of a G-CTA grid completes when the count reaches n G).
-struct GridBar {
-    unsigned long long arrived;
+// The grid-wide m = 1 loop (all CTAs co-resident: cooperative launch) hands
+// every round's CTA partials over through an exchange buffer whose words carry
+// the number of the round that wrote them, so a reader polls the data itself
+// instead of a barrier counter.  `round` counts the rounds published by earlier
+// launches (zero-initialised, never reset).
+struct GridRound {
+    unsigned long long round;
 };
+// 64-bit words per CTA partial in the exchange buffer: word k holds 32-bit
+// half k of the CdPartial in its low half and the round (mod 2^32) in its high
+// half, so every word validates itself (a 64-bit access is single-copy atomic;
+// a vector access is not as a whole).  Two buffers of G partials alternate.
+constexpr int kXchgWords = 20;
+static_assert(sizeof(CdPartial) == 4 * kXchgWords, "CdPartial is exchanged as 32-bit halves");
 
 // One problem of a batch of independent m = 1 solvers stepped in one launch.
 struct CdInstance {

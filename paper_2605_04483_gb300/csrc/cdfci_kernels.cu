@@ -326,11 +326,19 @@ struct LoopState {
 // Warp-level combine: argmax of (gbits desc, key asc) with payload (slot, b, c),
 // sums of the counters and a lane-ordered sum of the nonzero gather values;
 // every lane returns the result.  The maximum of gbits comes from a
-// butterfly on gbits alone; only exact ties look at the keys.
+// butterfly on gbits alone; only exact ties look at the keys.  The gather's
+// fixed shuffle-down tree (skipped when every lane holds 0) runs level by level
+// beside the butterfly, so their latencies overlap.
 __device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb, double &gather, int cnt[4], int &err) {
+    const bool any_g = __any_sync(0xffffffffu, !is_zero(gather));
+    for (int k = 0; k < 4; ++k) cnt[k] = __reduce_add_sync(0xffffffffu, (unsigned)cnt[k]);
+    err = (int)__reduce_or_sync(0xffffffffu, (unsigned)err);
     unsigned long long gmax = best.g;
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, gmax, off);
+        const double t = __shfl_down_sync(0xffffffffu, gather, off);
+        if (any_g) gather += t;
         gmax = y > gmax ? y : gmax;
     }
     const unsigned int cand = __ballot_sync(0xffffffffu, best.g == gmax && best.slot >= 0);
@@ -357,42 +365,85 @@ __device__ __forceinline__ void warp_combine(Best &best, double &bb, double &cb,
         bb = 0.0;
         cb = 0.0;
     }
-    for (int k = 0; k < 4; ++k) cnt[k] = __reduce_add_sync(0xffffffffu, (unsigned)cnt[k]);
-    err = (int)__reduce_or_sync(0xffffffffu, (unsigned)err);
-    // gather: a fixed shuffle-down tree (skipped when every lane holds 0)
-    if (__any_sync(0xffffffffu, !is_zero(gather))) {
-        for (int off = 16; off > 0; off >>= 1) gather += __shfl_down_sync(0xffffffffu, gather, off);
-        gather = __shfl_sync(0xffffffffu, gather, 0);
-    }
+    if (any_g) gather = __shfl_sync(0xffffffffu, gather, 0);
 }
 
-// Grid-wide barrier for the co-resident CTAs of a cooperative launch: one
-// atomic arrival on a counter that is never reset (the crossing completes
-// when it reaches the next multiple of the CTA count), a fence before it (this
-// CTA's table writes and partial become visible) and acquire loads while
-// waiting.  The wait is bounded: on expiry the status becomes
-// CDFCI_ERR_TIMEOUT and false is returned (all CTAs then leave).
-__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+// Partial exchange of the grid-wide loop (all CTAs co-resident: cooperative
+// launch).  At the end of round q every CTA publishes its partial into buffer
+// q & 1 as kXchgWords words, each (q mod 2^32) << 32 | one 32-bit half of the
+// partial; at the start of round q + 1 the control warps poll those words
+// until every one carries q.  The publishing lanes fence after the CTA barrier
+// that follows the element warps' table writes (release: those writes, the
+// slot of the processed coordinate and the partial become visible together),
+// and the readers fence after the poll (acquire), so a one-way pass of the data
+// replaces a barrier counter's round trip plus the read of the partials.  A CTA
+// publishes round q + 2 into the same buffer only after it has read every
+// partial of round q + 1, hence after every CTA has read round q: two buffers
+// suffice.  The waits are bounded: on expiry the status becomes
+// CDFCI_ERR_TIMEOUT and the loop ends.
+constexpr int kXchgSpins = 1 << 21;
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
-__device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, IterState *st) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned long long old = atomicAdd(&bar->arrived, 1ull);
-        const unsigned long long target = (old / nblocks + 1ull) * nblocks;
-        int ok = 1;
-        long long spins = 0;
-        while (ld_acquire_gpu(&bar->arrived) < target) {
-            if (++spins > (1ll << 22)) { set_status(st, kErrTimeout); ok = 0; break; }
-        }
-        s_ok = ok;
+__device__ __forceinline__ void xchg_publish(unsigned long long *dst, const CdPartial &p, unsigned int q, int lane) {
+    if (lane < kXchgWords / 2) {
+        const unsigned int *h = reinterpret_cast<const unsigned int *>(&p);
+        const unsigned long long w0 = ((unsigned long long)q << 32) | h[2 * lane];
+        const unsigned long long w1 = ((unsigned long long)q << 32) | h[2 * lane + 1];
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(dst + 2 * lane), "l"(w0), "l"(w1)
+                     : "memory");
     }
-    __syncthreads();
-    return s_ok != 0;
+}
+__device__ __forceinline__ void xchg_load(const unsigned long long *src, unsigned long long (&w)[kXchgWords]) {
+#pragma unroll
+    for (int k = 0; k < kXchgWords; k += 2)
+        asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w[k]), "=l"(w[k + 1]) : "l"(src + k)
+                     : "memory");
+}
+// true when every word carries round q (the padding word 19 is not checked)
+__device__ __forceinline__ bool xchg_check(const unsigned long long (&w)[kXchgWords], unsigned int q) {
+    unsigned int bad = 0u;
+#pragma unroll
+    for (int k = 0; k < kXchgWords - 1; ++k) bad |= (unsigned int)(w[k] >> 32) ^ q;
+    return bad == 0u;
+}
+__device__ __forceinline__ unsigned long long xchg_u64(const unsigned long long (&w)[kXchgWords], int k) {
+    return (w[k] & 0xffffffffull) | (w[k + 1] << 32);
+}
+// the partial from its words (the field order of CdPartial, low half first)
+__device__ __forceinline__ CdPartial xchg_unpack(const unsigned long long (&w)[kXchgWords]) {
+    CdPartial x;
+    x.gather = __longlong_as_double((long long)xchg_u64(w, 0));
+    x.gbits = xchg_u64(w, 2);
+    x.ka = xchg_u64(w, 4);
+    x.kb = xchg_u64(w, 6);
+    x.slot = (long long)xchg_u64(w, 8);
+    x.bj = __longlong_as_double((long long)xchg_u64(w, 10));
+    x.cj = __longlong_as_double((long long)xchg_u64(w, 12));
+    x.elements = (int)(unsigned int)w[14];
+    x.applied = (int)(unsigned int)w[15];
+    x.dropped = (int)(unsigned int)w[16];
+    x.inserted = (int)(unsigned int)w[17];
+    x.err = (int)(unsigned int)w[18];
+    return x;
+}
+// Warp-wide: polls the partial r (if r < G) of round q in buf into x, then
+// fences (acquire); false when the wait expired (uniform over the warp).
+__device__ __forceinline__ bool xchg_poll1(const unsigned long long *buf, int G, int r, unsigned int q, CdPartial &x) {
+    bool ok = r >= G;
+    unsigned long long w[kXchgWords];
+    for (int spins = 0;; ++spins) {
+        if (!ok) {
+            xchg_load(buf + (size_t)r * kXchgWords, w);
+            ok = xchg_check(w, q);
+        }
+        if (__all_sync(0xffffffffu, ok)) break;
+        if (spins >= kXchgSpins) return false;
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    if (r < G) x = xchg_unpack(w);
+    return true;
 }
 
 // A partial written by another SM in this round: read through L2 (an L1 line of
@@ -439,18 +490,22 @@ __device__ __forceinline__ void fold_partial(const CdPartial &x, bool first, Bes
 // cluster barrier.
 //
 // kGrid: the same loop over every CTA of a cooperative launch (more CTAs than
-// a cluster holds).  The partials then go through global memory (gbuf[0],
-// gbuf[1] = gpart, alternating) and a software grid barrier replaces the
-// cluster barrier.
+// a cluster holds).  The partials of a round then go through the round-numbered
+// exchange buffer xchg (see xchg_publish), which replaces the cluster barrier;
+// gpart holds the partials between launches (read in a launch's first round,
+// written once every CTA has published its last one).
 template <bool kGrid, int kE>
 __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart,
-                                             CdPartial *galt, GridBar *bar, long long n_iter) {
+                                             unsigned long long *xchg, GridRound *rnd, long long n_iter) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int G = kGrid ? (int)gridDim.x : (int)cluster.num_blocks();
     const int rank = kGrid ? (int)blockIdx.x : (int)cluster.block_rank();
-    CdPartial *gbuf[2] = {galt, gpart};
-    __shared__ CdPartial spart[2];
+    // grid mode: rounds published by earlier launches (mod 2^32); round q0 + it + 1 is published in
+    // iteration it
+    const unsigned int q0 = kGrid ? (unsigned int)__ldcg(&rnd->round) : 0u;
+    unsigned int n_pub = 0;                      // rounds this launch published (grid mode)
+    __shared__ CdPartial spart[2];               // cluster: this CTA's partials (alternating); grid: [0] the last published
     __shared__ ColLists Lw[kCdWarps];
     __shared__ Best r_best[kCdWarps];
     __shared__ double r_bc[kCdWarps][3];
@@ -461,6 +516,8 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     __shared__ double s_hii;
     __shared__ int s_err;
     __shared__ int s_fins;                       // 1: this CTA inserted the forced coordinate of this step
+    __shared__ int s_tmo;                        // grid mode: a wait for the partials expired
+    __shared__ CdPartial s_x1[kGrid ? 2 : 1][32];   // grid mode: the partials polled by warps 0 and 1
     extern __shared__ __align__(16) unsigned char s_dyn[];
     const CdSmem lay = cd_smem_layout(P);
     SingleEnt *tabA = reinterpret_cast<SingleEnt *>(s_dyn), *tabB = tabA + P.na * P.va;
@@ -491,6 +548,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
         s_err = 0;
         s_done = 0;
         s_fins = 0;
+        s_tmo = 0;
     }
     if (kGrid) __syncthreads(); else cluster.sync();
 
@@ -516,25 +574,58 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
     for (long long it = 0; it < n_iter; ++it) {
         const int pin = lastp, pout = lastp ^ 1;
         // ---- choice of i (Eq. choose-i), by the control warp ----
+        // every CTA's partial of the last column: lane l of the control warp folds CTAs l, l + 32, ...
+        // (all lanes take part in the combine)
+        {
+        Best bb{0ull, ~0ull, ~0ull, -1};
+        double bj = 0.0, cj = 0.0, gsum = 0.0;
+        int cnt[4] = {0, 0, 0, 0};
+        int err = 0;
+        bool tmo = false;
+        if (kGrid && it > 0 && warp < 2 && ls.have_prev) {
+            // grid mode: warp 0 polls partial r0 + lane, warp 1 partial r0 + 32 + lane (both staged in
+            // s_x1); warp 0 folds them in that order
+            const unsigned int q = q0 + (unsigned int)it;
+            for (int r0 = 0; r0 < G; r0 += 64) {
+                const int r = r0 + 32 * warp + lane;
+                CdPartial x;
+                const bool got = xchg_poll1(xchg + (size_t)(q & 1u) * G * kXchgWords, G, r, q, x);
+                if (!got && lane == 0) s_tmo = 1;
+                if (got && r < G) s_x1[warp][lane] = x;
+                named_bar_sync(2, 64);
+                if (s_tmo) { tmo = true; break; }              // uniform over warps 0 and 1
+                if (warp == 0) {
+                    if (r < G) fold_partial(s_x1[0][lane], r0 == 0, bb, bj, cj, gsum, cnt, err);
+                    if (r + 32 < G) fold_partial(s_x1[1][lane], false, bb, bj, cj, gsum, cnt, err);
+                }
+                if (r0 + 64 < G) named_bar_sync(2, 64);       // s_x1 read before it is restaged
+            }
+        }
         if (warp == 0) {
-            // every CTA's partial of the last column: lane l folds CTAs l, l + 32, ...
-            // (all lanes take part in the combine)
-            Best bb{0ull, ~0ull, ~0ull, -1};
-            double bj = 0.0, cj = 0.0, gsum = 0.0;
-            int cnt[4] = {0, 0, 0, 0};
-            int err = 0;
             if (ls.have_prev) {
-                for (int r = lane; r < G; r += 64) {           // two loads in flight per lane
-                    const bool two = r + 32 < G;
-                    const CdPartial x0 = kGrid ? ldcg_partial(gbuf[pin] + r) : *cluster.map_shared_rank(&spart[pin], r);
-                    CdPartial x1;
-                    if (two) x1 = kGrid ? ldcg_partial(gbuf[pin] + r + 32) : *cluster.map_shared_rank(&spart[pin], r + 32);
-                    fold_partial(x0, r == lane, bb, bj, cj, gsum, cnt, err);
-                    if (two) fold_partial(x1, false, bb, bj, cj, gsum, cnt, err);
+                if (kGrid && it > 0) {
+                    // folded above
+                } else {
+                    for (int r = lane; r < G; r += 64) {       // two loads in flight per lane
+                        const bool two = r + 32 < G;
+                        // grid mode: the partials of the previous launch (or a restore)
+                        const CdPartial x0 = kGrid ? ldcg_partial(gpart + r) : *cluster.map_shared_rank(&spart[pin], r);
+                        CdPartial x1;
+                        if (two)
+                            x1 = kGrid ? ldcg_partial(gpart + r + 32) : *cluster.map_shared_rank(&spart[pin], r + 32);
+                        fold_partial(x0, r == lane, bb, bj, cj, gsum, cnt, err);
+                        if (two) fold_partial(x1, false, bb, bj, cj, gsum, cnt, err);
+                    }
                 }
                 warp_combine(bb, bj, cj, gsum, cnt, err);
             }
-            if (lane == 0) {
+            if (tmo) {
+                if (lane == 0) {
+                    set_status(st, kErrTimeout);
+                    sel.stop = 1;
+                    s_tmo = 1;
+                }
+            } else if (lane == 0) {
                 long long nslots = ls.n_slots;
                 double pb = 0.0;
                 unsigned long long gp = 0ull;
@@ -582,6 +673,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 if (nslots > P.max_entries) set_status(st, kErrTableFull);
                 ls.n_slots = nslots;
             }
+        }
         }
         __syncthreads();
         if (sel.stop) break;                          // identical in every CTA of the cluster
@@ -775,7 +867,7 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 pp.elements = c4[0]; pp.applied = c4[1]; pp.dropped = c4[2]; pp.inserted = c4[3] + s_fins;
                 s_fins = 0;
                 pp.err = s_err | (bad ? 1 : 0);
-                if (kGrid) gbuf[pout][rank] = pp; else spart[pout] = pp;
+                if (kGrid) spart[0] = pp; else spart[pout] = pp;
                 // the coordinate's own slot: c_i += eta, b_i as used (rank 0 writes)
                 const double ci = sel.ci, ci_new = ci + sel.eta;
                 if (rank == 0 && !bad) {
@@ -783,6 +875,11 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                     P.table[sel.islot].bv = sel.bi;
                 }
                 if (bad && rank == 0) set_status(st, kErrNonfinite);
+            }
+            if (kGrid) {
+                __syncwarp();
+                const unsigned int q = q0 + (unsigned int)it + 1u;
+                xchg_publish(xchg + ((size_t)(q & 1u) * G + rank) * kXchgWords, spart[0], q, lane);
             }
             if (lane == 0) {
                 const double ci = sel.ci, ci_new = ci + sel.eta;
@@ -802,19 +899,38 @@ __device__ __forceinline__ void cd_loop_body(const Problem &P, IterState *st, Cd
                 s_done = ls.done;
             }
         }
-        bool synced = true;
-        if (kGrid) synced = grid_barrier(bar, (unsigned)G, st);     // partials and table writes visible grid-wide
-        else if (G == 1) __syncthreads();
-        else cluster.sync();                                         // ... cluster-wide
+        if (kGrid) {
+            ++n_pub;
+            __syncthreads();                          // s_done; the partials travel through xchg
+        } else if (G == 1) {
+            __syncthreads();
+        } else {
+            cluster.sync();                           // partials and table writes visible cluster-wide
+        }
         lastp = pout;
-        if (s_done || bad || !synced) break;              // identical in every CTA
+        if (s_done || bad) break;                     // identical in every CTA
     }
 
     // ---- state for the next launch / the finalisation ----
-    if (tid == 0) {
-        if (!kGrid) gpart[rank] = spart[lastp];
-        else if (lastp == 0) gpart[rank] = gbuf[0][rank];
+    if (kGrid && n_pub > 0 && warp == 0 && !s_tmo) {
+        // every CTA's last partial published, so no CTA still reads gpart, rec or the buffers of
+        // this launch: this CTA's last partial becomes its gpart entry, rank 0 advances the rounds
+        const unsigned int q = q0 + n_pub;
+        bool fin = true;
+        for (int r0 = 0; r0 < G && fin; r0 += 32) {
+            CdPartial x;
+            fin = xchg_poll1(xchg + (size_t)(q & 1u) * G * kXchgWords, G, r0 + lane, q, x);
+        }
+        if (lane == 0) {
+            if (fin) {
+                gpart[rank] = spart[0];
+                if (rank == 0) rnd->round = __ldcg(&rnd->round) + n_pub;   // written by rank 0 alone
+            } else {
+                set_status(st, kErrTimeout);
+            }
+        }
     }
+    if (!kGrid && tid == 0) gpart[rank] = spart[lastp];
     if (tid == 0 && rank == 0) {      // lane 0 of the control warp holds the state
         CdRecord o;
         o.a = ls.pA; o.b = ls.pB; o.slot = ls.pslot;
@@ -840,9 +956,9 @@ __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop(Problem P, IterState 
 // the loop over every CTA of a cooperative launch (see cd_loop_body)
 template <int kE>
 __global__ void __launch_bounds__(kCdThreads, 1) k_cd_loop_grid(Problem P, IterState *st, CdRecord *rec,
-                                                                CdPartial *gpart, CdPartial *galt, GridBar *bar,
-                                                                long long n_iter) {
-    cd_loop_body<true, kE>(P, st, rec, gpart, galt, bar, n_iter);
+                                                                CdPartial *gpart, unsigned long long *xchg,
+                                                                GridRound *rnd, long long n_iter) {
+    cd_loop_body<true, kE>(P, st, rec, gpart, xchg, rnd, n_iter);
 }
 
 // Many independent problems in one launch: cluster k (blocks k*G .. k*G+G-1)
@@ -1300,10 +1416,12 @@ cudaError_t launch_cd_finalize_batch(const CdInstance *inst, int n_inst, int clu
     return cudaGetLastError();
 }
 
-// The grid-wide loop: G co-resident CTAs (cooperative launch); gpart and galt
-// hold G partials each, bar a zeroed GridBar.
-cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart, CdPartial *galt,
-                                GridBar *bar, int G, long long n_iter, cudaStream_t s) {
+// The grid-wide loop: G co-resident CTAs (cooperative launch); gpart
+// holds G partials, xchg 2 G kXchgWords zero-initialised words, rnd a
+// zero-initialised GridRound (both kept between launches).
+cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart,
+                                unsigned long long *xchg, GridRound *rnd, int G, long long n_iter, cudaStream_t s) {
+    if (G < 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kCdThreads);
@@ -1314,8 +1432,8 @@ cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cd_one_round(P, G)) return cudaLaunchKernelEx(&cfg, k_cd_loop_grid<1>, P, st, rec, gpart, galt, bar, n_iter);
-    return cudaLaunchKernelEx(&cfg, k_cd_loop_grid<kCdMaxE>, P, st, rec, gpart, galt, bar, n_iter);
+    if (cd_one_round(P, G)) return cudaLaunchKernelEx(&cfg, k_cd_loop_grid<1>, P, st, rec, gpart, xchg, rnd, n_iter);
+    return cudaLaunchKernelEx(&cfg, k_cd_loop_grid<kCdMaxE>, P, st, rec, gpart, xchg, rnd, n_iter);
 }
 
 // The largest CTA count of the grid-wide loop that can be co-resident (0 if none).

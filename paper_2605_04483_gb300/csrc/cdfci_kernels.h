@@ -117,8 +117,8 @@ constexpr int kMcKernels = 10;      // launches of one mCDFCI iteration
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // the m = 1 loop over more CTAs than a cluster holds (cooperative launch)
-cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart, CdPartial *galt,
-                                GridBar *bar, int G, long long n_iter, cudaStream_t s);
+cudaError_t launch_cd_loop_grid(const Problem &P, IterState *st, CdRecord *rec, CdPartial *gpart,
+                                unsigned long long *xchg, GridRound *rnd, int G, long long n_iter, cudaStream_t s);
 int cd_max_grid(size_t smem);
 
 // batches of independent m = 1 problems: one launch, one cluster per instance
