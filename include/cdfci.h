@@ -231,10 +231,10 @@ int cdfci_energies(cdfci_handle h, double *E, int32_t cap, int32_t *n_out);
  * recorded before every launch on the handle's stream, and writes into ms the
  * milliseconds spent from each launch to the next, summed over the
  * iterations, in launch order: 0 choice keys + level-0 histogram, 1 level-1
- * histogram, 2 levels 2.., 3 collect, 4 exact ties, 5 sort of the chosen set,
- * 6 c_I / b_I / H_II, 7 reduced problem, 8 scatter of the m columns,
- * 9 b_I recalculated.  *n_kernels = 10 (host pointer); ms holds up to cap
- * values (host pointer).  CDFCI_ERR_CAPACITY if cap < 10,
+ * histogram and the levels below it, 2 collect, 3 exact ties and the sort of
+ * the chosen set, 4 c_I / b_I / H_II, 5 reduced problem, 6 scatter of the m
+ * columns, 7 b_I recalculated.  *n_kernels = 8 (host pointer); ms holds up to
+ * cap values (host pointer).  CDFCI_ERR_CAPACITY if cap < 8,
  * CDFCI_ERR_UNIMPLEMENTED for other handles.
  */
 int cdfci_time_kernels(cdfci_handle h, int64_t n_iter, double *ms, int32_t cap, int32_t *n_kernels);

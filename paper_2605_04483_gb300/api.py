@@ -296,8 +296,7 @@ def cdfci_set_initial_degenerate(handle: int, tol: float = 0.0, cap: int = 0) ->
     return int(n.value), float(E.value)
 
 
-MC_KERNELS = ["gkeys", "hist_level1", "hist_tail", "collect", "ties", "sortsel", "prepare", "eigen", "scatter",
-              "finalize"]
+MC_KERNELS = ["gkeys", "hist", "collect", "sortsel", "prepare", "eigen", "scatter", "finalize"]
 
 
 def cdfci_fcidump_header(path: str) -> Tuple[int, int, int]:

@@ -482,32 +482,11 @@ __global__ void __launch_bounds__(256) k_mc_gkeys(Problem P, McState *ms, IterSt
     }
 }
 
-// level >= 1: the keys on the current prefix
-__global__ void __launch_bounds__(256) k_mc_hist(McState *ms, const unsigned long long *gkey, unsigned int *hist,
-                                                 int level, long long cap) {
-    __shared__ unsigned int sh[kSelBins];
-    if (ms->done || ms->sel_resolved) return;
-    const int n = mc_ncand(ms, cap);
-    const unsigned long long prefix = ms->sel_prefix;
-    const int need = ms->sel_need;
-    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
-    __syncthreads();
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int t = base + threadIdx.x;
-        unsigned long long k = t < n ? gkey[t] : 0ull;
-        const bool ok = t < n && sel_top(k, level) == prefix;
-        sel_bin_add(sh, ok, sel_digit(k, level));
-    }
-    if (sel_merge(sh, hist, hist + kSelBins)) sel_scan(ms, hist, hist + kSelBins, level, need);
-}
-
-// Levels 2.. on one CTA of 1024 threads (one launch instead of one per level):
-// it returns at once when the selection is resolved, which is the common case;
-// otherwise it counts the keys on the prefix in a shared-memory histogram and
-// scans it, level by level, exactly as k_mc_hist and sel_scan do.
-__global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsigned long long *gkey, long long cap) {
-    __shared__ unsigned int sh[kSelBins];
+// Levels 2.. by the block that finished level 1 (1024 threads): it stops at once
+// when the selection is resolved, which is the common case; otherwise it counts
+// the keys on the prefix in a shared-memory histogram and scans it, level by
+// level, exactly as the level-1 pass and sel_scan do.
+__device__ void mc_hist_tail(McState *ms, const unsigned long long *gkey, long long cap, unsigned int *sh) {
     __shared__ unsigned int s_warp[32];
     __shared__ int s_stop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -515,7 +494,7 @@ __global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsign
         if (tid == 0) s_stop = (ms->done || ms->sel_resolved) ? 1 : 0;
         for (int d = tid; d < kSelBins; d += blockDim.x) sh[d] = 0u;
         __syncthreads();
-        if (s_stop) return;
+        if (s_stop) return;                               // uniform
         const int n = mc_ncand(ms, cap);
         const unsigned long long prefix = ms->sel_prefix;
         const int need = ms->sel_need;
@@ -560,6 +539,34 @@ __global__ void __launch_bounds__(1024) k_mc_hist_tail(McState *ms, const unsign
     }
 }
 
+// level 1 on the grid: the keys on the level-0 prefix; the last block to merge
+// its histogram scans it and goes on with the levels below (mc_hist_tail)
+constexpr int kHistThreads = 1024;
+__global__ void __launch_bounds__(kHistThreads) k_mc_hist(McState *ms, const unsigned long long *gkey,
+                                                          unsigned int *hist, long long cap) {
+    __shared__ unsigned int sh[kSelBins];
+    const int level = 1;
+    if (ms->done || ms->sel_resolved) return;
+    const int n = mc_ncand(ms, cap);
+    const unsigned long long prefix = ms->sel_prefix;
+    const int need = ms->sel_need;
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
+    __syncthreads();
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int t = base + threadIdx.x;
+        unsigned long long k = t < n ? gkey[t] : 0ull;
+        const bool ok = t < n && sel_top(k, level) == prefix;
+        sel_bin_add(sh, ok, sel_digit(k, level));
+    }
+    if (sel_merge(sh, hist, hist + kSelBins)) {
+        sel_scan(ms, hist, hist + kSelBins, level, need);
+        __threadfence_block();
+        __syncthreads();                                // the scan's McState fields visible to the block
+        mc_hist_tail(ms, gkey, cap, sh);
+    }
+}
+
 __global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, const unsigned long long *gkey,
                              McSel *sel, McSel *inbin) {
     if (ms->done) return;
@@ -597,12 +604,13 @@ __global__ void k_mc_collect(Problem P, McState *ms, const long long *cand, cons
 // by a radix selection on the 128-bit key (B, A), 8 bits per pass from the
 // top, in one CTA over a compacted copy of the tied candidates.  The chosen
 // ones replace the in-bin buffer.  Symmetric lattices produce such groups.
-__global__ void __launch_bounds__(1024) k_mc_ties(Problem P, McState *ms, const long long *cand,
-                                                   const unsigned long long *gkey, McSel *ties, McSel *inbin) {
+// Run by the sorting CTA before it sorts (the caller has checked the
+// condition; block-uniform).
+__device__ void mc_ties(const Problem &P, McState *ms, const long long *cand, const unsigned long long *gkey,
+                        McSel *ties, McSel *inbin) {
     __shared__ unsigned int hist[256];
     __shared__ int s_n, s_out, s_digit;
     __shared__ unsigned int s_below;
-    if (ms->done || ms->sel_level < kSelLevels || ms->n_inbin <= kInBin) return;
     const int n = mc_ncand(ms, P.cap_cand), tid = threadIdx.x;
     const unsigned long long g = ms->sel_prefix;
     int need = ms->sel_need;
@@ -668,6 +676,8 @@ __global__ void __launch_bounds__(1024) k_mc_ties(Problem P, McState *ms, const 
         }
     __syncthreads();
     if (tid == 0) ms->n_inbin = s_out;                 // = sel_need
+    __threadfence_block();
+    __syncthreads();
 }
 
 // Bitonic sort, in shared memory, of (choice key, index) pairs into the choice
@@ -715,14 +725,17 @@ __device__ void bitonic_reg(SelE &e, int n_pow2, SelE *buf) {
     }
 }
 
-// The in-bin candidates sorted, the first sel_need of them join the chosen
-// set; then the chosen set in the choice order (a canonical order for the
-// reduced problem's rows).  1024 threads, one element each.
-__global__ void __launch_bounds__(1024) k_mc_sortsel(McState *ms, McSel *sel, const McSel *inbin, int m,
-                                                      IterState *st) {
+// The in-bin candidates sorted (after the exact-tie pass when more than kInBin
+// share the whole 64-bit choice key), the first sel_need of them join the
+// chosen set; then the chosen set in the choice order (a canonical order for
+// the reduced problem's rows).  1024 threads, one element each.
+__global__ void __launch_bounds__(1024) k_mc_sortsel(Problem P, McState *ms, McSel *sel, McSel *inbin, int m,
+                                                      IterState *st, const long long *cand,
+                                                      const unsigned long long *gkey, McSel *ties) {
     __shared__ SelE buf[kInBin];
     const int tid = threadIdx.x;
     if (ms->done) return;
+    if (ms->sel_level >= kSelLevels && ms->n_inbin > kInBin) mc_ties(P, ms, cand, gkey, ties, inbin);   // uniform
     const int n_above = ms->n_above;
     int n_in = ms->n_inbin;
     if (ms->sel_level > 0 && n_in > kInBin) {
@@ -2443,15 +2456,11 @@ cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream
     mark();
     k_mc_gkeys<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.st, b.cand, b.gkey, b.hist, b.m);
     mark();
-    k_mc_hist<<<b.cand_grid, 256, 0, s>>>(b.ms, b.gkey, b.hist, 1, b.cap_cand);
-    mark();
-    k_mc_hist_tail<<<1, 1024, 0, s>>>(b.ms, b.gkey, b.cap_cand);
+    k_mc_hist<<<(b.cand_grid + 3) / 4, kHistThreads, 0, s>>>(b.ms, b.gkey, b.hist, b.cap_cand);
     mark();
     k_mc_collect<<<b.cand_grid, 256, 0, s>>>(P, b.ms, b.cand, b.gkey, b.sel, b.inbin);
     mark();
-    k_mc_ties<<<1, 1024, 0, s>>>(P, b.ms, b.cand, b.gkey, b.ties, b.inbin);
-    mark();
-    k_mc_sortsel<<<1, 1024, 0, s>>>(b.ms, b.sel, b.inbin, b.m, b.st);
+    k_mc_sortsel<<<1, 1024, 0, s>>>(P, b.ms, b.sel, b.inbin, b.m, b.st, b.cand, b.gkey, b.ties);
     mark();
     k_mc_prepare<<<(b.m + kPrepWarps - 1) / kPrepWarps, 32 * kPrepWarps, 0, s>>>(
         P, b.ms, b.sel, b.cI, b.bI, b.Hdiag, b.HIIc, b.rowf, b.Rh, b.Rl, b.ldr, b.coltab, b.collists,

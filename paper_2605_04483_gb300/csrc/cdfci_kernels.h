@@ -113,7 +113,7 @@ cudaError_t launch_entry(const Problem &P, unsigned long long A1, unsigned long 
 cudaError_t launch_mc_start(const Problem &P, const McBuffers &b, unsigned long long A, unsigned long long B,
                             double eta, int first, cudaStream_t s);
 cudaError_t launch_mc_scatter_finalize(const Problem &P, const McBuffers &b, cudaStream_t s);
-constexpr int kMcKernels = 10;      // launches of one mCDFCI iteration
+constexpr int kMcKernels = 8;       // launches of one mCDFCI iteration
 cudaError_t launch_mc_iteration(const Problem &P, const McBuffers &b, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // the m = 1 loop over more CTAs than a cluster holds (cooperative launch)
