@@ -68,8 +68,8 @@ typedef struct {
                                   thread-block cluster (rounded to a size that can be resident);
                                   above 16 the loop runs as one cooperative grid of that many CTAs
                                   (at most the number that can be co-resident, clamped) whose CTAs
-                                  meet at a bounded software barrier once per iteration; m > 1:
-                                  ignored */
+                                  hand their partials over once per iteration through round-numbered
+                                  words in device memory (bounded waits); m > 1: ignored */
     int32_t  graph_chunk;      /* m = 1: iterations per persistent launch (0 = 65536);
                                   m > 1: iterations per captured CUDA graph (0 = 8) */
     int32_t  deterministic;    /* reserved.  m = 1 is deterministic (fixed-order reductions, one update
