@@ -102,7 +102,8 @@ def test_trajectory_config2_full_size():
 @pytest.mark.parametrize("grid_blocks", [24, 48, 152])
 def test_trajectory_config2_grid_wide(grid_blocks):
     """The m = 1 loop over more CTAs than a cluster (cooperative launch, partials
-    through global memory, software grid barrier) follows the oracle as well."""
+    handed over through round-numbered words in global memory; 152 CTAs poll two
+    partial pairs per lane) follows the oracle as well."""
     w = inputs.config2()
     agreed, g, o = run_trajectory(w, 40, tau=1e-5, vec_every=20, log2_capacity=21, grid_blocks=grid_blocks)
     st = g.stats()
@@ -112,7 +113,9 @@ def test_trajectory_config2_grid_wide(grid_blocks):
 
 
 def test_grid_wide_steps_are_deterministic():
-    """Grid-wide loop: cdfci_step(n) == n calls of cdfci_step(1), and reruns are bit-identical."""
+    """Grid-wide loop: cdfci_step(n) == n calls of cdfci_step(1) (one published round per launch:
+    the exit handshake, the partials kept between launches and the round count), and reruns are
+    bit-identical."""
     w = inputs.ab_initio(12, 4, 4, seed=3)
     a = solver(w, grid_blocks=40)
     b = solver(w, grid_blocks=40)
