@@ -16,12 +16,16 @@
 // Each row j occurs once in a column, so B_j is updated by plain loads and
 // stores, and every reduction has a fixed order: the iteration is
 // deterministic.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "cdfci_internal.cuh"
 #include "cdfci_kernels.h"
 
 namespace cdfci {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -249,6 +253,7 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
     const double thr = xs->thr;
     const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
     double gat[kXMax];
+#pragma unroll
     for (int a = 0; a < kXMax; ++a) gat[a] = 0.0;
     unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     for (long long e = 1 + (long long)blockIdx.x * blockDim.x + tid; e < nh; e += (long long)gridDim.x * blockDim.x) {
@@ -260,8 +265,9 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
         long long s = table_find(P, st, oa, ob, false, &ins);
         double cj[kXMax];
         bool cnz = false;
-        for (int a = 0; a < k1; ++a) {
-            cj[a] = s >= 0 ? __ldcg(rows + s * 2 * k1 + a) : 0.0;
+#pragma unroll
+        for (int a = 0; a < kXMax; ++a) {
+            cj[a] = s >= 0 && a < k1 ? __ldcg(rows + s * 2 * k1 + a) : 0.0;
             cnz = cnz || cj[a] != 0.0;
         }
         if (!cnz && !(fabs(H) >= thr)) { ++c2; continue; }
@@ -272,20 +278,28 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
         }
         ++c1;
         double *br = rows + s * 2 * k1 + k1;
-        for (int a = 0; a < k1; ++a) {
+#pragma unroll
+        for (int a = 0; a < kXMax; ++a) {
+            if (a >= k1) break;
             br[a] = fma(H, sw[a], __ldcg(br + a));
             gat[a] = fma(H, cj[a], gat[a]);
         }
         const unsigned long long kb = P.table[s].b;
         if (!(kb & kMarkB)) {
             P.table[s].b = kb | kMarkB;
-            const int pos = atomicAdd(&xs->n_cand, 1);
+            // one reservation for the lanes that get here together (a warp-aggregated append)
+            const cg::coalesced_group grp = cg::coalesced_threads();
+            int base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(&xs->n_cand, (int)grp.size());
+            const int pos = grp.shfl(base, 0) + (int)grp.thread_rank();
             if (pos < cap_cand) cand[pos] = s;
             else set_status(st, kErrInternal);
         }
     }
     // gather: warp tree, then warps in order (fixed order)
-    for (int a = 0; a < k1; ++a) {
+#pragma unroll
+    for (int a = 0; a < kXMax; ++a) {
+        if (a >= k1) break;
         double v = gat[a];
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) sg[warp][a] = v;
@@ -303,23 +317,33 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
 __global__ void __launch_bounds__(kXThreads) k_x_finalize(Problem P, XState *xs, IterState *st, double *rows,
                                                           const double *gathp, int nblocks, long long *cand,
                                                           long long cap_cand) {
-    __shared__ double red[kXThreads];
+    __shared__ double red[kXMax][kXThreads];
     if (xs->eta == 0.0 || st->status) return;                        // no step this iteration
     const int k1 = xs->k1, tid = threadIdx.x;
     const long long s = xs->slot;
     const double Hii = xs->Hii;
-    for (int a = 0; a < k1; ++a) {
-        double v = 0.0;
-        for (int k = tid; k < nblocks; k += blockDim.x) v += gathp[(size_t)k * k1 + a];
-        red[tid] = v;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (tid < w) red[tid] += red[tid + w];
-            __syncthreads();
+    // every state at once: per state, the thread's blocks in order, then the same pairwise tree
+    double v[kXMax];
+#pragma unroll
+    for (int a = 0; a < kXMax; ++a) v[a] = 0.0;
+    for (int k = tid; k < nblocks; k += blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < kXMax; ++a)
+            if (a < k1) v[a] += gathp[(size_t)k * k1 + a];
+    }
+#pragma unroll
+    for (int a = 0; a < kXMax; ++a)
+        if (a < k1) red[a][tid] = v[a];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+#pragma unroll
+            for (int a = 0; a < kXMax; ++a)
+                if (a < k1) red[a][tid] += red[a][tid + w];
         }
-        if (tid == 0) rows[s * 2 * k1 + k1 + a] = fma(Hii, rows[s * 2 * k1 + a], red[0]);
         __syncthreads();
     }
+    if (tid < k1) rows[s * 2 * k1 + k1 + tid] = fma(Hii, rows[s * 2 * k1 + tid], red[tid][0]);
     if (tid == 0) {
         const unsigned long long kb = P.table[s].b;
         if (!(kb & kMarkB)) {
