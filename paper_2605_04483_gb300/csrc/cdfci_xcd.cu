@@ -242,20 +242,19 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
     __shared__ ColLists L;
     __shared__ double sw[kXMax];
     __shared__ double sg[kXThreads / 32][kXMax];
-    __shared__ unsigned long long s_cnt[4];
+    __shared__ unsigned int s_cnt[4][kXThreads / 32];
     if (xs->eta == 0.0 || st->status) return;                        // no step this iteration
     const int k1 = xs->k1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long A = xs->A, B = xs->B;
     build_lists(L, P.N, A, B);
     if (tid < k1) sw[tid] = xs->wv[tid];
-    if (tid < 4) s_cnt[tid] = 0ull;
     __syncthreads();
     const double thr = xs->thr;
     const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
     double gat[kXMax];
 #pragma unroll
     for (int a = 0; a < kXMax; ++a) gat[a] = 0.0;
-    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    unsigned int c0 = 0, c1 = 0, c2 = 0, c3 = 0;                     // elements, applied, dropped, inserted
     for (long long e = 1 + (long long)blockIdx.x * blockDim.x + tid; e < nh; e += (long long)gridDim.x * blockDim.x) {
         unsigned long long oa, ob;
         const double H = column_element(P, L, A, B, e, oa, ob);
@@ -304,14 +303,21 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) sg[warp][a] = v;
     }
-    atomicAdd(&s_cnt[0], c0); atomicAdd(&s_cnt[1], c1); atomicAdd(&s_cnt[2], c2); atomicAdd(&s_cnt[3], c3);
+    // counters: warp sums (no shared-memory atomics), then the warps in order
+    c0 = __reduce_add_sync(0xffffffffu, c0); c1 = __reduce_add_sync(0xffffffffu, c1);
+    c2 = __reduce_add_sync(0xffffffffu, c2); c3 = __reduce_add_sync(0xffffffffu, c3);
+    if (lane == 0) { s_cnt[0][warp] = c0; s_cnt[1][warp] = c1; s_cnt[2][warp] = c2; s_cnt[3][warp] = c3; }
     __syncthreads();
     if (tid < k1) {
         double v = sg[0][tid];
         for (int w = 1; w < kXThreads / 32; ++w) v += sg[w][tid];
         gathp[(size_t)blockIdx.x * k1 + tid] = v;
     }
-    if (tid < 4) atomicAdd(&xs->cnt[tid], s_cnt[tid]);
+    if (tid < 4) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kXThreads / 32; ++w) t += s_cnt[tid][w];
+        if (t) atomicAdd(&xs->cnt[tid], t);
+    }
 }
 
 __global__ void __launch_bounds__(kXThreads) k_x_finalize(Problem P, XState *xs, IterState *st, double *rows,
