@@ -237,6 +237,38 @@ __global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, 
     }
 }
 
+// Row j of C and of B (k1 values each) into cv and bv, all loads in flight together.
+__device__ __forceinline__ void x_load_row(const double *rows, long long j, int k1, double (&cv)[kXMax],
+                                           double (&bv)[kXMax]) {
+#pragma unroll
+    for (int a = 0; a < kXMax; ++a) {
+        cv[a] = a < k1 ? __ldcg(rows + j * 2 * k1 + a) : 0.0;
+        bv[a] = a < k1 ? __ldcg(rows + j * 2 * k1 + k1 + a) : 0.0;
+    }
+}
+
+// The slot of key {a, b} by linear probing from pos (no insert): -1 absent, -2
+// error (status set); kbo receives the slot's b word, candidate mark included.
+__device__ __forceinline__ long long x_find(const Problem &P, IterState *st, unsigned long long a,
+                                            unsigned long long b, unsigned long long pos, unsigned long long &kbo) {
+    const bool both_nonzero = (P.na > 0) && (P.nb > 0);
+    for (int probe = 0; probe < P.max_probe; ++probe) {
+        const Slot *s = P.table + pos;
+        unsigned long long ka = __ldcg(&s->a), kb = __ldcg(&s->b);
+        int spins = 0;
+        while (both_nonzero && ((ka == 0ull) != (kb == 0ull))) {     // an insert in flight
+            if (++spins > (1 << 20)) { set_status(st, kErrTimeout); return -2; }
+            ka = __ldcg(&s->a);
+            kb = __ldcg(&s->b);
+        }
+        if (ka == a && (kb & kKeyMaskB) == b) { kbo = kb; return (long long)pos; }
+        if (ka == 0ull && kb == 0ull) return -1;
+        pos = (pos + 1) & P.mask;
+    }
+    set_status(st, kErrTableFull);
+    return -2;
+}
+
 __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, IterState *st, double *rows,
                                                          long long *cand, long long cap_cand, double *gathp) {
     __shared__ ColLists L;
@@ -260,30 +292,39 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
         const double H = column_element(P, L, A, B, e, oa, ob);
         if (is_zero(H)) continue;
         ++c0;
-        bool ins = false;
-        long long s = table_find(P, st, oa, ob, false, &ins);
+        // the row at the key's first probe position loads beside the key (it is usually found
+        // there); no other thread of this launch writes row j or the mark of j (each row occurs
+        // once in a column), so the values loaded here are current
+        const unsigned long long pos0 = key_hash(oa, ob) & P.mask;
+        double rc[kXMax], rb[kXMax];
+        x_load_row(rows, (long long)pos0, k1, rc, rb);
+        unsigned long long kb = 0ull;
+        long long s = x_find(P, st, oa, ob, pos0, kb);
+        if (s >= 0 && s != (long long)pos0) x_load_row(rows, s, k1, rc, rb);
         double cj[kXMax];
         bool cnz = false;
 #pragma unroll
         for (int a = 0; a < kXMax; ++a) {
-            cj[a] = s >= 0 && a < k1 ? __ldcg(rows + s * 2 * k1 + a) : 0.0;
+            cj[a] = s >= 0 && a < k1 ? rc[a] : 0.0;
             cnz = cnz || cj[a] != 0.0;
         }
         if (!cnz && !(fabs(H) >= thr)) { ++c2; continue; }
         if (s < 0) {
+            bool ins = false;
             s = table_find(P, st, oa, ob, true, &ins);
             if (s < 0) continue;                                      // table full: status set
             if (ins) ++c3;
+            x_load_row(rows, s, k1, rc, rb);
+            kb = __ldcg(&P.table[s].b);
         }
         ++c1;
         double *br = rows + s * 2 * k1 + k1;
 #pragma unroll
         for (int a = 0; a < kXMax; ++a) {
             if (a >= k1) break;
-            br[a] = fma(H, sw[a], __ldcg(br + a));
+            br[a] = fma(H, sw[a], rb[a]);
             gat[a] = fma(H, cj[a], gat[a]);
         }
-        const unsigned long long kb = P.table[s].b;
         if (!(kb & kMarkB)) {
             P.table[s].b = kb | kMarkB;
             // one reservation for the lanes that get here together (a warp-aggregated append)
