@@ -237,13 +237,31 @@ __global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, 
     }
 }
 
-// Row j of C and of B (k1 values each) into cv and bv, all loads in flight together.
+// Row j of C and of B (k1 values each) into cv and bv, all loads in flight
+// together: 16-byte loads when k1 is even (each half is then whole pairs, and
+// a row starts at a multiple of 16 bytes), else 8-byte ones.  The scatter is
+// bound by the number of memory requests its elements make at once.
 __device__ __forceinline__ void x_load_row(const double *rows, long long j, int k1, double (&cv)[kXMax],
                                            double (&bv)[kXMax]) {
+    const double *r = rows + j * 2 * k1;
+    if ((k1 & 1) == 0) {                                             // uniform
+        const double2 *r2 = reinterpret_cast<const double2 *>(r);
+#pragma unroll
+        for (int q = 0; q < kXMax / 2; ++q) {
+            double2 c2 = make_double2(0.0, 0.0), b2 = c2;
+            if (2 * q < k1) {
+                c2 = __ldcg(r2 + q);
+                b2 = __ldcg(r2 + k1 / 2 + q);
+            }
+            cv[2 * q] = c2.x; cv[2 * q + 1] = c2.y;
+            bv[2 * q] = b2.x; bv[2 * q + 1] = b2.y;
+        }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < kXMax; ++a) {
-        cv[a] = a < k1 ? __ldcg(rows + j * 2 * k1 + a) : 0.0;
-        bv[a] = a < k1 ? __ldcg(rows + j * 2 * k1 + k1 + a) : 0.0;
+        cv[a] = a < k1 ? __ldcg(r + a) : 0.0;
+        bv[a] = a < k1 ? __ldcg(r + k1 + a) : 0.0;
     }
 }
 
@@ -254,13 +272,13 @@ __device__ __forceinline__ long long x_find(const Problem &P, IterState *st, uns
     const bool both_nonzero = (P.na > 0) && (P.nb > 0);
     for (int probe = 0; probe < P.max_probe; ++probe) {
         const Slot *s = P.table + pos;
-        unsigned long long ka = __ldcg(&s->a), kb = __ldcg(&s->b);
+        ulonglong2 k = __ldcg(reinterpret_cast<const ulonglong2 *>(s));         // the key in one request
         int spins = 0;
-        while (both_nonzero && ((ka == 0ull) != (kb == 0ull))) {     // an insert in flight
+        while (both_nonzero && ((k.x == 0ull) != (k.y == 0ull))) {   // an insert in flight
             if (++spins > (1 << 20)) { set_status(st, kErrTimeout); return -2; }
-            ka = __ldcg(&s->a);
-            kb = __ldcg(&s->b);
+            k = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
         }
+        const unsigned long long ka = k.x, kb = k.y;
         if (ka == a && (kb & kKeyMaskB) == b) { kbo = kb; return (long long)pos; }
         if (ka == 0ull && kb == 0ull) return -1;
         pos = (pos + 1) & P.mask;
@@ -279,7 +297,7 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
     const int k1 = xs->k1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long A = xs->A, B = xs->B;
     build_lists(L, P.N, A, B);
-    if (tid < k1) sw[tid] = xs->wv[tid];
+    if (tid < kXMax) sw[tid] = tid < k1 ? xs->wv[tid] : 0.0;
     __syncthreads();
     const double thr = xs->thr;
     const long long nh = P.doubles_vanish ? P.seg[2] : P.seg[5];
@@ -319,11 +337,20 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
         }
         ++c1;
         double *br = rows + s * 2 * k1 + k1;
+        double bn[kXMax];
 #pragma unroll
         for (int a = 0; a < kXMax; ++a) {
-            if (a >= k1) break;
-            br[a] = fma(H, sw[a], rb[a]);
-            gat[a] = fma(H, cj[a], gat[a]);
+            bn[a] = fma(H, sw[a], rb[a]);
+            if (a < k1) gat[a] = fma(H, cj[a], gat[a]);
+        }
+        if ((k1 & 1) == 0) {                                          // 16-byte stores (see x_load_row)
+#pragma unroll
+            for (int q = 0; q < kXMax / 2; ++q)
+                if (2 * q < k1) reinterpret_cast<double2 *>(br)[q] = make_double2(bn[2 * q], bn[2 * q + 1]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < kXMax; ++a)
+                if (a < k1) br[a] = bn[a];
         }
         if (!(kb & kMarkB)) {
             P.table[s].b = kb | kMarkB;
