@@ -131,13 +131,54 @@ __global__ void __launch_bounds__(kXThreads) k_x_select(Problem P, XState *xs, I
     xs->slot = b.slot; xs->A = b.a; xs->B = b.b;
 }
 
+// H_ii exactly as diag_warp(P, L) computes it (the same terms, per-lane sums
+// in the same order, the same tree), with every lane's loads issued before the
+// first addition: one round trip for the integrals of up to 16 electrons.
+__device__ __forceinline__ double x_diag(const Problem &P, const ColLists &L) {
+    const int lane = threadIdx.x & 31;
+    const int N = P.N, n = P.na + P.nb, n2 = n * n;
+    if (n > 16) return diag_warp(P, L);                               // more than two rounds per lane
+    const int ph = lane < n ? (lane < P.na ? L.occA[lane] : L.occB[lane - P.na]) : 0;
+    const double hv = lane < n ? __ldg(P.h + ph * (N + 1)) : 0.0;
+    double tv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {                                     // t = lane + 128 (k / 4) + 32 (k % 4)
+        const int t = lane + 128 * (k >> 2) + 32 * (k & 3);
+        tv[k] = 0.0;
+        if (t < n2) {
+            const int u = t / n, w = t - u * n;
+            if (u != w) {
+                const bool ua = u < P.na, wa = w < P.na;
+                const int p = ua ? L.occA[u] : L.occB[u - P.na];
+                const int q = wa ? L.occA[w] : L.occB[w - P.na];
+                const double jv = P.J[p * N + q];
+                tv[k] = (ua == wa) ? (jv - P.K[p * N + q]) : jv;
+            }
+        }
+    }
+    double x = 0.0;
+    if (lane < n) x += hv;
+    double y4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int t = lane + 128 * (k >> 2) + 32 * (k & 3);
+        if (t < n2) {
+            const int u = t / n, w = t - u * n;
+            if (u != w) y4[k & 3] += tv[k];
+        }
+    }
+    x = fma(0.5, (y4[0] + y4[1]) + (y4[2] + y4[3]), x);
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    return __shfl_sync(0xffffffffu, x, 0);
+}
+
 // forced >= 0: the start step of row {fA, fB} with g = e_forced and eta = 1.
 __global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, int forced, unsigned long long fA,
                             unsigned long long fB) {
     __shared__ ColLists L;
     __shared__ long long s_slot;
-    __shared__ double s_c[kXMax], s_g[kXMax], s_b[kXMax];
-    __shared__ double s_eta;
+    __shared__ double s_c[kXMax], s_g[kXMax], s_b[kXMax], s_t[kXMax];
+    __shared__ double s_eta, s_gn, s_w[kXMax];
     __shared__ int s_stop;
     if (xs->done || st->status) return;
     const int k1 = xs->k1, lane = threadIdx.x;
@@ -158,13 +199,18 @@ __global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, 
     __syncwarp();
     if (s_stop) return;
     build_lists(L, P.N, xs->A, xs->B);
-    __syncwarp();
-    const double Hii = diag_warp(P, L);
     const long long s = s_slot;
-    if (lane < k1) {
+    if (lane < k1) {                                                  // loads in flight beside H_ii's
         s_c[lane] = rows[s * 2 * k1 + lane];
         s_b[lane] = rows[s * 2 * k1 + k1 + lane];
         s_g[lane] = xs->g[lane];
+    }
+    __syncwarp();
+    const double Hii = x_diag(P, L);
+    if (lane < k1 && forced < 0) {                                    // (S g)_a, lane a: the term of g S g^T
+        double t = 0.0;
+        for (int b = 0; b < k1; ++b) t = fma(xs->S[lane * k1 + b].hi + xs->S[lane * k1 + b].lo, s_g[b], t);
+        s_t[lane] = t;
     }
     __syncwarp();
     if (lane == 0) {
@@ -178,14 +224,13 @@ __global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, 
                 gg = fma(s_g[a], s_g[a], gg);
                 cg = fma(s_c[a], s_g[a], cg);
                 cc = fma(s_c[a], s_c[a], cc);
-                double t = 0.0;
-                for (int b = 0; b < k1; ++b) t = fma(xs->S[a * k1 + b].hi + xs->S[a * k1 + b].lo, s_g[b], t);
-                gSg = fma(s_g[a], t, gSg);
+                gSg = fma(s_g[a], s_t[a], gSg);
             }
             // In t = eta ||g|| the quartic is monic with O(1) coefficients (w / w4 would grow like
             // 1 / ||g||^2 near convergence and overflow the single-precision root stage):
             // t^4 + 4 (c.u) t^3 + (2 H_ii + 2 (c.u)^2 + 2 ||c||^2 + 2 u S u^T) t^2 + ||g|| t, u = g / ||g||.
             const double gn = sqrt(gg);
+            s_gn = gn;
             if (!(gn > 0.0)) { xs->done = 1; s_stop = 1; }
             else {
                 const double cu = cg / gn;
@@ -212,25 +257,28 @@ __global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, 
         xs->S[t] = dd_add(xs->S[t], ds);
         xs->M[t] = dd_add(xs->M[t], dm);
     }
+    // C_i += eta g (lane a), the scatter weights eta g and their largest magnitude
+    const bool on = lane < k1;
+    double cn = 0.0;
+    if (on) {
+        cn = fma(eta, s_g[lane], s_c[lane]);
+        rows[s * 2 * k1 + lane] = cn;
+        const double wa = eta * s_g[lane];
+        xs->wv[lane] = wa;
+        s_w[lane] = fabs(wa);
+    }
+    const unsigned was = __ballot_sync(0xffffffffu, on && s_c[lane] != 0.0);
+    const unsigned now = __ballot_sync(0xffffffffu, on && cn != 0.0);
+    __syncwarp();
     if (lane == 0) {
-        bool was = false, now = false;
         double wmax = 0.0;
-        for (int a = 0; a < k1; ++a) {
-            const double cn = fma(eta, s_g[a], s_c[a]);
-            was = was || s_c[a] != 0.0;
-            now = now || cn != 0.0;
-            rows[s * 2 * k1 + a] = cn;
-            xs->wv[a] = eta * s_g[a];
-            wmax = fmax(wmax, fabs(eta * s_g[a]));
-        }
+        for (int a = 0; a < k1; ++a) wmax = fmax(wmax, s_w[a]);
         xs->nnz_c += (now ? 1 : 0) - (was ? 1 : 0);
         xs->thr = wmax > 0.0 ? P.tau / wmax : 1.0e308;
         xs->eta = eta;
         xs->Hii = Hii;
         if (forced < 0) {
-            double gn = 0.0;
-            for (int a = 0; a < k1; ++a) gn = fma(s_g[a], s_g[a], gn);
-            xs->dx = P.theta * xs->dx + (1.0 - P.theta) * fabs(eta) * sqrt(gn);
+            xs->dx = P.theta * xs->dx + (1.0 - P.theta) * fabs(eta) * s_gn;   // s_gn = ||g||
             xs->iterations += 1;
             if (P.dx_threshold > 0.0 && xs->dx < P.dx_threshold) xs->done = 1;
         }
