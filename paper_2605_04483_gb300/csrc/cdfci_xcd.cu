@@ -45,16 +45,21 @@ __device__ __forceinline__ bool x_better(const XBest &x, const XBest &y) {
     return x.gbits > y.gbits || (x.gbits == y.gbits && key_less(x.a, x.b, y.a, y.b));
 }
 
-__device__ __forceinline__ double x_gnorm(const double *row, const double *S, int k1, double *G) {
+
+// ||G_j||_inf and G_j = 4 B_j + 4 C_j S from the row's C and B halves (G may be null)
+__device__ __forceinline__ double x_gnorm(const double (&c)[kXMax], const double (&bb)[kXMax], const double *S, int k1,
+                                           double *G) {
     double m = 0.0;
+#pragma unroll
     for (int a = 0; a < kXMax; ++a) {
         if (a >= k1) break;
         double s = 0.0;
+#pragma unroll
         for (int b = 0; b < kXMax; ++b) {
             if (b >= k1) break;
-            s = fma(row[b], S[b * k1 + a], s);
+            s = fma(c[b], S[b * k1 + a], s);
         }
-        const double ga = 4.0 * row[k1 + a] + 4.0 * s;
+        const double ga = 4.0 * bb[a] + 4.0 * s;
         if (G) G[a] = ga;
         m = fmax(m, fabs(ga));
     }
@@ -64,6 +69,34 @@ __device__ __forceinline__ double x_gnorm(const double *row, const double *S, in
 }  // namespace
 
 constexpr int kXThreads = 256;
+
+// Row j of C and of B (k1 values each) into cv and bv, all loads in flight
+// together: 16-byte loads when k1 is even (each half is then whole pairs, and
+// a row starts at a multiple of 16 bytes), else 8-byte ones.  The scatter is
+// bound by the number of memory requests its elements make at once.
+__device__ __forceinline__ void x_load_row(const double *rows, long long j, int k1, double (&cv)[kXMax],
+                                           double (&bv)[kXMax]) {
+    const double *r = rows + j * 2 * k1;
+    if ((k1 & 1) == 0) {                                             // uniform
+        const double2 *r2 = reinterpret_cast<const double2 *>(r);
+#pragma unroll
+        for (int q = 0; q < kXMax / 2; ++q) {
+            double2 c2 = make_double2(0.0, 0.0), b2 = c2;
+            if (2 * q < k1) {
+                c2 = __ldcg(r2 + q);
+                b2 = __ldcg(r2 + k1 / 2 + q);
+            }
+            cv[2 * q] = c2.x; cv[2 * q + 1] = c2.y;
+            bv[2 * q] = b2.x; bv[2 * q + 1] = b2.y;
+        }
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < kXMax; ++a) {
+        cv[a] = a < k1 ? __ldcg(r + a) : 0.0;
+        bv[a] = a < k1 ? __ldcg(r + k1 + a) : 0.0;
+    }
+}
 
 __global__ void __launch_bounds__(kXThreads) k_x_select(Problem P, XState *xs, IterState *st, const long long *cand,
                                                         const double *rows, XBest *bbest, unsigned int *counter) {
@@ -78,11 +111,11 @@ __global__ void __launch_bounds__(kXThreads) k_x_select(Problem P, XState *xs, I
     XBest best{0ull, ~0ull, ~0ull, -1};
     for (int t = blockIdx.x * blockDim.x + tid; t < n; t += gridDim.x * blockDim.x) {
         const long long s = cand[t];
-        double row[2 * kXMax];
-        for (int a = 0; a < 2 * k1; ++a) row[a] = __ldcg(rows + s * 2 * k1 + a);
-        const Slot sl = P.table[s];
-        P.table[s].b = sl.b & kKeyMaskB;                           // no longer a candidate
-        const XBest x{x_abs_bits(x_gnorm(row, sS, k1, nullptr)), sl.a, sl.b & kKeyMaskB, s};
+        double rc[kXMax], rb[kXMax];
+        x_load_row(rows, s, k1, rc, rb);
+        const ulonglong2 key = __ldcg(reinterpret_cast<const ulonglong2 *>(P.table + s));
+        P.table[s].b = key.y & kKeyMaskB;                          // no longer a candidate
+        const XBest x{x_abs_bits(x_gnorm(rc, rb, sS, k1, nullptr)), key.x, key.y & kKeyMaskB, s};
         if (x_better(x, best)) best = x;
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -124,9 +157,9 @@ __global__ void __launch_bounds__(kXThreads) k_x_select(Problem P, XState *xs, I
     *counter = 0u;
     xs->n_cand = 0;
     if (b.slot < 0) { xs->done = 1; xs->eta = 0.0; return; }     // nothing left to choose
-    double row[2 * kXMax], G[kXMax];
-    for (int a = 0; a < 2 * k1; ++a) row[a] = __ldcg(rows + b.slot * 2 * k1 + a);
-    x_gnorm(row, sS, k1, G);
+    double rc[kXMax], rb[kXMax], G[kXMax];
+    x_load_row(rows, b.slot, k1, rc, rb);
+    x_gnorm(rc, rb, sS, k1, G);
     for (int a = 0; a < k1; ++a) xs->g[a] = G[a];
     xs->slot = b.slot; xs->A = b.a; xs->B = b.b;
 }
@@ -285,33 +318,6 @@ __global__ void k_x_prepare(Problem P, XState *xs, IterState *st, double *rows, 
     }
 }
 
-// Row j of C and of B (k1 values each) into cv and bv, all loads in flight
-// together: 16-byte loads when k1 is even (each half is then whole pairs, and
-// a row starts at a multiple of 16 bytes), else 8-byte ones.  The scatter is
-// bound by the number of memory requests its elements make at once.
-__device__ __forceinline__ void x_load_row(const double *rows, long long j, int k1, double (&cv)[kXMax],
-                                           double (&bv)[kXMax]) {
-    const double *r = rows + j * 2 * k1;
-    if ((k1 & 1) == 0) {                                             // uniform
-        const double2 *r2 = reinterpret_cast<const double2 *>(r);
-#pragma unroll
-        for (int q = 0; q < kXMax / 2; ++q) {
-            double2 c2 = make_double2(0.0, 0.0), b2 = c2;
-            if (2 * q < k1) {
-                c2 = __ldcg(r2 + q);
-                b2 = __ldcg(r2 + k1 / 2 + q);
-            }
-            cv[2 * q] = c2.x; cv[2 * q + 1] = c2.y;
-            bv[2 * q] = b2.x; bv[2 * q + 1] = b2.y;
-        }
-        return;
-    }
-#pragma unroll
-    for (int a = 0; a < kXMax; ++a) {
-        cv[a] = a < k1 ? __ldcg(r + a) : 0.0;
-        bv[a] = a < k1 ? __ldcg(r + k1 + a) : 0.0;
-    }
-}
 
 // The slot of key {a, b} by linear probing from pos (no insert): -1 absent, -2
 // error (status set); kbo receives the slot's b word, candidate mark included.
