@@ -74,9 +74,25 @@ constexpr int kXThreads = 256;
 // together: 16-byte loads when k1 is even (each half is then whole pairs, and
 // a row starts at a multiple of 16 bytes), else 8-byte ones.  The scatter is
 // bound by the number of memory requests its elements make at once.
+__device__ __forceinline__ void x_ld32(const double *p, double &a, double &b, double &c, double &d) {
+    asm volatile("ld.global.cg.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a), "=d"(b), "=d"(c), "=d"(d) : "l"(p));
+}
 __device__ __forceinline__ void x_load_row(const double *rows, long long j, int k1, double (&cv)[kXMax],
                                            double (&bv)[kXMax]) {
     const double *r = rows + j * 2 * k1;
+    if ((k1 & 3) == 0) {                                             // uniform: 32-byte loads (halves 32-byte aligned)
+#pragma unroll
+        for (int q = 0; q < kXMax / 4; ++q) {
+            double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+            if (4 * q < k1) {
+                x_ld32(r + 4 * q, c0, c1, c2, c3);
+                x_ld32(r + k1 + 4 * q, b0, b1, b2, b3);
+            }
+            cv[4 * q] = c0; cv[4 * q + 1] = c1; cv[4 * q + 2] = c2; cv[4 * q + 3] = c3;
+            bv[4 * q] = b0; bv[4 * q + 1] = b1; bv[4 * q + 2] = b2; bv[4 * q + 3] = b3;
+        }
+        return;
+    }
     if ((k1 & 1) == 0) {                                             // uniform
         const double2 *r2 = reinterpret_cast<const double2 *>(r);
 #pragma unroll
@@ -397,7 +413,14 @@ __global__ void __launch_bounds__(kXThreads) k_x_scatter(Problem P, XState *xs, 
             bn[a] = fma(H, sw[a], rb[a]);
             if (a < k1) gat[a] = fma(H, cj[a], gat[a]);
         }
-        if ((k1 & 1) == 0) {                                          // 16-byte stores (see x_load_row)
+        if ((k1 & 3) == 0) {                                          // 32-byte stores (see x_load_row)
+#pragma unroll
+            for (int q = 0; q < kXMax / 4; ++q)
+                if (4 * q < k1)
+                    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(br + 4 * q), "d"(bn[4 * q]),
+                                 "d"(bn[4 * q + 1]), "d"(bn[4 * q + 2]), "d"(bn[4 * q + 3])
+                                 : "memory");
+        } else if ((k1 & 1) == 0) {                                   // 16-byte stores (see x_load_row)
 #pragma unroll
             for (int q = 0; q < kXMax / 2; ++q)
                 if (2 * q < k1) reinterpret_cast<double2 *>(br)[q] = make_double2(bn[2 * q], bn[2 * q + 1]);
