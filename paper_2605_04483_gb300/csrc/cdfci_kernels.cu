@@ -211,6 +211,15 @@ __device__ __forceinline__ double single_sum(const double *row, int nocc, unsign
 
 // Decode element e (singles and opposite-spin doubles from the tables) and
 // issue the load of its first probe slot (32 bytes).
+// A whole 32-byte slot {key, c, b} in one request (two 16-byte loads of one
+// slot are two DRAM accesses on this memory system); L2 only.
+__device__ __forceinline__ void ld_slot32(const Slot *s, ulonglong2 &k, double2 &cb) {
+    unsigned long long c, b;
+    asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(k.x), "=l"(k.y), "=l"(c), "=l"(b) : "l"(s));
+    cb.x = __longlong_as_double((long long)c);
+    cb.y = __longlong_as_double((long long)b);
+}
+
 __device__ __forceinline__ void issue_elem(const Problem &P, const ColLists &L, const SingleEnt *tabA,
                                            const SingleEnt *tabB, unsigned long long iA, unsigned long long iB,
                                            unsigned long long hA, unsigned long long hB, long long e, long long nh,
@@ -248,8 +257,7 @@ __device__ __forceinline__ void issue_elem(const Problem &P, const ColLists &L, 
     if (have_prev && x.ka == pA && x.kb == pB) { x.state = 3; return; }
     x.pos = (long long)(h & P.mask);
     const Slot *s = P.table + x.pos;
-    x.k0 = __ldcg(reinterpret_cast<const ulonglong2 *>(s));
-    x.cb0 = __ldcg(reinterpret_cast<const double2 *>(&s->c));
+    ld_slot32(s, x.k0, x.cb0);
     x.state = 4;
 }
 
@@ -267,14 +275,12 @@ __device__ __forceinline__ void resolve_elem(const Problem &P, IterState *st, El
         int spins = 0;
         while (both_nonzero && ((k.x == 0ull) != (k.y == 0ull))) {
             if (++spins > (1 << 20)) { set_status(st, kErrTimeout); *err = 1; x.state = 0; return; }
-            k = __ldcg(reinterpret_cast<const ulonglong2 *>(P.table + p));
-            cb = __ldcg(reinterpret_cast<const double2 *>(&P.table[p].c));
+            ld_slot32(P.table + p, k, cb);
         }
         if (k.x == x.ka && (k.y & kKeyMaskB) == x.kb) { x.pos = (long long)p; x.cb0 = cb; x.state = 1; return; }
         if (k.x == 0ull && k.y == 0ull) { x.pos = (long long)p; x.state = 2; return; }
         p = (p + 1) & P.mask;
-        k = __ldcg(reinterpret_cast<const ulonglong2 *>(P.table + p));
-        cb = __ldcg(reinterpret_cast<const double2 *>(&P.table[p].c));
+        ld_slot32(P.table + p, k, cb);
     }
     set_status(st, kErrTableFull);
     *err = 1;
