@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <chrono>
@@ -17,6 +18,15 @@
 #include "cdfci_kernels.h"
 
 using namespace cdfci;
+
+// The grid-wide m = 1 loop exchanges a CdPartial as 32-bit halves in this field
+// order (the loop kernel's xchg_unpack reads them back by offset).
+static_assert(offsetof(CdPartial, gather) == 0 && offsetof(CdPartial, gbits) == 8 && offsetof(CdPartial, ka) == 16 &&
+                  offsetof(CdPartial, kb) == 24 && offsetof(CdPartial, slot) == 32 && offsetof(CdPartial, bj) == 40 &&
+                  offsetof(CdPartial, cj) == 48 && offsetof(CdPartial, elements) == 56 &&
+                  offsetof(CdPartial, applied) == 60 && offsetof(CdPartial, dropped) == 64 &&
+                  offsetof(CdPartial, inserted) == 68 && offsetof(CdPartial, err) == 72,
+              "CdPartial layout of the partial exchange");
 
 namespace {
 

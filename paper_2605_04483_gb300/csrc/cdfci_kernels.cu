@@ -417,7 +417,8 @@ __device__ __forceinline__ bool xchg_check(const unsigned long long (&w)[kXchgWo
 __device__ __forceinline__ unsigned long long xchg_u64(const unsigned long long (&w)[kXchgWords], int k) {
     return (w[k] & 0xffffffffull) | (w[k + 1] << 32);
 }
-// the partial from its words (the field order of CdPartial, low half first)
+// the partial from its words (the field order of CdPartial, low half first;
+// cdfci_api.cu asserts that layout)
 __device__ __forceinline__ CdPartial xchg_unpack(const unsigned long long (&w)[kXchgWords]) {
     CdPartial x;
     x.gather = __longlong_as_double((long long)xchg_u64(w, 0));
