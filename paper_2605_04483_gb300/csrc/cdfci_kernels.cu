@@ -41,43 +41,13 @@ __device__ __forceinline__ bool better(unsigned long long g1, unsigned long long
     return g1 > g2 || (g1 == g2 && key_less(a1, b1, a2, b2));
 }
 
-// warp argmax of (gbits desc, key asc) + sum of `acc`; result valid in lane 0
+// a candidate of the argmax of (gbits desc, key asc)
 struct Best {
     unsigned long long g, a, b;
     long long slot;
 };
-__device__ __forceinline__ void warp_best(Best &x) {
-    for (int off = 16; off > 0; off >>= 1) {
-        Best y;
-        y.g = __shfl_down_sync(0xffffffffu, x.g, off);
-        y.a = __shfl_down_sync(0xffffffffu, x.a, off);
-        y.b = __shfl_down_sync(0xffffffffu, x.b, off);
-        y.slot = __shfl_down_sync(0xffffffffu, x.slot, off);
-        if (better(y.g, y.a, y.b, x.g, x.a, x.b)) x = y;
-    }
-}
 __device__ __forceinline__ double warp_sum(double x) {
     for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    return x;
-}
-__device__ __forceinline__ int warp_isum(int x) {
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    return x;
-}
-
-__device__ __forceinline__ CdPartial load_partial(const CdPartial *p) {
-    CdPartial x;
-    x.gather = __ldcg(&p->gather);
-    x.gbits = __ldcg(&p->gbits);
-    x.ka = __ldcg(&p->ka);
-    x.kb = __ldcg(&p->kb);
-    x.slot = __ldcg(&p->slot);
-    x.bj = __ldcg(&p->bj);
-    x.cj = __ldcg(&p->cj);
-    x.elements = __ldcg(&p->elements);
-    x.applied = __ldcg(&p->applied);
-    x.dropped = __ldcg(&p->dropped);
-    x.inserted = __ldcg(&p->inserted);
     return x;
 }
 
